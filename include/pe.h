@@ -1,0 +1,213 @@
+/*
+ * pe.h -- C-ABI of libpe, a GB300 (sm_103a) implementation of the data-parallel
+ * hot path of the Parareal exponential-integrator Q1 finite element method
+ * (PEIFE-linear) of Huang & Xu, arXiv 2412.01138.
+ *
+ * Problem (Sec. 2, Eq. (1-1) with homogeneous Dirichlet data, Eq. (3-1)):
+ *     u_t = D Lap u + f(t, x)  on a rectangle  Omega = prod_a (lo_a, hi_a),
+ *     u = 0 on the boundary,  u(t0) = u0,  t in [t0, t0 + T].
+ * Space: Q1 elements on a uniform grid with n_a interior nodes per axis
+ * (h_a = (hi_a - lo_a)/(n_a + 1)), Sec. 2.1.  The mass and stiffness matrices
+ * are diagonalised at once by the orthonormal tensor DST-I V = kron_a S_a
+ * (closing paragraph of Sec. 2.3), which turns the semi-discrete system
+ * Eq. (1-5) into independent scalar ODEs c_J' = -lam_J c_J + ghat_J(t).
+ * Time: the exponential Runge-Kutta step Eq. (1-7) with weights Eq. (3-12);
+ * coarse propagator G = one step of dT = T/N with p nodes, fine propagator
+ * F^M = M steps of dt = dT/M with q nodes, combined by Algorithm 1.
+ *
+ * Array layout: nodal and modal arrays are C-ordered, shape (n_0, .., n_{d-1}),
+ * axis d-1 contiguous, float64 unless stated.  Slice arrays are [N+1][Ndof].
+ *
+ * Ownership: the caller owns every buffer it passes; the library copies what
+ * it needs during the call and keeps no caller pointer.  A pointer argument
+ * may be host or device memory wherever a comment says "host or device"; the
+ * library inspects it with cudaPointerGetAttributes.  All device work is
+ * issued on the stream given in pe_options (NULL: the legacy default stream);
+ * every call that returns data to a host pointer synchronises that stream.
+ *
+ * Errors: every function returns a pe_status; no exception crosses the ABI.
+ * pe_last_error() returns a message for the most recent failure on the
+ * calling thread.  A context is not thread-safe: use one per thread.
+ */
+#ifndef PE_H
+#define PE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pe_ctx pe_ctx; /* opaque; owns its device memory */
+
+typedef enum {
+  PE_OK = 0,
+  PE_EINVAL = -1,      /* invalid argument (sizes, D <= 0, duplicate nodes, ...) */
+  PE_ENOMEM = -2,      /* device or host allocation failed */
+  PE_ECUDA = -3,       /* a CUDA call failed; message in pe_last_error() */
+  PE_ENOCONV = -4,     /* pe_solve: residual above tol after max_iter iterations */
+  PE_ENONFINITE = -5,  /* a NaN/Inf reached the Parareal residual */
+  PE_ETIMEOUT = -6,    /* a bounded device-side wait expired */
+  PE_ESTATE = -7       /* call out of order (e.g. iterate before a problem is set) */
+} pe_status;
+
+/* precision of the fine propagator (pe_options.precision) */
+enum { PE_FP64 = 0,   /* every step in float64 */
+       PE_MIXED = 1   /* fine stages in float32 on the zero-start forced part, the
+                         homogeneous part e^{-lam M dt} v, tables, correction and
+                         residual in float64 */ };
+
+/* DST-I backend (pe_options.dst_backend) */
+enum { PE_DST_AUTO = 0, PE_DST_MATRIX = 1 };
+
+/* separable factor kinds: spatial  S_ONE 1 | S_SIN sin(p0 x + p1) |
+ * S_GAUSS exp(-(x-p0)^2/(2 p1^2)) | S_POLY p0 + p1 x + p2 x^2 + p3 x^3;
+ * time  T_EXP exp(p0 t) | T_SIN sin(p0 t + p1) */
+enum { PE_S_ONE = 0, PE_S_SIN = 1, PE_S_GAUSS = 2, PE_S_POLY = 3 };
+enum { PE_T_EXP = 0, PE_T_SIN = 1 };
+
+/* One separable term  amp * time(t) * prod_{a<d} spatial_a(x_a). */
+typedef struct {
+  double amp;
+  int32_t tkind;
+  double tp[2];
+  int32_t skind[3];
+  double sp[3][4];
+} pe_term;
+
+/* Interpolation nodes c_1..c_s in [0,1] of one exponential RK tableau (Eq. (1-7)).
+ * c == NULL and random == 0: c_i = (i-1)/s.  random != 0: s nodes drawn from
+ * SplitMix64(seed) as doubles (x >> 11) * 2^-53, sorted, the whole set redrawn
+ * while two nodes are closer than 1e-3 (Theorem 3.1 holds for any distinct
+ * nodes).  Nodes must be distinct (Lagrange basis of Eq. (3-12)): else PE_EINVAL. */
+typedef struct {
+  int32_t s;          /* 1 <= s <= 8 */
+  const double* c;    /* host, s values, or NULL */
+  int32_t random;
+  uint64_t seed;
+} pe_tableau;
+
+typedef struct {
+  int32_t precision;    /* PE_FP64 | PE_MIXED */
+  int32_t dst_backend;  /* PE_DST_AUTO | PE_DST_MATRIX */
+  int32_t quad_pts;     /* Gauss points per axis per element for loads (1..8, 0 = 3) */
+  int32_t max_iter;     /* pe_solve iteration cap, 0 = N (Theorem 4.3: k = N is exact) */
+  void* cuda_stream;    /* cudaStream_t or NULL */
+} pe_options;
+
+/* Initial data: u0 = sum of separable terms (time factors ignored), projected
+ * onto V_h by P_h (L2 projection, Eq. (3-11)), or nodal values of a V_h function. */
+enum { PE_FIELD_TERMS_SEPARABLE = 0, /* P_h by per-axis 1D loads and 1D DST-I */
+       PE_FIELD_TERMS_QUADRATURE = 1, /* P_h by d-D element quadrature + d-D DST-I */
+       PE_FIELD_NODAL = 2 };          /* u0 already in V_h: c0 = V^T u0 */
+typedef struct {
+  int32_t kind;
+  int32_t n_terms;
+  const pe_term* terms;  /* host */
+  const double* nodal;   /* host or device, Ndof values (kind == PE_FIELD_NODAL) */
+} pe_field;
+
+/* Source f = sum of separable terms (host array, 0 <= n_terms <= PE_MAX_TERMS). */
+#define PE_MAX_TERMS 32
+typedef struct {
+  int32_t n_terms;
+  const pe_term* terms;
+} pe_forcing;
+
+typedef struct {
+  int32_t k;                 /* Parareal iterations performed */
+  double residual;           /* last relative residual r_k (defined at pe_parareal_iter) */
+  double* residual_history;  /* host, caller-owned, capacity history_cap (may be NULL) */
+  int32_t history_cap;
+  int64_t fine_sweeps;       /* fine propagator sweeps executed (= k) */
+  double ms_tables;          /* device time of the phi/b coefficient tables */
+  double ms_prepare;         /* forcing tables, projection of u0, coarse sweep */
+  double ms_iterations;      /* all fine sweeps + corrections + residuals */
+  double ms_output;          /* inverse DST of the final slice */
+} pe_result;
+
+/*
+ * pe_setup -- validate the problem, allocate the context and its device memory
+ * (slice arrays U, G(U) and F^M(U) of N x Ndof float64 each, plus tables).
+ * d in 1..3; n: host int32[d], n_a >= 1; box: host double[2d] as lo0,hi0,lo1,hi1,..;
+ * D > 0; T > 0; n_slices = N >= 1; n_substeps = M >= 1; fine (q nodes) and
+ * coarse (p nodes) tableaux; opt may be NULL (defaults).  On success *out owns
+ * everything; release with pe_destroy.
+ */
+pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const double* box, double D,
+                   double t0, double T, int32_t n_slices, int32_t n_substeps,
+                   const pe_tableau* fine, const pe_tableau* coarse, const pe_options* opt);
+
+/*
+ * pe_set_problem -- Algorithm 1 up to its loop: compute lam_J (Sec. 2.3) and the
+ * phi/b tables (Eq. (3-12)) for the fine and coarse steps, the modal factors of
+ * P_h f (outer products of 1D projections of each separable term), U^0 = P_h u0,
+ * and the coarse sweep U^{n+1,(0)} = G(U^{n,(0)}).  Sets k = 0.
+ */
+pe_status pe_set_problem(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f);
+
+/*
+ * pe_parareal_iter -- one pass of Algorithm 1's loop: the fine propagator from
+ * every slice start in parallel, then the sequential correction
+ *   U^{n+1,(k+1)} = G(U^{n,(k+1)}) + F^M(U^{n,(k)}) - G(U^{n,(k)}),
+ * and the relative residual
+ *   r = sqrt(sum_{n=1}^N ||U^{n,(k+1)} - U^{n,(k)}||_0^2) / sqrt(sum_{n=1}^N ||U^{n,(k+1)}||_0^2)
+ * in float64 (the paper leaves the stopping rule open; this relative residual is the rule used).
+ * rel_residual_out: host, may be NULL.  Returns PE_ENONFINITE if a sum is not finite.
+ */
+pe_status pe_parareal_iter(pe_ctx* ctx, double* rel_residual_out);
+
+/*
+ * pe_solve -- pe_set_problem, then pe_parareal_iter until r <= tol or k = N
+ * (or max_iter), then the inverse DST of U^N into the context's output buffer
+ * (read with pe_get_solution).  Returns PE_ENOCONV if max_iter < N stopped it
+ * above tol.  out may be NULL.
+ */
+pe_status pe_solve(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f, double tol, pe_result* out);
+
+/* Nodal values u_h(T_slice) = V U^{slice} (slice in 0..N) into nodal_out (host or device, Ndof). */
+pe_status pe_get_solution(pe_ctx* ctx, int32_t slice, double* nodal_out);
+
+/* Modal coefficients U^{slice} (slice in 0..N) into modal_out (host or device, Ndof). */
+pe_status pe_get_modal(pe_ctx* ctx, int32_t slice, double* modal_out);
+
+/* lam_J into out (host or device, Ndof): lam_J = D sum_a mu^K_a(j_a)/mu^M_a(j_a). */
+pe_status pe_get_lambda(pe_ctx* ctx, double* out);
+
+/* Coefficient table of one propagator (which = 0 fine, 1 coarse) into out (host or
+ * device, (s+1) x Ndof): row 0 = e^{-lam tau}, row 1+i = tau * b_i(-lam tau). */
+pe_status pe_get_coefficients(pe_ctx* ctx, int32_t which, double* out);
+
+/* Modal coefficients of P_h f(t) into out (host or device, Ndof); needs a problem. */
+pe_status pe_forcing_modal(pe_ctx* ctx, double t, double* out);
+
+/* Interpolation nodes actually used (which = 0 fine, 1 coarse) into host c_out[s]. */
+pe_status pe_get_nodes(pe_ctx* ctx, int32_t which, double* c_out);
+
+/* Parareal state (k, U, G(U)) to / from a host buffer: resume gives identical results.
+ * pe_save_state with buf == NULL reports the size in *bytes. */
+pe_status pe_save_state(pe_ctx* ctx, void* buf, size_t* bytes);
+pe_status pe_load_state(pe_ctx* ctx, const void* buf, size_t bytes);
+
+/*
+ * pe_dst -- orthonormal tensor DST-I (S_a[k][j] = sqrt(2/(n_a+1)) sin(pi j k/(n_a+1)))
+ * applied along every axis of a C-ordered float64 array: out = (kron_a S_a) in.
+ * V is symmetric and orthogonal, so the same call is the forward and the inverse
+ * transform (Sec. 2.3).  in/out: device, Ndof values, may alias.  d in 1..3.
+ * stream: cudaStream_t or NULL.
+ */
+pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, void* stream);
+
+/* Same transform in float32 (device in/out). */
+pe_status pe_dst_f32(int32_t d, const int32_t* n, const float* in, float* out, void* stream);
+
+/* Most recent error message on this thread ("" if none). */
+const char* pe_last_error(void);
+
+void pe_destroy(pe_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PE_H */

@@ -66,22 +66,27 @@ def assemble(n, box, D):
 def dst1_matrix(n: int) -> np.ndarray:
     """Orthonormal DST-I: S[k-1, j-1] = sqrt(2/(n+1)) sin(j k pi/(n+1)).
 
-    S is symmetric and S @ S = I.
+    S is symmetric and S @ S = I.  The integer j*k is reduced modulo 2(n+1)
+    (the period of the sine in that index) before it is scaled by pi/(n+1),
+    so every argument lies in [0, 2 pi) and carries no large rounding error.
     """
-    k = np.arange(1, n + 1, dtype=np.float64)
-    return np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(k, k) * np.pi / (n + 1))
+    k = np.arange(1, n + 1, dtype=np.int64)
+    m = np.outer(k, k) % (2 * (n + 1))
+    return np.sqrt(2.0 / (n + 1)) * np.sin(m.astype(np.float64) * np.pi / (n + 1))
 
 
 def axis_eigenvalues(n: int, h: float):
     """Closed-form eigenvalues of the 1D mass and stiffness matrices in the DST-I basis.
 
     With theta_j = j pi/(n+1):  mu^M_j = (h/3)(2 + cos theta_j),
-    mu^K_j = (2/h)(1 - cos theta_j), so that S M_a S = diag(mu^M),
-    S K_a S = diag(mu^K).
+    mu^K_j = (2/h)(1 - cos theta_j) = (4/h) sin^2(theta_j/2), so that
+    S M_a S = diag(mu^M), S K_a S = diag(mu^K).  mu^K is evaluated in the
+    sin^2 form, which keeps full relative precision for the slow modes
+    (1 - cos theta_1 cancels to ~1e-12 relative at n = 255).
     """
     theta = np.arange(1, n + 1, dtype=np.float64) * np.pi / (n + 1)
     muM = (h / 3.0) * (2.0 + np.cos(theta))
-    muK = (2.0 / h) * (1.0 - np.cos(theta))
+    muK = (4.0 / h) * np.sin(0.5 * theta) ** 2
     return muM, muK
 
 
