@@ -1,0 +1,500 @@
+// Host side of libpe: the C-ABI declared in include/pe.h.
+//
+// Validates arguments, owns device memory, and sequences the kernels of
+// Algorithm 1 (PEIFE-linear): tables -> P_h u0 -> coarse sweep -> loop of
+// {fine sweep, correction + residual} -> inverse DST of the last slice.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "pe_internal.h"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+void pe_set_error(const std::string& msg) { g_err = msg; }
+
+pe_status pe_fail(pe_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+pe_status pe_cuda_fail(cudaError_t err, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+  return err == cudaErrorMemoryAllocation ? PE_ENOMEM : PE_ECUDA;
+}
+
+extern "C" const char* pe_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// interpolation nodes
+// ---------------------------------------------------------------------------
+namespace {
+
+// SplitMix64 (Steele, Lea & Flood 2014): counter += golden gamma, two xor-shift-multiply rounds.
+uint64_t splitmix64_next(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+const double kMinNodeGap = 1e-3;
+
+pe_status resolve_nodes(const pe_tableau* tb, const char* name, int* s_out, double* c) {
+  if (!tb) return pe_fail(PE_EINVAL, std::string(name) + " tableau is NULL");
+  const int s = tb->s;
+  if (s < 1 || s > PE_MAX_S) return pe_fail(PE_EINVAL, std::string(name) + " tableau: s must be in 1..8");
+  if (tb->random) {
+    uint64_t state = tb->seed;
+    for (int attempt = 0; attempt < 100000; ++attempt) {
+      for (int i = 0; i < s; ++i) c[i] = (double)(splitmix64_next(state) >> 11) * (1.0 / 9007199254740992.0);
+      std::sort(c, c + s);
+      double gap = 1.0;
+      for (int i = 1; i < s; ++i) gap = std::min(gap, c[i] - c[i - 1]);
+      if (s == 1 || gap >= kMinNodeGap) {
+        *s_out = s;
+        return PE_OK;
+      }
+    }
+    return pe_fail(PE_EINVAL, std::string(name) + " tableau: could not draw separated random nodes");
+  }
+  for (int i = 0; i < s; ++i) c[i] = tb->c ? tb->c[i] : (double)i / (double)s;
+  for (int i = 0; i < s; ++i) {
+    if (!(c[i] >= 0.0 && c[i] <= 1.0)) return pe_fail(PE_EINVAL, std::string(name) + " tableau: nodes must lie in [0,1]");
+    for (int j = 0; j < i; ++j)
+      if (c[i] == c[j]) return pe_fail(PE_EINVAL, std::string(name) + " tableau: nodes must be distinct");
+  }
+  *s_out = s;
+  return PE_OK;
+}
+
+// a[i][m]: coefficient of theta^m in the Lagrange basis polynomial l_i.
+void lagrange_coeffs(int s, const double* c, double a[PE_MAX_S][PE_MAX_S]) {
+  for (int i = 0; i < PE_MAX_S; ++i)
+    for (int m = 0; m < PE_MAX_S; ++m) a[i][m] = 0.0;
+  for (int i = 0; i < s; ++i) {
+    double poly[PE_MAX_S + 1] = {1.0};
+    int deg = 0;
+    for (int m = 0; m < s; ++m) {
+      if (m == i) continue;
+      const double den = c[i] - c[m];
+      double nxt[PE_MAX_S + 1] = {0.0};
+      for (int k = 0; k <= deg; ++k) {
+        nxt[k + 1] += poly[k] / den;
+        nxt[k] -= poly[k] * c[m] / den;
+      }
+      ++deg;
+      for (int k = 0; k <= deg; ++k) poly[k] = nxt[k];
+    }
+    for (int k = 0; k < s; ++k) a[i][k] = poly[k];
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+pe_status dev_alloc(T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return pe_fail(PE_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed");
+  }
+  return PE_OK;
+}
+
+void free_ctx(pe_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->muM_axis, c->ratio_axis, c->S[0], c->S[1], c->S[2], c->lam, c->coefF, c->coefG,
+                  c->coefF32, c->U, c->Gold, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
+                  c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->loads};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  for (int i = 0; i < 8; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  delete c;
+}
+
+pe_status copy_out(pe_ctx* c, const double* src_dev, double* out, size_t count) {
+  if (!out) return pe_fail(PE_EINVAL, "output pointer is NULL");
+  const bool dev = is_device_ptr(out);
+  PE_CUDA_TRY(cudaMemcpyAsync(out, src_dev, sizeof(double) * count,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PE_OK;
+}
+
+pe_status validate_terms(int n, const pe_term* t, int d, const char* what) {
+  if (n < 0 || n > PE_MAX_TERMS) return pe_fail(PE_EINVAL, std::string(what) + ": n_terms must be in 0..32");
+  if (n > 0 && !t) return pe_fail(PE_EINVAL, std::string(what) + ": terms is NULL");
+  for (int i = 0; i < n; ++i) {
+    if (t[i].tkind != PE_T_EXP && t[i].tkind != PE_T_SIN)
+      return pe_fail(PE_EINVAL, std::string(what) + ": unknown time factor kind");
+    for (int a = 0; a < d; ++a) {
+      const int k = t[i].skind[a];
+      if (k < PE_S_ONE || k > PE_S_POLY) return pe_fail(PE_EINVAL, std::string(what) + ": unknown spatial kind");
+      if (k == PE_S_GAUSS && !(t[i].sp[a][1] != 0.0))
+        return pe_fail(PE_EINVAL, std::string(what) + ": Gaussian width must be nonzero");
+    }
+  }
+  return PE_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// setup / destroy
+// ---------------------------------------------------------------------------
+extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const double* box, double D, double t0,
+                              double T, int32_t n_slices, int32_t n_substeps, const pe_tableau* fine,
+                              const pe_tableau* coarse, const pe_options* opt) {
+  if (!out) return pe_fail(PE_EINVAL, "pe_setup: out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > PE_MAX_D) return pe_fail(PE_EINVAL, "pe_setup: d must be 1, 2 or 3");
+  if (!n || !box) return pe_fail(PE_EINVAL, "pe_setup: n or box is NULL");
+  if (!(D > 0.0) || !isfinite(D)) return pe_fail(PE_EINVAL, "pe_setup: D must be positive");
+  if (!(T > 0.0) || !isfinite(T) || !isfinite(t0)) return pe_fail(PE_EINVAL, "pe_setup: T must be positive");
+  if (n_slices < 1 || n_substeps < 1) return pe_fail(PE_EINVAL, "pe_setup: n_slices and n_substeps must be >= 1");
+  if (n_slices > 65535) return pe_fail(PE_EINVAL, "pe_setup: n_slices must be <= 65535");
+  int64_t ndof = 1;
+  int nsum = 0;
+  for (int a = 0; a < d; ++a) {
+    if (n[a] < 1 || n[a] > 16384) return pe_fail(PE_EINVAL, "pe_setup: n_a must be in 1..16384");
+    if (!(box[2 * a + 1] > box[2 * a])) return pe_fail(PE_EINVAL, "pe_setup: box needs lo < hi on every axis");
+    ndof *= n[a];
+    nsum += n[a];
+  }
+  if (ndof > ((int64_t)1 << 31)) return pe_fail(PE_EINVAL, "pe_setup: too many degrees of freedom");
+
+  pe_ctx* c = new (std::nothrow) pe_ctx();
+  if (!c) return pe_fail(PE_ENOMEM, "pe_setup: host allocation failed");
+  for (int i = 0; i < 8; ++i) c->ev[i] = nullptr;
+  c->g.d = d;
+  c->g.ndof = ndof;
+  c->nsum = nsum;
+  int off = 0;
+  for (int a = 0; a < PE_MAX_D; ++a) {
+    c->g.n[a] = a < d ? n[a] : 1;
+    c->g.off[a] = off;
+    if (a < d) {
+      c->lo[a] = box[2 * a];
+      c->hi[a] = box[2 * a + 1];
+      c->h[a] = (c->hi[a] - c->lo[a]) / (double)(n[a] + 1);
+      off += n[a];
+    } else {
+      c->lo[a] = 0.0; c->hi[a] = 1.0; c->h[a] = 1.0;
+    }
+  }
+  c->D = D; c->t0 = t0; c->T = T;
+  c->N = n_slices; c->M = n_substeps;
+  c->dT = T / (double)n_slices;
+  c->dt = c->dT / (double)n_substeps;
+  pe_status st = resolve_nodes(fine, "fine", &c->q, c->cF);
+  if (st == PE_OK) st = resolve_nodes(coarse, "coarse", &c->p, c->cG);
+  if (st != PE_OK) { delete c; return st; }
+  lagrange_coeffs(c->q, c->cF, c->lagF);
+  lagrange_coeffs(c->p, c->cG, c->lagG);
+  pe_options o{};
+  if (opt) o = *opt;
+  if (o.precision != PE_FP64 && o.precision != PE_MIXED) { delete c; return pe_fail(PE_EINVAL, "pe_setup: bad precision"); }
+  if (o.quad_pts == 0) o.quad_pts = 3;
+  if (o.quad_pts < 1 || o.quad_pts > 8) { delete c; return pe_fail(PE_EINVAL, "pe_setup: quad_pts must be in 1..8"); }
+  if (o.max_iter < 0) { delete c; return pe_fail(PE_EINVAL, "pe_setup: max_iter must be >= 0"); }
+  c->precision = o.precision;
+  c->dst_backend = o.dst_backend;
+  c->quad_pts = o.quad_pts;
+  c->max_iter = o.max_iter == 0 ? n_slices : std::min(o.max_iter, n_slices);
+  c->stream = (cudaStream_t)o.cuda_stream;
+
+  const int threads = 256;
+  c->max_blocks = (int)((ndof + threads - 1) / threads) + 1;
+  const size_t N = (size_t)n_slices, nd = (size_t)ndof, MT = PE_MAX_TERMS;
+  st = PE_OK;
+  if (st == PE_OK) st = dev_alloc(&c->muM_axis, nsum);
+  if (st == PE_OK) st = dev_alloc(&c->ratio_axis, nsum);
+  for (int a = 0; a < d && st == PE_OK; ++a) st = dev_alloc(&c->S[a], (size_t)n[a] * n[a]);
+  if (st == PE_OK) st = dev_alloc(&c->lam, nd);
+  if (st == PE_OK) st = dev_alloc(&c->coefF, (size_t)(c->q + 2) * nd);
+  if (st == PE_OK) st = dev_alloc(&c->coefG, (size_t)(c->p + 1) * nd);
+  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->coefF32, (size_t)(c->q + 2) * nd);
+  if (st == PE_OK) st = dev_alloc(&c->U, (N + 1) * nd);
+  if (st == PE_OK) st = dev_alloc(&c->Gold, N * nd);
+  if (st == PE_OK) st = dev_alloc(&c->Fbar, N * nd);
+  if (st == PE_OK) st = dev_alloc(&c->gG, N * nd);
+  if (st == PE_OK) st = dev_alloc(&c->work0, nd + 64);
+  if (st == PE_OK) st = dev_alloc(&c->work1, nd + 64);
+  if (st == PE_OK) st = dev_alloc(&c->out_nodal, nd);
+  if (st == PE_OK) st = dev_alloc(&c->partials, 2 * (size_t)c->max_blocks + 64);
+  if (st == PE_OK) st = dev_alloc(&c->red, 2);
+  if (st == PE_OK) st = dev_alloc(&c->axisF, MT * nsum);
+  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->axisF32, MT * nsum);
+  if (st == PE_OK) st = dev_alloc(&c->axisU0, MT * nsum);
+  if (st == PE_OK) st = dev_alloc(&c->loads, MT * nsum);
+  if (st == PE_OK) st = dev_alloc(&c->AF, N * n_substeps * c->q * MT);
+  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AF32, N * n_substeps * c->q * MT);
+  if (st == PE_OK) st = dev_alloc(&c->AG, N * c->p * MT);
+  if (st == PE_OK && cudaMallocHost((void**)&c->h_red, 4 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");
+  }
+  for (int i = 0; i < 8 && st == PE_OK; ++i)
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = pe_cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  if (st == PE_OK) st = launch_axis_tables(c);
+  for (int a = 0; a < d && st == PE_OK; ++a) st = build_dst_matrix(n[a], c->S[a], c->stream);
+  if (st == PE_OK) st = launch_coef_tables(c);
+  if (st == PE_OK) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_setup");
+  }
+  if (st != PE_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return PE_OK;
+}
+
+extern "C" void pe_destroy(pe_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+// ---------------------------------------------------------------------------
+// problem, iteration, solve
+// ---------------------------------------------------------------------------
+static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
+  if (!u0) return pe_fail(PE_EINVAL, "pe_set_problem: u0 is NULL");
+  const int nf = f ? f->n_terms : 0;
+  PE_TRY(validate_terms(nf, f ? f->terms : nullptr, c->g.d, "forcing"));
+  if (nf == 0) {
+    // no source: one zero term keeps every kernel shape valid
+    c->R = 1;
+    memset(&c->terms[0], 0, sizeof(pe_term));
+  } else {
+    c->R = nf;
+    for (int i = 0; i < nf; ++i) c->terms[i] = f->terms[i];
+  }
+  // coefficient tables (a function of lam, dt, dT and the nodes)
+  PE_TRY(launch_coef_tables(c));
+  PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
+  // forcing: time factors and per-axis modal factors
+  PE_TRY(launch_time_tables(c));
+  PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1));
+  // U^0 = P_h u0
+  double* U0 = c->U;
+  if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {
+    PE_TRY(validate_terms(u0->n_terms, u0->terms, c->g.d, "u0"));
+    if (u0->n_terms == 0) {
+      PE_CUDA_TRY(cudaMemsetAsync(U0, 0, sizeof(double) * c->g.ndof, c->stream));
+    } else if (u0->kind == PE_FIELD_TERMS_SEPARABLE) {
+      PE_TRY(launch_separable_factors(c, u0->terms, u0->n_terms, c->axisU0, 1));
+      PE_TRY(launch_outer_sum(c, c->axisU0, u0->terms, u0->n_terms, U0, 0));
+    } else {
+      // nodal consistent load F = sum_t amp_t kron_a F_{t,a}, then c0 = Lambda_M^{-1} V^T F
+      PE_TRY(launch_separable_factors(c, u0->terms, u0->n_terms, c->axisU0, 0));
+      PE_TRY(launch_outer_sum(c, c->axisU0, u0->terms, u0->n_terms, c->work0, 1));
+      PE_TRY(dst_nd_f64(c, c->work0, U0));
+      PE_TRY(launch_scale_by_muM(c, U0, 1));
+    }
+  } else if (u0->kind == PE_FIELD_NODAL) {
+    if (!u0->nodal) return pe_fail(PE_EINVAL, "pe_set_problem: nodal u0 is NULL");
+    const bool dev = is_device_ptr(u0->nodal);
+    PE_CUDA_TRY(cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->g.ndof,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    PE_TRY(dst_nd_f64(c, c->work0, U0));
+  } else {
+    return pe_fail(PE_EINVAL, "pe_set_problem: unknown u0 kind");
+  }
+  // k = 0: coarse sweep
+  PE_TRY(launch_coarse_sweep(c));
+  c->k = 0;
+  c->have_problem = true;
+  c->have_output = false;
+  return PE_OK;
+}
+
+extern "C" pe_status pe_set_problem(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_set_problem: ctx is NULL");
+  c->have_problem = false;
+  PE_CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
+  PE_TRY(set_problem_impl(c, u0, f));
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PE_OK;
+}
+
+static pe_status iter_impl(pe_ctx* c, double* r_out) {
+  PE_TRY(launch_fine_sweep(c));
+  double num = 0.0, den = 0.0;
+  PE_TRY(launch_correction(c, &num, &den));
+  c->k += 1;
+  if (!isfinite(num) || !isfinite(den)) {
+    c->have_problem = false;
+    return pe_fail(PE_ENONFINITE, "Parareal residual is not finite (NaN/Inf in the iterate)");
+  }
+  const double r = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+  if (r_out) *r_out = r;
+  return PE_OK;
+}
+
+extern "C" pe_status pe_parareal_iter(pe_ctx* c, double* rel_residual_out) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_parareal_iter: ctx is NULL");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_parareal_iter: no problem set (call pe_set_problem)");
+  c->have_output = false;
+  return iter_impl(c, rel_residual_out);
+}
+
+extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, pe_result* res) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_solve: ctx is NULL");
+  if (!(tol >= 0.0)) return pe_fail(PE_EINVAL, "pe_solve: tol must be >= 0");
+  c->have_problem = false;
+  PE_CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
+  PE_TRY(set_problem_impl(c, u0, f));
+  PE_CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
+  double r = INFINITY;
+  int hist = 0;
+  while (c->k < c->max_iter) {
+    PE_TRY(iter_impl(c, &r));
+    if (res && res->residual_history && hist < res->history_cap) res->residual_history[hist] = r;
+    ++hist;
+    if (r <= tol) break;
+  }
+  PE_CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
+  PE_TRY(dst_nd_f64(c, c->U + (int64_t)c->N * c->g.ndof, c->out_nodal));
+  PE_CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->have_output = true;
+  if (res) {
+    res->k = c->k;
+    res->residual = r;
+    res->fine_sweeps = c->k;
+    res->ms_tables = elapsed(c->ev[0], c->ev[1]);
+    res->ms_prepare = elapsed(c->ev[1], c->ev[2]);
+    res->ms_iterations = elapsed(c->ev[2], c->ev[3]);
+    res->ms_output = elapsed(c->ev[3], c->ev[4]);
+  }
+  if (r > tol && c->k < c->N) return pe_fail(PE_ENOCONV, "pe_solve: residual above tol after max_iter iterations");
+  return PE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// getters, state
+// ---------------------------------------------------------------------------
+extern "C" pe_status pe_get_solution(pe_ctx* c, int32_t slice, double* nodal_out) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_get_solution: ctx is NULL");
+  if (slice < 0 || slice > c->N) return pe_fail(PE_EINVAL, "pe_get_solution: slice out of range");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_get_solution: no problem set");
+  if (slice == c->N && c->have_output) return copy_out(c, c->out_nodal, nodal_out, c->g.ndof);
+  PE_TRY(dst_nd_f64(c, c->U + (int64_t)slice * c->g.ndof, c->work0));
+  return copy_out(c, c->work0, nodal_out, c->g.ndof);
+}
+
+extern "C" pe_status pe_get_modal(pe_ctx* c, int32_t slice, double* modal_out) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_get_modal: ctx is NULL");
+  if (slice < 0 || slice > c->N) return pe_fail(PE_EINVAL, "pe_get_modal: slice out of range");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_get_modal: no problem set");
+  return copy_out(c, c->U + (int64_t)slice * c->g.ndof, modal_out, c->g.ndof);
+}
+
+extern "C" pe_status pe_get_lambda(pe_ctx* c, double* out) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_get_lambda: ctx is NULL");
+  return copy_out(c, c->lam, out, c->g.ndof);
+}
+
+extern "C" pe_status pe_get_coefficients(pe_ctx* c, int32_t which, double* out) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_get_coefficients: ctx is NULL");
+  if (which == 0) return copy_out(c, c->coefF, out, (size_t)(c->q + 1) * c->g.ndof);
+  if (which == 1) return copy_out(c, c->coefG, out, (size_t)(c->p + 1) * c->g.ndof);
+  return pe_fail(PE_EINVAL, "pe_get_coefficients: which must be 0 (fine) or 1 (coarse)");
+}
+
+extern "C" pe_status pe_forcing_modal(pe_ctx* c, double t, double* out) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_forcing_modal: ctx is NULL");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_forcing_modal: no problem set");
+  PE_TRY(launch_forcing_modal(c, t, c->work0));
+  return copy_out(c, c->work0, out, c->g.ndof);
+}
+
+extern "C" pe_status pe_get_nodes(pe_ctx* c, int32_t which, double* c_out) {
+  if (!c || !c_out) return pe_fail(PE_EINVAL, "pe_get_nodes: NULL argument");
+  if (which == 0) memcpy(c_out, c->cF, sizeof(double) * c->q);
+  else if (which == 1) memcpy(c_out, c->cG, sizeof(double) * c->p);
+  else return pe_fail(PE_EINVAL, "pe_get_nodes: which must be 0 or 1");
+  return PE_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  int32_t d, N, k, pad;
+  int64_t ndof;
+  int32_t n[3], pad2;
+};
+const uint64_t kStateMagic = 0x3130353135504550ull;  // "PEP51501"
+}  // namespace
+
+extern "C" pe_status pe_save_state(pe_ctx* c, void* buf, size_t* bytes) {
+  if (!c || !bytes) return pe_fail(PE_EINVAL, "pe_save_state: NULL argument");
+  const size_t nd = (size_t)c->g.ndof, N = (size_t)c->N;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * ((N + 1) * nd + N * nd);
+  if (!buf) {
+    *bytes = need;
+    return PE_OK;
+  }
+  if (*bytes < need) return pe_fail(PE_EINVAL, "pe_save_state: buffer too small");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_save_state: no problem set");
+  StateHeader h{};
+  h.magic = kStateMagic;
+  h.d = c->g.d; h.N = c->N; h.k = c->k; h.ndof = c->g.ndof;
+  for (int a = 0; a < 3; ++a) h.n[a] = c->g.n[a];
+  memcpy(buf, &h, sizeof(h));
+  char* p = (char*)buf + sizeof(h);
+  PE_CUDA_TRY(cudaMemcpyAsync(p, c->U, sizeof(double) * (N + 1) * nd, cudaMemcpyDeviceToHost, c->stream));
+  PE_CUDA_TRY(cudaMemcpyAsync(p + sizeof(double) * (N + 1) * nd, c->Gold, sizeof(double) * N * nd,
+                              cudaMemcpyDeviceToHost, c->stream));
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  *bytes = need;
+  return PE_OK;
+}
+
+extern "C" pe_status pe_load_state(pe_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return pe_fail(PE_EINVAL, "pe_load_state: NULL argument");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_load_state: set the same problem first (pe_set_problem)");
+  const size_t nd = (size_t)c->g.ndof, N = (size_t)c->N;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * ((N + 1) * nd + N * nd);
+  if (bytes < need) return pe_fail(PE_EINVAL, "pe_load_state: buffer too small");
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.d != c->g.d || h.N != c->N || h.ndof != c->g.ndof)
+    return pe_fail(PE_EINVAL, "pe_load_state: state does not match this context");
+  const char* p = (const char*)buf + sizeof(h);
+  PE_CUDA_TRY(cudaMemcpyAsync(c->U, p, sizeof(double) * (N + 1) * nd, cudaMemcpyHostToDevice, c->stream));
+  PE_CUDA_TRY(cudaMemcpyAsync(c->Gold, p + sizeof(double) * (N + 1) * nd, sizeof(double) * N * nd,
+                              cudaMemcpyHostToDevice, c->stream));
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->k = h.k;
+  c->have_output = false;
+  return PE_OK;
+}

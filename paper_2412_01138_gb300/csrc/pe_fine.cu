@@ -1,0 +1,16 @@
+// Dispatch of the fine propagator sweep over the number of forcing terms R
+// (kernels in pe_fine_kernels.cuh, instantiated in pe_fine_rXX_YY.cu).
+#include "pe_internal.h"
+#include "pe_sweep_common.cuh"
+
+template <int R>
+pe_status fine_launch(pe_ctx* c);
+
+namespace {
+template <int R>
+struct FineLaunch {
+  static pe_status run(pe_ctx* c) { return fine_launch<R>(c); }
+};
+}  // namespace
+
+pe_status launch_fine_sweep(pe_ctx* c) { return dispatch_R<FineLaunch>(c->R, c); }

@@ -1,0 +1,265 @@
+// The load P_h f in mode space for separable sources, and the projection of u0.
+//
+// P_h is the L2 projection (Sec. 2.1, Eq. (3-11)); its modal coefficients are
+// ghat = Lambda_M^{-1} V^T F with F_k = (f, phi_k) the consistent load.  For a
+// separable term amp * time(t) * prod_a g_a(x_a) the load is the outer product
+// of 1D loads F_a[k] = int g_a phi_k, so
+//   ghat_J(t) = sum_r amp_r time_r(t) prod_a (S_a F_{r,a})_{j_a} / mu^M_a(j_a).
+// 1D loads use a Gauss-Legendre rule with quad_pts points on each element.
+// The per-axis modal factors and the time factors at every stage time of the
+// fine and coarse steps (Eq. (1-7)) are tabulated here; the sweeps multiply
+// them together on the fly.
+#include <math.h>
+
+#include "pe_internal.h"
+
+namespace {
+
+struct TermsDev {
+  int n;
+  pe_term t[PE_MAX_TERMS];
+};
+
+struct Nodes {
+  double c[PE_MAX_S];
+};
+
+struct Gauss {
+  int npts;
+  double s[8];  // nodes in [0,1]
+  double w[8];  // weights summing to 1
+};
+
+__device__ inline double eval_space(int kind, const double* p, double x) {
+  switch (kind) {
+    case PE_S_SIN: return sin(p[0] * x + p[1]);
+    case PE_S_GAUSS: { const double u = x - p[0]; return exp(-(u * u) / (2.0 * p[1] * p[1])); }
+    case PE_S_POLY: return p[0] + x * (p[1] + x * (p[2] + x * p[3]));
+    default: return 1.0;
+  }
+}
+
+__device__ inline double eval_time(const pe_term& t, double tt) {
+  if (t.tkind == PE_T_SIN) return sin(t.tp[0] * tt + t.tp[1]);
+  return exp(t.tp[0] * tt);
+}
+
+// AF[((n*M + m)*q + i)*R + r] and AG[(n*p + i)*R + r]
+__global__ void time_tables_kernel(TermsDev T, int N, int M, int q, int p, double t0, double dT, double dt,
+                                   Nodes cF, Nodes cG, double* __restrict__ AF, float* __restrict__ AF32,
+                                   double* __restrict__ AG) {
+  const int R = T.n;
+  const int64_t nf = (int64_t)N * M * q * R;
+  const int64_t ng = (int64_t)N * p * R;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < nf) {
+    int64_t rest = idx;
+    const int r = (int)(rest % R); rest /= R;
+    const int i = (int)(rest % q); rest /= q;
+    const int m = (int)(rest % M); rest /= M;
+    const int n = (int)rest;
+    const double Tn = t0 + (double)n * dT;
+    const double tl = Tn + (double)m * dt;
+    const double t = tl + cF.c[i] * dt;
+    const double v = T.t[r].amp * eval_time(T.t[r], t);
+    AF[idx] = v;
+    if (AF32) AF32[idx] = (float)v;
+  } else if (idx < nf + ng) {
+    int64_t rest = idx - nf;
+    const int r = (int)(rest % R); rest /= R;
+    const int i = (int)(rest % p); rest /= p;
+    const int n = (int)rest;
+    const double Tn = t0 + (double)n * dT;
+    const double t = Tn + cG.c[i] * dT;
+    AG[idx - nf] = T.t[r].amp * eval_time(T.t[r], t);
+  }
+}
+
+// 1D consistent loads of every (term, axis): out[R*off[a] + r*n_a + k] = int g_{r,a} phi_{k+1}.
+__global__ void loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2, double h0, double h1,
+                                double h2, Gauss G, double* __restrict__ out) {
+  const int a = blockIdx.z;
+  const int r = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // 0-based node, node number k+1
+  if (a >= g.d || r >= T.n || k >= g.n[a]) return;
+  const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
+  const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
+  const pe_term& t = T.t[r];
+  // element k spans nodes k, k+1 (this node is its right vertex: shape s);
+  // element k+1 spans nodes k+1, k+2 (this node is its left vertex: shape 1-s)
+  double left = 0.0, right = 0.0;
+  for (int qi = 0; qi < G.npts; ++qi) {
+    const double xl = lo + ((double)k + G.s[qi]) * h;
+    const double xr = lo + ((double)(k + 1) + G.s[qi]) * h;
+    left += G.w[qi] * eval_space(t.skind[a], t.sp[a], xl) * G.s[qi];
+    right += G.w[qi] * eval_space(t.skind[a], t.sp[a], xr) * (1.0 - G.s[qi]);
+  }
+  out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = h * left + h * right;
+}
+
+__global__ void divide_axis_mu_kernel(Geom g, int R, const double* __restrict__ muM, double* __restrict__ x,
+                                      float* __restrict__ x32) {
+  const int a = blockIdx.z;
+  const int r = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= g.d || r >= R || j >= g.n[a]) return;
+  const int64_t idx = (int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j;
+  const double v = x[idx] / muM[g.off[a] + j];
+  x[idx] = v;
+  if (x32) x32[idx] = (float)v;
+}
+
+// out[J] = sum_r w_r prod_a fac[R*off[a] + r*n_a + j_a]
+__global__ void outer_sum_kernel(Geom g, int R, const double* __restrict__ fac, const double* __restrict__ w,
+                                 double* __restrict__ out) {
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= g.ndof) return;
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
+  double acc = 0.0;
+  for (int r = 0; r < R; ++r) {
+    double P = fac[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+    for (int a = 1; a < g.d; ++a) P *= fac[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+    acc += w[r] * P;
+  }
+  out[J] = acc;
+}
+
+__global__ void scale_mu_kernel(Geom g, const double* __restrict__ muM, double* __restrict__ x, int inverse) {
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= g.ndof) return;
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
+  double mu = muM[g.off[0] + j[0]];
+  for (int a = 1; a < g.d; ++a) mu *= muM[g.off[a] + j[a]];
+  x[J] = inverse ? x[J] / mu : x[J] * mu;
+}
+
+__global__ void weights_at_time_kernel(TermsDev T, double t, double* w) {
+  const int r = threadIdx.x;
+  if (r < T.n) w[r] = T.t[r].amp * eval_time(T.t[r], t);
+}
+
+__global__ void amps_kernel(TermsDev T, double* w) {
+  const int r = threadIdx.x;
+  if (r < T.n) w[r] = T.t[r].amp;
+}
+
+// Gauss-Legendre rule on [0,1] by Newton iteration on the Legendre polynomial.
+Gauss make_gauss(int npts) {
+  Gauss G{};
+  G.npts = npts;
+  for (int i = 0; i < npts; ++i) {
+    double x = cos(M_PI * (i + 0.75) / (npts + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= npts; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (npts == 1) { p1 = x; p0 = 1.0; }
+      dp = npts * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-17) break;
+    }
+    // recompute derivative at the converged root
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= npts; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (npts == 1) { p1 = x; p0 = 1.0; }
+    dp = npts * (x * p1 - p0) / (x * x - 1.0);
+    const double w = 2.0 / ((1.0 - x * x) * dp * dp);
+    G.s[npts - 1 - i] = 0.5 * (x + 1.0);
+    G.w[npts - 1 - i] = 0.5 * w;
+  }
+  return G;
+}
+
+TermsDev pack_terms(const pe_term* terms, int n) {
+  TermsDev T{};
+  T.n = n;
+  for (int i = 0; i < n; ++i) T.t[i] = terms[i];
+  return T;
+}
+
+}  // namespace
+
+pe_status launch_time_tables(pe_ctx* c) {
+  const int R = c->R;
+  if (R == 0) return PE_OK;
+  TermsDev T = pack_terms(c->terms, R);
+  Nodes nF{}, nG{};
+  for (int i = 0; i < PE_MAX_S; ++i) {
+    nF.c[i] = c->cF[i];
+    nG.c[i] = c->cG[i];
+  }
+  const int64_t total = (int64_t)c->N * c->M * c->q * R + (int64_t)c->N * c->p * R;
+  const int threads = 256;
+  time_tables_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, c->stream>>>(
+      T, c->N, c->M, c->q, c->p, c->t0, c->dT, c->dt, nF, nG, c->AF,
+      c->precision == PE_MIXED ? c->AF32 : nullptr, c->AG);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+// mode 0: 1D loads only (axis_out gets loads); mode 1: modal factors (S_a F)/mu^M.
+pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode) {
+  if (nterms == 0) return PE_OK;
+  TermsDev T = pack_terms(terms, nterms);
+  Gauss G = make_gauss(c->quad_pts);
+  int nmax = 1;
+  for (int a = 0; a < c->g.d; ++a) nmax = c->g.n[a] > nmax ? c->g.n[a] : nmax;
+  dim3 grid((nmax + 127) / 128, nterms, c->g.d);
+  double* loads = mode == 0 ? axis_out : c->loads;
+  loads_1d_kernel<<<grid, 128, 0, c->stream>>>(T, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2],
+                                                G, loads);
+  PE_CUDA_TRY(cudaGetLastError());
+  if (mode == 0) return PE_OK;
+  for (int a = 0; a < c->g.d; ++a) {
+    const int64_t base = (int64_t)nterms * c->g.off[a];
+    PE_TRY(dst_axis_f64(c->S[a], loads + base, axis_out + base, nterms, c->g.n[a], 1, c->stream));
+  }
+  const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
+  divide_axis_mu_kernel<<<grid, 128, 0, c->stream>>>(c->g, nterms, c->muM_axis, axis_out,
+                                                     f32 ? c->axisF32 : nullptr);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+// out[J] = sum_r amp_r prod_a fac_{r,a}[j_a] (nodal_loads: fac are 1D loads, out a nodal load vector)
+pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* terms, int nterms, double* out,
+                           int /*nodal_loads*/) {
+  double* w = c->partials;  // at least PE_MAX_TERMS doubles
+  TermsDev T = pack_terms(terms, nterms);
+  amps_kernel<<<1, PE_MAX_TERMS, 0, c->stream>>>(T, w);
+  const int threads = 256;
+  outer_sum_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, nterms,
+                                                                                               axis_fac, w, out);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status launch_forcing_modal(pe_ctx* c, double t, double* out) {
+  double* w = c->partials;
+  TermsDev T = pack_terms(c->terms, c->R);
+  weights_at_time_kernel<<<1, PE_MAX_TERMS, 0, c->stream>>>(T, t, w);
+  const int threads = 256;
+  outer_sum_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, c->R,
+                                                                                               c->axisF, w, out);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse) {
+  const int threads = 256;
+  scale_mu_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, c->muM_axis, x,
+                                                                                              inverse);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}

@@ -1,0 +1,129 @@
+// Internal declarations shared by the libpe translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pe.h"
+
+#define PE_MAX_D 3
+#define PE_MAX_S 8
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local message behind pe_last_error)
+// ---------------------------------------------------------------------------
+void pe_set_error(const std::string& msg);
+pe_status pe_fail(pe_status st, const std::string& msg);
+pe_status pe_cuda_fail(cudaError_t err, const char* what);
+
+#define PE_CUDA_TRY(call)                                  \
+  do {                                                     \
+    cudaError_t err__ = (call);                            \
+    if (err__ != cudaSuccess) return pe_cuda_fail(err__, #call); \
+  } while (0)
+
+#define PE_TRY(call)                          \
+  do {                                        \
+    pe_status st__ = (call);                  \
+    if (st__ != PE_OK) return st__;           \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// geometry shared by the kernels: per-axis sizes and strides of a mode index
+// ---------------------------------------------------------------------------
+struct Geom {
+  int d;
+  int n[PE_MAX_D];        // interior nodes per axis
+  int off[PE_MAX_D];      // offset of axis a in concatenated per-axis tables
+  int64_t ndof;
+};
+
+// Decompose a flat C-ordered mode index into per-axis indices (0-based).
+__host__ __device__ inline void unflatten(const Geom& g, int64_t J, int* j) {
+  for (int a = g.d - 1; a >= 0; --a) {
+    j[a] = (int)(J % g.n[a]);
+    J /= g.n[a];
+  }
+}
+
+// Separable forcing, device layout (R terms):
+//   axisF[R * off[a] + r * n_a + j]         = modal factor (S_a F_{r,a})_j / mu^M_a(j)
+//   AF[((n * M + m) * q + i) * R + r]       = amp_r * time_r(T_n + (m + c_i) dt)
+//   AG[(n * p + i) * R + r]                 = amp_r * time_r(T_n + c_i dT)
+struct pe_ctx {
+  // problem
+  Geom g;
+  double lo[PE_MAX_D], hi[PE_MAX_D], h[PE_MAX_D];
+  double D, t0, T, dT, dt;
+  int N, M, q, p;
+  double cF[PE_MAX_S], cG[PE_MAX_S];
+  double lagF[PE_MAX_S][PE_MAX_S], lagG[PE_MAX_S][PE_MAX_S];  // Lagrange monomial coefficients
+  int nsum;  // sum_a n_a
+  // options
+  int precision, dst_backend, quad_pts, max_iter;
+  cudaStream_t stream;
+  // device memory
+  double* muM_axis = nullptr;   // [nsum]
+  double* ratio_axis = nullptr; // [nsum] mu^K/mu^M
+  double* S[PE_MAX_D] = {nullptr, nullptr, nullptr};  // DST-I matrices n_a x n_a
+  double* lam = nullptr;        // [ndof]
+  double* coefF = nullptr;      // [(q+2) * ndof]: E, dt*b_1..q, exp(-lam M dt)
+  double* coefG = nullptr;      // [(p+1) * ndof]: E, dT*b_1..p
+  float* coefF32 = nullptr;     // [(q+2) * ndof]: E_hi, E_lo, dt*b_i (float)
+  double* U = nullptr;          // [(N+1) * ndof]
+  double* Gold = nullptr;       // [N * ndof]
+  double* Fbar = nullptr;       // [N * ndof]
+  double* gG = nullptr;         // [N * ndof] coarse forcing of each slice
+  double* work0 = nullptr;      // [ndof] nodal / DST scratch
+  double* work1 = nullptr;      // [ndof]
+  double* out_nodal = nullptr;  // [ndof] inverse DST of U^N after pe_solve
+  double* partials = nullptr;   // [2 * max_blocks]
+  double* red = nullptr;        // [2] device
+  double* h_red = nullptr;      // [2] pinned host
+  int max_blocks = 0;
+  // forcing (set by pe_set_problem)
+  int R = 0;
+  pe_term terms[PE_MAX_TERMS];
+  double* axisF = nullptr;      // [PE_MAX_TERMS * nsum]
+  float* axisF32 = nullptr;     // [PE_MAX_TERMS * nsum]
+  double* axisU0 = nullptr;     // [PE_MAX_TERMS * nsum] factors of separable u0
+  double* AF = nullptr;         // [N*M*q*PE_MAX_TERMS]
+  float* AF32 = nullptr;
+  double* AG = nullptr;         // [N*p*PE_MAX_TERMS]
+  double* loads = nullptr;      // [PE_MAX_TERMS * nsum] 1D loads before the DST
+  // state
+  int k = 0;
+  bool have_problem = false;
+  bool have_output = false;
+  cudaEvent_t ev[8];
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each returns a pe_status and reports errors through pe_set_error)
+// ---------------------------------------------------------------------------
+// pe_tables.cu
+pe_status launch_axis_tables(pe_ctx* c);
+pe_status launch_coef_tables(pe_ctx* c);
+pe_status build_dst_matrix(int n, double* S, cudaStream_t st);
+
+// pe_forcing.cu
+pe_status launch_time_tables(pe_ctx* c);
+pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode);
+pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* terms, int nterms, double* out,
+                           int nodal_loads);
+pe_status launch_forcing_modal(pe_ctx* c, double t, double* out);
+
+// pe_dst.cu
+pe_status dst_axis_f64(const double* S, const double* in, double* out, int64_t outer, int n, int64_t inner,
+                       cudaStream_t st);
+pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t outer, int n, int64_t inner,
+                       cudaStream_t st);
+pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);  // uses c->S, c->work1
+
+// pe_sweep.cu
+pe_status launch_coarse_sweep(pe_ctx* c);
+pe_status launch_fine_sweep(pe_ctx* c);
+pe_status launch_correction(pe_ctx* c, double* num, double* den);
+pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse);

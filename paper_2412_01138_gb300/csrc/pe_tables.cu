@@ -1,0 +1,163 @@
+// Closed-form spectra of the Q1 matrices, lam_J, and the phi/b coefficient tables.
+//
+// Sec. 2.3 (closing paragraph): the Q1 mass and stiffness matrices are
+// diagonalised at once by the tensor DST-I.  Per axis, with
+// theta_j = j pi/(n+1):  mu^M_j = (h/3)(2 + cos theta_j),
+// mu^K_j = (4/h) sin^2(theta_j/2), and lam_J = D sum_a mu^K_a/mu^M_a.
+//
+// Eq. (3-12): b_i(z) = int_0^1 e^{z(1-theta)} l_i(theta) dtheta.  Writing the
+// Lagrange basis in monomials, l_i(theta) = sum_m a_{im} theta^m, gives
+// b_i(z) = sum_m a_{im} m! phi_{m+1}(z) with phi_j as in Theorem 3.1's proof.
+// phi_s is summed as a Taylor series for |z| < 2 and the lower phi_j follow by
+// the backward recurrence phi_j = z phi_{j+1} + 1/j! (stable there); for
+// |z| >= 2, phi_1 = expm1(z)/z and phi_{j+1} = (phi_j - 1/j!)/z.
+#include <math.h>
+
+#include "pe_internal.h"
+
+namespace {
+
+__constant__ double c_inv_fact[48];
+
+// 1D eigenvalue tables of every axis, concatenated.
+__global__ void axis_tables_kernel(Geom g, double h0, double h1, double h2, double* muM, double* ratio) {
+  const int a = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;  // 0-based mode index, mode number j+1
+  if (a >= g.d || j >= g.n[a]) return;
+  const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
+  const double np1 = (double)(g.n[a] + 1);
+  const double cth = cospi((double)(j + 1) / np1);
+  const double sh = sinpi((double)(j + 1) / (2.0 * np1));
+  const double mM = (h / 3.0) * (2.0 + cth);
+  const double mK = (4.0 / h) * (sh * sh);
+  muM[g.off[a] + j] = mM;
+  ratio[g.off[a] + j] = mK / mM;
+}
+
+// phi_1..phi_s at z into ph[0..s-1].
+__device__ inline void phi_all(double z, int s, double* ph) {
+  if (fabs(z) < 2.0) {
+    const int K = 27;
+    double acc = c_inv_fact[K + s];
+    for (int k = K - 1; k >= 0; --k) acc = fma(acc, z, c_inv_fact[k + s]);
+    ph[s - 1] = acc;
+    for (int j = s - 1; j >= 1; --j) ph[j - 1] = fma(z, ph[j], c_inv_fact[j]);
+  } else {
+    ph[0] = expm1(z) / z;
+    for (int j = 1; j < s; ++j) ph[j] = (ph[j - 1] - c_inv_fact[j]) / z;
+  }
+}
+
+struct Lag {
+  double a[PE_MAX_S][PE_MAX_S];  // a[i][m]: coefficient of theta^m in l_i
+};
+
+__device__ inline void b_weights(double z, int s, const Lag& L, double* b) {
+  double ph[PE_MAX_S];
+  phi_all(z, s, ph);
+  for (int i = 0; i < s; ++i) {
+    double acc = 0.0;
+    double mf = 1.0;  // m!
+    for (int m = 0; m < s; ++m) {
+      acc = fma(L.a[i][m] * mf, ph[m], acc);
+      mf *= (double)(m + 1);
+    }
+    b[i] = acc;
+  }
+}
+
+__global__ void coef_tables_kernel(Geom g, const double* __restrict__ ratio, double D, double dt, double dT,
+                                   int M, int q, int p, Lag LF, Lag LG, double* __restrict__ lam_out,
+                                   double* __restrict__ coefF, double* __restrict__ coefG,
+                                   float* __restrict__ coefF32) {
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= g.ndof) return;
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
+  double s = 0.0;
+  for (int a = 0; a < g.d; ++a) s += ratio[g.off[a] + j[a]];
+  const double lam = D * s;
+  lam_out[J] = lam;
+  const int64_t nd = g.ndof;
+  double b[PE_MAX_S];
+  // fine step dt, q nodes
+  {
+    const double z = -lam * dt;
+    const double E = exp(z);
+    b_weights(z, q, LF, b);
+    coefF[J] = E;
+    for (int i = 0; i < q; ++i) coefF[(1 + i) * nd + J] = dt * b[i];
+    const double EM = exp(-lam * ((double)M * dt));
+    coefF[(q + 1) * nd + J] = EM;
+    if (coefF32) {
+      const float ehi = (float)E;
+      coefF32[J] = ehi;
+      coefF32[nd + J] = (float)(E - (double)ehi);
+      for (int i = 0; i < q; ++i) coefF32[(2 + i) * nd + J] = (float)(dt * b[i]);
+    }
+  }
+  // coarse step dT, p nodes
+  {
+    const double z = -lam * dT;
+    b_weights(z, p, LG, b);
+    coefG[J] = exp(z);
+    for (int i = 0; i < p; ++i) coefG[(1 + i) * nd + J] = dT * b[i];
+  }
+}
+
+__global__ void dst_matrix_kernel(int n, double* S) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (k >= n || j >= n) return;
+  const int64_t period = 2 * (int64_t)(n + 1);
+  const int64_t m = ((int64_t)(j + 1) * (k + 1)) % period;
+  S[(int64_t)j * n + k] = sqrt(2.0 / (double)(n + 1)) * sinpi((double)m / (double)(n + 1));
+}
+
+bool g_fact_ready = false;
+
+pe_status ensure_factorials() {
+  if (g_fact_ready) return PE_OK;
+  double f[48];
+  f[0] = 1.0;
+  for (int i = 1; i < 48; ++i) f[i] = f[i - 1] / (double)i;
+  PE_CUDA_TRY(cudaMemcpyToSymbol(c_inv_fact, f, sizeof(f)));
+  g_fact_ready = true;
+  return PE_OK;
+}
+
+}  // namespace
+
+pe_status launch_axis_tables(pe_ctx* c) {
+  int nmax = 1;
+  for (int a = 0; a < c->g.d; ++a) nmax = c->g.n[a] > nmax ? c->g.n[a] : nmax;
+  dim3 grid((nmax + 127) / 128, c->g.d);
+  axis_tables_kernel<<<grid, 128, 0, c->stream>>>(c->g, c->h[0], c->g.d > 1 ? c->h[1] : 1.0,
+                                                  c->g.d > 2 ? c->h[2] : 1.0, c->muM_axis, c->ratio_axis);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status launch_coef_tables(pe_ctx* c) {
+  PE_TRY(ensure_factorials());
+  Lag LF{}, LG{};
+  for (int i = 0; i < PE_MAX_S; ++i)
+    for (int m = 0; m < PE_MAX_S; ++m) {
+      LF.a[i][m] = c->lagF[i][m];
+      LG.a[i][m] = c->lagG[i][m];
+    }
+  const int threads = 256;
+  const int64_t blocks = (c->g.ndof + threads - 1) / threads;
+  coef_tables_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(
+      c->g, c->ratio_axis, c->D, c->dt, c->dT, c->M, c->q, c->p, LF, LG, c->lam, c->coefF, c->coefG,
+      c->precision == PE_MIXED ? c->coefF32 : nullptr);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status build_dst_matrix(int n, double* S, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, n);
+  dst_matrix_kernel<<<grid, 128, 0, st>>>(n, S);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}

@@ -1,0 +1,283 @@
+"""ctypes binding of libpe (include/pe.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts
+Python descriptors (``inputs.Problem``, ``inputs.Term``) into the C structs,
+passes pointers (numpy host arrays or torch device tensors) and raises
+``PEError`` with the library's message on any non-zero status.  Importing it
+loads ``_lib/libpe.so`` and fails loudly when the library has not been built
+(``python -m paper_2412_01138_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import inputs as _in
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libpe.so")
+
+PE_OK, PE_EINVAL, PE_ENOMEM, PE_ECUDA, PE_ENOCONV, PE_ENONFINITE, PE_ETIMEOUT, PE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+PE_FP64, PE_MIXED = 0, 1
+PE_DST_AUTO, PE_DST_MATRIX = 0, 1
+PE_FIELD_TERMS_SEPARABLE, PE_FIELD_TERMS_QUADRATURE, PE_FIELD_NODAL = 0, 1, 2
+PE_MAX_TERMS = 32
+
+_STATUS_NAMES = {0: "PE_OK", -1: "PE_EINVAL", -2: "PE_ENOMEM", -3: "PE_ECUDA", -4: "PE_ENOCONV",
+                 -5: "PE_ENONFINITE", -6: "PE_ETIMEOUT", -7: "PE_ESTATE"}
+
+#: every symbol include/pe.h declares (checked by the CPU test suite)
+EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_solve", "pe_get_solution", "pe_get_modal",
+            "pe_get_lambda", "pe_get_coefficients", "pe_forcing_modal", "pe_get_nodes", "pe_save_state",
+            "pe_load_state", "pe_dst", "pe_dst_f32", "pe_last_error", "pe_destroy")
+
+
+class PEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pe_term(C.Structure):
+    _fields_ = [("amp", C.c_double), ("tkind", C.c_int32), ("tp", C.c_double * 2), ("skind", C.c_int32 * 3),
+                ("sp", (C.c_double * 4) * 3)]
+
+
+class pe_tableau(C.Structure):
+    _fields_ = [("s", C.c_int32), ("c", C.POINTER(C.c_double)), ("random", C.c_int32), ("seed", C.c_uint64)]
+
+
+class pe_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("dst_backend", C.c_int32), ("quad_pts", C.c_int32),
+                ("max_iter", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class pe_field(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_terms", C.c_int32), ("terms", C.POINTER(pe_term)),
+                ("nodal", C.c_void_p)]
+
+
+class pe_forcing(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("terms", C.POINTER(pe_term))]
+
+
+class pe_result(C.Structure):
+    _fields_ = [("k", C.c_int32), ("residual", C.c_double), ("residual_history", C.POINTER(C.c_double)),
+                ("history_cap", C.c_int32), ("fine_sweeps", C.c_int64), ("ms_tables", C.c_double),
+                ("ms_prepare", C.c_double), ("ms_iterations", C.c_double), ("ms_output", C.c_double)]
+
+
+def load_library(path: str = _LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libpe is not built ({path} missing); run python -m paper_2412_01138_gb300.build")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "pe_setup": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_double,
+                               C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(pe_tableau),
+                               C.POINTER(pe_tableau), C.POINTER(pe_options)]),
+        "pe_set_problem": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing)]),
+        "pe_parareal_iter": (C.c_int, [P, C.POINTER(C.c_double)]),
+        "pe_solve": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing), C.c_double, C.POINTER(pe_result)]),
+        "pe_get_solution": (C.c_int, [P, C.c_int32, P]),
+        "pe_get_modal": (C.c_int, [P, C.c_int32, P]),
+        "pe_get_lambda": (C.c_int, [P, P]),
+        "pe_get_coefficients": (C.c_int, [P, C.c_int32, P]),
+        "pe_forcing_modal": (C.c_int, [P, C.c_double, P]),
+        "pe_get_nodes": (C.c_int, [P, C.c_int32, C.POINTER(C.c_double)]),
+        "pe_save_state": (C.c_int, [P, P, C.POINTER(C.c_size_t)]),
+        "pe_load_state": (C.c_int, [P, P, C.c_size_t]),
+        "pe_dst": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
+        "pe_dst_f32": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
+        "pe_last_error": (C.c_char_p, []),
+        "pe_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(status: int):
+    if status != PE_OK:
+        raise PEError(status, lib().pe_last_error().decode())
+
+
+def _ptr(x) -> int:
+    """Raw address of a numpy array or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def make_terms(terms: Sequence["_in.Term"]):
+    arr = (pe_term * max(1, len(terms)))()
+    for k, t in enumerate(terms):
+        arr[k].amp = t.amp
+        arr[k].tkind = t.tkind
+        arr[k].tp[0], arr[k].tp[1] = t.tp
+        for a, f in enumerate(t.factors):
+            arr[k].skind[a] = f.kind
+            for i, v in enumerate(f.params4()):
+                arr[k].sp[a][i] = v
+    return arr
+
+
+def stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Solver:
+    """One pe_ctx: a Parareal EIFE-linear solver for a fixed grid and time partition."""
+
+    def __init__(self, prob: "_in.Problem", precision: int = PE_FP64, stream=None, max_iter: int = 0,
+                 random_coarse_seed: Optional[int] = None):
+        self.prob = prob
+        self._lib = lib()
+        n = (C.c_int32 * prob.d)(*prob.n)
+        box = (C.c_double * (2 * prob.d))(*[v for lohi in prob.box for v in lohi])
+        self._cF = (C.c_double * prob.q)(*prob.fine_nodes)
+        self._cG = (C.c_double * prob.p)(*prob.coarse_nodes)
+        fine = pe_tableau(prob.q, C.cast(self._cF, C.POINTER(C.c_double)), 0, 0)
+        if random_coarse_seed is None:
+            coarse = pe_tableau(prob.p, C.cast(self._cG, C.POINTER(C.c_double)), 0, 0)
+        else:
+            coarse = pe_tableau(prob.p, None, 1, random_coarse_seed)
+        opt = pe_options(precision, PE_DST_AUTO, prob.quad_pts, max_iter, stream_handle(stream))
+        ctx = C.c_void_p()
+        _check(self._lib.pe_setup(C.byref(ctx), prob.d, n, box, prob.D, prob.t0, prob.T, prob.N, prob.M,
+                                  C.byref(fine), C.byref(coarse), C.byref(opt)))
+        self.ctx = ctx
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.pe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- problem data -------------------------------------------------------
+    def _field(self, kind: int, nodal=None):
+        prob = self.prob
+        if kind == PE_FIELD_NODAL:
+            return pe_field(kind, 0, None, _ptr(nodal))
+        terms = make_terms(prob.u0)
+        self._keep.append(terms)
+        return pe_field(kind, len(prob.u0), C.cast(terms, C.POINTER(pe_term)), None)
+
+    def _forcing(self):
+        terms = make_terms(self.prob.forcing)
+        self._keep.append(terms)
+        return pe_forcing(len(self.prob.forcing), C.cast(terms, C.POINTER(pe_term)))
+
+    def set_problem(self, u0_kind: int = PE_FIELD_TERMS_SEPARABLE, nodal=None):
+        self._keep = []
+        f = self._field(u0_kind, nodal)
+        _check(self._lib.pe_set_problem(self.ctx, C.byref(f), C.byref(self._forcing())))
+
+    def iterate(self) -> float:
+        r = C.c_double()
+        _check(self._lib.pe_parareal_iter(self.ctx, C.byref(r)))
+        return r.value
+
+    def solve(self, tol: Optional[float] = None, u0_kind: int = PE_FIELD_TERMS_SEPARABLE, nodal=None,
+              history: int = 64) -> dict:
+        self._keep = []
+        f = self._field(u0_kind, nodal)
+        hist = (C.c_double * history)()
+        res = pe_result()
+        res.residual_history = C.cast(hist, C.POINTER(C.c_double))
+        res.history_cap = history
+        tol = self.prob.tol if tol is None else tol
+        _check(self._lib.pe_solve(self.ctx, C.byref(f), C.byref(self._forcing()), tol, C.byref(res)))
+        return {"k": res.k, "residual": res.residual, "history": list(hist[: min(res.k, history)]),
+                "fine_sweeps": res.fine_sweeps, "ms_tables": res.ms_tables, "ms_prepare": res.ms_prepare,
+                "ms_iterations": res.ms_iterations, "ms_output": res.ms_output}
+
+    # -- outputs ------------------------------------------------------------
+    def _out(self, count: int, out):
+        return np.empty(count, dtype=np.float64) if out is None else out
+
+    def solution(self, slice_: int, out=None):
+        out = self._out(self.prob.ndof, out)
+        _check(self._lib.pe_get_solution(self.ctx, slice_, _ptr(out)))
+        return out
+
+    def modal(self, slice_: int, out=None):
+        out = self._out(self.prob.ndof, out)
+        _check(self._lib.pe_get_modal(self.ctx, slice_, _ptr(out)))
+        return out
+
+    def lam(self, out=None):
+        out = self._out(self.prob.ndof, out)
+        _check(self._lib.pe_get_lambda(self.ctx, _ptr(out)))
+        return out
+
+    def coefficients(self, which: int, out=None):
+        s = self.prob.q if which == 0 else self.prob.p
+        out = self._out((s + 1) * self.prob.ndof, out)
+        _check(self._lib.pe_get_coefficients(self.ctx, which, _ptr(out)))
+        return out.reshape(s + 1, self.prob.ndof) if isinstance(out, np.ndarray) else out
+
+    def forcing_modal(self, t: float, out=None):
+        out = self._out(self.prob.ndof, out)
+        _check(self._lib.pe_forcing_modal(self.ctx, t, _ptr(out)))
+        return out
+
+    def nodes(self, which: int):
+        s = self.prob.q if which == 0 else self.prob.p
+        out = (C.c_double * s)()
+        _check(self._lib.pe_get_nodes(self.ctx, which, out))
+        return tuple(out)
+
+    def save_state(self) -> bytes:
+        size = C.c_size_t()
+        _check(self._lib.pe_save_state(self.ctx, None, C.byref(size)))
+        buf = C.create_string_buffer(size.value)
+        _check(self._lib.pe_save_state(self.ctx, buf, C.byref(size)))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(self._lib.pe_load_state(self.ctx, buf, len(blob)))
+
+
+def dst(d: int, n: Sequence[int], x_in, x_out, stream=None, f32: bool = False):
+    """Orthonormal tensor DST-I of a device buffer (torch tensor), out may alias in."""
+    nn = (C.c_int32 * d)(*n)
+    fn = lib().pe_dst_f32 if f32 else lib().pe_dst
+    _check(fn(d, nn, _ptr(x_in), _ptr(x_out), stream_handle(stream)))

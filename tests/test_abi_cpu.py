@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every symbol include/pe.h declares.
+
+Runs without a GPU: only argument validation that fails before any device
+work is exercised (no compute call).
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_01138_gb300 import build, pe
+
+    build.build()
+    return pe.lib()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            # function declarations: "<return type> pe_name(" at the start of a line
+            names |= set(re.findall(r"^(?:pe_status|void|const char\*)\s+(pe_[a-z0-9_]+)\(", text, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    from paper_2412_01138_gb300 import pe
+    assert set(pe.EXPORTED) == declared
+
+
+def test_invalid_setup_arguments_rejected_before_device_work(lib):
+    from paper_2412_01138_gb300 import pe
+
+    ctx = C.c_void_p()
+    n = (C.c_int32 * 1)(15)
+    box = (C.c_double * 2)(0.0, 1.0)
+    good = pe.pe_tableau(2, None, 0, 0)
+    cases = [
+        dict(d=0), dict(d=4), dict(D=0.0), dict(D=-1.0), dict(T=0.0), dict(N=0), dict(M=0),
+    ]
+    for kw in cases:
+        args = dict(d=1, D=1.0, T=1.0, N=4, M=4)
+        args.update(kw)
+        st = lib.pe_setup(C.byref(ctx), args["d"], n, box, args["D"], 0.0, args["T"], args["N"], args["M"],
+                          C.byref(good), C.byref(good), None)
+        assert st == pe.PE_EINVAL, kw
+        assert lib.pe_last_error().decode()
+    # duplicate interpolation nodes (the Lagrange basis of Eq. (3-12) needs distinct nodes)
+    c = (C.c_double * 2)(0.5, 0.5)
+    dup = pe.pe_tableau(2, C.cast(c, C.POINTER(C.c_double)), 0, 0)
+    st = lib.pe_setup(C.byref(ctx), 1, n, box, 1.0, 0.0, 1.0, 4, 4, C.byref(dup), C.byref(good), None)
+    assert st == pe.PE_EINVAL and "distinct" in lib.pe_last_error().decode()
+    # box with lo >= hi
+    bad_box = (C.c_double * 2)(1.0, 1.0)
+    st = lib.pe_setup(C.byref(ctx), 1, n, bad_box, 1.0, 0.0, 1.0, 4, 4, C.byref(good), C.byref(good), None)
+    assert st == pe.PE_EINVAL
+    # NULL context pointers are rejected
+    assert lib.pe_parareal_iter(None, None) == pe.PE_EINVAL
+    assert lib.pe_dst(0, n, None, None, None) == pe.PE_EINVAL

@@ -1,0 +1,60 @@
+"""GPU parity of the mixed-precision form (float32 fine stages) against the float64 oracle.
+
+Bound: relative L2 <= 1e-6 (the precision workload's stated bound before
+float64 refinement).
+"""
+import numpy as np
+import pytest
+
+from oracle import solver as osolver
+from paper_2412_01138_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_01138_gb300 import pe as _pe
+
+    _pe.lib()
+    return _pe
+
+
+def _rel(a, b, w):
+    return float(np.sqrt(np.sum(w * (a - b) ** 2)) / np.sqrt(np.sum(w * b * b)))
+
+
+@pytest.mark.parametrize("which", ["c3_small", "c2_small", "c5_small"])
+def test_mixed_small_all_modes(pe, which):
+    if which == "c3_small":
+        prob = I.scaled(I.config3(), (15, 13, 17), N=16, M=32)
+    elif which == "c2_small":
+        prob = I.scaled(I.config2(), (63, 50), N=8, M=64)
+    else:
+        prob = I.scaled(I.config5(), (63, 63), N=16, M=32)
+    sys_ = osolver.ModalSystem(prob)
+    ref = osolver.parareal(sys_, tol=0.0, k_max=2)
+    with pe.Solver(prob, precision=pe.PE_MIXED) as s:
+        info = s.solve(tol=1e-6)
+        assert info["k"] == 2
+        for n in range(1, prob.N + 1):
+            assert _rel(s.modal(n), ref.U[n], sys_.norm_w) <= TOL_MIXED, n
+
+
+def test_mixed_config3_full_size_sampled(pe):
+    """Config 3 at full size (127^3, 64 x 32, RK4, R = 17), sampled modes."""
+    prob = I.config3()
+    rng = np.random.default_rng(3)
+    idx = np.unique(np.concatenate([[0, 1, 127, prob.ndof - 1], rng.integers(0, prob.ndof, 300)]))
+    sys_ = osolver.ModalSystem(prob, modes=idx)
+    ref = osolver.parareal(sys_, tol=0.0, k_max=1)
+    with pe.Solver(prob, precision=pe.PE_MIXED) as s:
+        info = s.solve(tol=1e-6)
+        assert info["k"] == 2 and info["residual"] <= 1e-6
+        for n in (1, prob.N // 2, prob.N):
+            assert _rel(s.modal(n)[idx], ref.U[n], sys_.norm_w) <= TOL_MIXED, n
