@@ -1,0 +1,372 @@
+"""Benchmark: Parareal EIFE-linear on the 2D 255^2 workload, float64 vs mixed precision.
+
+One step = one pe_solve of the workload: phi/b tables, P_h f tables, the
+projection of u0 (forward tensor DST-I), the coarse sweep, Parareal
+iterations (fine sweep from every slice + correction + float64 residual)
+until the relative residual reaches 1e-6, and the inverse DST of the final
+slice.  The metric is fine DoF*substeps per second:
+    Ndof * N * M * (fine sweeps executed) / step time.
+
+Workload: d = 2, 255 x 255 interior Q1 nodes on (0,1)^2, D = 0.1, t in [0,1],
+u0 = nodal values of sin(pi x) sin(pi y), f = manufactured term + 8 seeded
+Gaussian bumps modulated by sin(w t + phi), 32 slices x 64 substeps, RK4 fine
+(c = 0, 1/4, 1/2, 3/4), 2-stage coarse with seeded random nodes.  The main
+line is the float64 path; "chosen" reports the mixed-precision form on the
+same workload.  --impl reference times the CPU oracle instead.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       (N > 1: launch with torch.distributed.run; ranks solve independent
+       replicas of the workload, no collective on the data path)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2412_01138_gb300 import inputs as I  # noqa: E402
+
+METRIC = "time to rel-L2 1e-6 & fine DoF·substeps/s: chosen form vs plain FP64, 1 GB300"
+UNIT = "fine DoF*substeps/s"
+TOL = 1e-6
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workload():
+    return I.config2()
+
+
+def nodal_u0(prob):
+    """Synthetic initial data: sin(pi x) sin(pi y) at the interior nodes."""
+    xs = []
+    for a in range(prob.d):
+        lo, hi = prob.box[a]
+        h = (hi - lo) / (prob.n[a] + 1)
+        xs.append(lo + h * np.arange(1, prob.n[a] + 1))
+    out = np.ones(())
+    for x in xs:
+        out = np.multiply.outer(out, np.sin(np.pi * x))
+    return np.ascontiguousarray(out.reshape(-1))
+
+
+def fine_flops_per_unit(prob):
+    """FLOPs per DoF*substep of the fine propagator: q(R+1)+1 FMAs, 2 FLOPs each."""
+    return 2 * (prob.q * (prob.R + 1) + 1)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh)
+    return None
+
+
+def fp64_peak_tflops(sm_mhz: float):
+    """FP64 FMA peak: 152 SMs x 2 FP64 FMA lanes per clock x 2 FLOPs x clock."""
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak_tflops(sm_mhz: float):
+    """FP32 FMA peak: 152 SMs x 128 FP32 lanes per clock x 2 FLOPs x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_rank{device_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(prob, n_modes: int, seed: int = 0, u0_nodal=None):
+    """Run the oracle's Parareal (to the same residual tolerance) on a random sample of modes.
+
+    Modes are independent after the diagonalisation, so the sample is an exact
+    restriction of the full solve.  u0_nodal: nodal initial data (as the bench
+    feeds the library), else P_h of the descriptor.  Returns the rate in fine
+    DoF*substeps/s and the pieces needed for a parity check.
+    """
+    from oracle import fem
+    from oracle import solver as osolver
+
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(prob.ndof, size=min(n_modes, prob.ndof), replace=False))
+    t0 = time.perf_counter()
+    sys_ = osolver.ModalSystem(prob, modes=idx)
+    if u0_nodal is not None:
+        basis = fem.ClosedFormBasis(prob.n, prob.box, prob.D)
+        sys_.c0 = basis.to_modal_from_nodal(u0_nodal.reshape(prob.n)).reshape(-1)[idx]
+    res = osolver.parareal(sys_, tol=TOL, keep_history=False)
+    dt = time.perf_counter() - t0
+    units = len(idx) * prob.N * prob.M * res.k
+    return units / dt, dt, len(idx), res.k, sys_, res, idx
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    prob = workload()
+    n_modes = 256
+    for _ in range(args.warmup):
+        oracle_sample(prob, 32, seed=99)
+    t_total, units_total = 0.0, 0
+    for s in range(args.steps):
+        rate, dt, nm, k, *_ = oracle_sample(prob, n_modes, seed=s)
+        t_total += dt
+        units_total += nm * prob.N * prob.M * k
+    value = units_total / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": prob.label, "ndof": prob.ndof, "slices": prob.N, "substeps": prob.M,
+                   "fine_stages": prob.q, "forcing_terms": prob.R},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_modes} random modes of {prob.ndof} per step, full Parareal to rel "
+                                   f"residual {TOL} (k=2 fine sweeps of {prob.N}x{prob.M} substeps)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_2412_01138_gb300 import pe
+
+    prob = workload()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    stream = torch.cuda.current_stream(dev)
+    u0_host = nodal_u0(prob)
+    u0_dev = torch.from_numpy(u0_host).to(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    out_dev = torch.empty(prob.ndof, dtype=torch.float64, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed_steps(solver, steps, warmup, nodal):
+        for _ in range(warmup):
+            solver.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=nodal)
+        barrier()
+        total_ms, infos = 0.0, []
+        for _ in range(steps):
+            flush.fill_(1.0)  # evict the working set from L2 between steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = solver.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=nodal)
+            solver.solution(prob.N, out=out_dev)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            infos.append(info)
+        barrier()
+        return total_ms, infos
+
+    results = {}
+    with ClockSampler(local if world > 1 else 0) as clocks:
+        for name, precision in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
+            with pe.Solver(prob, precision=precision, stream=stream) as s:
+                total_ms, infos = timed_steps(s, args.steps, args.warmup, u0_dev)
+                modal = s.modal(prob.N)
+                # end to end through the C-ABI with host buffers: H2D of u0, D2H of the solution
+                out_host = np.empty(prob.ndof)
+                s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_host)
+                barrier()
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_host)
+                    s.solution(prob.N, out=out_host)
+                e2e_s = time.perf_counter() - t0
+            results[name] = dict(total_ms=total_ms, infos=infos, modal=modal, e2e_s=e2e_s)
+    clock = clocks.summary()
+
+    # max over ranks
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for r in results.values():
+        r["total_ms"] = allmax(r["total_ms"])
+        r["e2e_s"] = allmax(r["e2e_s"])
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    def summarize(r):
+        k = r["infos"][-1]["k"]
+        units = prob.ndof * prob.N * prob.M * sum(i["fine_sweeps"] for i in r["infos"]) * world
+        value = units / (r["total_ms"] / 1e3)
+        e2e_units = prob.ndof * prob.N * prob.M * k * args.steps * world
+        ms_fine = np.mean([i["ms_fine_kernel"] / max(i["fine_sweeps"], 1) for i in r["infos"]])
+        return dict(value=value, k=k, ms_per_step=r["total_ms"] / args.steps, e2e=e2e_units / r["e2e_s"],
+                    ms_fine_launch=ms_fine, launches=r["infos"][-1]["kernel_launches"],
+                    residual=r["infos"][-1]["residual"])
+
+    plain = summarize(results["fp64"])
+    chosen = summarize(results["mixed"])
+
+    # parity of both forms on sampled modes against the oracle (outside the timed region);
+    # the same run is the CPU baseline (the oracle as it stands, one core)
+    rate, dt, nm, k_or, sys_, ref, idx = oracle_sample(prob, 256, seed=7, u0_nodal=u0_host)
+    w = sys_.norm_w
+
+    def rel(a):
+        return float(np.sqrt(np.sum(w * (a[idx] - ref.U[-1]) ** 2)) / np.sqrt(np.sum(w * ref.U[-1] ** 2)))
+
+    err_plain, err_chosen = rel(results["fp64"]["modal"]), rel(results["mixed"]["modal"])
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nm} random modes of {prob.ndof}, Parareal to rel residual {TOL} "
+                         f"(k={k_or} sweeps of {prob.N}x{prob.M} substeps), {dt:.1f} s"}
+
+    flops_launch = fine_flops_per_unit(prob) * prob.ndof * prob.N * prob.M
+    achieved = flops_launch / (plain["ms_fine_launch"] / 1e3) / 1e12
+    sm_mhz = clock.get("sm_max_mhz") or 2070.0
+    peak = fp64_peak_tflops(sm_mhz)
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "fine_f64_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as fh:
+            traffic = json.load(fh).get("bytes_per_launch")
+
+    line = {
+        "metric": METRIC,
+        "value": plain["value"],
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": plain["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": prob.label, "d": prob.d, "n": list(prob.n), "slices": prob.N,
+                   "substeps": prob.M, "fine_stages": prob.q, "coarse_stages": prob.p, "forcing_terms": prob.R,
+                   "tol": TOL, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_tol_ms": plain["ms_per_step"],
+        "iterations": plain["k"],
+        "rel_l2_vs_oracle": err_plain,
+        "chosen": {"form": "mixed: float32 fine stages (hi/lo E), float64 tables, correction, residual",
+                   "value": chosen["value"], "unit": UNIT, "time_to_tol_ms": chosen["ms_per_step"],
+                   "iterations": chosen["k"], "rel_l2_vs_oracle": err_chosen, "dtype": "f32",
+                   "speedup_time_to_tol": plain["ms_per_step"] / chosen["ms_per_step"],
+                   "fine_kernel_ms": chosen["ms_fine_launch"],
+                   "fine_kernel_tflops": fine_flops_per_unit(prob) * prob.ndof * prob.N * prob.M
+                   / (chosen["ms_fine_launch"] / 1e3) / 1e12,
+                   "fp32_peak_tflops": fp32_peak_tflops(sm_mhz),
+                   "e2e": chosen["e2e"]},
+        "roofline": {"kernel": "fine_f64_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x max SM clock",
+                     "flops_per_launch": flops_launch},
+        "e2e": {"value": plain["e2e"], "unit": UNIT, "h2d_bytes_per_step": prob.ndof * 8,
+                "d2h_bytes_per_step": prob.ndof * 8 + 16 * plain["k"]},
+        "gpu_launches": int(plain["launches"] + 0) * args.steps,
+        "clocks": clock,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

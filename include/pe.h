@@ -125,6 +125,8 @@ typedef struct {
   double ms_prepare;         /* forcing tables, projection of u0, coarse sweep */
   double ms_iterations;      /* all fine sweeps + corrections + residuals */
   double ms_output;          /* inverse DST of the final slice */
+  double ms_fine_kernel;     /* device time of the fine-propagator kernels alone (sum over sweeps) */
+  int64_t kernel_launches;   /* kernels this call launched */
 } pe_result;
 
 /*

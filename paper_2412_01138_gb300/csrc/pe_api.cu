@@ -346,9 +346,12 @@ extern "C" pe_status pe_set_problem(pe_ctx* c, const pe_field* u0, const pe_forc
 }
 
 static pe_status iter_impl(pe_ctx* c, double* r_out) {
+  PE_CUDA_TRY(cudaEventRecord(c->ev[5], c->stream));
   PE_TRY(launch_fine_sweep(c));
+  PE_CUDA_TRY(cudaEventRecord(c->ev[6], c->stream));
   double num = 0.0, den = 0.0;
-  PE_TRY(launch_correction(c, &num, &den));
+  PE_TRY(launch_correction(c, &num, &den));  // synchronises the stream
+  c->ms_fine += elapsed(c->ev[5], c->ev[6]);
   c->k += 1;
   if (!isfinite(num) || !isfinite(den)) {
     c->have_problem = false;
@@ -370,6 +373,8 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   if (!c) return pe_fail(PE_EINVAL, "pe_solve: ctx is NULL");
   if (!(tol >= 0.0)) return pe_fail(PE_EINVAL, "pe_solve: tol must be >= 0");
   c->have_problem = false;
+  c->launches = 0;
+  c->ms_fine = 0.0;
   PE_CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
   PE_TRY(set_problem_impl(c, u0, f));
   PE_CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
@@ -394,6 +399,8 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
     res->ms_prepare = elapsed(c->ev[1], c->ev[2]);
     res->ms_iterations = elapsed(c->ev[2], c->ev[3]);
     res->ms_output = elapsed(c->ev[3], c->ev[4]);
+    res->ms_fine_kernel = c->ms_fine;
+    res->kernel_launches = c->launches;
   }
   if (r > tol && c->k < c->N) return pe_fail(PE_ENOCONV, "pe_solve: residual above tol after max_iter iterations");
   return PE_OK;

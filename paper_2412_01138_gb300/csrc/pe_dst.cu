@@ -177,6 +177,7 @@ pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t oute
 }
 
 pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out) {
+  c->launches += c->g.d;
   return dst_nd<double>(c->g.d, c->g.n, c->S, in, out, c->work1, c->stream);
 }
 

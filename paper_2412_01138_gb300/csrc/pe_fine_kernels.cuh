@@ -165,6 +165,7 @@ pe_status fine_launch(pe_ctx* c) {
       fine_f64_kernel<R><<<grid, threads, sizeof(double) * mc * per_m, c->stream>>>(
           c->g, c->M, c->q, mc, c->axisF, c->AF, c->coefF, c->U, c->Fbar);
     }
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

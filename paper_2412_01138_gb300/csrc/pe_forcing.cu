@@ -204,6 +204,7 @@ pe_status launch_time_tables(pe_ctx* c) {
   time_tables_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, c->stream>>>(
       T, c->N, c->M, c->q, c->p, c->t0, c->dT, c->dt, nF, nG, c->AF,
       c->precision == PE_MIXED ? c->AF32 : nullptr, c->AG);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -219,15 +220,18 @@ pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, 
   double* loads = mode == 0 ? axis_out : c->loads;
   loads_1d_kernel<<<grid, 128, 0, c->stream>>>(T, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2],
                                                 G, loads);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   if (mode == 0) return PE_OK;
   for (int a = 0; a < c->g.d; ++a) {
     const int64_t base = (int64_t)nterms * c->g.off[a];
     PE_TRY(dst_axis_f64(c->S[a], loads + base, axis_out + base, nterms, c->g.n[a], 1, c->stream));
+    c->launches += 1;
   }
   const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
   divide_axis_mu_kernel<<<grid, 128, 0, c->stream>>>(c->g, nterms, c->muM_axis, axis_out,
                                                      f32 ? c->axisF32 : nullptr);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -241,6 +245,7 @@ pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* ter
   const int threads = 256;
   outer_sum_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, nterms,
                                                                                                axis_fac, w, out);
+  c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -252,6 +257,7 @@ pe_status launch_forcing_modal(pe_ctx* c, double t, double* out) {
   const int threads = 256;
   outer_sum_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, c->R,
                                                                                                c->axisF, w, out);
+  c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -260,6 +266,7 @@ pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse) {
   const int threads = 256;
   scale_mu_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, c->muM_axis, x,
                                                                                               inverse);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

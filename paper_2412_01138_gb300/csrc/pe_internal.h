@@ -93,6 +93,9 @@ struct pe_ctx {
   float* AF32 = nullptr;
   double* AG = nullptr;         // [N*p*PE_MAX_TERMS]
   double* loads = nullptr;      // [PE_MAX_TERMS * nsum] 1D loads before the DST
+  // accounting
+  int64_t launches = 0;     // kernels launched since the last reset
+  double ms_fine = 0.0;     // device time of fine-propagator kernels since the last reset
   // state
   int k = 0;
   bool have_problem = false;

@@ -134,6 +134,7 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
     PE_CUDA_TRY(cudaFuncSetAttribute(coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   coarse_kernel<<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, c->axisF, c->AG, c->coefG, c->U,
                                                       c->Gold, c->gG);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -146,6 +147,7 @@ pe_status launch_correction(pe_ctx* c, double* num, double* den) {
                                                        c->U, c->partials);
   PE_CUDA_TRY(cudaGetLastError());
   final_reduce_kernel<<<1, 1024, 0, c->stream>>>(c->partials, blocks, c->red);
+  c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   PE_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));

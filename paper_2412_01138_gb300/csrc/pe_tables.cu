@@ -134,6 +134,7 @@ pe_status launch_axis_tables(pe_ctx* c) {
   dim3 grid((nmax + 127) / 128, c->g.d);
   axis_tables_kernel<<<grid, 128, 0, c->stream>>>(c->g, c->h[0], c->g.d > 1 ? c->h[1] : 1.0,
                                                   c->g.d > 2 ? c->h[2] : 1.0, c->muM_axis, c->ratio_axis);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -151,6 +152,7 @@ pe_status launch_coef_tables(pe_ctx* c) {
   coef_tables_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(
       c->g, c->ratio_axis, c->D, c->dt, c->dT, c->M, c->q, c->p, LF, LG, c->lam, c->coefF, c->coefG,
       c->precision == PE_MIXED ? c->coefF32 : nullptr);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

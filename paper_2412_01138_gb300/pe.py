@@ -66,7 +66,8 @@ class pe_forcing(C.Structure):
 class pe_result(C.Structure):
     _fields_ = [("k", C.c_int32), ("residual", C.c_double), ("residual_history", C.POINTER(C.c_double)),
                 ("history_cap", C.c_int32), ("fine_sweeps", C.c_int64), ("ms_tables", C.c_double),
-                ("ms_prepare", C.c_double), ("ms_iterations", C.c_double), ("ms_output", C.c_double)]
+                ("ms_prepare", C.c_double), ("ms_iterations", C.c_double), ("ms_output", C.c_double),
+                ("ms_fine_kernel", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 def load_library(path: str = _LIB_PATH) -> C.CDLL:
@@ -226,7 +227,8 @@ class Solver:
         _check(self._lib.pe_solve(self.ctx, C.byref(f), C.byref(self._forcing()), tol, C.byref(res)))
         return {"k": res.k, "residual": res.residual, "history": list(hist[: min(res.k, history)]),
                 "fine_sweeps": res.fine_sweeps, "ms_tables": res.ms_tables, "ms_prepare": res.ms_prepare,
-                "ms_iterations": res.ms_iterations, "ms_output": res.ms_output}
+                "ms_iterations": res.ms_iterations, "ms_output": res.ms_output,
+                "ms_fine_kernel": res.ms_fine_kernel, "kernel_launches": res.kernel_launches}
 
     # -- outputs ------------------------------------------------------------
     def _out(self, count: int, out):
