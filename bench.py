@@ -167,7 +167,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     prob = workload()
-    n_modes = 256
+    n_modes = 16384
     for _ in range(args.warmup):
         oracle_sample(prob, 32, seed=99)
     t_total, units_total = 0.0, 0
@@ -301,7 +301,7 @@ def main():
 
     # parity of both forms on sampled modes against the oracle (outside the timed region);
     # the same run is the CPU baseline (the oracle as it stands, one core)
-    rate, dt, nm, k_or, sys_, ref, idx = oracle_sample(prob, 256, seed=7, u0_nodal=u0_host)
+    rate, dt, nm, k_or, sys_, ref, idx = oracle_sample(prob, 16384, seed=7, u0_nodal=u0_host)
     w = sys_.norm_w
 
     def rel(a):
