@@ -161,6 +161,15 @@ pe_status pe_set_problem(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f);
 pe_status pe_parareal_iter(pe_ctx* ctx, double* rel_residual_out);
 
 /*
+ * pe_refine -- one Parareal iteration exactly like pe_parareal_iter but with the
+ * fine propagator in float64 whatever pe_options.precision says.  Because G and
+ * F share the homogeneous propagator e^{-lam dT} (up to rounding), one float64
+ * iteration from a mixed-precision iterate reproduces the float64 fine solution
+ * (the float64 refinement of the mixed form).  rel_residual_out: host, may be NULL.
+ */
+pe_status pe_refine(pe_ctx* ctx, double* rel_residual_out);
+
+/*
  * pe_solve -- pe_set_problem, then pe_parareal_iter until r <= tol or k = N
  * (or max_iter), then the inverse DST of U^N into the context's output buffer
  * (read with pe_get_solution).  Returns PE_ENOCONV if max_iter < N stopped it

@@ -345,9 +345,9 @@ extern "C" pe_status pe_set_problem(pe_ctx* c, const pe_field* u0, const pe_forc
   return PE_OK;
 }
 
-static pe_status iter_impl(pe_ctx* c, double* r_out) {
+static pe_status iter_impl(pe_ctx* c, double* r_out, int precision) {
   PE_CUDA_TRY(cudaEventRecord(c->ev[5], c->stream));
-  PE_TRY(launch_fine_sweep(c));
+  PE_TRY(launch_fine_sweep(c, precision));
   PE_CUDA_TRY(cudaEventRecord(c->ev[6], c->stream));
   double num = 0.0, den = 0.0;
   PE_TRY(launch_correction(c, &num, &den));  // synchronises the stream
@@ -366,7 +366,14 @@ extern "C" pe_status pe_parareal_iter(pe_ctx* c, double* rel_residual_out) {
   if (!c) return pe_fail(PE_EINVAL, "pe_parareal_iter: ctx is NULL");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_parareal_iter: no problem set (call pe_set_problem)");
   c->have_output = false;
-  return iter_impl(c, rel_residual_out);
+  return iter_impl(c, rel_residual_out, c->precision);
+}
+
+extern "C" pe_status pe_refine(pe_ctx* c, double* rel_residual_out) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_refine: ctx is NULL");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_refine: no problem set (call pe_set_problem)");
+  c->have_output = false;
+  return iter_impl(c, rel_residual_out, PE_FP64);
 }
 
 extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, pe_result* res) {
@@ -381,7 +388,7 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   double r = INFINITY;
   int hist = 0;
   while (c->k < c->max_iter) {
-    PE_TRY(iter_impl(c, &r));
+    PE_TRY(iter_impl(c, &r, c->precision));
     if (res && res->residual_history && hist < res->history_cap) res->residual_history[hist] = r;
     ++hist;
     if (r <= tol) break;

@@ -4,14 +4,19 @@
 // S_a[j][k] = sqrt(2/(n_a+1)) sin(pi (j+1)(k+1)/(n_a+1)):
 //   last axis   : out[o][j]    = sum_k X[o][k] S[k][j]     (one GEMM, outer x n times n x n)
 //   other axes  : out[o][j][i] = sum_k S[j][k] X[o][k][i]  (batched over o)
-// Both are served by one shared-memory tiled, strided, batched GEMM.  In
-// float64 the kernel is bound by GB300's float64 FMA rate; the transform is
-// applied only to initial data and output on the separable-forcing path.
+// Two kernels serve every axis pass:
+//  * n + 1 = 2^k (n <= 1023): a radix-2 FFT in shared memory.  Two real pencils
+//    x, y are packed as z = x + i y; the odd extension of z over 2(n+1) points is
+//    transformed by an in-place decimation-in-time FFT (bit-reversed load), and
+//    DST(x)_k = -Im V_k / 2, DST(y)_k = Re V_k / 2.  About 5 log2(2n+2) flops per
+//    element instead of the 2n of the matrix form.
+//  * any other n: a shared-memory tiled, strided, batched GEMM with the matrix S_a
+//    (tile shape chosen so that the grid covers the GPU).
 #include "pe_internal.h"
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+constexpr int BK = 16, TM = 4, TN = 4;
 
 struct GemmArgs {
   int rows, cols, K;
@@ -21,13 +26,19 @@ struct GemmArgs {
   int64_t sCb, sCi;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) strided_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B,
-                                                           T* __restrict__ C, GemmArgs g) {
+// BM x BN output tile, (BM/TM) x (BN/TN) threads, each owning a TM x TN block
+// (rows ty + r*(BM/TM), columns tx + s*(BN/TN)).
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) strided_gemm_kernel(const T* __restrict__ A,
+                                                                          const T* __restrict__ B,
+                                                                          T* __restrict__ C, GemmArgs g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int TX = BN / TN;  // threads along a row of the tile
+  constexpr int TY = BM / TM;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN];
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % TX, ty = tid / TX;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   const int64_t b = blockIdx.z;
   const T* Ab = A + b * g.sAb;
@@ -39,12 +50,13 @@ __global__ void __launch_bounds__(256) strided_gemm_kernel(const T* __restrict__
     for (int s = 0; s < TN; ++s) acc[r][s] = T(0);
 
   for (int k0 = 0; k0 < g.K; k0 += BK) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int li = tid / 16 + 16 * r, lk = tid % 16;
+    for (int e = tid; e < BM * BK; e += NT) {
+      const int li = e / BK, lk = e % BK;
       const int gi = i0 + li, gk = k0 + lk;
       As[lk][li] = (gi < g.rows && gk < g.K) ? Ab[gi * g.sAi + gk * g.sAk] : T(0);
-      const int bk = tid / 64 + 4 * r, bj = tid % 64;
+    }
+    for (int e = tid; e < BK * BN; e += NT) {
+      const int bk = e / BN, bj = e % BN;
       const int gk2 = k0 + bk, gj = j0 + bj;
       Bs[bk][bj] = (gk2 < g.K && gj < g.cols) ? Bb[gk2 * g.sBk + gj * g.sBj] : T(0);
     }
@@ -53,9 +65,9 @@ __global__ void __launch_bounds__(256) strided_gemm_kernel(const T* __restrict__
     for (int kk = 0; kk < BK; ++kk) {
       T a[TM], bv[TN];
 #pragma unroll
-      for (int r = 0; r < TM; ++r) a[r] = As[kk][ty + 16 * r];
+      for (int r = 0; r < TM; ++r) a[r] = As[kk][ty + TY * r];
 #pragma unroll
-      for (int s = 0; s < TN; ++s) bv[s] = Bs[kk][tx + 16 * s];
+      for (int s = 0; s < TN; ++s) bv[s] = Bs[kk][tx + TX * s];
 #pragma unroll
       for (int r = 0; r < TM; ++r)
 #pragma unroll
@@ -66,19 +78,20 @@ __global__ void __launch_bounds__(256) strided_gemm_kernel(const T* __restrict__
   T* Cb = C + b * g.sCb;
 #pragma unroll
   for (int r = 0; r < TM; ++r) {
-    const int gi = i0 + ty + 16 * r;
+    const int gi = i0 + ty + TY * r;
     if (gi >= g.rows) continue;
 #pragma unroll
     for (int s = 0; s < TN; ++s) {
-      const int gj = j0 + tx + 16 * s;
+      const int gj = j0 + tx + TX * s;
       if (gj < g.cols) Cb[gi * g.sCi + gj] = acc[r][s];
     }
   }
 }
 
-template <typename T>
-pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_t inner, cudaStream_t st) {
+template <typename T, int BM, int BN>
+pe_status gemm_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_t inner, cudaStream_t st) {
   GemmArgs g{};
+  constexpr int NT = (BM / TM) * (BN / TN);
   if (inner == 1) {
     g.rows = (int)outer; g.cols = n; g.K = n; g.batch = 1;
     g.sAb = 0; g.sAi = n; g.sAk = 1;
@@ -86,7 +99,7 @@ pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_
     g.sCb = 0; g.sCi = n;
     if (outer > (int64_t)1 << 30) return pe_fail(PE_EINVAL, "dst: too many pencils");
     dim3 grid((n + BN - 1) / BN, (unsigned)((outer + BM - 1) / BM), 1);
-    strided_gemm_kernel<T><<<grid, 256, 0, st>>>(in, S, out, g);
+    strided_gemm_kernel<T, BM, BN><<<grid, NT, 0, st>>>(in, S, out, g);
   } else {
     g.rows = n; g.cols = (int)inner; g.K = n; g.batch = outer;
     g.sAb = 0; g.sAi = n; g.sAk = 1;
@@ -94,10 +107,162 @@ pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_
     g.sCb = (int64_t)n * inner; g.sCi = inner;
     if (outer > 65535) return pe_fail(PE_EINVAL, "dst: batch too large");
     dim3 grid((unsigned)((inner + BN - 1) / BN), (n + BM - 1) / BM, (unsigned)outer);
-    strided_gemm_kernel<T><<<grid, 256, 0, st>>>(S, in, out, g);
+    strided_gemm_kernel<T, BM, BN><<<grid, NT, 0, st>>>(S, in, out, g);
   }
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FFT form (n + 1 a power of two)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cplx {
+  T re, im;
+};
+
+template <typename T>
+__device__ inline void sincospi_t(T x, T* s, T* c);
+template <>
+__device__ inline void sincospi_t<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+template <>
+__device__ inline void sincospi_t<float>(float x, float* s, float* c) { sincospif(x, s, c); }
+
+// One CTA transforms `pairs` pencil pairs (2*pairs consecutive pencils) of length n,
+// L = 2(n+1) = 2^logL.  Pencil p lives at o*n*inner + j*inner + i with o = p / inner,
+// i = p % inner.  Dynamic shared memory: pairs*L complex values + L/2 twiddles.
+template <typename T>
+__global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
+                                                      int logL, int64_t inner, int64_t npencils, int pairs,
+                                                      T scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << logL;
+  Cplx<T>* buf = reinterpret_cast<Cplx<T>*>(smem_raw);
+  Cplx<T>* tw = buf + (size_t)pairs * L;
+  const int tid = threadIdx.x, B = blockDim.x;
+  const int64_t p0 = (int64_t)blockIdx.x * (2 * pairs);
+  for (int k = tid; k < L / 2; k += B) {
+    T s, c;
+    sincospi_t<T>((T)(2 * k) / (T)L, &s, &c);
+    tw[k].re = c;
+    tw[k].im = -s;  // e^{-2 pi i k / L}
+  }
+  // zero the two fixed points of the odd extension (positions 0 and n+1)
+  const int np1 = n + 1;
+  const int shift = 32 - logL;
+  for (int q = tid; q < pairs; q += B) {
+    buf[(size_t)q * L + 0] = Cplx<T>{T(0), T(0)};
+    buf[(size_t)q * L + (__brev((unsigned)np1) >> shift)] = Cplx<T>{T(0), T(0)};
+  }
+  // load: consecutive threads take consecutive pencils (coalesced when inner > 1)
+  // or consecutive elements (inner == 1)
+  const int npen = 2 * pairs;
+  for (int e = tid; e < npen * n; e += B) {
+    int pl, j;
+    if (inner == 1) {
+      pl = e / n;
+      j = e - pl * n;
+    } else {
+      j = e / npen;
+      pl = e - j * npen;
+    }
+    const int64_t p = p0 + pl;
+    T v = T(0);
+    if (p < npencils) {
+      const int64_t o = p / inner, i = p - o * inner;
+      v = in[o * (int64_t)n * inner + (int64_t)j * inner + i];
+    }
+    const int q = pl >> 1;
+    const int jj = j + 1;  // 1-based position in the extension
+    const unsigned a = __brev((unsigned)jj) >> shift;
+    const unsigned b = __brev((unsigned)(L - jj)) >> shift;
+    Cplx<T>* row = buf + (size_t)q * L;
+    if (pl & 1) {
+      row[a].im = v;
+      row[b].im = -v;
+    } else {
+      row[a].re = v;
+      row[b].re = -v;
+    }
+  }
+  __syncthreads();
+  // radix-2 decimation-in-time stages
+  for (int s = 1; s <= logL; ++s) {
+    const int half = 1 << (s - 1);
+    const int tstride = L >> s;  // twiddle index stride
+    for (int bfly = tid; bfly < pairs * (L / 2); bfly += B) {
+      const int q = bfly / (L / 2);
+      const int r = bfly - q * (L / 2);
+      const int grp = r / half, pos = r - grp * half;
+      const int i0 = grp * 2 * half + pos, i1 = i0 + half;
+      Cplx<T>* row = buf + (size_t)q * L;
+      const Cplx<T> w = tw[pos * tstride];
+      const Cplx<T> u = row[i0], x = row[i1];
+      const T tr = w.re * x.re - w.im * x.im;
+      const T ti = w.re * x.im + w.im * x.re;
+      row[i0] = Cplx<T>{u.re + tr, u.im + ti};
+      row[i1] = Cplx<T>{u.re - tr, u.im - ti};
+    }
+    __syncthreads();
+  }
+  // store: DST(x)_k = -Im V_k / 2, DST(y)_k = Re V_k / 2, k = 1..n, times sqrt(2/(n+1))
+  for (int e = tid; e < npen * n; e += B) {
+    int pl, k;
+    if (inner == 1) {
+      pl = e / n;
+      k = e - pl * n;
+    } else {
+      k = e / npen;
+      pl = e - k * npen;
+    }
+    const int64_t p = p0 + pl;
+    if (p >= npencils) continue;
+    const Cplx<T> V = buf[(size_t)(pl >> 1) * L + (k + 1)];
+    const T val = (pl & 1) ? V.re * scale : -V.im * scale;
+    const int64_t o = p / inner, i = p - o * inner;
+    out[o * (int64_t)n * inner + (int64_t)k * inner + i] = val;
+  }
+}
+
+inline bool fft_size_ok(int n, int* logL) {
+  const int np1 = n + 1;
+  if (np1 < 2 || np1 > 1024 || (np1 & (np1 - 1)) != 0) return false;
+  int l = 0;
+  while ((1 << l) < 2 * np1) ++l;
+  *logL = l;
+  return true;
+}
+
+template <typename T>
+pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, cudaStream_t st) {
+  const int L = 1 << logL;
+  const int64_t npencils = outer * inner;
+  // pencil pairs per CTA: enough to fill the shared memory moderately and keep
+  // >= 16 consecutive pencils per CTA for coalescing when inner > 1
+  int pairs = (int)((48 * 1024) / ((size_t)L * sizeof(Cplx<T>)));
+  pairs = pairs < 1 ? 1 : (pairs > 16 ? 16 : pairs);
+  const int64_t want_ctas = (npencils + 2 * pairs - 1) / (2 * pairs);
+  const size_t smem = sizeof(Cplx<T>) * ((size_t)pairs * L + L / 2);
+  if (smem > 48 * 1024) {
+    PE_CUDA_TRY(cudaFuncSetAttribute(dst_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  const T scale = (T)(0.5 * sqrt(2.0 / (double)(n + 1)));
+  dst_fft_kernel<T><<<(unsigned)want_ctas, 256, smem, st>>>(in, out, n, logL, inner, npencils, pairs, scale);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+template <typename T>
+pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_t inner, cudaStream_t st) {
+  int logL = 0;
+  if (fft_size_ok(n, &logL)) return fft_axis<T>(in, out, outer, n, inner, logL, st);
+  // matrix form: large tiles when they still give >= 2 CTAs per SM, else small ones
+  const int64_t rows = inner == 1 ? outer : n;
+  const int64_t cols = inner == 1 ? n : inner;
+  const int64_t batch = inner == 1 ? 1 : outer;
+  const int64_t big = ((rows + 63) / 64) * ((cols + 63) / 64) * batch;
+  if (big >= 2 * 152) return gemm_axis<T, 64, 64>(S, in, out, outer, n, inner, st);
+  return gemm_axis<T, 32, 32>(S, in, out, outer, n, inner, st);
 }
 
 // Apply S_a along every axis; tmp (ndof elements) may be null when d == 1 and in != out.

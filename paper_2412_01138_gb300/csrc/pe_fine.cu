@@ -4,13 +4,13 @@
 #include "pe_sweep_common.cuh"
 
 template <int R>
-pe_status fine_launch(pe_ctx* c);
+pe_status fine_launch(pe_ctx* c, int precision);
 
 namespace {
 template <int R>
 struct FineLaunch {
-  static pe_status run(pe_ctx* c) { return fine_launch<R>(c); }
+  static pe_status run(pe_ctx* c, int precision) { return fine_launch<R>(c, precision); }
 };
 }  // namespace
 
-pe_status launch_fine_sweep(pe_ctx* c) { return dispatch_R<FineLaunch>(c->R, c); }
+pe_status launch_fine_sweep(pe_ctx* c, int precision) { return dispatch_R<FineLaunch>(c->R, c, precision); }

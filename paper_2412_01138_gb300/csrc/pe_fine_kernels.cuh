@@ -2,7 +2,7 @@
 // parallel part of each Parareal iteration), Eq. (1-7) applied M times:
 //   c <- E_F c + sum_{i<q} (dt b_i) ghat_J(T_n + (m + c_i) dt),  m = 0..M-1,
 //   ghat_J(t) = sum_r A_r(t) P_{r,J}.
-// One CTA owns one slice n and 256 (float64) or 512 (mixed) consecutive modes.
+// One CTA owns one slice n and 256 (float64) or 256*MPT (mixed) modes.
 // The slice's time factors A_r(t) for all M*q stage times are staged in
 // shared memory and read as warp-wide broadcasts; the per-mode weights
 // P_{r,J}, E_F and b_i stay in registers for the whole slice.  The kernel
@@ -68,75 +68,91 @@ __global__ void __launch_bounds__(256) fine_f64_kernel(Geom g, int M, int q, int
   if (active) Fbar[(int64_t)n * nd + J] = c;
 }
 
-template <int R>
+// MPT modes per thread (threadIdx.x + k * 256 within the CTA's 256*MPT modes, so
+// every global access stays coalesced); each float4 broadcast load of four time
+// factors feeds 4*MPT FMAs.  Rows of the staged table are padded to R4 floats.
+template <int R, int MPT>
 __global__ void __launch_bounds__(256) fine_mixed_kernel(Geom g, int M, int q, int mchunk,
                                                          const float* __restrict__ axisF32,
                                                          const float* __restrict__ AF32,
                                                          const float* __restrict__ coefF32,
                                                          const double* __restrict__ coefF,
                                                          const double* __restrict__ U, double* __restrict__ Fbar) {
-  extern __shared__ float sAf[];
+  constexpr int R4 = (R + 3) / 4 * 4;
+  extern __shared__ __align__(16) float sAf[];
   const int n = blockIdx.y;
   const int64_t nd = g.ndof;
-  const int64_t J0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-  const int64_t J1 = J0 + 1;
-  const bool a0 = J0 < nd, a1 = J1 < nd;
-  float P0[R], P1[R];
-  float b0[PE_MAX_S], b1[PE_MAX_S];
-  float eh0 = 0.f, el0 = 0.f, eh1 = 0.f, el1 = 0.f;
+  const int64_t base = (int64_t)blockIdx.x * (256 * MPT) + threadIdx.x;
+  float P[MPT][R];
+  float b[MPT][PE_MAX_S];
+  float eh[MPT], el[MPT], w[MPT];
 #pragma unroll
-  for (int r = 0; r < R; ++r) { P0[r] = 0.f; P1[r] = 0.f; }
+  for (int k = 0; k < MPT; ++k) {
+    const int64_t J = base + 256 * k;
+    eh[k] = 0.f;
+    el[k] = 0.f;
+    w[k] = 0.f;
 #pragma unroll
-  for (int i = 0; i < PE_MAX_S; ++i) { b0[i] = 0.f; b1[i] = 0.f; }
-  if (a0) {
-    load_P<R, float>(g, J0, axisF32, P0);
-    eh0 = coefF32[J0];
-    el0 = coefF32[nd + J0];
+    for (int r = 0; r < R; ++r) P[k][r] = 0.f;
 #pragma unroll
-    for (int i = 0; i < PE_MAX_S; ++i)
-      if (i < q) b0[i] = coefF32[(2 + i) * nd + J0];
+    for (int i = 0; i < PE_MAX_S; ++i) b[k][i] = 0.f;
+    if (J < nd) {
+      load_P<R, float>(g, J, axisF32, P[k]);
+      eh[k] = coefF32[J];
+      el[k] = coefF32[nd + J];
+#pragma unroll
+      for (int i = 0; i < PE_MAX_S; ++i)
+        if (i < q) b[k][i] = coefF32[(2 + i) * nd + J];
+    }
   }
-  if (a1) {
-    load_P<R, float>(g, J1, axisF32, P1);
-    eh1 = coefF32[J1];
-    el1 = coefF32[nd + J1];
-#pragma unroll
-    for (int i = 0; i < PE_MAX_S; ++i)
-      if (i < q) b1[i] = coefF32[(2 + i) * nd + J1];
-  }
-  float w0 = 0.f, w1 = 0.f;
   const int per_m = q * R;
   const float* An = AF32 + (int64_t)n * M * per_m;
   for (int m0 = 0; m0 < M; m0 += mchunk) {
     const int mc = min(mchunk, M - m0);
     __syncthreads();
-    for (int t = threadIdx.x; t < mc * per_m; t += blockDim.x) sAf[t] = An[(int64_t)m0 * per_m + t];
+    for (int t = threadIdx.x; t < mc * q * R4; t += blockDim.x) {
+      const int row = t / R4, r = t - row * R4;
+      sAf[t] = r < R ? An[((int64_t)m0 * q + row) * R + r] : 0.f;
+    }
     __syncthreads();
     for (int m = 0; m < mc; ++m) {
-      float acc0 = 0.f, acc1 = 0.f;
+      float acc[MPT];
+#pragma unroll
+      for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
 #pragma unroll
       for (int i = 0; i < PE_MAX_S; ++i) {
         if (i < q) {
-          const float* a = sAf + (m * q + i) * R;
-          float g0 = 0.f, g1 = 0.f;
+          const float4* a4 = reinterpret_cast<const float4*>(sAf + (m * q + i) * R4);
+          float gk[MPT];
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float av = a[r];
-            g0 = fmaf(av, P0[r], g0);
-            g1 = fmaf(av, P1[r], g1);
+          for (int k = 0; k < MPT; ++k) gk[k] = 0.f;
+#pragma unroll
+          for (int c4 = 0; c4 < R4 / 4; ++c4) {
+            const float4 v = a4[c4];
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (4 * c4 + e < R) {
+#pragma unroll
+                for (int k = 0; k < MPT; ++k) gk[k] = fmaf(vv[e], P[k][4 * c4 + e], gk[k]);
+              }
+            }
           }
-          acc0 = fmaf(b0[i], g0, acc0);
-          acc1 = fmaf(b1[i], g1, acc1);
+#pragma unroll
+          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(b[k][i], gk[k], acc[k]);
         }
       }
-      w0 = fmaf(eh0, w0, fmaf(el0, w0, acc0));
-      w1 = fmaf(eh1, w1, fmaf(el1, w1, acc1));
+#pragma unroll
+      for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
     }
   }
   const int64_t off = (int64_t)n * nd;
   const double* EM = coefF + (int64_t)(q + 1) * nd;
-  if (a0) Fbar[off + J0] = fma(EM[J0], U[off + J0], (double)w0);
-  if (a1) Fbar[off + J1] = fma(EM[J1], U[off + J1], (double)w1);
+#pragma unroll
+  for (int k = 0; k < MPT; ++k) {
+    const int64_t J = base + 256 * k;
+    if (J < nd) Fbar[off + J] = fma(EM[J], U[off + J], (double)w[k]);
+  }
 }
 
 inline int pick_mchunk(int M, int per_m, size_t elem) {
@@ -149,22 +165,23 @@ inline int pick_mchunk(int M, int per_m, size_t elem) {
 }  // namespace
 
 template <int R>
-pe_status fine_launch(pe_ctx* c) {
+pe_status fine_launch(pe_ctx* c, int precision) {
   const int per_m = c->q * R;
-    if (c->precision == PE_MIXED) {
-      const int mc = pick_mchunk(c->M, per_m, sizeof(float));
-      const int threads = 256;
-      const int64_t pairs = (c->g.ndof + 1) / 2;
-      dim3 grid((unsigned)((pairs + threads - 1) / threads), c->N);
-      fine_mixed_kernel<R><<<grid, threads, sizeof(float) * mc * per_m, c->stream>>>(
-          c->g, c->M, c->q, mc, c->axisF32, c->AF32, c->coefF32, c->coefF, c->U, c->Fbar);
-    } else {
-      const int mc = pick_mchunk(c->M, per_m, sizeof(double));
-      const int threads = 256;
-      dim3 grid((unsigned)((c->g.ndof + threads - 1) / threads), c->N);
-      fine_f64_kernel<R><<<grid, threads, sizeof(double) * mc * per_m, c->stream>>>(
-          c->g, c->M, c->q, mc, c->axisF, c->AF, c->coefF, c->U, c->Fbar);
-    }
+  const int threads = 256;
+  if (precision == PE_MIXED) {
+    constexpr int MPT = R <= 16 ? 4 : 2;
+    constexpr int R4 = (R + 3) / 4 * 4;
+    const int mc = pick_mchunk(c->M, c->q * R4, sizeof(float));
+    const int64_t per_cta = 256 * MPT;
+    dim3 grid((unsigned)((c->g.ndof + per_cta - 1) / per_cta), c->N);
+    fine_mixed_kernel<R, MPT><<<grid, threads, sizeof(float) * mc * c->q * R4, c->stream>>>(
+        c->g, c->M, c->q, mc, c->axisF32, c->AF32, c->coefF32, c->coefF, c->U, c->Fbar);
+  } else {
+    const int mc = pick_mchunk(c->M, per_m, sizeof(double));
+    dim3 grid((unsigned)((c->g.ndof + threads - 1) / threads), c->N);
+    fine_f64_kernel<R><<<grid, threads, sizeof(double) * mc * per_m, c->stream>>>(
+        c->g, c->M, c->q, mc, c->axisF, c->AF, c->coefF, c->U, c->Fbar);
+  }
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;

@@ -127,6 +127,6 @@ pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);  // uses c->S, c
 
 // pe_sweep.cu
 pe_status launch_coarse_sweep(pe_ctx* c);
-pe_status launch_fine_sweep(pe_ctx* c);
+pe_status launch_fine_sweep(pe_ctx* c, int precision);
 pe_status launch_correction(pe_ctx* c, double* num, double* den);
 pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse);

@@ -88,17 +88,28 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
     for (int a = 1; a < g.d; ++a) w *= muM_axis[g.off[a] + j[a]];
     const double E = coefG[J];
     double unew = U[J];
+    // the four streams of slice n+1 are loaded before slice n is combined, so
+    // each thread keeps two slices of loads in flight (the recurrence itself only
+    // carries unew)
+    double g0 = gG[J], f0 = Fbar[J], o0 = Gold[J], u0 = U[nd + J];
     for (int n = 0; n < N; ++n) {
       const int64_t o = (int64_t)n * nd + J;
-      const double Gn = fma(E, unew, gG[o]);
-      const double nxt = (Gn + Fbar[o]) - Gold[o];
+      double g1 = 0.0, f1 = 0.0, o1 = 0.0, u1 = 0.0;
+      if (n + 1 < N) {
+        g1 = gG[o + nd];
+        f1 = Fbar[o + nd];
+        o1 = Gold[o + nd];
+        u1 = U[o + 2 * nd];
+      }
+      const double Gn = fma(E, unew, g0);
+      const double nxt = (Gn + f0) - o0;
       Gold[o] = Gn;
-      const double old = U[o + nd];
       U[o + nd] = nxt;
-      const double df = nxt - old;
+      const double df = nxt - u0;
       sd = fma(w * df, df, sd);
       su = fma(w * nxt, nxt, su);
       unew = nxt;
+      g0 = g1; f0 = f1; o0 = o1; u0 = u1;
     }
   }
   sd = block_sum(sd, sh);

@@ -29,7 +29,7 @@ _STATUS_NAMES = {0: "PE_OK", -1: "PE_EINVAL", -2: "PE_ENOMEM", -3: "PE_ECUDA", -
                  -5: "PE_ENONFINITE", -6: "PE_ETIMEOUT", -7: "PE_ESTATE"}
 
 #: every symbol include/pe.h declares (checked by the CPU test suite)
-EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_solve", "pe_get_solution", "pe_get_modal",
+EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_solve", "pe_get_solution", "pe_get_modal",
             "pe_get_lambda", "pe_get_coefficients", "pe_forcing_modal", "pe_get_nodes", "pe_save_state",
             "pe_load_state", "pe_dst", "pe_dst_f32", "pe_last_error", "pe_destroy")
 
@@ -81,6 +81,7 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
                                C.POINTER(pe_tableau), C.POINTER(pe_options)]),
         "pe_set_problem": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing)]),
         "pe_parareal_iter": (C.c_int, [P, C.POINTER(C.c_double)]),
+        "pe_refine": (C.c_int, [P, C.POINTER(C.c_double)]),
         "pe_solve": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing), C.c_double, C.POINTER(pe_result)]),
         "pe_get_solution": (C.c_int, [P, C.c_int32, P]),
         "pe_get_modal": (C.c_int, [P, C.c_int32, P]),
@@ -213,6 +214,12 @@ class Solver:
     def iterate(self) -> float:
         r = C.c_double()
         _check(self._lib.pe_parareal_iter(self.ctx, C.byref(r)))
+        return r.value
+
+    def refine(self) -> float:
+        """One float64 Parareal iteration (float64 refinement of a mixed-precision iterate)."""
+        r = C.c_double()
+        _check(self._lib.pe_refine(self.ctx, C.byref(r)))
         return r.value
 
     def solve(self, tol: Optional[float] = None, u0_kind: int = PE_FIELD_TERMS_SEPARABLE, nodal=None,

@@ -58,3 +58,22 @@ def test_mixed_config3_full_size_sampled(pe):
         assert info["k"] == 2 and info["residual"] <= 1e-6
         for n in (1, prob.N // 2, prob.N):
             assert _rel(s.modal(n)[idx], ref.U[n], sys_.norm_w) <= TOL_MIXED, n
+
+
+@pytest.mark.parametrize("which", ["c3_small", "c2_small"])
+def test_float64_refinement_reaches_float64_parity(pe, which):
+    """One float64 iteration from the mixed iterate gives the float64 fine solution (<= 1e-12)."""
+    if which == "c3_small":
+        prob = I.scaled(I.config3(), (15, 13, 17), N=16, M=32)
+    else:
+        prob = I.scaled(I.config2(), (63, 50), N=8, M=64)
+    sys_ = osolver.ModalSystem(prob)
+    ref = osolver.parareal(sys_, tol=0.0, k_max=2)
+    with pe.Solver(prob, precision=pe.PE_MIXED) as s:
+        s.solve(tol=1e-6)
+        before = max(_rel(s.modal(n), ref.U[n], sys_.norm_w) for n in range(1, prob.N + 1))
+        r = s.refine()
+        after = max(_rel(s.modal(n), ref.U[n], sys_.norm_w) for n in range(1, prob.N + 1))
+    assert 1e-12 < before <= TOL_MIXED
+    assert after <= 1e-12
+    assert r == pytest.approx(before, rel=0.5)  # the residual of the refinement measures the mixed error

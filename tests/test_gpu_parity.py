@@ -49,7 +49,8 @@ def _bump_problem(n, N, M, seed=11, q=4, p=2, random_coarse=True, R=6, D=0.07, b
 # ---------------------------------------------------------------------------
 # a7: tensor DST-I
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("n", [(1,), (63,), (300,), (17, 29), (64, 65), (5, 7, 9), (31, 1, 33)])
+@pytest.mark.parametrize("n", [(1,), (63,), (300,), (1023,), (17, 29), (64, 65), (255, 255), (511, 3), (5, 7, 9),
+                               (31, 1, 33), (127, 15, 31)])
 def test_dst_matches_oracle(pe, n):
     import torch
 
