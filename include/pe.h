@@ -213,6 +213,65 @@ pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, voi
 /* Same transform in float32 (device in/out). */
 pe_status pe_dst_f32(int32_t d, const int32_t* n, const float* in, float* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched solver: many independent problems (uneven grids, D, sources and
+ * slice counts) advanced together.  Every phase of Algorithm 1 over all
+ * problems is one kernel launch whose CTAs pull (problem, slice, mode-tile)
+ * work items from a queue; the Parareal iteration (fine sweep, correction,
+ * per-problem residuals and stop flags) is captured once as a CUDA graph and
+ * replayed; problems whose residual reached tol (or k = N) drop out.  Only
+ * separable initial data (PE_FIELD_TERMS_SEPARABLE) is accepted; each
+ * problem has at most PE_BATCH_MAX_TERMS forcing terms.
+ * ------------------------------------------------------------------------ */
+#define PE_BATCH_MAX_TERMS 20
+typedef struct pe_batch pe_batch; /* opaque */
+
+typedef struct {
+  int32_t d;
+  int32_t n[3];
+  double box[6];        /* lo0, hi0, lo1, hi1, lo2, hi2 (first 2d used) */
+  double D, t0, T;
+  int32_t n_slices, n_substeps;
+  pe_tableau fine, coarse;
+  pe_field u0;
+  pe_forcing forcing;
+} pe_problem;
+
+typedef struct {
+  int32_t graph_replays;      /* Parareal iterations run (graph launches) */
+  int32_t max_k;              /* largest per-problem iteration count */
+  double max_residual;        /* largest per-problem final relative residual */
+  int64_t fine_dof_substeps;  /* sum over problems of Ndof * N * M * (its fine sweeps) */
+  double ms_prepare;          /* tables, forcing, u0 projection, coarse sweeps */
+  double ms_iterations;       /* all graph replays */
+  int64_t kernel_launches;    /* kernels launched (graph nodes counted per replay) */
+  int32_t threads, ctas_per_sm; /* launch shape of the persistent fine kernel */
+} pe_batch_result;
+
+/* Validate and lay out all problems (one arena per array kind), compute their
+ * spectra and DST-I-free 1D factor transforms.  opt->precision selects the fine
+ * stages (PE_MIXED: float32 stages, float64 tables/correction/residual).
+ * problems: host array of n_problems. */
+pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe_problem* problems, const pe_options* opt);
+
+/* Pick the persistent fine kernel's launch shape (threads per CTA x CTAs per SM)
+ * by timing the candidates on this batch; cache_path (may be NULL) is a text file
+ * of previous choices keyed by device and batch signature, read and appended. */
+pe_status pe_batch_autotune(pe_batch* b, const char* cache_path);
+
+/* Tables, P_h f, U^0, coarse sweeps, then graph replays of the Parareal iteration
+ * until every problem has r <= tol or k = N.  res may be NULL. */
+pe_status pe_batch_solve(pe_batch* b, double tol, pe_batch_result* res);
+
+/* Per-problem modal U^{slice} / nodal u_h(T) (host or device out, Ndof of that problem). */
+pe_status pe_batch_get_modal(pe_batch* b, int32_t problem, int32_t slice, double* out);
+pe_status pe_batch_get_solution(pe_batch* b, int32_t problem, double* nodal_out);
+
+/* Per-problem final relative residuals and iteration counts (host arrays of n_problems; may be NULL). */
+pe_status pe_batch_status(pe_batch* b, double* residuals, int32_t* iterations);
+
+void pe_batch_destroy(pe_batch* b);
+
 /* Most recent error message on this thread ("" if none). */
 const char* pe_last_error(void);
 

@@ -48,7 +48,9 @@ uint64_t splitmix64_next(uint64_t& state) {
 
 const double kMinNodeGap = 1e-3;
 
-pe_status resolve_nodes(const pe_tableau* tb, const char* name, int* s_out, double* c) {
+}  // namespace
+
+pe_status pe_resolve_nodes(const pe_tableau* tb, const char* name, int* s_out, double* c) {
   if (!tb) return pe_fail(PE_EINVAL, std::string(name) + " tableau is NULL");
   const int s = tb->s;
   if (s < 1 || s > PE_MAX_S) return pe_fail(PE_EINVAL, std::string(name) + " tableau: s must be in 1..8");
@@ -77,7 +79,7 @@ pe_status resolve_nodes(const pe_tableau* tb, const char* name, int* s_out, doub
 }
 
 // a[i][m]: coefficient of theta^m in the Lagrange basis polynomial l_i.
-void lagrange_coeffs(int s, const double* c, double a[PE_MAX_S][PE_MAX_S]) {
+void pe_lagrange_coeffs(int s, const double* c, double a[PE_MAX_S][PE_MAX_S]) {
   for (int i = 0; i < PE_MAX_S; ++i)
     for (int m = 0; m < PE_MAX_S; ++m) a[i][m] = 0.0;
   for (int i = 0; i < s; ++i) {
@@ -98,7 +100,7 @@ void lagrange_coeffs(int s, const double* c, double a[PE_MAX_S][PE_MAX_S]) {
   }
 }
 
-bool is_device_ptr(const void* p) {
+bool pe_is_device_ptr(const void* p) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
@@ -106,6 +108,8 @@ bool is_device_ptr(const void* p) {
   }
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
+
+namespace {
 
 template <typename T>
 pe_status dev_alloc(T** p, size_t count) {
@@ -133,14 +137,16 @@ void free_ctx(pe_ctx* c) {
 
 pe_status copy_out(pe_ctx* c, const double* src_dev, double* out, size_t count) {
   if (!out) return pe_fail(PE_EINVAL, "output pointer is NULL");
-  const bool dev = is_device_ptr(out);
+  const bool dev = pe_is_device_ptr(out);
   PE_CUDA_TRY(cudaMemcpyAsync(out, src_dev, sizeof(double) * count,
                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PE_OK;
 }
 
-pe_status validate_terms(int n, const pe_term* t, int d, const char* what) {
+}  // namespace
+
+pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what) {
   if (n < 0 || n > PE_MAX_TERMS) return pe_fail(PE_EINVAL, std::string(what) + ": n_terms must be in 0..32");
   if (n > 0 && !t) return pe_fail(PE_EINVAL, std::string(what) + ": terms is NULL");
   for (int i = 0; i < n; ++i) {
@@ -155,6 +161,8 @@ pe_status validate_terms(int n, const pe_term* t, int d, const char* what) {
   }
   return PE_OK;
 }
+
+namespace {
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
@@ -211,11 +219,11 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   c->N = n_slices; c->M = n_substeps;
   c->dT = T / (double)n_slices;
   c->dt = c->dT / (double)n_substeps;
-  pe_status st = resolve_nodes(fine, "fine", &c->q, c->cF);
-  if (st == PE_OK) st = resolve_nodes(coarse, "coarse", &c->p, c->cG);
+  pe_status st = pe_resolve_nodes(fine, "fine", &c->q, c->cF);
+  if (st == PE_OK) st = pe_resolve_nodes(coarse, "coarse", &c->p, c->cG);
   if (st != PE_OK) { delete c; return st; }
-  lagrange_coeffs(c->q, c->cF, c->lagF);
-  lagrange_coeffs(c->p, c->cG, c->lagG);
+  pe_lagrange_coeffs(c->q, c->cF, c->lagF);
+  pe_lagrange_coeffs(c->p, c->cG, c->lagG);
   pe_options o{};
   if (opt) o = *opt;
   if (o.precision != PE_FP64 && o.precision != PE_MIXED) { delete c; return pe_fail(PE_EINVAL, "pe_setup: bad precision"); }
@@ -288,7 +296,7 @@ extern "C" void pe_destroy(pe_ctx* c) {
 static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
   if (!u0) return pe_fail(PE_EINVAL, "pe_set_problem: u0 is NULL");
   const int nf = f ? f->n_terms : 0;
-  PE_TRY(validate_terms(nf, f ? f->terms : nullptr, c->g.d, "forcing"));
+  PE_TRY(pe_validate_terms(nf, f ? f->terms : nullptr, c->g.d, "forcing"));
   if (nf == 0) {
     // no source: one zero term keeps every kernel shape valid
     c->R = 1;
@@ -306,7 +314,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   // U^0 = P_h u0
   double* U0 = c->U;
   if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {
-    PE_TRY(validate_terms(u0->n_terms, u0->terms, c->g.d, "u0"));
+    PE_TRY(pe_validate_terms(u0->n_terms, u0->terms, c->g.d, "u0"));
     if (u0->n_terms == 0) {
       PE_CUDA_TRY(cudaMemsetAsync(U0, 0, sizeof(double) * c->g.ndof, c->stream));
     } else if (u0->kind == PE_FIELD_TERMS_SEPARABLE) {
@@ -321,7 +329,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     }
   } else if (u0->kind == PE_FIELD_NODAL) {
     if (!u0->nodal) return pe_fail(PE_EINVAL, "pe_set_problem: nodal u0 is NULL");
-    const bool dev = is_device_ptr(u0->nodal);
+    const bool dev = pe_is_device_ptr(u0->nodal);
     PE_CUDA_TRY(cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->g.ndof,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     PE_TRY(dst_nd_f64(c, c->work0, U0));

@@ -1,0 +1,456 @@
+// Batched Parareal EIFE-linear: many independent problems in one set of launches.
+//
+// Each array kind (slice arrays, tables, forcing factors) lives in one arena; a
+// device table of per-problem records (BProb) holds offsets into the arenas.
+// Work is cut into items:
+//   mode items  (problem, 256 consecutive modes)          coefficient tables, U^0,
+//                                                         coarse sweep, correction
+//   fine items  (problem, slice n, threads*MPT modes)     fine propagator
+// The fine kernel is persistent: every CTA pulls items from an atomic counter
+// and dispatches on the problem's number of forcing terms R (each R has its own
+// register-resident tile body).  One Parareal iteration (reset of the counter,
+// fine sweep, correction, per-problem residual + stop flags, readback of the
+// number of active problems) is captured once as a CUDA graph and replayed.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <fstream>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "pe_batch.h"
+#include "pe_phi.cuh"
+
+namespace {
+
+__device__ __forceinline__ int find_prob(const int64_t* __restrict__ prefix, int P, int64_t idx) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= idx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// setup kernels
+// ---------------------------------------------------------------------------
+__global__ void b_axis_tables_kernel(const BProb* __restrict__ probs, const int64_t* __restrict__ mu_prefix, int P,
+                                     int64_t total, double* __restrict__ muM, double* __restrict__ ratio) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int p = find_prob(mu_prefix, P, idx);
+  const BProb& B = probs[p];
+  const int local = (int)(idx - B.oMu);
+  int a = 0;
+  while (a + 1 < B.g.d && local >= B.g.off[a + 1]) ++a;
+  const int j = local - B.g.off[a];
+  const double h = B.h[a];
+  const double np1 = (double)(B.g.n[a] + 1);
+  const double cth = cospi((double)(j + 1) / np1);
+  const double sh = sinpi((double)(j + 1) / (2.0 * np1));
+  const double mM = (h / 3.0) * (2.0 + cth);
+  const double mK = (4.0 / h) * (sh * sh);
+  muM[idx] = mM;
+  ratio[idx] = mK / mM;
+}
+
+__global__ void b_coef_tables_kernel(const BProb* __restrict__ probs, const ModeItem* __restrict__ items,
+                                     int n_items, const double* __restrict__ ratio, double* __restrict__ coefF,
+                                     double* __restrict__ coefG, float* __restrict__ coefF32) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const ModeItem m = items[it];
+    const BProb& B = probs[m.p];
+    const int64_t J = m.J0 + threadIdx.x;
+    if (J >= B.g.ndof) continue;
+    const int64_t nd = B.g.ndof;
+    int j[PE_MAX_D];
+    unflatten(B.g, J, j);
+    double s = 0.0;
+    for (int a = 0; a < B.g.d; ++a) s += ratio[B.oMu + B.g.off[a] + j[a]];
+    const double lam = B.D * s;
+    Lag LF, LG;
+    for (int i = 0; i < PE_MAX_S; ++i)
+      for (int k = 0; k < PE_MAX_S; ++k) {
+        LF.a[i][k] = B.lagF[i][k];
+        LG.a[i][k] = B.lagG[i][k];
+      }
+    double b[PE_MAX_S];
+    {
+      const double z = -lam * B.dt;
+      const double E = exp(z);
+      b_weights(z, B.q, LF, b);
+      double* cf = coefF + B.oCF;
+      cf[J] = E;
+      for (int i = 0; i < B.q; ++i) cf[(1 + i) * nd + J] = B.dt * b[i];
+      cf[(B.q + 1) * nd + J] = exp(-lam * ((double)B.M * B.dt));
+      if (coefF32) {
+        float* c32 = coefF32 + B.oCF;
+        const float ehi = (float)E;
+        c32[J] = ehi;
+        c32[nd + J] = (float)(E - (double)ehi);
+        for (int i = 0; i < B.q; ++i) c32[(2 + i) * nd + J] = (float)(B.dt * b[i]);
+      }
+    }
+    {
+      const double z = -lam * B.dT;
+      b_weights(z, B.p, LG, b);
+      double* cg = coefG + B.oCG;
+      cg[J] = exp(z);
+      for (int i = 0; i < B.p; ++i) cg[(1 + i) * nd + J] = B.dT * b[i];
+    }
+  }
+}
+
+// fine (n, m, i, r) and coarse (n, i, r) time factors of every problem
+__global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int64_t* __restrict__ tt_prefix, int P,
+                                     int64_t total, const pe_term* __restrict__ terms, double* __restrict__ AF,
+                                     float* __restrict__ AF32, double* __restrict__ AG) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int p = find_prob(tt_prefix, P, idx);
+  const BProb& B = probs[p];
+  const int R = B.R;
+  const int64_t nf = (int64_t)B.N * B.M * B.q * R;
+  int64_t local = idx - tt_prefix[p];
+  if (local < nf) {
+    int64_t rest = local;
+    const int r = (int)(rest % R); rest /= R;
+    const int i = (int)(rest % B.q); rest /= B.q;
+    const int m = (int)(rest % B.M); rest /= B.M;
+    const int n = (int)rest;
+    const double Tn = B.t0 + (double)n * B.dT;
+    const double tl = Tn + (double)m * B.dt;
+    const double t = tl + B.cF[i] * B.dt;
+    const pe_term& T = terms[B.tf + r];
+    const double v = T.amp * eval_time(T, t);
+    AF[B.oAF + local] = v;
+    if (AF32) AF32[B.oAF + local] = (float)v;
+  } else {
+    local -= nf;
+    int64_t rest = local;
+    const int r = (int)(rest % R); rest /= R;
+    const int i = (int)(rest % B.p); rest /= B.p;
+    const int n = (int)rest;
+    const double Tn = B.t0 + (double)n * B.dT;
+    const double t = Tn + B.cG[i] * B.dT;
+    const pe_term& T = terms[B.tf + r];
+    AG[B.oAG + local] = T.amp * eval_time(T, t);
+  }
+}
+
+// One CTA per (problem, axis, term): the 1D consistent load of the term's factor
+// on that axis, its DST-I (sine table in shared memory) and the division by mu^M.
+__global__ void b_axis_factor_kernel(const BProb* __restrict__ probs, const FactorJob* __restrict__ jobs,
+                                     const pe_term* __restrict__ terms, Gauss G, const double* __restrict__ muM,
+                                     double* __restrict__ axisF, float* __restrict__ axisF32,
+                                     double* __restrict__ axisU0) {
+  extern __shared__ double sh[];
+  const FactorJob job = jobs[blockIdx.x];
+  const BProb& B = probs[job.p];
+  const int a = job.axis;
+  const int n = B.g.n[a];
+  const int period = 2 * (n + 1);
+  double* F = sh;             // [n]
+  double* tab = sh + n;       // [period]: sin(pi m/(n+1))
+  const pe_term& T = terms[job.u0 ? B.tu + job.r : B.tf + job.r];
+  const double lo = B.lo[a], h = B.h[a];
+  for (int m = threadIdx.x; m < period; m += blockDim.x) tab[m] = sinpi((double)m / (double)(n + 1));
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double left = 0.0, right = 0.0;
+    for (int qi = 0; qi < G.npts; ++qi) {
+      const double xl = lo + ((double)k + G.s[qi]) * h;
+      const double xr = lo + ((double)(k + 1) + G.s[qi]) * h;
+      left += G.w[qi] * eval_space(T.skind[a], T.sp[a], xl) * G.s[qi];
+      right += G.w[qi] * eval_space(T.skind[a], T.sp[a], xr) * (1.0 - G.s[qi]);
+    }
+    F[k] = h * left + h * right;
+  }
+  __syncthreads();
+  const double scale = sqrt(2.0 / (double)(n + 1));
+  const int Rj = job.u0 ? B.Ru : B.R;
+  const int64_t obase = (job.u0 ? B.oAxU : B.oAx) + (int64_t)Rj * B.g.off[a] + (int64_t)job.r * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double acc = 0.0;
+    int idx = 0;
+    const int step = j + 1;
+    for (int k = 0; k < n; ++k) {
+      idx += step;
+      if (idx >= period) idx -= period;
+      acc = fma(tab[idx], F[k], acc);
+    }
+    const double v = scale * acc / muM[B.oMu + B.g.off[a] + j];
+    if (job.u0) {
+      axisU0[obase + j] = v;
+    } else {
+      axisF[obase + j] = v;
+      if (axisF32) axisF32[obase + j] = (float)v;
+    }
+  }
+}
+
+// U^0 = sum_t amp_t prod_a axisU0 (P_h of separable initial data)
+__global__ void b_u0_kernel(const BProb* __restrict__ probs, const ModeItem* __restrict__ items, int n_items,
+                            const pe_term* __restrict__ terms, const double* __restrict__ axisU0,
+                            double* __restrict__ U) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const ModeItem m = items[it];
+    const BProb& B = probs[m.p];
+    const int64_t J = m.J0 + threadIdx.x;
+    if (J >= B.g.ndof) continue;
+    int j[PE_MAX_D];
+    unflatten(B.g, J, j);
+    double acc = 0.0;
+    for (int t = 0; t < B.Ru; ++t) {
+      double v = axisU0[B.oAxU + (int64_t)B.Ru * B.g.off[0] + (int64_t)t * B.g.n[0] + j[0]];
+      for (int a = 1; a < B.g.d; ++a) v *= axisU0[B.oAxU + (int64_t)B.Ru * B.g.off[a] + (int64_t)t * B.g.n[a] + j[a]];
+      acc += terms[B.tu + t].amp * v;
+    }
+    U[B.oU + J] = acc;
+  }
+}
+
+// coarse sweep (k = 0) of every problem; P_{r,J} staged per thread in shared memory
+__global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__ probs,
+                                                       const ModeItem* __restrict__ items, int n_items,
+                                                       const double* __restrict__ axisF, const double* __restrict__ AG,
+                                                       const double* __restrict__ coefG, double* __restrict__ U,
+                                                       double* __restrict__ Gold, double* __restrict__ gG) {
+  extern __shared__ double sP[];  // [PE_BATCH_MAX_TERMS][256]
+  const int tid = threadIdx.x, BD = blockDim.x;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const ModeItem m = items[it];
+    const BProb& B = probs[m.p];
+    const int64_t J = m.J0 + tid;
+    if (J >= B.g.ndof) continue;
+    const int64_t nd = B.g.ndof;
+    const int R = B.R;
+    int j[PE_MAX_D];
+    unflatten(B.g, J, j);
+    for (int r = 0; r < R; ++r) {
+      double v = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
+      for (int a = 1; a < B.g.d; ++a) v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+      sP[r * BD + tid] = v;
+    }
+    const double* cg = coefG + B.oCG;
+    const double E = cg[J];
+    double b[PE_MAX_S];
+    for (int i = 0; i < B.p; ++i) b[i] = cg[(1 + i) * nd + J];
+    double* Up = U + B.oU;
+    double* Gp = Gold + B.oS;
+    double* gp = gG + B.oS;
+    const double* ag = AG + B.oAG;
+    double c = Up[J];
+    for (int n = 0; n < B.N; ++n) {
+      double acc = 0.0;
+      for (int i = 0; i < B.p; ++i) {
+        const double* arow = ag + ((int64_t)n * B.p + i) * R;
+        double gi = 0.0;
+        for (int r = 0; r < R; ++r) gi = fma(__ldg(arow + r), sP[r * BD + tid], gi);
+        acc = fma(b[i], gi, acc);
+      }
+      gp[(int64_t)n * nd + J] = acc;
+      c = fma(E, c, acc);
+      Up[(int64_t)(n + 1) * nd + J] = c;
+      Gp[(int64_t)n * nd + J] = c;
+    }
+  }
+}
+
+template <typename T>
+__device__ inline T block_sum(T v, T* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T out = T(0);
+  if (threadIdx.x < 32) {
+    T x = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : T(0);
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    out = x;
+  }
+  __syncthreads();
+  return out;
+}
+
+// correction + residual partial sums of every active problem (item-strided grid)
+__global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restrict__ probs,
+                                                           const ModeItem* __restrict__ items, int n_items,
+                                                           const int* __restrict__ active,
+                                                           const double* __restrict__ muM,
+                                                           const double* __restrict__ coefG,
+                                                           const double* __restrict__ gG,
+                                                           const double* __restrict__ Fbar, double* __restrict__ Gold,
+                                                           double* __restrict__ U, double* __restrict__ partials) {
+  __shared__ double sh[32];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const ModeItem m = items[it];
+    const BProb& B = probs[m.p];
+    if (!active[m.p]) continue;  // uniform over the CTA
+    const int64_t J = m.J0 + threadIdx.x;
+    double sd = 0.0, su = 0.0;
+    if (J < B.g.ndof) {
+      const int64_t nd = B.g.ndof;
+      int j[PE_MAX_D];
+      unflatten(B.g, J, j);
+      double w = muM[B.oMu + B.g.off[0] + j[0]];
+      for (int a = 1; a < B.g.d; ++a) w *= muM[B.oMu + B.g.off[a] + j[a]];
+      const double E = coefG[B.oCG + J];
+      double* Up = U + B.oU;
+      double* Gp = Gold + B.oS;
+      const double* gp = gG + B.oS;
+      const double* fp = Fbar + B.oS;
+      double unew = Up[J];
+      double g0 = gp[J], f0 = fp[J], o0 = Gp[J], u0 = Up[nd + J];
+      for (int n = 0; n < B.N; ++n) {
+        const int64_t o = (int64_t)n * nd + J;
+        double g1 = 0.0, f1 = 0.0, o1 = 0.0, u1 = 0.0;
+        if (n + 1 < B.N) {
+          g1 = gp[o + nd];
+          f1 = fp[o + nd];
+          o1 = Gp[o + nd];
+          u1 = Up[o + 2 * nd];
+        }
+        const double Gn = fma(E, unew, g0);
+        const double nxt = (Gn + f0) - o0;
+        Gp[o] = Gn;
+        Up[o + nd] = nxt;
+        const double df = nxt - u0;
+        sd = fma(w * df, df, sd);
+        su = fma(w * nxt, nxt, su);
+        unew = nxt;
+        g0 = g1; f0 = f1; o0 = o1; u0 = u1;
+      }
+    }
+    sd = block_sum(sd, sh);
+    su = block_sum(su, sh);
+    if (threadIdx.x == 0) {
+      partials[2 * it] = sd;
+      partials[2 * it + 1] = su;
+    }
+  }
+}
+
+// one CTA per problem: residual, iteration count, stop flag, active count
+__global__ void b_reduce_kernel(const BProb* __restrict__ probs, int P, const double* __restrict__ partials,
+                                int* __restrict__ active, int* __restrict__ kcount, double* __restrict__ resid,
+                                double tol, int* __restrict__ n_active, int* __restrict__ nonfinite) {
+  __shared__ double sh[32];
+  const int p = blockIdx.x;
+  if (p >= P) return;
+  const BProb& B = probs[p];
+  if (!active[p]) return;  // uniform
+  double sd = 0.0, su = 0.0;
+  for (int i = threadIdx.x; i < B.nItems; i += blockDim.x) {
+    sd += partials[2 * (B.oItems + i)];
+    su += partials[2 * (B.oItems + i) + 1];
+  }
+  sd = block_sum(sd, sh);
+  su = block_sum(su, sh);
+  if (threadIdx.x == 0) {
+    const double r = su > 0.0 ? sqrt(sd) / sqrt(su) : sqrt(sd);
+    resid[p] = r;
+    const int k = kcount[p] + 1;
+    kcount[p] = k;
+    if (!isfinite(r)) {
+      atomicExch(nonfinite, 1);
+      active[p] = 0;
+    } else if (r <= tol || k >= B.N) {
+      active[p] = 0;
+    } else {
+      atomicAdd(n_active, 1);
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+pe_status batch_set_attributes(pe_batch* b) {
+  const size_t smem = sizeof(double) * (size_t)(b->nmax + 2 * (b->nmax + 1));
+  PE_CUDA_TRY(cudaFuncSetAttribute(b_axis_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t csmem = sizeof(double) * PE_BATCH_MAX_TERMS * 256;
+  PE_CUDA_TRY(cudaFuncSetAttribute(b_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+  return batch_fine_set_smem(b->precision, b->fine_smem);
+}
+
+pe_status batch_launch_axis_tables(pe_batch* b) {
+  const int64_t total = b->mu_total;
+  b_axis_tables_kernel<<<(unsigned)((total + 255) / 256), 256, 0, b->stream>>>(b->d_probs, b->d_mu_prefix, b->P,
+                                                                              total, b->muM, b->ratio);
+  b->launches += 1;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status batch_launch_prepare(pe_batch* b) {
+  const int grid_items = b->sm_count * 8;
+  // coefficient tables
+  b_coef_tables_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->ratio,
+                                                         b->coefF, b->coefG, b->coefF32);
+  // time factors
+  b_time_tables_kernel<<<(unsigned)((b->tt_total + 255) / 256), 256, 0, b->stream>>>(
+      b->d_probs, b->d_tt_prefix, b->P, b->tt_total, b->d_terms, b->AF, b->AF32, b->AG);
+  // per-axis factors of forcing and initial data
+  const size_t smem = sizeof(double) * (size_t)(b->nmax + 2 * (b->nmax + 1));
+  b_axis_factor_kernel<<<b->n_factor_jobs, 256, smem, b->stream>>>(b->d_probs, b->d_factor_jobs, b->d_terms,
+                                                                   b->gauss, b->muM, b->axisF, b->axisF32,
+                                                                   b->axisU0);
+  b_u0_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->d_terms, b->axisU0,
+                                                 b->U);
+  const size_t csmem = sizeof(double) * PE_BATCH_MAX_TERMS * 256;
+  b_coarse_kernel<<<grid_items, 256, csmem, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF,
+                                                          b->AG, b->coefG, b->U, b->Gold, b->gG);
+  b->launches += 5;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+static pe_status launch_fine(pe_batch* b, cudaStream_t st, int threads, int ctas_per_sm) {
+  const FineItems& fi = threads == 128 ? b->fine128 : b->fine256;
+  BatchArrays A{};
+  A.axisF = b->axisF; A.axisF32 = b->axisF32; A.AF = b->AF; A.AF32 = b->AF32;
+  A.coefF = b->coefF; A.coefF32 = b->coefF32; A.U = b->U; A.Fbar = b->Fbar;
+  const int grid = b->sm_count * ctas_per_sm;
+  if (b->precision == PE_MIXED)
+    return batch_launch_fine_mixed(b->d_probs, fi.d_items, fi.n, b->active, b->counter, A, grid, threads,
+                                   b->fine_smem, st);
+  return batch_launch_fine_f64(b->d_probs, fi.d_items, fi.n, b->active, b->counter, A, grid, threads, b->fine_smem,
+                               st);
+}
+
+pe_status batch_enqueue_iteration(pe_batch* b, cudaStream_t st, double tol) {
+  PE_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), st));
+  PE_CUDA_TRY(cudaMemsetAsync(b->n_active, 0, sizeof(int), st));
+  PE_TRY(launch_fine(b, st, b->tune_threads, b->tune_ctas));
+  b_correction_kernel<<<b->sm_count * 8, 256, 0, st>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->active,
+                                                       b->muM, b->coefG, b->gG, b->Fbar, b->Gold, b->U, b->partials);
+  b_reduce_kernel<<<b->P, 256, 0, st>>>(b->d_probs, b->P, b->partials, b->active, b->kcount, b->resid, tol,
+                                        b->n_active, b->nonfinite);
+  PE_CUDA_TRY(cudaMemcpyAsync(b->h_flags, b->n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status batch_time_fine(pe_batch* b, int threads, int ctas, float* ms) {
+  cudaEvent_t e0, e1;
+  PE_CUDA_TRY(cudaEventCreate(&e0));
+  PE_CUDA_TRY(cudaEventCreate(&e1));
+  PE_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+  PE_CUDA_TRY(cudaEventRecord(e0, b->stream));
+  PE_TRY(launch_fine(b, b->stream, threads, ctas));
+  PE_CUDA_TRY(cudaEventRecord(e1, b->stream));
+  PE_CUDA_TRY(cudaEventSynchronize(e1));
+  PE_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->launches += 1;
+  return PE_OK;
+}

@@ -1,0 +1,130 @@
+// Internal layout of the batched solver (pe_batch): per-problem records,
+// work items and arenas.  Not part of the ABI.
+#pragma once
+#include <vector>
+
+#include "pe_forcing_common.cuh"
+#include "pe_internal.h"
+
+// One problem of the batch, as the kernels see it (offsets index the arenas).
+struct BProb {
+  Geom g;
+  int N, M, q, p, R, Ru;   // slices, substeps, fine/coarse stages, forcing / u0 terms
+  int mchunk;              // substeps of time factors staged per shared-memory fill
+  int tf, tu;              // first forcing / u0 term in the terms array
+  double D, t0, dT, dt;
+  double lo[PE_MAX_D], h[PE_MAX_D];
+  double cF[PE_MAX_S], cG[PE_MAX_S];
+  double lagF[PE_MAX_S][PE_MAX_S], lagG[PE_MAX_S][PE_MAX_S];
+  int64_t oU;    // U arena: (N+1)*ndof
+  int64_t oS;    // Gold/Fbar/gG arenas: N*ndof
+  int64_t oCF;   // coefF / coefF32 arenas: (q+2)*ndof
+  int64_t oCG;   // coefG arena: (p+1)*ndof
+  int64_t oAx;   // axisF / axisF32: R*nsum
+  int64_t oAxU;  // axisU0: Ru*nsum
+  int64_t oAF;   // AF / AF32: N*M*q*R
+  int64_t oAG;   // AG: N*p*R
+  int64_t oMu;   // muM / ratio: nsum
+  int64_t oItems;  // first mode item of this problem
+  int nItems;
+};
+
+struct ModeItem {
+  int p;
+  int pad;
+  int64_t J0;
+};
+
+struct FineItem {
+  int p;
+  int n;
+  int64_t J0;
+};
+
+struct FactorJob {
+  int p, axis, r, u0;
+};
+
+struct BatchArrays {
+  const double* axisF;
+  const float* axisF32;
+  const double* AF;
+  const float* AF32;
+  const double* coefF;
+  const float* coefF32;
+  const double* U;
+  double* Fbar;
+};
+
+struct FineItems {
+  FineItem* d_items = nullptr;
+  int n = 0;
+};
+
+struct pe_batch {
+  int P = 0;
+  int precision = PE_MIXED;
+  int quad_pts = 3;
+  int sm_count = 152;
+  cudaStream_t stream = nullptr;   // owned, non-blocking (graph capture needs one)
+  cudaStream_t user_stream = nullptr;
+  std::vector<BProb> probs;
+  BProb* d_probs = nullptr;
+  std::vector<pe_term> terms;
+  pe_term* d_terms = nullptr;
+  Gauss gauss;
+  int nmax = 1;
+  // items
+  ModeItem* d_mode_items = nullptr;
+  int n_mode_items = 0;
+  FineItems fine128, fine256;
+  FactorJob* d_factor_jobs = nullptr;
+  int n_factor_jobs = 0;
+  int64_t* d_mu_prefix = nullptr;
+  int64_t mu_total = 0;
+  int64_t* d_tt_prefix = nullptr;
+  int64_t tt_total = 0;
+  size_t fine_smem = 0;
+  // arenas
+  double *muM = nullptr, *ratio = nullptr;
+  double *coefF = nullptr, *coefG = nullptr;
+  float* coefF32 = nullptr;
+  double *U = nullptr, *Gold = nullptr, *Fbar = nullptr, *gG = nullptr;
+  double *axisF = nullptr, *axisU0 = nullptr;
+  float* axisF32 = nullptr;
+  double *AF = nullptr, *AG = nullptr;
+  float* AF32 = nullptr;
+  double* partials = nullptr;
+  // per-problem iteration state
+  int *active = nullptr, *kcount = nullptr;
+  double* resid = nullptr;
+  int* counter = nullptr;
+  int* dflags = nullptr;   // [0] active problems after the last iteration, [1] non-finite seen
+  int* n_active = nullptr;
+  int* nonfinite = nullptr;
+  int* h_flags = nullptr;  // pinned copy of dflags
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  double graph_tol = -1.0;
+  int graph_threads = 0, graph_ctas = 0;
+  // launch shape of the persistent fine kernel
+  int tune_threads = 256, tune_ctas = 2;
+  bool tuned = false;
+  bool have_problem = false;
+  int64_t launches = 0;
+  uint64_t signature = 0;
+};
+
+// pe_batch.cu
+pe_status batch_set_attributes(pe_batch* b);
+pe_status batch_launch_axis_tables(pe_batch* b);
+pe_status batch_launch_prepare(pe_batch* b);
+pe_status batch_enqueue_iteration(pe_batch* b, cudaStream_t st, double tol);
+pe_status batch_time_fine(pe_batch* b, int threads, int ctas, float* ms);
+// pe_batch_fine_*.cu
+pe_status batch_launch_fine_mixed(const BProb* probs, const FineItem* items, int n_items, const int* active,
+                                  int* counter, BatchArrays A, int grid, int threads, size_t smem, cudaStream_t st);
+pe_status batch_launch_fine_f64(const BProb* probs, const FineItem* items, int n_items, const int* active,
+                                int* counter, BatchArrays A, int grid, int threads, size_t smem, cudaStream_t st);
+pe_status batch_fine_set_smem(int precision, size_t smem);

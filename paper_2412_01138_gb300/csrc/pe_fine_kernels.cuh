@@ -19,100 +19,76 @@
 
 namespace {
 
-template <int R>
-__global__ void __launch_bounds__(256) fine_f64_kernel(Geom g, int M, int q, int mchunk,
-                                                       const double* __restrict__ axisF,
-                                                       const double* __restrict__ AF,
-                                                       const double* __restrict__ coefF,
-                                                       const double* __restrict__ U, double* __restrict__ Fbar) {
-  extern __shared__ double sA[];
-  const int n = blockIdx.y;
-  const int64_t nd = g.ndof;
-  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = J < nd;
-  double P[R];
-  double b[PE_MAX_S];
-  double E = 0.0, c = 0.0;
-  if (active) {
-    load_P<R, double>(g, J, axisF, P);
-    E = coefF[J];
+// Operands of one fine-propagator tile: one slice n of one problem, blockDim.x*MPT
+// modes starting at `base` (thread t owns base + t + k*blockDim.x, k < MPT, so every
+// global access stays coalesced).
+struct FineTile {
+  Geom g;
+  int M, q, mchunk;
+  int64_t base;
+  const float* axisF32;   // per-axis modal factors (float)
+  const double* axisF;    // per-axis modal factors (double)
+  const float* AFn32;     // time factors of slice n [M][q][R] (float)
+  const double* AFn;      // time factors of slice n [M][q][R] (double)
+  const float* coefF32;   // E_hi, E_lo, dt*b_i  (rows of ndof)
+  const double* coefF;    // E, dt*b_i, exp(-lam M dt) (rows of ndof)
+  const double* Un;       // U^n
+  double* Fn;             // F^M(U^n)
+};
+
+// P[r] = prod_a axisF[R*off[a] + r*n_a + j_a] for r < R, zero for R <= r < RC.
+template <int RC, typename T>
+__device__ __forceinline__ void load_P_rt(const Geom& g, int64_t J, const T* __restrict__ axisF, int R, T* P) {
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
 #pragma unroll
-    for (int i = 0; i < PE_MAX_S; ++i)
-      if (i < q) b[i] = coefF[(1 + i) * nd + J];
-    c = U[(int64_t)n * nd + J];
-  }
-  const int per_m = q * R;
-  const double* An = AF + (int64_t)n * M * per_m;
-  for (int m0 = 0; m0 < M; m0 += mchunk) {
-    const int mc = min(mchunk, M - m0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < mc * per_m; t += blockDim.x) sA[t] = An[(int64_t)m0 * per_m + t];
-    __syncthreads();
-    if (active) {
-      for (int m = 0; m < mc; ++m) {
-        double acc = 0.0;
-#pragma unroll
-        for (int i = 0; i < PE_MAX_S; ++i) {
-          if (i < q) {
-            const double* a = sA + (m * q + i) * R;
-            double gi = 0.0;
-#pragma unroll
-            for (int r = 0; r < R; ++r) gi = fma(a[r], P[r], gi);
-            acc = fma(b[i], gi, acc);
-          }
-        }
-        c = fma(E, c, acc);
-      }
+  for (int r = 0; r < RC; ++r) {
+    T v = T(0);
+    if (r < R) {
+      v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+      for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     }
+    P[r] = v;
   }
-  if (active) Fbar[(int64_t)n * nd + J] = c;
 }
 
-// MPT modes per thread (threadIdx.x + k * 256 within the CTA's 256*MPT modes, so
-// every global access stays coalesced); each float4 broadcast load of four time
-// factors feeds 4*MPT FMAs.  Rows of the staged table are padded to R4 floats.
-template <int R, int MPT>
-__global__ void __launch_bounds__(256) fine_mixed_kernel(Geom g, int M, int q, int mchunk,
-                                                         const float* __restrict__ axisF32,
-                                                         const float* __restrict__ AF32,
-                                                         const float* __restrict__ coefF32,
-                                                         const double* __restrict__ coefF,
-                                                         const double* __restrict__ U, double* __restrict__ Fbar) {
-  constexpr int R4 = (R + 3) / 4 * 4;
-  extern __shared__ __align__(16) float sAf[];
-  const int n = blockIdx.y;
+// Mixed precision, R <= RC forcing terms (RC a multiple of 4): each float4 broadcast
+// load of four time factors feeds 4*MPT FMAs; staged rows are zero-padded to RC.
+template <int RC, int MPT>
+__device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float* sAf) {
+  static_assert(RC % 4 == 0, "RC must be a multiple of 4");
+  const Geom& g = a.g;
+  const int q = a.q, M = a.M, B = blockDim.x;
   const int64_t nd = g.ndof;
-  const int64_t base = (int64_t)blockIdx.x * (256 * MPT) + threadIdx.x;
-  float P[MPT][R];
+  const int64_t base = a.base + threadIdx.x;
+  float P[MPT][RC];
   float b[MPT][PE_MAX_S];
   float eh[MPT], el[MPT], w[MPT];
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
-    const int64_t J = base + 256 * k;
+    const int64_t J = base + (int64_t)B * k;
     eh[k] = 0.f;
     el[k] = 0.f;
     w[k] = 0.f;
 #pragma unroll
-    for (int r = 0; r < R; ++r) P[k][r] = 0.f;
+    for (int r = 0; r < RC; ++r) P[k][r] = 0.f;
 #pragma unroll
     for (int i = 0; i < PE_MAX_S; ++i) b[k][i] = 0.f;
     if (J < nd) {
-      load_P<R, float>(g, J, axisF32, P[k]);
-      eh[k] = coefF32[J];
-      el[k] = coefF32[nd + J];
+      load_P_rt<RC, float>(g, J, a.axisF32, R, P[k]);
+      eh[k] = a.coefF32[J];
+      el[k] = a.coefF32[nd + J];
 #pragma unroll
       for (int i = 0; i < PE_MAX_S; ++i)
-        if (i < q) b[k][i] = coefF32[(2 + i) * nd + J];
+        if (i < q) b[k][i] = a.coefF32[(2 + i) * nd + J];
     }
   }
-  const int per_m = q * R;
-  const float* An = AF32 + (int64_t)n * M * per_m;
-  for (int m0 = 0; m0 < M; m0 += mchunk) {
-    const int mc = min(mchunk, M - m0);
+  for (int m0 = 0; m0 < M; m0 += a.mchunk) {
+    const int mc = min(a.mchunk, M - m0);
     __syncthreads();
-    for (int t = threadIdx.x; t < mc * q * R4; t += blockDim.x) {
-      const int row = t / R4, r = t - row * R4;
-      sAf[t] = r < R ? An[((int64_t)m0 * q + row) * R + r] : 0.f;
+    for (int t = threadIdx.x; t < mc * q * RC; t += B) {
+      const int row = t / RC, r = t - row * RC;
+      sAf[t] = r < R ? a.AFn32[((int64_t)m0 * q + row) * R + r] : 0.f;
     }
     __syncthreads();
     for (int m = 0; m < mc; ++m) {
@@ -122,65 +98,144 @@ __global__ void __launch_bounds__(256) fine_mixed_kernel(Geom g, int M, int q, i
 #pragma unroll
       for (int i = 0; i < PE_MAX_S; ++i) {
         if (i < q) {
-          const float4* a4 = reinterpret_cast<const float4*>(sAf + (m * q + i) * R4);
-          float gk[MPT];
+          const float4* a4 = reinterpret_cast<const float4*>(sAf + (m * q + i) * RC);
+          // two partial sums per mode (even / odd float4 chunks) shorten the FMA chains
+          float ge[MPT], go[MPT];
 #pragma unroll
-          for (int k = 0; k < MPT; ++k) gk[k] = 0.f;
+          for (int k = 0; k < MPT; ++k) {
+            ge[k] = 0.f;
+            go[k] = 0.f;
+          }
 #pragma unroll
-          for (int c4 = 0; c4 < R4 / 4; ++c4) {
+          for (int c4 = 0; c4 < RC / 4; ++c4) {
             const float4 v = a4[c4];
-            const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              if (4 * c4 + e < R) {
-#pragma unroll
-                for (int k = 0; k < MPT; ++k) gk[k] = fmaf(vv[e], P[k][4 * c4 + e], gk[k]);
-              }
+            for (int k = 0; k < MPT; ++k) {
+              float& g2 = (c4 & 1) ? go[k] : ge[k];
+              g2 = fmaf(v.x, P[k][4 * c4 + 0], g2);
+              g2 = fmaf(v.y, P[k][4 * c4 + 1], g2);
+              g2 = fmaf(v.z, P[k][4 * c4 + 2], g2);
+              g2 = fmaf(v.w, P[k][4 * c4 + 3], g2);
             }
           }
 #pragma unroll
-          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(b[k][i], gk[k], acc[k]);
+          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(b[k][i], ge[k] + go[k], acc[k]);
         }
       }
 #pragma unroll
       for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
     }
   }
-  const int64_t off = (int64_t)n * nd;
-  const double* EM = coefF + (int64_t)(q + 1) * nd;
+  const double* EM = a.coefF + (int64_t)(q + 1) * nd;
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
-    const int64_t J = base + 256 * k;
-    if (J < nd) Fbar[off + J] = fma(EM[J], U[off + J], (double)w[k]);
+    const int64_t J = base + (int64_t)B * k;
+    if (J < nd) a.Fn[J] = fma(EM[J], a.Un[J], (double)w[k]);
   }
 }
 
-inline int pick_mchunk(int M, int per_m, size_t elem) {
-  const size_t budget = 48 * 1024;
-  int mc = (int)(budget / (elem * (size_t)per_m));
-  if (mc < 1) mc = 1;
-  return mc < M ? mc : M;
+// Float64, R <= RC forcing terms: one mode per thread, the plain recurrence of Eq. (1-7).
+template <int RC>
+__device__ __forceinline__ void fine_f64_tile(const FineTile& a, int R, double* sA) {
+  const Geom& g = a.g;
+  const int q = a.q, M = a.M, B = blockDim.x;
+  const int64_t nd = g.ndof;
+  const int64_t J = a.base + threadIdx.x;
+  const bool active = J < nd;
+  double P[RC];
+  double b[PE_MAX_S];
+  double E = 0.0, c = 0.0;
+  if (active) {
+    load_P_rt<RC, double>(g, J, a.axisF, R, P);
+    E = a.coefF[J];
+#pragma unroll
+    for (int i = 0; i < PE_MAX_S; ++i)
+      if (i < q) b[i] = a.coefF[(1 + i) * nd + J];
+    c = a.Un[J];
+  }
+  for (int m0 = 0; m0 < M; m0 += a.mchunk) {
+    const int mc = min(a.mchunk, M - m0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < mc * q * RC; t += B) {
+      const int row = t / RC, r = t - row * RC;
+      sA[t] = r < R ? a.AFn[((int64_t)m0 * q + row) * R + r] : 0.0;
+    }
+    __syncthreads();
+    if (active) {
+      for (int m = 0; m < mc; ++m) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < PE_MAX_S; ++i) {
+          if (i < q) {
+            const double* ap = sA + (m * q + i) * RC;
+            double gi = 0.0;
+#pragma unroll
+            for (int r = 0; r < RC; ++r) gi = fma(ap[r], P[r], gi);
+            acc = fma(b[i], gi, acc);
+          }
+        }
+        c = fma(E, c, acc);
+      }
+    }
+  }
+  if (active) a.Fn[J] = c;
+}
+
+template <int R, int MPT>
+__global__ void __launch_bounds__(256) fine_mixed_kernel(FineTile t, int64_t slice_stride_af) {
+  constexpr int RC = (R + 3) / 4 * 4;
+  extern __shared__ __align__(16) float sAf[];
+  const int n = blockIdx.y;
+  const int64_t nd = t.g.ndof;
+  t.base = (int64_t)blockIdx.x * (blockDim.x * MPT);
+  t.AFn32 += (int64_t)n * slice_stride_af;
+  t.Un += (int64_t)n * nd;
+  t.Fn += (int64_t)n * nd;
+  fine_mixed_tile<RC, MPT>(t, R, sAf);
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) fine_f64_kernel(FineTile t, int64_t slice_stride_af) {
+  extern __shared__ __align__(16) double sA[];
+  const int n = blockIdx.y;
+  const int64_t nd = t.g.ndof;
+  t.base = (int64_t)blockIdx.x * blockDim.x;
+  t.AFn += (int64_t)n * slice_stride_af;
+  t.Un += (int64_t)n * nd;
+  t.Fn += (int64_t)n * nd;
+  fine_f64_tile<R>(t, R, sA);
 }
 
 }  // namespace
 
+
 template <int R>
 pe_status fine_launch(pe_ctx* c, int precision) {
-  const int per_m = c->q * R;
   const int threads = 256;
+  FineTile t{};
+  t.g = c->g;
+  t.M = c->M;
+  t.q = c->q;
+  t.axisF32 = c->axisF32;
+  t.axisF = c->axisF;
+  t.AFn32 = c->AF32;
+  t.AFn = c->AF;
+  t.coefF32 = c->coefF32;
+  t.coefF = c->coefF;
+  t.Un = c->U;
+  t.Fn = c->Fbar;
+  const int64_t stride = (int64_t)c->M * c->q * R;
   if (precision == PE_MIXED) {
     constexpr int MPT = R <= 16 ? 4 : 2;
     constexpr int R4 = (R + 3) / 4 * 4;
-    const int mc = pick_mchunk(c->M, c->q * R4, sizeof(float));
-    const int64_t per_cta = 256 * MPT;
+    t.mchunk = pick_mchunk(c->M, c->q * R4, sizeof(float));
+    const int64_t per_cta = (int64_t)threads * MPT;
     dim3 grid((unsigned)((c->g.ndof + per_cta - 1) / per_cta), c->N);
-    fine_mixed_kernel<R, MPT><<<grid, threads, sizeof(float) * mc * c->q * R4, c->stream>>>(
-        c->g, c->M, c->q, mc, c->axisF32, c->AF32, c->coefF32, c->coefF, c->U, c->Fbar);
+    fine_mixed_kernel<R, MPT><<<grid, threads, sizeof(float) * t.mchunk * c->q * R4, c->stream>>>(t, stride);
   } else {
-    const int mc = pick_mchunk(c->M, per_m, sizeof(double));
+    t.mchunk = pick_mchunk(c->M, c->q * R, sizeof(double));
     dim3 grid((unsigned)((c->g.ndof + threads - 1) / threads), c->N);
-    fine_f64_kernel<R><<<grid, threads, sizeof(double) * mc * per_m, c->stream>>>(
-        c->g, c->M, c->q, mc, c->axisF, c->AF, c->coefF, c->U, c->Fbar);
+    fine_f64_kernel<R><<<grid, threads, sizeof(double) * t.mchunk * c->q * R, c->stream>>>(t, stride);
   }
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());

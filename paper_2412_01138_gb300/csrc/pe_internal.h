@@ -103,9 +103,23 @@ struct pe_ctx {
   cudaEvent_t ev[8];
 };
 
+// Substeps of time factors (per_m values each) staged per shared-memory fill.
+inline int pick_mchunk(int M, int per_m, size_t elem) {
+  const size_t budget = 48 * 1024;
+  int mc = (int)(budget / (elem * (size_t)per_m));
+  if (mc < 1) mc = 1;
+  return mc < M ? mc : M;
+}
+
 // ---------------------------------------------------------------------------
 // launchers (each returns a pe_status and reports errors through pe_set_error)
 // ---------------------------------------------------------------------------
+// pe_api.cu (shared host helpers)
+pe_status pe_resolve_nodes(const pe_tableau* tb, const char* name, int* s_out, double* c);
+void pe_lagrange_coeffs(int s, const double* c, double a[PE_MAX_S][PE_MAX_S]);
+bool pe_is_device_ptr(const void* p);
+pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what);
+
 // pe_tables.cu
 pe_status launch_axis_tables(pe_ctx* c);
 pe_status launch_coef_tables(pe_ctx* c);

@@ -14,10 +14,10 @@
 #include <math.h>
 
 #include "pe_internal.h"
+#include "pe_phi.cuh"
+
 
 namespace {
-
-__constant__ double c_inv_fact[48];
 
 // 1D eigenvalue tables of every axis, concatenated.
 __global__ void axis_tables_kernel(Geom g, double h0, double h1, double h2, double* muM, double* ratio) {
@@ -32,38 +32,6 @@ __global__ void axis_tables_kernel(Geom g, double h0, double h1, double h2, doub
   const double mK = (4.0 / h) * (sh * sh);
   muM[g.off[a] + j] = mM;
   ratio[g.off[a] + j] = mK / mM;
-}
-
-// phi_1..phi_s at z into ph[0..s-1].
-__device__ inline void phi_all(double z, int s, double* ph) {
-  if (fabs(z) < 2.0) {
-    const int K = 27;
-    double acc = c_inv_fact[K + s];
-    for (int k = K - 1; k >= 0; --k) acc = fma(acc, z, c_inv_fact[k + s]);
-    ph[s - 1] = acc;
-    for (int j = s - 1; j >= 1; --j) ph[j - 1] = fma(z, ph[j], c_inv_fact[j]);
-  } else {
-    ph[0] = expm1(z) / z;
-    for (int j = 1; j < s; ++j) ph[j] = (ph[j - 1] - c_inv_fact[j]) / z;
-  }
-}
-
-struct Lag {
-  double a[PE_MAX_S][PE_MAX_S];  // a[i][m]: coefficient of theta^m in l_i
-};
-
-__device__ inline void b_weights(double z, int s, const Lag& L, double* b) {
-  double ph[PE_MAX_S];
-  phi_all(z, s, ph);
-  for (int i = 0; i < s; ++i) {
-    double acc = 0.0;
-    double mf = 1.0;  // m!
-    for (int m = 0; m < s; ++m) {
-      acc = fma(L.a[i][m] * mf, ph[m], acc);
-      mf *= (double)(m + 1);
-    }
-    b[i] = acc;
-  }
 }
 
 __global__ void coef_tables_kernel(Geom g, const double* __restrict__ ratio, double D, double dt, double dT,
@@ -114,18 +82,6 @@ __global__ void dst_matrix_kernel(int n, double* S) {
   S[(int64_t)j * n + k] = sqrt(2.0 / (double)(n + 1)) * sinpi((double)m / (double)(n + 1));
 }
 
-bool g_fact_ready = false;
-
-pe_status ensure_factorials() {
-  if (g_fact_ready) return PE_OK;
-  double f[48];
-  f[0] = 1.0;
-  for (int i = 1; i < 48; ++i) f[i] = f[i - 1] / (double)i;
-  PE_CUDA_TRY(cudaMemcpyToSymbol(c_inv_fact, f, sizeof(f)));
-  g_fact_ready = true;
-  return PE_OK;
-}
-
 }  // namespace
 
 pe_status launch_axis_tables(pe_ctx* c) {
@@ -140,7 +96,6 @@ pe_status launch_axis_tables(pe_ctx* c) {
 }
 
 pe_status launch_coef_tables(pe_ctx* c) {
-  PE_TRY(ensure_factorials());
   Lag LF{}, LG{};
   for (int i = 0; i < PE_MAX_S; ++i)
     for (int m = 0; m < PE_MAX_S; ++m) {

@@ -31,7 +31,9 @@ _STATUS_NAMES = {0: "PE_OK", -1: "PE_EINVAL", -2: "PE_ENOMEM", -3: "PE_ECUDA", -
 #: every symbol include/pe.h declares (checked by the CPU test suite)
 EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_solve", "pe_get_solution", "pe_get_modal",
             "pe_get_lambda", "pe_get_coefficients", "pe_forcing_modal", "pe_get_nodes", "pe_save_state",
-            "pe_load_state", "pe_dst", "pe_dst_f32", "pe_last_error", "pe_destroy")
+            "pe_load_state", "pe_dst", "pe_dst_f32", "pe_last_error", "pe_destroy", "pe_setup_batch",
+            "pe_batch_autotune", "pe_batch_solve", "pe_batch_get_modal", "pe_batch_get_solution", "pe_batch_status",
+            "pe_batch_destroy")
 
 
 class PEError(RuntimeError):
@@ -70,6 +72,18 @@ class pe_result(C.Structure):
                 ("ms_fine_kernel", C.c_double), ("kernel_launches", C.c_int64)]
 
 
+class pe_problem(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n", C.c_int32 * 3), ("box", C.c_double * 6), ("D", C.c_double),
+                ("t0", C.c_double), ("T", C.c_double), ("n_slices", C.c_int32), ("n_substeps", C.c_int32),
+                ("fine", pe_tableau), ("coarse", pe_tableau), ("u0", pe_field), ("forcing", pe_forcing)]
+
+
+class pe_batch_result(C.Structure):
+    _fields_ = [("graph_replays", C.c_int32), ("max_k", C.c_int32), ("max_residual", C.c_double),
+                ("fine_dof_substeps", C.c_int64), ("ms_prepare", C.c_double), ("ms_iterations", C.c_double),
+                ("kernel_launches", C.c_int64), ("threads", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
 def load_library(path: str = _LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libpe is not built ({path} missing); run python -m paper_2412_01138_gb300.build")
@@ -94,6 +108,13 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_dst": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
         "pe_dst_f32": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
         "pe_last_error": (C.c_char_p, []),
+        "pe_setup_batch": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(pe_problem), C.POINTER(pe_options)]),
+        "pe_batch_autotune": (C.c_int, [P, C.c_char_p]),
+        "pe_batch_solve": (C.c_int, [P, C.c_double, C.POINTER(pe_batch_result)]),
+        "pe_batch_get_modal": (C.c_int, [P, C.c_int32, C.c_int32, P]),
+        "pe_batch_get_solution": (C.c_int, [P, C.c_int32, P]),
+        "pe_batch_status": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+        "pe_batch_destroy": (None, [P]),
         "pe_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -290,3 +311,76 @@ def dst(d: int, n: Sequence[int], x_in, x_out, stream=None, f32: bool = False):
     nn = (C.c_int32 * d)(*n)
     fn = lib().pe_dst_f32 if f32 else lib().pe_dst
     _check(fn(d, nn, _ptr(x_in), _ptr(x_out), stream_handle(stream)))
+
+
+class BatchSolver:
+    """One pe_batch: many independent problems advanced by shared persistent launches."""
+
+    def __init__(self, probs: Sequence["_in.Problem"], precision: int = PE_MIXED, stream=None):
+        self.probs = list(probs)
+        self._lib = lib()
+        arr = (pe_problem * len(self.probs))()
+        self._keep = []
+        for k, p in enumerate(self.probs):
+            q = arr[k]
+            q.d = p.d
+            for a in range(p.d):
+                q.n[a] = p.n[a]
+                q.box[2 * a], q.box[2 * a + 1] = p.box[a]
+            q.D, q.t0, q.T = p.D, p.t0, p.T
+            q.n_slices, q.n_substeps = p.N, p.M
+            cF = (C.c_double * p.q)(*p.fine_nodes)
+            cG = (C.c_double * p.p)(*p.coarse_nodes)
+            tu = make_terms(p.u0)
+            tf = make_terms(p.forcing)
+            self._keep += [cF, cG, tu, tf]
+            q.fine = pe_tableau(p.q, C.cast(cF, C.POINTER(C.c_double)), 0, 0)
+            q.coarse = pe_tableau(p.p, C.cast(cG, C.POINTER(C.c_double)), 0, 0)
+            q.u0 = pe_field(PE_FIELD_TERMS_SEPARABLE, len(p.u0), C.cast(tu, C.POINTER(pe_term)), None)
+            q.forcing = pe_forcing(len(p.forcing), C.cast(tf, C.POINTER(pe_term)))
+        opt = pe_options(precision, PE_DST_AUTO, self.probs[0].quad_pts, 0, stream_handle(stream))
+        ctx = C.c_void_p()
+        _check(self._lib.pe_setup_batch(C.byref(ctx), len(self.probs), arr, C.byref(opt)))
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.pe_batch_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def autotune(self, cache_path: Optional[str] = None):
+        _check(self._lib.pe_batch_autotune(self.ctx, cache_path.encode() if cache_path else None))
+
+    def solve(self, tol: float) -> dict:
+        res = pe_batch_result()
+        _check(self._lib.pe_batch_solve(self.ctx, tol, C.byref(res)))
+        return {f: getattr(res, f) for f, _ in pe_batch_result._fields_}
+
+    def modal(self, problem: int, slice_: int, out=None):
+        out = np.empty(self.probs[problem].ndof) if out is None else out
+        _check(self._lib.pe_batch_get_modal(self.ctx, problem, slice_, _ptr(out)))
+        return out
+
+    def solution(self, problem: int, out=None):
+        out = np.empty(self.probs[problem].ndof) if out is None else out
+        _check(self._lib.pe_batch_get_solution(self.ctx, problem, _ptr(out)))
+        return out
+
+    def status(self):
+        r = np.empty(len(self.probs))
+        k = np.empty(len(self.probs), dtype=np.int32)
+        _check(self._lib.pe_batch_status(self.ctx, r.ctypes.data_as(C.POINTER(C.c_double)),
+                                         k.ctypes.data_as(C.POINTER(C.c_int32))))
+        return r, k

@@ -1,0 +1,111 @@
+"""GPU parity of the batched solver (uneven problems, one set of persistent launches).
+
+Float64 batches must match the oracle problem by problem to relative L2 <= 1e-12;
+mixed-precision batches (float32 fine stages) to <= 1e-6, the batched workload's bound.
+"""
+import numpy as np
+import pytest
+
+from oracle import solver as osolver
+from paper_2412_01138_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_01138_gb300 import pe as _pe
+
+    _pe.lib()
+    return _pe
+
+
+def _rel(a, b, w):
+    return float(np.sqrt(np.sum(w * (a - b) ** 2)) / np.sqrt(np.sum(w * b * b)))
+
+
+def _mixed_batch():
+    """Uneven small problems: d = 1, 2, 3, different R (1..20), N, M, q, p, D, boxes."""
+    probs = []
+    for i in range(10):
+        p = I.config4_problem(i)
+        probs.append(I.scaled(p, (7 + 5 * i, 40 - 3 * i), N=2 + (i % 5), M=3 + (i % 4)))
+    rng = I.SplitMix64(77)
+    box1 = ((0.0, 2.0),)
+    u0, f, _ = I.sin_mode(1, box1, 0.4)
+    probs.append(I.Problem(1, (100,), box1, 0.4, 0.1, 0.9, 6, 5, I.uniform_nodes(3), I.draw_random_nodes(2, 3),
+                           u0, f + I.gaussian_bumps(rng, 1, 19), 3, 1e-12))
+    box3 = ((0.0, 1.0), (0.0, 0.5), (0.0, 1.5))
+    u0, f, _ = I.sin_mode(3, box3, 0.2)
+    probs.append(I.Problem(3, (9, 6, 11), box3, 0.2, 0.0, 1.0, 4, 4, I.uniform_nodes(4), I.uniform_nodes(2),
+                           u0, f + I.gaussian_bumps(rng, 3, 3), 3, 1e-12))
+    probs.append(I.Problem(2, (5, 5), ((0.0, 1.0),) * 2, 1.0, 0.0, 1.0, 1, 2, I.uniform_nodes(2),
+                           I.uniform_nodes(1), I.sin_mode(2, ((0.0, 1.0),) * 2, 1.0)[0], (), 3, 1e-12))
+    return probs
+
+
+def test_batch_float64_matches_oracle_per_problem(pe):
+    probs = _mixed_batch()
+    with pe.BatchSolver(probs, precision=pe.PE_FP64) as b:
+        info = b.solve(tol=1e-12)
+        r, k = b.status()
+        for i, prob in enumerate(probs):
+            sys_ = osolver.ModalSystem(prob)
+            ref = osolver.parareal(sys_, tol=1e-12)
+            assert k[i] == ref.k, (i, k[i], ref.k)
+            for n in range(prob.N + 1):
+                assert _rel(b.modal(i, n), ref.U[n], sys_.norm_w) <= 1e-12, (i, n)
+            nodal = b.solution(i)
+            ref_nodal = sys_.to_nodal(ref.U[-1]).reshape(-1)
+            assert np.abs(nodal - ref_nodal).max() <= 1e-12 * np.abs(ref_nodal).max(), i
+    assert info["max_k"] == max(k)
+    assert info["fine_dof_substeps"] == sum(p.ndof * p.N * p.M * int(kk) for p, kk in zip(probs, k))
+
+
+def test_batch_mixed_matches_oracle_per_problem(pe):
+    probs = _mixed_batch()
+    with pe.BatchSolver(probs, precision=pe.PE_MIXED) as b:
+        b.solve(tol=1e-6)
+        r, k = b.status()
+        for i, prob in enumerate(probs):
+            sys_ = osolver.ModalSystem(prob)
+            ref = osolver.parareal(sys_, tol=0.0, k_max=prob.N)
+            assert r[i] <= 1e-6 or k[i] == prob.N
+            for n in range(1, prob.N + 1):
+                assert _rel(b.modal(i, n), ref.U[n], sys_.norm_w) <= 1e-6, (i, n)
+
+
+def test_batch_autotune_and_cache(pe, tmp_path):
+    probs = _mixed_batch()
+    cache = tmp_path / "tune.txt"
+    with pe.BatchSolver(probs, precision=pe.PE_MIXED) as b:
+        b.autotune(str(cache))
+        info = b.solve(tol=1e-6)
+        assert info["threads"] in (128, 256) and 1 <= info["ctas_per_sm"] <= 4
+    text = cache.read_text().split()
+    assert len(text) == 3 and int(text[1]) == info["threads"] and int(text[2]) == info["ctas_per_sm"]
+    with pe.BatchSolver(probs, precision=pe.PE_MIXED) as b2:
+        b2.autotune(str(cache))  # read back, no new line
+        assert b2.solve(tol=1e-6)["threads"] == info["threads"]
+    assert len(cache.read_text().strip().splitlines()) == 1
+
+
+def test_batch_config4_full(pe):
+    """The 512-problem batched workload (mixed precision) to rel residual 1e-6, sampled parity."""
+    probs = I.config4()
+    with pe.BatchSolver(probs, precision=pe.PE_MIXED) as b:
+        b.autotune(None)
+        info = b.solve(tol=1e-6)
+        r, k = b.status()
+        assert np.all(r <= 1e-6) and np.all(k == 2)
+        assert info["graph_replays"] == 2
+        rng = np.random.default_rng(4)
+        for i in (0, 1, 137, 511):
+            prob = probs[i]
+            idx = np.unique(np.concatenate([[0, prob.ndof - 1], rng.integers(0, prob.ndof, 64)]))
+            sys_ = osolver.ModalSystem(prob, modes=idx)
+            ref = osolver.parareal(sys_, tol=0.0, k_max=1)
+            assert _rel(b.modal(i, prob.N)[idx], ref.U[prob.N], sys_.norm_w) <= 1e-6, i
