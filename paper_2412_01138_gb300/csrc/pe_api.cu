@@ -126,7 +126,7 @@ void free_ctx(pe_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->muM_axis, c->ratio_axis, c->S[0], c->S[1], c->S[2], c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Gold, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
-                  c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->loads};
+                  c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -263,6 +263,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->AF, N * n_substeps * c->q * MT);
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AF32, N * n_substeps * c->q * MT);
   if (st == PE_OK) st = dev_alloc(&c->AG, N * c->p * MT);
+  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AG32, N * c->p * MT);
   if (st == PE_OK && cudaMallocHost((void**)&c->h_red, 4 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");

@@ -12,6 +12,8 @@
 //    element instead of the 2n of the matrix form.
 //  * any other n: a shared-memory tiled, strided, batched GEMM with the matrix S_a
 //    (tile shape chosen so that the grid covers the GPU).
+#include <mutex>
+
 #include "pe_internal.h"
 
 namespace {
@@ -134,19 +136,14 @@ __device__ inline void sincospi_t<float>(float x, float* s, float* c) { sincospi
 template <typename T>
 __global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
                                                       int logL, int64_t inner, int64_t npencils, int pairs,
-                                                      T scale) {
+                                                      T scale, const Cplx<T>* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
   Cplx<T>* buf = reinterpret_cast<Cplx<T>*>(smem_raw);
   Cplx<T>* tw = buf + (size_t)pairs * L;
   const int tid = threadIdx.x, B = blockDim.x;
   const int64_t p0 = (int64_t)blockIdx.x * (2 * pairs);
-  for (int k = tid; k < L / 2; k += B) {
-    T s, c;
-    sincospi_t<T>((T)(2 * k) / (T)L, &s, &c);
-    tw[k].re = c;
-    tw[k].im = -s;  // e^{-2 pi i k / L}
-  }
+  for (int k = tid; k < L / 2; k += B) tw[k] = twg[k];  // e^{-2 pi i k / L}
   // zero the two fixed points of the odd extension (positions 0 and n+1)
   const int np1 = n + 1;
   const int shift = 32 - logL;
@@ -234,20 +231,65 @@ inline bool fft_size_ok(int n, int* logL) {
 }
 
 template <typename T>
+__global__ void twiddle_kernel(int L, Cplx<T>* tw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L / 2) return;
+  T s, c;
+  sincospi_t<T>((T)(2 * k) / (T)L, &s, &c);
+  tw[k].re = c;
+  tw[k].im = -s;
+}
+
+// Twiddles e^{-2 pi i k/L}, k < L/2, of every FFT length 2(n+1) <= 2048 (L = 2^1..2^11),
+// built once per process and device-resident: table for length L starts at L/2 - 1.
+template <typename T>
+const Cplx<T>* twiddles(int logL, cudaStream_t st) {
+  static Cplx<T>* table[64] = {nullptr};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!table[dev]) {
+    Cplx<T>* p = nullptr;
+    if (cudaMalloc((void**)&p, sizeof(Cplx<T>) * 2048) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int l = 1; l <= 11; ++l) {
+      const int L = 1 << l;
+      twiddle_kernel<T><<<(L / 2 + 255) / 256, 256, 0, st>>>(L, p + (L / 2 - 1));
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(p);
+      return nullptr;
+    }
+    table[dev] = p;
+  }
+  const int L = 1 << logL;
+  return table[dev] + (L / 2 - 1);
+}
+
+template <typename T>
 pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, cudaStream_t st) {
   const int L = 1 << logL;
   const int64_t npencils = outer * inner;
-  // pencil pairs per CTA: enough to fill the shared memory moderately and keep
-  // >= 16 consecutive pencils per CTA for coalescing when inner > 1
-  int pairs = (int)((48 * 1024) / ((size_t)L * sizeof(Cplx<T>)));
-  pairs = pairs < 1 ? 1 : (pairs > 16 ? 16 : pairs);
+  const Cplx<T>* tw = twiddles<T>(logL, st);
+  if (!tw) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  // pencil pairs per CTA: as many as keep >= 2 CTAs per SM, bounded by shared memory
+  int max_pairs = (int)((48 * 1024) / ((size_t)L * sizeof(Cplx<T>)));
+  max_pairs = max_pairs < 1 ? 1 : (max_pairs > 16 ? 16 : max_pairs);
+  int64_t pairs64 = (npencils + 1) / 2 / (2 * 152);
+  int pairs = (int)(pairs64 < 1 ? 1 : (pairs64 > max_pairs ? max_pairs : pairs64));
   const int64_t want_ctas = (npencils + 2 * pairs - 1) / (2 * pairs);
   const size_t smem = sizeof(Cplx<T>) * ((size_t)pairs * L + L / 2);
   if (smem > 48 * 1024) {
     PE_CUDA_TRY(cudaFuncSetAttribute(dst_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   const T scale = (T)(0.5 * sqrt(2.0 / (double)(n + 1)));
-  dst_fft_kernel<T><<<(unsigned)want_ctas, 256, smem, st>>>(in, out, n, logL, inner, npencils, pairs, scale);
+  const int threads = L / 2 * pairs >= 256 ? 256 : (L / 2 * pairs >= 128 ? 128 : 64);
+  dst_fft_kernel<T><<<(unsigned)want_ctas, threads, smem, st>>>(in, out, n, logL, inner, npencils, pairs, scale, tw);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

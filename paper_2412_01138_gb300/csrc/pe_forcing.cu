@@ -19,7 +19,7 @@ namespace {
 // AF[((n*M + m)*q + i)*R + r] and AG[(n*p + i)*R + r]
 __global__ void time_tables_kernel(TermsDev T, int N, int M, int q, int p, double t0, double dT, double dt,
                                    Nodes cF, Nodes cG, double* __restrict__ AF, float* __restrict__ AF32,
-                                   double* __restrict__ AG) {
+                                   double* __restrict__ AG, float* __restrict__ AG32) {
   const int R = T.n;
   const int64_t nf = (int64_t)N * M * q * R;
   const int64_t ng = (int64_t)N * p * R;
@@ -43,7 +43,9 @@ __global__ void time_tables_kernel(TermsDev T, int N, int M, int q, int p, doubl
     const int n = (int)rest;
     const double Tn = t0 + (double)n * dT;
     const double t = Tn + cG.c[i] * dT;
-    AG[idx - nf] = T.t[r].amp * eval_time(T.t[r], t);
+    const double v = T.t[r].amp * eval_time(T.t[r], t);
+    AG[idx - nf] = v;
+    if (AG32) AG32[idx - nf] = (float)v;
   }
 }
 
@@ -132,7 +134,7 @@ pe_status launch_time_tables(pe_ctx* c) {
   const int threads = 256;
   time_tables_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, c->stream>>>(
       T, c->N, c->M, c->q, c->p, c->t0, c->dT, c->dt, nF, nG, c->AF,
-      c->precision == PE_MIXED ? c->AF32 : nullptr, c->AG);
+      c->precision == PE_MIXED ? c->AF32 : nullptr, c->AG, c->precision == PE_MIXED ? c->AG32 : nullptr);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;

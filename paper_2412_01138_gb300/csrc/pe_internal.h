@@ -92,6 +92,7 @@ struct pe_ctx {
   double* AF = nullptr;         // [N*M*q*PE_MAX_TERMS]
   float* AF32 = nullptr;
   double* AG = nullptr;         // [N*p*PE_MAX_TERMS]
+  float* AG32 = nullptr;
   double* loads = nullptr;      // [PE_MAX_TERMS * nsum] 1D loads before the DST
   // accounting
   int64_t launches = 0;     // kernels launched since the last reset

@@ -14,13 +14,18 @@
 
 namespace {
 
-// Each thread keeps its mode's weights P_{r,J} in a column of shared memory
-// (R x 256 doubles), so R is a run-time value here.
-__global__ void __launch_bounds__(256) coarse_kernel(Geom g, int N, int p, int R, const double* __restrict__ axisF,
-                                                     const double* __restrict__ AG, const double* __restrict__ coefG,
-                                                     double* __restrict__ U, double* __restrict__ Gold,
-                                                     double* __restrict__ gG) {
-  extern __shared__ double sP[];  // [R][blockDim.x]
+// Coarse forcing of every slice, in parallel over slices: each thread owns one
+// mode and SL consecutive slices; its weights P_{r,J} sit in a column of shared
+// memory (R x blockDim doubles / floats), so R is a run-time value.  T = double
+// on the float64 path; float in the mixed form, where gG only enters through
+// G(U^{new}) - G(U^{old}), in which the same stored gG cancels.
+template <typename T>
+__global__ void __launch_bounds__(256) coarse_forcing_kernel(Geom g, int N, int p, int R, int SL,
+                                                            const T* __restrict__ axisF, const T* __restrict__ AG,
+                                                            const double* __restrict__ coefG,
+                                                            double* __restrict__ gG) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sP = reinterpret_cast<T*>(smem_raw);  // [R][blockDim.x]
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   const int64_t nd = g.ndof;
@@ -28,31 +33,47 @@ __global__ void __launch_bounds__(256) coarse_kernel(Geom g, int N, int p, int R
   int j[PE_MAX_D];
   unflatten(g, J, j);
   for (int r = 0; r < R; ++r) {
-    double v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+    T v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
     for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     sP[r * B + tid] = v;
   }
-  const double E = coefG[J];
-  double b[PE_MAX_S];
+  T b[PE_MAX_S];
 #pragma unroll
   for (int i = 0; i < PE_MAX_S; ++i)
-    if (i < p) b[i] = coefG[(1 + i) * nd + J];
-  double c = U[J];
-  for (int n = 0; n < N; ++n) {
-    double acc = 0.0;
+    if (i < p) b[i] = (T)coefG[(1 + i) * nd + J];
+  const int n0 = blockIdx.y * SL;
+  const int n1 = min(N, n0 + SL);
+  for (int n = n0; n < n1; ++n) {
+    T acc = T(0);
 #pragma unroll
     for (int i = 0; i < PE_MAX_S; ++i) {
       if (i < p) {
-        const double* a = AG + ((int64_t)n * p + i) * R;
-        double gi = 0.0;
+        const T* a = AG + ((int64_t)n * p + i) * R;
+        T gi = T(0);
         for (int r = 0; r < R; ++r) gi = fma(__ldg(a + r), sP[r * B + tid], gi);
         acc = fma(b[i], gi, acc);
       }
     }
-    gG[(int64_t)n * nd + J] = acc;
-    c = fma(E, c, acc);
+    gG[(int64_t)n * nd + J] = (double)acc;
+  }
+}
+
+// Sequential coarse sweep U^{n+1,(0)} = E_G U^{n,(0)} + gG_n (one thread per mode).
+__global__ void __launch_bounds__(256) coarse_recurrence_kernel(Geom g, int N, const double* __restrict__ coefG,
+                                                               const double* __restrict__ gG,
+                                                               double* __restrict__ U, double* __restrict__ Gold) {
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= g.ndof) return;
+  const int64_t nd = g.ndof;
+  const double E = coefG[J];
+  double c = U[J];
+  double gn = gG[J];
+  for (int n = 0; n < N; ++n) {
+    const double gnext = n + 1 < N ? gG[(int64_t)(n + 1) * nd + J] : 0.0;
+    c = fma(E, c, gn);
     U[(int64_t)(n + 1) * nd + J] = c;
     Gold[(int64_t)n * nd + J] = c;
+    gn = gnext;
   }
 }
 
@@ -140,12 +161,25 @@ __global__ void final_reduce_kernel(const double* __restrict__ partials, int nbl
 pe_status launch_coarse_sweep(pe_ctx* c) {
   const int threads = 256;
   const unsigned blocks = (unsigned)((c->g.ndof + threads - 1) / threads);
-  const size_t smem = sizeof(double) * (size_t)c->R * threads;
-  if (smem > 48 * 1024)
-    PE_CUDA_TRY(cudaFuncSetAttribute(coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  coarse_kernel<<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, c->axisF, c->AG, c->coefG, c->U,
-                                                      c->Gold, c->gG);
-  c->launches += 1;
+  // slices per thread: enough CTAs to cover the GPU twice, at least one slice each
+  int64_t want = (2 * 152 * 2 + blocks - 1) / blocks;
+  int SL = (int)((c->N + want - 1) / want);
+  SL = SL < 1 ? 1 : SL;
+  dim3 grid(blocks, (unsigned)((c->N + SL - 1) / SL));
+  if (c->precision == PE_MIXED) {
+    const size_t smem = sizeof(float) * (size_t)c->R * threads;
+    coarse_forcing_kernel<float><<<grid, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, SL, c->axisF32, c->AG32,
+                                                                    c->coefG, c->gG);
+  } else {
+    const size_t smem = sizeof(double) * (size_t)c->R * threads;
+    if (smem > 48 * 1024)
+      PE_CUDA_TRY(cudaFuncSetAttribute(coarse_forcing_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    coarse_forcing_kernel<double><<<grid, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, SL, c->axisF, c->AG,
+                                                                     c->coefG, c->gG);
+  }
+  coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U, c->Gold);
+  c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
