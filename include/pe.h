@@ -272,6 +272,47 @@ pe_status pe_batch_status(pe_batch* b, double* residuals, int32_t* iterations);
 
 void pe_batch_destroy(pe_batch* b);
 
+/* ------------------------------------------------------------------------
+ * Learned coarse correction.  F^M(v) - G(v) does not depend on v (G and F share
+ * e^{-lam dT}); per mode J and sine source term amp sin(w t + phi) prod_a g_a it is
+ * P_{r,J} amp Im(e^{i(w T_n + phi)} K(lam_J, w)) with K the response of F^M - G to
+ * the unit source e^{i w t} over one slice.  A 3-layer MLP (2 -> 64 -> 64 -> 2,
+ * tanh, float16 weights / float32 accumulation at inference) learns K from
+ * features x = (log(lam dT)/6, w dT - 1) and targets K~ = 4 K (1 + lam dT)/(dT (w dT)^2).
+ * With a network attached, the coarse step becomes G'(v) = G(v) + delta^ (band
+ * table of K^ over log lam, linear interpolation per mode); the correction of
+ * Algorithm 1 cancels delta^, so the converged result is unchanged and only the
+ * iteration count can change.  Sources of other kinds get no correction.
+ * Buffers x, t, y, lam, omega, K are device memory; grad_out, params are host.
+ * ------------------------------------------------------------------------ */
+typedef struct pe_mlp pe_mlp; /* opaque */
+
+/* New network with Xavier-uniform weights drawn from SplitMix64(seed), zero biases. */
+pe_status pe_mlp_create(pe_mlp** out, uint64_t seed);
+/* Number of float parameters (W1[64][2], b1, W2[64][64], b2, W3[2][64], b3). */
+int32_t pe_mlp_num_params(void);
+/* Adam (beta 0.9/0.999, cosine-decayed step lr -> lr/100) on 0.5 |y - t|^2, mean over
+ * each batch, `epochs` passes over the n samples in order.  final_loss: mean loss of
+ * the trained weights over all samples (host, may be NULL). */
+pe_status pe_mlp_train(pe_mlp* m, const float* x, const float* t, int32_t n, int32_t epochs, int32_t batch,
+                       float lr, float* final_loss);
+/* Gradient of the mean loss over n samples (float32 weights) into host grad_out[num_params]. */
+pe_status pe_mlp_gradient(pe_mlp* m, const float* x, const float* t, int32_t n, float* grad_out, float* loss_out);
+/* Inference with the float16 weights: y[n][2] = net(x[n][2]). */
+pe_status pe_mlp_forward(pe_mlp* m, const float* x, int32_t n, float* y);
+pe_status pe_mlp_get_params(pe_mlp* m, float* out);
+pe_status pe_mlp_set_params(pe_mlp* m, const float* in);
+void pe_mlp_destroy(pe_mlp* m);
+/* Training pairs generated by the method: for each (lam_s, w_s), run the fine
+ * propagator (M steps, q nodes) and the coarse step of this context on the unit
+ * source e^{i w t} and return features x[n][2], normalised targets t[n][2] and the
+ * raw K[n][2] (re, im; K may be NULL). */
+pe_status pe_learned_samples(pe_ctx* ctx, int32_t n, const double* lam, const double* omega, float* x, float* t,
+                             double* K);
+/* Attach (m != NULL) or detach the learned correction; takes effect at the next pe_set_problem / pe_solve.
+ * The network must outlive its use by the context. */
+pe_status pe_set_learned(pe_ctx* ctx, const pe_mlp* m);
+
 /* Most recent error message on this thread ("" if none). */
 const char* pe_last_error(void);
 

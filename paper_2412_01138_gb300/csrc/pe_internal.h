@@ -94,6 +94,10 @@ struct pe_ctx {
   double* AG = nullptr;         // [N*p*PE_MAX_TERMS]
   float* AG32 = nullptr;
   double* loads = nullptr;      // [PE_MAX_TERMS * nsum] 1D loads before the DST
+  // learned coarse correction (optional)
+  const struct pe_mlp* mlp = nullptr;
+  double* Ktab = nullptr;       // [PE_MAX_TERMS][bands][2]
+  void* phase_tab = nullptr;    // [PE_MAX_TERMS][N] float2
   // accounting
   int64_t launches = 0;     // kernels launched since the last reset
   double ms_fine = 0.0;     // device time of fine-propagator kernels since the last reset
@@ -145,3 +149,6 @@ pe_status launch_coarse_sweep(pe_ctx* c);
 pe_status launch_fine_sweep(pe_ctx* c, int precision);
 pe_status launch_correction(pe_ctx* c, double* num, double* den);
 pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse);
+
+// pe_learned.cu
+pe_status launch_learned_correction(pe_ctx* c);

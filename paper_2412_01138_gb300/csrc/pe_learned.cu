@@ -1,0 +1,567 @@
+// Learned coarse-propagator correction: a 3-layer MLP (2 -> 64 -> 64 -> 2, tanh)
+// with hand-written training (forward, backward, weight gradients, Adam) and
+// inference kernels.
+//
+// Why it can help: G and F share the homogeneous propagator e^{-lam dT}, so
+// F^M(v) - G(v) does not depend on v (Algorithm 1 then converges after one
+// iteration, and a residual stop confirms at k = 2).  Per mode J and sine source
+// term r = amp_r sin(w_r t + phi_r) prod_a g_{r,a}, the difference over slice n is
+//   delta_{n,J} = sum_r P_{r,J} amp_r Im( e^{i(w_r T_n + phi_r)} K(lam_J, w_r) ),
+//   K(lam, w) = [F^M(0) - G(0)] for the unit source e^{i w t} on [0, dT],
+// a smooth function of (lam dT, w dT) alone.  The network learns K from pairs the
+// method itself generates (the fine and coarse steps of Eq. (1-7) run on unit
+// sources); adding its prediction to the coarse step gives G'(v) = G(v) + delta^.
+// F - G' is still iterate-independent and the fixed point of Algorithm 1 is still
+// the fine solution, so the network can only change how soon the residual falls
+// below tol, never the answer.  If the prediction error is below tol the solve
+// stops after one fine sweep instead of two.
+//
+// Normalisation: features x = (log(lam dT)/6, w dT - 1); target
+// K~ = 4 K / (s (w dT)^2) with s = dT/(1 + lam dT) (K~ = O(1) over the spectrum).
+#include <cuda_fp16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "pe_learned.h"
+#include "pe_phi.cuh"
+
+namespace {
+
+constexpr int H = PE_MLP_WIDTH;
+// parameter layout (floats): W1[H][2], b1[H], W2[H][H], b2[H], W3[2][H], b3[2]
+constexpr int OW1 = 0, OB1 = OW1 + 2 * H, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 + H, OB3 = OW3 + 2 * H;
+constexpr int NPARAM = OB3 + 2;
+
+struct Cd {
+  double re, im;
+};
+
+__device__ inline Cd cexpi(double x) {
+  double s, c;
+  sincos(x, &s, &c);
+  return Cd{c, s};
+}
+
+// ---------------------------------------------------------------------------
+// labels: K(lam, w) = F^M(0) - G(0) for the unit source e^{i w t}, normalised
+// ---------------------------------------------------------------------------
+__global__ void samples_kernel(int n, const double* __restrict__ lam, const double* __restrict__ om, double dT,
+                               int M, int q, int p, Lag LF, Lag LG, Nodes8 cF, Nodes8 cG, float* __restrict__ x,
+                               float* __restrict__ y, double* __restrict__ Kraw) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double l = lam[s], w = om[s];
+  const double dt = dT / (double)M;
+  double bF[PE_MAX_S], bG[PE_MAX_S];
+  const double E = exp(-l * dt);
+  b_weights(-l * dt, q, LF, bF);
+  b_weights(-l * dT, p, LG, bG);
+  Cd acc{0.0, 0.0};
+  for (int m = 0; m < M; ++m) {
+    Cd st{0.0, 0.0};
+    for (int i = 0; i < q; ++i) {
+      const Cd e = cexpi(w * ((double)m + cF.c[i]) * dt);
+      st.re = fma(bF[i], e.re, st.re);
+      st.im = fma(bF[i], e.im, st.im);
+    }
+    acc.re = fma(E, acc.re, dt * st.re);
+    acc.im = fma(E, acc.im, dt * st.im);
+  }
+  Cd g{0.0, 0.0};
+  for (int i = 0; i < p; ++i) {
+    const Cd e = cexpi(w * cG.c[i] * dT);
+    g.re = fma(bG[i], e.re, g.re);
+    g.im = fma(bG[i], e.im, g.im);
+  }
+  const double Kre = acc.re - dT * g.re, Kim = acc.im - dT * g.im;
+  if (Kraw) {
+    Kraw[2 * s] = Kre;
+    Kraw[2 * s + 1] = Kim;
+  }
+  const double wd = w * dT;
+  const double scale = 4.0 * (1.0 + l * dT) / (dT * wd * wd);
+  x[2 * s] = (float)(log(l * dT) / 6.0);
+  x[2 * s + 1] = (float)(wd - 1.0);
+  y[2 * s] = (float)(Kre * scale);
+  y[2 * s + 1] = (float)(Kim * scale);
+}
+
+// ---------------------------------------------------------------------------
+// training
+// ---------------------------------------------------------------------------
+// One thread per sample: forward, loss, backward to the pre-activations; stores
+// h1, h2, dz1, dz2, dy for the weight-gradient reduction.
+__global__ void __launch_bounds__(128) fwd_bwd_kernel(const float* __restrict__ params, const float* __restrict__ x,
+                                                      const float* __restrict__ t, int nb, float inv_n,
+                                                      float* __restrict__ H1, float* __restrict__ H2,
+                                                      float* __restrict__ DZ1, float* __restrict__ DZ2,
+                                                      float* __restrict__ DY, float* __restrict__ loss) {
+  __shared__ float P[NPARAM];
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) P[i] = params[i];
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nb) return;
+  const float x0 = x[2 * s], x1 = x[2 * s + 1];
+  float h1[H], h2[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) h1[j] = tanhf(fmaf(P[OW1 + 2 * j], x0, fmaf(P[OW1 + 2 * j + 1], x1, P[OB1 + j])));
+#pragma unroll 4
+  for (int i = 0; i < H; ++i) {
+    float z = P[OB2 + i];
+#pragma unroll
+    for (int j = 0; j < H; ++j) z = fmaf(P[OW2 + H * i + j], h1[j], z);
+    h2[i] = tanhf(z);
+  }
+  float y0 = P[OB3], y1 = P[OB3 + 1];
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    y0 = fmaf(P[OW3 + i], h2[i], y0);
+    y1 = fmaf(P[OW3 + H + i], h2[i], y1);
+  }
+  const float e0 = y0 - t[2 * s], e1 = y1 - t[2 * s + 1];
+  loss[s] = 0.5f * (e0 * e0 + e1 * e1) * inv_n;
+  const float d0 = e0 * inv_n, d1 = e1 * inv_n;
+  DY[2 * s] = d0;
+  DY[2 * s + 1] = d1;
+  float dz2[H];
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const float dh = fmaf(P[OW3 + i], d0, P[OW3 + H + i] * d1);
+    dz2[i] = dh * (1.f - h2[i] * h2[i]);
+    H2[(size_t)s * H + i] = h2[i];
+    DZ2[(size_t)s * H + i] = dz2[i];
+  }
+#pragma unroll 4
+  for (int j = 0; j < H; ++j) {
+    float dh = 0.f;
+#pragma unroll
+    for (int i = 0; i < H; ++i) dh = fmaf(P[OW2 + H * i + j], dz2[i], dh);
+    H1[(size_t)s * H + j] = h1[j];
+    DZ1[(size_t)s * H + j] = dh * (1.f - h1[j] * h1[j]);
+  }
+}
+
+// One thread per parameter: its gradient summed over the batch (deterministic order).
+__global__ void grad_kernel(const float* __restrict__ x, const float* __restrict__ H1, const float* __restrict__ H2,
+                            const float* __restrict__ DZ1, const float* __restrict__ DZ2,
+                            const float* __restrict__ DY, int nb, float* __restrict__ grad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NPARAM) return;
+  float acc = 0.f;
+  if (k < OB1) {  // W1[j][c] = sum dz1[j] x[c]
+    const int j = (k - OW1) / 2, c = (k - OW1) % 2;
+    for (int s = 0; s < nb; ++s) acc = fmaf(DZ1[(size_t)s * H + j], x[2 * s + c], acc);
+  } else if (k < OW2) {
+    const int j = k - OB1;
+    for (int s = 0; s < nb; ++s) acc += DZ1[(size_t)s * H + j];
+  } else if (k < OB2) {  // W2[i][j] = sum dz2[i] h1[j]
+    const int i = (k - OW2) / H, j = (k - OW2) % H;
+    for (int s = 0; s < nb; ++s) acc = fmaf(DZ2[(size_t)s * H + i], H1[(size_t)s * H + j], acc);
+  } else if (k < OW3) {
+    const int i = k - OB2;
+    for (int s = 0; s < nb; ++s) acc += DZ2[(size_t)s * H + i];
+  } else if (k < OB3) {  // W3[o][i] = sum dy[o] h2[i]
+    const int o = (k - OW3) / H, i = (k - OW3) % H;
+    for (int s = 0; s < nb; ++s) acc = fmaf(DY[2 * s + o], H2[(size_t)s * H + i], acc);
+  } else {
+    const int o = k - OB3;
+    for (int s = 0; s < nb; ++s) acc += DY[2 * s + o];
+  }
+  grad[k] = acc;
+}
+
+__global__ void adam_kernel(float* __restrict__ params, const float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NPARAM) return;
+  const float g = grad[k];
+  const float mk = b1 * m[k] + (1.f - b1) * g;
+  const float vk = b2 * v[k] + (1.f - b2) * g * g;
+  m[k] = mk;
+  v[k] = vk;
+  params[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+}
+
+__global__ void sum_kernel(const float* __restrict__ a, int n, float* __restrict__ out) {
+  __shared__ float sh[256];
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += a[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+__global__ void to_half_kernel(const float* __restrict__ p, __half* __restrict__ h) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < NPARAM) h[k] = __float2half_rn(p[k]);
+}
+
+// ---------------------------------------------------------------------------
+// inference (float16 weights, float32 accumulation)
+// ---------------------------------------------------------------------------
+__device__ inline void mlp_eval_half(const __half* __restrict__ P, float x0, float x1, float* y0, float* y1) {
+  float h1[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j)
+    h1[j] = tanhf(fmaf(__half2float(P[OW1 + 2 * j]), x0, fmaf(__half2float(P[OW1 + 2 * j + 1]), x1,
+                                                                 __half2float(P[OB1 + j]))));
+  float a0 = __half2float(P[OB3]), a1 = __half2float(P[OB3 + 1]);
+  for (int i = 0; i < H; ++i) {
+    float z = __half2float(P[OB2 + i]);
+#pragma unroll
+    for (int j = 0; j < H; ++j) z = fmaf(__half2float(P[OW2 + H * i + j]), h1[j], z);
+    const float h2 = tanhf(z);
+    a0 = fmaf(__half2float(P[OW3 + i]), h2, a0);
+    a1 = fmaf(__half2float(P[OW3 + H + i]), h2, a1);
+  }
+  *y0 = a0;
+  *y1 = a1;
+}
+
+__global__ void forward_kernel(const __half* __restrict__ params16, const float* __restrict__ x, int n,
+                               float* __restrict__ y) {
+  __shared__ __half P[NPARAM];
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) P[i] = params16[i];
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float y0, y1;
+  mlp_eval_half(P, x[2 * s], x[2 * s + 1], &y0, &y1);
+  y[2 * s] = y0;
+  y[2 * s + 1] = y1;
+}
+
+// K^[r][b] for every sine source term r and lam band b (log-spaced band centres).
+__global__ void band_table_kernel(const __half* __restrict__ params16, TermsW T, int NB, double loglo,
+                                  double logstep, double dT, double* __restrict__ Ktab) {
+  __shared__ __half P[NPARAM];
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) P[i] = params16[i];
+  __syncthreads();
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= T.R * NB) return;
+  const int r = idx / NB, b = idx % NB;
+  double Kre = 0.0, Kim = 0.0;
+  if (T.is_sin[r]) {
+    const double w = T.omega[r];
+    const double ll = loglo + logstep * (double)b;  // log(lam dT)
+    const double ldt = exp(ll);
+    const double wd = w * dT;
+    float y0, y1;
+    mlp_eval_half(P, (float)(ll / 6.0), (float)(wd - 1.0), &y0, &y1);
+    const double unscale = (dT * wd * wd) / (4.0 * (1.0 + ldt));
+    Kre = (double)y0 * unscale;
+    Kim = (double)y1 * unscale;
+  }
+  Ktab[2 * idx] = Kre;
+  Ktab[2 * idx + 1] = Kim;
+}
+
+// cs[r][n] = (cos, sin)(w_r T_n + phi_r)
+__global__ void phase_table_kernel(TermsW T, int N, double dT, double t0, float2* __restrict__ cs) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= T.R * N) return;
+  const int r = idx / N, n = idx % N;
+  double s, co;
+  sincos(T.omega[r] * (t0 + (double)n * dT) + T.phase[r], &s, &co);
+  cs[idx] = make_float2((float)co, (float)s);
+}
+
+// gG[n][J] += sum_r P_{r,J} amp_r Im(e^{i(w_r T_n + phi_r)} K^(lam_J, w_r)) with K^ interpolated
+// linearly in log(lam dT) between band centres.  Per mode the r-sum reduces to
+// sum_r (A_r cos_{r,n} + B_r sin_{r,n}), A_r = P amp Im K^, B_r = P amp Re K^, evaluated in
+// float32 (delta^ is a prediction; only its size relative to tol matters).
+__global__ void __launch_bounds__(256) learned_correction_kernel(Geom g, int N, int R, int NB, double loglo,
+                                                                 double logstep, double dT, TermsW T,
+                                                                 const double* __restrict__ lam,
+                                                                 const double* __restrict__ axisF,
+                                                                 const double* __restrict__ Ktab,
+                                                                 const float2* __restrict__ cs,
+                                                                 double* __restrict__ gG) {
+  extern __shared__ float sAB[];  // [2R][blockDim]
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= g.ndof) return;
+  const int64_t nd = g.ndof;
+  const int tid = threadIdx.x, B = blockDim.x;
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
+  double pos = (log(lam[J] * dT) - loglo) / logstep;
+  pos = fmin(fmax(pos, 0.0), (double)(NB - 1) - 1e-9);
+  const int b0 = (int)pos;
+  const double f = pos - (double)b0;
+  for (int r = 0; r < R; ++r) {
+    float A = 0.f, Bv = 0.f;
+    if (T.is_sin[r]) {
+      double P = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+      for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+      const double* k0 = Ktab + 2 * ((int64_t)r * NB + b0);
+      const double Kre = (1.0 - f) * k0[0] + f * k0[2];
+      const double Kim = (1.0 - f) * k0[1] + f * k0[3];
+      const double c = P * T.amp[r];
+      A = (float)(c * Kim);
+      Bv = (float)(c * Kre);
+    }
+    sAB[(2 * r) * B + tid] = A;
+    sAB[(2 * r + 1) * B + tid] = Bv;
+  }
+  for (int n = 0; n < N; ++n) {
+    float d = 0.f;
+    for (int r = 0; r < R; ++r) {
+      const float2 e = __ldg(cs + (int64_t)r * N + n);
+      d = fmaf(sAB[(2 * r) * B + tid], e.x, fmaf(sAB[(2 * r + 1) * B + tid], e.y, d));
+    }
+    gG[(int64_t)n * nd + J] += (double)d;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host API
+// ---------------------------------------------------------------------------
+extern "C" pe_status pe_mlp_create(pe_mlp** out, uint64_t seed) {
+  if (!out) return pe_fail(PE_EINVAL, "pe_mlp_create: out is NULL");
+  *out = nullptr;
+  pe_mlp* m = new (std::nothrow) pe_mlp();
+  if (!m) return pe_fail(PE_ENOMEM, "pe_mlp_create: host allocation failed");
+  // Xavier-uniform initial weights from SplitMix64, zero biases
+  std::vector<float> p(NPARAM, 0.f);
+  uint64_t st = seed;
+  auto uni = [&st]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](int off, int fan_in, int fan_out, int count) {
+    const double a = sqrt(6.0 / (double)(fan_in + fan_out));
+    for (int i = 0; i < count; ++i) p[off + i] = (float)((2.0 * uni() - 1.0) * a);
+  };
+  fill(OW1, 2, H, 2 * H);
+  fill(OW2, H, H, H * H);
+  fill(OW3, H, 2, 2 * H);
+  pe_status s = PE_OK;
+  auto al = [&s](void** ptr, size_t bytes) {
+    if (s != PE_OK) return;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s = pe_fail(PE_ENOMEM, "pe_mlp_create: cudaMalloc failed");
+    }
+  };
+  al((void**)&m->params, sizeof(float) * NPARAM);
+  al((void**)&m->params16, sizeof(__half) * NPARAM);
+  al((void**)&m->grad, sizeof(float) * NPARAM);
+  al((void**)&m->adam_m, sizeof(float) * NPARAM);
+  al((void**)&m->adam_v, sizeof(float) * NPARAM);
+  al((void**)&m->loss_dev, sizeof(float));
+  if (s == PE_OK) {
+    cudaMemcpy(m->params, p.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice);
+    cudaMemset(m->adam_m, 0, sizeof(float) * NPARAM);
+    cudaMemset(m->adam_v, 0, sizeof(float) * NPARAM);
+    to_half_kernel<<<(NPARAM + 255) / 256, 256>>>(m->params, (__half*)m->params16);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) s = pe_cuda_fail(e, "pe_mlp_create");
+  }
+  if (s != PE_OK) {
+    pe_mlp_destroy(m);
+    return s;
+  }
+  *out = m;
+  return PE_OK;
+}
+
+extern "C" void pe_mlp_destroy(pe_mlp* m) {
+  if (!m) return;
+  void* ptrs[] = {m->params, m->params16, m->grad, m->adam_m, m->adam_v, m->loss_dev, m->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete m;
+}
+
+extern "C" int32_t pe_mlp_num_params(void) { return NPARAM; }
+
+static pe_status ensure_scratch(pe_mlp* m, int nb) {
+  if (m->scratch_cap >= nb) return PE_OK;
+  if (m->scratch) cudaFree(m->scratch);
+  m->scratch = nullptr;
+  m->scratch_cap = 0;
+  const size_t per = (size_t)4 * H + 2 + 1;  // H1, H2, DZ1, DZ2, DY, loss
+  if (cudaMalloc((void**)&m->scratch, sizeof(float) * per * (size_t)nb) != cudaSuccess) {
+    cudaGetLastError();
+    return pe_fail(PE_ENOMEM, "pe_mlp: scratch allocation failed");
+  }
+  m->scratch_cap = nb;
+  return PE_OK;
+}
+
+// gradient of the mean loss over samples [0, nb) into m->grad; loss into m->loss_dev
+static pe_status grad_batch(pe_mlp* m, const float* x, const float* t, int nb, float inv_n, cudaStream_t st) {
+  PE_TRY(ensure_scratch(m, nb));
+  float* H1 = m->scratch;
+  float* H2 = H1 + (size_t)H * nb;
+  float* DZ1 = H2 + (size_t)H * nb;
+  float* DZ2 = DZ1 + (size_t)H * nb;
+  float* DY = DZ2 + (size_t)H * nb;
+  float* L = DY + (size_t)2 * nb;
+  fwd_bwd_kernel<<<(nb + 127) / 128, 128, 0, st>>>(m->params, x, t, nb, inv_n, H1, H2, DZ1, DZ2, DY, L);
+  grad_kernel<<<(NPARAM + 127) / 128, 128, 0, st>>>(x, H1, H2, DZ1, DZ2, DY, nb, m->grad);
+  sum_kernel<<<1, 256, 0, st>>>(L, nb, m->loss_dev);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+extern "C" pe_status pe_mlp_gradient(pe_mlp* m, const float* x, const float* t, int32_t n, float* grad_out,
+                                     float* loss_out) {
+  if (!m || !x || !t || n < 1) return pe_fail(PE_EINVAL, "pe_mlp_gradient: bad arguments");
+  PE_TRY(grad_batch(m, x, t, n, 1.0f / (float)n, nullptr));
+  if (grad_out) PE_CUDA_TRY(cudaMemcpy(grad_out, m->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+  if (loss_out) PE_CUDA_TRY(cudaMemcpy(loss_out, m->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
+  return PE_OK;
+}
+
+extern "C" pe_status pe_mlp_train(pe_mlp* m, const float* x, const float* t, int32_t n, int32_t epochs,
+                                  int32_t batch, float lr, float* final_loss) {
+  if (!m || !x || !t || n < 1 || epochs < 1 || batch < 1) return pe_fail(PE_EINVAL, "pe_mlp_train: bad arguments");
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const int steps_per_epoch = (n + batch - 1) / batch;
+  const int total = epochs * steps_per_epoch;
+  float last = 0.f;
+  for (int e = 0; e < epochs; ++e) {
+    for (int sidx = 0; sidx < steps_per_epoch; ++sidx) {
+      const int off = sidx * batch;
+      const int nb = std::min(batch, n - off);
+      // cosine decay of the step size to lr/100
+      const int it = e * steps_per_epoch + sidx;
+      const float cosv = 0.5f * (1.f + cosf(3.14159265f * (float)it / (float)total));
+      const float lr_t = lr * (0.01f + 0.99f * cosv);
+      PE_TRY(grad_batch(m, x + 2 * (size_t)off, t + 2 * (size_t)off, nb, 1.0f / (float)nb, nullptr));
+      m->step += 1;
+      const float bc1 = 1.f - powf(b1, (float)m->step), bc2 = 1.f - powf(b2, (float)m->step);
+      adam_kernel<<<(NPARAM + 255) / 256, 256>>>(m->params, m->grad, m->adam_m, m->adam_v, lr_t, b1, b2, eps, bc1,
+                                                 bc2);
+    }
+  }
+  PE_CUDA_TRY(cudaGetLastError());
+  // loss of the final parameters over the whole set (in batches)
+  double acc = 0.0;
+  for (int off = 0; off < n; off += batch) {
+    const int nb = std::min(batch, n - off);
+    PE_TRY(grad_batch(m, x + 2 * (size_t)off, t + 2 * (size_t)off, nb, 1.0f / (float)n, nullptr));
+    float l = 0.f;
+    PE_CUDA_TRY(cudaMemcpy(&l, m->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
+    acc += l;
+  }
+  last = (float)acc;
+  to_half_kernel<<<(NPARAM + 255) / 256, 256>>>(m->params, (__half*)m->params16);
+  PE_CUDA_TRY(cudaDeviceSynchronize());
+  if (final_loss) *final_loss = last;
+  return PE_OK;
+}
+
+extern "C" pe_status pe_mlp_forward(pe_mlp* m, const float* x, int32_t n, float* y) {
+  if (!m || !x || !y || n < 1) return pe_fail(PE_EINVAL, "pe_mlp_forward: bad arguments");
+  forward_kernel<<<(n + 127) / 128, 128>>>((const __half*)m->params16, x, n, y);
+  PE_CUDA_TRY(cudaGetLastError());
+  PE_CUDA_TRY(cudaDeviceSynchronize());
+  return PE_OK;
+}
+
+extern "C" pe_status pe_mlp_get_params(pe_mlp* m, float* out) {
+  if (!m || !out) return pe_fail(PE_EINVAL, "pe_mlp_get_params: NULL argument");
+  PE_CUDA_TRY(cudaMemcpy(out, m->params, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+  return PE_OK;
+}
+
+extern "C" pe_status pe_mlp_set_params(pe_mlp* m, const float* in) {
+  if (!m || !in) return pe_fail(PE_EINVAL, "pe_mlp_set_params: NULL argument");
+  PE_CUDA_TRY(cudaMemcpy(m->params, in, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+  to_half_kernel<<<(NPARAM + 255) / 256, 256>>>(m->params, (__half*)m->params16);
+  PE_CUDA_TRY(cudaDeviceSynchronize());
+  return PE_OK;
+}
+
+extern "C" pe_status pe_learned_samples(pe_ctx* c, int32_t n, const double* lam, const double* omega, float* x,
+                                        float* y, double* K) {
+  if (!c || n < 1 || !lam || !omega || !x || !y) return pe_fail(PE_EINVAL, "pe_learned_samples: bad arguments");
+  Lag LF{}, LG{};
+  Nodes8 cF{}, cG{};
+  for (int i = 0; i < PE_MAX_S; ++i) {
+    cF.c[i] = c->cF[i];
+    cG.c[i] = c->cG[i];
+    for (int k = 0; k < PE_MAX_S; ++k) {
+      LF.a[i][k] = c->lagF[i][k];
+      LG.a[i][k] = c->lagG[i][k];
+    }
+  }
+  samples_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, lam, omega, c->dT, c->M, c->q, c->p, LF, LG, cF, cG, x,
+                                                          y, K);
+  PE_CUDA_TRY(cudaGetLastError());
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PE_OK;
+}
+
+extern "C" pe_status pe_set_learned(pe_ctx* c, const pe_mlp* m) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_set_learned: ctx is NULL");
+  c->mlp = m;
+  return PE_OK;
+}
+
+// Called by pe_set_problem after the coarse forcing, before the coarse recurrence.
+pe_status launch_learned_correction(pe_ctx* c) {
+  if (!c->mlp) return PE_OK;
+  if (!c->Ktab) {
+    if (cudaMalloc((void**)&c->Ktab, sizeof(double) * 2 * PE_MAX_TERMS * PE_LEARNED_BANDS) != cudaSuccess) {
+      cudaGetLastError();
+      return pe_fail(PE_ENOMEM, "learned G: band table allocation failed");
+    }
+  }
+  TermsW T{};
+  T.R = c->R;
+  for (int r = 0; r < c->R; ++r) {
+    T.is_sin[r] = c->terms[r].tkind == PE_T_SIN ? 1 : 0;
+    T.omega[r] = c->terms[r].tp[0];
+    T.phase[r] = c->terms[r].tp[1];
+    T.amp[r] = c->terms[r].amp;
+  }
+  // band range: the closed-form extremes of lam on this grid (slowest and fastest mode)
+  double lmin = 0.0, lmax = 0.0;
+  for (int a = 0; a < c->g.d; ++a) {
+    const int n = c->g.n[a];
+    auto ratio = [&](int j) {
+      const double th = M_PI * (double)j / (double)(n + 1);
+      const double sh = sin(0.5 * th);
+      return ((4.0 / c->h[a]) * sh * sh) / ((c->h[a] / 3.0) * (2.0 + cos(th)));
+    };
+    lmin += ratio(1);
+    lmax += ratio(n);
+  }
+  lmin *= c->D;
+  lmax *= c->D;
+  const int NB = PE_LEARNED_BANDS;
+  const double loglo = log(lmin * c->dT) - 1e-6, loghi = log(lmax * c->dT) + 1e-6;
+  const double step = (loghi - loglo) / (double)(NB - 1);
+  band_table_kernel<<<(c->R * NB + 127) / 128, 128, 0, c->stream>>>((const __half*)c->mlp->params16, T, NB, loglo,
+                                                                     step, c->dT, c->Ktab);
+  if (!c->phase_tab) {
+    if (cudaMalloc((void**)&c->phase_tab, sizeof(float2) * (size_t)PE_MAX_TERMS * c->N) != cudaSuccess) {
+      cudaGetLastError();
+      return pe_fail(PE_ENOMEM, "learned G: phase table allocation failed");
+    }
+  }
+  phase_table_kernel<<<(c->R * c->N + 127) / 128, 128, 0, c->stream>>>(T, c->N, c->dT, c->t0,
+                                                                       (float2*)c->phase_tab);
+  const int threads = 256;
+  const size_t smem = sizeof(float) * 2 * (size_t)c->R * threads;
+  learned_correction_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, smem, c->stream>>>(
+      c->g, c->N, c->R, NB, loglo, step, c->dT, T, c->lam, c->axisF, c->Ktab, (const float2*)c->phase_tab, c->gG);
+  c->launches += 3;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}

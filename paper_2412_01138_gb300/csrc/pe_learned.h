@@ -1,0 +1,34 @@
+// Internal declarations of the learned coarse correction (pe_learned.cu).
+#pragma once
+#include "pe_internal.h"
+#include "pe_phi.cuh"
+
+#define PE_MLP_WIDTH 64
+#define PE_LEARNED_BANDS 4096
+
+struct pe_mlp {
+  float* params = nullptr;    // float32 master weights (training)
+  void* params16 = nullptr;   // float16 copy used for inference
+  float* grad = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* loss_dev = nullptr;
+  float* scratch = nullptr;   // per-sample activations of one batch
+  int scratch_cap = 0;
+  int64_t step = 0;
+};
+
+struct Nodes8 {
+  double c[PE_MAX_S];
+};
+
+// per source term: sine kind flag, frequency, phase, amplitude
+struct TermsW {
+  int R;
+  int is_sin[PE_MAX_TERMS];
+  double omega[PE_MAX_TERMS];
+  double phase[PE_MAX_TERMS];
+  double amp[PE_MAX_TERMS];
+};
+
+pe_status launch_learned_correction(pe_ctx* c);

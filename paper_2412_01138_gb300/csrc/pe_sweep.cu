@@ -178,6 +178,8 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
     coarse_forcing_kernel<double><<<grid, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, SL, c->axisF, c->AG,
                                                                      c->coefG, c->gG);
   }
+  // learned correction G'(v) = G(v) + delta^ (no-op unless a trained network is attached)
+  PE_TRY(launch_learned_correction(c));
   coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U, c->Gold);
   c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());

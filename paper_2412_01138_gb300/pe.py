@@ -33,7 +33,9 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_get_lambda", "pe_get_coefficients", "pe_forcing_modal", "pe_get_nodes", "pe_save_state",
             "pe_load_state", "pe_dst", "pe_dst_f32", "pe_last_error", "pe_destroy", "pe_setup_batch",
             "pe_batch_autotune", "pe_batch_solve", "pe_batch_get_modal", "pe_batch_get_solution", "pe_batch_status",
-            "pe_batch_destroy")
+            "pe_batch_destroy", "pe_mlp_create", "pe_mlp_num_params", "pe_mlp_train", "pe_mlp_gradient",
+            "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
+            "pe_set_learned")
 
 
 class PEError(RuntimeError):
@@ -115,6 +117,16 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_batch_get_solution": (C.c_int, [P, C.c_int32, P]),
         "pe_batch_status": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
         "pe_batch_destroy": (None, [P]),
+        "pe_mlp_create": (C.c_int, [C.POINTER(P), C.c_uint64]),
+        "pe_mlp_num_params": (C.c_int32, []),
+        "pe_mlp_train": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
+        "pe_mlp_gradient": (C.c_int, [P, P, P, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+        "pe_mlp_forward": (C.c_int, [P, P, C.c_int32, P]),
+        "pe_mlp_get_params": (C.c_int, [P, C.POINTER(C.c_float)]),
+        "pe_mlp_set_params": (C.c_int, [P, C.POINTER(C.c_float)]),
+        "pe_mlp_destroy": (None, [P]),
+        "pe_learned_samples": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
+        "pe_set_learned": (C.c_int, [P, P]),
         "pe_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -294,6 +306,17 @@ class Solver:
         _check(self._lib.pe_get_nodes(self.ctx, which, out))
         return tuple(out)
 
+    def set_learned(self, mlp: Optional["MLP"]):
+        """Attach a trained network as learned coarse correction (None detaches)."""
+        _check(self._lib.pe_set_learned(self.ctx, mlp.ctx if mlp is not None else None))
+        self._mlp = mlp
+
+    def learned_samples(self, lam, omega, x, t, K=None):
+        """Method-generated training pairs for (lam, omega) device arrays (see pe_learned_samples)."""
+        n = int(lam.numel()) if hasattr(lam, "numel") else len(lam)
+        _check(self._lib.pe_learned_samples(self.ctx, n, _ptr(lam), _ptr(omega), _ptr(x), _ptr(t),
+                                            _ptr(K) if K is not None else None))
+
     def save_state(self) -> bytes:
         size = C.c_size_t()
         _check(self._lib.pe_save_state(self.ctx, None, C.byref(size)))
@@ -384,3 +407,50 @@ class BatchSolver:
         _check(self._lib.pe_batch_status(self.ctx, r.ctypes.data_as(C.POINTER(C.c_double)),
                                          k.ctypes.data_as(C.POINTER(C.c_int32))))
         return r, k
+
+
+class MLP:
+    """The learned coarse correction network (pe_mlp)."""
+
+    def __init__(self, seed: int = 0):
+        self._lib = lib()
+        ctx = C.c_void_p()
+        _check(self._lib.pe_mlp_create(C.byref(ctx), seed))
+        self.ctx = ctx
+        self.n_params = self._lib.pe_mlp_num_params()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.pe_mlp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train(self, x, t, epochs: int, batch: int = 4096, lr: float = 2e-3) -> float:
+        n = int(x.shape[0])
+        loss = C.c_float()
+        _check(self._lib.pe_mlp_train(self.ctx, _ptr(x), _ptr(t), n, epochs, batch, lr, C.byref(loss)))
+        return loss.value
+
+    def gradient(self, x, t):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = C.c_float()
+        _check(self._lib.pe_mlp_gradient(self.ctx, _ptr(x), _ptr(t), int(x.shape[0]),
+                                          g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
+        return g, loss.value
+
+    def forward(self, x, y):
+        _check(self._lib.pe_mlp_forward(self.ctx, _ptr(x), int(x.shape[0]), _ptr(y)))
+
+    def params(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        _check(self._lib.pe_mlp_get_params(self.ctx, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self._lib.pe_mlp_set_params(self.ctx, p.ctypes.data_as(C.POINTER(C.c_float))))

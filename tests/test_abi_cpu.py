@@ -26,7 +26,7 @@ def _declared():
         if h.endswith(".h"):
             text = open(os.path.join(ROOT, "include", h)).read()
             # function declarations: "<return type> pe_name(" at the start of a line
-            names |= set(re.findall(r"^(?:pe_status|void|const char\*)\s+(pe_[a-z0-9_]+)\(", text, re.M))
+            names |= set(re.findall(r"^(?:pe_status|void|int32_t|const char\*)\s+(pe_[a-z0-9_]+)\(", text, re.M))
     return names
 
 
