@@ -53,8 +53,9 @@ __device__ __forceinline__ void load_P_rt(const Geom& g, int64_t J, const T* __r
 }
 
 // Mixed precision, R <= RC forcing terms (RC a multiple of 4): each float4 broadcast
-// load of four time factors feeds 4*MPT FMAs; staged rows are zero-padded to RC.
-template <int RC, int MPT>
+// load of four time factors feeds up to 4*MPT FMAs; staged rows are zero-padded to
+// RC.  RX > 0: R == RX is known at compile time and the padding lanes are skipped.
+template <int RC, int MPT, int RX = 0>
 __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float* sAf) {
   static_assert(RC % 4 == 0, "RC must be a multiple of 4");
   const Geom& g = a.g;
@@ -109,13 +110,16 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float*
 #pragma unroll
           for (int c4 = 0; c4 < RC / 4; ++c4) {
             const float4 v = a4[c4];
+            const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int k = 0; k < MPT; ++k) {
-              float& g2 = (c4 & 1) ? go[k] : ge[k];
-              g2 = fmaf(v.x, P[k][4 * c4 + 0], g2);
-              g2 = fmaf(v.y, P[k][4 * c4 + 1], g2);
-              g2 = fmaf(v.z, P[k][4 * c4 + 2], g2);
-              g2 = fmaf(v.w, P[k][4 * c4 + 3], g2);
+            for (int e = 0; e < 4; ++e) {
+              if (RX == 0 || 4 * c4 + e < RX) {
+#pragma unroll
+                for (int k = 0; k < MPT; ++k) {
+                  float& g2 = (c4 & 1) ? go[k] : ge[k];
+                  g2 = fmaf(vv[e], P[k][4 * c4 + e], g2);
+                }
+              }
             }
           }
 #pragma unroll
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(256) fine_mixed_kernel(FineTile t, int64_t sli
   t.AFn32 += (int64_t)n * slice_stride_af;
   t.Un += (int64_t)n * nd;
   t.Fn += (int64_t)n * nd;
-  fine_mixed_tile<RC, MPT>(t, R, sAf);
+  fine_mixed_tile<RC, MPT, R>(t, R, sAf);
 }
 
 template <int R>

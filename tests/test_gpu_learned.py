@@ -99,7 +99,7 @@ def trained(env):
     with pe.Solver(prob) as s:
         L, W, x, t, K = training_set(pe, torch, s, prob, range(100000, 100400), 32)
         loss0 = net.gradient(x[:4096], t[:4096])[1]
-        loss = net.train(x, t, epochs=40, batch=2048, lr=3e-3)
+        loss = net.train(x, t, epochs=270, batch=2048, lr=3e-3)  # about 20000 Adam steps
         # held-out seeds
         Lh, Wh, xh, th, Kh = training_set(pe, torch, s, prob, range(200000, 200020), 32, rng_seed=9)
     return net, loss0, loss, xh, th
@@ -128,7 +128,10 @@ def test_learned_coarse_correction_saves_a_sweep(env, trained, precision):
         plain = s.solve(tol=tol)
         s.set_learned(net)
         s.set_problem()
-        k0_err = max(osolver.rel_l2(s.modal(n), fine[n], sys_.norm_w) for n in range(1, prob.N + 1))
+        # the k = 0 iterate's distance to the fine solution, in the residual's norm
+        num = sum(sys_.norm(s.modal(n) - fine[n]) ** 2 for n in range(1, prob.N + 1))
+        den = sum(sys_.norm(fine[n]) ** 2 for n in range(1, prob.N + 1))
+        k0_err = (num / den) ** 0.5
         lrn = s.solve(tol=tol)
         got = [s.modal(n) for n in range(prob.N + 1)]
     assert plain["k"] == 2
