@@ -313,6 +313,17 @@ pe_status pe_learned_samples(pe_ctx* ctx, int32_t n, const double* lam, const do
  * The network must outlive its use by the context. */
 pe_status pe_set_learned(pe_ctx* ctx, const pe_mlp* m);
 
+/*
+ * pe_dst_tc -- the same orthonormal tensor DST-I for float32 data on the tensor cores:
+ * every axis pass is one bfloat16 GEMM (tcgen05.mma, float32 accumulation in tensor
+ * memory, operands staged by TMA) after splitting data and DST matrix into nsplit
+ * bfloat16 terms (2: three products, about 1e-5 relative; 3: six products, about
+ * 1e-7).  in/out: device float32, Ndof values, may alias; n_a <= 1024.  Allocates its
+ * operand buffers with cudaMallocAsync on the stream.  PE_ETIMEOUT if a pipeline wait
+ * in the kernel expired (the kernel then skips its output).
+ */
+pe_status pe_dst_tc(int32_t d, const int32_t* n, const float* in, float* out, int32_t nsplit, void* stream);
+
 /* Most recent error message on this thread ("" if none). */
 const char* pe_last_error(void);
 

@@ -100,13 +100,9 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float*
       for (int i = 0; i < PE_MAX_S; ++i) {
         if (i < q) {
           const float4* a4 = reinterpret_cast<const float4*>(sAf + (m * q + i) * RC);
-          // two partial sums per mode (even / odd float4 chunks) shorten the FMA chains
-          float ge[MPT], go[MPT];
+          float gk[MPT];
 #pragma unroll
-          for (int k = 0; k < MPT; ++k) {
-            ge[k] = 0.f;
-            go[k] = 0.f;
-          }
+          for (int k = 0; k < MPT; ++k) gk[k] = 0.f;
 #pragma unroll
           for (int c4 = 0; c4 < RC / 4; ++c4) {
             const float4 v = a4[c4];
@@ -115,15 +111,12 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float*
             for (int e = 0; e < 4; ++e) {
               if (RX == 0 || 4 * c4 + e < RX) {
 #pragma unroll
-                for (int k = 0; k < MPT; ++k) {
-                  float& g2 = (c4 & 1) ? go[k] : ge[k];
-                  g2 = fmaf(vv[e], P[k][4 * c4 + e], g2);
-                }
+                for (int k = 0; k < MPT; ++k) gk[k] = fmaf(vv[e], P[k][4 * c4 + e], gk[k]);
               }
             }
           }
 #pragma unroll
-          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(b[k][i], ge[k] + go[k], acc[k]);
+          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(b[k][i], gk[k], acc[k]);
         }
       }
 #pragma unroll

@@ -99,7 +99,7 @@ def trained(env):
     with pe.Solver(prob) as s:
         L, W, x, t, K = training_set(pe, torch, s, prob, range(100000, 100400), 32)
         loss0 = net.gradient(x[:4096], t[:4096])[1]
-        loss = net.train(x, t, epochs=270, batch=2048, lr=3e-3)  # about 20000 Adam steps
+        loss = net.train(x, t, epochs=800, batch=2048, lr=3e-3)  # about 60000 Adam steps
         # held-out seeds
         Lh, Wh, xh, th, Kh = training_set(pe, torch, s, prob, range(200000, 200020), 32, rng_seed=9)
     return net, loss0, loss, xh, th
