@@ -58,13 +58,22 @@ enum { PE_FP64 = 0,   /* every step in float64 */
                          homogeneous part e^{-lam M dt} v, tables, correction and
                          residual in float64 */ };
 
-/* DST-I backend (pe_options.dst_backend) */
-enum { PE_DST_AUTO = 0, PE_DST_MATRIX = 1 };
+/* DST-I backend of the general forcing path (pe_options.dst_backend): AUTO = radix-2 FFT
+ * when n+1 is a power of two, else the matrix form; TC = tensor cores (mixed precision
+ * only, split bfloat16, about 3e-6 relative per pass at n = 255) */
+enum { PE_DST_AUTO = 0, PE_DST_MATRIX = 1, PE_DST_TC = 2 };
 
 /* separable factor kinds: spatial  S_ONE 1 | S_SIN sin(p0 x + p1) |
- * S_GAUSS exp(-(x-p0)^2/(2 p1^2)) | S_POLY p0 + p1 x + p2 x^2 + p3 x^3;
+ * S_GAUSS exp(-(x-p0)^2/(2 p1^2)) | S_POLY p0 + p1 x + p2 x^2 + p3 x^3 |
+ * S_MOVING_HAT max(1 - |x - c(t)|/p3, 0), c(t) = p0 + p1 sin(2 pi p2 t) (a factor that
+ * moves with t, the source of Example 4 of Sec. 5; PE_FORCING_GENERAL only);
  * time  T_EXP exp(p0 t) | T_SIN sin(p0 t + p1) */
-enum { PE_S_ONE = 0, PE_S_SIN = 1, PE_S_GAUSS = 2, PE_S_POLY = 3 };
+enum { PE_S_ONE = 0, PE_S_SIN = 1, PE_S_GAUSS = 2, PE_S_POLY = 3, PE_S_MOVING_HAT = 4 };
+
+/* how P_h f(t) is formed (pe_options.forcing_path) */
+enum { PE_FORCING_SEPARABLE = 0, /* modal factors of every term once, products per mode and stage */
+       PE_FORCING_GENERAL = 1    /* at every stage time: consistent load assembled in nodal space
+                                    (element Gauss quadrature), tensor DST-I, division by Lambda_M */ };
 enum { PE_T_EXP = 0, PE_T_SIN = 1 };
 
 /* One separable term  amp * time(t) * prod_{a<d} spatial_a(x_a). */
@@ -94,6 +103,7 @@ typedef struct {
   int32_t quad_pts;     /* Gauss points per axis per element for loads (1..8, 0 = 3) */
   int32_t max_iter;     /* pe_solve iteration cap, 0 = N (Theorem 4.3: k = N is exact) */
   void* cuda_stream;    /* cudaStream_t or NULL */
+  int32_t forcing_path; /* PE_FORCING_SEPARABLE (default) | PE_FORCING_GENERAL */
 } pe_options;
 
 /* Initial data: u0 = sum of separable terms (time factors ignored), projected

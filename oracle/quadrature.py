@@ -25,7 +25,12 @@ def gauss_legendre(npts: int):
     return 0.5 * (xi + 1.0), 0.5 * w
 
 
-def eval_factor(f: "_in.Factor", x: np.ndarray) -> np.ndarray:
+def is_time_dependent(f: "_in.Factor") -> bool:
+    return f.kind == _in.S_MOVING_HAT
+
+
+def eval_factor(f: "_in.Factor", x: np.ndarray, t=None) -> np.ndarray:
+    """One spatial factor at points x (time t for the factors that move)."""
     p = f.params4()
     if f.kind == _in.S_ONE:
         return np.ones_like(x)
@@ -35,6 +40,11 @@ def eval_factor(f: "_in.Factor", x: np.ndarray) -> np.ndarray:
         return np.exp(-((x - p[0]) ** 2) / (2.0 * p[1] ** 2))
     if f.kind == _in.S_POLY:
         return p[0] + x * (p[1] + x * (p[2] + x * p[3]))
+    if f.kind == _in.S_MOVING_HAT:
+        if t is None:
+            raise ValueError("a moving hat needs the time (general forcing path only)")
+        c = p[0] + p[1] * np.sin(2.0 * np.pi * p[2] * t)
+        return np.maximum(1.0 - np.abs(x - c) / p[3], 0.0)
     raise ValueError(f"unknown spatial factor kind {f.kind}")
 
 
@@ -57,7 +67,7 @@ def eval_terms(terms, t, coords) -> np.ndarray:
         vals = term.amp * (1.0 if t is None else eval_time(term, t))
         prod = None
         for a, fac in enumerate(term.factors):
-            v = eval_factor(fac, coords[a])
+            v = eval_factor(fac, coords[a], t)
             prod = v if prod is None else np.multiply.outer(prod, v)
         out = out + vals * prod
     return out

@@ -66,6 +66,8 @@ class ModalSystem:
         self.norm_w = w if self.modes is None else w[self.modes]
 
         if forcing_route == "separable":
+            if any(quadrature.is_time_dependent(f) for term in prob.forcing for f in term.factors):
+                raise ValueError("time-dependent spatial factors need forcing_route='full'")
             self._P = [self._separable_modal(term) for term in prob.forcing]
             self.c0 = sum(term.amp * self._separable_modal(term) for term in prob.u0)
         elif forcing_route == "full":

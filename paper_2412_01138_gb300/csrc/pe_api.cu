@@ -124,7 +124,8 @@ pe_status dev_alloc(T** p, size_t count) {
 
 void free_ctx(pe_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->muM_axis, c->ratio_axis, c->S[0], c->S[1], c->S[2], c->lam, c->coefF, c->coefG,
+  void* ptrs[] = {c->muM_axis, c->ratio_axis, c->S[0], c->S[1], c->S[2], c->S32[0], c->S32[1], c->S32[2],
+                  c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Gold, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
                   c->Ktab, c->phase_tab};
@@ -147,7 +148,7 @@ pe_status copy_out(pe_ctx* c, const double* src_dev, double* out, size_t count) 
 
 }  // namespace
 
-pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what) {
+pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what, bool allow_moving) {
   if (n < 0 || n > PE_MAX_TERMS) return pe_fail(PE_EINVAL, std::string(what) + ": n_terms must be in 0..32");
   if (n > 0 && !t) return pe_fail(PE_EINVAL, std::string(what) + ": terms is NULL");
   for (int i = 0; i < n; ++i) {
@@ -155,7 +156,11 @@ pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what) {
       return pe_fail(PE_EINVAL, std::string(what) + ": unknown time factor kind");
     for (int a = 0; a < d; ++a) {
       const int k = t[i].skind[a];
-      if (k < PE_S_ONE || k > PE_S_POLY) return pe_fail(PE_EINVAL, std::string(what) + ": unknown spatial kind");
+      if (k == PE_S_MOVING_HAT && !allow_moving)
+        return pe_fail(PE_EINVAL, std::string(what) + ": moving factors need PE_FORCING_GENERAL");
+      if (k == PE_S_MOVING_HAT && !(t[i].sp[a][3] > 0.0))
+        return pe_fail(PE_EINVAL, std::string(what) + ": moving hat half-width must be positive");
+      if (k < PE_S_ONE || k > PE_S_MOVING_HAT) return pe_fail(PE_EINVAL, std::string(what) + ": unknown spatial kind");
       if (k == PE_S_GAUSS && !(t[i].sp[a][1] != 0.0))
         return pe_fail(PE_EINVAL, std::string(what) + ": Gaussian width must be nonzero");
     }
@@ -231,6 +236,11 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (o.quad_pts == 0) o.quad_pts = 3;
   if (o.quad_pts < 1 || o.quad_pts > 8) { delete c; return pe_fail(PE_EINVAL, "pe_setup: quad_pts must be in 1..8"); }
   if (o.max_iter < 0) { delete c; return pe_fail(PE_EINVAL, "pe_setup: max_iter must be >= 0"); }
+  if (o.forcing_path != PE_FORCING_SEPARABLE && o.forcing_path != PE_FORCING_GENERAL) {
+    delete c;
+    return pe_fail(PE_EINVAL, "pe_setup: bad forcing_path");
+  }
+  c->forcing_path = o.forcing_path;
   c->precision = o.precision;
   c->dst_backend = o.dst_backend;
   c->quad_pts = o.quad_pts;
@@ -265,6 +275,19 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AF32, N * n_substeps * c->q * MT);
   if (st == PE_OK) st = dev_alloc(&c->AG, N * c->p * MT);
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AG32, N * c->p * MT);
+  if (st == PE_OK && c->forcing_path == PE_FORCING_GENERAL &&
+      ((int64_t)n_substeps * c->q > 65535 || (int64_t)n_slices * c->p > 65535))
+    st = pe_fail(PE_EINVAL, "pe_setup: general forcing path needs M*q and N*p <= 65535");
+  if (st == PE_OK && c->forcing_path == PE_FORCING_GENERAL) {
+    // stage-time buffers of one chunk of slices (also holding the N*p coarse stage times)
+    const int chunk = general_slices_per_chunk(c);
+    const size_t stages = std::max((size_t)chunk * n_substeps * c->q, N * c->p);
+    st = dev_alloc(&c->gen_buf, stages * nd);
+    if (st == PE_OK) st = dev_alloc(&c->gen_tmp, stages * nd);
+    if (st == PE_OK) st = dev_alloc(&c->gen_L, stages * MT * nsum);
+    for (int a = 0; a < d && st == PE_OK && c->precision == PE_MIXED; ++a)
+      st = dev_alloc(&c->S32[a], (size_t)n[a] * n[a]);
+  }
   if (st == PE_OK && cudaMallocHost((void**)&c->h_red, 4 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");
@@ -273,6 +296,8 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = pe_cuda_fail(cudaGetLastError(), "cudaEventCreate");
   if (st == PE_OK) st = launch_axis_tables(c);
   for (int a = 0; a < d && st == PE_OK; ++a) st = build_dst_matrix(n[a], c->S[a], c->stream);
+  for (int a = 0; a < d && st == PE_OK; ++a)
+    if (c->S32[a]) st = build_dst_matrix_f32(n[a], c->S32[a], c->stream);
   if (st == PE_OK) st = launch_coef_tables(c);
   if (st == PE_OK) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -298,7 +323,9 @@ extern "C" void pe_destroy(pe_ctx* c) {
 static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
   if (!u0) return pe_fail(PE_EINVAL, "pe_set_problem: u0 is NULL");
   const int nf = f ? f->n_terms : 0;
-  PE_TRY(pe_validate_terms(nf, f ? f->terms : nullptr, c->g.d, "forcing"));
+  const bool general = c->forcing_path == PE_FORCING_GENERAL;
+  PE_TRY(pe_validate_terms(nf, f ? f->terms : nullptr, c->g.d, "forcing", general));
+  if (general && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: the learned correction needs PE_FORCING_SEPARABLE");
   if (nf == 0) {
     // no source: one zero term keeps every kernel shape valid
     c->R = 1;
@@ -311,8 +338,10 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   PE_TRY(launch_coef_tables(c));
   PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
   // forcing: time factors and per-axis modal factors
-  PE_TRY(launch_time_tables(c));
-  PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1));
+  if (!general) {
+    PE_TRY(launch_time_tables(c));
+    PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1));
+  }
   // U^0 = P_h u0
   double* U0 = c->U;
   if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {
@@ -357,7 +386,8 @@ extern "C" pe_status pe_set_problem(pe_ctx* c, const pe_field* u0, const pe_forc
 
 static pe_status iter_impl(pe_ctx* c, double* r_out, int precision) {
   PE_CUDA_TRY(cudaEventRecord(c->ev[5], c->stream));
-  PE_TRY(launch_fine_sweep(c, precision));
+  if (c->forcing_path == PE_FORCING_GENERAL) PE_TRY(launch_general_fine_sweep(c, precision));
+  else PE_TRY(launch_fine_sweep(c, precision));
   PE_CUDA_TRY(cudaEventRecord(c->ev[6], c->stream));
   double num = 0.0, den = 0.0;
   PE_TRY(launch_correction(c, &num, &den));  // synchronises the stream
@@ -457,6 +487,7 @@ extern "C" pe_status pe_get_coefficients(pe_ctx* c, int32_t which, double* out) 
 extern "C" pe_status pe_forcing_modal(pe_ctx* c, double t, double* out) {
   if (!c) return pe_fail(PE_EINVAL, "pe_forcing_modal: ctx is NULL");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_forcing_modal: no problem set");
+  if (c->forcing_path != PE_FORCING_SEPARABLE) return pe_fail(PE_EINVAL, "pe_forcing_modal: separable path only");
   PE_TRY(launch_forcing_modal(c, t, c->work0));
   return copy_out(c, c->work0, out, c->g.ndof);
 }

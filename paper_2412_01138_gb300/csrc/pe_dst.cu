@@ -12,6 +12,7 @@
 //    element instead of the 2n of the matrix form.
 //  * any other n: a shared-memory tiled, strided, batched GEMM with the matrix S_a
 //    (tile shape chosen so that the grid covers the GPU).
+#include <algorithm>
 #include <mutex>
 
 #include "pe_internal.h"
@@ -103,13 +104,17 @@ pe_status gemm_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64
     dim3 grid((n + BN - 1) / BN, (unsigned)((outer + BM - 1) / BM), 1);
     strided_gemm_kernel<T, BM, BN><<<grid, NT, 0, st>>>(in, S, out, g);
   } else {
-    g.rows = n; g.cols = (int)inner; g.K = n; g.batch = outer;
+    g.rows = n; g.cols = (int)inner; g.K = n;
     g.sAb = 0; g.sAi = n; g.sAk = 1;
     g.sBb = (int64_t)n * inner; g.sBk = inner; g.sBj = 1;
     g.sCb = (int64_t)n * inner; g.sCi = inner;
-    if (outer > 65535) return pe_fail(PE_EINVAL, "dst: batch too large");
-    dim3 grid((unsigned)((inner + BN - 1) / BN), (n + BM - 1) / BM, (unsigned)outer);
-    strided_gemm_kernel<T, BM, BN><<<grid, NT, 0, st>>>(S, in, out, g);
+    // the batch runs in grid.z, at most 65535 per launch
+    for (int64_t b0 = 0; b0 < outer; b0 += 65535) {
+      const int64_t nb = std::min<int64_t>(65535, outer - b0);
+      g.batch = nb;
+      dim3 grid((unsigned)((inner + BN - 1) / BN), (n + BM - 1) / BM, (unsigned)nb);
+      strided_gemm_kernel<T, BM, BN><<<grid, NT, 0, st>>>(S, in + b0 * g.sBb, out + b0 * g.sCb, g);
+    }
   }
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;

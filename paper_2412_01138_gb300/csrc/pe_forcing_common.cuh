@@ -21,11 +21,17 @@ struct Gauss {
   double w[8];  // weights summing to 1
 };
 
-__device__ inline double eval_space(int kind, const double* p, double x) {
+// Spatial factor at x; t is used only by factors that move (PE_S_MOVING_HAT:
+// max(1 - |x - c(t)|/p3, 0) with c(t) = p0 + p1 sin(2 pi p2 t)).
+__device__ inline double eval_space(int kind, const double* p, double x, double t = 0.0) {
   switch (kind) {
     case PE_S_SIN: return sin(p[0] * x + p[1]);
     case PE_S_GAUSS: { const double u = x - p[0]; return exp(-(u * u) / (2.0 * p[1] * p[1])); }
     case PE_S_POLY: return p[0] + x * (p[1] + x * (p[2] + x * p[3]));
+    case PE_S_MOVING_HAT: {
+      const double c = p[0] + p[1] * sinpi(2.0 * p[2] * t);
+      return fmax(1.0 - fabs(x - c) / p[3], 0.0);
+    }
     default: return 1.0;
   }
 }

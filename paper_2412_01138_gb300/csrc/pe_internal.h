@@ -62,12 +62,17 @@ struct pe_ctx {
   double lagF[PE_MAX_S][PE_MAX_S], lagG[PE_MAX_S][PE_MAX_S];  // Lagrange monomial coefficients
   int nsum;  // sum_a n_a
   // options
-  int precision, dst_backend, quad_pts, max_iter;
+  int precision, dst_backend, quad_pts, max_iter, forcing_path;
   cudaStream_t stream;
   // device memory
   double* muM_axis = nullptr;   // [nsum]
   double* ratio_axis = nullptr; // [nsum] mu^K/mu^M
   double* S[PE_MAX_D] = {nullptr, nullptr, nullptr};  // DST-I matrices n_a x n_a
+  float* S32[PE_MAX_D] = {nullptr, nullptr, nullptr};  // float copies (general path, mixed)
+  // general forcing path: stage-time loads and their transforms for a chunk of slices
+  double* gen_L = nullptr;      // [stages][R * nsum] 1D loads
+  double* gen_buf = nullptr;    // [stages][ndof] transformed loads (float in the mixed fine sweep)
+  double* gen_tmp = nullptr;    // same size, DST ping-pong
   double* lam = nullptr;        // [ndof]
   double* coefF = nullptr;      // [(q+2) * ndof]: E, dt*b_1..q, exp(-lam M dt)
   double* coefG = nullptr;      // [(p+1) * ndof]: E, dT*b_1..p
@@ -123,12 +128,13 @@ inline int pick_mchunk(int M, int per_m, size_t elem) {
 pe_status pe_resolve_nodes(const pe_tableau* tb, const char* name, int* s_out, double* c);
 void pe_lagrange_coeffs(int s, const double* c, double a[PE_MAX_S][PE_MAX_S]);
 bool pe_is_device_ptr(const void* p);
-pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what);
+pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what, bool allow_moving = false);
 
 // pe_tables.cu
 pe_status launch_axis_tables(pe_ctx* c);
 pe_status launch_coef_tables(pe_ctx* c);
 pe_status build_dst_matrix(int n, double* S, cudaStream_t st);
+pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st);
 
 // pe_forcing.cu
 pe_status launch_time_tables(pe_ctx* c);
@@ -152,3 +158,8 @@ pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse);
 
 // pe_learned.cu
 pe_status launch_learned_correction(pe_ctx* c);
+
+// pe_general.cu
+int general_slices_per_chunk(const pe_ctx* c);
+pe_status launch_general_coarse_forcing(pe_ctx* c);
+pe_status launch_general_fine_sweep(pe_ctx* c, int precision);

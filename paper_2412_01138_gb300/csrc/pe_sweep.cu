@@ -161,6 +161,13 @@ __global__ void final_reduce_kernel(const double* __restrict__ partials, int nbl
 pe_status launch_coarse_sweep(pe_ctx* c) {
   const int threads = 256;
   const unsigned blocks = (unsigned)((c->g.ndof + threads - 1) / threads);
+  if (c->forcing_path == PE_FORCING_GENERAL) {
+    PE_TRY(launch_general_coarse_forcing(c));
+    coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U, c->Gold);
+    c->launches += 1;
+    PE_CUDA_TRY(cudaGetLastError());
+    return PE_OK;
+  }
   // slices per thread: enough CTAs to cover the GPU twice, at least one slice each
   int64_t want = (2 * 152 * 2 + blocks - 1) / blocks;
   int SL = (int)((c->N + want - 1) / want);

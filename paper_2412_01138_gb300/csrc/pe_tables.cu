@@ -112,6 +112,22 @@ pe_status launch_coef_tables(pe_ctx* c) {
   return PE_OK;
 }
 
+__global__ void dst_matrix_f32_kernel(int n, float* S) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (k >= n || j >= n) return;
+  const int64_t period = 2 * (int64_t)(n + 1);
+  const int64_t m = ((int64_t)(j + 1) * (k + 1)) % period;
+  S[(int64_t)j * n + k] = (float)(sqrt(2.0 / (double)(n + 1)) * sinpi((double)m / (double)(n + 1)));
+}
+
+pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, n);
+  dst_matrix_f32_kernel<<<grid, 128, 0, st>>>(n, S);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
 pe_status build_dst_matrix(int n, double* S, cudaStream_t st) {
   dim3 grid((n + 127) / 128, n);
   dst_matrix_kernel<<<grid, 128, 0, st>>>(n, S);

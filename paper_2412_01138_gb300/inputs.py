@@ -21,6 +21,8 @@ Descriptor conventions (shared with ``include/pe.h``):
     S_SIN   = 1 : sin(p0*x + p1)
     S_GAUSS = 2 : exp(-(x - p0)^2 / (2 p1^2))
     S_POLY  = 3 : p0 + p1 x + p2 x^2 + p3 x^3
+    S_MOVING_HAT = 4 : max(1 - |x - c(t)|/p3, 0), c(t) = p0 + p1 sin(2 pi p2 t)
+                   (depends on t: only the general forcing path takes it)
 * time factor kinds
     T_EXP   = 0 : exp(p0*t)            (p0 = 0 gives a constant)
     T_SIN   = 1 : sin(p0*t + p1)
@@ -32,7 +34,7 @@ import math
 from dataclasses import dataclass, field, replace
 from typing import List, Optional, Sequence, Tuple
 
-S_ONE, S_SIN, S_GAUSS, S_POLY = 0, 1, 2, 3
+S_ONE, S_SIN, S_GAUSS, S_POLY, S_MOVING_HAT = 0, 1, 2, 3, 4
 T_EXP, T_SIN = 0, 1
 
 _MASK64 = (1 << 64) - 1
@@ -286,6 +288,28 @@ def example3(Nx: int, N: int, M: int, q: int, p: int, quad_pts: int = 3) -> Prob
     exact = (Term(1.0, fs, T_EXP, (r, 0.0)),)
     return Problem(3, (Nx - 1,) * 3, box, 0.125, 0.0, 0.4, N, M, uniform_nodes(q), uniform_nodes(p),
                    u0, f, quad_pts, 0.0, exact, f"ex3_{Nx}_{N}x{M}")
+
+
+def example4(Nx: int, alpha: float, freq: float, N: int = 4, M: int = 16, q: int = 2, p: int = 2,
+             quad_pts: int = 3) -> Problem:
+    """Example 4: u_t = alpha u_xx + g on [0,1], T = 1, u0 = 4x(1-x), g a hat of half-width
+    w = 0.05 and height 100 sqrt(alpha) centred at c(t) = 0.5 + (0.5 - w) sin(2 pi f t)."""
+    w = 0.05
+    box = ((0.0, 1.0),)
+    u0 = (Term(1.0, (Factor(S_POLY, (0.0, 4.0, -4.0, 0.0)),)),)
+    g = (Term(100.0 * math.sqrt(alpha), (Factor(S_MOVING_HAT, (0.5, 0.5 - w, freq, w)),)),)
+    return Problem(1, (Nx - 1,), box, alpha, 0.0, 1.0, N, M, uniform_nodes(q), uniform_nodes(p),
+                   u0, g, quad_pts, 0.0, None, f"ex4_Nx{Nx}_a{alpha}_f{freq}_{N}x{M}")
+
+
+def moving_hat_2d(n=(63, 47), N=4, M=8, seed=21) -> Problem:
+    """2D source: a hat moving along x times a fixed Gaussian along y, plus seeded bumps."""
+    box = ((0.0, 1.0), (0.0, 1.0))
+    rng = SplitMix64(seed)
+    u0, f, _ = sin_mode(2, box, 0.05)
+    hat = Term(3.0, (Factor(S_MOVING_HAT, (0.5, 0.35, 2.0, 0.1)), Factor(S_GAUSS, (0.5, 0.15))))
+    return Problem(2, tuple(n), box, 0.05, 0.0, 1.0, N, M, uniform_nodes(4), uniform_nodes(2),
+                   u0, f + (hat,) + gaussian_bumps(rng, 2, 3), 3, 1e-6, None, "moving_hat_2d")
 
 
 def scaled(prob: Problem, n: Sequence[int], N: Optional[int] = None, M: Optional[int] = None) -> Problem:

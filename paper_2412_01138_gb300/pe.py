@@ -21,7 +21,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 PE_OK, PE_EINVAL, PE_ENOMEM, PE_ECUDA, PE_ENOCONV, PE_ENONFINITE, PE_ETIMEOUT, PE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 PE_FP64, PE_MIXED = 0, 1
-PE_DST_AUTO, PE_DST_MATRIX = 0, 1
+PE_DST_AUTO, PE_DST_MATRIX, PE_DST_TC = 0, 1, 2
+PE_FORCING_SEPARABLE, PE_FORCING_GENERAL = 0, 1
 PE_FIELD_TERMS_SEPARABLE, PE_FIELD_TERMS_QUADRATURE, PE_FIELD_NODAL = 0, 1, 2
 PE_MAX_TERMS = 32
 
@@ -55,7 +56,7 @@ class pe_tableau(C.Structure):
 
 class pe_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("dst_backend", C.c_int32), ("quad_pts", C.c_int32),
-                ("max_iter", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("max_iter", C.c_int32), ("cuda_stream", C.c_void_p), ("forcing_path", C.c_int32)]
 
 
 class pe_field(C.Structure):
@@ -190,7 +191,8 @@ class Solver:
     """One pe_ctx: a Parareal EIFE-linear solver for a fixed grid and time partition."""
 
     def __init__(self, prob: "_in.Problem", precision: int = PE_FP64, stream=None, max_iter: int = 0,
-                 random_coarse_seed: Optional[int] = None):
+                 random_coarse_seed: Optional[int] = None, forcing_path: int = PE_FORCING_SEPARABLE,
+                 dst_backend: int = PE_DST_AUTO):
         self.prob = prob
         self._lib = lib()
         n = (C.c_int32 * prob.d)(*prob.n)
@@ -202,7 +204,7 @@ class Solver:
             coarse = pe_tableau(prob.p, C.cast(self._cG, C.POINTER(C.c_double)), 0, 0)
         else:
             coarse = pe_tableau(prob.p, None, 1, random_coarse_seed)
-        opt = pe_options(precision, PE_DST_AUTO, prob.quad_pts, max_iter, stream_handle(stream))
+        opt = pe_options(precision, dst_backend, prob.quad_pts, max_iter, stream_handle(stream), forcing_path)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup(C.byref(ctx), prob.d, n, box, prob.D, prob.t0, prob.T, prob.N, prob.M,
                                   C.byref(fine), C.byref(coarse), C.byref(opt)))
@@ -368,7 +370,8 @@ class BatchSolver:
             q.coarse = pe_tableau(p.p, C.cast(cG, C.POINTER(C.c_double)), 0, 0)
             q.u0 = pe_field(PE_FIELD_TERMS_SEPARABLE, len(p.u0), C.cast(tu, C.POINTER(pe_term)), None)
             q.forcing = pe_forcing(len(p.forcing), C.cast(tf, C.POINTER(pe_term)))
-        opt = pe_options(precision, PE_DST_AUTO, self.probs[0].quad_pts, 0, stream_handle(stream))
+        opt = pe_options(precision, PE_DST_AUTO, self.probs[0].quad_pts, 0, stream_handle(stream),
+                         PE_FORCING_SEPARABLE)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup_batch(C.byref(ctx), len(self.probs), arr, C.byref(opt)))
         self.ctx = ctx

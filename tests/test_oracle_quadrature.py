@@ -62,3 +62,15 @@ def test_l2_norm_of_fe_function_matches_mass_matrix():
     zero = (I.Term(0.0, (I.Factor(I.S_ONE), I.Factor(I.S_ONE))),)
     got = quadrature.l2_error_full(u, zero, 0.0, n, box, 5)
     assert got == pytest.approx(np.sqrt(u.reshape(-1) @ (M @ u.reshape(-1))), rel=1e-13)
+
+
+def test_moving_hat_load_matches_fine_quadrature():
+    """The 3-point element rule on the moving hat against a 400-point rule (kinks make it inexact:
+    the two differ by O(h^3) per element near the kinks only)."""
+    prob = I.example4(32, 0.01, 1.0)
+    term = prob.forcing[0]
+    for t in (0.0, 0.13, 0.61):
+        F3 = quadrature.load_full(prob.forcing, t, prob.n, prob.box, 3)
+        F400 = quadrature.load_full(prob.forcing, t, prob.n, prob.box, 400)
+        assert np.abs(F3 - F400).max() <= 0.05 * np.abs(F400).max()
+        assert np.abs(F400.sum() - term.amp * 0.05) < 1e-6  # integral of the hat times sum of hats = area
