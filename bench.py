@@ -200,6 +200,89 @@ def run_batch(pe, args, barrier):
     return out
 
 
+def run_learned(pe, args, barrier):
+    """511^2 workload, 128 x 32: plain coarse step vs the learned coarse correction (mixed form).
+
+    The network is trained on pairs the method generates from the source frequencies of the
+    held-apart seeds 100000..101999 (lam log-uniform over the grid's spectrum); the solve is on seed 1.
+    """
+    import torch
+
+    prob = I.config5(seed=1)
+    dev = torch.device("cuda")
+    out = {"workload": prob.label}
+    with pe.Solver(prob, precision=pe.PE_MIXED) as s:
+        lam = s.lam()
+        lo, hi = np.log(lam.min()), np.log(lam.max())
+        rng = np.random.default_rng(2024)
+        L, W = [], []
+        for seed in range(100000, 102000):
+            ws = [t.tp[0] for t in I.config5(seed=seed, n=prob.n[0]).forcing]
+            ls = np.exp(rng.uniform(lo, hi, 64))
+            L.append(np.repeat(ls, len(ws)))
+            W.append(np.tile(ws, 64))
+        L, W = np.concatenate(L), np.concatenate(W)
+        perm = rng.permutation(L.size)
+        lam_d = torch.tensor(L[perm], device=dev)
+        om_d = torch.tensor(W[perm], device=dev)
+        x = torch.empty((L.size, 2), device=dev, dtype=torch.float32)
+        t = torch.empty((L.size, 2), device=dev, dtype=torch.float32)
+        t0 = time.perf_counter()
+        s.learned_samples(lam_d, om_d, x, t)
+        net = pe.MLP(seed=3)
+        loss = net.train(x, t, epochs=max(1, 60000 // ((L.size + 4095) // 4096)), batch=4096, lr=3e-3)
+        torch.cuda.synchronize()
+        out["training"] = {"pairs": int(L.size), "seeds": "100000..101999", "final_loss": loss,
+                           "seconds": time.perf_counter() - t0}
+        res = {}
+        for name, mlp in (("plain_G", None), ("learned_G", net)):
+            s.set_learned(mlp)
+            for _ in range(max(1, args.warmup)):
+                s.solve(tol=TOL)
+            barrier()
+            t1 = time.perf_counter()
+            infos = [s.solve(tol=TOL) for _ in range(args.steps)]
+            barrier()
+            dt = (time.perf_counter() - t1) / args.steps
+            modal = s.modal(prob.N)
+            res[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
+                         "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
+                         "residual": infos[-1]["residual"], "modal": modal}
+        s.set_learned(None)
+    rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=11)
+    w = sys_.norm_w
+    for name in res:
+        m = res[name].pop("modal")
+        res[name]["rel_l2_vs_oracle"] = float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) /
+                                              np.sqrt(np.sum(w * ref.U[-1] ** 2)))
+    out.update(res)
+    out["speedup_time_to_tol"] = res["plain_G"]["time_to_tol_ms"] / res["learned_G"]["time_to_tol_ms"]
+    net.close()
+    return out
+
+
+def run_general(pe, args, barrier, u0_dev):
+    """The 255^2 workload through the general forcing path: consistent load + tensor DST-I at
+    every one of the 32 x 64 x 4 fine stage times, per sweep."""
+    prob = workload()
+    out = {"workload": prob.label + " general forcing path (DST per stage time)"}
+    for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
+        with pe.Solver(prob, precision=prec, forcing_path=pe.PE_FORCING_GENERAL) as s:
+            for _ in range(max(1, args.warmup)):
+                s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
+            barrier()
+            t1 = time.perf_counter()
+            steps = max(1, args.steps // 2)
+            infos = [s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev) for _ in range(steps)]
+            barrier()
+            dt = (time.perf_counter() - t1) / steps
+        sweeps = infos[-1]["fine_sweeps"]
+        out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
+                     "value": prob.ndof * prob.N * prob.M * sweeps / dt, "unit": UNIT,
+                     "dst_transforms_per_step": sweeps * prob.N * prob.M * prob.q + prob.N * prob.p + 2}
+    return out
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle as it stands, on a bounded sample of the workload."""
     if rank != 0:
@@ -236,6 +319,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batched workload")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned coarse correction workload")
+    ap.add_argument("--no-general", action="store_true", help="skip the general forcing path workload")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -307,6 +392,8 @@ def main():
                 e2e_s = time.perf_counter() - t0
             results[name] = dict(total_ms=total_ms, infos=infos, modal=modal, e2e_s=e2e_s)
         batch = None if args.no_batch else run_batch(pe, args, barrier)
+        learned = None if args.no_learned else run_learned(pe, args, barrier)
+        general = None if args.no_general else run_general(pe, args, barrier, u0_dev)
     clock = clocks.summary()
 
     # max over ranks
@@ -403,6 +490,8 @@ def main():
         "clocks": clock,
         "cpu_baseline": cpu,
         "batched": batch,
+        "learned": learned,
+        "general": general,
     }
     print(json.dumps(line))
     if dist is not None:

@@ -14,10 +14,14 @@
 //     layout: K-chunk c of a stage at c * rows * 16 bytes, 8-row groups 128 bytes
 //     apart), two stages, mbarrier transaction counts;
 //   * one thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128,
-//     N = 128, K = 16 per instruction) with the accumulator in tensor memory,
-//     tcgen05.commit releases each stage;
-//   * epilogue: every warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) and
-//     writes its rows straight to the strided destination of the axis pass.
+//     N = 128, K = 16 per instruction) with the accumulators in tensor memory,
+//     tcgen05.commit releases each stage.  K tile kt accumulates into TMEM
+//     accumulator kt % 4 (4 x 128 columns): the tensor core's float32
+//     accumulation error grows with the number of products summed into one
+//     accumulator, so four partial sums, added in float32 with round-to-nearest
+//     in the epilogue, cut it about fourfold;
+//   * epilogue: every warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) of each
+//     accumulator and writes its rows straight to the strided destination.
 // Every mbarrier wait is bounded (about a second of clock cycles); on expiry the
 // CTA records an error code, skips the epilogue, frees its tensor memory and exits.
 #include <cuda.h>
@@ -35,6 +39,7 @@ constexpr int TBM = 128;  // rows of a CTA tile (TMEM lanes)
 constexpr int TBN = 128;  // columns of a CTA tile (TMEM columns)
 constexpr int TBK = 64;   // K per stage (4 MMAs of K = 16)
 constexpr int TSTAGES = 2;
+constexpr int NACC = 4;   // TMEM accumulators (NACC * TBN = 512 columns)
 constexpr int A_STAGE_BYTES = TBM * TBK * 2;  // 16 KB
 constexpr int B_STAGE_BYTES = TBN * TBK * 2;  // 16 KB
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TBN)
+                 "r"(NACC * TBN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -176,10 +181,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
       const uint32_t b0 = a0 + A_STAGE_BYTES;
+      const uint32_t dacc = tmem + (uint32_t)((kt % NACC) * TBN);
       for (int kk = 0; kk < TBK / 16; ++kk) {
         const uint64_t da = smem_desc(a0 + (2 * kk) * (TBM * 16), TBM * 16, 128);
         const uint64_t db = smem_desc(b0 + (2 * kk) * (TBN * 16), TBN * 16, 128);
-        mma_bf16(tmem, da, db, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(dacc, da, db, idesc, (kt >= NACC || kk > 0) ? 1u : 0u);
       }
       mma_commit(&empty_bar[s]);
       if (kt + TSTAGES < k_tiles) {
@@ -208,21 +214,29 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     const int64_t p = (int64_t)m0 + 32 * warp + lane;
     const bool row_ok = p < o.rows_valid;
     const int64_t ob = row_ok ? (p / o.inner) * (int64_t)o.n_valid * o.inner + (p % o.inner) : 0;
+    const int nacc = k_tiles < NACC ? k_tiles : NACC;
     for (int c = 0; c < TBN / 16; ++c) {
-      uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(c * 16);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-          "%14, %15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float sum[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) sum[e] = 0.f;
+      for (int ac = 0; ac < nacc; ++ac) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ac * TBN + c * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sum[e] += __uint_as_float(r[e]);
+      }
       if (row_ok) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int j = n0 + c * 16 + e;
-          if (j < o.n_valid) o.out[ob + (int64_t)j * o.inner] = __uint_as_float(r[e]) * o.scale;
+          if (j < o.n_valid) o.out[ob + (int64_t)j * o.inner] = sum[e] * o.scale;
         }
       }
     }
@@ -230,7 +244,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TBN) : "memory");
   }
 }
 
