@@ -223,6 +223,25 @@ pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, voi
 /* Same transform in float32 (device in/out). */
 pe_status pe_dst_f32(int32_t d, const int32_t* n, const float* in, float* out, void* stream);
 
+/*
+ * pe_dst_noalloc -- pe_dst for callers that cannot allocate device memory (code running
+ * while a CUDA graph is being captured, applications that own a fixed memory pool and
+ * forbid the runtime allocator, hosts whose device memory is reserved up front).  The
+ * paper has no counterpart: this is an interface variant, not a step of the method.
+ * It calls no cudaMalloc, cudaFree or other allocating routine; its scratch (ping-pong
+ * array, DST-I matrices, FFT twiddles) is one file-scope device array of 1,835,008
+ * doubles (about 14.7 MB) that every GPU loading the library holds until the process
+ * exits.  Limits: at most 1,048,576 values in total; an axis whose n+1 is not a power
+ * of two must have n <= 512.  Larger sizes return PE_EINVAL with a message.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind; nothing in it has to
+ * start at zero (each call writes what it reads), but calls that overlap on the GPU
+ * (different streams, or different host threads on one device) race on it.
+ * in/out: device float64, may alias; stream: cudaStream_t or NULL.
+ */
+pe_status pe_dst_noalloc(int32_t d, const int32_t* n, const double* in, double* out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched solver: many independent problems (uneven grids, D, sources and
  * slice counts) advanced together.  Every phase of Algorithm 1 over all

@@ -400,3 +400,123 @@ extern "C" pe_status pe_dst(int32_t d, const int32_t* n, const double* in, doubl
 extern "C" pe_status pe_dst_f32(int32_t d, const int32_t* n, const float* in, float* out, void* stream) {
   return standalone_dst<float>(d, n, in, out, stream);
 }
+
+// ---------------------------------------------------------------------------
+// pe_dst_noalloc: the same transform with no device allocation at all.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being
+// captured (an allocation would break or be recorded into the capture), callers
+// that own a fixed memory pool and forbid the runtime allocator, and hosts whose
+// device memory is fully reserved up front.  This entry point keeps every scratch
+// buffer of the transform (the ping-pong array, the DST-I matrices of axes without
+// an FFT length, the FFT twiddles) in one file-scope device array.  Every GPU that
+// loads the library holds that array (about 14.7 MB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoallocMaxNdof = (int64_t)1 << 20;     // ping-pong capacity (doubles)
+constexpr int kNoallocMaxMatrixN = 512;                   // axes on the matrix path
+constexpr int64_t kNoallocSlot = (int64_t)kNoallocMaxMatrixN * kNoallocMaxMatrixN;  // per axis
+constexpr int64_t kNoallocDoubles = kNoallocMaxNdof + PE_MAX_D * kNoallocSlot;
+
+static __device__ __align__(256) double g_dst_scratch[kNoallocDoubles];
+
+// Device address of g_dst_scratch on the current device, looked up once per device.
+pe_status noalloc_scratch(double** out) {
+  static double* addr[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return pe_fail(PE_EINVAL, "pe_dst_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_dst_scratch);
+    if (e != cudaSuccess) return pe_cuda_fail(e, "pe_dst_noalloc: cudaGetSymbolAddress");
+    addr[dev] = (double*)p;
+  }
+  *out = addr[dev];
+  return PE_OK;
+}
+
+// FFT pass with caller-provided twiddles (tw: L/2 values for L = 2^logL).
+pe_status fft_axis_tw(const double* in, double* out, int64_t outer, int n, int64_t inner, int logL,
+                      const Cplx<double>* tw, cudaStream_t st) {
+  const int L = 1 << logL;
+  const int64_t npencils = outer * inner;
+  int max_pairs = (int)((48 * 1024) / ((size_t)L * sizeof(Cplx<double>)));
+  max_pairs = max_pairs < 1 ? 1 : (max_pairs > 16 ? 16 : max_pairs);
+  int64_t pairs64 = (npencils + 1) / 2 / (2 * 152);
+  const int pairs = (int)(pairs64 < 1 ? 1 : (pairs64 > max_pairs ? max_pairs : pairs64));
+  const int64_t ctas = (npencils + 2 * pairs - 1) / (2 * pairs);
+  const size_t smem = sizeof(Cplx<double>) * ((size_t)pairs * L + L / 2);
+  if (smem > 48 * 1024)
+    PE_CUDA_TRY(cudaFuncSetAttribute(dst_fft_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  const int threads = L / 2 * pairs >= 256 ? 256 : (L / 2 * pairs >= 128 ? 128 : 64);
+  dst_fft_kernel<double><<<(unsigned)ctas, threads, smem, st>>>(in, out, n, logL, inner, npencils, pairs,
+                                                                0.5 * sqrt(2.0 / (double)(n + 1)), tw);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+}  // namespace
+
+extern "C" pe_status pe_dst_noalloc(int32_t d, const int32_t* n, const double* in, double* out, void* stream) {
+  if (d < 1 || d > PE_MAX_D || !n || !in || !out) return pe_fail(PE_EINVAL, "pe_dst_noalloc: bad arguments");
+  int64_t ndof = 1;
+  int logL[PE_MAX_D] = {0, 0, 0};
+  bool fft[PE_MAX_D] = {false, false, false};
+  for (int a = 0; a < d; ++a) {
+    if (n[a] < 1) return pe_fail(PE_EINVAL, "pe_dst_noalloc: n_a must be >= 1");
+    fft[a] = fft_size_ok(n[a], &logL[a]);
+    if (!fft[a] && n[a] > kNoallocMaxMatrixN)
+      return pe_fail(PE_EINVAL, "pe_dst_noalloc: an axis with n+1 not a power of two must have n <= 512 "
+                                "(its DST-I matrix must fit the built-in scratch array)");
+    ndof *= n[a];
+    if (ndof > kNoallocMaxNdof)
+      return pe_fail(PE_EINVAL, "pe_dst_noalloc: at most 1048576 values (the built-in scratch array's capacity)");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* scratch = nullptr;
+  PE_TRY(noalloc_scratch(&scratch));
+  double* tmp = scratch;  // ping-pong buffer, kNoallocMaxNdof values
+  // per-axis slot: the DST-I matrix (matrix path) or the twiddles (FFT path); every value the
+  // passes read is written here first, so nothing in the array has to start at zero
+  for (int a = 0; a < d; ++a) {
+    double* slot = scratch + kNoallocMaxNdof + (int64_t)a * kNoallocSlot;
+    if (fft[a]) {
+      const int L = 1 << logL[a];
+      twiddle_kernel<double><<<(L / 2 + 255) / 256, 256, 0, st>>>(L, reinterpret_cast<Cplx<double>*>(slot));
+    } else {
+      dim3 grid((n[a] + 127) / 128, n[a]);
+      dst_matrix_kernel_t<double><<<grid, 128, 0, st>>>(n[a], slot);
+    }
+  }
+  PE_CUDA_TRY(cudaGetLastError());
+  // passes: a pass never writes the array it reads (in may alias out)
+  const double* src = in;
+  if (in == out && (d % 2 == 1)) {
+    PE_CUDA_TRY(cudaMemcpyAsync(tmp, in, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, st));
+    src = tmp;
+  }
+  for (int a = 0; a < d; ++a) {
+    double* dst = ((d - 1 - a) % 2 == 0) ? out : tmp;
+    int64_t outer = 1, inner = 1;
+    for (int b = 0; b < a; ++b) outer *= n[b];
+    for (int b = a + 1; b < d; ++b) inner *= n[b];
+    double* slot = scratch + kNoallocMaxNdof + (int64_t)a * kNoallocSlot;
+    if (fft[a]) {
+      PE_TRY(fft_axis_tw(src, dst, outer, n[a], inner, logL[a], reinterpret_cast<const Cplx<double>*>(slot), st));
+    } else {
+      const int64_t rows = inner == 1 ? outer : n[a];
+      const int64_t cols = inner == 1 ? n[a] : inner;
+      const int64_t batch = inner == 1 ? 1 : outer;
+      const int64_t big = ((rows + 63) / 64) * ((cols + 63) / 64) * batch;
+      if (big >= 2 * 152) PE_TRY((gemm_axis<double, 64, 64>(slot, src, dst, outer, n[a], inner, st)));
+      else PE_TRY((gemm_axis<double, 32, 32>(slot, src, dst, outer, n[a], inner, st)));
+    }
+    src = dst;
+  }
+  return PE_OK;
+}

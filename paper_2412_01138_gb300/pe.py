@@ -36,7 +36,7 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_batch_autotune", "pe_batch_solve", "pe_batch_get_modal", "pe_batch_get_solution", "pe_batch_status",
             "pe_batch_destroy", "pe_mlp_create", "pe_mlp_num_params", "pe_mlp_train", "pe_mlp_gradient",
             "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
-            "pe_set_learned", "pe_dst_tc")
+            "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc")
 
 
 class PEError(RuntimeError):
@@ -129,6 +129,7 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_learned_samples": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
         "pe_set_learned": (C.c_int, [P, P]),
         "pe_dst_tc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, C.c_int32, P]),
+        "pe_dst_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
         "pe_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -336,6 +337,12 @@ def dst_tc(d: int, n: Sequence[int], x_in, x_out, nsplit: int = 3, stream=None):
     """Tensor-core (tcgen05) DST-I of a float32 device buffer, split-bfloat16 operands."""
     nn = (C.c_int32 * d)(*n)
     _check(lib().pe_dst_tc(d, nn, _ptr(x_in), _ptr(x_out), nsplit, stream_handle(stream)))
+
+
+def dst_noalloc(d: int, n: Sequence[int], x_in, x_out, stream=None):
+    """Float64 DST-I that allocates nothing (scratch in a built-in device array); see pe_dst_noalloc."""
+    nn = (C.c_int32 * d)(*n)
+    _check(lib().pe_dst_noalloc(d, nn, _ptr(x_in), _ptr(x_out), stream_handle(stream)))
 
 
 def dst(d: int, n: Sequence[int], x_in, x_out, stream=None, f32: bool = False):
