@@ -128,7 +128,7 @@ void free_ctx(pe_ctx* c) {
                   c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Gold, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
-                  c->Ktab, c->phase_tab};
+                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -271,8 +271,9 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->axisF32, MT * nsum);
   if (st == PE_OK) st = dev_alloc(&c->axisU0, MT * nsum);
   if (st == PE_OK) st = dev_alloc(&c->loads, MT * nsum);
-  if (st == PE_OK) st = dev_alloc(&c->AF, N * n_substeps * c->q * MT);
-  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AF32, N * n_substeps * c->q * MT);
+  if (st == PE_OK) st = dev_alloc(&c->AF, N * n_substeps * 2 * MT);
+  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AF32, N * n_substeps * 2 * MT);
+  if (st == PE_OK) st = dev_alloc(&c->Zst, (size_t)PE_MAX_S * 2 * MT);
   if (st == PE_OK) st = dev_alloc(&c->AG, N * c->p * MT);
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AG32, N * c->p * MT);
   if (st == PE_OK && c->forcing_path == PE_FORCING_GENERAL &&
@@ -341,6 +342,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   if (!general) {
     PE_TRY(launch_time_tables(c));
     PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1));
+    PE_TRY(launch_stage_weights(c));
   }
   // U^0 = P_h u0
   double* U0 = c->U;

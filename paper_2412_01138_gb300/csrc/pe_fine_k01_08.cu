@@ -1,4 +1,4 @@
-// Instantiations of the fine-sweep kernels for R = 1..8 forcing terms
+// Instantiations of the fine-sweep kernels for K = 1..8 stage-contracted columns
 // (split across translation units to keep compile times short).
 #include "pe_fine_kernels.cuh"
 

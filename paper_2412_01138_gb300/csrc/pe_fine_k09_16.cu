@@ -1,4 +1,4 @@
-// Instantiations of the fine-sweep kernels for R = 9..16 forcing terms
+// Instantiations of the fine-sweep kernels for K = 9..16 stage-contracted columns
 // (split across translation units to keep compile times short).
 #include "pe_fine_kernels.cuh"
 

@@ -2,11 +2,23 @@
 // parallel part of each Parareal iteration), Eq. (1-7) applied M times:
 //   c <- E_F c + sum_{i<q} (dt b_i) ghat_J(T_n + (m + c_i) dt),  m = 0..M-1,
 //   ghat_J(t) = sum_r A_r(t) P_{r,J}.
-// One CTA owns one slice n and 256 (float64) or 256*MPT (mixed) modes.
-// The slice's time factors A_r(t) for all M*q stage times are staged in
-// shared memory and read as warp-wide broadcasts; the per-mode weights
-// P_{r,J}, E_F and b_i stay in registers for the whole slice.  The kernel
-// is bound by the FMA rate: q(R+1)+1 FMAs per mode and substep.
+//
+// Stage contraction.  Every time factor of a separable source is shift
+// invariant: exp(a(t+s)) = exp(at) exp(as) and
+// sin(w(t+s)+phi) = sin(wt+phi) cos(ws) + cos(wt+phi) sin(ws).  Writing
+// A_r(t + s) = sum_k Y_{r,k}(t) Z_{r,k}(s) (one column k for an exponential,
+// two for a sinusoid; K columns in all), the stage sum of one substep is
+//   sum_i dt b_i ghat_J(t_m + c_i dt) = sum_k Y_k(t_m) W_{k,J},
+//   W_{k,J} = P_{r(k),J} sum_i dt b_i(-lam_J dt) Z_k(c_i dt),
+// with the per-mode weights W tabulated once per problem (stage_weights_kernel)
+// and Y_k at the substep starts t_m = T_n + m dt tabulated per slice.  This is
+// the same sum, regrouped: every substep is still taken, at K + 1 FMAs per mode
+// instead of q(R + 1) + 1.
+//
+// One CTA owns one slice n and 256 (float64) or 256*MPT (mixed) modes.  The
+// slice's Y_k(t_m) are staged in shared memory and read as warp-wide broadcasts;
+// W, E_F stay in registers for the whole slice.  The float64 kernel is bound
+// by the FP64 FMA rate.
 //
 // PE_MIXED splits F^M(v) = E_F^M v + F^M(0) (the step is affine in v): the
 // homogeneous part uses the float64 table value exp(-lam M dt), and the
@@ -15,55 +27,36 @@
 // compound over the M substeps.
 #pragma once
 #include "pe_internal.h"
-#include "pe_sweep_common.cuh"
 
 namespace {
 
-// Operands of one fine-propagator tile: one slice n of one problem, blockDim.x*MPT
-// modes starting at `base` (thread t owns base + t + k*blockDim.x, k < MPT, so every
+// Operands of one fine-propagator tile: one slice n, blockDim.x*MPT modes
+// starting at `base` (thread t owns base + t + k*blockDim.x, k < MPT, so every
 // global access stays coalesced).
 struct FineTile {
-  Geom g;
-  int M, q, mchunk;
+  int64_t ndof;
+  int M, mchunk;
   int64_t base;
-  const float* axisF32;   // per-axis modal factors (float)
-  const double* axisF;    // per-axis modal factors (double)
-  const float* AFn32;     // time factors of slice n [M][q][R] (float)
-  const double* AFn;      // time factors of slice n [M][q][R] (double)
-  const float* coefF32;   // E_hi, E_lo, dt*b_i  (rows of ndof)
+  const float* W32;       // stage weights [K][ndof] (float)
+  const double* W;        // stage weights [K][ndof] (double)
+  const float* Yn32;      // substep time factors of slice n [M][K] (float)
+  const double* Yn;       // substep time factors of slice n [M][K] (double)
+  const float* coefF32;   // E_hi, E_lo (rows of ndof)
   const double* coefF;    // E, dt*b_i, exp(-lam M dt) (rows of ndof)
+  int q;
   const double* Un;       // U^n
   double* Fn;             // F^M(U^n)
 };
 
-// P[r] = prod_a axisF[R*off[a] + r*n_a + j_a] for r < R, zero for R <= r < RC.
-template <int RC, typename T>
-__device__ __forceinline__ void load_P_rt(const Geom& g, int64_t J, const T* __restrict__ axisF, int R, T* P) {
-  int j[PE_MAX_D];
-  unflatten(g, J, j);
-#pragma unroll
-  for (int r = 0; r < RC; ++r) {
-    T v = T(0);
-    if (r < R) {
-      v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-      for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
-    }
-    P[r] = v;
-  }
-}
-
-// Mixed precision, R <= RC forcing terms (RC a multiple of 4): each float4 broadcast
-// load of four time factors feeds up to 4*MPT FMAs; staged rows are zero-padded to
-// RC.  RX > 0: R == RX is known at compile time and the padding lanes are skipped.
-template <int RC, int MPT, int RX = 0>
-__device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float* sAf) {
-  static_assert(RC % 4 == 0, "RC must be a multiple of 4");
-  const Geom& g = a.g;
-  const int q = a.q, M = a.M, B = blockDim.x;
-  const int64_t nd = g.ndof;
+// Mixed precision, K columns staged as KC = roundup(K, 4) floats per substep so
+// that each float4 broadcast load feeds 4*MPT FMAs; the padding lanes are skipped.
+template <int K, int MPT>
+__device__ __forceinline__ void fine_mixed_tile(const FineTile& a, float* sY) {
+  constexpr int KC = (K + 3) / 4 * 4;
+  const int M = a.M, B = blockDim.x;
+  const int64_t nd = a.ndof;
   const int64_t base = a.base + threadIdx.x;
-  float P[MPT][RC];
-  float b[MPT][PE_MAX_S];
+  float W[MPT][K];
   float eh[MPT], el[MPT], w[MPT];
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
@@ -72,58 +65,44 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float*
     el[k] = 0.f;
     w[k] = 0.f;
 #pragma unroll
-    for (int r = 0; r < RC; ++r) P[k][r] = 0.f;
-#pragma unroll
-    for (int i = 0; i < PE_MAX_S; ++i) b[k][i] = 0.f;
+    for (int c = 0; c < K; ++c) W[k][c] = 0.f;
     if (J < nd) {
-      load_P_rt<RC, float>(g, J, a.axisF32, R, P[k]);
+#pragma unroll
+      for (int c = 0; c < K; ++c) W[k][c] = a.W32[(int64_t)c * nd + J];
       eh[k] = a.coefF32[J];
       el[k] = a.coefF32[nd + J];
-#pragma unroll
-      for (int i = 0; i < PE_MAX_S; ++i)
-        if (i < q) b[k][i] = a.coefF32[(2 + i) * nd + J];
     }
   }
   for (int m0 = 0; m0 < M; m0 += a.mchunk) {
     const int mc = min(a.mchunk, M - m0);
     __syncthreads();
-    for (int t = threadIdx.x; t < mc * q * RC; t += B) {
-      const int row = t / RC, r = t - row * RC;
-      sAf[t] = r < R ? a.AFn32[((int64_t)m0 * q + row) * R + r] : 0.f;
+    for (int t = threadIdx.x; t < mc * KC; t += B) {
+      const int row = t / KC, c = t - row * KC;
+      sY[t] = c < K ? a.Yn32[(int64_t)(m0 + row) * K + c] : 0.f;
     }
     __syncthreads();
     for (int m = 0; m < mc; ++m) {
+      const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
       float acc[MPT];
 #pragma unroll
       for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
 #pragma unroll
-      for (int i = 0; i < PE_MAX_S; ++i) {
-        if (i < q) {
-          const float4* a4 = reinterpret_cast<const float4*>(sAf + (m * q + i) * RC);
-          float gk[MPT];
+      for (int c4 = 0; c4 < KC / 4; ++c4) {
+        const float4 v = y4[c4];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-          for (int k = 0; k < MPT; ++k) gk[k] = 0.f;
+        for (int e = 0; e < 4; ++e) {
+          if (4 * c4 + e < K) {
 #pragma unroll
-          for (int c4 = 0; c4 < RC / 4; ++c4) {
-            const float4 v = a4[c4];
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              if (RX == 0 || 4 * c4 + e < RX) {
-#pragma unroll
-                for (int k = 0; k < MPT; ++k) gk[k] = fmaf(vv[e], P[k][4 * c4 + e], gk[k]);
-              }
-            }
+            for (int k = 0; k < MPT; ++k) acc[k] = fmaf(vv[e], W[k][4 * c4 + e], acc[k]);
           }
-#pragma unroll
-          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(b[k][i], gk[k], acc[k]);
         }
       }
 #pragma unroll
       for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
     }
   }
-  const double* EM = a.coefF + (int64_t)(q + 1) * nd;
+  const double* EM = a.coefF + (int64_t)(a.q + 1) * nd;
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
     const int64_t J = base + (int64_t)B * k;
@@ -131,46 +110,34 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, int R, float*
   }
 }
 
-// Float64, R <= RC forcing terms: one mode per thread, the plain recurrence of Eq. (1-7).
-template <int RC>
-__device__ __forceinline__ void fine_f64_tile(const FineTile& a, int R, double* sA) {
-  const Geom& g = a.g;
-  const int q = a.q, M = a.M, B = blockDim.x;
-  const int64_t nd = g.ndof;
+// Float64: one mode per thread, the contracted recurrence c <- E c + sum_k Y_k W_k.
+template <int K>
+__device__ __forceinline__ void fine_f64_tile(const FineTile& a, double* sY) {
+  const int M = a.M, B = blockDim.x;
+  const int64_t nd = a.ndof;
   const int64_t J = a.base + threadIdx.x;
   const bool active = J < nd;
-  double P[RC];
-  double b[PE_MAX_S];
+  double W[K];
   double E = 0.0, c = 0.0;
-  if (active) {
-    load_P_rt<RC, double>(g, J, a.axisF, R, P);
-    E = a.coefF[J];
 #pragma unroll
-    for (int i = 0; i < PE_MAX_S; ++i)
-      if (i < q) b[i] = a.coefF[(1 + i) * nd + J];
+  for (int k = 0; k < K; ++k) W[k] = 0.0;
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) W[k] = a.W[(int64_t)k * nd + J];
+    E = a.coefF[J];
     c = a.Un[J];
   }
   for (int m0 = 0; m0 < M; m0 += a.mchunk) {
     const int mc = min(a.mchunk, M - m0);
     __syncthreads();
-    for (int t = threadIdx.x; t < mc * q * RC; t += B) {
-      const int row = t / RC, r = t - row * RC;
-      sA[t] = r < R ? a.AFn[((int64_t)m0 * q + row) * R + r] : 0.0;
-    }
+    for (int t = threadIdx.x; t < mc * K; t += B) sY[t] = a.Yn[(int64_t)m0 * K + t];
     __syncthreads();
     if (active) {
       for (int m = 0; m < mc; ++m) {
+        const double* yp = sY + m * K;
         double acc = 0.0;
 #pragma unroll
-        for (int i = 0; i < PE_MAX_S; ++i) {
-          if (i < q) {
-            const double* ap = sA + (m * q + i) * RC;
-            double gi = 0.0;
-#pragma unroll
-            for (int r = 0; r < RC; ++r) gi = fma(ap[r], P[r], gi);
-            acc = fma(b[i], gi, acc);
-          }
-        }
+        for (int k = 0; k < K; ++k) acc = fma(yp[k], W[k], acc);
         c = fma(E, c, acc);
       }
     }
@@ -178,61 +145,60 @@ __device__ __forceinline__ void fine_f64_tile(const FineTile& a, int R, double* 
   if (active) a.Fn[J] = c;
 }
 
-template <int R, int MPT>
-__global__ void __launch_bounds__(256) fine_mixed_kernel(FineTile t, int64_t slice_stride_af) {
-  constexpr int RC = (R + 3) / 4 * 4;
-  extern __shared__ __align__(16) float sAf[];
+template <int K, int MPT>
+__global__ void __launch_bounds__(256) fine_mixed_kernel(FineTile t, int64_t slice_stride_y) {
+  extern __shared__ __align__(16) float sYf[];
   const int n = blockIdx.y;
-  const int64_t nd = t.g.ndof;
+  const int64_t nd = t.ndof;
   t.base = (int64_t)blockIdx.x * (blockDim.x * MPT);
-  t.AFn32 += (int64_t)n * slice_stride_af;
+  t.Yn32 += (int64_t)n * slice_stride_y;
   t.Un += (int64_t)n * nd;
   t.Fn += (int64_t)n * nd;
-  fine_mixed_tile<RC, MPT, R>(t, R, sAf);
+  fine_mixed_tile<K, MPT>(t, sYf);
 }
 
-template <int R>
-__global__ void __launch_bounds__(256) fine_f64_kernel(FineTile t, int64_t slice_stride_af) {
-  extern __shared__ __align__(16) double sA[];
+template <int K>
+__global__ void __launch_bounds__(256) fine_f64_kernel(FineTile t, int64_t slice_stride_y) {
+  extern __shared__ __align__(16) double sY[];
   const int n = blockIdx.y;
-  const int64_t nd = t.g.ndof;
+  const int64_t nd = t.ndof;
   t.base = (int64_t)blockIdx.x * blockDim.x;
-  t.AFn += (int64_t)n * slice_stride_af;
+  t.Yn += (int64_t)n * slice_stride_y;
   t.Un += (int64_t)n * nd;
   t.Fn += (int64_t)n * nd;
-  fine_f64_tile<R>(t, R, sA);
+  fine_f64_tile<K>(t, sY);
 }
 
 }  // namespace
 
 
-template <int R>
+template <int K>
 pe_status fine_launch(pe_ctx* c, int precision) {
   const int threads = 256;
   FineTile t{};
-  t.g = c->g;
+  t.ndof = c->g.ndof;
   t.M = c->M;
   t.q = c->q;
-  t.axisF32 = c->axisF32;
-  t.axisF = c->axisF;
-  t.AFn32 = c->AF32;
-  t.AFn = c->AF;
+  t.W32 = c->Wst32;
+  t.W = c->Wst;
+  t.Yn32 = c->AF32;
+  t.Yn = c->AF;
   t.coefF32 = c->coefF32;
   t.coefF = c->coefF;
   t.Un = c->U;
   t.Fn = c->Fbar;
-  const int64_t stride = (int64_t)c->M * c->q * R;
+  const int64_t stride = (int64_t)c->M * K;
   if (precision == PE_MIXED) {
-    constexpr int MPT = R <= 16 ? 4 : 2;
-    constexpr int R4 = (R + 3) / 4 * 4;
-    t.mchunk = pick_mchunk(c->M, c->q * R4, sizeof(float));
+    constexpr int MPT = K <= 24 ? 4 : (K <= 40 ? 2 : 1);
+    constexpr int KC = (K + 3) / 4 * 4;
+    t.mchunk = pick_mchunk(c->M, KC, sizeof(float));
     const int64_t per_cta = (int64_t)threads * MPT;
     dim3 grid((unsigned)((c->g.ndof + per_cta - 1) / per_cta), c->N);
-    fine_mixed_kernel<R, MPT><<<grid, threads, sizeof(float) * t.mchunk * c->q * R4, c->stream>>>(t, stride);
+    fine_mixed_kernel<K, MPT><<<grid, threads, sizeof(float) * t.mchunk * KC, c->stream>>>(t, stride);
   } else {
-    t.mchunk = pick_mchunk(c->M, c->q * R, sizeof(double));
+    t.mchunk = pick_mchunk(c->M, K, sizeof(double));
     dim3 grid((unsigned)((c->g.ndof + threads - 1) / threads), c->N);
-    fine_f64_kernel<R><<<grid, threads, sizeof(double) * t.mchunk * c->q * R, c->stream>>>(t, stride);
+    fine_f64_kernel<K><<<grid, threads, sizeof(double) * t.mchunk * K, c->stream>>>(t, stride);
   }
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());

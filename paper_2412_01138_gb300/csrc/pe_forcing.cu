@@ -6,9 +6,10 @@
 // of 1D loads F_a[k] = int g_a phi_k, so
 //   ghat_J(t) = sum_r amp_r time_r(t) prod_a (S_a F_{r,a})_{j_a} / mu^M_a(j_a).
 // 1D loads use a Gauss-Legendre rule with quad_pts points on each element.
-// The per-axis modal factors and the time factors at every stage time of the
-// fine and coarse steps (Eq. (1-7)) are tabulated here; the sweeps multiply
-// them together on the fly.
+// The per-axis modal factors, the time factors of the coarse stages and of the
+// fine substep starts, and the per-mode stage weights of the fine step
+// (Eq. (1-7), with the stage sum contracted as described in pe_fine_kernels.cuh)
+// are tabulated here; the sweeps multiply them together on the fly.
 #include <math.h>
 
 #include "pe_internal.h"
@@ -16,24 +17,29 @@
 
 namespace {
 
-// AF[((n*M + m)*q + i)*R + r] and AG[(n*p + i)*R + r]
-__global__ void time_tables_kernel(TermsDev T, int N, int M, int q, int p, double t0, double dT, double dt,
-                                   Nodes cF, Nodes cG, double* __restrict__ AF, float* __restrict__ AF32,
-                                   double* __restrict__ AG, float* __restrict__ AG32) {
-  const int R = T.n;
-  const int64_t nf = (int64_t)N * M * q * R;
+// Time tables of one problem, one thread per entry:
+//   AF[(n*M + m)*K + k] = Y_k(T_n + m dt)   (fine substep starts, stage-contracted columns)
+//   AG[(n*p + i)*R + r] = amp_r time_r(T_n + c_i dT)   (coarse stage times)
+//   Z[i*K + k]          = Z_k(c_i dt)       (shift of column k to fine stage i)
+__global__ void time_tables_kernel(TermsDev T, StageCols C, int N, int M, int q, int p, double t0, double dT,
+                                   double dt, Nodes cF, Nodes cG, double* __restrict__ AF,
+                                   float* __restrict__ AF32, double* __restrict__ AG, float* __restrict__ AG32,
+                                   double* __restrict__ Z) {
+  const int R = T.n, K = C.K;
+  const int64_t nf = (int64_t)N * M * K;
   const int64_t ng = (int64_t)N * p * R;
+  const int64_t nz = (int64_t)q * K;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < nf) {
     int64_t rest = idx;
-    const int r = (int)(rest % R); rest /= R;
-    const int i = (int)(rest % q); rest /= q;
+    const int k = (int)(rest % K); rest /= K;
     const int m = (int)(rest % M); rest /= M;
     const int n = (int)rest;
-    const double Tn = t0 + (double)n * dT;
-    const double tl = Tn + (double)m * dt;
-    const double t = tl + cF.c[i] * dt;
-    const double v = T.t[r].amp * eval_time(T.t[r], t);
+    const double t = t0 + (double)n * dT + (double)m * dt;
+    const pe_term& tr = T.t[C.term[k]];
+    double v;
+    if (C.kind[k] == 1) v = tr.amp * cos(tr.tp[0] * t + tr.tp[1]);  // partner of a sinusoid
+    else v = tr.amp * eval_time(tr, t);
     AF[idx] = v;
     if (AF32) AF32[idx] = (float)v;
   } else if (idx < nf + ng) {
@@ -46,6 +52,38 @@ __global__ void time_tables_kernel(TermsDev T, int N, int M, int q, int p, doubl
     const double v = T.t[r].amp * eval_time(T.t[r], t);
     AG[idx - nf] = v;
     if (AG32) AG32[idx - nf] = (float)v;
+  } else if (idx < nf + ng + nz) {
+    const int64_t e = idx - nf - ng;
+    const int k = (int)(e % K), i = (int)(e / K);
+    const pe_term& tr = T.t[C.term[k]];
+    const double s = cF.c[i] * dt;
+    double v;
+    if (tr.tkind == PE_T_SIN) v = C.kind[k] == 1 ? sin(tr.tp[0] * s) : cos(tr.tp[0] * s);
+    else v = exp(tr.tp[0] * s);
+    Z[e] = v;
+  }
+}
+
+// W[k*ndof + J] = P_{r(k),J} sum_i (dt b_i)_J Z[i*K + k], with P_{r,J} = prod_a axisF[R off_a + r n_a + j_a].
+__global__ void stage_weights_kernel(Geom g, StageCols C, int R, int q, const double* __restrict__ axisF,
+                                     const double* __restrict__ coefF, const double* __restrict__ Z,
+                                     double* __restrict__ W, float* __restrict__ W32) {
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= g.ndof) return;
+  const int64_t nd = g.ndof;
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
+  double b[PE_MAX_S];
+  for (int i = 0; i < q; ++i) b[i] = coefF[(int64_t)(1 + i) * nd + J];
+  for (int k = 0; k < C.K; ++k) {
+    const int r = C.term[k];
+    double P = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+    for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+    double s = 0.0;
+    for (int i = 0; i < q; ++i) s = fma(b[i], Z[i * C.K + k], s);
+    const double w = P * s;
+    W[(int64_t)k * nd + J] = w;
+    if (W32) W32[(int64_t)k * nd + J] = (float)w;
   }
 }
 
@@ -130,11 +168,50 @@ pe_status launch_time_tables(pe_ctx* c) {
     nF.c[i] = c->cF[i];
     nG.c[i] = c->cG[i];
   }
-  const int64_t total = (int64_t)c->N * c->M * c->q * R + (int64_t)c->N * c->p * R;
+  // stage-contracted columns: one per exponential term, two per sinusoid
+  StageCols C{};
+  for (int r = 0; r < R; ++r) {
+    C.term[C.K] = (signed char)r;
+    C.kind[C.K++] = 0;
+    if (c->terms[r].tkind == PE_T_SIN) {
+      C.term[C.K] = (signed char)r;
+      C.kind[C.K++] = 1;
+    }
+  }
+  c->cols = C;
+  c->K = C.K;
+  const int64_t total = (int64_t)c->N * c->M * C.K + (int64_t)c->N * c->p * R + (int64_t)c->q * C.K;
   const int threads = 256;
   time_tables_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, c->stream>>>(
-      T, c->N, c->M, c->q, c->p, c->t0, c->dT, c->dt, nF, nG, c->AF,
-      c->precision == PE_MIXED ? c->AF32 : nullptr, c->AG, c->precision == PE_MIXED ? c->AG32 : nullptr);
+      T, C, c->N, c->M, c->q, c->p, c->t0, c->dT, c->dt, nF, nG, c->AF,
+      c->precision == PE_MIXED ? c->AF32 : nullptr, c->AG, c->precision == PE_MIXED ? c->AG32 : nullptr, c->Zst);
+  c->launches += 1;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status launch_stage_weights(pe_ctx* c) {
+  const int K = c->K;
+  if (K > c->Wcap) {
+    // grown on demand (first problem, or a problem with more columns than before)
+    PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->Wst) cudaFree(c->Wst);
+    if (c->Wst32) cudaFree(c->Wst32);
+    c->Wst = nullptr;
+    c->Wst32 = nullptr;
+    c->Wcap = 0;
+    const size_t n = (size_t)K * (size_t)c->g.ndof;
+    if (cudaMalloc((void**)&c->Wst, n * sizeof(double)) != cudaSuccess ||
+        (c->precision == PE_MIXED && cudaMalloc((void**)&c->Wst32, n * sizeof(float)) != cudaSuccess)) {
+      cudaGetLastError();
+      return pe_fail(PE_ENOMEM, "pe_set_problem: stage-weight table allocation failed");
+    }
+    c->Wcap = K;
+  }
+  const int threads = 256;
+  stage_weights_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(
+      c->g, c->cols, c->R, c->q, c->axisF, c->coefF, c->Zst, c->Wst,
+      c->precision == PE_MIXED ? c->Wst32 : nullptr);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;

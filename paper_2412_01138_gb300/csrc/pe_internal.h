@@ -48,10 +48,20 @@ __host__ __device__ inline void unflatten(const Geom& g, int64_t J, int* j) {
   }
 }
 
-// Separable forcing, device layout (R terms):
+// Separable forcing, device layout (R terms, K stage-contracted columns):
 //   axisF[R * off[a] + r * n_a + j]         = modal factor (S_a F_{r,a})_j / mu^M_a(j)
-//   AF[((n * M + m) * q + i) * R + r]       = amp_r * time_r(T_n + (m + c_i) dt)
+//   AF[(n * M + m) * K + k]                 = Y_k(T_n + m dt)   (substep-start time factors)
+//   Zst[i * K + k]                          = Z_k(c_i dt)       (stage shifts)
+//   Wst[k * ndof + J]                       = P_{r(k),J} sum_i dt b_i(J) Z_k(c_i dt)
 //   AG[(n * p + i) * R + r]                 = amp_r * time_r(T_n + c_i dT)
+// Column k belongs to term colTerm[k]: an exponential time factor gives one
+// column (Y = amp e^{at}, Z = e^{as}); a sinusoid gives two (kind 0:
+// Y = amp sin(wt+phi), Z = cos(ws); kind 1: Y = amp cos(wt+phi), Z = sin(ws)).
+struct StageCols {
+  int K;
+  signed char term[2 * PE_MAX_TERMS];
+  signed char kind[2 * PE_MAX_TERMS];
+};
 struct pe_ctx {
   // problem
   Geom g;
@@ -94,8 +104,14 @@ struct pe_ctx {
   double* axisF = nullptr;      // [PE_MAX_TERMS * nsum]
   float* axisF32 = nullptr;     // [PE_MAX_TERMS * nsum]
   double* axisU0 = nullptr;     // [PE_MAX_TERMS * nsum] factors of separable u0
-  double* AF = nullptr;         // [N*M*q*PE_MAX_TERMS]
+  double* AF = nullptr;         // [N*M*2*PE_MAX_TERMS]
   float* AF32 = nullptr;
+  int K = 0;                    // stage-contracted columns of the current forcing
+  StageCols cols{};
+  double* Zst = nullptr;        // [PE_MAX_S * 2*PE_MAX_TERMS]
+  double* Wst = nullptr;        // [K * ndof] (allocated on first use, grown with K)
+  float* Wst32 = nullptr;       // [K * ndof] (mixed precision)
+  int Wcap = 0;                 // columns allocated in Wst / Wst32
   double* AG = nullptr;         // [N*p*PE_MAX_TERMS]
   float* AG32 = nullptr;
   double* loads = nullptr;      // [PE_MAX_TERMS * nsum] 1D loads before the DST
@@ -137,7 +153,8 @@ pe_status build_dst_matrix(int n, double* S, cudaStream_t st);
 pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st);
 
 // pe_forcing.cu
-pe_status launch_time_tables(pe_ctx* c);
+pe_status launch_time_tables(pe_ctx* c);   // also sets c->K, c->cols and Zst
+pe_status launch_stage_weights(pe_ctx* c);  // Wst (and Wst32) from coefF, axisF, Zst
 pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode);
 pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* terms, int nterms, double* out,
                            int nodal_loads);

@@ -179,6 +179,42 @@ def test_parareal_iterates_match_oracle(pe, case):
     assert _rel(nodal, ref_nodal) <= TOL
 
 
+def _term_mix(kinds, seed):
+    """Separable terms with the given time kinds ('e' exponential, 's' sinusoid); rates, frequencies
+    (up to 200, several turns per substep) and phases from a SplitMix64 stream."""
+    rng = I.SplitMix64(seed)
+    out = []
+    for k in kinds:
+        facs = (I.Factor(I.S_SIN, (math.pi * (1 + int(4 * rng.uniform())), 0.0)),
+                I.Factor(I.S_GAUSS, (rng.uniform(), 0.05 + 0.1 * rng.uniform())))
+        amp = 2.0 * rng.uniform() - 1.0
+        if k == "e":
+            out.append(I.Term(amp, facs, I.T_EXP, (8.0 * rng.uniform() - 6.0, 0.0)))
+        else:
+            out.append(I.Term(amp, facs, I.T_SIN, (200.0 * rng.uniform(), 2.0 * math.pi * rng.uniform())))
+    return tuple(out)
+
+
+@pytest.mark.parametrize("kinds", ["e", "s", "es", "e" * 32, "s" * 32, "esse" * 4 + "s", "ses" * 10])
+def test_stage_contraction_all_column_counts(pe, kinds):
+    """The fine step regroups the q-stage forcing sum into K columns (one per exponential, two per
+    sinusoid): K from 1 to the maximum 64, odd and even, against the oracle's stage-by-stage sum."""
+    box = ((0.0, 1.0), (0.0, 1.0))
+    u0, _, _ = I.sin_mode(2, box, 0.05)
+    fine = I.draw_random_nodes(5, 77)
+    prob = I.Problem(2, (19, 23), box, 0.05, 0.1, 0.6, 3, 7, fine, I.uniform_nodes(2), u0,
+                     _term_mix(kinds, len(kinds)), 3, 1e-12)
+    sys_ = osolver.ModalSystem(prob)
+    ref = osolver.parareal(sys_, tol=0.0, k_max=2)
+    w = sys_.norm_w
+    with pe.Solver(prob) as s:
+        s.set_problem()
+        for k in range(1, 3):
+            s.iterate()
+            for n in range(1, prob.N + 1):
+                assert _rel(s.modal(n), ref.history[k][n], w) <= TOL, (k, n)
+
+
 def test_config1_solve_to_tolerance(pe):
     """Config 1: 1D, 63 nodes, 8 x 16 RK2/RK2, FP64, residual 1e-12."""
     prob = I.config1()
