@@ -204,8 +204,8 @@ def oracle_sample(prob, n_modes: int, seed: int = 0, u0_nodal=None):
 
 def run_batch(pe, args, barrier):
     """512 uneven 2D problems: batched persistent mixed form vs a per-problem float64 loop."""
-    probs = I.config4()
-    out = {"workload": "512 uneven 2D problems (n 31..511, 16-64 slices x 32 substeps, RK4/RK2)"}
+    probs = I.config4(count=args.batch_count)
+    out = {"workload": f"{len(probs)} uneven 2D problems (n 31..511, 16-64 slices x 32 substeps, RK4/RK2)"}
     with pe.BatchSolver(probs, precision=pe.PE_MIXED) as b:
         b.autotune(None)
         for _ in range(max(1, args.warmup)):
@@ -224,16 +224,21 @@ def run_batch(pe, args, barrier):
                                                                                   infos[-1]["ctas_per_sm"]],
                      "ms_prepare": infos[-1]["ms_prepare"], "ms_iterations": infos[-1]["ms_iterations"],
                      "gpu_launches": infos[-1]["kernel_launches"]}
-    # plain: one problem after another, float64, host-driven iteration loop
-    barrier()
-    t0 = time.perf_counter()
-    units_p = 0
-    for prob in probs:
-        with pe.Solver(prob, precision=pe.PE_FP64) as s:
+    # plain: one problem after another, float64, host-driven iteration loop (solvers set up
+    # before the timed region, as the batch is)
+    solvers = [pe.Solver(prob, precision=pe.PE_FP64) for prob in probs]
+    try:
+        barrier()
+        t0 = time.perf_counter()
+        units_p = 0
+        for prob, s in zip(probs, solvers):
             info = s.solve(tol=TOL)
             units_p += prob.ndof * prob.N * prob.M * info["fine_sweeps"]
-    barrier()
-    dtp = time.perf_counter() - t0
+        barrier()
+        dtp = time.perf_counter() - t0
+    finally:
+        for s in solvers:
+            s.close()
     out["plain"] = {"form": "float64, one problem per launch sequence", "time_to_tol_ms": 1e3 * dtp,
                     "value": units_p / dtp, "unit": UNIT}
     out["speedup_time_to_tol"] = dtp / dt
@@ -301,6 +306,51 @@ def run_learned(pe, args, barrier):
     return out
 
 
+DST_SHAPE = (511, 511, 255)
+
+
+def run_dst(pe, args, barrier):
+    """Tensor DST-I of a (511, 511, 255) grid (every axis, n + 1 a power of two: the FFT kernels)
+    in float64 and float32, and the tcgen05 split-bf16 form (float32 in/out).  Algorithmic bytes per
+    call: one read and one write of the grid per axis pass.  L2 flushed before every call."""
+    import torch
+
+    dev = torch.device("cuda")
+    n = DST_SHAPE
+    size = int(np.prod(n))
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    peaks = measured_peaks() or {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    stream = torch.cuda.current_stream(dev)
+    out = {"shape": list(n), "hbm_peak_gbs": hbm}
+    forms = (("f64", torch.float64, lambda x, y: pe.dst(3, n, x, y)),
+             ("f32", torch.float32, lambda x, y: pe.dst(3, n, x, y, f32=True)),
+             ("tc_bf16x3", torch.float32, lambda x, y: pe.dst_tc(3, n, x, y, nsplit=3)))
+    gen = torch.Generator(device=dev).manual_seed(5)
+    for name, dt, fn in forms:
+        x = torch.randn(size, dtype=dt, device=dev, generator=gen)
+        y = torch.empty_like(x)
+        for _ in range(max(1, args.warmup)):
+            fn(x, y)
+        barrier()
+        times = []
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(x, y)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        nbytes = 3 * 2 * size * x.element_size()
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "gbs": nbytes / (ms / 1e3) / 1e9,
+                     "frac_hbm": nbytes / (ms / 1e3) / 1e9 / hbm}
+        del x, y
+    return out
+
+
 def run_general(pe, args, barrier, u0_dev):
     """The 255^2 workload through the general forcing path: consistent load + tensor DST-I at
     every one of the 32 x 64 x 4 fine stage times, per sweep."""
@@ -361,6 +411,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned coarse correction workload")
     ap.add_argument("--no-general", action="store_true", help="skip the general forcing path workload")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="problems in the batched workload (512; fewer only for small profiling captures)")
+    ap.add_argument("--no-dst", action="store_true", help="skip the standalone DST-I measurement")
+    ap.add_argument("--only", choices=["batch", "learned", "general", "dst"],
+                    help="run one secondary workload alone and print its record (for profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -415,6 +470,15 @@ def main():
         barrier()
         return total_ms, infos
 
+    if args.only:
+        run = {"batch": lambda: run_batch(pe, args, barrier), "learned": lambda: run_learned(pe, args, barrier),
+               "general": lambda: run_general(pe, args, barrier, u0_dev),
+               "dst": lambda: run_dst(pe, args, barrier)}[args.only]
+        rec = run()
+        if rank == 0:
+            print(json.dumps({"section": args.only, **rec}))
+        return
+
     results = {}
     with ClockSampler(local if world > 1 else 0) as clocks:
         for name, precision in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
@@ -434,6 +498,7 @@ def main():
         batch = None if args.no_batch else run_batch(pe, args, barrier)
         learned = None if args.no_learned else run_learned(pe, args, barrier)
         general = None if args.no_general else run_general(pe, args, barrier, u0_dev)
+        dst = None if args.no_dst else run_dst(pe, args, barrier)
     clock = clocks.summary()
 
     # max over ranks
@@ -459,9 +524,11 @@ def main():
         value = units / (r["total_ms"] / 1e3)
         e2e_units = prob.ndof * prob.N * prob.M * k * args.steps * world
         ms_fine = np.mean([i["ms_fine_kernel"] / max(i["fine_sweeps"], 1) for i in r["infos"]])
+        phases = {key: float(np.mean([i[key] for i in r["infos"]]))
+                  for key in ("ms_tables", "ms_prepare", "ms_iterations", "ms_output", "ms_fine_kernel")}
         return dict(value=value, k=k, ms_per_step=r["total_ms"] / args.steps, e2e=e2e_units / r["e2e_s"],
                     ms_fine_launch=ms_fine, launches=r["infos"][-1]["kernel_launches"],
-                    residual=r["infos"][-1]["residual"])
+                    residual=r["infos"][-1]["residual"], phases=phases)
 
     plain = summarize(results["fp64"])
     chosen = summarize(results["mixed"])
@@ -521,7 +588,8 @@ def main():
                    "fine_kernel_tflops": fine_flops_per_unit(prob, mixed=True) * prob.ndof * prob.N * prob.M
                    / (chosen["ms_fine_launch"] / 1e3) / 1e12,
                    "fp32_peak_tflops": fp32_peak_tflops(sm_mhz),
-                   "e2e": chosen["e2e"]},
+                   "e2e": chosen["e2e"], "phases_ms": chosen["phases"]},
+        "phases_ms": plain["phases"],
         "roofline": {"kernel": "fine_f64_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x max SM clock",
@@ -534,6 +602,7 @@ def main():
         "batched": batch,
         "learned": learned,
         "general": general,
+        "dst": dst,
     }
     print(json.dumps(line))
     if dist is not None:

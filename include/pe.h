@@ -131,8 +131,10 @@ typedef struct {
   double* residual_history;  /* host, caller-owned, capacity history_cap (may be NULL) */
   int32_t history_cap;
   int64_t fine_sweeps;       /* fine propagator sweeps executed (= k) */
-  double ms_tables;          /* device time of the phi/b coefficient tables */
-  double ms_prepare;         /* forcing tables, projection of u0, coarse sweep */
+  double ms_tables;          /* device time of the forcing tables (time factors, per-axis modal
+                                factors, fine-step stage weights); the phi/b coefficient tables
+                                depend only on pe_setup's arguments and are made there */
+  double ms_prepare;         /* projection of u0, coarse sweep */
   double ms_iterations;      /* all fine sweeps + corrections + residuals */
   double ms_output;          /* inverse DST of the final slice */
   double ms_fine_kernel;     /* device time of the fine-propagator kernels alone (sum over sweeps) */
@@ -271,7 +273,7 @@ typedef struct {
   int32_t max_k;              /* largest per-problem iteration count */
   double max_residual;        /* largest per-problem final relative residual */
   int64_t fine_dof_substeps;  /* sum over problems of Ndof * N * M * (its fine sweeps) */
-  double ms_prepare;          /* tables, forcing, u0 projection, coarse sweeps */
+  double ms_prepare;          /* forcing tables, u0 projection, coarse sweeps (phi/b tables: set-up) */
   double ms_iterations;       /* all graph replays */
   int64_t kernel_launches;    /* kernels launched (graph nodes counted per replay) */
   int32_t threads, ctas_per_sm; /* launch shape of the persistent fine kernel */

@@ -335,15 +335,14 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     c->R = nf;
     for (int i = 0; i < nf; ++i) c->terms[i] = f->terms[i];
   }
-  // coefficient tables (a function of lam, dt, dT and the nodes)
-  PE_TRY(launch_coef_tables(c));
-  PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
-  // forcing: time factors and per-axis modal factors
+  // The phi/b coefficient tables depend only on lam, dt, dT and the nodes: pe_setup made them.
+  // Forcing: time factors, per-axis modal factors and the stage weights of the fine step.
   if (!general) {
     PE_TRY(launch_time_tables(c));
     PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1));
     PE_TRY(launch_stage_weights(c));
   }
+  PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
   // U^0 = P_h u0
   double* U0 = c->U;
   if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {

@@ -107,31 +107,36 @@ __global__ void b_coef_tables_kernel(const BProb* __restrict__ probs, const Mode
   }
 }
 
-// fine (n, m, i, r) and coarse (n, i, r) time factors of every problem
+// Time tables of every problem, one thread per entry (layout as in the single-problem
+// solver): fine substep starts Y[(n*M + m)*K + k], coarse stage times AG[(n*p + i)*R + r],
+// stage shifts Z[i*K + k].  Column k of a problem is cols[oCol + k] = (term << 1) | kind:
+// kind 0 is amp*time(t) (shift factor e^{as} or cos(ws)), kind 1 the partner amp*cos(wt+phi)
+// of a sinusoid (shift factor sin(ws)).
 __global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int64_t* __restrict__ tt_prefix, int P,
-                                     int64_t total, const pe_term* __restrict__ terms, double* __restrict__ AF,
-                                     float* __restrict__ AF32, double* __restrict__ AG) {
+                                     int64_t total, const pe_term* __restrict__ terms,
+                                     const short* __restrict__ cols, double* __restrict__ AF,
+                                     float* __restrict__ AF32, double* __restrict__ AG, float* __restrict__ AG32,
+                                     double* __restrict__ Z) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int p = find_prob(tt_prefix, P, idx);
   const BProb& B = probs[p];
-  const int R = B.R;
-  const int64_t nf = (int64_t)B.N * B.M * B.q * R;
+  const int R = B.R, K = B.K;
+  const int64_t nf = (int64_t)B.N * B.M * K;
+  const int64_t ng = (int64_t)B.N * B.p * R;
   int64_t local = idx - tt_prefix[p];
   if (local < nf) {
     int64_t rest = local;
-    const int r = (int)(rest % R); rest /= R;
-    const int i = (int)(rest % B.q); rest /= B.q;
+    const int k = (int)(rest % K); rest /= K;
     const int m = (int)(rest % B.M); rest /= B.M;
     const int n = (int)rest;
-    const double Tn = B.t0 + (double)n * B.dT;
-    const double tl = Tn + (double)m * B.dt;
-    const double t = tl + B.cF[i] * B.dt;
-    const pe_term& T = terms[B.tf + r];
-    const double v = T.amp * eval_time(T, t);
+    const double t = B.t0 + (double)n * B.dT + (double)m * B.dt;
+    const int c = cols[B.oCol + k];
+    const pe_term& T = terms[B.tf + (c >> 1)];
+    const double v = (c & 1) ? T.amp * cos(T.tp[0] * t + T.tp[1]) : T.amp * eval_time(T, t);
     AF[B.oAF + local] = v;
     if (AF32) AF32[B.oAF + local] = (float)v;
-  } else {
+  } else if (local < nf + ng) {
     local -= nf;
     int64_t rest = local;
     const int r = (int)(rest % R); rest /= R;
@@ -140,7 +145,49 @@ __global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int6
     const double Tn = B.t0 + (double)n * B.dT;
     const double t = Tn + B.cG[i] * B.dT;
     const pe_term& T = terms[B.tf + r];
-    AG[B.oAG + local] = T.amp * eval_time(T, t);
+    const double v = T.amp * eval_time(T, t);
+    AG[B.oAG + local] = v;
+    if (AG32) AG32[B.oAG + local] = (float)v;
+  } else {
+    local -= nf + ng;
+    const int k = (int)(local % K), i = (int)(local / K);
+    const int c = cols[B.oCol + k];
+    const pe_term& T = terms[B.tf + (c >> 1)];
+    const double s = B.cF[i] * B.dt;
+    double v;
+    if (T.tkind == PE_T_SIN) v = (c & 1) ? sin(T.tp[0] * s) : cos(T.tp[0] * s);
+    else v = exp(T.tp[0] * s);
+    Z[B.oZ + local] = v;
+  }
+}
+
+// Per-mode stage weights W[oW + k*ndof + J] = P_{r(k),J} sum_i (dt b_i)_J Z[oZ + i*K + k].
+__global__ void b_stage_weights_kernel(const BProb* __restrict__ probs, const ModeItem* __restrict__ items,
+                                       int n_items, const short* __restrict__ cols,
+                                       const double* __restrict__ axisF, const double* __restrict__ coefF,
+                                       const double* __restrict__ Z, double* __restrict__ W,
+                                       float* __restrict__ W32) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const ModeItem mi = items[it];
+    const BProb& B = probs[mi.p];
+    const int64_t J = mi.J0 + threadIdx.x;
+    if (J >= B.g.ndof) continue;
+    const int64_t nd = B.g.ndof;
+    int j[PE_MAX_D];
+    unflatten(B.g, J, j);
+    double b[PE_MAX_S];
+    for (int i = 0; i < B.q; ++i) b[i] = coefF[B.oCF + (int64_t)(1 + i) * nd + J];
+    const double* ax = axisF + B.oAx;
+    for (int k = 0; k < B.K; ++k) {
+      const int r = cols[B.oCol + k] >> 1;
+      double P = ax[(int64_t)B.R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
+      for (int a = 1; a < B.g.d; ++a) P *= ax[(int64_t)B.R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+      double sum = 0.0;
+      for (int i = 0; i < B.q; ++i) sum = fma(b[i], Z[B.oZ + (int64_t)i * B.K + k], sum);
+      const double w = P * sum;
+      W[B.oW + (int64_t)k * nd + J] = w;
+      if (W32) W32[B.oW + (int64_t)k * nd + J] = (float)w;
+    }
   }
 }
 
@@ -216,12 +263,14 @@ __global__ void b_u0_kernel(const BProb* __restrict__ probs, const ModeItem* __r
 }
 
 // coarse sweep (k = 0) of every problem; P_{r,J} staged per thread in shared memory
+template <typename TF>
 __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__ probs,
                                                        const ModeItem* __restrict__ items, int n_items,
-                                                       const double* __restrict__ axisF, const double* __restrict__ AG,
+                                                       const double* __restrict__ axisF, const TF* __restrict__ AG,
                                                        const double* __restrict__ coefG, double* __restrict__ U,
                                                        double* __restrict__ Gold, double* __restrict__ gG) {
-  extern __shared__ double sP[];  // [PE_BATCH_MAX_TERMS][256]
+  extern __shared__ __align__(16) unsigned char sP_raw[];
+  TF* sP = reinterpret_cast<TF*>(sP_raw);  // [PE_BATCH_MAX_TERMS][256]
   const int tid = threadIdx.x, BD = blockDim.x;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const ModeItem m = items[it];
@@ -235,27 +284,27 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
     for (int r = 0; r < R; ++r) {
       double v = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
       for (int a = 1; a < B.g.d; ++a) v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
-      sP[r * BD + tid] = v;
+      sP[r * BD + tid] = (TF)v;
     }
     const double* cg = coefG + B.oCG;
     const double E = cg[J];
-    double b[PE_MAX_S];
-    for (int i = 0; i < B.p; ++i) b[i] = cg[(1 + i) * nd + J];
+    TF b[PE_MAX_S];
+    for (int i = 0; i < B.p; ++i) b[i] = (TF)cg[(1 + i) * nd + J];
     double* Up = U + B.oU;
     double* Gp = Gold + B.oS;
     double* gp = gG + B.oS;
-    const double* ag = AG + B.oAG;
+    const TF* ag = AG + B.oAG;
     double c = Up[J];
     for (int n = 0; n < B.N; ++n) {
-      double acc = 0.0;
+      TF acc = TF(0);
       for (int i = 0; i < B.p; ++i) {
-        const double* arow = ag + ((int64_t)n * B.p + i) * R;
-        double gi = 0.0;
+        const TF* arow = ag + ((int64_t)n * B.p + i) * R;
+        TF gi = TF(0);
         for (int r = 0; r < R; ++r) gi = fma(__ldg(arow + r), sP[r * BD + tid], gi);
         acc = fma(b[i], gi, acc);
       }
-      gp[(int64_t)n * nd + J] = acc;
-      c = fma(E, c, acc);
+      gp[(int64_t)n * nd + J] = (double)acc;
+      c = fma(E, c, (double)acc);
       Up[(int64_t)(n + 1) * nd + J] = c;
       Gp[(int64_t)n * nd + J] = c;
     }
@@ -377,8 +426,8 @@ pe_status batch_set_attributes(pe_batch* b) {
   const size_t smem = sizeof(double) * (size_t)(b->nmax + 2 * (b->nmax + 1));
   PE_CUDA_TRY(cudaFuncSetAttribute(b_axis_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const size_t csmem = sizeof(double) * PE_BATCH_MAX_TERMS * 256;
-  PE_CUDA_TRY(cudaFuncSetAttribute(b_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
-  return batch_fine_set_smem(b->precision, b->fine_smem);
+  PE_CUDA_TRY(cudaFuncSetAttribute(b_coarse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+  return PE_OK;  // the fine kernels stage at most 48 KB (pick_mchunk), the default limit
 }
 
 pe_status batch_launch_axis_tables(pe_batch* b) {
@@ -390,44 +439,73 @@ pe_status batch_launch_axis_tables(pe_batch* b) {
   return PE_OK;
 }
 
+// phi/b coefficient tables: a function of lam, the step sizes and the nodes only (made at set-up)
+pe_status batch_launch_coef_tables(pe_batch* b) {
+  b_coef_tables_kernel<<<b->sm_count * 8, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items,
+                                                               b->ratio, b->coefF, b->coefG, b->coefF32);
+  b->launches += 1;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
 pe_status batch_launch_prepare(pe_batch* b) {
   const int grid_items = b->sm_count * 8;
-  // coefficient tables
-  b_coef_tables_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->ratio,
-                                                         b->coefF, b->coefG, b->coefF32);
   // time factors
   b_time_tables_kernel<<<(unsigned)((b->tt_total + 255) / 256), 256, 0, b->stream>>>(
-      b->d_probs, b->d_tt_prefix, b->P, b->tt_total, b->d_terms, b->AF, b->AF32, b->AG);
+      b->d_probs, b->d_tt_prefix, b->P, b->tt_total, b->d_terms, b->d_cols, b->AF, b->AF32, b->AG, b->AG32, b->Z);
   // per-axis factors of forcing and initial data
   const size_t smem = sizeof(double) * (size_t)(b->nmax + 2 * (b->nmax + 1));
   b_axis_factor_kernel<<<b->n_factor_jobs, 256, smem, b->stream>>>(b->d_probs, b->d_factor_jobs, b->d_terms,
                                                                    b->gauss, b->muM, b->axisF, b->axisF32,
                                                                    b->axisU0);
+  // per-mode stage weights of the fine step
+  b_stage_weights_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->d_cols,
+                                                            b->axisF, b->coefF, b->Z, b->W, b->W32);
   b_u0_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->d_terms, b->axisU0,
                                                  b->U);
-  const size_t csmem = sizeof(double) * PE_BATCH_MAX_TERMS * 256;
-  b_coarse_kernel<<<grid_items, 256, csmem, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF,
-                                                          b->AG, b->coefG, b->U, b->Gold, b->gG);
+  // the coarse forcing is iterate-independent and cancels in G(U^{k+1}) - G(U^k): the mixed
+  // form evaluates it in float32, the recurrence stays float64
+  if (b->precision == PE_MIXED)
+    b_coarse_kernel<float><<<grid_items, 256, sizeof(float) * PE_BATCH_MAX_TERMS * 256, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, b->Gold, b->gG);
+  else
+    b_coarse_kernel<double><<<grid_items, 256, sizeof(double) * PE_BATCH_MAX_TERMS * 256, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, b->Gold, b->gG);
   b->launches += 5;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
 
+// One persistent launch per column class present in the batch, each over its own items
+// and counter (counter[c]); grids never exceed the class's item count.
 static pe_status launch_fine(pe_batch* b, cudaStream_t st, int threads, int ctas_per_sm) {
   const FineItems& fi = threads == 128 ? b->fine128 : b->fine256;
   BatchArrays A{};
-  A.axisF = b->axisF; A.axisF32 = b->axisF32; A.AF = b->AF; A.AF32 = b->AF32;
+  A.W = b->W; A.W32 = b->W32; A.AF = b->AF; A.AF32 = b->AF32;
   A.coefF = b->coefF; A.coefF32 = b->coefF32; A.U = b->U; A.Fbar = b->Fbar;
-  const int grid = b->sm_count * ctas_per_sm;
-  if (b->precision == PE_MIXED)
-    return batch_launch_fine_mixed(b->d_probs, fi.d_items, fi.n, b->active, b->counter, A, grid, threads,
-                                   b->fine_smem, st);
-  return batch_launch_fine_f64(b->d_probs, fi.d_items, fi.n, b->active, b->counter, A, grid, threads, b->fine_smem,
-                               st);
+  for (int c = 0; c < kBatchClasses; ++c) {
+    const int n = fi.begin[c + 1] - fi.begin[c];
+    if (n == 0) continue;
+    const int grid = std::min(b->sm_count * ctas_per_sm, n);
+    const FineItem* items = fi.d_items + fi.begin[c];
+    if (b->precision == PE_MIXED)
+      PE_TRY(batch_launch_fine_mixed(4 * (c + 1), b->d_probs, items, n, b->active, b->counter + c, A, grid, threads,
+                                     fi.smem[c], st));
+    else
+      PE_TRY(batch_launch_fine_f64(4 * (c + 1), b->d_probs, items, n, b->active, b->counter + c, A, grid, threads,
+                                   fi.smem[c], st));
+  }
+  return PE_OK;
+}
+
+int batch_fine_launches(const pe_batch* b) {
+  int k = 0;
+  for (int c = 0; c < kBatchClasses; ++c) k += b->fine256.begin[c + 1] > b->fine256.begin[c];
+  return k;
 }
 
 pe_status batch_enqueue_iteration(pe_batch* b, cudaStream_t st, double tol) {
-  PE_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), st));
+  PE_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int) * kBatchClasses, st));
   PE_CUDA_TRY(cudaMemsetAsync(b->n_active, 0, sizeof(int), st));
   PE_TRY(launch_fine(b, st, b->tune_threads, b->tune_ctas));
   b_correction_kernel<<<b->sm_count * 8, 256, 0, st>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->active,
@@ -443,7 +521,7 @@ pe_status batch_time_fine(pe_batch* b, int threads, int ctas, float* ms) {
   cudaEvent_t e0, e1;
   PE_CUDA_TRY(cudaEventCreate(&e0));
   PE_CUDA_TRY(cudaEventCreate(&e1));
-  PE_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream));
+  PE_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int) * kBatchClasses, b->stream));
   PE_CUDA_TRY(cudaEventRecord(e0, b->stream));
   PE_TRY(launch_fine(b, b->stream, threads, ctas));
   PE_CUDA_TRY(cudaEventRecord(e1, b->stream));
@@ -451,6 +529,6 @@ pe_status batch_time_fine(pe_batch* b, int threads, int ctas, float* ms) {
   PE_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->launches += 1;
+  b->launches += batch_fine_launches(b);
   return PE_OK;
 }

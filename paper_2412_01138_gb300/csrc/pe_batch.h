@@ -10,6 +10,7 @@
 struct BProb {
   Geom g;
   int N, M, q, p, R, Ru;   // slices, substeps, fine/coarse stages, forcing / u0 terms
+  int K;                   // stage-contracted columns of the fine step (one per exponential, two per sinusoid)
   int mchunk;              // substeps of time factors staged per shared-memory fill
   int tf, tu;              // first forcing / u0 term in the terms array
   double D, t0, dT, dt;
@@ -22,12 +23,19 @@ struct BProb {
   int64_t oCG;   // coefG arena: (p+1)*ndof
   int64_t oAx;   // axisF / axisF32: R*nsum
   int64_t oAxU;  // axisU0: Ru*nsum
-  int64_t oAF;   // AF / AF32: N*M*q*R
+  int64_t oAF;   // AF / AF32: substep-start time factors Y, N*M*K
+  int64_t oW;    // W / W32: per-mode stage weights, K*ndof
+  int64_t oZ;    // Z: stage shifts, q*K
+  int64_t oCol;  // column map: K entries, (term << 1) | kind
   int64_t oAG;   // AG: N*p*R
   int64_t oMu;   // muM / ratio: nsum
   int64_t oItems;  // first mode item of this problem
   int nItems;
 };
+
+// Modes per thread of the mixed-precision fine tile for a problem with K stage columns
+// (the work items and the kernel's tile dispatch both use it).
+__host__ __device__ constexpr int batch_mixed_mpt(int KC) { return KC <= 16 ? 4 : 2; }
 
 struct ModeItem {
   int p;
@@ -46,8 +54,8 @@ struct FactorJob {
 };
 
 struct BatchArrays {
-  const double* axisF;
-  const float* axisF32;
+  const double* W;
+  const float* W32;
   const double* AF;
   const float* AF32;
   const double* coefF;
@@ -56,9 +64,14 @@ struct BatchArrays {
   double* Fbar;
 };
 
+// Fine work items of one tile width, grouped by column class: the items of class c
+// (KC = 4(c+1)) are d_items[begin[c] .. begin[c+1]).
+constexpr int kBatchClasses = (2 * PE_BATCH_MAX_TERMS + 3) / 4;
 struct FineItems {
   FineItem* d_items = nullptr;
   int n = 0;
+  int begin[kBatchClasses + 1] = {};
+  size_t smem[kBatchClasses] = {};
 };
 
 struct pe_batch {
@@ -84,7 +97,6 @@ struct pe_batch {
   int64_t mu_total = 0;
   int64_t* d_tt_prefix = nullptr;
   int64_t tt_total = 0;
-  size_t fine_smem = 0;
   // arenas
   double *muM = nullptr, *ratio = nullptr;
   double *coefF = nullptr, *coefG = nullptr;
@@ -94,6 +106,10 @@ struct pe_batch {
   float* axisF32 = nullptr;
   double *AF = nullptr, *AG = nullptr;
   float* AF32 = nullptr;
+  double *W = nullptr, *Z = nullptr;
+  float* AG32 = nullptr;
+  float* W32 = nullptr;
+  short* d_cols = nullptr;
   double* partials = nullptr;
   // per-problem iteration state
   int *active = nullptr, *kcount = nullptr;
@@ -119,12 +135,13 @@ struct pe_batch {
 // pe_batch.cu
 pe_status batch_set_attributes(pe_batch* b);
 pe_status batch_launch_axis_tables(pe_batch* b);
+pe_status batch_launch_coef_tables(pe_batch* b);
 pe_status batch_launch_prepare(pe_batch* b);
 pe_status batch_enqueue_iteration(pe_batch* b, cudaStream_t st, double tol);
 pe_status batch_time_fine(pe_batch* b, int threads, int ctas, float* ms);
-// pe_batch_fine_*.cu
-pe_status batch_launch_fine_mixed(const BProb* probs, const FineItem* items, int n_items, const int* active,
+int batch_fine_launches(const pe_batch* b);  // fine kernels per iteration (one per column class)
+// pe_batch_fine_*.cu (KC: the column class of the launch)
+pe_status batch_launch_fine_mixed(int KC, const BProb* probs, const FineItem* items, int n_items, const int* active,
                                   int* counter, BatchArrays A, int grid, int threads, size_t smem, cudaStream_t st);
-pe_status batch_launch_fine_f64(const BProb* probs, const FineItem* items, int n_items, const int* active,
+pe_status batch_launch_fine_f64(int KC, const BProb* probs, const FineItem* items, int n_items, const int* active,
                                 int* counter, BatchArrays A, int grid, int threads, size_t smem, cudaStream_t st);
-pe_status batch_fine_set_smem(int precision, size_t smem);

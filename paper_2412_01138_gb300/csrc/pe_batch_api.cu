@@ -40,7 +40,8 @@ void free_batch(pe_batch* b) {
   void* ptrs[] = {b->d_probs, b->d_terms, b->d_mode_items, b->fine128.d_items, b->fine256.d_items,
                   b->d_factor_jobs, b->d_mu_prefix, b->d_tt_prefix, b->muM, b->ratio, b->coefF, b->coefG,
                   b->coefF32, b->U, b->Gold, b->Fbar, b->gG, b->axisF, b->axisU0, b->axisF32, b->AF, b->AG,
-                  b->AF32, b->partials, b->active, b->kcount, b->resid, b->counter, b->dflags};
+                  b->AF32, b->partials, b->active, b->kcount, b->resid, b->counter, b->dflags,
+                  b->W, b->W32, b->Z, b->d_cols, b->AG32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_flags) cudaFreeHost(b->h_flags);
@@ -57,17 +58,27 @@ uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
   return h;
 }
 
+// Fine work items (problem, slice, tile of threads*MPT modes), grouped by column class,
+// and the dynamic shared memory each class needs (its widest staged chunk of time factors).
 pe_status build_fine_items(pe_batch* b, int threads, FineItems* out) {
   std::vector<FineItem> items;
-  for (int p = 0; p < b->P; ++p) {
-    const BProb& B = b->probs[p];
-    const int RC = (B.R + 3) / 4 * 4;
-    const int mpt = b->precision == PE_MIXED ? (RC <= 16 ? 4 : 2) : 1;
-    const int64_t tile = (int64_t)threads * mpt;
-    for (int n = 0; n < B.N; ++n)
-      for (int64_t J0 = 0; J0 < B.g.ndof; J0 += tile) items.push_back(FineItem{p, n, J0});
+  const size_t elem = b->precision == PE_MIXED ? sizeof(float) : sizeof(double);
+  for (int c = 0; c < kBatchClasses; ++c) {
+    out->begin[c] = (int)std::min<size_t>(items.size(), INT32_MAX);
+    out->smem[c] = 0;
+    for (int p = 0; p < b->P; ++p) {
+      const BProb& B = b->probs[p];
+      const int KC = (B.K + 3) / 4 * 4;
+      if (KC != 4 * (c + 1)) continue;
+      out->smem[c] = std::max(out->smem[c], elem * (size_t)B.mchunk * KC);
+      const int mpt = b->precision == PE_MIXED ? batch_mixed_mpt(KC) : 1;
+      const int64_t tile = (int64_t)threads * mpt;
+      for (int n = 0; n < B.N; ++n)
+        for (int64_t J0 = 0; J0 < B.g.ndof; J0 += tile) items.push_back(FineItem{p, n, J0});
+    }
   }
   if (items.size() > (size_t)INT32_MAX) return pe_fail(PE_EINVAL, "batch: too many work items");
+  out->begin[kBatchClasses] = (int)items.size();
   out->n = (int)items.size();
   return upload(&out->d_items, items, b->stream);
 }
@@ -109,7 +120,9 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
 
   // ---- validate and lay out every problem --------------------------------
   int64_t oU = 0, oS = 0, oCF = 0, oCG = 0, oAx = 0, oAxU = 0, oAF = 0, oAG = 0, oMu = 0, oItems = 0;
+  int64_t oW = 0, oZ = 0;
   std::vector<int64_t> mu_prefix, tt_prefix;
+  std::vector<short> cols;
   int64_t tt = 0;
   uint64_t sig = 0xcbf29ce484222325ull;
   b->probs.resize(n_problems);
@@ -186,25 +199,32 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
       B.Ru = q.u0.n_terms;
     }
     if (B.Ru > PE_MAX_TERMS) { st = pe_fail(PE_EINVAL, tag + "too many u0 terms"); break; }
-    // tile bodies run with R rounded up to a multiple of 4 (zero-padded staging rows)
-    const int RC = (B.R + 3) / 4 * 4;
+    // stage-contracted columns of the fine step: one per exponential term, two per sinusoid
+    B.oCol = (int64_t)cols.size();
+    for (int r = 0; r < B.R; ++r) {
+      cols.push_back((short)(r << 1));
+      if (b->terms[B.tf + r].tkind == PE_T_SIN) cols.push_back((short)((r << 1) | 1));
+    }
+    B.K = (int)((int64_t)cols.size() - B.oCol);
+    // tile bodies run with K rounded up to a multiple of 4 (zero-padded staging rows)
+    const int KC = (B.K + 3) / 4 * 4;
     const size_t elem = b->precision == PE_MIXED ? sizeof(float) : sizeof(double);
-    B.mchunk = pick_mchunk(B.M, B.q * RC, elem);
-    const size_t smem = elem * (size_t)B.mchunk * B.q * RC;
-    b->fine_smem = std::max(b->fine_smem, smem);
+    B.mchunk = pick_mchunk(B.M, KC, elem);
     B.oU = oU; oU += (int64_t)(B.N + 1) * ndof;
     B.oS = oS; oS += (int64_t)B.N * ndof;
     B.oCF = oCF; oCF += (int64_t)(B.q + 2) * ndof;
     B.oCG = oCG; oCG += (int64_t)(B.p + 1) * ndof;
     B.oAx = oAx; oAx += (int64_t)B.R * nsum;
     B.oAxU = oAxU; oAxU += (int64_t)B.Ru * nsum;
-    B.oAF = oAF; oAF += (int64_t)B.N * B.M * B.q * B.R;
+    B.oAF = oAF; oAF += (int64_t)B.N * B.M * B.K;
+    B.oW = oW; oW += (int64_t)B.K * ndof;
+    B.oZ = oZ; oZ += (int64_t)B.q * B.K;
     B.oAG = oAG; oAG += (int64_t)B.N * B.p * B.R;
     B.oMu = oMu;
     mu_prefix.push_back(oMu);
     oMu += nsum;
     tt_prefix.push_back(tt);
-    tt += (int64_t)B.N * B.M * B.q * B.R + (int64_t)B.N * B.p * B.R;
+    tt += (int64_t)B.N * B.M * B.K + (int64_t)B.N * B.p * B.R + (int64_t)B.q * B.K;
     B.oItems = oItems;
     B.nItems = (int)((ndof + 255) / 256);
     oItems += B.nItems;
@@ -236,11 +256,15 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
   if (st == PE_OK) st = balloc(&b->AF, oAF);
   if (st == PE_OK && mixed) st = balloc(&b->AF32, oAF);
   if (st == PE_OK) st = balloc(&b->AG, oAG);
+  if (st == PE_OK && mixed) st = balloc(&b->AG32, oAG);
+  if (st == PE_OK) st = balloc(&b->W, oW);
+  if (st == PE_OK && mixed) st = balloc(&b->W32, oW);
+  if (st == PE_OK) st = balloc(&b->Z, oZ);
   if (st == PE_OK) st = balloc(&b->partials, 2 * (size_t)oItems);
   if (st == PE_OK) st = balloc(&b->active, (size_t)b->P);
   if (st == PE_OK) st = balloc(&b->kcount, (size_t)b->P);
   if (st == PE_OK) st = balloc(&b->resid, (size_t)b->P);
-  if (st == PE_OK) st = balloc(&b->counter, 1);
+  if (st == PE_OK) st = balloc(&b->counter, (size_t)kBatchClasses);
   if (st == PE_OK) st = balloc(&b->dflags, 2);
   if (st == PE_OK && cudaMallocHost((void**)&b->h_flags, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -275,11 +299,13 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
     if (st == PE_OK) st = upload(&b->d_factor_jobs, jobs, b->stream);
     if (st == PE_OK) st = upload(&b->d_mu_prefix, mu_prefix, b->stream);
     if (st == PE_OK) st = upload(&b->d_tt_prefix, tt_prefix, b->stream);
+    if (st == PE_OK) st = upload(&b->d_cols, cols, b->stream);
     if (st == PE_OK) st = build_fine_items(b, 128, &b->fine128);
     if (st == PE_OK) st = build_fine_items(b, 256, &b->fine256);
   }
   if (st == PE_OK) st = batch_set_attributes(b);
   if (st == PE_OK) st = batch_launch_axis_tables(b);
+  if (st == PE_OK) st = batch_launch_coef_tables(b);
   if (st == PE_OK) {
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_setup_batch");
@@ -426,7 +452,7 @@ extern "C" pe_status pe_batch_solve(pe_batch* b, double tol, pe_batch_result* re
     PE_CUDA_TRY(cudaGraphLaunch(b->graph_exec, b->stream));
     PE_CUDA_TRY(cudaStreamSynchronize(b->stream));
     ++replays;
-    b->launches += 3;
+    b->launches += batch_fine_launches(b) + 2;  // graph: fine kernels, correction, reduction
     if (b->h_flags[1]) {
       b->have_problem = false;
       return pe_fail(PE_ENONFINITE, "batch: a problem's Parareal residual is not finite");

@@ -4,12 +4,14 @@
 // S_a[j][k] = sqrt(2/(n_a+1)) sin(pi (j+1)(k+1)/(n_a+1)):
 //   last axis   : out[o][j]    = sum_k X[o][k] S[k][j]     (one GEMM, outer x n times n x n)
 //   other axes  : out[o][j][i] = sum_k S[j][k] X[o][k][i]  (batched over o)
-// Two kernels serve every axis pass:
-//  * n + 1 = 2^k (n <= 1023): a radix-2 FFT in shared memory.  Two real pencils
-//    x, y are packed as z = x + i y; the odd extension of z over 2(n+1) points is
-//    transformed by an in-place decimation-in-time FFT (bit-reversed load), and
-//    DST(x)_k = -Im V_k / 2, DST(y)_k = Re V_k / 2.  About 5 log2(2n+2) flops per
-//    element instead of the 2n of the matrix form.
+// Two kernel families serve every axis pass:
+//  * n + 1 = 2^k (n <= 1023): an FFT.  Two real pencils x, y are packed as
+//    z = x + i y; the odd extension of z over 2(n+1) points is Fourier
+//    transformed, and DST(x)_k = -Im V_k / 2, DST(y)_k = Re V_k / 2.  About
+//    5 log2(2n+2) flops per element instead of the 2n of the matrix form.  For
+//    n + 1 >= 16 one warp owns a pencil pair (self-sorting radix-16 passes,
+//    dst_fft_warp_kernel); shorter pencils (and float64 at n + 1 = 1024) use a
+//    block-wide radix-2 kernel (dst_fft_kernel).
 //  * any other n: a shared-memory tiled, strided, batched GEMM with the matrix S_a
 //    (tile shape chosen so that the grid covers the GPU).
 #include <algorithm>
@@ -276,12 +278,312 @@ const Cplx<T>* twiddles(int logL, cudaStream_t st) {
   return table[dev] + (L / 2 - 1);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-pencil-pair FFT form (n + 1 = 2^k, 16 <= n + 1 <= 1024): the same odd
+// extension of z = x + i y over L = 2(n+1) points, transformed by a self-sorting
+// (Stockham) FFT in radix-16 passes (a radix-2/4/8 pass finishes odd log2 L).
+// One warp owns one pencil pair's L values in shared memory, so the passes need
+// only __syncwarp; each lane holds L/32 values in registers between a pass's
+// loads and stores.  A CTA stages WARPS pencil pairs: the global loads and
+// stores are CTA-wide and coalesced (contiguous for the last axis, rows of
+// 2*WARPS consecutive pencils for the others).  Pass twiddles are tabulated per
+// CTA as [r][k] (k fastest) so that lanes read consecutive entries.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
+  return Cplx<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// padded shared-memory index: one gap every 16 values keeps the strided pass
+// stores free of bank conflicts
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
+constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+__host__ __device__ constexpr int brevc(int i, int bits) {  // bit reversal of i < 16 over `bits` bits
+  return (((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)) >> (4 - bits);
+}
+
+// e^{-2 pi i t/16}, t = 0..7 (cos and sin of multiples of pi/8)
+__device__ __forceinline__ constexpr double w16_re(int t) {
+  return t == 0 ? 1.0 : t == 1 ? 0.92387953251128674 : t == 2 ? 0.70710678118654752 : t == 3 ? 0.38268343236508978
+       : t == 4 ? 0.0 : t == 5 ? -0.38268343236508978 : t == 6 ? -0.70710678118654752 : -0.92387953251128674;
+}
+__device__ __forceinline__ constexpr double w16_im(int t) {
+  return t == 0 ? 0.0 : t == 1 ? -0.38268343236508978 : t == 2 ? -0.70710678118654752 : t == 3 ? -0.92387953251128674
+       : t == 4 ? -1.0 : t == 5 ? -0.92387953251128674 : t == 6 ? -0.70710678118654752 : -0.38268343236508978;
+}
+
+// In-register forward DFT of R = 2, 4, 8 or 16 values: radix-2 decimation in frequency,
+// natural-order input, output in bit-reversed order (X[r] = v[brevc(r, log2 R)]).
+template <typename T, int R>
+__device__ __forceinline__ void dft_regs(Cplx<T> (&v)[R]) {
+#pragma unroll
+  for (int len = R; len >= 2; len >>= 1) {
+#pragma unroll
+    for (int s = 0; s < R; s += len) {
+#pragma unroll
+      for (int k = 0; k < len / 2; ++k) {
+        const int t = k * (16 / len);
+        const Cplx<T> a = v[s + k], b = v[s + k + len / 2];
+        v[s + k] = Cplx<T>{a.re + b.re, a.im + b.im};
+        const Cplx<T> d{a.re - b.re, a.im - b.im};
+        if (t == 0) v[s + k + len / 2] = d;
+        else if (t == 4) v[s + k + len / 2] = Cplx<T>{d.im, -d.re};  // times -i
+        else v[s + k + len / 2] = cmul(d, Cplx<T>{(T)w16_re(t), (T)w16_im(t)});
+      }
+    }
+  }
+}
+
+// One Stockham pass of radix R after NS points have been combined; tw = this pass's
+// table [r][k] = e^{-2 pi i k r / (NS R)}, k < NS (unused when NS == 1).
+template <typename T, int LOGL, int R, int NS>
+__device__ __forceinline__ void stockham_pass(Cplx<T>* a, const Cplx<T>* tw, int lane) {
+  constexpr int L = 1 << LOGL, NG = L / R, G = (NG + 31) / 32;
+  Cplx<T> v[G][R];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = lane + 32 * g;
+    if (NG % 32 == 0 || j < NG) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[g][r] = a[fpad(j + r * NG)];
+      if (NS > 1) {
+        const int k = j & (NS - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[g][r] = cmul(v[g][r], tw[r * NS + k]);
+      }
+      dft_regs<T, R>(v[g]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = lane + 32 * g;
+    if (NG % 32 == 0 || j < NG) {
+      const int k = j & (NS - 1);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[fpad(base + r * NS)] = v[g][brevc(r, ilog2c(R))];
+    }
+  }
+  __syncwarp();
+}
+
+// All passes: radix 16 while at least 4 bits remain, then one pass of the rest.
+template <typename T, int LOGL, int LEFT, int NS>
+struct StockhamPasses {
+  static __device__ __forceinline__ void run(Cplx<T>* a, const Cplx<T>* tw, int lane) {
+    constexpr int RB = LEFT >= 4 ? 4 : LEFT;
+    constexpr int R = 1 << RB;
+    stockham_pass<T, LOGL, R, NS>(a, tw, lane);
+    StockhamPasses<T, LOGL, LEFT - RB, NS * R>::run(a, tw + (NS > 1 ? NS * R : 0), lane);
+  }
+};
+template <typename T, int LOGL, int NS>
+struct StockhamPasses<T, LOGL, 0, NS> {
+  static __device__ __forceinline__ void run(Cplx<T>*, const Cplx<T>*, int) {}
+};
+
+// entries of the pass twiddle tables of a length-2^LOGL transform
+constexpr int pass_tw_entries(int left, int ns) {
+  return left == 0 ? 0 : (ns > 1 ? ns * (1 << (left >= 4 ? 4 : left)) : 0) +
+                             pass_tw_entries(left - (left >= 4 ? 4 : left), ns * (1 << (left >= 4 ? 4 : left)));
+}
+
+// blockDim.x = 32 * warps (warps = 1, 2, 4 or 8): P = 2 * warps pencils per block of work.
+template <typename T, int LOGL>
+__global__ void __launch_bounds__(256) dst_fft_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
+                                                           int64_t inner, int64_t npencils, T scale,
+                                                           const Cplx<T>* __restrict__ twg) {
+  constexpr int L = 1 << LOGL, N = L / 2, PADL = L + L / 16;
+  constexpr int NTW = pass_tw_entries(LOGL, 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int B = blockDim.x, WARPS = B >> 5, P = 2 * WARPS, logP = __ffs(P) - 1;
+  Cplx<T>* bufs = reinterpret_cast<Cplx<T>*>(smem_raw);
+  Cplx<T>* ptw = bufs + (size_t)WARPS * PADL;
+  int64_t* off = reinterpret_cast<int64_t*>(ptw + NTW);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // pass twiddle tables from the global table e^{-2 pi i t / L}, t < L/2
+  {
+    int e0 = 0;
+    int ns = 1, left = LOGL;
+    while (left > 0) {
+      const int rb = left >= 4 ? 4 : left, R = 1 << rb;
+      if (ns > 1) {
+        const int stride = L / (ns * R);
+        for (int e = tid; e < ns * R; e += B) {
+          const int r = e / ns, k = e - r * ns;
+          const int t = k * r * stride;
+          const Cplx<T> w = t < N ? twg[t] : Cplx<T>{-twg[t - N].re, -twg[t - N].im};
+          ptw[e0 + e] = w;
+        }
+        e0 += ns * R;
+      }
+      ns *= R;
+      left -= rb;
+    }
+  }
+  if (inner == 1) {
+    // contiguous pencils (last axis): each warp loads, transforms and stores its own pencil
+    // pairs (rows of n consecutive values), with no block-wide barrier after the tables
+    __syncthreads();
+    constexpr int JL = (N + 31) / 32;  // values per lane and pencil (n <= N - 1)
+    Cplx<T>* a = bufs + (size_t)warp * PADL;
+    const int64_t npairs = (npencils + 1) / 2;
+    for (int64_t pr = (int64_t)blockIdx.x * WARPS + warp; pr < npairs; pr += (int64_t)gridDim.x * WARPS) {
+      const int64_t pa = 2 * pr, pb = pa + 1;
+      const bool has_b = pb < npencils;
+      const T* xa = in + pa * n;
+      const T* xb = in + pb * n;
+      T ra[JL], rb[JL];
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int j = lane + 32 * t;
+        ra[t] = j < n ? xa[j] : T(0);
+        rb[t] = (j < n && has_b) ? xb[j] : T(0);
+      }
+      if (lane == 0) {
+        a[fpad(0)] = Cplx<T>{T(0), T(0)};
+        a[fpad(N)] = Cplx<T>{T(0), T(0)};
+      }
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int j = lane + 32 * t;
+        if (j < n) {
+          a[fpad(j + 1)] = Cplx<T>{ra[t], rb[t]};
+          a[fpad(L - 1 - j)] = Cplx<T>{-ra[t], -rb[t]};
+        }
+      }
+      __syncwarp();
+      StockhamPasses<T, LOGL, LOGL, 1>::run(a, ptw, lane);
+      T* ya = out + pa * n;
+      T* yb = out + pb * n;
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int k = lane + 32 * t;
+        if (k < n) {
+          const Cplx<T> Z = a[fpad(k + 1)];
+          ya[k] = -Z.im * scale;
+          if (has_b) yb[k] = Z.re * scale;
+        }
+      }
+      __syncwarp();
+    }
+    return;
+  }
+  // strided pencils: the block stages P consecutive pencils so that each row j is one
+  // contiguous run of P values
+  const int64_t nblk = (npencils + P - 1) / P;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t p0 = blk * P;
+    if (tid < P) {
+      const int64_t p = p0 + tid;
+      off[tid] = p < npencils ? (p / inner) * (int64_t)n * inner + (p % inner) : -1;
+    }
+    __syncthreads();
+    // the fixed points of the odd extension
+    if (tid < 2 * WARPS) {
+      Cplx<T>* a = bufs + (size_t)(tid >> 1) * PADL;
+      a[fpad((tid & 1) ? N : 0)] = Cplx<T>{T(0), T(0)};
+    }
+    // load: z_j = x_j + i y_j at j = 1..n and -z_j at L - j.  U loads per thread are issued
+    // back to back before any of them is placed, so one DRAM latency covers U values.
+    const int total = P * n;
+    constexpr int U = sizeof(T) == 4 ? 16 : 8;
+    for (int e0 = 0; e0 < total; e0 += U * B) {
+      T r[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * B + tid;
+        r[u] = T(0);
+        if (e < total) {
+          const int64_t o = off[e & (P - 1)];
+          if (o >= 0) r[u] = in[o + (int64_t)(e >> logP) * inner];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * B + tid;
+        if (e < total) {
+          const int pl = e & (P - 1), j = e >> logP;
+          Cplx<T>* a = bufs + (size_t)(pl >> 1) * PADL;
+          reinterpret_cast<T*>(a + fpad(j + 1))[pl & 1] = r[u];
+          reinterpret_cast<T*>(a + fpad(L - 1 - j))[pl & 1] = -r[u];
+        }
+      }
+    }
+    __syncthreads();
+    StockhamPasses<T, LOGL, LOGL, 1>::run(bufs + (size_t)warp * PADL, ptw, lane);
+    __syncthreads();
+    // store: DST(x)_k = -Im Z_k / 2, DST(y)_k = Re Z_k / 2 (times sqrt(2/(n+1)))
+    for (int e = tid; e < total; e += B) {
+      const int pl = e & (P - 1), k = e >> logP;
+      const Cplx<T> Z = bufs[(size_t)(pl >> 1) * PADL + fpad(k + 1)];
+      const T val = (pl & 1) ? Z.re * scale : -Z.im * scale;
+      const int64_t o = off[pl];
+      if (o >= 0) out[o + (int64_t)k * inner] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Warps per CTA: as many (up to 8, float64 up to 4) as still give >= 2 CTAs per SM.
+template <typename T, int LOGL>
+pe_status fft_warp_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, T scale, const Cplx<T>* tw,
+                          cudaStream_t st) {
+  constexpr int L = 1 << LOGL, PADL = L + L / 16;
+  constexpr int NTW = pass_tw_entries(LOGL, 1);
+  int dev = 0, sms = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int warps = sizeof(T) == 4 ? 8 : 4;
+  while (warps > 1 && (npencils + 2 * warps - 1) / (2 * warps) < 2 * (int64_t)sms) warps >>= 1;
+  const int P = 2 * warps;
+  const size_t smem = sizeof(Cplx<T>) * ((size_t)warps * PADL + NTW) + sizeof(int64_t) * P;
+  auto kern = dst_fft_warp_kernel<T, LOGL>;
+  if (smem > 48 * 1024) PE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
+  const int64_t nblk = (npencils + P - 1) / P;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * std::max(per_sm, 1)));
+  kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, tw);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+template <typename T>
+pe_status fft_warp_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, const Cplx<T>* tw,
+                        cudaStream_t st, bool* done) {
+  const int64_t np = outer * inner;
+  const T scale = (T)(0.5 * sqrt(2.0 / (double)(n + 1)));
+  *done = true;
+  switch (logL) {
+    case 5: return fft_warp_launch<T, 5>(in, out, n, inner, np, scale, tw, st);
+    case 6: return fft_warp_launch<T, 6>(in, out, n, inner, np, scale, tw, st);
+    case 7: return fft_warp_launch<T, 7>(in, out, n, inner, np, scale, tw, st);
+    case 8: return fft_warp_launch<T, 8>(in, out, n, inner, np, scale, tw, st);
+    case 9: return fft_warp_launch<T, 9>(in, out, n, inner, np, scale, tw, st);
+    case 10: return fft_warp_launch<T, 10>(in, out, n, inner, np, scale, tw, st);
+    case 11:
+      if constexpr (sizeof(T) == 4) return fft_warp_launch<T, 11>(in, out, n, inner, np, scale, tw, st);
+      break;
+    default:
+      break;
+  }
+  *done = false;
+  return PE_OK;
+}
+
 template <typename T>
 pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, cudaStream_t st) {
   const int L = 1 << logL;
   const int64_t npencils = outer * inner;
   const Cplx<T>* tw = twiddles<T>(logL, st);
   if (!tw) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  bool done = false;
+  PE_TRY(fft_warp_axis<T>(in, out, outer, n, inner, logL, tw, st, &done));
+  if (done) return PE_OK;
+  // short transforms (n + 1 < 16) and float64 at n + 1 = 1024: the block-wide radix-2 kernel;
   // pencil pairs per CTA: as many as keep >= 2 CTAs per SM, bounded by shared memory
   int max_pairs = (int)((48 * 1024) / ((size_t)L * sizeof(Cplx<T>)));
   max_pairs = max_pairs < 1 ? 1 : (max_pairs > 16 ? 16 : max_pairs);

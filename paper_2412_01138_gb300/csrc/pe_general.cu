@@ -9,6 +9,8 @@
 // Lambda_M^{-1} into the stage weights of the fine and coarse recurrences.  The
 // fine propagator then reads ghat(t) from HBM instead of forming it from
 // per-axis factors: the step is memory-bound, and the transform dominates.
+// In the mixed form the fine sweep's loads, assembly and transforms run in
+// float32 (the coarse forcing, computed once per problem, stays float64).
 //
 // Slices are processed in chunks so that the stage-time loads of a chunk fit a
 // fixed device budget.
@@ -44,9 +46,11 @@ __device__ inline double stage_time(const StageGen& G, int idx) {
   return tl + G.c[i] * G.dt;
 }
 
-// L[st][R*off[a] + r*n_a + k] = int g_{r,a}(x, t_st) phi_{k+1}(x) dx  (grid: nodes, R*d, stages)
+// L[st][R*off[a] + r*n_a + k] = int g_{r,a}(x, t_st) phi_{k+1}(x) dx  (grid: nodes, R*d, stages);
+// TL = float evaluates the factors in float32 (mixed precision), double in float64.
+template <typename TL>
 __global__ void gen_loads_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2, double h0, double h1,
-                                 double h2, Gauss Q, StageGen SG, int nsum, double* __restrict__ L) {
+                                 double h2, Gauss Q, StageGen SG, int nsum, TL* __restrict__ L) {
   const int st = blockIdx.z;
   const int ra = blockIdx.y;
   const int r = ra / g.d, a = ra % g.d;
@@ -56,34 +60,49 @@ __global__ void gen_loads_kernel(TermsDev T, Geom g, double lo0, double lo1, dou
   const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
   const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
   const pe_term& tm = T.t[r];
-  double left = 0.0, right = 0.0;
+  TL left = TL(0), right = TL(0);
   for (int qi = 0; qi < Q.npts; ++qi) {
-    const double xl = lo + ((double)k + Q.s[qi]) * h;
-    const double xr = lo + ((double)(k + 1) + Q.s[qi]) * h;
-    left += Q.w[qi] * eval_space(tm.skind[a], tm.sp[a], xl, t) * Q.s[qi];
-    right += Q.w[qi] * eval_space(tm.skind[a], tm.sp[a], xr, t) * (1.0 - Q.s[qi]);
+    const TL xl = (TL)(lo + ((double)k + Q.s[qi]) * h);
+    const TL xr = (TL)(lo + ((double)(k + 1) + Q.s[qi]) * h);
+    TL gl, gr;
+    if constexpr (sizeof(TL) == 4) {
+      gl = eval_space_f(tm.skind[a], tm.sp[a], xl, t);
+      gr = eval_space_f(tm.skind[a], tm.sp[a], xr, t);
+    } else {
+      gl = eval_space(tm.skind[a], tm.sp[a], xl, t);
+      gr = eval_space(tm.skind[a], tm.sp[a], xr, t);
+    }
+    left += (TL)Q.w[qi] * gl * (TL)Q.s[qi];
+    right += (TL)Q.w[qi] * gr * (TL)(1.0 - Q.s[qi]);
   }
-  L[(int64_t)st * T.n * nsum + (int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = h * left + h * right;
+  L[(int64_t)st * T.n * nsum + (int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = (TL)h * left + (TL)h * right;
 }
 
-// F[st][J] = sum_r amp_r time_r(t_st) prod_a L[st][...]  (nodal consistent load)
+// F[st][J] = sum_r amp_r time_r(t_st) prod_a L[st][...]  (nodal consistent load).  The
+// time weights amp_r time_r(t_st) are the same for every node of a stage: one thread per
+// term evaluates them into shared memory.
 template <typename Tout>
-__global__ void gen_assemble_kernel(TermsDev T, Geom g, StageGen SG, int nsum, const double* __restrict__ L,
+__global__ void gen_assemble_kernel(TermsDev T, Geom g, StageGen SG, int nsum, const Tout* __restrict__ L,
                                     Tout* __restrict__ F) {
+  __shared__ Tout w[PE_MAX_TERMS];
   const int st = blockIdx.y;
+  if (threadIdx.x < T.n) {
+    const pe_term& tm = T.t[threadIdx.x];
+    w[threadIdx.x] = (Tout)(tm.amp * eval_time(tm, stage_time(SG, st)));
+  }
+  __syncthreads();
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   int j[PE_MAX_D];
   unflatten(g, J, j);
-  const double t = stage_time(SG, st);
-  const double* Ls = L + (int64_t)st * T.n * nsum;
-  double acc = 0.0;
+  const Tout* Ls = L + (int64_t)st * T.n * nsum;
+  Tout acc = Tout(0);
   for (int r = 0; r < T.n; ++r) {
-    double P = Ls[(int64_t)T.n * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+    Tout P = Ls[(int64_t)T.n * g.off[0] + (int64_t)r * g.n[0] + j[0]];
     for (int a = 1; a < g.d; ++a) P *= Ls[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + j[a]];
-    acc += T.t[r].amp * eval_time(T.t[r], t) * P;
+    acc += w[r] * P;
   }
-  F[(int64_t)st * g.ndof + J] = (Tout)acc;
+  F[(int64_t)st * g.ndof + J] = acc;
 }
 
 // fine propagator from the stored transformed loads: Gh[(n - n0) M q + m q + i][J] = (V^T F)_J
@@ -188,12 +207,13 @@ pe_status stage_transforms(pe_ctx* c, const StageGen& SG, int count, T* out, T* 
   int nmax = 1;
   for (int a = 0; a < c->g.d; ++a) nmax = std::max(nmax, c->g.n[a]);
   dim3 gl((nmax + 127) / 128, c->R * c->g.d, count);
-  gen_loads_kernel<<<gl, 128, 0, c->stream>>>(TD, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2], Q,
-                                              SG, c->nsum, c->gen_L);
+  T* L = reinterpret_cast<T*>(c->gen_L);
+  gen_loads_kernel<T><<<gl, 128, 0, c->stream>>>(TD, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2], Q,
+                                                 SG, c->nsum, L);
   dim3 ga((unsigned)((c->g.ndof + 255) / 256), count);
   // the assembled loads go to tmp or out so that the last DST pass lands in out
   T* F = (c->g.d % 2 == 1) ? tmp : out;
-  gen_assemble_kernel<T><<<ga, 256, 0, c->stream>>>(TD, c->g, SG, c->nsum, c->gen_L, F);
+  gen_assemble_kernel<T><<<ga, 256, 0, c->stream>>>(TD, c->g, SG, c->nsum, L, F);
   c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   const T* src = F;
