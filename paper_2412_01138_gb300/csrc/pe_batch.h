@@ -45,7 +45,7 @@ struct ModeItem {
 
 struct FineItem {
   int p;
-  int n;
+  int unused;   // padding (an item covers every slice of its problem)
   int64_t J0;
 };
 

@@ -58,23 +58,27 @@ uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
   return h;
 }
 
-// Fine work items (problem, slice, tile of threads*MPT modes), grouped by column class,
-// and the dynamic shared memory each class needs (its widest staged chunk of time factors).
+// Fine work items (problem, tile of threads*MPT modes; the item runs every slice of its
+// problem), grouped by column class, longest (most slices) first within a class, and the
+// dynamic shared memory each class needs (its widest staged chunk of time factors).
 pe_status build_fine_items(pe_batch* b, int threads, FineItems* out) {
   std::vector<FineItem> items;
   const size_t elem = b->precision == PE_MIXED ? sizeof(float) : sizeof(double);
+  std::vector<int> order((size_t)b->P);
+  for (int p = 0; p < b->P; ++p) order[(size_t)p] = p;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return (int64_t)b->probs[x].N * b->probs[x].M > (int64_t)b->probs[y].N * b->probs[y].M; });
   for (int c = 0; c < kBatchClasses; ++c) {
     out->begin[c] = (int)std::min<size_t>(items.size(), INT32_MAX);
     out->smem[c] = 0;
-    for (int p = 0; p < b->P; ++p) {
+    for (int p : order) {
       const BProb& B = b->probs[p];
       const int KC = (B.K + 3) / 4 * 4;
       if (KC != 4 * (c + 1)) continue;
       out->smem[c] = std::max(out->smem[c], elem * (size_t)B.mchunk * KC);
       const int mpt = b->precision == PE_MIXED ? batch_mixed_mpt(KC) : 1;
       const int64_t tile = (int64_t)threads * mpt;
-      for (int n = 0; n < B.N; ++n)
-        for (int64_t J0 = 0; J0 < B.g.ndof; J0 += tile) items.push_back(FineItem{p, n, J0});
+      for (int64_t J0 = 0; J0 < B.g.ndof; J0 += tile) items.push_back(FineItem{p, 0, J0});
     }
   }
   if (items.size() > (size_t)INT32_MAX) return pe_fail(PE_EINVAL, "batch: too many work items");

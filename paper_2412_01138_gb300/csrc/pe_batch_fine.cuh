@@ -1,131 +1,127 @@
 // Persistent fine-propagator kernels of the batched solver: CTAs pull
-// (problem, slice, mode-tile) items from an atomic counter and run the tile
-// body specialised for the column class KC of the launch.  Each tile is Eq. (1-7)
-// applied M times in the stage-contracted form of the single-problem solver:
+// (problem, mode-tile) items from an atomic counter and run, for every slice n
+// of the problem in turn, Eq. (1-7) applied M times in the stage-contracted form
+// of the single-problem solver:
 //   c <- E_F c + sum_k Y_k(T_n + m dt) W_{k,J},
 // with the K per-mode stage weights W (one column per exponential source term,
-// two per sinusoid) tabulated at preparation.  The slice's Y rows are staged in
-// shared memory, zero-padded to KC = roundup(K, 4) (warp-wide broadcasts); W
-// and E_F stay in registers.
+// two per sinusoid) tabulated at preparation.  W and E_F do not depend on the
+// slice, so an item loads them into registers once and reuses them for all N
+// slices; each slice's Y rows are staged in shared memory, zero-padded to
+// KC = roundup(K, 4) (warp-wide broadcasts).  Items are ordered by decreasing
+// slice count so that the longest start first.
 // PE_MIXED: F^M(v) = E_F^M v (float64) + F^M(0) (float32, E_F as hi + lo).
 #pragma once
 #include "pe_batch.h"
 
 namespace {
 
-// Operands of one tile: one slice n of one problem, blockDim.x*MPT modes from `base`.
-struct BFineTile {
-  int64_t ndof;
-  int M, mchunk, q, K;
-  int64_t base;
-  const float* W32;       // stage weights of the problem [K][ndof]
-  const double* W;
-  const float* Yn32;      // substep time factors of slice n [M][K]
-  const double* Yn;
-  const float* coefF32;   // E_hi, E_lo (rows of ndof)
-  const double* coefF;    // E, dt*b_i, exp(-lam M dt) (rows of ndof)
-  const double* Un;
-  double* Fn;
-};
+// Stage rows m0 .. m0+mc-1 of one slice's time factors (row length K, padded to KC).
+template <typename T, int KC>
+__device__ __forceinline__ void b_stage_rows(const T* __restrict__ Yn, int K, int m0, int mc, T* sY) {
+  for (int t = threadIdx.x; t < mc * KC; t += blockDim.x) {
+    const int row = t / KC, c = t - row * KC;
+    sY[t] = c < K ? Yn[(int64_t)(m0 + row) * K + c] : T(0);
+  }
+}
 
 template <int KC, int MPT>
-__device__ __forceinline__ void b_fine_mixed_tile(const BFineTile& a, float* sY) {
-  const int M = a.M, B = blockDim.x, K = a.K;
-  const int64_t nd = a.ndof;
-  const int64_t base = a.base + threadIdx.x;
+__device__ __forceinline__ void b_fine_mixed_item(const BProb& P, int64_t J0, const BatchArrays& A, float* sY) {
+  const int M = P.M, K = P.K, Bd = blockDim.x;
+  const int64_t nd = P.g.ndof;
+  const int64_t base = J0 + threadIdx.x;
+  const float* W32 = A.W32 + P.oW;
+  const float* cf32 = A.coefF32 + P.oCF;
+  const double* EM = A.coefF + P.oCF + (int64_t)(P.q + 1) * nd;
   float W[MPT][KC];
-  float eh[MPT], el[MPT], w[MPT];
+  float eh[MPT], el[MPT];
+  double em[MPT];
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
-    const int64_t J = base + (int64_t)B * k;
-    eh[k] = 0.f;
-    el[k] = 0.f;
-    w[k] = 0.f;
+    const int64_t J = base + (int64_t)Bd * k;
+    const bool on = J < nd;
 #pragma unroll
-    for (int c = 0; c < KC; ++c) W[k][c] = (J < nd && c < K) ? a.W32[(int64_t)c * nd + J] : 0.f;
-    if (J < nd) {
-      eh[k] = a.coefF32[J];
-      el[k] = a.coefF32[nd + J];
-    }
+    for (int c = 0; c < KC; ++c) W[k][c] = (on && c < K) ? W32[(int64_t)c * nd + J] : 0.f;
+    eh[k] = on ? cf32[J] : 0.f;
+    el[k] = on ? cf32[nd + J] : 0.f;
+    em[k] = on ? EM[J] : 0.0;
   }
-  for (int m0 = 0; m0 < M; m0 += a.mchunk) {
-    const int mc = min(a.mchunk, M - m0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < mc * KC; t += B) {
-      const int row = t / KC, c = t - row * KC;
-      sY[t] = c < K ? a.Yn32[(int64_t)(m0 + row) * K + c] : 0.f;
+  for (int n = 0; n < P.N; ++n) {
+    const float* Yn = A.AF32 + P.oAF + (int64_t)n * M * K;
+    const double* Un = A.U + P.oU + (int64_t)n * nd;
+    double* Fn = A.Fbar + P.oS + (int64_t)n * nd;
+    double u[MPT];
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) {
+      const int64_t J = base + (int64_t)Bd * k;
+      u[k] = J < nd ? Un[J] : 0.0;  // consumed after the recurrence: its latency is hidden
     }
-    __syncthreads();
-    for (int m = 0; m < mc; ++m) {
-      const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
-      float acc[MPT];
+    float w[MPT];
 #pragma unroll
-      for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
+    for (int k = 0; k < MPT; ++k) w[k] = 0.f;
+    for (int m0 = 0; m0 < M; m0 += P.mchunk) {
+      const int mc = min(P.mchunk, M - m0);
+      __syncthreads();
+      b_stage_rows<float, KC>(Yn, K, m0, mc, sY);
+      __syncthreads();
+      for (int m = 0; m < mc; ++m) {
+        const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
+        float acc[MPT];
 #pragma unroll
-      for (int c4 = 0; c4 < KC / 4; ++c4) {
-        if (4 * c4 < K) {
-          const float4 v = y4[c4];
-          const float vv[4] = {v.x, v.y, v.z, v.w};
+        for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
+        for (int c4 = 0; c4 < KC / 4; ++c4) {
+          if (4 * c4 < K) {
+            const float4 v = y4[c4];
+            const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int k = 0; k < MPT; ++k) acc[k] = fmaf(vv[e], W[k][4 * c4 + e], acc[k]);
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+              for (int k = 0; k < MPT; ++k) acc[k] = fmaf(vv[e], W[k][4 * c4 + e], acc[k]);
+          }
         }
+#pragma unroll
+        for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
       }
-#pragma unroll
-      for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
     }
-  }
-  const double* EM = a.coefF + (int64_t)(a.q + 1) * nd;
 #pragma unroll
-  for (int k = 0; k < MPT; ++k) {
-    const int64_t J = base + (int64_t)B * k;
-    if (J < nd) a.Fn[J] = fma(EM[J], a.Un[J], (double)w[k]);
+    for (int k = 0; k < MPT; ++k) {
+      const int64_t J = base + (int64_t)Bd * k;
+      if (J < nd) Fn[J] = fma(em[k], u[k], (double)w[k]);
+    }
   }
 }
 
 template <int KC>
-__device__ __forceinline__ void b_fine_f64_tile(const BFineTile& a, double* sY) {
-  const int M = a.M, B = blockDim.x, K = a.K;
-  const int64_t nd = a.ndof;
-  const int64_t J = a.base + threadIdx.x;
-  const bool active = J < nd;
+__device__ __forceinline__ void b_fine_f64_item(const BProb& P, int64_t J0, const BatchArrays& A, double* sY) {
+  const int M = P.M, K = P.K;
+  const int64_t nd = P.g.ndof;
+  const int64_t J = J0 + threadIdx.x;
+  const bool on = J < nd;
+  const double* Wp = A.W + P.oW;
   double W[KC];
-  double E = 0.0, c = 0.0;
 #pragma unroll
-  for (int k = 0; k < KC; ++k) W[k] = (active && k < K) ? a.W[(int64_t)k * nd + J] : 0.0;
-  if (active) {
-    E = a.coefF[J];
-    c = a.Un[J];
-  }
-  for (int m0 = 0; m0 < M; m0 += a.mchunk) {
-    const int mc = min(a.mchunk, M - m0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < mc * KC; t += B) {
-      const int row = t / KC, col = t - row * KC;
-      sY[t] = col < K ? a.Yn[(int64_t)(m0 + row) * K + col] : 0.0;
-    }
-    __syncthreads();
-    if (active) {
-      for (int m = 0; m < mc; ++m) {
-        const double* yp = sY + m * KC;
-        double acc = 0.0;
+  for (int k = 0; k < KC; ++k) W[k] = (on && k < K) ? Wp[(int64_t)k * nd + J] : 0.0;
+  const double E = on ? A.coefF[P.oCF + J] : 0.0;
+  for (int n = 0; n < P.N; ++n) {
+    const double* Yn = A.AF + P.oAF + (int64_t)n * M * K;
+    double c = on ? A.U[P.oU + (int64_t)n * nd + J] : 0.0;
+    for (int m0 = 0; m0 < M; m0 += P.mchunk) {
+      const int mc = min(P.mchunk, M - m0);
+      __syncthreads();
+      b_stage_rows<double, KC>(Yn, K, m0, mc, sY);
+      __syncthreads();
+      if (on) {
+        for (int m = 0; m < mc; ++m) {
+          const double* yp = sY + m * KC;
+          double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < KC; ++k)
-          if (k < K) acc = fma(yp[k], W[k], acc);
-        c = fma(E, c, acc);
+          for (int k = 0; k < KC; ++k)
+            if (k < K) acc = fma(yp[k], W[k], acc);
+          c = fma(E, c, acc);
+        }
       }
     }
-  }
-  if (active) a.Fn[J] = c;
-}
-
-template <int PREC, int KC>
-__device__ __forceinline__ void run_tile(const BFineTile& t, double* smem) {
-  if constexpr (PREC == PE_MIXED) {
-    b_fine_mixed_tile<KC, batch_mixed_mpt(KC)>(t, reinterpret_cast<float*>(smem));
-  } else {
-    b_fine_f64_tile<KC>(t, smem);
+    if (on) A.Fbar[P.oS + (int64_t)n * nd + J] = c;
   }
 }
 
@@ -145,27 +141,13 @@ __global__ void __launch_bounds__(256) b_fine_kernel(const BProb* __restrict__ p
     __syncthreads();
     if (it >= n_items) break;
     const FineItem f = items[it];
-    const BProb& B = probs[f.p];
     if (!active[f.p]) continue;  // uniform over the CTA
-    BFineTile t{};
-    t.ndof = B.g.ndof;
-    t.M = B.M;
-    t.q = B.q;
-    t.K = B.K;
-    t.base = f.J0;
-    t.mchunk = B.mchunk;
-    const int64_t slice_y = (int64_t)B.M * B.K;
-    t.W = A.W + B.oW;
-    t.Yn = A.AF + B.oAF + (int64_t)f.n * slice_y;
-    t.coefF = A.coefF + B.oCF;
-    if (PREC == PE_MIXED) {
-      t.W32 = A.W32 + B.oW;
-      t.Yn32 = A.AF32 + B.oAF + (int64_t)f.n * slice_y;
-      t.coefF32 = A.coefF32 + B.oCF;
+    const BProb& P = probs[f.p];
+    if constexpr (PREC == PE_MIXED) {
+      b_fine_mixed_item<KC, batch_mixed_mpt(KC)>(P, f.J0, A, reinterpret_cast<float*>(smem_d));
+    } else {
+      b_fine_f64_item<KC>(P, f.J0, A, smem_d);
     }
-    t.Un = A.U + B.oU + (int64_t)f.n * B.g.ndof;
-    t.Fn = A.Fbar + B.oS + (int64_t)f.n * B.g.ndof;
-    run_tile<PREC, KC>(t, smem_d);
   }
 }
 

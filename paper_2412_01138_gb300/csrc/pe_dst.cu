@@ -8,10 +8,12 @@
 //  * n + 1 = 2^k (n <= 1023): an FFT.  Two real pencils x, y are packed as
 //    z = x + i y; the odd extension of z over 2(n+1) points is Fourier
 //    transformed, and DST(x)_k = -Im V_k / 2, DST(y)_k = Re V_k / 2.  About
-//    5 log2(2n+2) flops per element instead of the 2n of the matrix form.  For
-//    n + 1 >= 16 one warp owns a pencil pair (self-sorting radix-16 passes,
-//    dst_fft_warp_kernel); shorter pencils (and float64 at n + 1 = 1024) use a
-//    block-wide radix-2 kernel (dst_fft_kernel).
+//    5 log2(2n+2) flops per element instead of the 2n of the matrix form.  In
+//    float64 with n + 1 >= 128 the half-length form folds each pencil so that the
+//    pair needs a complex FFT of n + 1 points only (dst_half_warp_kernel); float32
+//    and shorter float64 pencils transform the full odd extension with one warp per
+//    pencil pair (dst_fft_warp_kernel); both run self-sorting radix-4..32 passes.
+//    Pencils with n + 1 < 16 use a block-wide radix-2 kernel (dst_fft_kernel).
 //  * any other n: a shared-memory tiled, strided, batched GEMM with the matrix S_a
 //    (tile shape chosen so that the grid covers the GPU).
 #include <algorithm>
@@ -281,7 +283,7 @@ const Cplx<T>* twiddles(int logL, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Warp-per-pencil-pair FFT form (n + 1 = 2^k, 16 <= n + 1 <= 1024): the same odd
 // extension of z = x + i y over L = 2(n+1) points, transformed by a self-sorting
-// (Stockham) FFT in radix-16 passes (a radix-2/4/8 pass finishes odd log2 L).
+// (Stockham) FFT in radix-16/32 passes (a radix-2/4/8 pass finishes the rest).
 // One warp owns one pencil pair's L values in shared memory, so the passes need
 // only __syncwarp; each lane holds L/32 values in registers between a pass's
 // loads and stores.  A CTA stages WARPS pencil pairs: the global loads and
@@ -294,26 +296,36 @@ __device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
   return Cplx<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
 
+// read-only (non-coherent cache) load of one complex value
+template <typename T>
+__device__ __forceinline__ Cplx<T> ldg_cplx(const Cplx<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return Cplx<T>{v.x, v.y};
+  } else {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return Cplx<T>{v.x, v.y};
+  }
+}
+
 // padded shared-memory index: one gap every 16 values keeps the strided pass
 // stores free of bank conflicts
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 
 constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
-__host__ __device__ constexpr int brevc(int i, int bits) {  // bit reversal of i < 16 over `bits` bits
-  return (((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)) >> (4 - bits);
+__host__ __device__ constexpr int brevc(int i, int bits) {  // bit reversal of i < 32 over `bits` bits
+  return (((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4)) >> (5 - bits);
 }
 
-// e^{-2 pi i t/16}, t = 0..7 (cos and sin of multiples of pi/8)
-__device__ __forceinline__ constexpr double w16_re(int t) {
-  return t == 0 ? 1.0 : t == 1 ? 0.92387953251128674 : t == 2 ? 0.70710678118654752 : t == 3 ? 0.38268343236508978
-       : t == 4 ? 0.0 : t == 5 ? -0.38268343236508978 : t == 6 ? -0.70710678118654752 : -0.92387953251128674;
+// e^{-2 pi i t/32}, t = 0..15 (cos and -sin of multiples of pi/16)
+__device__ __forceinline__ constexpr double w32_re(int t) {
+  return t == 0 ? 1.0 : t == 1 ? 0.98078528040323044913 : t == 2 ? 0.92387953251128675613 : t == 3 ? 0.83146961230254523708 : t == 4 ? 0.70710678118654752440 : t == 5 ? 0.55557023301960222474 : t == 6 ? 0.38268343236508977173 : t == 7 ? 0.19509032201612826785 : t == 8 ? 0.0 : t == 9 ? -0.19509032201612826785 : t == 10 ? -0.38268343236508977173 : t == 11 ? -0.55557023301960222474 : t == 12 ? -0.70710678118654752440 : t == 13 ? -0.83146961230254523708 : t == 14 ? -0.92387953251128675613 : -0.98078528040323044913;
 }
-__device__ __forceinline__ constexpr double w16_im(int t) {
-  return t == 0 ? 0.0 : t == 1 ? -0.38268343236508978 : t == 2 ? -0.70710678118654752 : t == 3 ? -0.92387953251128674
-       : t == 4 ? -1.0 : t == 5 ? -0.92387953251128674 : t == 6 ? -0.70710678118654752 : -0.38268343236508978;
+__device__ __forceinline__ constexpr double w32_im(int t) {
+  return t == 0 ? 0.0 : t == 1 ? -0.19509032201612826785 : t == 2 ? -0.38268343236508977173 : t == 3 ? -0.55557023301960222474 : t == 4 ? -0.70710678118654752440 : t == 5 ? -0.83146961230254523708 : t == 6 ? -0.92387953251128675613 : t == 7 ? -0.98078528040323044913 : t == 8 ? -1.0 : t == 9 ? -0.98078528040323044913 : t == 10 ? -0.92387953251128675613 : t == 11 ? -0.83146961230254523708 : t == 12 ? -0.70710678118654752440 : t == 13 ? -0.55557023301960222474 : t == 14 ? -0.38268343236508977173 : -0.19509032201612826785;
 }
 
-// In-register forward DFT of R = 2, 4, 8 or 16 values: radix-2 decimation in frequency,
+// In-register forward DFT of R = 2, 4, ..., 32 values: radix-2 decimation in frequency,
 // natural-order input, output in bit-reversed order (X[r] = v[brevc(r, log2 R)]).
 template <typename T, int R>
 __device__ __forceinline__ void dft_regs(Cplx<T> (&v)[R]) {
@@ -323,16 +335,24 @@ __device__ __forceinline__ void dft_regs(Cplx<T> (&v)[R]) {
     for (int s = 0; s < R; s += len) {
 #pragma unroll
       for (int k = 0; k < len / 2; ++k) {
-        const int t = k * (16 / len);
+        const int t = k * (32 / len);
         const Cplx<T> a = v[s + k], b = v[s + k + len / 2];
         v[s + k] = Cplx<T>{a.re + b.re, a.im + b.im};
         const Cplx<T> d{a.re - b.re, a.im - b.im};
         if (t == 0) v[s + k + len / 2] = d;
-        else if (t == 4) v[s + k + len / 2] = Cplx<T>{d.im, -d.re};  // times -i
-        else v[s + k + len / 2] = cmul(d, Cplx<T>{(T)w16_re(t), (T)w16_im(t)});
+        else if (t == 8) v[s + k + len / 2] = Cplx<T>{d.im, -d.re};  // times -i
+        else v[s + k + len / 2] = cmul(d, Cplx<T>{(T)w32_re(t), (T)w32_im(t)});
       }
     }
   }
+}
+
+// Radix (as log2) of the pass that starts with `left` of the LOGL bits still to combine:
+// float32 uses 32-point passes from L = 512 on ([16, 32], [32, 32], [32, 32, 2]); float64
+// keeps 16-point passes (register budget).
+template <typename T>
+__host__ __device__ constexpr int pass_bits(int left, int logl) {
+  return (sizeof(T) == 4 && logl >= 9 && left >= 5 && !(logl == 9 && left == 9)) ? 5 : (left >= 4 ? 4 : left);
 }
 
 // One Stockham pass of radix R after NS points have been combined; tw = this pass's
@@ -350,7 +370,7 @@ __device__ __forceinline__ void stockham_pass(Cplx<T>* a, const Cplx<T>* tw, int
       if (NS > 1) {
         const int k = j & (NS - 1);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[g][r] = cmul(v[g][r], tw[r * NS + k]);
+        for (int r = 1; r < R; ++r) v[g][r] = cmul(v[g][r], ldg_cplx(tw + r * NS + k));
       }
       dft_regs<T, R>(v[g]);
     }
@@ -373,7 +393,7 @@ __device__ __forceinline__ void stockham_pass(Cplx<T>* a, const Cplx<T>* tw, int
 template <typename T, int LOGL, int LEFT, int NS>
 struct StockhamPasses {
   static __device__ __forceinline__ void run(Cplx<T>* a, const Cplx<T>* tw, int lane) {
-    constexpr int RB = LEFT >= 4 ? 4 : LEFT;
+    constexpr int RB = pass_bits<T>(LEFT, LOGL);
     constexpr int R = 1 << RB;
     stockham_pass<T, LOGL, R, NS>(a, tw, lane);
     StockhamPasses<T, LOGL, LEFT - RB, NS * R>::run(a, tw + (NS > 1 ? NS * R : 0), lane);
@@ -385,48 +405,27 @@ struct StockhamPasses<T, LOGL, 0, NS> {
 };
 
 // entries of the pass twiddle tables of a length-2^LOGL transform
-constexpr int pass_tw_entries(int left, int ns) {
-  return left == 0 ? 0 : (ns > 1 ? ns * (1 << (left >= 4 ? 4 : left)) : 0) +
-                             pass_tw_entries(left - (left >= 4 ? 4 : left), ns * (1 << (left >= 4 ? 4 : left)));
+template <typename T>
+constexpr int pass_tw_entries(int left, int ns, int logl) {
+  return left == 0 ? 0
+                   : (ns > 1 ? ns * (1 << pass_bits<T>(left, logl)) : 0) +
+                         pass_tw_entries<T>(left - pass_bits<T>(left, logl), ns * (1 << pass_bits<T>(left, logl)), logl);
 }
 
 // blockDim.x = 32 * warps (warps = 1, 2, 4 or 8): P = 2 * warps pencils per block of work.
 template <typename T, int LOGL>
-__global__ void __launch_bounds__(256) dst_fft_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGL <= 9) ? 2 : 1) dst_fft_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
                                                            int64_t inner, int64_t npencils, T scale,
-                                                           const Cplx<T>* __restrict__ twg) {
+                                                           const Cplx<T>* __restrict__ ptw) {
   constexpr int L = 1 << LOGL, N = L / 2, PADL = L + L / 16;
-  constexpr int NTW = pass_tw_entries(LOGL, 1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int B = blockDim.x, WARPS = B >> 5, P = 2 * WARPS, logP = __ffs(P) - 1;
   Cplx<T>* bufs = reinterpret_cast<Cplx<T>*>(smem_raw);
-  Cplx<T>* ptw = bufs + (size_t)WARPS * PADL;
-  int64_t* off = reinterpret_cast<int64_t*>(ptw + NTW);
+  int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)WARPS * PADL);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // pass twiddle tables from the global table e^{-2 pi i t / L}, t < L/2
-  {
-    int e0 = 0;
-    int ns = 1, left = LOGL;
-    while (left > 0) {
-      const int rb = left >= 4 ? 4 : left, R = 1 << rb;
-      if (ns > 1) {
-        const int stride = L / (ns * R);
-        for (int e = tid; e < ns * R; e += B) {
-          const int r = e / ns, k = e - r * ns;
-          const int t = k * r * stride;
-          const Cplx<T> w = t < N ? twg[t] : Cplx<T>{-twg[t - N].re, -twg[t - N].im};
-          ptw[e0 + e] = w;
-        }
-        e0 += ns * R;
-      }
-      ns *= R;
-      left -= rb;
-    }
-  }
   if (inner == 1) {
     // contiguous pencils (last axis): each warp loads, transforms and stores its own pencil
-    // pairs (rows of n consecutive values), with no block-wide barrier after the tables
-    __syncthreads();
+    // pairs (rows of n consecutive values), with no block-wide barrier
     constexpr int JL = (N + 31) / 32;  // values per lane and pencil (n <= N - 1)
     Cplx<T>* a = bufs + (size_t)warp * PADL;
     const int64_t npairs = (npencils + 1) / 2;
@@ -527,48 +526,379 @@ __global__ void __launch_bounds__(256) dst_fft_warp_kernel(const T* __restrict__
   }
 }
 
-// Warps per CTA: as many (up to 8, float64 up to 4) as still give >= 2 CTAs per SM.
-template <typename T, int LOGL>
-pe_status fft_warp_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, T scale, const Cplx<T>* tw,
-                          cudaStream_t st) {
-  constexpr int L = 1 << LOGL, PADL = L + L / 16;
-  constexpr int NTW = pass_tw_entries(LOGL, 1);
+// ---------------------------------------------------------------------------
+// Half-length form (128 <= n + 1 = N <= 1024).  The odd extension wastes half of
+// a length-2N transform; instead each real pencil x (x_0 = x_N = 0) is folded to
+//   y_j = sin(pi j/N) (x_j + x_{N-j}) + (x_j - x_{N-j}) / 2,   j = 0..N-1,
+// whose length-N real DFT Y_k = R_k + i I_k (kernel e^{+2 pi i jk/N}) gives the
+// sine sums F_m = sum_j x_j sin(pi j m/N) as F_{2k} = I_k and
+// F_{2k+1} = R_0/2 + R_1 + ... + R_k (a prefix sum).  Two pencils a, b share one
+// complex FFT of z = y^a + i y^b (length N, forward kernel e^{-2 pi i jk/N}):
+// with W = conj(Z_{N-k}), Y^a = (Z_k + W)/2 and Y^b = (Z_k - W)/(2i), so
+// R^a = (Re Z_k + Re Z_{N-k})/2, I^a = (Im Z_{N-k} - Im Z_k)/2,
+// R^b = (Im Z_k + Im Z_{N-k})/2, I^b = (Re Z_k - Re Z_{N-k})/2.
+// One warp owns a pair; radices keep all 32 lanes busy (N/R >= 32 groups).  The
+// prefix sum runs per lane over a contiguous chunk of N/64 indices, then across
+// lanes with warp shuffles.
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ constexpr int half_pass_bits(int left, int logn) {
+  const int cap = sizeof(T) == 4 ? 5 : 4;
+  const int lim = logn - 5 < 2 ? 2 : (logn - 5 > cap ? cap : logn - 5);
+  return left >= lim ? lim : left;
+}
+
+template <typename T, int LOGN, int LEFT, int NS>
+struct HalfPasses {
+  static __device__ __forceinline__ void run(Cplx<T>* a, const Cplx<T>* tw, int lane) {
+    constexpr int RB = half_pass_bits<T>(LEFT, LOGN);
+    constexpr int R = 1 << RB;
+    stockham_pass<T, LOGN, R, NS>(a, tw, lane);
+    HalfPasses<T, LOGN, LEFT - RB, NS * R>::run(a, tw + (NS > 1 ? NS * R : 0), lane);
+  }
+};
+template <typename T, int LOGN, int NS>
+struct HalfPasses<T, LOGN, 0, NS> {
+  static __device__ __forceinline__ void run(Cplx<T>*, const Cplx<T>*, int) {}
+};
+
+template <typename T>
+constexpr int half_tw_entries(int left, int ns, int logn) {
+  return left == 0 ? 0
+                   : (ns > 1 ? ns * (1 << half_pass_bits<T>(left, logn)) : 0) +
+                         half_tw_entries<T>(left - half_pass_bits<T>(left, logn),
+                                            ns * (1 << half_pass_bits<T>(left, logn)), logn);
+}
+
+// Fold (pre-processing), FFT and unfold (post-processing) of one pencil pair held in a:
+// on entry a[fpad(p)] = (x^a_p, x^b_p) for p = 1..N-1 and a[fpad(0)] = 0; on exit
+// a[fpad(m)] = (F^a_m, F^b_m) for m = 1..N-1 (unscaled sine sums).
+template <typename T, int LOGN>
+__device__ __forceinline__ void half_dst_pair(Cplx<T>* a, const Cplx<T>* __restrict__ ptw,
+                                              const T* __restrict__ sinN, int lane) {
+  constexpr int N = 1 << LOGN, V = N / 32, C = N / 64;
+  // fold
+  Cplx<T> z[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int j = lane + 32 * t;
+    const Cplx<T> x = a[fpad(j)];
+    const Cplx<T> xm = j == 0 ? Cplx<T>{T(0), T(0)} : a[fpad(N - j)];
+    const T s = __ldg(sinN + j);
+    z[t] = Cplx<T>{s * (x.re + xm.re) + T(0.5) * (x.re - xm.re), s * (x.im + xm.im) + T(0.5) * (x.im - xm.im)};
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < V; ++t) a[fpad(lane + 32 * t)] = z[t];
+  __syncwarp();
+  HalfPasses<T, LOGN, LOGN, 1>::run(a, ptw, lane);
+  // unfold: lane owns k = lane*C .. lane*C + C - 1 of the N/2 output pairs
+  T ia[C], ib[C], sa[C], sb[C];
+  T ta = T(0), tb = T(0);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int k = lane * C + c;
+    const Cplx<T> Z = a[fpad(k)];
+    const Cplx<T> Wm = a[fpad((N - k) & (N - 1))];
+    T ra = T(0.5) * (Z.re + Wm.re), rb = T(0.5) * (Z.im + Wm.im);
+    ia[c] = T(0.5) * (Wm.im - Z.im);
+    ib[c] = T(0.5) * (Z.re - Wm.re);
+    if (k == 0) {
+      ra *= T(0.5);
+      rb *= T(0.5);
+    }
+    ta += ra;
+    tb += rb;
+    sa[c] = ta;
+    sb[c] = tb;
+  }
+  // exclusive scan of the lane totals
+  T ea = ta, eb = tb;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T ua = __shfl_up_sync(0xffffffffu, ea, d), ub = __shfl_up_sync(0xffffffffu, eb, d);
+    if (lane >= d) {
+      ea += ua;
+      eb += ub;
+    }
+  }
+  ea -= ta;
+  eb -= tb;
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int k = lane * C + c;
+    if (k > 0) a[fpad(2 * k)] = Cplx<T>{ia[c], ib[c]};
+    a[fpad(2 * k + 1)] = Cplx<T>{sa[c] + ea, sb[c] + eb};
+  }
+  __syncwarp();
+}
+
+// blockDim.x = 32 * warps; one warp per pencil pair (P = 2 * warps pencils per block of
+// work for strided pencils).
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
+    dst_half_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int64_t inner, int64_t npencils,
+                         T scale, const Cplx<T>* __restrict__ ptw, const T* __restrict__ sinN) {
+  constexpr int N = 1 << LOGN, PADN = N + N / 16, JL = N / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int B = blockDim.x, WARPS = B >> 5, P = 2 * WARPS, logP = __ffs(P) - 1;
+  Cplx<T>* bufs = reinterpret_cast<Cplx<T>*>(smem_raw);
+  int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)WARPS * PADN);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Cplx<T>* a = bufs + (size_t)warp * PADN;
+  if (inner == 1) {
+    const int64_t npairs = (npencils + 1) / 2;
+    for (int64_t pr = (int64_t)blockIdx.x * WARPS + warp; pr < npairs; pr += (int64_t)gridDim.x * WARPS) {
+      const int64_t pa = 2 * pr, pb = pa + 1;
+      const bool has_b = pb < npencils;
+      const T* xa = in + pa * n;
+      const T* xb = in + pb * n;
+      T ra[JL], rb[JL];
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int j = lane + 32 * t;
+        ra[t] = j < n ? xa[j] : T(0);
+        rb[t] = (j < n && has_b) ? xb[j] : T(0);
+      }
+      if (lane == 0) a[fpad(0)] = Cplx<T>{T(0), T(0)};
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int j = lane + 32 * t;
+        if (j < n) a[fpad(j + 1)] = Cplx<T>{ra[t], rb[t]};
+      }
+      __syncwarp();
+      half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
+      T* ya = out + pa * n;
+      T* yb = out + pb * n;
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int k = lane + 32 * t;
+        if (k < n) {
+          const Cplx<T> F = a[fpad(k + 1)];
+          ya[k] = F.re * scale;
+          if (has_b) yb[k] = F.im * scale;
+        }
+      }
+      __syncwarp();
+    }
+    return;
+  }
+  const int64_t nblk = (npencils + P - 1) / P;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t p0 = blk * P;
+    if (tid < P) {
+      const int64_t p = p0 + tid;
+      off[tid] = p < npencils ? (p / inner) * (int64_t)n * inner + (p % inner) : -1;
+    }
+    if (tid < WARPS) bufs[(size_t)tid * PADN] = Cplx<T>{T(0), T(0)};
+    __syncthreads();
+    const int total = P * n;
+    constexpr int U = sizeof(T) == 4 ? 16 : 8;
+    for (int e0 = 0; e0 < total; e0 += U * B) {
+      T r[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * B + tid;
+        r[u] = T(0);
+        if (e < total) {
+          const int64_t o = off[e & (P - 1)];
+          if (o >= 0) r[u] = in[o + (int64_t)(e >> logP) * inner];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * B + tid;
+        if (e < total) {
+          const int pl = e & (P - 1), j = e >> logP;
+          reinterpret_cast<T*>(bufs + (size_t)(pl >> 1) * PADN + fpad(j + 1))[pl & 1] = r[u];
+        }
+      }
+    }
+    __syncthreads();
+    half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
+    __syncthreads();
+    for (int e = tid; e < total; e += B) {
+      const int pl = e & (P - 1), k = e >> logP;
+      const Cplx<T> F = bufs[(size_t)(pl >> 1) * PADN + fpad(k + 1)];
+      const int64_t o = off[pl];
+      if (o >= 0) out[o + (int64_t)k * inner] = ((pl & 1) ? F.im : F.re) * scale;
+    }
+    __syncthreads();
+  }
+}
+
+// Pass twiddle tables of one length 2^logl, in pass order, each laid out [r][k] (k fastest):
+// entry = e^{-2 pi i k r / (NS R)}, evaluated in float64 and rounded to T.  HALF selects the
+// radix plan of the half-length form.
+template <typename T, bool HALF>
+__global__ void pass_twiddle_kernel(int logl, int total, Cplx<T>* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int e0 = 0, ns = 1, left = logl;
+  while (left > 0) {
+    const int rb = HALF ? half_pass_bits<T>(left, logl) : pass_bits<T>(left, logl);
+    const int R = 1 << rb;
+    if (ns > 1) {
+      if (e < e0 + ns * R) {
+        const int r = (e - e0) / ns, k = (e - e0) - r * ns;
+        double sn, cs;
+        sincospi(2.0 * (double)(k * r) / (double)(ns * R), &sn, &cs);
+        out[e] = Cplx<T>{(T)cs, (T)(-sn)};
+        return;
+      }
+      e0 += ns * R;
+    }
+    ns *= R;
+    left -= rb;
+  }
+}
+
+// sin(pi j / N), j < N (the fold of the half-length form)
+template <typename T>
+__global__ void sin_table_kernel(int N, T* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N) out[j] = (T)sinpi((double)j / (double)N);
+}
+
+// Device-resident tables (pass twiddles, the fold's sines), built once per device and length.
+template <typename T, bool HALF>
+const Cplx<T>* pass_twiddles(int logl, int total, cudaStream_t st) {
+  static Cplx<T>* table[64][12] = {};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || logl < 0 || logl > 11) return nullptr;
+  if (table[dev][logl]) return table[dev][logl];
+  Cplx<T>* p = nullptr;
+  if (cudaMalloc((void**)&p, sizeof(Cplx<T>) * (size_t)std::max(total, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (total > 0) pass_twiddle_kernel<T, HALF><<<(total + 255) / 256, 256, 0, st>>>(logl, total, p);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+    return nullptr;
+  }
+  table[dev][logl] = p;
+  return p;
+}
+
+template <typename T>
+const T* half_sines(int logn, cudaStream_t st) {
+  static T* table[64][12] = {};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || logn < 0 || logn > 11) return nullptr;
+  if (table[dev][logn]) return table[dev][logn];
+  const int N = 1 << logn;
+  T* p = nullptr;
+  if (cudaMalloc((void**)&p, sizeof(T) * (size_t)N) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  sin_table_kernel<T><<<(N + 255) / 256, 256, 0, st>>>(N, p);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+    return nullptr;
+  }
+  table[dev][logn] = p;
+  return p;
+}
+
+// warps per CTA: as many (up to 8, float64 up to 4) as still give >= 2 CTAs per SM
+template <typename T>
+pe_status fft_grid(const void* kern, int64_t npencils, size_t smem_per_warp, int* warps_out, size_t* smem_out,
+                   int64_t* grid_out) {
   int dev = 0, sms = 0;
   PE_CUDA_TRY(cudaGetDevice(&dev));
   PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int warps = sizeof(T) == 4 ? 8 : 4;
   while (warps > 1 && (npencils + 2 * warps - 1) / (2 * warps) < 2 * (int64_t)sms) warps >>= 1;
   const int P = 2 * warps;
-  const size_t smem = sizeof(Cplx<T>) * ((size_t)warps * PADL + NTW) + sizeof(int64_t) * P;
-  auto kern = dst_fft_warp_kernel<T, LOGL>;
+  const size_t smem = smem_per_warp * (size_t)warps + sizeof(int64_t) * P;
   if (smem > 48 * 1024) PE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
   const int64_t nblk = (npencils + P - 1) / P;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * std::max(per_sm, 1)));
-  kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, tw);
+  *grid_out = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * std::max(per_sm, 1)));
+  *warps_out = warps;
+  *smem_out = smem;
+  return PE_OK;
+}
+
+template <typename T, int LOGN>
+pe_status fft_half_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, cudaStream_t st) {
+  constexpr int N = 1 << LOGN, PADN = N + N / 16;
+  constexpr int NTW = half_tw_entries<T>(LOGN, 1, LOGN);
+  const Cplx<T>* ptw = pass_twiddles<T, true>(LOGN, NTW, st);
+  const T* sinN = half_sines<T>(LOGN, st);
+  if (!ptw || !sinN) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  auto kern = dst_half_warp_kernel<T, LOGN>;
+  int warps = 1;
+  size_t smem = 0;
+  int64_t grid = 1;
+  PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * PADN, &warps, &smem, &grid));
+  const T scale = (T)sqrt(2.0 / (double)N);
+  kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, ptw, sinN);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+template <typename T, int LOGL>
+pe_status fft_warp_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, T scale, cudaStream_t st) {
+  constexpr int L = 1 << LOGL, PADL = L + L / 16;
+  constexpr int NTW = pass_tw_entries<T>(LOGL, 1, LOGL);
+  const Cplx<T>* ptw = pass_twiddles<T, false>(LOGL, NTW, st);
+  if (!ptw) return pe_fail(PE_ECUDA, "dst: pass twiddle table allocation failed");
+  auto kern = dst_fft_warp_kernel<T, LOGL>;
+  int warps = 1;
+  size_t smem = 0;
+  int64_t grid = 1;
+  PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * PADL, &warps, &smem, &grid));
+  kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, ptw);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
 
 template <typename T>
-pe_status fft_warp_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, const Cplx<T>* tw,
-                        cudaStream_t st, bool* done) {
+pe_status fft_warp_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, cudaStream_t st,
+                        bool* done) {
   const int64_t np = outer * inner;
   const T scale = (T)(0.5 * sqrt(2.0 / (double)(n + 1)));
   *done = true;
-  switch (logL) {
-    case 5: return fft_warp_launch<T, 5>(in, out, n, inner, np, scale, tw, st);
-    case 6: return fft_warp_launch<T, 6>(in, out, n, inner, np, scale, tw, st);
-    case 7: return fft_warp_launch<T, 7>(in, out, n, inner, np, scale, tw, st);
-    case 8: return fft_warp_launch<T, 8>(in, out, n, inner, np, scale, tw, st);
-    case 9: return fft_warp_launch<T, 9>(in, out, n, inner, np, scale, tw, st);
-    case 10: return fft_warp_launch<T, 10>(in, out, n, inner, np, scale, tw, st);
-    case 11:
-      if constexpr (sizeof(T) == 4) return fft_warp_launch<T, 11>(in, out, n, inner, np, scale, tw, st);
-      break;
-    default:
-      break;
+  // float64: the half-length form (half the FP64 work; its prefix sum amplifies the FFT's
+  // rounding by about sqrt(n+1)/2, harmless at float64 precision).  float32: the full
+  // odd extension, whose error stays at the FFT's own level.
+  if constexpr (sizeof(T) == 8) {
+    switch (logL) {
+      case 5: return fft_warp_launch<T, 5>(in, out, n, inner, np, scale, st);
+      case 6: return fft_warp_launch<T, 6>(in, out, n, inner, np, scale, st);
+      case 7: return fft_warp_launch<T, 7>(in, out, n, inner, np, scale, st);
+      case 8: return fft_half_launch<T, 7>(in, out, n, inner, np, st);
+      case 9: return fft_half_launch<T, 8>(in, out, n, inner, np, st);
+      case 10: return fft_half_launch<T, 9>(in, out, n, inner, np, st);
+      case 11: return fft_half_launch<T, 10>(in, out, n, inner, np, st);
+      default:
+        break;
+    }
+  } else {
+    switch (logL) {
+      case 5: return fft_warp_launch<T, 5>(in, out, n, inner, np, scale, st);
+      case 6: return fft_warp_launch<T, 6>(in, out, n, inner, np, scale, st);
+      case 7: return fft_warp_launch<T, 7>(in, out, n, inner, np, scale, st);
+      case 8: return fft_warp_launch<T, 8>(in, out, n, inner, np, scale, st);
+      case 9: return fft_warp_launch<T, 9>(in, out, n, inner, np, scale, st);
+      case 10: return fft_warp_launch<T, 10>(in, out, n, inner, np, scale, st);
+      case 11: return fft_warp_launch<T, 11>(in, out, n, inner, np, scale, st);
+      default:
+        break;
+    }
   }
   *done = false;
   return PE_OK;
@@ -581,7 +911,7 @@ pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int
   const Cplx<T>* tw = twiddles<T>(logL, st);
   if (!tw) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
   bool done = false;
-  PE_TRY(fft_warp_axis<T>(in, out, outer, n, inner, logL, tw, st, &done));
+  PE_TRY(fft_warp_axis<T>(in, out, outer, n, inner, logL, st, &done));
   if (done) return PE_OK;
   // short transforms (n + 1 < 16) and float64 at n + 1 = 1024: the block-wide radix-2 kernel;
   // pencil pairs per CTA: as many as keep >= 2 CTAs per SM, bounded by shared memory

@@ -20,6 +20,7 @@
 
 #include "pe_forcing_common.cuh"
 #include "pe_internal.h"
+#include "pe_sweep_common.cuh"
 
 namespace {
 
@@ -78,31 +79,60 @@ __global__ void gen_loads_kernel(TermsDev T, Geom g, double lo0, double lo1, dou
   L[(int64_t)st * T.n * nsum + (int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = (TL)h * left + (TL)h * right;
 }
 
-// F[st][J] = sum_r amp_r time_r(t_st) prod_a L[st][...]  (nodal consistent load).  The
-// time weights amp_r time_r(t_st) are the same for every node of a stage: one thread per
-// term evaluates them into shared memory.
-template <typename Tout>
-__global__ void gen_assemble_kernel(TermsDev T, Geom g, StageGen SG, int nsum, const Tout* __restrict__ L,
-                                    Tout* __restrict__ F) {
+// F[st][J] = sum_r amp_r time_r(t_st) prod_a L[st][...]  (nodal consistent load), as
+// the rank-R product it is: with J = (o, j) split into the outer indices o and the last
+// axis j, F[st][o][j] = sum_r P_r(o) q_r(j), P_r(o) = prod_{a<d-1} L_a[r][o_a] and
+// q_r(j) = w_r L_{d-1}[r][j] (w_r = amp_r time_r(t_st)).  A block takes one stage and
+// OC outer indices: thread j keeps q_r(j) in registers, the block tabulates P_r(o) in
+// shared memory, and every output costs R FMAs (P read as a broadcast).
+// R is a template parameter so that the R-term loops unroll without predicated FMAs.
+constexpr int kAsmOC = 32;
+template <typename Tout, int R>
+__global__ void __launch_bounds__(256) gen_assemble_kernel(TermsDev T, Geom g, StageGen SG, int nsum, int count,
+                                                           const Tout* __restrict__ L, Tout* __restrict__ F) {
   __shared__ Tout w[PE_MAX_TERMS];
-  const int st = blockIdx.y;
-  if (threadIdx.x < T.n) {
-    const pe_term& tm = T.t[threadIdx.x];
-    w[threadIdx.x] = (Tout)(tm.amp * eval_time(tm, stage_time(SG, st)));
+  __shared__ Tout sP[kAsmOC][R];
+  const int d = g.d, nl = g.n[d - 1];
+  const int64_t outer = g.ndof / nl;
+  const int64_t chunks = (outer + kAsmOC - 1) / kAsmOC;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t yy = blockIdx.y; yy < (int64_t)count * chunks; yy += gridDim.y) {
+    const int st = (int)(yy / chunks);
+    const int64_t o0 = (yy - (int64_t)st * chunks) * kAsmOC;
+    const Tout* Ls = L + (int64_t)st * R * nsum;
+    __syncthreads();  // the previous iteration's readers of w and sP are done
+    if (threadIdx.x < R) {
+      const pe_term& tm = T.t[threadIdx.x];
+      w[threadIdx.x] = (Tout)(tm.amp * eval_time(tm, stage_time(SG, st)));
+    }
+    for (int e = threadIdx.x; e < kAsmOC * R; e += blockDim.x) {
+      const int oc = e / R, r = e - oc * R;
+      const int64_t o = o0 + oc;
+      Tout P = Tout(1);
+      if (o < outer) {
+        int64_t rest = o;
+        for (int a = d - 2; a >= 0; --a) {
+          const int ja = (int)(rest % g.n[a]);
+          rest /= g.n[a];
+          P *= Ls[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + ja];
+        }
+      }
+      sP[oc][r] = P;
+    }
+    __syncthreads();
+    if (j < nl) {
+      Tout q[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) q[r] = w[r] * Ls[(int64_t)R * g.off[d - 1] + (int64_t)r * nl + j];
+      const int oend = (int)min((int64_t)kAsmOC, outer - o0);
+      for (int oc = 0; oc < oend; ++oc) {
+        Tout acc = Tout(0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc = fma(sP[oc][r], q[r], acc);
+        F[(int64_t)st * g.ndof + (o0 + oc) * nl + j] = acc;
+      }
+    }
   }
-  __syncthreads();
-  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (J >= g.ndof) return;
-  int j[PE_MAX_D];
-  unflatten(g, J, j);
-  const Tout* Ls = L + (int64_t)st * T.n * nsum;
-  Tout acc = Tout(0);
-  for (int r = 0; r < T.n; ++r) {
-    Tout P = Ls[(int64_t)T.n * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-    for (int a = 1; a < g.d; ++a) P *= Ls[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + j[a]];
-    acc += w[r] * P;
-  }
-  F[(int64_t)st * g.ndof + J] = acc;
 }
 
 // fine propagator from the stored transformed loads: Gh[(n - n0) M q + m q + i][J] = (V^T F)_J
@@ -199,6 +229,18 @@ StageGen make_gen(const pe_ctx* c, int coarse, int n0) {
   return G;
 }
 
+template <typename T>
+struct AssembleLaunch {
+  template <int R>
+  struct L {
+    static pe_status run(dim3 grid, cudaStream_t st, TermsDev TD, Geom g, StageGen SG, int nsum, int count,
+                         const T* Lp, T* F) {
+      gen_assemble_kernel<T, R><<<grid, 256, 0, st>>>(TD, g, SG, nsum, count, Lp, F);
+      return PE_OK;
+    }
+  };
+};
+
 // loads + nodal assembly + batched DST of `count` stage times into out (element type T)
 template <typename T>
 pe_status stage_transforms(pe_ctx* c, const StageGen& SG, int count, T* out, T* tmp) {
@@ -210,10 +252,13 @@ pe_status stage_transforms(pe_ctx* c, const StageGen& SG, int count, T* out, T* 
   T* L = reinterpret_cast<T*>(c->gen_L);
   gen_loads_kernel<T><<<gl, 128, 0, c->stream>>>(TD, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2], Q,
                                                  SG, c->nsum, L);
-  dim3 ga((unsigned)((c->g.ndof + 255) / 256), count);
+  const int nl = c->g.n[c->g.d - 1];
+  const int64_t chunks = (c->g.ndof / nl + kAsmOC - 1) / kAsmOC;
+  dim3 ga((unsigned)((nl + 255) / 256), (unsigned)std::min<int64_t>((int64_t)count * chunks, 65535));
   // the assembled loads go to tmp or out so that the last DST pass lands in out
   T* F = (c->g.d % 2 == 1) ? tmp : out;
-  gen_assemble_kernel<T><<<ga, 256, 0, c->stream>>>(TD, c->g, SG, c->nsum, L, F);
+  PE_TRY(dispatch_R<AssembleLaunch<T>::template L>(c->R, ga, c->stream, TD, c->g, SG, c->nsum, count,
+                                                   (const T*)L, F));
   c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   const T* src = F;
