@@ -178,6 +178,37 @@ def fine_f64_traffic():
         return None
 
 
+def oracle_chunk(payload):
+    """Worker of the all-cores oracle run: Parareal on one contiguous block of modes."""
+    from oracle import fem
+    from oracle import solver as osolver
+
+    prob, idx, u0_nodal = payload
+    t0 = time.perf_counter()
+    sys_ = osolver.ModalSystem(prob, modes=idx)
+    basis = fem.ClosedFormBasis(prob.n, prob.box, prob.D)
+    sys_.c0 = basis.to_modal_from_nodal(u0_nodal.reshape(prob.n)).reshape(-1)[idx]
+    res = osolver.parareal(sys_, tol=TOL, keep_history=False)
+    return len(idx) * prob.N * prob.M * res.k, time.perf_counter() - t0
+
+
+def oracle_all_cores(prob, u0_nodal):
+    """The oracle as it stands over every host core: modes split into one contiguous block per
+    process (spawned, so no CUDA state is inherited); the pool is started before the timed region."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    blocks = np.array_split(np.arange(prob.ndof), cores)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(abs, range(cores))  # workers up
+        t0 = time.perf_counter()
+        out = pool.map(oracle_chunk, [(prob, b, u0_nodal) for b in blocks])
+        wall = time.perf_counter() - t0
+    units = sum(u for u, _ in out)
+    return {"value": units / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole workload split into {cores} blocks of modes, one process each, {wall:.1f} s"}
+
+
 def oracle_sample(prob, n_modes: int, seed: int = 0, u0_nodal=None):
     """Run the oracle's Parareal (to the same residual tolerance) on a random sample of modes.
 
@@ -306,6 +337,67 @@ def run_learned(pe, args, barrier):
     return out
 
 
+def run_precision(pe, args, barrier):
+    """The 3D 127^3 workload (64 slices x 32 substeps, 16 bumps): plain float64 against the mixed
+    form, its error against the oracle before and after one float64 refinement iteration."""
+    prob = I.config3()
+    out = {"workload": prob.label}
+    steps = max(1, min(args.steps, 2))
+    rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 512, seed=13)
+    w = sys_.norm_w
+
+    def rel(m):
+        return float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) / np.sqrt(np.sum(w * ref.U[-1] ** 2)))
+
+    for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
+        with pe.Solver(prob, precision=prec) as s:
+            s.solve(tol=TOL)
+            barrier()
+            t0 = time.perf_counter()
+            infos = [s.solve(tol=TOL) for _ in range(steps)]
+            barrier()
+            dt = (time.perf_counter() - t0) / steps
+            rec = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
+                   "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
+                   "rel_l2_vs_oracle": rel(s.modal(prob.N))}
+            if prec == pe.PE_MIXED:
+                barrier()
+                t0 = time.perf_counter()
+                s.refine()
+                barrier()
+                rec["refine_ms"] = 1e3 * (time.perf_counter() - t0)
+                rec["rel_l2_after_refine"] = rel(s.modal(prob.N))
+            out[name] = rec
+    out["speedup_time_to_tol"] = out["fp64"]["time_to_tol_ms"] / out["mixed"]["time_to_tol_ms"]
+    out["oracle_sample"] = f"{nm} random modes of {prob.ndof}"
+    return out
+
+
+def run_cached(pe, args, barrier, u0_dev, u0_host):
+    """The main workload with the forced part F^M(0) of every slice kept after the first sweep
+    (exact, the fine propagator being affine); later iterations run no fine sweep.  Reported as
+    time to tolerance only: the reused forced parts are not counted as fine substeps."""
+    prob = workload()
+    out = {"workload": prob.label + " with cached F^M(0)"}
+    rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=17, u0_nodal=u0_host)
+    w = sys_.norm_w
+    for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
+        with pe.Solver(prob, precision=prec, cache_forced=True) as s:
+            for _ in range(max(1, args.warmup)):
+                s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
+            barrier()
+            t0 = time.perf_counter()
+            infos = [s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev) for _ in range(args.steps)]
+            barrier()
+            dt = (time.perf_counter() - t0) / args.steps
+            m = s.modal(prob.N)
+        out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
+                     "fine_sweeps_executed": infos[-1]["fine_sweeps"],
+                     "rel_l2_vs_oracle": float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) /
+                                               np.sqrt(np.sum(w * ref.U[-1] ** 2)))}
+    return out
+
+
 DST_SHAPE = (511, 511, 255)
 
 
@@ -414,7 +506,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512,
                     help="problems in the batched workload (512; fewer only for small profiling captures)")
     ap.add_argument("--no-dst", action="store_true", help="skip the standalone DST-I measurement")
-    ap.add_argument("--only", choices=["batch", "learned", "general", "dst"],
+    ap.add_argument("--no-precision", action="store_true", help="skip the 3D 127^3 precision workload")
+    ap.add_argument("--no-cached", action="store_true", help="skip the cached-F^M(0) line")
+    ap.add_argument("--only", choices=["batch", "learned", "general", "dst", "precision", "cached"],
                     help="run one secondary workload alone and print its record (for profiling)")
     args = ap.parse_args()
 
@@ -473,7 +567,9 @@ def main():
     if args.only:
         run = {"batch": lambda: run_batch(pe, args, barrier), "learned": lambda: run_learned(pe, args, barrier),
                "general": lambda: run_general(pe, args, barrier, u0_dev),
-               "dst": lambda: run_dst(pe, args, barrier)}[args.only]
+               "dst": lambda: run_dst(pe, args, barrier),
+               "precision": lambda: run_precision(pe, args, barrier),
+               "cached": lambda: run_cached(pe, args, barrier, u0_dev, u0_host)}[args.only]
         rec = run()
         if rank == 0:
             print(json.dumps({"section": args.only, **rec}))
@@ -499,6 +595,8 @@ def main():
         learned = None if args.no_learned else run_learned(pe, args, barrier)
         general = None if args.no_general else run_general(pe, args, barrier, u0_dev)
         dst = None if args.no_dst else run_dst(pe, args, barrier)
+        precision = None if args.no_precision else run_precision(pe, args, barrier)
+        cached = None if args.no_cached else run_cached(pe, args, barrier, u0_dev, u0_host)
     clock = clocks.summary()
 
     # max over ranks
@@ -544,6 +642,10 @@ def main():
         r2 = oracle_sample(prob, prob.ndof, seed=7, u0_nodal=u0_host)
         cpu_passes, cpu_s, cpu_units = cpu_passes + 1, cpu_s + r2[1], cpu_units + r2[2] * prob.N * prob.M * r2[3]
 
+    all_cores = None
+    if not args.no_cpu_baseline and rank == 0:
+        all_cores = oracle_all_cores(prob, u0_host)
+
     def rel(a):
         return float(np.sqrt(np.sum(w * (a[idx] - ref.U[-1]) ** 2)) / np.sqrt(np.sum(w * ref.U[-1] ** 2)))
 
@@ -552,7 +654,8 @@ def main():
     if not args.no_cpu_baseline:
         cpu = {"value": cpu_units / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the whole workload ({nm} of {prob.ndof} modes), Parareal to rel residual {TOL} "
-                         f"(k={k_or} sweeps of {prob.N}x{prob.M} substeps), {cpu_passes} pass(es), {cpu_s:.1f} s"}
+                         f"(k={k_or} sweeps of {prob.N}x{prob.M} substeps), {cpu_passes} pass(es), {cpu_s:.1f} s",
+               "all_cores": all_cores}
 
     flops_launch = fine_flops_per_unit(prob) * prob.ndof * prob.N * prob.M
     achieved = flops_launch / (plain["ms_fine_launch"] / 1e3) / 1e12
@@ -603,6 +706,8 @@ def main():
         "learned": learned,
         "general": general,
         "dst": dst,
+        "precision": precision,
+        "affine_cached": cached,
     }
     print(json.dumps(line))
     if dist is not None:

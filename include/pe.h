@@ -104,6 +104,11 @@ typedef struct {
   int32_t max_iter;     /* pe_solve iteration cap, 0 = N (Theorem 4.3: k = N is exact) */
   void* cuda_stream;    /* cudaStream_t or NULL */
   int32_t forcing_path; /* PE_FORCING_SEPARABLE (default) | PE_FORCING_GENERAL */
+  int32_t cache_forced; /* 1: keep the forced part F^M(0) of every slice after the first fine
+                           sweep and reuse it in later iterations (exact, since the fine
+                           propagator is affine: F^M(v) = exp(-lam M dt) v + F^M(0)); later
+                           iterations then run no fine sweep.  Separable forcing only; the
+                           float64 refinement of a mixed run makes its own float64 copy. */
 } pe_options;
 
 /* Initial data: u0 = sum of separable terms (time factors ignored), projected
@@ -130,7 +135,7 @@ typedef struct {
   double residual;           /* last relative residual r_k (defined at pe_parareal_iter) */
   double* residual_history;  /* host, caller-owned, capacity history_cap (may be NULL) */
   int32_t history_cap;
-  int64_t fine_sweeps;       /* fine propagator sweeps executed (= k) */
+  int64_t fine_sweeps;       /* fine propagator sweeps executed (= k; 1 with cache_forced) */
   double ms_tables;          /* device time of the forcing tables (time factors, per-axis modal
                                 factors, fine-step stage weights); the phi/b coefficient tables
                                 depend only on pe_setup's arguments and are made there */

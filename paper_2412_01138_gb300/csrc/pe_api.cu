@@ -128,7 +128,7 @@ void free_ctx(pe_ctx* c) {
                   c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Gold, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
-                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32};
+                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -240,7 +240,12 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     delete c;
     return pe_fail(PE_EINVAL, "pe_setup: bad forcing_path");
   }
+  if (o.cache_forced && o.forcing_path == PE_FORCING_GENERAL) {
+    delete c;
+    return pe_fail(PE_EINVAL, "pe_setup: cache_forced needs PE_FORCING_SEPARABLE");
+  }
   c->forcing_path = o.forcing_path;
+  c->cache_forced = o.cache_forced ? 1 : 0;
   c->precision = o.precision;
   c->dst_backend = o.dst_backend;
   c->quad_pts = o.quad_pts;
@@ -261,6 +266,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->U, (N + 1) * nd);
   if (st == PE_OK) st = dev_alloc(&c->Gold, N * nd);
   if (st == PE_OK) st = dev_alloc(&c->Fbar, N * nd);
+  if (st == PE_OK && c->cache_forced) st = dev_alloc(&c->Fz, N * nd);
   if (st == PE_OK) st = dev_alloc(&c->gG, N * nd);
   if (st == PE_OK) st = dev_alloc(&c->work0, nd + 64);
   if (st == PE_OK) st = dev_alloc(&c->work1, nd + 64);
@@ -370,6 +376,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   }
   // k = 0: coarse sweep
   PE_TRY(launch_coarse_sweep(c));
+  c->fz_prec = -1;
   c->k = 0;
   c->have_problem = true;
   c->have_output = false;
@@ -423,6 +430,7 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   c->have_problem = false;
   c->launches = 0;
   c->ms_fine = 0.0;
+  c->sweeps = 0;
   PE_CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
   PE_TRY(set_problem_impl(c, u0, f));
   PE_CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
@@ -442,7 +450,7 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   if (res) {
     res->k = c->k;
     res->residual = r;
-    res->fine_sweeps = c->k;
+    res->fine_sweeps = c->sweeps;
     res->ms_tables = elapsed(c->ev[0], c->ev[1]);
     res->ms_prepare = elapsed(c->ev[1], c->ev[2]);
     res->ms_iterations = elapsed(c->ev[2], c->ev[3]);

@@ -44,8 +44,9 @@ struct FineTile {
   const float* coefF32;   // E_hi, E_lo (rows of ndof)
   const double* coefF;    // E, dt*b_i, exp(-lam M dt) (rows of ndof)
   int q;
+  int from_zero;          // 1: propagate 0 instead of U^n (the forced part F^M(0))
   const double* Un;       // U^n
-  double* Fn;             // F^M(U^n)
+  double* Fn;             // F^M(U^n), or F^M(0) when from_zero
 };
 
 // Mixed precision, K columns staged as KC = roundup(K, 4) floats per substep so
@@ -81,6 +82,9 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, float* sY) {
       sY[t] = c < K ? a.Yn32[(int64_t)(m0 + row) * K + c] : 0.f;
     }
     __syncthreads();
+    // two substeps per trip: the second substep's broadcast loads and FMA chains are
+    // independent of the first one's recurrence, so they overlap its latency
+#pragma unroll 2
     for (int m = 0; m < mc; ++m) {
       const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
       float acc[MPT];
@@ -106,7 +110,7 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, float* sY) {
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
     const int64_t J = base + (int64_t)B * k;
-    if (J < nd) a.Fn[J] = fma(EM[J], a.Un[J], (double)w[k]);
+    if (J < nd) a.Fn[J] = a.from_zero ? (double)w[k] : fma(EM[J], a.Un[J], (double)w[k]);
   }
 }
 
@@ -125,7 +129,7 @@ __device__ __forceinline__ void fine_f64_tile(const FineTile& a, double* sY) {
 #pragma unroll
     for (int k = 0; k < K; ++k) W[k] = a.W[(int64_t)k * nd + J];
     E = a.coefF[J];
-    c = a.Un[J];
+    c = a.from_zero ? 0.0 : a.Un[J];
   }
   for (int m0 = 0; m0 < M; m0 += a.mchunk) {
     const int mc = min(a.mchunk, M - m0);
@@ -172,8 +176,9 @@ __global__ void __launch_bounds__(256) fine_f64_kernel(FineTile t, int64_t slice
 }  // namespace
 
 
+// from_zero: write F^M(0) of every slice to `out` instead of F^M(U^n) to c->Fbar.
 template <int K>
-pe_status fine_launch(pe_ctx* c, int precision) {
+pe_status fine_launch(pe_ctx* c, int precision, int from_zero, double* out) {
   const int threads = 256;
   FineTile t{};
   t.ndof = c->g.ndof;
@@ -185,8 +190,9 @@ pe_status fine_launch(pe_ctx* c, int precision) {
   t.Yn = c->AF;
   t.coefF32 = c->coefF32;
   t.coefF = c->coefF;
+  t.from_zero = from_zero;
   t.Un = c->U;
-  t.Fn = c->Fbar;
+  t.Fn = out;
   const int64_t stride = (int64_t)c->M * K;
   if (precision == PE_MIXED) {
     constexpr int MPT = K <= 24 ? 4 : (K <= 40 ? 2 : 1);

@@ -64,26 +64,25 @@ __global__ void time_tables_kernel(TermsDev T, StageCols C, int N, int M, int q,
   }
 }
 
-// W[k*ndof + J] = P_{r(k),J} sum_i (dt b_i)_J Z[i*K + k], with P_{r,J} = prod_a axisF[R off_a + r n_a + j_a].
-__global__ void stage_weights_kernel(Geom g, StageCols C, int R, int q, const double* __restrict__ axisF,
-                                     const double* __restrict__ coefF, const double* __restrict__ Z,
-                                     double* __restrict__ W, float* __restrict__ W32) {
+// W[k*ndof + J] = P_{r(k),J} sum_i (dt b_i)_J Z[i*K + k], with P_{r,J} = prod_a axisF[R off_a + r n_a + j_a],
+// in the arithmetic of T (coefficient row i of dt b_i at coef + i * ndof).
+template <typename T>
+__global__ void stage_weights_kernel(Geom g, StageCols C, int R, int q, const T* __restrict__ axisF,
+                                     const T* __restrict__ coef, const double* __restrict__ Z, T* __restrict__ W) {
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   const int64_t nd = g.ndof;
   int j[PE_MAX_D];
   unflatten(g, J, j);
-  double b[PE_MAX_S];
-  for (int i = 0; i < q; ++i) b[i] = coefF[(int64_t)(1 + i) * nd + J];
+  T b[PE_MAX_S];
+  for (int i = 0; i < q; ++i) b[i] = coef[(int64_t)i * nd + J];
   for (int k = 0; k < C.K; ++k) {
     const int r = C.term[k];
-    double P = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+    T P = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
     for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
-    double s = 0.0;
-    for (int i = 0; i < q; ++i) s = fma(b[i], Z[i * C.K + k], s);
-    const double w = P * s;
-    W[(int64_t)k * nd + J] = w;
-    if (W32) W32[(int64_t)k * nd + J] = (float)w;
+    T s = T(0);
+    for (int i = 0; i < q; ++i) s = fma(b[i], (T)Z[i * C.K + k], s);
+    W[(int64_t)k * nd + J] = P * s;
   }
 }
 
@@ -209,11 +208,31 @@ pe_status launch_stage_weights(pe_ctx* c) {
     c->Wcap = K;
   }
   const int threads = 256;
-  stage_weights_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(
-      c->g, c->cols, c->R, c->q, c->axisF, c->coefF, c->Zst, c->Wst,
-      c->precision == PE_MIXED ? c->Wst32 : nullptr);
+  const unsigned blocks = (unsigned)((c->g.ndof + threads - 1) / threads);
+  if (c->precision == PE_MIXED) {
+    // the float32 fine sweeps need only the float32 weights; the float64 ones follow on the
+    // first float64 sweep (pe_refine)
+    stage_weights_kernel<float><<<blocks, threads, 0, c->stream>>>(c->g, c->cols, c->R, c->q, c->axisF32,
+                                                                   c->coefF32 + 2 * c->g.ndof, c->Zst, c->Wst32);
+    c->Wst_valid = false;
+  } else {
+    stage_weights_kernel<double><<<blocks, threads, 0, c->stream>>>(c->g, c->cols, c->R, c->q, c->axisF,
+                                                                    c->coefF + c->g.ndof, c->Zst, c->Wst);
+    c->Wst_valid = true;
+  }
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status launch_stage_weights_f64(pe_ctx* c) {
+  if (c->Wst_valid) return PE_OK;
+  const int threads = 256;
+  stage_weights_kernel<double><<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(
+      c->g, c->cols, c->R, c->q, c->axisF, c->coefF + c->g.ndof, c->Zst, c->Wst);
+  c->launches += 1;
+  PE_CUDA_TRY(cudaGetLastError());
+  c->Wst_valid = true;
   return PE_OK;
 }
 

@@ -47,36 +47,50 @@ __device__ inline double stage_time(const StageGen& G, int idx) {
   return tl + G.c[i] * G.dt;
 }
 
-// L[st][R*off[a] + r*n_a + k] = int g_{r,a}(x, t_st) phi_{k+1}(x) dx  (grid: nodes, R*d, stages);
-// TL = float evaluates the factors in float32 (mixed precision), double in float64.
+// L[st][R*off[a] + r*n_a + k] = int g_{r,a}(x, t_st) phi_{k+1}(x) dx  (grid: node blocks of
+// 128, R*d, stages).  Element m = [lo + m h, lo + (m+1) h] contributes h int g s ds to its
+// right node and h int g (1-s) ds to its left node; each element's quadrature is evaluated
+// once (into shared memory) and node k sums the rising part of element k and the falling
+// part of element k+1.  TL = float evaluates the factors in float32 (mixed precision).
 template <typename TL>
-__global__ void gen_loads_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2, double h0, double h1,
-                                 double h2, Gauss Q, StageGen SG, int nsum, TL* __restrict__ L) {
+__global__ void __launch_bounds__(128) gen_loads_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2,
+                                                        double h0, double h1, double h2, Gauss Q, StageGen SG,
+                                                        int nsum, TL* __restrict__ L) {
+  __shared__ TL rise[129], fall[129];
   const int st = blockIdx.z;
   const int ra = blockIdx.y;
   const int r = ra / g.d, a = ra % g.d;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= T.n || k >= g.n[a]) return;
+  if (r >= T.n) return;
+  const int n = g.n[a];
+  const int k0 = blockIdx.x * 128;
+  if (k0 >= n) return;  // uniform over the block
   const double t = stage_time(SG, st);
   const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
   const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
   const pe_term& tm = T.t[r];
-  TL left = TL(0), right = TL(0);
-  for (int qi = 0; qi < Q.npts; ++qi) {
-    const TL xl = (TL)(lo + ((double)k + Q.s[qi]) * h);
-    const TL xr = (TL)(lo + ((double)(k + 1) + Q.s[qi]) * h);
-    TL gl, gr;
-    if constexpr (sizeof(TL) == 4) {
-      gl = eval_space_f(tm.skind[a], tm.sp[a], xl, t);
-      gr = eval_space_f(tm.skind[a], tm.sp[a], xr, t);
-    } else {
-      gl = eval_space(tm.skind[a], tm.sp[a], xl, t);
-      gr = eval_space(tm.skind[a], tm.sp[a], xr, t);
+  // elements k0 .. k0 + 128 (the last one only for its falling part)
+  for (int i = threadIdx.x; i <= 128; i += blockDim.x) {
+    const int m = k0 + i;
+    TL up = TL(0), dn = TL(0);
+    if (m <= n) {
+      for (int qi = 0; qi < Q.npts; ++qi) {
+        const TL x = (TL)(lo + ((double)m + Q.s[qi]) * h);
+        TL gv;
+        if constexpr (sizeof(TL) == 4) gv = eval_space_f(tm.skind[a], tm.sp[a], x, t);
+        else gv = eval_space(tm.skind[a], tm.sp[a], x, t);
+        const TL wg = (TL)Q.w[qi] * gv;
+        up += wg * (TL)Q.s[qi];
+        dn += wg * (TL)(1.0 - Q.s[qi]);
+      }
     }
-    left += (TL)Q.w[qi] * gl * (TL)Q.s[qi];
-    right += (TL)Q.w[qi] * gr * (TL)(1.0 - Q.s[qi]);
+    rise[i] = up;
+    fall[i] = dn;
   }
-  L[(int64_t)st * T.n * nsum + (int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = (TL)h * left + (TL)h * right;
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (k < n)
+    L[(int64_t)st * T.n * nsum + (int64_t)T.n * g.off[a] + (int64_t)r * n + k] =
+        (TL)h * rise[threadIdx.x] + (TL)h * fall[threadIdx.x + 1];
 }
 
 // F[st][J] = sum_r amp_r time_r(t_st) prod_a L[st][...]  (nodal consistent load), as
@@ -304,6 +318,7 @@ pe_status launch_general_coarse_forcing(pe_ctx* c) {
 }
 
 pe_status launch_general_fine_sweep(pe_ctx* c, int precision) {
+  c->sweeps += 1;
   const int chunk = general_slices_per_chunk(c);
   for (int n0 = 0; n0 < c->N; n0 += chunk) {
     const int ns = std::min(chunk, c->N - n0);

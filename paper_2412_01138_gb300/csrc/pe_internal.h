@@ -72,7 +72,7 @@ struct pe_ctx {
   double lagF[PE_MAX_S][PE_MAX_S], lagG[PE_MAX_S][PE_MAX_S];  // Lagrange monomial coefficients
   int nsum;  // sum_a n_a
   // options
-  int precision, dst_backend, quad_pts, max_iter, forcing_path;
+  int precision, dst_backend, quad_pts, max_iter, forcing_path, cache_forced;
   cudaStream_t stream;
   // device memory
   double* muM_axis = nullptr;   // [nsum]
@@ -89,6 +89,9 @@ struct pe_ctx {
   float* coefF32 = nullptr;     // [(q+2) * ndof]: E_hi, E_lo, dt*b_i (float)
   double* U = nullptr;          // [(N+1) * ndof]
   double* Gold = nullptr;       // [N * ndof]
+  double* Fz = nullptr;         // [N * ndof] cached F^M(0) per slice (cache_forced)
+  int fz_prec = -1;             // precision Fz was computed in, -1: none for this problem
+  int64_t sweeps = 0;           // fine sweeps executed since the last reset
   double* Fbar = nullptr;       // [N * ndof]
   double* gG = nullptr;         // [N * ndof] coarse forcing of each slice
   double* work0 = nullptr;      // [ndof] nodal / DST scratch
@@ -112,6 +115,7 @@ struct pe_ctx {
   double* Wst = nullptr;        // [K * ndof] (allocated on first use, grown with K)
   float* Wst32 = nullptr;       // [K * ndof] (mixed precision)
   int Wcap = 0;                 // columns allocated in Wst / Wst32
+  bool Wst_valid = false;       // Wst holds the current problem's float64 weights
   double* AG = nullptr;         // [N*p*PE_MAX_TERMS]
   float* AG32 = nullptr;
   double* loads = nullptr;      // [PE_MAX_TERMS * nsum] 1D loads before the DST
@@ -154,7 +158,8 @@ pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st);
 
 // pe_forcing.cu
 pe_status launch_time_tables(pe_ctx* c);   // also sets c->K, c->cols and Zst
-pe_status launch_stage_weights(pe_ctx* c);  // Wst (and Wst32) from coefF, axisF, Zst
+pe_status launch_stage_weights(pe_ctx* c);  // Wst (float64 form) or Wst32 (mixed form)
+pe_status launch_stage_weights_f64(pe_ctx* c);  // Wst, if not yet made for this problem
 pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode);
 pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* terms, int nterms, double* out,
                            int nodal_loads);

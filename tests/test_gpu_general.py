@@ -47,6 +47,22 @@ def test_example4_moving_hat(pe, alpha, freq, q, p):
     assert np.abs(nodal - ref_nodal).max() <= 1e-12 * np.abs(ref_nodal).max()
 
 
+@pytest.mark.parametrize("alpha,freq", [(0.01, 1.0), (0.01, 10.0), (0.1, 1.0), (0.1, 10.0)])
+def test_example4_paper_size(pe, alpha, freq):
+    """Example 4 at the paper's size: N_x = 1024 (1023 interior nodes), 4 x 16, k = 4 iterations,
+    every (alpha, f) pair the paper runs, float64 and mixed."""
+    prob = I.example4(1024, alpha, freq, 4, 16, 3, 3)
+    sys_ = osolver.ModalSystem(prob, forcing_route="full")
+    ref = osolver.parareal(sys_, tol=0.0, k_max=4)
+    for prec, bound in ((pe.PE_FP64, 1e-12), (pe.PE_MIXED, 1e-6)):
+        with pe.Solver(prob, precision=prec, forcing_path=pe.PE_FORCING_GENERAL) as s:
+            s.set_problem()
+            for _ in range(4):
+                s.iterate()
+            for n in range(1, prob.N + 1):
+                assert _rel(s.modal(n), ref.U[n], sys_.norm_w) <= bound, (prec, n)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_moving_hat_2d(pe, precision):
     prob = I.moving_hat_2d()
