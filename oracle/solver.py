@@ -27,7 +27,7 @@ from typing import Callable, List, Optional
 
 import numpy as np
 
-from . import fem, quadrature
+from . import dirichlet, fem, quadrature
 from .phi import b_weights
 
 
@@ -76,6 +76,14 @@ class ModalSystem:
             self.c0 = np.asarray(self.basis.to_modal_from_load(F0)).reshape(-1)
         else:
             raise ValueError(forcing_route)
+        # non-homogeneous Dirichlet data: w = u_h - I_h g, w(t0) = P_h(u0 - I_h g(t0))
+        self.lift = dirichlet.DirichletLift(prob) if getattr(prob, "boundary", ()) else None
+        if self.lift is not None:
+            self.c0 = self.c0 - self._restrict(self.basis.to_modal_from_load(self.lift.lift_load(prob.t0)))
+
+    def _restrict(self, c: np.ndarray) -> np.ndarray:
+        c = np.asarray(c).reshape(-1)
+        return c if self.modes is None else c[self.modes]
 
     def _separable_modal(self, term) -> np.ndarray:
         """Modal coefficients of P_h of the spatial part of one separable term."""
@@ -94,15 +102,23 @@ class ModalSystem:
         return np.asarray(self.basis.to_modal_from_load(F)).reshape(-1)
 
     def ghat(self, t: float) -> np.ndarray:
-        """Modal coefficients of P_h f(t)."""
+        """Modal coefficients of P_h f(t) (plus the lifting's extra load under Dirichlet data)."""
         if self.forcing_route == "separable":
             out = np.zeros_like(self.lam)
             for term, P in zip(self.prob.forcing, self._P):
                 out = out + (term.amp * quadrature.eval_time(term, t)) * P
-            return out
-        prob = self.prob
-        F = quadrature.load_full(prob.forcing, t, prob.n, prob.box, prob.quad_pts)
-        return np.asarray(self.basis.to_modal_from_load(F)).reshape(-1)
+        else:
+            prob = self.prob
+            F = quadrature.load_full(prob.forcing, t, prob.n, prob.box, prob.quad_pts)
+            out = np.asarray(self.basis.to_modal_from_load(F)).reshape(-1)
+        if self.lift is not None:
+            out = out + self._restrict(self.basis.to_modal_from_load(self.lift.extra_load(t)))
+        return out
+
+    def solution_nodal(self, c: np.ndarray, t: float) -> np.ndarray:
+        """Interior nodal values of u_h = w + I_h g at time t for the modal state c of w."""
+        u = self.to_nodal(c)
+        return u if self.lift is None else u + self.lift.interior(t)
 
     def norm(self, c: np.ndarray) -> float:
         """||v||_0 of the FE function with modal coefficients c."""

@@ -133,6 +133,7 @@ class Problem:
     tol: float = 1e-12
     exact: Optional[Tuple[Term, ...]] = None  # exact solution, when known
     label: str = ""
+    boundary: Tuple[Term, ...] = ()          # Dirichlet data: separable terms on the closed box
 
     @property
     def ndof(self) -> int:
