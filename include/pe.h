@@ -167,6 +167,23 @@ pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const double* box,
 pe_status pe_set_problem(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f);
 
 /*
+ * pe_set_dirichlet -- non-homogeneous Dirichlet data u = g on the boundary, for the
+ * following pe_set_problem / pe_solve calls (n_terms = 0 restores u = 0).  The paper
+ * treats u = 0 and states (openings of Sec. 3 and Sec. 4) that its results extend to
+ * non-homogeneous data, without formulas; this library's reading: g is given as
+ * separable terms (time factor exp or sin, spatial factors of the pe_term kinds except
+ * the moving hat) on the CLOSED box, its values on the boundary are the data, and the
+ * lifting is the Q1 interpolant I_h g on all nodes.  The solver integrates
+ * w = u_h - I_h g (zero on the boundary) with the extra load
+ * -(M d/dt I_h g + K I_h g) on interior nodes, from w(t0) = P_h(u0 - I_h g(t0))
+ * (descriptor u0) or u0 - I_h g(t0) (nodal u0); pe_get_solution returns the interior
+ * nodal values of u_h = w + I_h g, pe_get_modal the modal coefficients of w.  Each data
+ * term adds 1 + d separable forcing terms (at most 32 in all).  Separable forcing path
+ * only, not with the learned correction (PE_EINVAL).  g is copied (host array).
+ */
+pe_status pe_set_dirichlet(pe_ctx* ctx, int32_t n_terms, const pe_term* g);
+
+/*
  * pe_parareal_iter -- one pass of Algorithm 1's loop: the fine propagator from
  * every slice start in parallel, then the sequential correction
  *   U^{n+1,(k+1)} = G(U^{n,(k+1)}) + F^M(U^{n,(k)}) - G(U^{n,(k)}),

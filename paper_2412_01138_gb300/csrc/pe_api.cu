@@ -325,6 +325,84 @@ extern "C" void pe_destroy(pe_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------
+// non-homogeneous Dirichlet data by lifting
+//
+// Data g(t, x) = sum_s A_s theta_s(t) prod_a gamma_{s,a}(x_a) on the closed box; the lifting
+// is the Q1 interpolant I_h g on all nodes and the solver integrates w = u_h - I_h g, which
+// vanishes on the boundary.  Testing with the interior hat functions adds the load
+//   r_i = -(M_full d/dt I_h g + K_full I_h g)_i,
+// a sum of separable terms whose per-axis 1D vectors are interior rows of the full-grid
+// 1D mass and stiffness matrices applied to gamma's nodal values (load kinds 1 and 2): per
+// data term one mass term with time factor -A theta' and d stiffness terms -A D theta.
+// ---------------------------------------------------------------------------
+static double time_factor(const pe_term& t, double tt) {
+  return t.tkind == PE_T_SIN ? sin(t.tp[0] * tt + t.tp[1]) : exp(t.tp[0] * tt);
+}
+
+static pe_status expand_dirichlet_terms(pe_ctx* c) {
+  const int d = c->g.d;
+  for (int s = 0; s < c->nbd; ++s) {
+    const pe_term& b = c->bterms[s];
+    if (c->R + 1 + d > PE_MAX_TERMS)
+      return pe_fail(PE_EINVAL, "pe_set_problem: forcing plus Dirichlet terms exceed 32 (each data term adds 1 + d)");
+    // mass term: time factor d/dt theta (exp(a t) -> a exp(a t); sin(w t + phi) -> w sin(w t + phi + pi/2))
+    pe_term m = b;
+    if (b.tkind == PE_T_SIN) {
+      m.amp = -b.amp * b.tp[0];
+      m.tp[1] = b.tp[1] + 0.5 * M_PI;
+    } else {
+      m.amp = -b.amp * b.tp[0];
+    }
+    if (m.amp != 0.0) {
+      c->terms[c->R] = m;
+      for (int a = 0; a < d; ++a) c->lkind[c->R][a] = 1;
+      c->R += 1;
+    }
+    for (int a = 0; a < d; ++a) {
+      pe_term k = b;
+      k.amp = -b.amp * c->D;
+      c->terms[c->R] = k;
+      for (int e = 0; e < d; ++e) c->lkind[c->R][e] = e == a ? 2 : 1;
+      c->R += 1;
+    }
+  }
+  if (c->R == 0) {  // data only through terms that vanished: keep one zero term
+    c->R = 1;
+    memset(&c->terms[0], 0, sizeof(pe_term));
+  }
+  return PE_OK;
+}
+
+// out += sign * I_h g(t) in one of three forms: kind 1 the modal P_h of the interpolant,
+// kind 2 the modal V^T of its interior values, kind 3 its interior nodal values.
+static pe_status add_lift(pe_ctx* c, double t, double sign, int kind, double* out) {
+  if (c->nbd == 0) return PE_OK;
+  pe_term tt[PE_MAX_TERMS];
+  signed char lk[PE_MAX_TERMS][PE_MAX_D] = {};
+  for (int s = 0; s < c->nbd; ++s) {
+    tt[s] = c->bterms[s];
+    tt[s].amp = sign * c->bterms[s].amp * time_factor(c->bterms[s], t);
+    for (int a = 0; a < c->g.d; ++a) lk[s][a] = kind == 1 ? 1 : 3;
+  }
+  const int mode = kind == 1 ? 1 : (kind == 2 ? 2 : 0);
+  PE_TRY(launch_separable_factors(c, tt, c->nbd, c->axisU0, mode, lk));
+  return launch_outer_sum(c, c->axisU0, tt, c->nbd, out, 1);
+}
+
+extern "C" pe_status pe_set_dirichlet(pe_ctx* c, int32_t n_terms, const pe_term* g) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_set_dirichlet: ctx is NULL");
+  if (n_terms < 0 || n_terms > PE_MAX_TERMS) return pe_fail(PE_EINVAL, "pe_set_dirichlet: n_terms out of range");
+  if (n_terms > 0 && !g) return pe_fail(PE_EINVAL, "pe_set_dirichlet: terms is NULL");
+  PE_TRY(pe_validate_terms(n_terms, g, c->g.d, "Dirichlet data"));
+  if (n_terms > 0 && c->forcing_path == PE_FORCING_GENERAL)
+    return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data need PE_FORCING_SEPARABLE");
+  c->nbd = n_terms;
+  for (int i = 0; i < n_terms; ++i) c->bterms[i] = g[i];
+  c->have_problem = false;  // the next pe_set_problem / pe_solve takes the data into account
+  return PE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // problem, iteration, solve
 // ---------------------------------------------------------------------------
 static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
@@ -333,19 +411,23 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   const bool general = c->forcing_path == PE_FORCING_GENERAL;
   PE_TRY(pe_validate_terms(nf, f ? f->terms : nullptr, c->g.d, "forcing", general));
   if (general && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: the learned correction needs PE_FORCING_SEPARABLE");
-  if (nf == 0) {
+  if (c->nbd > 0 && general) return pe_fail(PE_EINVAL, "pe_set_problem: Dirichlet data need PE_FORCING_SEPARABLE");
+  if (c->nbd > 0 && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: Dirichlet data and the learned correction");
+  memset(c->lkind, 0, sizeof(c->lkind));
+  if (nf == 0 && c->nbd == 0) {
     // no source: one zero term keeps every kernel shape valid
     c->R = 1;
     memset(&c->terms[0], 0, sizeof(pe_term));
   } else {
     c->R = nf;
     for (int i = 0; i < nf; ++i) c->terms[i] = f->terms[i];
+    PE_TRY(expand_dirichlet_terms(c));
   }
   // The phi/b coefficient tables depend only on lam, dt, dT and the nodes: pe_setup made them.
   // Forcing: time factors, per-axis modal factors and the stage weights of the fine step.
   if (!general) {
     PE_TRY(launch_time_tables(c));
-    PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1));
+    PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1, c->lkind));
     PE_TRY(launch_stage_weights(c));
   }
   PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
@@ -361,7 +443,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     } else {
       // nodal consistent load F = sum_t amp_t kron_a F_{t,a}, then c0 = Lambda_M^{-1} V^T F
       PE_TRY(launch_separable_factors(c, u0->terms, u0->n_terms, c->axisU0, 0));
-      PE_TRY(launch_outer_sum(c, c->axisU0, u0->terms, u0->n_terms, c->work0, 1));
+      PE_TRY(launch_outer_sum(c, c->axisU0, u0->terms, u0->n_terms, c->work0, 0));
       PE_TRY(dst_nd_f64(c, c->work0, U0));
       PE_TRY(launch_scale_by_muM(c, U0, 1));
     }
@@ -373,6 +455,12 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     PE_TRY(dst_nd_f64(c, c->work0, U0));
   } else {
     return pe_fail(PE_EINVAL, "pe_set_problem: unknown u0 kind");
+  }
+  // Dirichlet lifting: w(t0) = P_h(u0 - I_h g(t0)) for descriptor data, u0 - I_h g(t0) for
+  // nodal data (taken as already in V_h)
+  if (c->nbd > 0) {
+    const bool nodal = u0->kind == PE_FIELD_NODAL;
+    PE_TRY(add_lift(c, c->t0, -1.0, nodal ? 2 : 1, U0));
   }
   // k = 0: coarse sweep
   PE_TRY(launch_coarse_sweep(c));
@@ -444,6 +532,7 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   }
   PE_CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
   PE_TRY(dst_nd_f64(c, c->U + (int64_t)c->N * c->g.ndof, c->out_nodal));
+  PE_TRY(add_lift(c, c->t0 + c->T, 1.0, 3, c->out_nodal));
   PE_CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->have_output = true;
@@ -471,6 +560,7 @@ extern "C" pe_status pe_get_solution(pe_ctx* c, int32_t slice, double* nodal_out
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_get_solution: no problem set");
   if (slice == c->N && c->have_output) return copy_out(c, c->out_nodal, nodal_out, c->g.ndof);
   PE_TRY(dst_nd_f64(c, c->U + (int64_t)slice * c->g.ndof, c->work0));
+  PE_TRY(add_lift(c, c->t0 + slice * c->dT, 1.0, 3, c->work0));
   return copy_out(c, c->work0, nodal_out, c->g.ndof);
 }
 

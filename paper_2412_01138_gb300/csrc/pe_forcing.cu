@@ -96,6 +96,18 @@ __global__ void loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, doub
   const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
   const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
   const pe_term& t = T.t[r];
+  const int lk = T.lk[r][a];
+  if (lk != 0) {
+    // lifting of Dirichlet data: the factor at full-grid nodes k, k+1, k+2 (x = lo + i h)
+    const double g0 = eval_space(t.skind[a], t.sp[a], lo + (double)k * h);
+    const double g1 = eval_space(t.skind[a], t.sp[a], lo + (double)(k + 1) * h);
+    const double g2 = eval_space(t.skind[a], t.sp[a], lo + (double)(k + 2) * h);
+    double v = g1;
+    if (lk == 1) v = (h / 6.0) * (g0 + 4.0 * g1 + g2);
+    else if (lk == 2) v = (1.0 / h) * (2.0 * g1 - g0 - g2);
+    out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = v;
+    return;
+  }
   // element k spans nodes k, k+1 (this node is its right vertex: shape s);
   // element k+1 spans nodes k+1, k+2 (this node is its left vertex: shape 1-s)
   double left = 0.0, right = 0.0;
@@ -122,7 +134,7 @@ __global__ void divide_axis_mu_kernel(Geom g, int R, const double* __restrict__ 
 
 // out[J] = sum_r w_r prod_a fac[R*off[a] + r*n_a + j_a]
 __global__ void outer_sum_kernel(Geom g, int R, const double* __restrict__ fac, const double* __restrict__ w,
-                                 double* __restrict__ out) {
+                                 double* __restrict__ out, int accumulate) {
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   int j[PE_MAX_D];
@@ -133,7 +145,7 @@ __global__ void outer_sum_kernel(Geom g, int R, const double* __restrict__ fac, 
     for (int a = 1; a < g.d; ++a) P *= fac[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     acc += w[r] * P;
   }
-  out[J] = acc;
+  out[J] = accumulate ? out[J] + acc : acc;
 }
 
 __global__ void scale_mu_kernel(Geom g, const double* __restrict__ muM, double* __restrict__ x, int inverse) {
@@ -236,10 +248,13 @@ pe_status launch_stage_weights_f64(pe_ctx* c) {
   return PE_OK;
 }
 
-// mode 0: 1D loads only (axis_out gets loads); mode 1: modal factors (S_a F)/mu^M.
-pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode) {
+// mode 0: 1D loads only (axis_out gets loads); mode 1: modal factors (S_a F)/mu^M;
+// mode 2: S_a F only (the modal coefficients V^T y of a separable nodal vector y).
+// lk (may be NULL): per-term, per-axis load kinds of the Dirichlet lifting (TermsDev).
+pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode,
+                                   const signed char (*lk)[PE_MAX_D]) {
   if (nterms == 0) return PE_OK;
-  TermsDev T = pack_terms(terms, nterms);
+  TermsDev T = pack_terms(terms, nterms, lk);
   Gauss G = make_gauss(c->quad_pts);
   int nmax = 1;
   for (int a = 0; a < c->g.d; ++a) nmax = c->g.n[a] > nmax ? c->g.n[a] : nmax;
@@ -255,6 +270,7 @@ pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, 
     PE_TRY(dst_axis_f64(c->S[a], loads + base, axis_out + base, nterms, c->g.n[a], 1, c->stream));
     c->launches += 1;
   }
+  if (mode == 2) return PE_OK;  // V^T of nodal values: no division by mu^M
   const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
   divide_axis_mu_kernel<<<grid, 128, 0, c->stream>>>(c->g, nterms, c->muM_axis, axis_out,
                                                      f32 ? c->axisF32 : nullptr);
@@ -265,13 +281,15 @@ pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, 
 
 // out[J] = sum_r amp_r prod_a fac_{r,a}[j_a] (nodal_loads: fac are 1D loads, out a nodal load vector)
 pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* terms, int nterms, double* out,
-                           int /*nodal_loads*/) {
+                           int accumulate) {
+  if (nterms == 0) return PE_OK;
   double* w = c->partials;  // at least PE_MAX_TERMS doubles
   TermsDev T = pack_terms(terms, nterms);
   amps_kernel<<<1, PE_MAX_TERMS, 0, c->stream>>>(T, w);
   const int threads = 256;
   outer_sum_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, nterms,
-                                                                                               axis_fac, w, out);
+                                                                                               axis_fac, w, out,
+                                                                                               accumulate);
   c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
@@ -283,7 +301,7 @@ pe_status launch_forcing_modal(pe_ctx* c, double t, double* out) {
   weights_at_time_kernel<<<1, PE_MAX_TERMS, 0, c->stream>>>(T, t, w);
   const int threads = 256;
   outer_sum_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, c->R,
-                                                                                               c->axisF, w, out);
+                                                                                               c->axisF, w, out, 0);
   c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;

@@ -6,9 +6,15 @@
 
 #include "pe_internal.h"
 
+// lk[r][a]: how the 1D "load" of term r along axis a is formed from its factor g:
+// 0 consistent load int g phi_k (Gauss quadrature); for the Dirichlet lifting, from the
+// factor's values at the full-grid nodes x_{k}, x_{k+1}, x_{k+2} around interior node k:
+// 1 mass rows (h/6)(g_k + 4 g_{k+1} + g_{k+2}), 2 stiffness rows (1/h)(-g_k + 2 g_{k+1} - g_{k+2}),
+// 3 the nodal value g_{k+1}.
 struct TermsDev {
   int n;
   pe_term t[PE_MAX_TERMS];
+  signed char lk[PE_MAX_TERMS][PE_MAX_D];
 };
 
 struct Nodes {
@@ -93,10 +99,13 @@ inline Gauss make_gauss(int npts) {
   return G;
 }
 
-inline TermsDev pack_terms(const pe_term* terms, int n) {
+inline TermsDev pack_terms(const pe_term* terms, int n, const signed char (*lk)[PE_MAX_D] = nullptr) {
   TermsDev T{};
   T.n = n;
-  for (int i = 0; i < n; ++i) T.t[i] = terms[i];
+  for (int i = 0; i < n; ++i) {
+    T.t[i] = terms[i];
+    for (int a = 0; a < PE_MAX_D; ++a) T.lk[i][a] = lk ? lk[i][a] : 0;
+  }
   return T;
 }
 

@@ -104,6 +104,10 @@ struct pe_ctx {
   // forcing (set by pe_set_problem)
   int R = 0;
   pe_term terms[PE_MAX_TERMS];
+  signed char lkind[PE_MAX_TERMS][PE_MAX_D] = {};  // load kinds of terms (Dirichlet lifting)
+  // non-homogeneous Dirichlet data (pe_set_dirichlet): separable terms on the closed box
+  int nbd = 0;
+  pe_term bterms[PE_MAX_TERMS];
   double* axisF = nullptr;      // [PE_MAX_TERMS * nsum]
   float* axisF32 = nullptr;     // [PE_MAX_TERMS * nsum]
   double* axisU0 = nullptr;     // [PE_MAX_TERMS * nsum] factors of separable u0
@@ -160,9 +164,10 @@ pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st);
 pe_status launch_time_tables(pe_ctx* c);   // also sets c->K, c->cols and Zst
 pe_status launch_stage_weights(pe_ctx* c);  // Wst (float64 form) or Wst32 (mixed form)
 pe_status launch_stage_weights_f64(pe_ctx* c);  // Wst, if not yet made for this problem
-pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode);
+pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode,
+                                   const signed char (*lk)[PE_MAX_D] = nullptr);
 pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* terms, int nterms, double* out,
-                           int nodal_loads);
+                           int accumulate);
 pe_status launch_forcing_modal(pe_ctx* c, double t, double* out);
 
 // pe_dst.cu

@@ -36,7 +36,7 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_batch_autotune", "pe_batch_solve", "pe_batch_get_modal", "pe_batch_get_solution", "pe_batch_status",
             "pe_batch_destroy", "pe_mlp_create", "pe_mlp_num_params", "pe_mlp_train", "pe_mlp_gradient",
             "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
-            "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc")
+            "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc", "pe_set_dirichlet")
 
 
 class PEError(RuntimeError):
@@ -131,6 +131,7 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_set_learned": (C.c_int, [P, P]),
         "pe_dst_tc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, C.c_int32, P]),
         "pe_dst_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
+        "pe_set_dirichlet": (C.c_int, [P, C.c_int32, P]),
         "pe_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -213,6 +214,13 @@ class Solver:
                                   C.byref(fine), C.byref(coarse), C.byref(opt)))
         self.ctx = ctx
         self._keep = []
+        if getattr(prob, "boundary", ()):
+            self.set_dirichlet(prob.boundary)
+
+    def set_dirichlet(self, terms) -> None:
+        """Non-homogeneous Dirichlet data (separable terms on the closed box); () restores u = 0."""
+        arr = make_terms(tuple(terms)) if terms else None
+        _check(self._lib.pe_set_dirichlet(self.ctx, len(terms), C.cast(arr, C.c_void_p) if arr is not None else None))
 
     def close(self):
         if getattr(self, "ctx", None):
