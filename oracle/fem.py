@@ -8,7 +8,9 @@ L_h defined by a(w,v) = (L_h w, v)) and the closing paragraph of Sec. 2.3
 applied by tensor products).
 
 Conventions: axis a has n_a interior nodes x_k = lo_a + k h_a, k = 1..n_a,
-h_a = (hi_a - lo_a)/(n_a + 1) (the paper's N_a subintervals are n_a + 1).
+h_a = (hi_a - lo_a)/(n_a + 1) (the paper's N_a subintervals are n_a + 1); a periodic
+axis has n_a nodes x_k = lo_a + k h_a, k = 0..n_a - 1, h_a = (hi_a - lo_a)/n_a, and the
+discrete Hartley transform takes the place of the DST-I.
 Nodal and modal arrays are C-ordered with shape (n_0, ..., n_{d-1}).
 """
 from __future__ import annotations
@@ -18,11 +20,53 @@ import scipy.linalg
 import scipy.sparse as sp
 
 
-def axis_grid(lo: float, hi: float, n: int):
-    """Mesh size and interior node coordinates of one axis."""
+def axis_grid(lo: float, hi: float, n: int, periodic: bool = False):
+    """Mesh size and node coordinates of one axis: n interior nodes x_k = lo + k h, k = 1..n,
+    h = (hi - lo)/(n + 1) (Dirichlet), or n nodes x_k = lo + k h, k = 0..n-1, h = (hi - lo)/n
+    on a periodic axis (node n is node 0)."""
+    if periodic:
+        h = (hi - lo) / n
+        return h, lo + h * np.arange(0, n, dtype=np.float64)
     h = (hi - lo) / (n + 1)
     x = lo + h * np.arange(1, n + 1, dtype=np.float64)
     return h, x
+
+
+def mass_1d_periodic(n: int, h: float) -> np.ndarray:
+    """1D P1 mass matrix of a periodic axis: circulant (h/6)[1 4 1]."""
+    A = 4.0 * np.eye(n)
+    for k in range(n):
+        A[k, (k + 1) % n] += 1.0
+        A[k, (k - 1) % n] += 1.0
+    return (h / 6.0) * A
+
+
+def stiffness_1d_periodic(n: int, h: float) -> np.ndarray:
+    """1D P1 stiffness matrix of a periodic axis: circulant (1/h)[-1 2 -1]."""
+    A = 2.0 * np.eye(n)
+    for k in range(n):
+        A[k, (k + 1) % n] -= 1.0
+        A[k, (k - 1) % n] -= 1.0
+    return A / h
+
+
+def dht_matrix(n: int) -> np.ndarray:
+    """Orthonormal discrete Hartley transform: H[k, j] = (cos + sin)(2 pi j k / n) / sqrt(n).
+
+    Symmetric with H @ H = I; every circulant symmetric matrix is diagonal in it (the
+    cosine and sine vectors of one frequency share an eigenvalue).  j k is reduced modulo n.
+    """
+    k = np.arange(n, dtype=np.int64)
+    m = np.outer(k, k) % n
+    ang = 2.0 * np.pi * m.astype(np.float64) / n
+    return (np.cos(ang) + np.sin(ang)) / np.sqrt(n)
+
+
+def axis_eigenvalues_periodic(n: int, h: float):
+    """Eigenvalues of the periodic 1D mass and stiffness matrices in the DHT basis:
+    theta_j = 2 pi j / n, j = 0..n-1, mu^M = (h/3)(2 + cos theta), mu^K = (4/h) sin^2(theta/2)."""
+    theta = 2.0 * np.pi * np.arange(n, dtype=np.float64) / n
+    return (h / 3.0) * (2.0 + np.cos(theta)), (4.0 / h) * np.sin(0.5 * theta) ** 2
 
 
 def mass_1d(n: int, h: float) -> np.ndarray:
@@ -35,18 +79,24 @@ def stiffness_1d(n: int, h: float) -> np.ndarray:
     return (1.0 / h) * (2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1))
 
 
-def assemble(n, box, D):
+def assemble(n, box, D, periodic=()):
     """Q1 mass M = kron_a M_a and stiffness K = D sum_a M_1 x .. K_a .. x M_d.
 
     Returned as scipy sparse CSR matrices acting on C-ordered nodal vectors
-    (axis d-1 fastest), i.e. kron(A_0, kron(A_1, ...)).
+    (axis d-1 fastest), i.e. kron(A_0, kron(A_1, ...)).  periodic[a] selects the
+    circulant matrices of a periodic axis.
     """
     d = len(n)
+    per = tuple(periodic) + (False,) * (d - len(periodic))
     Ms, Ks = [], []
     for a in range(d):
-        h, _ = axis_grid(box[a][0], box[a][1], n[a])
-        Ms.append(sp.csr_matrix(mass_1d(n[a], h)))
-        Ks.append(sp.csr_matrix(stiffness_1d(n[a], h)))
+        h, _ = axis_grid(box[a][0], box[a][1], n[a], per[a])
+        if per[a]:
+            Ms.append(sp.csr_matrix(mass_1d_periodic(n[a], h)))
+            Ks.append(sp.csr_matrix(stiffness_1d_periodic(n[a], h)))
+        else:
+            Ms.append(sp.csr_matrix(mass_1d(n[a], h)))
+            Ks.append(sp.csr_matrix(stiffness_1d(n[a], h)))
 
     def kron_all(mats):
         out = mats[0]
@@ -116,16 +166,21 @@ class ClosedFormBasis:
 
     route = "closed_form"
 
-    def __init__(self, n, box, D):
+    def __init__(self, n, box, D, periodic=()):
         self.n = tuple(int(v) for v in n)
         self.box = tuple(box)
         self.D = float(D)
+        self.periodic = tuple(periodic) + (False,) * (len(self.n) - len(periodic))
         self.S = []
         self.muM_axes, self.muK_axes, self.h = [], [], []
         for a, na in enumerate(self.n):
-            h, _ = axis_grid(box[a][0], box[a][1], na)
-            muM, muK = axis_eigenvalues(na, h)
-            self.S.append(dst1_matrix(na))
+            h, _ = axis_grid(box[a][0], box[a][1], na, self.periodic[a])
+            if self.periodic[a]:
+                muM, muK = axis_eigenvalues_periodic(na, h)
+                self.S.append(dht_matrix(na))
+            else:
+                muM, muK = axis_eigenvalues(na, h)
+                self.S.append(dst1_matrix(na))
             self.muM_axes.append(muM)
             self.muK_axes.append(muK)
             self.h.append(h)
@@ -174,9 +229,9 @@ class DenseBasis:
 
     route = "dense"
 
-    def __init__(self, n, box, D):
+    def __init__(self, n, box, D, periodic=()):
         self.n = tuple(int(v) for v in n)
-        M, K = assemble(self.n, box, D)
+        M, K = assemble(self.n, box, D, periodic)
         self.M = M.toarray()
         self.K = K.toarray()
         lam, W = scipy.linalg.eigh(self.K, self.M)

@@ -90,7 +90,21 @@ def load_1d(fun, lo: float, hi: float, n: int, qp: int) -> np.ndarray:
     return F[1:-1]
 
 
-def load_full(terms, t, n, box, qp: int) -> np.ndarray:
+def load_1d_periodic(fun, lo: float, hi: float, n: int, qp: int) -> np.ndarray:
+    """F_k = int fun(x) phi_k(x) dx for the n hats of a periodic axis (nodes x_k = lo + k h,
+    h = (hi - lo)/n): element e = 0..n-1 spans [lo + e h, lo + (e+1) h], its left node is e
+    and its right node (e+1) mod n."""
+    h, _ = axis_grid(lo, hi, n, True)
+    s, w = gauss_legendre(qp)
+    F = np.zeros(n)
+    for e in range(n):
+        gq = fun(lo + (e + s) * h)
+        F[e] += h * np.sum(w * gq * (1.0 - s))
+        F[(e + 1) % n] += h * np.sum(w * gq * s)
+    return F
+
+
+def load_full(terms, t, n, box, qp: int, periodic=()) -> np.ndarray:
     """d-D consistent load by tensor Gauss quadrature on every Q1 element.
 
     t = None loads the spatial part only (initial data).
@@ -100,14 +114,16 @@ def load_full(terms, t, n, box, qp: int) -> np.ndarray:
     2^d vertices.  Slow, used on small grids.
     """
     d = len(n)
+    per = tuple(periodic) + (False,) * (d - len(periodic))
     s, w = gauss_legendre(qp)
-    hs = [axis_grid(box[a][0], box[a][1], n[a])[0] for a in range(d)]
-    # quadrature points along each axis for all elements: shape (n_a+1, qp)
-    pts = [box[a][0] + (np.arange(n[a] + 1)[:, None] + s[None, :]) * hs[a] for a in range(d)]
-    F = np.zeros(tuple(v + 2 for v in n))
-    # f at all points: shape (n0+1, qp, n1+1, qp, ...)
+    hs = [axis_grid(box[a][0], box[a][1], n[a], per[a])[0] for a in range(d)]
+    ne = [n[a] if per[a] else n[a] + 1 for a in range(d)]  # elements per axis
+    # quadrature points along each axis for all elements: shape (ne_a, qp)
+    pts = [box[a][0] + (np.arange(ne[a])[:, None] + s[None, :]) * hs[a] for a in range(d)]
+    F = np.zeros(tuple(v + 1 for v in ne))
+    # f at all points: shape (ne0, qp, ne1, qp, ...)
     fvals = eval_terms(terms, t, [p.reshape(-1) for p in pts])
-    fvals = fvals.reshape(sum(((n[a] + 1, qp) for a in range(d)), ()))
+    fvals = fvals.reshape(sum(((ne[a], qp) for a in range(d)), ()))
     for corner in range(2 ** d):
         bits = [(corner >> (d - 1 - a)) & 1 for a in range(d)]
         weight = None
@@ -115,11 +131,18 @@ def load_full(terms, t, n, box, qp: int) -> np.ndarray:
             shp = (s if bits[a] else 1.0 - s) * w * hs[a]
             weight = shp if weight is None else np.multiply.outer(weight, shp)
         # contract quadrature axes: fvals indices (e0,q0,e1,q1,...) with weight (q0,q1,...)
-        contracted = _contract(fvals, weight, d, qp, n)
-        sl = tuple(slice(bits[a], bits[a] + n[a] + 1) for a in range(d))
+        contracted = _contract(fvals, weight, d, qp, ne)
+        sl = tuple(slice(bits[a], bits[a] + ne[a]) for a in range(d))
         F[sl] += contracted
-    inner = tuple(slice(1, -1) for _ in range(d))
-    return F[inner]
+    # Dirichlet axes drop their two boundary nodes; periodic axes fold node n onto node 0
+    for a in range(d):
+        if per[a]:
+            F = np.moveaxis(F, a, 0)
+            F[0] += F[-1]
+            F = np.moveaxis(F[:-1], 0, a)
+        else:
+            F = np.moveaxis(np.moveaxis(F, a, 0)[1:-1], 0, a)
+    return F
 
 
 def _contract(fvals, weight, d, qp, n):
@@ -130,11 +153,13 @@ def _contract(fvals, weight, d, qp, n):
     return np.tensordot(fv, weight, axes=(list(range(d, 2 * d)), list(range(d))))
 
 
-def separable_load_factors(term, n, box, qp: int):
+def separable_load_factors(term, n, box, qp: int, periodic=()):
     """Per-axis 1D consistent loads of one separable term (spatial part only)."""
+    per = tuple(periodic) + (False,) * (len(n) - len(periodic))
     out = []
     for a, fac in enumerate(term.factors):
-        out.append(load_1d(lambda x, fac=fac: eval_factor(fac, x), box[a][0], box[a][1], n[a], qp))
+        load = load_1d_periodic if per[a] else load_1d
+        out.append(load(lambda x, fac=fac: eval_factor(fac, x), box[a][0], box[a][1], n[a], qp))
     return out
 
 

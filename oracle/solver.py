@@ -50,10 +50,13 @@ class ModalSystem:
         self.prob = prob
         self.forcing_route = forcing_route
         n, box, qp = prob.n, prob.box, prob.quad_pts
+        self.periodic = tuple(getattr(prob, "periodic", ())) + (False,) * (prob.d - len(getattr(prob, "periodic", ())))
+        if any(self.periodic) and getattr(prob, "boundary", ()):
+            raise ValueError("Dirichlet data with periodic axes are not supported")
         if basis == "closed_form":
-            self.basis = fem.ClosedFormBasis(n, box, prob.D)
+            self.basis = fem.ClosedFormBasis(n, box, prob.D, self.periodic)
         elif basis == "dense":
-            self.basis = fem.DenseBasis(n, box, prob.D)
+            self.basis = fem.DenseBasis(n, box, prob.D, self.periodic)
         else:
             raise ValueError(basis)
         self.modes = None if modes is None else np.asarray(modes, dtype=np.int64)
@@ -72,7 +75,7 @@ class ModalSystem:
             self.c0 = sum(term.amp * self._separable_modal(term) for term in prob.u0)
         elif forcing_route == "full":
             self._P = None
-            F0 = quadrature.load_full(prob.u0, None, n, box, qp)
+            F0 = quadrature.load_full(prob.u0, None, n, box, qp, self.periodic)
             self.c0 = np.asarray(self.basis.to_modal_from_load(F0)).reshape(-1)
         else:
             raise ValueError(forcing_route)
@@ -88,7 +91,7 @@ class ModalSystem:
     def _separable_modal(self, term) -> np.ndarray:
         """Modal coefficients of P_h of the spatial part of one separable term."""
         prob = self.prob
-        loads = quadrature.separable_load_factors(term, prob.n, prob.box, prob.quad_pts)
+        loads = quadrature.separable_load_factors(term, prob.n, prob.box, prob.quad_pts, self.periodic)
         if isinstance(self.basis, fem.ClosedFormBasis):
             axis = [self.basis.axis_modal_factor(a, loads[a]) for a in range(prob.d)]
             if self.modes is None:
@@ -109,7 +112,7 @@ class ModalSystem:
                 out = out + (term.amp * quadrature.eval_time(term, t)) * P
         else:
             prob = self.prob
-            F = quadrature.load_full(prob.forcing, t, prob.n, prob.box, prob.quad_pts)
+            F = quadrature.load_full(prob.forcing, t, prob.n, prob.box, prob.quad_pts, self.periodic)
             out = np.asarray(self.basis.to_modal_from_load(F)).reshape(-1)
         if self.lift is not None:
             out = out + self._restrict(self.basis.to_modal_from_load(self.lift.extra_load(t)))

@@ -134,6 +134,7 @@ class Problem:
     exact: Optional[Tuple[Term, ...]] = None  # exact solution, when known
     label: str = ""
     boundary: Tuple[Term, ...] = ()          # Dirichlet data: separable terms on the closed box
+    periodic: Tuple[bool, ...] = ()          # per-axis periodic flags (missing = Dirichlet)
 
     @property
     def ndof(self) -> int:
