@@ -398,6 +398,38 @@ def run_cached(pe, args, barrier, u0_dev, u0_host):
     return out
 
 
+def dirichlet_problem():
+    """The main workload with non-homogeneous Dirichlet data: two separable data terms (an
+    exponentially decaying bilinear ramp and an oscillating sine product) on the closed box."""
+    prob = workload()
+    poly = lambda c0, c1: I.Factor(I.S_POLY, (c0, c1, 0.0, 0.0))  # noqa: E731
+    g = (I.Term(0.8, (poly(1.0, 0.5), poly(0.5, -1.0)), I.T_EXP, (-0.5, 0.0)),
+         I.Term(0.3, (I.Factor(I.S_SIN, (2.0, 0.4)), I.Factor(I.S_SIN, (1.5, 0.2))), I.T_SIN, (6.0, 0.3)))
+    return I.Problem(prob.d, prob.n, prob.box, prob.D, prob.t0, prob.T, prob.N, prob.M, prob.fine_nodes,
+                     prob.coarse_nodes, prob.u0, prob.forcing, prob.quad_pts, prob.tol, None,
+                     prob.label + "_dirichlet2", g)
+
+
+def run_dirichlet(pe, args, barrier):
+    """Time to tolerance of the main workload with Dirichlet data (each data term adds 1 + d
+    forcing terms), both forms.  Parity of this path is checked against the oracle in the GPU
+    tests on smaller grids (the oracle's full-grid lifting route is too slow at 255^2)."""
+    prob = dirichlet_problem()
+    out = {"workload": prob.label}
+    for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
+        with pe.Solver(prob, precision=prec) as s:
+            for _ in range(max(1, args.warmup)):
+                s.solve(tol=TOL)
+            barrier()
+            t0 = time.perf_counter()
+            infos = [s.solve(tol=TOL) for _ in range(args.steps)]
+            barrier()
+            dt = (time.perf_counter() - t0) / args.steps
+        out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
+                     "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT}
+    return out
+
+
 DST_SHAPE = (511, 511, 255)
 
 
@@ -508,7 +540,8 @@ def main():
     ap.add_argument("--no-dst", action="store_true", help="skip the standalone DST-I measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the 3D 127^3 precision workload")
     ap.add_argument("--no-cached", action="store_true", help="skip the cached-F^M(0) line")
-    ap.add_argument("--only", choices=["batch", "learned", "general", "dst", "precision", "cached"],
+    ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-data line")
+    ap.add_argument("--only", choices=["batch", "learned", "general", "dst", "precision", "cached", "dirichlet"],
                     help="run one secondary workload alone and print its record (for profiling)")
     args = ap.parse_args()
 
@@ -569,7 +602,8 @@ def main():
                "general": lambda: run_general(pe, args, barrier, u0_dev),
                "dst": lambda: run_dst(pe, args, barrier),
                "precision": lambda: run_precision(pe, args, barrier),
-               "cached": lambda: run_cached(pe, args, barrier, u0_dev, u0_host)}[args.only]
+               "cached": lambda: run_cached(pe, args, barrier, u0_dev, u0_host),
+               "dirichlet": lambda: run_dirichlet(pe, args, barrier)}[args.only]
         rec = run()
         if rank == 0:
             print(json.dumps({"section": args.only, **rec}))
@@ -597,6 +631,7 @@ def main():
         dst = None if args.no_dst else run_dst(pe, args, barrier)
         precision = None if args.no_precision else run_precision(pe, args, barrier)
         cached = None if args.no_cached else run_cached(pe, args, barrier, u0_dev, u0_host)
+        dirichlet = None if args.no_dirichlet else run_dirichlet(pe, args, barrier)
     clock = clocks.summary()
 
     # max over ranks
@@ -708,6 +743,7 @@ def main():
         "dst": dst,
         "precision": precision,
         "affine_cached": cached,
+        "dirichlet": dirichlet,
     }
     print(json.dumps(line))
     if dist is not None:

@@ -312,6 +312,42 @@ __device__ __forceinline__ Cplx<T> ldg_cplx(const Cplx<T>* p) {
 // stores free of bank conflicts
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 
+// Asynchronous global -> shared copies (cp.async, Ampere and later): the strided-pencil
+// paths stage the next block of pencils while the current one is transformed.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Offsets of the P pencils of block blk (o * n * inner + i for pencil p = o * inner + i, -1 past the end).
+__device__ __forceinline__ void block_offsets(int64_t blk, int P, int n, int64_t inner, int64_t npencils,
+                                              int64_t* off) {
+  if ((int)threadIdx.x < P) {
+    const int64_t p = blk * P + threadIdx.x;
+    off[threadIdx.x] = p < npencils ? (p / inner) * (int64_t)n * inner + (p % inner) : -1;
+  }
+}
+
+// Stage the block's rows, stage[pl * n + j] = pencil pl's value j (consecutive threads take
+// consecutive pencils of one row, so each row is one coalesced run); pencils past the end are 0.
+template <typename T>
+__device__ __forceinline__ void stage_block_async(const T* __restrict__ in, const int64_t* off, int P, int logP,
+                                                  int n, int64_t inner, T* stage) {
+  for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+    const int pl = e & (P - 1), j = e >> logP;
+    const int64_t o = off[pl];
+    if (o >= 0) cp_async_elem(stage + pl * n + j, in + o + (int64_t)j * inner);
+    else stage[pl * n + j] = T(0);
+  }
+  cp_async_commit();
+}
+
 constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 __host__ __device__ constexpr int brevc(int i, int bits) {  // bit reversal of i < 32 over `bits` bits
   return (((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4)) >> (5 - bits);
@@ -417,17 +453,19 @@ template <typename T, int LOGL>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGL <= 9) ? 2 : 1) dst_fft_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
                                                            int64_t inner, int64_t npencils, T scale,
                                                            const Cplx<T>* __restrict__ ptw) {
-  constexpr int L = 1 << LOGL, N = L / 2, PADL = L + L / 16;
+  // PS: pair-buffer stride, one more than the padded length so that the pair buffers of a
+  // block start in different banks (the strided load and store walk across pairs)
+  constexpr int L = 1 << LOGL, N = L / 2, PADL = L + L / 16, PS = PADL + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int B = blockDim.x, WARPS = B >> 5, P = 2 * WARPS, logP = __ffs(P) - 1;
   Cplx<T>* bufs = reinterpret_cast<Cplx<T>*>(smem_raw);
-  int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)WARPS * PADL);
+  int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)WARPS * PS);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (inner == 1) {
     // contiguous pencils (last axis): each warp loads, transforms and stores its own pencil
     // pairs (rows of n consecutive values), with no block-wide barrier
     constexpr int JL = (N + 31) / 32;  // values per lane and pencil (n <= N - 1)
-    Cplx<T>* a = bufs + (size_t)warp * PADL;
+    Cplx<T>* a = bufs + (size_t)warp * PS;
     const int64_t npairs = (npencils + 1) / 2;
     for (int64_t pr = (int64_t)blockIdx.x * WARPS + warp; pr < npairs; pr += (int64_t)gridDim.x * WARPS) {
       const int64_t pa = 2 * pr, pb = pa + 1;
@@ -470,59 +508,49 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGL <= 9) ? 2 : 1) ds
     }
     return;
   }
-  // strided pencils: the block stages P consecutive pencils so that each row j is one
-  // contiguous run of P values
+  // strided pencils: blocks of P consecutive pencils, each row j one contiguous run of P
+  // values; the next block's rows are staged (cp.async) while this block is transformed
   const int64_t nblk = (npencils + P - 1) / P;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int64_t p0 = blk * P;
-    if (tid < P) {
-      const int64_t p = p0 + tid;
-      off[tid] = p < npencils ? (p / inner) * (int64_t)n * inner + (p % inner) : -1;
-    }
+  int64_t* offs[2] = {off, off + P};
+  T* stage = reinterpret_cast<T*>(off + 2 * P);
+  int cur = 0;
+  if ((int64_t)blockIdx.x < nblk) {
+    block_offsets(blockIdx.x, P, n, inner, npencils, offs[0]);
     __syncthreads();
-    // the fixed points of the odd extension
+    stage_block_async(in, offs[0], P, logP, n, inner, stage);
+  }
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x, cur ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    // z_j = x_j + i y_j at j = 1..n, -z_j at L - j, 0 at the fixed points 0 and N
     if (tid < 2 * WARPS) {
-      Cplx<T>* a = bufs + (size_t)(tid >> 1) * PADL;
+      Cplx<T>* a = bufs + (size_t)(tid >> 1) * PS;
       a[fpad((tid & 1) ? N : 0)] = Cplx<T>{T(0), T(0)};
     }
-    // load: z_j = x_j + i y_j at j = 1..n and -z_j at L - j.  U loads per thread are issued
-    // back to back before any of them is placed, so one DRAM latency covers U values.
-    const int total = P * n;
-    constexpr int U = sizeof(T) == 4 ? 16 : 8;
-    for (int e0 = 0; e0 < total; e0 += U * B) {
-      T r[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * B + tid;
-        r[u] = T(0);
-        if (e < total) {
-          const int64_t o = off[e & (P - 1)];
-          if (o >= 0) r[u] = in[o + (int64_t)(e >> logP) * inner];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * B + tid;
-        if (e < total) {
-          const int pl = e & (P - 1), j = e >> logP;
-          Cplx<T>* a = bufs + (size_t)(pl >> 1) * PADL;
-          reinterpret_cast<T*>(a + fpad(j + 1))[pl & 1] = r[u];
-          reinterpret_cast<T*>(a + fpad(L - 1 - j))[pl & 1] = -r[u];
-        }
-      }
+    for (int e = tid; e < P * n; e += B) {
+      const int pl = e & (P - 1), j = e >> logP;
+      const T v = stage[pl * n + j];
+      Cplx<T>* a = bufs + (size_t)(pl >> 1) * PS;
+      reinterpret_cast<T*>(a + fpad(j + 1))[pl & 1] = v;
+      reinterpret_cast<T*>(a + fpad(L - 1 - j))[pl & 1] = -v;
     }
     __syncthreads();
-    StockhamPasses<T, LOGL, LOGL, 1>::run(bufs + (size_t)warp * PADL, ptw, lane);
+    const int64_t next = blk + gridDim.x;
+    if (next < nblk) {
+      block_offsets(next, P, n, inner, npencils, offs[cur ^ 1]);
+      __syncthreads();
+      stage_block_async(in, offs[cur ^ 1], P, logP, n, inner, stage);
+    }
+    StockhamPasses<T, LOGL, LOGL, 1>::run(bufs + (size_t)warp * PS, ptw, lane);
     __syncthreads();
     // store: DST(x)_k = -Im Z_k / 2, DST(y)_k = Re Z_k / 2 (times sqrt(2/(n+1)))
-    for (int e = tid; e < total; e += B) {
+    for (int e = tid; e < P * n; e += B) {
       const int pl = e & (P - 1), k = e >> logP;
-      const Cplx<T> Z = bufs[(size_t)(pl >> 1) * PADL + fpad(k + 1)];
+      const Cplx<T> Z = bufs[(size_t)(pl >> 1) * PS + fpad(k + 1)];
       const T val = (pl & 1) ? Z.re * scale : -Z.im * scale;
-      const int64_t o = off[pl];
+      const int64_t o = offs[cur][pl];
       if (o >= 0) out[o + (int64_t)k * inner] = val;
     }
-    __syncthreads();
   }
 }
 
@@ -640,13 +668,13 @@ template <typename T, int LOGN>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
     dst_half_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int64_t inner, int64_t npencils,
                          T scale, const Cplx<T>* __restrict__ ptw, const T* __restrict__ sinN) {
-  constexpr int N = 1 << LOGN, PADN = N + N / 16, JL = N / 32;
+  constexpr int N = 1 << LOGN, PADN = N + N / 16, PS = PADN + 1, JL = N / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int B = blockDim.x, WARPS = B >> 5, P = 2 * WARPS, logP = __ffs(P) - 1;
   Cplx<T>* bufs = reinterpret_cast<Cplx<T>*>(smem_raw);
-  int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)WARPS * PADN);
+  int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)WARPS * PS);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  Cplx<T>* a = bufs + (size_t)warp * PADN;
+  Cplx<T>* a = bufs + (size_t)warp * PS;
   if (inner == 1) {
     const int64_t npairs = (npencils + 1) / 2;
     for (int64_t pr = (int64_t)blockIdx.x * WARPS + warp; pr < npairs; pr += (int64_t)gridDim.x * WARPS) {
@@ -684,47 +712,39 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
     }
     return;
   }
+  // strided pencils: as in dst_fft_warp_kernel, the next block is staged while this one runs
   const int64_t nblk = (npencils + P - 1) / P;
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int64_t p0 = blk * P;
-    if (tid < P) {
-      const int64_t p = p0 + tid;
-      off[tid] = p < npencils ? (p / inner) * (int64_t)n * inner + (p % inner) : -1;
-    }
-    if (tid < WARPS) bufs[(size_t)tid * PADN] = Cplx<T>{T(0), T(0)};
+  int64_t* offs[2] = {off, off + P};
+  T* stage = reinterpret_cast<T*>(off + 2 * P);
+  int cur = 0;
+  if ((int64_t)blockIdx.x < nblk) {
+    block_offsets(blockIdx.x, P, n, inner, npencils, offs[0]);
     __syncthreads();
-    const int total = P * n;
-    constexpr int U = sizeof(T) == 4 ? 16 : 8;
-    for (int e0 = 0; e0 < total; e0 += U * B) {
-      T r[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * B + tid;
-        r[u] = T(0);
-        if (e < total) {
-          const int64_t o = off[e & (P - 1)];
-          if (o >= 0) r[u] = in[o + (int64_t)(e >> logP) * inner];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + u * B + tid;
-        if (e < total) {
-          const int pl = e & (P - 1), j = e >> logP;
-          reinterpret_cast<T*>(bufs + (size_t)(pl >> 1) * PADN + fpad(j + 1))[pl & 1] = r[u];
-        }
-      }
+    stage_block_async(in, offs[0], P, logP, n, inner, stage);
+  }
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x, cur ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid < WARPS) bufs[(size_t)tid * PS] = Cplx<T>{T(0), T(0)};
+    for (int e = tid; e < P * n; e += B) {
+      const int pl = e & (P - 1), j = e >> logP;
+      reinterpret_cast<T*>(bufs + (size_t)(pl >> 1) * PS + fpad(j + 1))[pl & 1] = stage[pl * n + j];
     }
     __syncthreads();
+    const int64_t next = blk + gridDim.x;
+    if (next < nblk) {
+      block_offsets(next, P, n, inner, npencils, offs[cur ^ 1]);
+      __syncthreads();
+      stage_block_async(in, offs[cur ^ 1], P, logP, n, inner, stage);
+    }
     half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
     __syncthreads();
-    for (int e = tid; e < total; e += B) {
+    for (int e = tid; e < P * n; e += B) {
       const int pl = e & (P - 1), k = e >> logP;
-      const Cplx<T> F = bufs[(size_t)(pl >> 1) * PADN + fpad(k + 1)];
-      const int64_t o = off[pl];
+      const Cplx<T> F = bufs[(size_t)(pl >> 1) * PS + fpad(k + 1)];
+      const int64_t o = offs[cur][pl];
       if (o >= 0) out[o + (int64_t)k * inner] = ((pl & 1) ? F.im : F.re) * scale;
     }
-    __syncthreads();
   }
 }
 
@@ -813,15 +833,16 @@ const T* half_sines(int logn, cudaStream_t st) {
 
 // warps per CTA: as many (up to 8, float64 up to 4) as still give >= 2 CTAs per SM
 template <typename T>
-pe_status fft_grid(const void* kern, int64_t npencils, size_t smem_per_warp, int* warps_out, size_t* smem_out,
-                   int64_t* grid_out) {
+pe_status fft_grid(const void* kern, int64_t npencils, size_t smem_per_warp, size_t stage_per_pencil,
+                   int* warps_out, size_t* smem_out, int64_t* grid_out) {
   int dev = 0, sms = 0;
   PE_CUDA_TRY(cudaGetDevice(&dev));
   PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int warps = sizeof(T) == 4 ? 8 : 4;
   while (warps > 1 && (npencils + 2 * warps - 1) / (2 * warps) < 2 * (int64_t)sms) warps >>= 1;
   const int P = 2 * warps;
-  const size_t smem = smem_per_warp * (size_t)warps + sizeof(int64_t) * P;
+  // pair buffers, two offset lists, and (strided launches) the staged rows of one block
+  const size_t smem = smem_per_warp * (size_t)warps + 2 * sizeof(int64_t) * P + stage_per_pencil * P;
   if (smem > 48 * 1024) PE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
@@ -843,7 +864,8 @@ pe_status fft_half_launch(const T* in, T* out, int n, int64_t inner, int64_t npe
   int warps = 1;
   size_t smem = 0;
   int64_t grid = 1;
-  PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * PADN, &warps, &smem, &grid));
+  PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * (PADN + 1), inner > 1 ? sizeof(T) * n : 0, &warps,
+                     &smem, &grid));
   const T scale = (T)sqrt(2.0 / (double)N);
   kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, ptw, sinN);
   PE_CUDA_TRY(cudaGetLastError());
@@ -860,7 +882,8 @@ pe_status fft_warp_launch(const T* in, T* out, int n, int64_t inner, int64_t npe
   int warps = 1;
   size_t smem = 0;
   int64_t grid = 1;
-  PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * PADL, &warps, &smem, &grid));
+  PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * (PADL + 1), inner > 1 ? sizeof(T) * n : 0, &warps,
+                     &smem, &grid));
   kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, ptw);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
