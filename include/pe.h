@@ -109,6 +109,12 @@ typedef struct {
                            propagator is affine: F^M(v) = exp(-lam M dt) v + F^M(0)); later
                            iterations then run no fine sweep.  Separable forcing only; the
                            float64 refinement of a mixed run makes its own float64 copy. */
+  int32_t periodic_mask;  /* bit a set: axis a is periodic -- n_a nodes x_k = lo + k h, k < n_a,
+                             h = (hi - lo)/n_a, node n_a identified with node 0; the circulant Q1
+                             matrices are diagonalised by the discrete Hartley transform
+                             (DHT) in place of the DST-I, theta_j = 2 pi j / n_a, and the mode
+                             j = 0 of an all-periodic problem has lam = 0.  Not with Dirichlet
+                             data or the learned correction. */
 } pe_options;
 
 /* Initial data: u0 = sum of separable terms (time factors ignored), projected

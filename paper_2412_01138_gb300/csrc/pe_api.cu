@@ -240,6 +240,14 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     delete c;
     return pe_fail(PE_EINVAL, "pe_setup: bad forcing_path");
   }
+  if (o.periodic_mask < 0 || o.periodic_mask >= (1 << d)) {
+    delete c;
+    return pe_fail(PE_EINVAL, "pe_setup: periodic_mask has bits beyond the problem's axes");
+  }
+  for (int a = 0; a < PE_MAX_D; ++a) {
+    c->g.per[a] = a < d ? ((o.periodic_mask >> a) & 1) : 0;
+    if (c->g.per[a]) c->h[a] = (c->hi[a] - c->lo[a]) / (double)n[a];  // n nodes, node n is node 0
+  }
   if (o.cache_forced && o.forcing_path == PE_FORCING_GENERAL) {
     delete c;
     return pe_fail(PE_EINVAL, "pe_setup: cache_forced needs PE_FORCING_SEPARABLE");
@@ -302,9 +310,9 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   for (int i = 0; i < 8 && st == PE_OK; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = pe_cuda_fail(cudaGetLastError(), "cudaEventCreate");
   if (st == PE_OK) st = launch_axis_tables(c);
-  for (int a = 0; a < d && st == PE_OK; ++a) st = build_dst_matrix(n[a], c->S[a], c->stream);
+  for (int a = 0; a < d && st == PE_OK; ++a) st = build_dst_matrix(n[a], c->S[a], c->stream, c->g.per[a]);
   for (int a = 0; a < d && st == PE_OK; ++a)
-    if (c->S32[a]) st = build_dst_matrix_f32(n[a], c->S32[a], c->stream);
+    if (c->S32[a]) st = build_dst_matrix_f32(n[a], c->S32[a], c->stream, c->g.per[a]);
   if (st == PE_OK) st = launch_coef_tables(c);
   if (st == PE_OK) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -396,6 +404,8 @@ extern "C" pe_status pe_set_dirichlet(pe_ctx* c, int32_t n_terms, const pe_term*
   PE_TRY(pe_validate_terms(n_terms, g, c->g.d, "Dirichlet data"));
   if (n_terms > 0 && c->forcing_path == PE_FORCING_GENERAL)
     return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data need PE_FORCING_SEPARABLE");
+  if (n_terms > 0 && (c->g.per[0] || c->g.per[1] || c->g.per[2]))
+    return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data with periodic axes");
   c->nbd = n_terms;
   for (int i = 0; i < n_terms; ++i) c->bterms[i] = g[i];
   c->have_problem = false;  // the next pe_set_problem / pe_solve takes the data into account
@@ -413,6 +423,8 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   if (general && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: the learned correction needs PE_FORCING_SEPARABLE");
   if (c->nbd > 0 && general) return pe_fail(PE_EINVAL, "pe_set_problem: Dirichlet data need PE_FORCING_SEPARABLE");
   if (c->nbd > 0 && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: Dirichlet data and the learned correction");
+  const bool any_periodic = c->g.per[0] || c->g.per[1] || c->g.per[2];
+  if (any_periodic && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: periodic axes and the learned correction");
   memset(c->lkind, 0, sizeof(c->lkind));
   if (nf == 0 && c->nbd == 0) {
     // no source: one zero term keeps every kernel shape valid

@@ -955,9 +955,10 @@ pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int
 }
 
 template <typename T>
-pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_t inner, cudaStream_t st) {
+pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_t inner, cudaStream_t st,
+                   int periodic = 0) {
   int logL = 0;
-  if (fft_size_ok(n, &logL)) return fft_axis<T>(in, out, outer, n, inner, logL, st);
+  if (!periodic && fft_size_ok(n, &logL)) return fft_axis<T>(in, out, outer, n, inner, logL, st);
   // matrix form: large tiles when they still give >= 2 CTAs per SM, else small ones
   const int64_t rows = inner == 1 ? outer : n;
   const int64_t cols = inner == 1 ? n : inner;
@@ -969,7 +970,8 @@ pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_
 
 // Apply S_a along every axis; tmp (ndof elements) may be null when d == 1 and in != out.
 template <typename T>
-pe_status dst_nd(int d, const int* n, T* const* S, const T* in, T* out, T* tmp, cudaStream_t st) {
+pe_status dst_nd(int d, const int* n, T* const* S, const T* in, T* out, T* tmp, cudaStream_t st,
+                 const int* per = nullptr) {
   int64_t ndof = 1;
   for (int a = 0; a < d; ++a) ndof *= n[a];
   const T* src = in;
@@ -982,7 +984,7 @@ pe_status dst_nd(int d, const int* n, T* const* S, const T* in, T* out, T* tmp, 
     int64_t outer = 1, inner = 1;
     for (int b = 0; b < a; ++b) outer *= n[b];
     for (int b = a + 1; b < d; ++b) inner *= n[b];
-    PE_TRY(dst_axis<T>(S[a], src, dst, outer, n[a], inner, st));
+    PE_TRY(dst_axis<T>(S[a], src, dst, outer, n[a], inner, st, per ? per[a] : 0));
     src = dst;
   }
   return PE_OK;
@@ -1034,18 +1036,18 @@ pe_status standalone_dst(int32_t d, const int32_t* n, const T* in, T* out, void*
 }  // namespace
 
 pe_status dst_axis_f64(const double* S, const double* in, double* out, int64_t outer, int n, int64_t inner,
-                       cudaStream_t st) {
-  return dst_axis<double>(S, in, out, outer, n, inner, st);
+                       cudaStream_t st, int periodic) {
+  return dst_axis<double>(S, in, out, outer, n, inner, st, periodic);
 }
 
 pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t outer, int n, int64_t inner,
-                       cudaStream_t st) {
-  return dst_axis<float>(S, in, out, outer, n, inner, st);
+                       cudaStream_t st, int periodic) {
+  return dst_axis<float>(S, in, out, outer, n, inner, st, periodic);
 }
 
 pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out) {
   c->launches += c->g.d;
-  return dst_nd<double>(c->g.d, c->g.n, c->S, in, out, c->work1, c->stream);
+  return dst_nd<double>(c->g.d, c->g.n, c->S, in, out, c->work1, c->stream, c->g.per);
 }
 
 extern "C" pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, void* stream) {

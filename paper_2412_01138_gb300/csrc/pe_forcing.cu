@@ -108,12 +108,15 @@ __global__ void loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, doub
     out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = v;
     return;
   }
-  // element k spans nodes k, k+1 (this node is its right vertex: shape s);
-  // element k+1 spans nodes k+1, k+2 (this node is its left vertex: shape 1-s)
+  // Dirichlet: node k sits at lo + (k+1) h; element k ([lo + k h, lo + (k+1) h]) has it as
+  // right vertex (shape s), element k+1 as left vertex (shape 1-s).  Periodic: node k sits
+  // at lo + k h; the elements are k-1 (element n-1 for k = 0) and k.
+  const int el = g.per[a] ? (k == 0 ? g.n[a] - 1 : k - 1) : k;
+  const int er = g.per[a] ? k : k + 1;
   double left = 0.0, right = 0.0;
   for (int qi = 0; qi < G.npts; ++qi) {
-    const double xl = lo + ((double)k + G.s[qi]) * h;
-    const double xr = lo + ((double)(k + 1) + G.s[qi]) * h;
+    const double xl = lo + ((double)el + G.s[qi]) * h;
+    const double xr = lo + ((double)er + G.s[qi]) * h;
     left += G.w[qi] * eval_space(t.skind[a], t.sp[a], xl) * G.s[qi];
     right += G.w[qi] * eval_space(t.skind[a], t.sp[a], xr) * (1.0 - G.s[qi]);
   }
@@ -267,7 +270,7 @@ pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, 
   if (mode == 0) return PE_OK;
   for (int a = 0; a < c->g.d; ++a) {
     const int64_t base = (int64_t)nterms * c->g.off[a];
-    PE_TRY(dst_axis_f64(c->S[a], loads + base, axis_out + base, nterms, c->g.n[a], 1, c->stream));
+    PE_TRY(dst_axis_f64(c->S[a], loads + base, axis_out + base, nterms, c->g.n[a], 1, c->stream, c->g.per[a]));
     c->launches += 1;
   }
   if (mode == 2) return PE_OK;  // V^T of nodal values: no division by mu^M

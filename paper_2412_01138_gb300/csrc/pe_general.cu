@@ -68,11 +68,14 @@ __global__ void __launch_bounds__(128) gen_loads_kernel(TermsDev T, Geom g, doub
   const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
   const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
   const pe_term& tm = T.t[r];
-  // elements k0 .. k0 + 128 (the last one only for its falling part)
+  // elements k0 .. k0 + 128 (the last one only for its falling part); on a periodic axis
+  // node k's elements are k-1 and k, i.e. k0-1 .. k0+127 taken modulo n
+  const bool per = g.per[a] != 0;
   for (int i = threadIdx.x; i <= 128; i += blockDim.x) {
-    const int m = k0 + i;
+    int m = per ? k0 - 1 + i : k0 + i;
+    if (per) m = (m + n) % n;
     TL up = TL(0), dn = TL(0);
-    if (m <= n) {
+    if (per || m <= n) {
       for (int qi = 0; qi < Q.npts; ++qi) {
         const TL x = (TL)(lo + ((double)m + Q.s[qi]) * h);
         TL gv;
@@ -282,9 +285,9 @@ pe_status stage_transforms(pe_ctx* c, const StageGen& SG, int count, T* out, T* 
     for (int b = 0; b < a; ++b) outer *= c->g.n[b];
     for (int b = a + 1; b < c->g.d; ++b) inner *= c->g.n[b];
     if constexpr (sizeof(T) == 8)
-      PE_TRY(dst_axis_f64(c->S[a], src, dst, outer, c->g.n[a], inner, c->stream));
+      PE_TRY(dst_axis_f64(c->S[a], src, dst, outer, c->g.n[a], inner, c->stream, c->g.per[a]));
     else
-      PE_TRY(dst_axis_f32(c->S32[a], src, dst, outer, c->g.n[a], inner, c->stream));
+      PE_TRY(dst_axis_f32(c->S32[a], src, dst, outer, c->g.n[a], inner, c->stream, c->g.per[a]));
     c->launches += 1;
     src = dst;
   }

@@ -35,8 +35,9 @@ pe_status pe_cuda_fail(cudaError_t err, const char* what);
 // ---------------------------------------------------------------------------
 struct Geom {
   int d;
-  int n[PE_MAX_D];        // interior nodes per axis
+  int n[PE_MAX_D];        // interior nodes per axis (all nodes of a periodic axis)
   int off[PE_MAX_D];      // offset of axis a in concatenated per-axis tables
+  int per[PE_MAX_D];      // 1: periodic axis (DHT basis), 0: Dirichlet (DST-I basis)
   int64_t ndof;
 };
 
@@ -157,8 +158,8 @@ pe_status pe_validate_terms(int n, const pe_term* t, int d, const char* what, bo
 // pe_tables.cu
 pe_status launch_axis_tables(pe_ctx* c);
 pe_status launch_coef_tables(pe_ctx* c);
-pe_status build_dst_matrix(int n, double* S, cudaStream_t st);
-pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st);
+pe_status build_dst_matrix(int n, double* S, cudaStream_t st, int periodic = 0);  // DST-I, or the DHT
+pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st, int periodic = 0);
 
 // pe_forcing.cu
 pe_status launch_time_tables(pe_ctx* c);   // also sets c->K, c->cols and Zst
@@ -171,10 +172,11 @@ pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* ter
 pe_status launch_forcing_modal(pe_ctx* c, double t, double* out);
 
 // pe_dst.cu
+// periodic: the axis' transform is the DHT held in S (matrix form; no FFT)
 pe_status dst_axis_f64(const double* S, const double* in, double* out, int64_t outer, int n, int64_t inner,
-                       cudaStream_t st);
+                       cudaStream_t st, int periodic = 0);
 pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t outer, int n, int64_t inner,
-                       cudaStream_t st);
+                       cudaStream_t st, int periodic = 0);
 pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);  // uses c->S, c->work1
 
 // pe_sweep.cu

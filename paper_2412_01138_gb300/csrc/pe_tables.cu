@@ -25,9 +25,16 @@ __global__ void axis_tables_kernel(Geom g, double h0, double h1, double h2, doub
   const int j = blockIdx.x * blockDim.x + threadIdx.x;  // 0-based mode index, mode number j+1
   if (a >= g.d || j >= g.n[a]) return;
   const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
-  const double np1 = (double)(g.n[a] + 1);
-  const double cth = cospi((double)(j + 1) / np1);
-  const double sh = sinpi((double)(j + 1) / (2.0 * np1));
+  // theta = (j+1) pi/(n+1) (Dirichlet, DST-I) or 2 pi j/n (periodic, DHT)
+  double cth, sh;
+  if (g.per[a]) {
+    cth = cospi(2.0 * (double)j / (double)g.n[a]);
+    sh = sinpi((double)j / (double)g.n[a]);
+  } else {
+    const double np1 = (double)(g.n[a] + 1);
+    cth = cospi((double)(j + 1) / np1);
+    sh = sinpi((double)(j + 1) / (2.0 * np1));
+  }
   const double mM = (h / 3.0) * (2.0 + cth);
   const double mK = (4.0 / h) * (sh * sh);
   muM[g.off[a] + j] = mM;
@@ -73,13 +80,25 @@ __global__ void coef_tables_kernel(Geom g, const double* __restrict__ ratio, dou
   }
 }
 
-__global__ void dst_matrix_kernel(int n, double* S) {
+// DST-I (Dirichlet) or, for a periodic axis, the DHT H[j][k] = (cos + sin)(2 pi j k/n)/sqrt(n)
+// (j k reduced modulo the period in both cases)
+__device__ inline double axis_transform_entry(int n, int j, int k, int periodic) {
+  if (periodic) {
+    const int64_t m = ((int64_t)j * k) % n;
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n, &s, &c);
+    return (c + s) / sqrt((double)n);
+  }
+  const int64_t period = 2 * (int64_t)(n + 1);
+  const int64_t m = ((int64_t)(j + 1) * (k + 1)) % period;
+  return sqrt(2.0 / (double)(n + 1)) * sinpi((double)m / (double)(n + 1));
+}
+
+__global__ void dst_matrix_kernel(int n, double* S, int periodic) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (k >= n || j >= n) return;
-  const int64_t period = 2 * (int64_t)(n + 1);
-  const int64_t m = ((int64_t)(j + 1) * (k + 1)) % period;
-  S[(int64_t)j * n + k] = sqrt(2.0 / (double)(n + 1)) * sinpi((double)m / (double)(n + 1));
+  S[(int64_t)j * n + k] = axis_transform_entry(n, j, k, periodic);
 }
 
 }  // namespace
@@ -112,25 +131,23 @@ pe_status launch_coef_tables(pe_ctx* c) {
   return PE_OK;
 }
 
-__global__ void dst_matrix_f32_kernel(int n, float* S) {
+__global__ void dst_matrix_f32_kernel(int n, float* S, int periodic) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (k >= n || j >= n) return;
-  const int64_t period = 2 * (int64_t)(n + 1);
-  const int64_t m = ((int64_t)(j + 1) * (k + 1)) % period;
-  S[(int64_t)j * n + k] = (float)(sqrt(2.0 / (double)(n + 1)) * sinpi((double)m / (double)(n + 1)));
+  S[(int64_t)j * n + k] = (float)axis_transform_entry(n, j, k, periodic);
 }
 
-pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st) {
+pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st, int periodic) {
   dim3 grid((n + 127) / 128, n);
-  dst_matrix_f32_kernel<<<grid, 128, 0, st>>>(n, S);
+  dst_matrix_f32_kernel<<<grid, 128, 0, st>>>(n, S, periodic);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
 
-pe_status build_dst_matrix(int n, double* S, cudaStream_t st) {
+pe_status build_dst_matrix(int n, double* S, cudaStream_t st, int periodic) {
   dim3 grid((n + 127) / 128, n);
-  dst_matrix_kernel<<<grid, 128, 0, st>>>(n, S);
+  dst_matrix_kernel<<<grid, 128, 0, st>>>(n, S, periodic);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

@@ -57,7 +57,7 @@ class pe_tableau(C.Structure):
 class pe_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("dst_backend", C.c_int32), ("quad_pts", C.c_int32),
                 ("max_iter", C.c_int32), ("cuda_stream", C.c_void_p), ("forcing_path", C.c_int32),
-                ("cache_forced", C.c_int32)]
+                ("cache_forced", C.c_int32), ("periodic_mask", C.c_int32)]
 
 
 class pe_field(C.Structure):
@@ -207,8 +207,9 @@ class Solver:
             coarse = pe_tableau(prob.p, C.cast(self._cG, C.POINTER(C.c_double)), 0, 0)
         else:
             coarse = pe_tableau(prob.p, None, 1, random_coarse_seed)
+        mask = sum(1 << a for a, p in enumerate(getattr(prob, "periodic", ())) if p)
         opt = pe_options(precision, dst_backend, prob.quad_pts, max_iter, stream_handle(stream), forcing_path,
-                         1 if cache_forced else 0)
+                         1 if cache_forced else 0, mask)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup(C.byref(ctx), prob.d, n, box, prob.D, prob.t0, prob.T, prob.N, prob.M,
                                   C.byref(fine), C.byref(coarse), C.byref(opt)))
