@@ -430,6 +430,39 @@ def run_dirichlet(pe, args, barrier):
     return out
 
 
+def periodic_problem():
+    """The main workload's forcing and slices on a grid periodic along x (256 nodes) and
+    Dirichlet along y (255 interior nodes)."""
+    prob = workload()
+    return I.Problem(prob.d, (256, 255), prob.box, prob.D, prob.t0, prob.T, prob.N, prob.M, prob.fine_nodes,
+                     prob.coarse_nodes, prob.u0, prob.forcing, prob.quad_pts, prob.tol, None,
+                     "d2_n256p_x_255_N32_M64_bumps8", (), (True, False))
+
+
+def run_periodic(pe, args, barrier):
+    """Time to tolerance with a periodic axis (DHT basis along x), both forms, and the error
+    against the oracle on sampled modes."""
+    prob = periodic_problem()
+    out = {"workload": prob.label}
+    rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=19)
+    w = sys_.norm_w
+    for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
+        with pe.Solver(prob, precision=prec) as s:
+            for _ in range(max(1, args.warmup)):
+                s.solve(tol=TOL)
+            barrier()
+            t0 = time.perf_counter()
+            infos = [s.solve(tol=TOL) for _ in range(args.steps)]
+            barrier()
+            dt = (time.perf_counter() - t0) / args.steps
+            m = s.modal(prob.N)
+        out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
+                     "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
+                     "rel_l2_vs_oracle": float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) /
+                                               np.sqrt(np.sum(w * ref.U[-1] ** 2)))}
+    return out
+
+
 DST_SHAPE = (511, 511, 255)
 
 
@@ -541,7 +574,9 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the 3D 127^3 precision workload")
     ap.add_argument("--no-cached", action="store_true", help="skip the cached-F^M(0) line")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-data line")
-    ap.add_argument("--only", choices=["batch", "learned", "general", "dst", "precision", "cached", "dirichlet"],
+    ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-axis line")
+    ap.add_argument("--only", choices=["batch", "learned", "general", "dst", "precision", "cached", "dirichlet",
+                                       "periodic"],
                     help="run one secondary workload alone and print its record (for profiling)")
     args = ap.parse_args()
 
@@ -603,7 +638,8 @@ def main():
                "dst": lambda: run_dst(pe, args, barrier),
                "precision": lambda: run_precision(pe, args, barrier),
                "cached": lambda: run_cached(pe, args, barrier, u0_dev, u0_host),
-               "dirichlet": lambda: run_dirichlet(pe, args, barrier)}[args.only]
+               "dirichlet": lambda: run_dirichlet(pe, args, barrier),
+               "periodic": lambda: run_periodic(pe, args, barrier)}[args.only]
         rec = run()
         if rank == 0:
             print(json.dumps({"section": args.only, **rec}))
@@ -632,6 +668,7 @@ def main():
         precision = None if args.no_precision else run_precision(pe, args, barrier)
         cached = None if args.no_cached else run_cached(pe, args, barrier, u0_dev, u0_host)
         dirichlet = None if args.no_dirichlet else run_dirichlet(pe, args, barrier)
+        periodic = None if args.no_periodic else run_periodic(pe, args, barrier)
     clock = clocks.summary()
 
     # max over ranks
@@ -744,6 +781,7 @@ def main():
         "precision": precision,
         "affine_cached": cached,
         "dirichlet": dirichlet,
+        "periodic": periodic,
     }
     print(json.dumps(line))
     if dist is not None:

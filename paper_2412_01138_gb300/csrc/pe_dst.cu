@@ -662,12 +662,39 @@ __device__ __forceinline__ void half_dst_pair(Cplx<T>* a, const Cplx<T>* __restr
   __syncwarp();
 }
 
+// Discrete Hartley transform of a pencil pair of N = 2^LOGN points (a periodic axis): with
+// Z = FFT(x^a + i x^b), X^a = (Z_k + conj Z_{N-k})/2, X^b = (Z_k - conj Z_{N-k})/(2i) and
+// H_k = Re X_k - Im X_k.  On entry a[fpad(j)] = (x^a_j, x^b_j), j = 0..N-1; on exit
+// a[fpad(k)] = (H^a_k, H^b_k) (unscaled).
+template <typename T, int LOGN>
+__device__ __forceinline__ void dht_pair(Cplx<T>* a, const Cplx<T>* __restrict__ ptw, int lane) {
+  constexpr int N = 1 << LOGN, C = N / 32;
+  HalfPasses<T, LOGN, LOGN, 1>::run(a, ptw, lane);
+  Cplx<T> hv[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int k = lane * C + c;
+    const Cplx<T> Z = a[fpad(k)];
+    const Cplx<T> Wm = a[fpad((N - k) & (N - 1))];
+    const T rea = T(0.5) * (Z.re + Wm.re), ima = T(0.5) * (Z.im - Wm.im);
+    const T reb = T(0.5) * (Z.im + Wm.im), imb = T(0.5) * (Wm.re - Z.re);
+    hv[c] = Cplx<T>{rea - ima, reb - imb};
+  }
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < C; ++c) a[fpad(lane * C + c)] = hv[c];
+  __syncwarp();
+}
+
 // blockDim.x = 32 * warps; one warp per pencil pair (P = 2 * warps pencils per block of
 // work for strided pencils).
-template <typename T, int LOGN>
+// DHT = true: the same machinery computes the discrete Hartley transform of periodic
+// pencils (n = N points, positions 0..N-1, no fold).
+template <typename T, int LOGN, bool DHT = false>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
     dst_half_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int64_t inner, int64_t npencils,
                          T scale, const Cplx<T>* __restrict__ ptw, const T* __restrict__ sinN) {
+  constexpr int SH = DHT ? 0 : 1;  // buffer position of value j
   constexpr int N = 1 << LOGN, PADN = N + N / 16, PS = PADN + 1, JL = N / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int B = blockDim.x, WARPS = B >> 5, P = 2 * WARPS, logP = __ffs(P) - 1;
@@ -689,21 +716,22 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
         ra[t] = j < n ? xa[j] : T(0);
         rb[t] = (j < n && has_b) ? xb[j] : T(0);
       }
-      if (lane == 0) a[fpad(0)] = Cplx<T>{T(0), T(0)};
+      if (!DHT && lane == 0) a[fpad(0)] = Cplx<T>{T(0), T(0)};
 #pragma unroll
       for (int t = 0; t < JL; ++t) {
         const int j = lane + 32 * t;
-        if (j < n) a[fpad(j + 1)] = Cplx<T>{ra[t], rb[t]};
+        if (j < n) a[fpad(j + SH)] = Cplx<T>{ra[t], rb[t]};
       }
       __syncwarp();
-      half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
+      if constexpr (DHT) dht_pair<T, LOGN>(a, ptw, lane);
+      else half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
       T* ya = out + pa * n;
       T* yb = out + pb * n;
 #pragma unroll
       for (int t = 0; t < JL; ++t) {
         const int k = lane + 32 * t;
         if (k < n) {
-          const Cplx<T> F = a[fpad(k + 1)];
+          const Cplx<T> F = a[fpad(k + SH)];
           ya[k] = F.re * scale;
           if (has_b) yb[k] = F.im * scale;
         }
@@ -725,10 +753,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
   for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x, cur ^= 1) {
     cp_async_wait_all();
     __syncthreads();
-    if (tid < WARPS) bufs[(size_t)tid * PS] = Cplx<T>{T(0), T(0)};
+    if (!DHT && tid < WARPS) bufs[(size_t)tid * PS] = Cplx<T>{T(0), T(0)};
     for (int e = tid; e < P * n; e += B) {
       const int pl = e & (P - 1), j = e >> logP;
-      reinterpret_cast<T*>(bufs + (size_t)(pl >> 1) * PS + fpad(j + 1))[pl & 1] = stage[pl * n + j];
+      reinterpret_cast<T*>(bufs + (size_t)(pl >> 1) * PS + fpad(j + SH))[pl & 1] = stage[pl * n + j];
     }
     __syncthreads();
     const int64_t next = blk + gridDim.x;
@@ -737,11 +765,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
       __syncthreads();
       stage_block_async(in, offs[cur ^ 1], P, logP, n, inner, stage);
     }
-    half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
+    if constexpr (DHT) dht_pair<T, LOGN>(a, ptw, lane);
+    else half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
     __syncthreads();
     for (int e = tid; e < P * n; e += B) {
       const int pl = e & (P - 1), k = e >> logP;
-      const Cplx<T> F = bufs[(size_t)(pl >> 1) * PS + fpad(k + 1)];
+      const Cplx<T> F = bufs[(size_t)(pl >> 1) * PS + fpad(k + SH)];
       const int64_t o = offs[cur][pl];
       if (o >= 0) out[o + (int64_t)k * inner] = ((pl & 1) ? F.im : F.re) * scale;
     }
@@ -853,6 +882,41 @@ pe_status fft_grid(const void* kern, int64_t npencils, size_t smem_per_warp, siz
   return PE_OK;
 }
 
+// DHT of periodic pencils with n = N = 2^LOGN points
+template <typename T, int LOGN>
+pe_status fft_dht_launch(const T* in, T* out, int64_t inner, int64_t npencils, cudaStream_t st) {
+  constexpr int N = 1 << LOGN, PADN = N + N / 16;
+  constexpr int NTW = half_tw_entries<T>(LOGN, 1, LOGN);
+  const Cplx<T>* ptw = pass_twiddles<T, true>(LOGN, NTW, st);
+  if (!ptw) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  auto kern = dst_half_warp_kernel<T, LOGN, true>;
+  int warps = 1;
+  size_t smem = 0;
+  int64_t grid = 1;
+  PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * (PADN + 1), inner > 1 ? sizeof(T) * N : 0, &warps,
+                     &smem, &grid));
+  const T scale = (T)(1.0 / sqrt((double)N));
+  kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, N, inner, npencils, scale, ptw, nullptr);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+template <typename T>
+pe_status dht_fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, cudaStream_t st, bool* done) {
+  const int64_t np = outer * inner;
+  *done = true;
+  switch (n) {
+    case 128: return fft_dht_launch<T, 7>(in, out, inner, np, st);
+    case 256: return fft_dht_launch<T, 8>(in, out, inner, np, st);
+    case 512: return fft_dht_launch<T, 9>(in, out, inner, np, st);
+    case 1024: return fft_dht_launch<T, 10>(in, out, inner, np, st);
+    default:
+      break;
+  }
+  *done = false;
+  return PE_OK;
+}
+
 template <typename T, int LOGN>
 pe_status fft_half_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, cudaStream_t st) {
   constexpr int N = 1 << LOGN, PADN = N + N / 16;
@@ -959,6 +1023,11 @@ pe_status dst_axis(const T* S, const T* in, T* out, int64_t outer, int n, int64_
                    int periodic = 0) {
   int logL = 0;
   if (!periodic && fft_size_ok(n, &logL)) return fft_axis<T>(in, out, outer, n, inner, logL, st);
+  if (periodic) {
+    bool done = false;
+    PE_TRY(dht_fft_axis<T>(in, out, outer, n, inner, st, &done));
+    if (done) return PE_OK;
+  }
   // matrix form: large tiles when they still give >= 2 CTAs per SM, else small ones
   const int64_t rows = inner == 1 ? outer : n;
   const int64_t cols = inner == 1 ? n : inner;

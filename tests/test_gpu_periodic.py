@@ -45,8 +45,11 @@ def _problem(n, periodic, N=4, M=6, seed=8, forcing=True):
                      u0, f, 3, 1e-12, None, "periodic", (), tuple(periodic))
 
 
+# n = 128 .. 1024 periodic axes run the DHT through the FFT kernels (contiguous and strided);
+# other sizes through the DHT matrix
 CASES = [((64,), (True,)), ((37,), (True,)), ((32, 27), (True, False)), ((20, 31), (False, True)),
-         ((24, 18), (True, True)), ((8, 9, 10), (True, False, True))]
+         ((24, 18), (True, True)), ((8, 9, 10), (True, False, True)), ((256,), (True,)),
+         ((128, 40), (True, False)), ((13, 512), (False, True)), ((1024,), (True,))]
 
 
 @pytest.mark.parametrize("n,periodic", CASES)
@@ -66,8 +69,9 @@ def test_periodic_iterates_match_oracle(pe, n, periodic):
     assert _rel(got, sys_.to_nodal(ref.U[-1])) <= 1e-12
 
 
-def test_periodic_mixed_precision(pe):
-    prob = _problem((48, 33), (True, False))
+@pytest.mark.parametrize("n", [(48, 33), (256, 33)])
+def test_periodic_mixed_precision(pe, n):
+    prob = _problem(n, (True, False))
     sys_ = osolver.ModalSystem(prob)
     fine = osolver.sequential_fine(sys_)
     with pe.Solver(prob, precision=pe.PE_MIXED) as s:
@@ -76,20 +80,22 @@ def test_periodic_mixed_precision(pe):
             assert _rel(s.modal(n_), fine[n_], sys_.norm_w) <= 1e-6, n_
 
 
-def test_periodic_general_path_moving_hat(pe):
+@pytest.mark.parametrize("nx,precision", [(24, "fp64"), (128, "fp64"), (128, "mixed")])
+def test_periodic_general_path_moving_hat(pe, nx, precision):
     box = ((0.0, 1.0), (0.0, 1.0))
     hat = I.Term(2.0, (I.Factor(I.S_MOVING_HAT, (0.5, 0.45, 1.0, 0.1)), I.Factor(I.S_SIN, (math.pi, 0.0))))
     u0 = (I.Term(1.0, (I.Factor(I.S_SIN, (2 * math.pi, 0.2)), I.Factor(I.S_SIN, (math.pi, 0.0)))),)
-    prob = I.Problem(2, (24, 19), box, 0.1, 0.0, 1.0, 3, 4, I.uniform_nodes(3), I.uniform_nodes(2), u0, (hat,),
+    prob = I.Problem(2, (nx, 19), box, 0.1, 0.0, 1.0, 3, 4, I.uniform_nodes(3), I.uniform_nodes(2), u0, (hat,),
                      3, 1e-12, None, "periodic_hat", (), (True, False))
     sys_ = osolver.ModalSystem(prob, forcing_route="full")
     ref = osolver.parareal(sys_, tol=0.0, k_max=2)
-    with pe.Solver(prob, forcing_path=pe.PE_FORCING_GENERAL) as s:
+    prec, bound = (pe.PE_FP64, 1e-12) if precision == "fp64" else (pe.PE_MIXED, 1e-6)
+    with pe.Solver(prob, precision=prec, forcing_path=pe.PE_FORCING_GENERAL) as s:
         s.set_problem()
         for _ in range(2):
             s.iterate()
         for n_ in range(1, prob.N + 1):
-            assert _rel(s.modal(n_), ref.U[n_], sys_.norm_w) <= 1e-12, n_
+            assert _rel(s.modal(n_), ref.U[n_], sys_.norm_w) <= bound, n_
 
 
 def test_constant_mode_is_kept_when_every_axis_is_periodic(pe):
