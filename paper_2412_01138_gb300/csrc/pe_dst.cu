@@ -991,6 +991,9 @@ pe_status fft_warp_axis(const T* in, T* out, int64_t outer, int n, int64_t inner
   return PE_OK;
 }
 
+// Pencil count up to which the block-wide kernel is used (two pencils per SM of 152).
+constexpr int64_t kFewPencils = 2 * 152;
+
 template <typename T>
 pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, cudaStream_t st) {
   const int L = 1 << logL;
@@ -998,9 +1001,12 @@ pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int
   const Cplx<T>* tw = twiddles<T>(logL, st);
   if (!tw) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
   bool done = false;
-  PE_TRY(fft_warp_axis<T>(in, out, outer, n, inner, logL, st, &done));
+  // Few pencils (small problems, the per-axis source factors): a warp per pencil pair
+  // would leave most SMs idle behind the FFT's chain of dependent float64 latencies, so
+  // those go to the block-wide kernel, which spreads every pencil pair over a CTA.
+  if (npencils > kFewPencils) PE_TRY(fft_warp_axis<T>(in, out, outer, n, inner, logL, st, &done));
   if (done) return PE_OK;
-  // short transforms (n + 1 < 16) and float64 at n + 1 = 1024: the block-wide radix-2 kernel;
+  // few pencils, short transforms (n + 1 < 16) and float64 at n + 1 = 1024: the block-wide radix-2 kernel;
   // pencil pairs per CTA: as many as keep >= 2 CTAs per SM, bounded by shared memory
   int max_pairs = (int)((48 * 1024) / ((size_t)L * sizeof(Cplx<T>)));
   max_pairs = max_pairs < 1 ? 1 : (max_pairs > 16 ? 16 : max_pairs);

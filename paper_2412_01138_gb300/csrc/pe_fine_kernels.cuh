@@ -49,22 +49,20 @@ struct FineTile {
   double* Fn;             // F^M(U^n), or F^M(0) when from_zero
 };
 
-// Mixed precision, K columns staged as KC = roundup(K, 4) floats per substep so
-// that each float4 broadcast load feeds 4*MPT FMAs; the padding lanes are skipped.
+// Mixed precision, K columns stored as KC = roundup(K, 4) floats per substep
+// (zero padding, [N][M][KC] in the float time table) so that each float4
+// broadcast load feeds 4*MPT FMAs; the padding lanes are skipped.
+//
+// W and the hi/lo E_F of the MPT modes base + k*blockDim.x (zero past the end).
 template <int K, int MPT>
-__device__ __forceinline__ void fine_mixed_tile(const FineTile& a, float* sY) {
-  constexpr int KC = (K + 3) / 4 * 4;
-  const int M = a.M, B = blockDim.x;
+__device__ __forceinline__ void mixed_load_weights(const FineTile& a, int64_t base, float (&W)[MPT][K],
+                                                   float (&eh)[MPT], float (&el)[MPT]) {
   const int64_t nd = a.ndof;
-  const int64_t base = a.base + threadIdx.x;
-  float W[MPT][K];
-  float eh[MPT], el[MPT], w[MPT];
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
-    const int64_t J = base + (int64_t)B * k;
+    const int64_t J = base + (int64_t)blockDim.x * k;
     eh[k] = 0.f;
     el[k] = 0.f;
-    w[k] = 0.f;
 #pragma unroll
     for (int c = 0; c < K; ++c) W[k][c] = 0.f;
     if (J < nd) {
@@ -74,43 +72,123 @@ __device__ __forceinline__ void fine_mixed_tile(const FineTile& a, float* sY) {
       el[k] = a.coefF32[nd + J];
     }
   }
-  for (int m0 = 0; m0 < M; m0 += a.mchunk) {
-    const int mc = min(a.mchunk, M - m0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < mc * KC; t += B) {
-      const int row = t / KC, c = t - row * KC;
-      sY[t] = c < K ? a.Yn32[(int64_t)(m0 + row) * K + c] : 0.f;
-    }
-    __syncthreads();
-    // two substeps per trip: the second substep's broadcast loads and FMA chains are
-    // independent of the first one's recurrence, so they overlap its latency
+}
+
+// mc substeps of the float32 forced recurrence w <- E_F w + sum_k Y_k(t_m) W_k
+// from the staged time factors sY[m*KC + k].
+template <int K, int MPT>
+__device__ __forceinline__ void mixed_substeps(const float* sY, int mc, const float (&W)[MPT][K],
+                                               const float (&eh)[MPT], const float (&el)[MPT], float (&w)[MPT]) {
+  constexpr int KC = (K + 3) / 4 * 4;
+  // two substeps per trip: the second substep's broadcast loads and FMA chains are
+  // independent of the first one's recurrence, so they overlap its latency
 #pragma unroll 2
-    for (int m = 0; m < mc; ++m) {
-      const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
-      float acc[MPT];
+  for (int m = 0; m < mc; ++m) {
+    const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
+    float acc[MPT];
 #pragma unroll
-      for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
+    for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
 #pragma unroll
-      for (int c4 = 0; c4 < KC / 4; ++c4) {
-        const float4 v = y4[c4];
-        const float vv[4] = {v.x, v.y, v.z, v.w};
+    for (int c4 = 0; c4 < KC / 4; ++c4) {
+      const float4 v = y4[c4];
+      const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (4 * c4 + e < K) {
+      for (int e = 0; e < 4; ++e) {
+        if (4 * c4 + e < K) {
 #pragma unroll
-            for (int k = 0; k < MPT; ++k) acc[k] = fmaf(vv[e], W[k][4 * c4 + e], acc[k]);
-          }
+          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(vv[e], W[k][4 * c4 + e], acc[k]);
         }
       }
-#pragma unroll
-      for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
     }
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
   }
+}
+
+// F^M(U^n) = exp(-lam M dt) U^n + w (float64), or w alone when from_zero.
+template <int MPT>
+__device__ __forceinline__ void mixed_store(const FineTile& a, int64_t base, const double* Un, double* Fn,
+                                            const float (&w)[MPT]) {
+  const int64_t nd = a.ndof;
   const double* EM = a.coefF + (int64_t)(a.q + 1) * nd;
 #pragma unroll
   for (int k = 0; k < MPT; ++k) {
-    const int64_t J = base + (int64_t)B * k;
-    if (J < nd) a.Fn[J] = a.from_zero ? (double)w[k] : fma(EM[J], a.Un[J], (double)w[k]);
+    const int64_t J = base + (int64_t)blockDim.x * k;
+    if (J < nd) Fn[J] = a.from_zero ? (double)w[k] : fma(EM[J], Un[J], (double)w[k]);
+  }
+}
+
+template <int K, int MPT>
+__device__ __forceinline__ void fine_mixed_tile(const FineTile& a, float* sY) {
+  constexpr int KC = (K + 3) / 4 * 4;
+  const int M = a.M, B = blockDim.x;
+  const int64_t base = a.base + threadIdx.x;
+  float W[MPT][K], eh[MPT], el[MPT], w[MPT];
+  mixed_load_weights<K, MPT>(a, base, W, eh, el);
+#pragma unroll
+  for (int k = 0; k < MPT; ++k) w[k] = 0.f;
+  for (int m0 = 0; m0 < M; m0 += a.mchunk) {
+    const int mc = min(a.mchunk, M - m0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < mc * KC; t += B) sY[t] = a.Yn32[(int64_t)m0 * KC + t];
+    __syncthreads();
+    mixed_substeps<K, MPT>(sY, mc, W, eh, el, w);
+  }
+  mixed_store<MPT>(a, base, a.Un, a.Fn, w);
+}
+
+// 16-byte asynchronous global -> shared copies (cp.async, waited on per group).
+__device__ __forceinline__ void y_copy16(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void y_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void y_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+// Persistent form of the mixed kernel.  The work items are (mode tile, slice)
+// pairs, tile-major, I = tiles * N of them; CTA b runs the contiguous range
+// [b I / G, (b+1) I / G) of a grid of G resident CTAs.  W and the hi/lo E_F stay
+// in registers until the range crosses a tile boundary (once or twice per CTA
+// instead of once per slice), and the next item's [M][KC] time factors are staged
+// by cp.async into the other half of a double buffer while the current item runs.
+template <int K, int MPT>
+__global__ void __launch_bounds__(256, 2) fine_mixed_persistent_kernel(FineTile t, int N, int64_t n_items) {
+  constexpr int KC = (K + 3) / 4 * 4;
+  extern __shared__ __align__(16) float sYb[];
+  const int B = blockDim.x;
+  const int64_t nd = t.ndof;
+  const int slab = t.M * KC;  // floats per slice, a multiple of 4
+  const int64_t i0 = (int64_t)blockIdx.x * n_items / gridDim.x;
+  const int64_t i1 = (int64_t)(blockIdx.x + 1) * n_items / gridDim.x;
+  auto stage = [&](int64_t i, int buf) {
+    const float4* src = reinterpret_cast<const float4*>(t.Yn32 + (i % N) * slab);
+    float4* dst = reinterpret_cast<float4*>(sYb + buf * slab);
+    for (int e = threadIdx.x; e < slab / 4; e += B) y_copy16(dst + e, src + e);
+    y_commit();
+  };
+  float W[MPT][K], eh[MPT], el[MPT];
+  int64_t loaded = -1;
+  if (i0 < i1) stage(i0, 0);
+  for (int64_t i = i0; i < i1; ++i) {
+    const int buf = (int)((i - i0) & 1);
+    const int64_t tile = i / N, n = i - tile * N;
+    // the other buffer was last read by the previous item, which ended with a barrier
+    if (i + 1 < i1) stage(i + 1, buf ^ 1);
+    const int64_t base = tile * (int64_t)(B * MPT) + threadIdx.x;
+    if (tile != loaded) {
+      mixed_load_weights<K, MPT>(t, base, W, eh, el);
+      loaded = tile;
+    }
+    if (i + 1 < i1) y_wait<1>();
+    else y_wait<0>();
+    __syncthreads();
+    float w[MPT];
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) w[k] = 0.f;
+    mixed_substeps<K, MPT>(sYb + buf * slab, t.M, W, eh, el, w);
+    mixed_store<MPT>(t, base, t.Un + n * nd, t.Fn + n * nd, w);
+    __syncthreads();
   }
 }
 
@@ -193,18 +271,33 @@ pe_status fine_launch(pe_ctx* c, int precision, int from_zero, double* out) {
   t.from_zero = from_zero;
   t.Un = c->U;
   t.Fn = out;
-  const int64_t stride = (int64_t)c->M * K;
   if (precision == PE_MIXED) {
     constexpr int MPT = K <= 24 ? 4 : (K <= 40 ? 2 : 1);
     constexpr int KC = (K + 3) / 4 * 4;
-    t.mchunk = pick_mchunk(c->M, KC, sizeof(float));
     const int64_t per_cta = (int64_t)threads * MPT;
-    dim3 grid((unsigned)((c->g.ndof + per_cta - 1) / per_cta), c->N);
-    fine_mixed_kernel<K, MPT><<<grid, threads, sizeof(float) * t.mchunk * KC, c->stream>>>(t, stride);
+    const int64_t tiles = (c->g.ndof + per_cta - 1) / per_cta;
+    const size_t slab_bytes = sizeof(float) * (size_t)c->M * KC;
+    if (2 * slab_bytes <= 48 * 1024) {
+      // persistent: one resident wave of CTAs over the (tile, slice) items
+      int dev = 0, sms = 0, occ = 0;
+      PE_CUDA_TRY(cudaGetDevice(&dev));
+      PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fine_mixed_persistent_kernel<K, MPT>,
+                                                                threads, 2 * slab_bytes));
+      if (occ < 1) return pe_fail(PE_EINVAL, "fine sweep: persistent kernel does not fit an SM");
+      const int64_t items = tiles * c->N;
+      const int64_t grid = items < (int64_t)sms * occ ? items : (int64_t)sms * occ;
+      fine_mixed_persistent_kernel<K, MPT><<<(unsigned)grid, threads, 2 * slab_bytes, c->stream>>>(t, c->N, items);
+    } else {
+      t.mchunk = pick_mchunk(c->M, KC, sizeof(float));
+      dim3 grid((unsigned)tiles, c->N);
+      fine_mixed_kernel<K, MPT><<<grid, threads, sizeof(float) * t.mchunk * KC, c->stream>>>(
+          t, (int64_t)c->M * KC);
+    }
   } else {
     t.mchunk = pick_mchunk(c->M, K, sizeof(double));
     dim3 grid((unsigned)((c->g.ndof + threads - 1) / threads), c->N);
-    fine_f64_kernel<K><<<grid, threads, sizeof(double) * t.mchunk * K, c->stream>>>(t, stride);
+    fine_f64_kernel<K><<<grid, threads, sizeof(double) * t.mchunk * K, c->stream>>>(t, (int64_t)c->M * K);
   }
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());

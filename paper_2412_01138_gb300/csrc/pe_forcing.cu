@@ -18,7 +18,8 @@
 namespace {
 
 // Time tables of one problem, one thread per entry:
-//   AF[(n*M + m)*K + k] = Y_k(T_n + m dt)   (fine substep starts, stage-contracted columns)
+//   AF[(n*M + m)*K + k] = Y_k(T_n + m dt)   (fine substep starts, stage-contracted columns;
+//                                            the float copy AF32 has rows of roundup(K, 4))
 //   AG[(n*p + i)*R + r] = amp_r time_r(T_n + c_i dT)   (coarse stage times)
 //   Z[i*K + k]          = Z_k(c_i dt)       (shift of column k to fine stage i)
 __global__ void time_tables_kernel(TermsDev T, StageCols C, int N, int M, int q, int p, double t0, double dT,
@@ -41,7 +42,14 @@ __global__ void time_tables_kernel(TermsDev T, StageCols C, int N, int M, int q,
     if (C.kind[k] == 1) v = tr.amp * cos(tr.tp[0] * t + tr.tp[1]);  // partner of a sinusoid
     else v = tr.amp * eval_time(tr, t);
     AF[idx] = v;
-    if (AF32) AF32[idx] = (float)v;
+    if (AF32) {
+      // float copy padded to KC = roundup(K, 4) columns: [N][M][KC], zeros past K
+      const int KC = (K + 3) & ~3;
+      float* row = AF32 + ((int64_t)n * M + m) * KC;
+      row[k] = (float)v;
+      if (k == K - 1)
+        for (int e = K; e < KC; ++e) row[e] = 0.f;
+    }
   } else if (idx < nf + ng) {
     int64_t rest = idx - nf;
     const int r = (int)(rest % R); rest /= R;

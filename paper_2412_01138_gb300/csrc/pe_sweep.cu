@@ -15,48 +15,106 @@
 namespace {
 
 // Coarse forcing of every slice, in parallel over slices: each thread owns one
-// mode and SL consecutive slices; its weights P_{r,J} sit in a column of shared
-// memory (R x blockDim doubles / floats), so R is a run-time value.  T = double
-// on the float64 path; float in the mixed form, where gG only enters through
+// mode and SL consecutive slices.  Its weights P_{r,J} sit in registers, padded
+// with zeros to RB = roundup(R, 4) terms; the CTA's coarse time factors
+// A_r(T_n + c_i dT) (n in its slice range) are staged in shared memory, rows of RB
+// with zero padding, and read as float4 / double2 broadcasts.  T = double on the
+// float64 path; float in the mixed form, where gG only enters through
 // G(U^{new}) - G(U^{old}), in which the same stored gG cancels.
-template <typename T>
+template <typename T, int RB>
 __global__ void __launch_bounds__(256) coarse_forcing_kernel(Geom g, int N, int p, int R, int SL,
                                                             const T* __restrict__ axisF, const T* __restrict__ AG,
                                                             const double* __restrict__ coefG,
                                                             double* __restrict__ gG) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sP = reinterpret_cast<T*>(smem_raw);  // [R][blockDim.x]
+  T* sA = reinterpret_cast<T*>(smem_raw);  // [SL * p][RB]
+  const int n0 = blockIdx.y * SL;
+  const int n1 = min(N, n0 + SL);
+  for (int e = threadIdx.x; e < (n1 - n0) * p * RB; e += blockDim.x) {
+    const int row = e / RB, r = e - row * RB;
+    sA[e] = r < R ? AG[((int64_t)n0 * p + row) * R + r] : T(0);
+  }
+  __syncthreads();
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   const int64_t nd = g.ndof;
-  const int tid = threadIdx.x, B = blockDim.x;
   int j[PE_MAX_D];
   unflatten(g, J, j);
-  for (int r = 0; r < R; ++r) {
-    T v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-    for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
-    sP[r * B + tid] = v;
+  T P[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    T v = T(0);
+    if (r < R) {
+      v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+      for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+    }
+    P[r] = v;
   }
   T b[PE_MAX_S];
 #pragma unroll
-  for (int i = 0; i < PE_MAX_S; ++i)
-    if (i < p) b[i] = (T)coefG[(1 + i) * nd + J];
-  const int n0 = blockIdx.y * SL;
-  const int n1 = min(N, n0 + SL);
+  for (int i = 0; i < PE_MAX_S; ++i) b[i] = i < p ? (T)coefG[(1 + i) * nd + J] : T(0);
   for (int n = n0; n < n1; ++n) {
     T acc = T(0);
 #pragma unroll
     for (int i = 0; i < PE_MAX_S; ++i) {
       if (i < p) {
-        const T* a = AG + ((int64_t)n * p + i) * R;
+        const T* a = sA + ((int64_t)(n - n0) * p + i) * RB;
         T gi = T(0);
-        for (int r = 0; r < R; ++r) gi = fma(__ldg(a + r), sP[r * B + tid], gi);
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+          for (int r = 0; r < RB; r += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(a + r);
+            gi = fmaf(v.x, P[r], gi);
+            gi = fmaf(v.y, P[r + 1], gi);
+            gi = fmaf(v.z, P[r + 2], gi);
+            gi = fmaf(v.w, P[r + 3], gi);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < RB; r += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(a + r);
+            gi = fma(v.x, P[r], gi);
+            gi = fma(v.y, P[r + 1], gi);
+          }
+        }
         acc = fma(b[i], gi, acc);
       }
     }
     gG[(int64_t)n * nd + J] = (double)acc;
   }
 }
+
+// The instantiation with RB = roundup(R, 4) (at least 4); SL slices per thread,
+// capped so that the staged time factors fit 48 KB.
+template <typename T>
+pe_status launch_coarse_forcing_t(pe_ctx* c, unsigned blocks, int threads, int SL, const T* axisF, const T* AG) {
+  const int RB = c->R < 4 ? 4 : (c->R + 3) / 4 * 4;  // no source terms: one all-zero group
+  const int sl_max = (int)((48 * 1024) / (sizeof(T) * (size_t)c->p * RB));
+  SL = SL > sl_max ? sl_max : SL;
+  const size_t smem = sizeof(T) * (size_t)SL * c->p * RB;
+  const dim3 grid(blocks, (unsigned)((c->N + SL - 1) / SL));
+  switch (RB) {
+#define PE_CF_CASE(X)                                                                                        \
+  case X:                                                                                                    \
+    coarse_forcing_kernel<T, X><<<grid, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, SL, axisF, AG, \
+                                                                    c->coefG, c->gG);                      \
+    break;
+    PE_CF_CASE(4) PE_CF_CASE(8) PE_CF_CASE(12) PE_CF_CASE(16) PE_CF_CASE(20) PE_CF_CASE(24) PE_CF_CASE(28)
+    PE_CF_CASE(32)
+#undef PE_CF_CASE
+    default:
+      return pe_fail(PE_EINVAL, "coarse forcing: too many source terms");
+  }
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+// Slices of loads each thread keeps in flight in the sequential sweeps below.
+// The recurrence carries one value per mode; its inputs do not depend on it,
+// so the loads of the next kPF slices are issued while the current kPF are
+// combined (one thread per mode leaves too few threads to cover HBM latency
+// with one slice in flight).
+constexpr int kPF = 4;
 
 // Sequential coarse sweep U^{n+1,(0)} = E_G U^{n,(0)} + gG_n (one thread per mode).
 __global__ void __launch_bounds__(256) coarse_recurrence_kernel(Geom g, int N, const double* __restrict__ coefG,
@@ -67,13 +125,26 @@ __global__ void __launch_bounds__(256) coarse_recurrence_kernel(Geom g, int N, c
   const int64_t nd = g.ndof;
   const double E = coefG[J];
   double c = U[J];
-  double gn = gG[J];
-  for (int n = 0; n < N; ++n) {
-    const double gnext = n + 1 < N ? gG[(int64_t)(n + 1) * nd + J] : 0.0;
-    c = fma(E, c, gn);
-    U[(int64_t)(n + 1) * nd + J] = c;
-    Gold[(int64_t)n * nd + J] = c;
-    gn = gnext;
+  double cur[kPF], nxt[kPF];
+#pragma unroll
+  for (int e = 0; e < kPF; ++e) cur[e] = e < N ? gG[(int64_t)e * nd + J] : 0.0;
+  for (int n0 = 0; n0 < N; n0 += kPF) {
+#pragma unroll
+    for (int e = 0; e < kPF; ++e) {
+      const int n = n0 + kPF + e;
+      nxt[e] = n < N ? gG[(int64_t)n * nd + J] : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kPF; ++e) {
+      const int n = n0 + e;
+      if (n < N) {
+        c = fma(E, c, cur[e]);
+        U[(int64_t)(n + 1) * nd + J] = c;
+        Gold[(int64_t)n * nd + J] = c;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < kPF; ++e) cur[e] = nxt[e];
   }
 }
 
@@ -100,39 +171,64 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
                                                          double* __restrict__ U, double* __restrict__ partials) {
   __shared__ double sh[32];
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double sd = 0.0, su = 0.0;
+  double sd = 0.0, su = 0.0, w = 0.0;
   if (J < g.ndof) {
     const int64_t nd = g.ndof;
     int j[PE_MAX_D];
     unflatten(g, J, j);
-    double w = muM_axis[g.off[0] + j[0]];
+    w = muM_axis[g.off[0] + j[0]];
     for (int a = 1; a < g.d; ++a) w *= muM_axis[g.off[a] + j[a]];
     const double E = coefG[J];
     double unew = U[J];
-    // the four streams of slice n+1 are loaded before slice n is combined, so
-    // each thread keeps two slices of loads in flight (the recurrence itself only
-    // carries unew)
-    double g0 = gG[J], f0 = Fbar[J], o0 = Gold[J], u0 = U[nd + J];
-    for (int n = 0; n < N; ++n) {
-      const int64_t o = (int64_t)n * nd + J;
-      double g1 = 0.0, f1 = 0.0, o1 = 0.0, u1 = 0.0;
-      if (n + 1 < N) {
-        g1 = gG[o + nd];
-        f1 = Fbar[o + nd];
-        o1 = Gold[o + nd];
-        u1 = U[o + 2 * nd];
+    // per slice n: gG_n, Fbar^{n+1}, G(U^{n,(k)}) and the old U^{n+1} (for the residual)
+    double g0[kPF], f0[kPF], o0[kPF], u0[kPF], g1[kPF], f1[kPF], o1[kPF], u1[kPF];
+#pragma unroll
+    for (int e = 0; e < kPF; ++e) {
+      const int64_t o = (int64_t)e * nd + J;
+      const bool in = e < N;
+      g0[e] = in ? gG[o] : 0.0;
+      f0[e] = in ? Fbar[o] : 0.0;
+      o0[e] = in ? Gold[o] : 0.0;
+      u0[e] = in ? U[o + nd] : 0.0;
+    }
+    for (int n0 = 0; n0 < N; n0 += kPF) {
+#pragma unroll
+      for (int e = 0; e < kPF; ++e) {
+        const int n = n0 + kPF + e;
+        const int64_t o = (int64_t)n * nd + J;
+        const bool in = n < N;
+        g1[e] = in ? gG[o] : 0.0;
+        f1[e] = in ? Fbar[o] : 0.0;
+        o1[e] = in ? Gold[o] : 0.0;
+        u1[e] = in ? U[o + nd] : 0.0;
       }
-      const double Gn = fma(E, unew, g0);
-      const double nxt = (Gn + f0) - o0;
-      Gold[o] = Gn;
-      U[o + nd] = nxt;
-      const double df = nxt - u0;
-      sd = fma(w * df, df, sd);
-      su = fma(w * nxt, nxt, su);
-      unew = nxt;
-      g0 = g1; f0 = f1; o0 = o1; u0 = u1;
+#pragma unroll
+      for (int e = 0; e < kPF; ++e) {
+        const int n = n0 + e;
+        if (n < N) {
+          const int64_t o = (int64_t)n * nd + J;
+          const double Gn = fma(E, unew, g0[e]);
+          const double nxt = (Gn + f0[e]) - o0[e];
+          Gold[o] = Gn;
+          U[o + nd] = nxt;
+          const double df = nxt - u0[e];
+          sd = fma(df, df, sd);
+          su = fma(nxt, nxt, su);
+          unew = nxt;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kPF; ++e) {
+        g0[e] = g1[e];
+        f0[e] = f1[e];
+        o0[e] = o1[e];
+        u0[e] = u1[e];
+      }
     }
   }
+  // the weight mu^M_J is the same for every slice of the mode: applied once
+  sd *= w;
+  su *= w;
   sd = block_sum(sd, sh);
   su = block_sum(su, sh);
   if (threadIdx.x == 0) {
@@ -172,19 +268,8 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
   int64_t want = (2 * 152 * 2 + blocks - 1) / blocks;
   int SL = (int)((c->N + want - 1) / want);
   SL = SL < 1 ? 1 : SL;
-  dim3 grid(blocks, (unsigned)((c->N + SL - 1) / SL));
-  if (c->precision == PE_MIXED) {
-    const size_t smem = sizeof(float) * (size_t)c->R * threads;
-    coarse_forcing_kernel<float><<<grid, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, SL, c->axisF32, c->AG32,
-                                                                    c->coefG, c->gG);
-  } else {
-    const size_t smem = sizeof(double) * (size_t)c->R * threads;
-    if (smem > 48 * 1024)
-      PE_CUDA_TRY(cudaFuncSetAttribute(coarse_forcing_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    coarse_forcing_kernel<double><<<grid, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, SL, c->axisF, c->AG,
-                                                                     c->coefG, c->gG);
-  }
+  if (c->precision == PE_MIXED) PE_TRY(launch_coarse_forcing_t<float>(c, blocks, threads, SL, c->axisF32, c->AG32));
+  else PE_TRY(launch_coarse_forcing_t<double>(c, blocks, threads, SL, c->axisF, c->AG));
   // learned correction G'(v) = G(v) + delta^ (no-op unless a trained network is attached)
   PE_TRY(launch_learned_correction(c));
   coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U, c->Gold);
