@@ -77,19 +77,28 @@ __global__ void time_tables_kernel(TermsDev T, StageCols C, int N, int M, int q,
 template <typename T>
 __global__ void stage_weights_kernel(Geom g, StageCols C, int R, int q, const T* __restrict__ axisF,
                                      const T* __restrict__ coef, const double* __restrict__ Z, T* __restrict__ W) {
+  // the shifts Z (converted to T once per CTA) and the column -> term map, in shared memory
+  __shared__ T sZ[PE_MAX_S * 2 * PE_MAX_TERMS];
+  __shared__ int sTerm[2 * PE_MAX_TERMS];
+  for (int e = threadIdx.x; e < q * C.K; e += blockDim.x) sZ[e] = (T)Z[e];
+  for (int e = threadIdx.x; e < C.K; e += blockDim.x) sTerm[e] = C.term[e];
+  __syncthreads();
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   const int64_t nd = g.ndof;
   int j[PE_MAX_D];
   unflatten(g, J, j);
   T b[PE_MAX_S];
-  for (int i = 0; i < q; ++i) b[i] = coef[(int64_t)i * nd + J];
+#pragma unroll
+  for (int i = 0; i < PE_MAX_S; ++i) b[i] = i < q ? coef[(int64_t)i * nd + J] : T(0);
   for (int k = 0; k < C.K; ++k) {
-    const int r = C.term[k];
+    const int r = sTerm[k];
     T P = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
     for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     T s = T(0);
-    for (int i = 0; i < q; ++i) s = fma(b[i], (T)Z[i * C.K + k], s);
+#pragma unroll
+    for (int i = 0; i < PE_MAX_S; ++i)
+      if (i < q) s = fma(b[i], sZ[i * C.K + k], s);
     W[(int64_t)k * nd + J] = P * s;
   }
 }
