@@ -108,7 +108,8 @@ __global__ void b_coef_tables_kernel(const BProb* __restrict__ probs, const Mode
 }
 
 // Time tables of every problem, one thread per entry (layout as in the single-problem
-// solver): fine substep starts Y[(n*M + m)*K + k], coarse stage times AG[(n*p + i)*R + r],
+// solver): fine substep starts Y[(n*M + m)*K + k] (float copy: rows of KC = roundup(K, 4)),
+// coarse stage times AG[(n*p + i)*R + r],
 // stage shifts Z[i*K + k].  Column k of a problem is cols[oCol + k] = (term << 1) | kind:
 // kind 0 is amp*time(t) (shift factor e^{as} or cos(ws)), kind 1 the partner amp*cos(wt+phi)
 // of a sinusoid (shift factor sin(ws)).
@@ -135,7 +136,13 @@ __global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int6
     const pe_term& T = terms[B.tf + (c >> 1)];
     const double v = (c & 1) ? T.amp * cos(T.tp[0] * t + T.tp[1]) : T.amp * eval_time(T, t);
     AF[B.oAF + local] = v;
-    if (AF32) AF32[B.oAF + local] = (float)v;
+    if (AF32) {
+      const int KC = (K + 3) & ~3;
+      float* row = AF32 + B.oAF32 + ((int64_t)n * B.M + m) * KC;
+      row[k] = (float)v;
+      if (k == K - 1)
+        for (int e = K; e < KC; ++e) row[e] = 0.f;
+    }
   } else if (local < nf + ng) {
     local -= nf;
     int64_t rest = local;

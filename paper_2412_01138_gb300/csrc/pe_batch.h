@@ -12,6 +12,7 @@ struct BProb {
   int N, M, q, p, R, Ru;   // slices, substeps, fine/coarse stages, forcing / u0 terms
   int K;                   // stage-contracted columns of the fine step (one per exponential, two per sinusoid)
   int mchunk;              // substeps of time factors staged per shared-memory fill
+  int dbuf;                // mixed: 1 if two whole [M][KC] slice blocks fit the staging buffer
   int tf, tu;              // first forcing / u0 term in the terms array
   double D, t0, dT, dt;
   double lo[PE_MAX_D], h[PE_MAX_D];
@@ -23,7 +24,8 @@ struct BProb {
   int64_t oCG;   // coefG arena: (p+1)*ndof
   int64_t oAx;   // axisF / axisF32: R*nsum
   int64_t oAxU;  // axisU0: Ru*nsum
-  int64_t oAF;   // AF / AF32: substep-start time factors Y, N*M*K
+  int64_t oAF;   // AF: substep-start time factors Y, N*M*K
+  int64_t oAF32; // AF32: the same in float, rows padded to KC = roundup(K, 4) (zeros), N*M*KC
   int64_t oW;    // W / W32: per-mode stage weights, K*ndof
   int64_t oZ;    // Z: stage shifts, q*K
   int64_t oCol;  // column map: K entries, (term << 1) | kind

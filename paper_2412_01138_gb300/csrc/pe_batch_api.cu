@@ -75,7 +75,8 @@ pe_status build_fine_items(pe_batch* b, int threads, FineItems* out) {
       const BProb& B = b->probs[p];
       const int KC = (B.K + 3) / 4 * 4;
       if (KC != 4 * (c + 1)) continue;
-      out->smem[c] = std::max(out->smem[c], elem * (size_t)B.mchunk * KC);
+      const size_t need = B.dbuf ? 2 * sizeof(float) * (size_t)B.M * KC : elem * (size_t)B.mchunk * KC;
+      out->smem[c] = std::max(out->smem[c], need);
       const int mpt = b->precision == PE_MIXED ? batch_mixed_mpt(KC) : 1;
       const int64_t tile = (int64_t)threads * mpt;
       for (int64_t J0 = 0; J0 < B.g.ndof; J0 += tile) items.push_back(FineItem{p, 0, J0});
@@ -123,7 +124,7 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
   }
 
   // ---- validate and lay out every problem --------------------------------
-  int64_t oU = 0, oS = 0, oCF = 0, oCG = 0, oAx = 0, oAxU = 0, oAF = 0, oAG = 0, oMu = 0, oItems = 0;
+  int64_t oU = 0, oS = 0, oCF = 0, oCG = 0, oAx = 0, oAxU = 0, oAF = 0, oAF32 = 0, oAG = 0, oMu = 0, oItems = 0;
   int64_t oW = 0, oZ = 0;
   std::vector<int64_t> mu_prefix, tt_prefix;
   std::vector<short> cols;
@@ -214,6 +215,7 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
     const int KC = (B.K + 3) / 4 * 4;
     const size_t elem = b->precision == PE_MIXED ? sizeof(float) : sizeof(double);
     B.mchunk = pick_mchunk(B.M, KC, elem);
+    B.dbuf = b->precision == PE_MIXED && 2 * (size_t)B.M * KC * sizeof(float) <= 48 * 1024 ? 1 : 0;
     B.oU = oU; oU += (int64_t)(B.N + 1) * ndof;
     B.oS = oS; oS += (int64_t)B.N * ndof;
     B.oCF = oCF; oCF += (int64_t)(B.q + 2) * ndof;
@@ -221,6 +223,7 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
     B.oAx = oAx; oAx += (int64_t)B.R * nsum;
     B.oAxU = oAxU; oAxU += (int64_t)B.Ru * nsum;
     B.oAF = oAF; oAF += (int64_t)B.N * B.M * B.K;
+    B.oAF32 = oAF32; oAF32 += (int64_t)B.N * B.M * KC;
     B.oW = oW; oW += (int64_t)B.K * ndof;
     B.oZ = oZ; oZ += (int64_t)B.q * B.K;
     B.oAG = oAG; oAG += (int64_t)B.N * B.p * B.R;
@@ -258,7 +261,7 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
   if (st == PE_OK && mixed) st = balloc(&b->axisF32, oAx);
   if (st == PE_OK) st = balloc(&b->axisU0, oAxU);
   if (st == PE_OK) st = balloc(&b->AF, oAF);
-  if (st == PE_OK && mixed) st = balloc(&b->AF32, oAF);
+  if (st == PE_OK && mixed) st = balloc(&b->AF32, oAF32);
   if (st == PE_OK) st = balloc(&b->AG, oAG);
   if (st == PE_OK && mixed) st = balloc(&b->AG32, oAG);
   if (st == PE_OK) st = balloc(&b->W, oW);

@@ -24,6 +24,45 @@ __device__ __forceinline__ void b_stage_rows(const T* __restrict__ Yn, int K, in
   }
 }
 
+// 16-byte asynchronous global -> shared copies (cp.async, waited on per group).
+__device__ __forceinline__ void b_copy16(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void b_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void b_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+// mc substeps of the float32 forced recurrence from staged rows sY[m*KC + k].
+template <int KC, int MPT>
+__device__ __forceinline__ void b_mixed_substeps(const float* sY, int mc, int K, const float (&W)[MPT][KC],
+                                                 const float (&eh)[MPT], const float (&el)[MPT], float (&w)[MPT]) {
+  // two substeps per trip: the second substep's loads and FMA chains overlap the first's latency
+#pragma unroll 2
+  for (int m = 0; m < mc; ++m) {
+    const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
+    float acc[MPT];
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int c4 = 0; c4 < KC / 4; ++c4) {
+      if (4 * c4 < K) {
+        const float4 v = y4[c4];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int k = 0; k < MPT; ++k) acc[k] = fmaf(vv[e], W[k][4 * c4 + e], acc[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
+  }
+}
+
+// The float time table holds rows of KC floats (zero padded), so a slice's block is
+// contiguous: when two whole blocks fit the staging buffer (P.dbuf), slice n + 1 is
+// staged by cp.async into one half while slice n runs from the other.
 template <int KC, int MPT>
 __device__ __forceinline__ void b_fine_mixed_item(const BProb& P, int64_t J0, const BatchArrays& A, float* sY) {
   const int M = P.M, K = P.K, Bd = blockDim.x;
@@ -32,6 +71,8 @@ __device__ __forceinline__ void b_fine_mixed_item(const BProb& P, int64_t J0, co
   const float* W32 = A.W32 + P.oW;
   const float* cf32 = A.coefF32 + P.oCF;
   const double* EM = A.coefF + P.oCF + (int64_t)(P.q + 1) * nd;
+  const float* Y = A.AF32 + P.oAF32;
+  const int slab = M * KC;  // floats per slice, a multiple of 4
   float W[MPT][KC];
   float eh[MPT], el[MPT];
   double em[MPT];
@@ -45,8 +86,17 @@ __device__ __forceinline__ void b_fine_mixed_item(const BProb& P, int64_t J0, co
     el[k] = on ? cf32[nd + J] : 0.f;
     em[k] = on ? EM[J] : 0.0;
   }
+  auto stage = [&](int n, float* dst) {
+    const float4* src = reinterpret_cast<const float4*>(Y + (int64_t)n * slab);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int e = threadIdx.x; e < slab / 4; e += Bd) b_copy16(d4 + e, src + e);
+    b_commit();
+  };
+  if (P.dbuf) {
+    __syncthreads();  // the previous item's last reads of the buffer are done
+    stage(0, sY);
+  }
   for (int n = 0; n < P.N; ++n) {
-    const float* Yn = A.AF32 + P.oAF + (int64_t)n * M * K;
     const double* Un = A.U + P.oU + (int64_t)n * nd;
     double* Fn = A.Fbar + P.oS + (int64_t)n * nd;
     double u[MPT];
@@ -58,29 +108,26 @@ __device__ __forceinline__ void b_fine_mixed_item(const BProb& P, int64_t J0, co
     float w[MPT];
 #pragma unroll
     for (int k = 0; k < MPT; ++k) w[k] = 0.f;
-    for (int m0 = 0; m0 < M; m0 += P.mchunk) {
-      const int mc = min(P.mchunk, M - m0);
+    if (P.dbuf) {
+      float* cur = sY + (n & 1) * slab;
+      // the other half was last read by slice n - 1, which ended with a barrier
+      if (n + 1 < P.N) {
+        stage(n + 1, sY + ((n + 1) & 1) * slab);
+        b_wait<1>();
+      } else {
+        b_wait<0>();
+      }
       __syncthreads();
-      b_stage_rows<float, KC>(Yn, K, m0, mc, sY);
+      b_mixed_substeps<KC, MPT>(cur, M, K, W, eh, el, w);
       __syncthreads();
-      for (int m = 0; m < mc; ++m) {
-        const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
-        float acc[MPT];
-#pragma unroll
-        for (int k = 0; k < MPT; ++k) acc[k] = 0.f;
-#pragma unroll
-        for (int c4 = 0; c4 < KC / 4; ++c4) {
-          if (4 * c4 < K) {
-            const float4 v = y4[c4];
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-#pragma unroll
-              for (int k = 0; k < MPT; ++k) acc[k] = fmaf(vv[e], W[k][4 * c4 + e], acc[k]);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < MPT; ++k) w[k] = fmaf(eh[k], w[k], fmaf(el[k], w[k], acc[k]));
+    } else {
+      for (int m0 = 0; m0 < M; m0 += P.mchunk) {
+        const int mc = min(P.mchunk, M - m0);
+        __syncthreads();
+        const float* src = Y + (int64_t)n * slab + (int64_t)m0 * KC;
+        for (int t = threadIdx.x; t < mc * KC; t += Bd) sY[t] = src[t];
+        __syncthreads();
+        b_mixed_substeps<KC, MPT>(sY, mc, K, W, eh, el, w);
       }
     }
 #pragma unroll
