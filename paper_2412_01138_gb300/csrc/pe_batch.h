@@ -37,7 +37,7 @@ struct BProb {
 
 // Modes per thread of the mixed-precision fine tile for a problem with K stage columns
 // (the work items and the kernel's tile dispatch both use it).
-__host__ __device__ constexpr int batch_mixed_mpt(int KC) { return KC <= 24 ? 4 : 2; }
+__host__ __device__ constexpr int batch_mixed_mpt(int KC) { return KC <= 16 ? 4 : (KC <= 24 ? 3 : 2); }
 
 struct ModeItem {
   int p;
