@@ -117,7 +117,7 @@ __global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int6
                                      int64_t total, const pe_term* __restrict__ terms,
                                      const short* __restrict__ cols, double* __restrict__ AF,
                                      float* __restrict__ AF32, double* __restrict__ AG, float* __restrict__ AG32,
-                                     double* __restrict__ Z) {
+                                     double* __restrict__ Z, float* __restrict__ Z32) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int p = find_prob(tt_prefix, P, idx);
@@ -165,15 +165,18 @@ __global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int6
     if (T.tkind == PE_T_SIN) v = (c & 1) ? sin(T.tp[0] * s) : cos(T.tp[0] * s);
     else v = exp(T.tp[0] * s);
     Z[B.oZ + local] = v;
+    if (Z32) Z32[B.oZ + local] = (float)v;
   }
 }
 
-// Per-mode stage weights W[oW + k*ndof + J] = P_{r(k),J} sum_i (dt b_i)_J Z[oZ + i*K + k].
+// Per-mode stage weights W[oW + k*ndof + J] = P_{r(k),J} sum_i (dt b_i)_J Z[oZ + i*K + k],
+// in the arithmetic of T: float64 into W for the float64 fine kernel; float32 (from the
+// float factors and shifts) into W32 in the mixed form, whose fine kernel reads only W32.
+template <typename T>
 __global__ void b_stage_weights_kernel(const BProb* __restrict__ probs, const ModeItem* __restrict__ items,
-                                       int n_items, const short* __restrict__ cols,
-                                       const double* __restrict__ axisF, const double* __restrict__ coefF,
-                                       const double* __restrict__ Z, double* __restrict__ W,
-                                       float* __restrict__ W32) {
+                                       int n_items, const short* __restrict__ cols, const T* __restrict__ axisF,
+                                       const double* __restrict__ coefF, const T* __restrict__ Z,
+                                       T* __restrict__ W) {
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const ModeItem mi = items[it];
     const BProb& B = probs[mi.p];
@@ -182,18 +185,20 @@ __global__ void b_stage_weights_kernel(const BProb* __restrict__ probs, const Mo
     const int64_t nd = B.g.ndof;
     int j[PE_MAX_D];
     unflatten(B.g, J, j);
-    double b[PE_MAX_S];
-    for (int i = 0; i < B.q; ++i) b[i] = coefF[B.oCF + (int64_t)(1 + i) * nd + J];
-    const double* ax = axisF + B.oAx;
+    T b[PE_MAX_S];
+#pragma unroll
+    for (int i = 0; i < PE_MAX_S; ++i) b[i] = i < B.q ? (T)coefF[B.oCF + (int64_t)(1 + i) * nd + J] : T(0);
+    const T* ax = axisF + B.oAx;
+    const T* z = Z + B.oZ;
     for (int k = 0; k < B.K; ++k) {
       const int r = cols[B.oCol + k] >> 1;
-      double P = ax[(int64_t)B.R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
+      T P = ax[(int64_t)B.R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
       for (int a = 1; a < B.g.d; ++a) P *= ax[(int64_t)B.R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
-      double sum = 0.0;
-      for (int i = 0; i < B.q; ++i) sum = fma(b[i], Z[B.oZ + (int64_t)i * B.K + k], sum);
-      const double w = P * sum;
-      W[B.oW + (int64_t)k * nd + J] = w;
-      if (W32) W32[B.oW + (int64_t)k * nd + J] = (float)w;
+      T sum = T(0);
+#pragma unroll
+      for (int i = 0; i < PE_MAX_S; ++i)
+        if (i < B.q) sum = fma(b[i], z[(int64_t)i * B.K + k], sum);
+      W[B.oW + (int64_t)k * nd + J] = P * sum;
     }
   }
 }
@@ -270,6 +275,10 @@ __global__ void b_u0_kernel(const BProb* __restrict__ probs, const ModeItem* __r
 }
 
 // coarse sweep (k = 0) of every problem; P_{r,J} staged per thread in shared memory
+// Slices of loads each thread keeps in flight in the sequential correction (its
+// inputs do not depend on the recurrence, so they are fetched kPF slices ahead).
+constexpr int kPF = 4;
+
 template <typename TF>
 __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__ probs,
                                                        const ModeItem* __restrict__ items, int n_items,
@@ -349,12 +358,13 @@ __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restri
     const BProb& B = probs[m.p];
     if (!active[m.p]) continue;  // uniform over the CTA
     const int64_t J = m.J0 + threadIdx.x;
-    double sd = 0.0, su = 0.0;
+    double sd = 0.0, su = 0.0, w = 0.0;
     if (J < B.g.ndof) {
       const int64_t nd = B.g.ndof;
+      const int N = B.N;
       int j[PE_MAX_D];
       unflatten(B.g, J, j);
-      double w = muM[B.oMu + B.g.off[0] + j[0]];
+      w = muM[B.oMu + B.g.off[0] + j[0]];
       for (int a = 1; a < B.g.d; ++a) w *= muM[B.oMu + B.g.off[a] + j[a]];
       const double E = coefG[B.oCG + J];
       double* Up = U + B.oU;
@@ -362,27 +372,55 @@ __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restri
       const double* gp = gG + B.oS;
       const double* fp = Fbar + B.oS;
       double unew = Up[J];
-      double g0 = gp[J], f0 = fp[J], o0 = Gp[J], u0 = Up[nd + J];
-      for (int n = 0; n < B.N; ++n) {
-        const int64_t o = (int64_t)n * nd + J;
-        double g1 = 0.0, f1 = 0.0, o1 = 0.0, u1 = 0.0;
-        if (n + 1 < B.N) {
-          g1 = gp[o + nd];
-          f1 = fp[o + nd];
-          o1 = Gp[o + nd];
-          u1 = Up[o + 2 * nd];
+      // the loads of the next kPF slices are issued while the current kPF are combined
+      double g0[kPF], f0[kPF], o0[kPF], u0[kPF], g1[kPF], f1[kPF], o1[kPF], u1[kPF];
+#pragma unroll
+      for (int e = 0; e < kPF; ++e) {
+        const int64_t o = (int64_t)e * nd + J;
+        const bool in = e < N;
+        g0[e] = in ? gp[o] : 0.0;
+        f0[e] = in ? fp[o] : 0.0;
+        o0[e] = in ? Gp[o] : 0.0;
+        u0[e] = in ? Up[o + nd] : 0.0;
+      }
+      for (int n0 = 0; n0 < N; n0 += kPF) {
+#pragma unroll
+        for (int e = 0; e < kPF; ++e) {
+          const int n = n0 + kPF + e;
+          const int64_t o = (int64_t)n * nd + J;
+          const bool in = n < N;
+          g1[e] = in ? gp[o] : 0.0;
+          f1[e] = in ? fp[o] : 0.0;
+          o1[e] = in ? Gp[o] : 0.0;
+          u1[e] = in ? Up[o + nd] : 0.0;
         }
-        const double Gn = fma(E, unew, g0);
-        const double nxt = (Gn + f0) - o0;
-        Gp[o] = Gn;
-        Up[o + nd] = nxt;
-        const double df = nxt - u0;
-        sd = fma(w * df, df, sd);
-        su = fma(w * nxt, nxt, su);
-        unew = nxt;
-        g0 = g1; f0 = f1; o0 = o1; u0 = u1;
+#pragma unroll
+        for (int e = 0; e < kPF; ++e) {
+          const int n = n0 + e;
+          if (n < N) {
+            const int64_t o = (int64_t)n * nd + J;
+            const double Gn = fma(E, unew, g0[e]);
+            const double nxt = (Gn + f0[e]) - o0[e];
+            Gp[o] = Gn;
+            Up[o + nd] = nxt;
+            const double df = nxt - u0[e];
+            sd = fma(df, df, sd);
+            su = fma(nxt, nxt, su);
+            unew = nxt;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < kPF; ++e) {
+          g0[e] = g1[e];
+          f0[e] = f1[e];
+          o0[e] = o1[e];
+          u0[e] = u1[e];
+        }
       }
     }
+    // the weight mu^M_J is the same for every slice of the mode: applied once
+    sd *= w;
+    su *= w;
     sd = block_sum(sd, sh);
     su = block_sum(su, sh);
     if (threadIdx.x == 0) {
@@ -459,15 +497,20 @@ pe_status batch_launch_prepare(pe_batch* b) {
   const int grid_items = b->sm_count * 8;
   // time factors
   b_time_tables_kernel<<<(unsigned)((b->tt_total + 255) / 256), 256, 0, b->stream>>>(
-      b->d_probs, b->d_tt_prefix, b->P, b->tt_total, b->d_terms, b->d_cols, b->AF, b->AF32, b->AG, b->AG32, b->Z);
+      b->d_probs, b->d_tt_prefix, b->P, b->tt_total, b->d_terms, b->d_cols, b->AF, b->AF32, b->AG, b->AG32, b->Z,
+      b->Z32);
   // per-axis factors of forcing and initial data
   const size_t smem = sizeof(double) * (size_t)(b->nmax + 2 * (b->nmax + 1));
   b_axis_factor_kernel<<<b->n_factor_jobs, 256, smem, b->stream>>>(b->d_probs, b->d_factor_jobs, b->d_terms,
                                                                    b->gauss, b->muM, b->axisF, b->axisF32,
                                                                    b->axisU0);
   // per-mode stage weights of the fine step
-  b_stage_weights_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->d_cols,
-                                                            b->axisF, b->coefF, b->Z, b->W, b->W32);
+  if (b->precision == PE_MIXED)
+    b_stage_weights_kernel<float><<<grid_items, 256, 0, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->d_cols, b->axisF32, b->coefF, b->Z32, b->W32);
+  else
+    b_stage_weights_kernel<double><<<grid_items, 256, 0, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->d_cols, b->axisF, b->coefF, b->Z, b->W);
   b_u0_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->d_terms, b->axisU0,
                                                  b->U);
   // the coarse forcing is iterate-independent and cancels in G(U^{k+1}) - G(U^k): the mixed

@@ -110,6 +110,7 @@ struct pe_batch {
   float* AF32 = nullptr;
   double *W = nullptr, *Z = nullptr;
   float* AG32 = nullptr;
+  float* Z32 = nullptr;  // mixed: float copy of the stage shifts Z
   float* W32 = nullptr;
   short* d_cols = nullptr;
   double* partials = nullptr;

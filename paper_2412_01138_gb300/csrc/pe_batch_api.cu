@@ -41,7 +41,7 @@ void free_batch(pe_batch* b) {
                   b->d_factor_jobs, b->d_mu_prefix, b->d_tt_prefix, b->muM, b->ratio, b->coefF, b->coefG,
                   b->coefF32, b->U, b->Gold, b->Fbar, b->gG, b->axisF, b->axisU0, b->axisF32, b->AF, b->AG,
                   b->AF32, b->partials, b->active, b->kcount, b->resid, b->counter, b->dflags,
-                  b->W, b->W32, b->Z, b->d_cols, b->AG32};
+                  b->W, b->W32, b->Z, b->d_cols, b->AG32, b->Z32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_flags) cudaFreeHost(b->h_flags);
@@ -264,9 +264,11 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
   if (st == PE_OK && mixed) st = balloc(&b->AF32, oAF32);
   if (st == PE_OK) st = balloc(&b->AG, oAG);
   if (st == PE_OK && mixed) st = balloc(&b->AG32, oAG);
-  if (st == PE_OK) st = balloc(&b->W, oW);
+  // float64 weights for the float64 fine kernel; the mixed form keeps only the float copy
+  if (st == PE_OK && !mixed) st = balloc(&b->W, oW);
   if (st == PE_OK && mixed) st = balloc(&b->W32, oW);
   if (st == PE_OK) st = balloc(&b->Z, oZ);
+  if (st == PE_OK && mixed) st = balloc(&b->Z32, oZ);
   if (st == PE_OK) st = balloc(&b->partials, 2 * (size_t)oItems);
   if (st == PE_OK) st = balloc(&b->active, (size_t)b->P);
   if (st == PE_OK) st = balloc(&b->kcount, (size_t)b->P);
