@@ -161,16 +161,20 @@ __global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, 
     buf[(size_t)q * L + (__brev((unsigned)np1) >> shift)] = Cplx<T>{T(0), T(0)};
   }
   // load: consecutive threads take consecutive pencils (coalesced when inner > 1)
-  // or consecutive elements (inner == 1)
+  // or consecutive elements (inner == 1); the (pencil, element) walk advances by
+  // carries instead of a division per element
   const int npen = 2 * pairs;
+  const int fast = inner == 1 ? n : npen;  // extent of the fast index
+  int e_hi = tid / fast, e_lo = tid - (tid / fast) * fast;
+  const int step_hi = B / fast, step_lo = B - (B / fast) * fast;
   for (int e = tid; e < npen * n; e += B) {
-    int pl, j;
-    if (inner == 1) {
-      pl = e / n;
-      j = e - pl * n;
-    } else {
-      j = e / npen;
-      pl = e - j * npen;
+    const int pl = inner == 1 ? e_hi : e_lo;
+    const int j = inner == 1 ? e_lo : e_hi;
+    e_lo += step_lo;
+    e_hi += step_hi;
+    if (e_lo >= fast) {
+      e_lo -= fast;
+      ++e_hi;
     }
     const int64_t p = p0 + pl;
     T v = T(0);
@@ -192,14 +196,14 @@ __global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, 
     }
   }
   __syncthreads();
-  // radix-2 decimation-in-time stages
+  // radix-2 decimation-in-time stages (L and half are powers of two: shifts and masks)
   for (int s = 1; s <= logL; ++s) {
     const int half = 1 << (s - 1);
     const int tstride = L >> s;  // twiddle index stride
     for (int bfly = tid; bfly < pairs * (L / 2); bfly += B) {
-      const int q = bfly / (L / 2);
-      const int r = bfly - q * (L / 2);
-      const int grp = r / half, pos = r - grp * half;
+      const int q = bfly >> (logL - 1);
+      const int r = bfly & (L / 2 - 1);
+      const int grp = r >> (s - 1), pos = r & (half - 1);
       const int i0 = grp * 2 * half + pos, i1 = i0 + half;
       Cplx<T>* row = buf + (size_t)q * L;
       const Cplx<T> w = tw[pos * tstride];
@@ -212,14 +216,16 @@ __global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, 
     __syncthreads();
   }
   // store: DST(x)_k = -Im V_k / 2, DST(y)_k = Re V_k / 2, k = 1..n, times sqrt(2/(n+1))
+  e_hi = tid / fast;
+  e_lo = tid - e_hi * fast;
   for (int e = tid; e < npen * n; e += B) {
-    int pl, k;
-    if (inner == 1) {
-      pl = e / n;
-      k = e - pl * n;
-    } else {
-      k = e / npen;
-      pl = e - k * npen;
+    const int pl = inner == 1 ? e_hi : e_lo;
+    const int k = inner == 1 ? e_lo : e_hi;
+    e_lo += step_lo;
+    e_hi += step_hi;
+    if (e_lo >= fast) {
+      e_lo -= fast;
+      ++e_hi;
     }
     const int64_t p = p0 + pl;
     if (p >= npencils) continue;
