@@ -1,29 +1,33 @@
 // Tensor-core tensor DST-I (mixed precision) on 5th-generation tensor cores.
 //
 // Each axis pass of the orthonormal DST-I (the diagonalising transform of Sec. 2.3)
-// is a contraction out[p][j] = sum_k X_p[k] S[k][j] over the pencils p of that axis.
-// Float32 data are split into nsplit bfloat16 terms x = x0 + x1 (+ x2) and the
-// products that carry about 2^-24 of relative weight are concatenated along K,
-//   nsplit 2:  [x0 x0 x1] . [s0 s1 s0]                (about 16 bits)
-//   nsplit 3:  [x0 x0 x1 x0 x1 x2] . [s0 s1 s0 s2 s1 s0]  (about 24 bits),
-// so one bfloat16 GEMM with float32 accumulation gives the pass.
+// is a contraction out[p][j] = sum_k X_p[k] S[j][k] over the pencils p of that axis.
+// Float32 operands are split into NSPLIT bfloat16 terms x = x0 + x1 (+ x2) and the
+// products that carry about 2^-24 of relative weight are summed,
+//   NSPLIT 2:  x0 s0 + x0 s1 + x1 s0                         (about 16 bits)
+//   NSPLIT 3:  x0 s0 + x0 s1 + x1 s0 + x0 s2 + x1 s1 + x2 s0   (about 24 bits),
+// by bfloat16 MMAs with float32 accumulation.
 //
-// GEMM kernel (one CTA per 128 x 128 output tile, 128 threads):
-//   * operands staged in shared memory by TMA (cp.async.bulk.tensor, 2D tiled
-//     maps, boxes of 8 elements x rows, i.e. the no-swizzle K-major core-matrix
-//     layout: K-chunk c of a stage at c * rows * 16 bytes, 8-row groups 128 bytes
-//     apart), two stages, mbarrier transaction counts;
-//   * one thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128,
-//     N = 128, K = 16 per instruction) with the accumulators in tensor memory,
-//     tcgen05.commit releases each stage.  K tile kt accumulates into TMEM
-//     accumulator kt % 4 (4 x 128 columns): the tensor core's float32
-//     accumulation error grows with the number of products summed into one
-//     accumulator, so four partial sums, added in float32 with round-to-nearest
-//     in the epilogue, cut it about fourfold;
-//   * epilogue: every warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) of each
-//     accumulator and writes its rows straight to the strided destination.
-// Every mbarrier wait is bounded (about a second of clock cycles); on expiry the
-// CTA records an error code, skips the epilogue, frees its tensor memory and exits.
+// Fused pass kernel (one CTA per 128 pencils x 128 outputs, 160 threads):
+//   * warps 0-3 (one pencil row per thread) read the float32 pencils straight from
+//     the strided array, split them and store the bfloat16 terms in shared memory
+//     in the no-swizzle K-major core-matrix layout (K-chunk c of a term at
+//     c * 128 * 16 bytes, row r at r * 16 bytes), so the split operand never goes
+//     through HBM; then fence the async proxy and arrive on the stage's barrier;
+//   * warp 4, one thread: TMA loads of the split DST matrix (prepared once per pass,
+//     2D tiled map, boxes of 8 elements x 128 rows) and the tcgen05.mma issue
+//     (kind::f16, M = N = 128, K = 16), accumulators in tensor memory; K tile kt
+//     accumulates into TMEM accumulator kt % NACC (partial sums added in float32 in
+//     the epilogue: the accumulator's rounding grows with the number of products
+//     summed into it); tcgen05.commit releases each stage and finally the tile;
+//   * STAGES-deep ring of (A, B) stages with full/empty mbarriers, so the split of
+//     the next K tiles and the TMA loads overlap the MMAs;
+//   * epilogue (warps 0-3): tcgen05.ld of each lane's row, partial sums added and
+//     scaled; strided passes store straight (consecutive lanes are consecutive
+//     pencils), the contiguous pass transposes 16-column chunks through shared
+//     memory so that each row is written with consecutive addresses.
+// Every mbarrier wait is bounded (about half a second of clock cycles); on expiry
+// the CTA records an error code, skips the epilogue, frees its tensor memory and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -35,18 +39,29 @@
 
 namespace {
 
-constexpr int TBM = 128;  // rows of a CTA tile (TMEM lanes)
-constexpr int TBN = 128;  // columns of a CTA tile (TMEM columns)
-constexpr int TBK = 64;   // K per stage (4 MMAs of K = 16)
-constexpr int TSTAGES = 2;
-constexpr int NACC = 4;   // TMEM accumulators (NACC * TBN = 512 columns)
-constexpr int A_STAGE_BYTES = TBM * TBK * 2;  // 16 KB
-constexpr int B_STAGE_BYTES = TBN * TBK * 2;  // 16 KB
-constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
-// shared memory: 1 KB alignment slack + stages + a guard region so that no
-// descriptor offset can leave the allocation
-constexpr int TC_SMEM = 1024 + TSTAGES * STAGE_BYTES + 64 * 1024;
-constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int TBM = 128;  // pencils of a CTA tile (TMEM lanes)
+constexpr int TBN = 128;  // outputs of a CTA tile (TMEM columns per accumulator)
+constexpr int TBK = 32;   // K per stage (2 MMA K-steps of 16)
+constexpr int A_TERM = TBM * TBK * 2;  // one bfloat16 split term of the A stage: 8 KB
+constexpr int B_TERM = TBN * TBK * 2;  // one bfloat16 split term of the B stage: 8 KB
+constexpr int TC_THREADS = 160;
+constexpr long long WAIT_CYCLES = 1000000000LL;  // ~0.5 s at 2 GHz
+
+// launch configuration per split depth: (stages, accumulators, CTAs per SM)
+template <int NSPLIT>
+struct TcCfg;
+template <>
+struct TcCfg<2> {
+  static constexpr int STAGES = 4, NACC = 4;
+};
+template <>
+struct TcCfg<3> {
+  static constexpr int STAGES = 4, NACC = 4;
+};
+template <int NSPLIT>
+constexpr int tc_smem_bytes() {
+  return 1024 + TcCfg<NSPLIT>::STAGES * NSPLIT * (A_TERM + B_TERM);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -118,35 +133,108 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-struct TcOut {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// make generic-proxy shared-memory writes visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// named barrier over the four converter / epilogue warps
+__device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// x = h[0] + h[1] (+ h[2]) to about 8 * NSPLIT bits, each term rounded to nearest
+template <int NSPLIT>
+__device__ __forceinline__ void split_terms(float x, __nv_bfloat16 (&h)[NSPLIT]) {
+  float r = x;
+#pragma unroll
+  for (int t = 0; t < NSPLIT; ++t) {
+    h[t] = __float2bfloat16_rn(r);
+    r = r - __bfloat162float(h[t]);
+  }
+}
+
+// (A term, B term) of every product kept at each split depth
+__device__ __forceinline__ void prod_terms(int nsplit, int q, int* ta, int* tb) {
+  const int a2[3] = {0, 0, 1}, b2[3] = {0, 1, 0};
+  const int a3[6] = {0, 0, 1, 0, 1, 2}, b3[6] = {0, 1, 0, 2, 1, 0};
+  *ta = nsplit == 2 ? a2[q] : a3[q];
+  *tb = nsplit == 2 ? b2[q] : b3[q];
+}
+
+struct TcPass {
+  const float* in;
   float* out;
-  int64_t rows_valid;  // pencils
-  int n_valid;         // output length of the pass
-  int64_t inner;       // pencil p lives at (p / inner) * n * inner + j * inner + (p % inner)
-  float scale;
+  int64_t rows;   // pencils of the pass
+  int n;          // pencil (and output) length
+  int kpad;       // roundup(n, TBK)
+  int64_t inner;  // pencil p lives at (p / inner) * n * inner + j * inner + (p % inner)
+  float scale;    // sqrt(2 / (n + 1))
 };
 
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                         const __grid_constant__ CUtensorMap mapB, int k_tiles,
-                                                         TcOut o, int* __restrict__ err) {
+// The TBK pencil values of K tile kt for this thread's row (zero past n or past the last pencil).
+__device__ __forceinline__ void load_row_tile(const TcPass& P, bool rok, int64_t rb, int kt, float (&x)[TBK]) {
+#pragma unroll
+  for (int e = 0; e < TBK; ++e) {
+    const int k = kt * TBK + e;
+    x[e] = (rok && k < P.n) ? __ldg(P.in + rb + (int64_t)k * P.inner) : 0.f;
+  }
+}
+
+// Split one row's K tile and store the NSPLIT bfloat16 terms in the core-matrix layout.
+template <int NSPLIT>
+__device__ __forceinline__ void store_row_tile(unsigned char* A, int row, const float (&x)[TBK]) {
+#pragma unroll
+  for (int c = 0; c < TBK / 8; ++c) {
+    uint32_t pk[NSPLIT][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      __nv_bfloat16 h0[NSPLIT], h1[NSPLIT];
+      split_terms<NSPLIT>(x[8 * c + e], h0);
+      split_terms<NSPLIT>(x[8 * c + e + 1], h1);
+#pragma unroll
+      for (int t = 0; t < NSPLIT; ++t) pk[t][e / 2] = pack_bf16(h0[t], h1[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < NSPLIT; ++t)
+      *reinterpret_cast<uint4*>(A + t * A_TERM + c * (TBM * 16) + row * 16) =
+          make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+  }
+}
+
+template <int NSPLIT>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_dst_kernel(const __grid_constant__ CUtensorMap mapB, TcPass P,
+                                                                int* __restrict__ err) {
+  constexpr int STAGES = TcCfg<NSPLIT>::STAGES, NACC = TcCfg<NSPLIT>::NACC;
+  constexpr int NPROD = NSPLIT == 2 ? 3 : 6;
+  constexpr int STAGE_BYTES = NSPLIT * (A_TERM + B_TERM);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[TSTAGES];
-  __shared__ __align__(8) uint64_t empty_bar[TSTAGES];
+  __shared__ __align__(8) uint64_t fullA[STAGES];
+  __shared__ __align__(8) uint64_t fullB[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
-
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int n0 = blockIdx.x * TBN;
+  const int64_t m0 = (int64_t)blockIdx.y * TBM;
+  const int KT = P.kpad / TBK;
   if (tid == 0) {
-    for (int s = 0; s < TSTAGES; ++s) {
-      mbar_init(&full_bar[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&fullA[s], 128);
+      mbar_init(&fullB[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
+    mbar_init(&done_bar, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(NACC * TBN)
                  : "memory");
@@ -157,151 +245,156 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (tid == 0) {
-    const uint32_t idesc = instr_desc_bf16(TBM, TBN);
-    auto load_stage = [&](int kt, int s) {
-      unsigned char* A = smem + s * STAGE_BYTES;
-      unsigned char* Bm = A + A_STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-      for (int c = 0; c < TBK / 8; ++c) {
-        tma_load_2d(A + c * (TBM * 16), &mapA, kt * TBK + c * 8, m0, &full_bar[s]);
-        tma_load_2d(Bm + c * (TBN * 16), &mapB, kt * TBK + c * 8, n0, &full_bar[s]);
+  if (warp < 4) {
+    // split-operand producers: thread tid owns pencil row tid of the tile; the next
+    // K tile's loads are issued before the current one is split (two tiles in flight)
+    const int64_t p = m0 + tid;
+    const bool rok = p < P.rows;
+    const int64_t rb = rok ? (p / P.inner) * (int64_t)P.n * P.inner + (p % P.inner) : 0;
+    float xa[TBK], xb[TBK];
+    load_row_tile(P, rok, rb, 0, xa);
+    for (int kt = 0; kt < KT; kt += 2) {
+      // even tile from xa, odd tile from xb (no register copies)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = kt + h;
+        if (k >= KT) break;
+        if (k + 1 < KT) {
+          if (h == 0) load_row_tile(P, rok, rb, k + 1, xb);
+          else load_row_tile(P, rok, rb, k + 1, xa);
+        }
+        const int s = k % STAGES;
+        if (k >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)(((k / STAGES) - 1) & 1))) {
+          atomicExch(err, 4);
+          s_fail = 1;
+          kt = KT;  // leave both loops
+          break;
+        }
+        if (h == 0) store_row_tile<NSPLIT>(smem + s * STAGE_BYTES, tid, xa);
+        else store_row_tile<NSPLIT>(smem + s * STAGE_BYTES, tid, xb);
+        fence_proxy_async();
+        mbar_arrive(&fullA[s]);
       }
+    }
+  } else if (tid == 128) {
+    // TMA producer of the split DST matrix and MMA issuer
+    const uint32_t idesc = instr_desc_bf16(TBM, TBN);
+    auto load_B = [&](int kt) {
+      const int s = kt % STAGES;
+      unsigned char* Bst = smem + s * STAGE_BYTES + NSPLIT * A_TERM;
+      mbar_expect_tx(&fullB[s], NSPLIT * B_TERM);
+      for (int t = 0; t < NSPLIT; ++t)
+        for (int c = 0; c < TBK / 8; ++c)
+          tma_load_2d(Bst + t * B_TERM + c * (TBN * 16), &mapB, t * P.kpad + kt * TBK + c * 8, n0, &fullB[s]);
     };
-    for (int s = 0; s < TSTAGES && s < k_tiles; ++s) load_stage(s, s);
+    for (int kt = 0; kt < STAGES && kt < KT; ++kt) load_B(kt);
     bool ok = true;
-    for (int kt = 0; kt < k_tiles && ok; ++kt) {
-      const int s = kt % TSTAGES;
-      const uint32_t ph = (uint32_t)((kt / TSTAGES) & 1);
-      if (!mbar_wait(&full_bar[s], ph)) {
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)((kt / STAGES) & 1);
+      if (!mbar_wait(&fullB[s], ph) || !mbar_wait(&fullA[s], ph)) {
         ok = false;
         atomicExch(err, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t b0 = a0 + A_STAGE_BYTES;
+      const uint32_t b0 = a0 + NSPLIT * A_TERM;
       const uint32_t dacc = tmem + (uint32_t)((kt % NACC) * TBN);
       for (int kk = 0; kk < TBK / 16; ++kk) {
-        const uint64_t da = smem_desc(a0 + (2 * kk) * (TBM * 16), TBM * 16, 128);
-        const uint64_t db = smem_desc(b0 + (2 * kk) * (TBN * 16), TBN * 16, 128);
-        mma_bf16(dacc, da, db, idesc, (kt >= NACC || kk > 0) ? 1u : 0u);
+        for (int q = 0; q < NPROD; ++q) {
+          int ta, tb;
+          prod_terms(NSPLIT, q, &ta, &tb);
+          const uint64_t da = smem_desc(a0 + ta * A_TERM + (2 * kk) * (TBM * 16), TBM * 16, 128);
+          const uint64_t db = smem_desc(b0 + tb * B_TERM + (2 * kk) * (TBN * 16), TBN * 16, 128);
+          mma_bf16(dacc, da, db, idesc, (kt >= NACC || kk > 0 || q > 0) ? 1u : 0u);
+        }
       }
       mma_commit(&empty_bar[s]);
-      if (kt + TSTAGES < k_tiles) {
-        if (!mbar_wait(&empty_bar[s], ph)) {
+      // refill the stage of the previous K tile once its MMAs have completed
+      const int kr = kt - 1 + STAGES;
+      if (kt >= 1 && kr < KT) {
+        if (!mbar_wait(&empty_bar[(kt - 1) % STAGES], (uint32_t)(((kt - 1) / STAGES) & 1))) {
           ok = false;
           atomicExch(err, 2);
           break;
         }
-        load_stage(kt + TSTAGES, s);
+        load_B(kr);
       }
     }
-    if (ok) {
-      const int last = k_tiles - 1;
-      if (!mbar_wait(&empty_bar[last % TSTAGES], (uint32_t)((last / TSTAGES) & 1))) {
-        ok = false;
-        atomicExch(err, 3);
-      }
-    }
-    if (!ok) s_fail = 1;
+    if (ok) mma_commit(&done_bar);
+    else s_fail = 1;
   }
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  if (!s_fail) {
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 (rows m0 + 32w + lane)
-    const int64_t p = (int64_t)m0 + 32 * warp + lane;
-    const bool row_ok = p < o.rows_valid;
-    const int64_t ob = row_ok ? (p / o.inner) * (int64_t)o.n_valid * o.inner + (p % o.inner) : 0;
-    const int nacc = k_tiles < NACC ? k_tiles : NACC;
-    for (int c = 0; c < TBN / 16; ++c) {
-      float sum[16];
+  if (warp < 4) {
+    if (!s_fail && !mbar_wait(&done_bar, 0)) {
+      atomicExch(err, 3);
+      s_fail = 1;
+    }
+    conv_bar();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_fail) {
+      // warp w reads TMEM lanes 32w..32w+31 = rows of the tile
+      const int nacc = KT < NACC ? KT : NACC;
+      const int64_t p = m0 + tid;
+      const bool rok = p < P.rows;
+      float* tile = reinterpret_cast<float*>(smem);  // contiguous pass: 128 x 17 floats
+      for (int c = 0; c < TBN / 16; ++c) {
+        float sum[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) sum[e] = 0.f;
-      for (int ac = 0; ac < nacc; ++ac) {
-        uint32_t r[16];
-        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ac * TBN + c * 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int e = 0; e < 16; ++e) sum[e] = 0.f;
+        for (int ac = 0; ac < nacc; ++ac) {
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ac * TBN + c * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int e = 0; e < 16; ++e) sum[e] += __uint_as_float(r[e]);
-      }
-      if (row_ok) {
+          for (int e = 0; e < 16; ++e) sum[e] += __uint_as_float(r[e]);
+        }
+        if (P.inner > 1) {
+          // strided pass: lanes are consecutive pencils, so every store instruction coalesces
+          if (rok) {
+            const int64_t ob = (p / P.inner) * (int64_t)P.n * P.inner + (p % P.inner);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int j = n0 + c * 16 + e;
-          if (j < o.n_valid) o.out[ob + (int64_t)j * o.inner] = sum[e] * o.scale;
+            for (int e = 0; e < 16; ++e) {
+              const int j = n0 + c * 16 + e;
+              if (j < P.n) P.out[ob + (int64_t)j * P.inner] = sum[e] * P.scale;
+            }
+          }
+        } else {
+          // contiguous pass: transpose the 128 x 16 chunk through shared memory, then
+          // half-warps write 16 consecutive outputs of one pencil
+#pragma unroll
+          for (int e = 0; e < 16; ++e) tile[tid * 17 + e] = sum[e] * P.scale;
+          conv_bar();
+          const int col = tid & 15;
+          const int j = n0 + c * 16 + col;
+          for (int rr = tid >> 4; rr < TBM; rr += 8) {
+            const int64_t pr = m0 + rr;
+            if (pr < P.rows && j < P.n) P.out[pr * (int64_t)P.n + j] = tile[rr * 17 + col];
+          }
+          conv_bar();
         }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TBN) : "memory");
+  if (warp == 4) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TcCfg<NSPLIT>::NACC * TBN)
+                 : "memory");
   }
 }
 
-// ---------------------------------------------------------------------------
-// operand preparation
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void split3(float x, __nv_bfloat16* h) {
-  const __nv_bfloat16 a = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(a);
-  const __nv_bfloat16 b = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(b);
-  h[0] = a;
-  h[1] = b;
-  h[2] = __float2bfloat16_rn(r2);
-}
-
-// segment order of the K-concatenated operands (index of the split term per segment)
-__constant__ int c_segA[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int c_segB[6] = {0, 1, 0, 2, 1, 0};
-
-// A'[p][seg * kpad + k] for pencils p < rows_pad (zero beyond rows / n); 64 x 64 tiles
-// through shared memory so that both the strided read and the row write coalesce.
-__global__ void split_pencils_kernel(const float* __restrict__ in, int n, int64_t inner, int64_t rows, int kpad,
-                                     int nseg, __nv_bfloat16* __restrict__ Ap) {
-  __shared__ float tile[64][65];
-  const int64_t p0 = (int64_t)blockIdx.x * 64;
-  const int k0 = blockIdx.y * 64;
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 256 threads: 64 x 4
-  for (int r = ty; r < 64; r += 4) {
-    float v = 0.f;
-    int64_t p;
-    int k;
-    if (inner == 1) {  // contiguous along k: threads walk k
-      p = p0 + r;
-      k = k0 + tx;
-    } else {           // contiguous along p: threads walk p
-      p = p0 + tx;
-      k = k0 + r;
-    }
-    if (p < rows && k < n) v = in[(p / inner) * (int64_t)n * inner + (int64_t)k * inner + (p % inner)];
-    if (inner == 1) tile[r][tx] = v;
-    else tile[tx][r] = v;
-  }
-  __syncthreads();
-  const int kk = tx;
-  for (int r = ty; r < 64; r += 4) {
-    const int64_t p = p0 + r;
-    const int k = k0 + kk;
-    __nv_bfloat16 h[3];
-    split3(tile[r][kk], h);
-    for (int s = 0; s < nseg; ++s) Ap[p * (int64_t)nseg * kpad + (int64_t)s * kpad + k] = h[c_segA[s]];
-  }
-}
-
-// B'[j][seg * kpad + k] = split term of S[j][k] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1)) (the scale
-// is applied in the epilogue), zero padded to npad_rows x kpad
-__global__ void split_dst_matrix_kernel(int n, int kpad, int nseg, __nv_bfloat16* __restrict__ Bp) {
+// B'[j][t * kpad + k] = split term t of S[j][k] = sin(pi (j+1)(k+1)/(n+1)) (the orthonormal
+// scale is applied in the epilogue), zero padded to npad rows x kpad columns per term
+__global__ void split_dst_matrix_kernel(int n, int kpad, int nsplit, __nv_bfloat16* __restrict__ Bp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (k >= kpad) return;
@@ -311,9 +404,12 @@ __global__ void split_dst_matrix_kernel(int n, int kpad, int nseg, __nv_bfloat16
     const int64_t m = ((int64_t)(j + 1) * (k + 1)) % period;
     v = (float)sinpi((double)m / (double)(n + 1));
   }
-  __nv_bfloat16 h[3];
-  split3(v, h);
-  for (int s = 0; s < nseg; ++s) Bp[(int64_t)j * nseg * kpad + (int64_t)s * kpad + k] = h[c_segB[s]];
+  float r = v;
+  for (int t = 0; t < nsplit; ++t) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(r);
+    Bp[(int64_t)j * nsplit * kpad + (int64_t)t * kpad + k] = h;
+    r -= __bfloat162float(h);
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -349,29 +445,37 @@ pe_status make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t r
 
 inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-// One axis pass: out = S applied along the axis (pencils of length n, stride inner).
-pe_status tc_axis(const float* in, float* out, int64_t outer, int n, int64_t inner, int nsplit, __nv_bfloat16* Ap,
-                  __nv_bfloat16* Bp, int* err, cudaStream_t st) {
-  const int nseg = nsplit == 2 ? 3 : 6;
-  const int kpad = (int)rup(n, TBK);
-  const int64_t kprime = (int64_t)nseg * kpad;
-  const int64_t rows = outer * inner;
-  const int64_t rows_pad = rup(rows, TBM);
-  const int npad = (int)rup(n, TBN);
-  dim3 g1((unsigned)(rows_pad / 64), kpad / 64);
-  split_pencils_kernel<<<g1, 256, 0, st>>>(in, n, inner, rows, kpad, nseg, Ap);
-  dim3 g2((kpad + 127) / 128, npad);
-  split_dst_matrix_kernel<<<g2, 128, 0, st>>>(n, kpad, nseg, Bp);
-  PE_CUDA_TRY(cudaGetLastError());
-  CUtensorMap mA, mB;
-  PE_TRY(make_map(&mA, Ap, (uint64_t)kprime, (uint64_t)rows_pad, TBM));
-  PE_TRY(make_map(&mB, Bp, (uint64_t)kprime, (uint64_t)npad, TBN));
-  TcOut o{out, rows, n, inner, (float)sqrt(2.0 / (double)(n + 1))};
-  dim3 grid((unsigned)(rows_pad / TBM), (unsigned)(npad / TBN));
-  if (grid.x > 2147483647u || grid.y > 65535u) return pe_fail(PE_EINVAL, "tensor-core DST: problem too large");
-  tc_gemm_kernel<<<grid, 128, TC_SMEM, st>>>(mA, mB, (int)(kprime / TBK), o, err);
+template <int NSPLIT>
+pe_status tc_launch(const CUtensorMap& mB, const TcPass& P, dim3 grid, int* err, cudaStream_t st) {
+  static bool attr_set = false;  // the same value for every device and call
+  if (!attr_set) {
+    PE_CUDA_TRY(cudaFuncSetAttribute(tc_dst_kernel<NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc_smem_bytes<NSPLIT>()));
+    attr_set = true;
+  }
+  tc_dst_kernel<NSPLIT><<<grid, TC_THREADS, tc_smem_bytes<NSPLIT>(), st>>>(mB, P, err);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
+}
+
+// One axis pass: out = S applied along the axis (pencils of length n, stride inner).
+pe_status tc_axis(const float* in, float* out, int64_t outer, int n, int64_t inner, int nsplit, __nv_bfloat16* Bp,
+                  int* err, cudaStream_t st) {
+  const int kpad = (int)rup(n, TBK);
+  const int npad = (int)rup(n, TBN);
+  const int64_t rows = outer * inner;
+  dim3 g2((kpad + 127) / 128, npad);
+  split_dst_matrix_kernel<<<g2, 128, 0, st>>>(n, kpad, nsplit, Bp);
+  PE_CUDA_TRY(cudaGetLastError());
+  CUtensorMap mB;
+  PE_TRY(make_map(&mB, Bp, (uint64_t)nsplit * kpad, (uint64_t)npad, TBN));
+  const TcPass P{in, out, rows, n, kpad, inner, (float)sqrt(2.0 / (double)(n + 1))};
+  // output tiles of one pencil block are adjacent in launch order, so the block's
+  // float32 rows are read from HBM once and from L2 for the other output tiles
+  const int64_t mt = rup(rows, TBM) / TBM;
+  if (mt > 65535) return pe_fail(PE_EINVAL, "tensor-core DST: problem too large");
+  const dim3 grid((unsigned)(npad / TBN), (unsigned)mt);
+  return nsplit == 2 ? tc_launch<2>(mB, P, grid, err, st) : tc_launch<3>(mB, P, grid, err, st);
 }
 
 }  // namespace
@@ -381,29 +485,18 @@ extern "C" pe_status pe_dst_tc(int32_t d, const int32_t* n, const float* in, flo
   if (d < 1 || d > PE_MAX_D || !n || !in || !out) return pe_fail(PE_EINVAL, "pe_dst_tc: bad arguments");
   if (nsplit != 2 && nsplit != 3) return pe_fail(PE_EINVAL, "pe_dst_tc: nsplit must be 2 or 3");
   int64_t ndof = 1;
-  int64_t worstA = 0, worstB = 0;
+  int64_t worstB = 0;
   for (int a = 0; a < d; ++a) {
     if (n[a] < 1 || n[a] > 1024) return pe_fail(PE_EINVAL, "pe_dst_tc: n_a must be in 1..1024");
     ndof *= n[a];
   }
-  const int nseg = nsplit == 2 ? 3 : 6;
-  for (int a = 0; a < d; ++a) {
-    const int64_t rows = ndof / n[a];
-    worstA = std::max<int64_t>(worstA, rup(rows, TBM) * nseg * rup(n[a], TBK));
-    worstB = std::max<int64_t>(worstB, rup(n[a], TBN) * nseg * rup(n[a], TBK));
-  }
+  for (int a = 0; a < d; ++a) worstB = std::max<int64_t>(worstB, rup(n[a], TBN) * nsplit * rup(n[a], TBK));
   cudaStream_t st = (cudaStream_t)stream;
-  static bool attr_set = false;
-  if (!attr_set) {
-    PE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    attr_set = true;
-  }
-  __nv_bfloat16 *Ap = nullptr, *Bp = nullptr;
+  __nv_bfloat16* Bp = nullptr;
   float* tmp = nullptr;
   int* err = nullptr;
   pe_status rc = PE_OK;
-  cudaError_t e = cudaMallocAsync((void**)&Ap, sizeof(__nv_bfloat16) * worstA, st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&Bp, sizeof(__nv_bfloat16) * worstB, st);
+  cudaError_t e = cudaMallocAsync((void**)&Bp, sizeof(__nv_bfloat16) * worstB, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&tmp, sizeof(float) * ndof, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&err, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
@@ -416,7 +509,7 @@ extern "C" pe_status pe_dst_tc(int32_t d, const int32_t* n, const float* in, flo
     int64_t outer = 1, inner = 1;
     for (int b = 0; b < a; ++b) outer *= n[b];
     for (int b = a + 1; b < d; ++b) inner *= n[b];
-    rc = tc_axis(src, dst, outer, n[a], inner, nsplit, Ap, Bp, err, st);
+    rc = tc_axis(src, dst, outer, n[a], inner, nsplit, Bp, err, st);
     src = dst;
   }
   if (rc == PE_OK && src != out) {
@@ -429,7 +522,6 @@ extern "C" pe_status pe_dst_tc(int32_t d, const int32_t* n, const float* in, flo
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = pe_cuda_fail(e, "pe_dst_tc");
   }
-  if (Ap) cudaFreeAsync(Ap, st);
   if (Bp) cudaFreeAsync(Bp, st);
   if (tmp) cudaFreeAsync(tmp, st);
   if (err) cudaFreeAsync(err, st);
