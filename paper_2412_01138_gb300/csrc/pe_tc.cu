@@ -47,20 +47,24 @@ constexpr int B_TERM = TBN * TBK * 2;  // one bfloat16 split term of the B stage
 constexpr int TC_THREADS = 160;
 constexpr long long WAIT_CYCLES = 1000000000LL;  // ~0.5 s at 2 GHz
 
-// launch configuration per split depth: (stages, accumulators, CTAs per SM)
+constexpr int XROW = TBK + 1;             // float32 staging row (one pad word: conflict-free)
+constexpr int X_SLOT = TBM * XROW * 4;     // one float32 K tile of the 128 pencils
+
+// per split depth: STAGES split-operand stages, SF float32 staging slots (the pencils'
+// K tiles are fetched by cp.async up to SF tiles ahead of the split), NACC accumulators
 template <int NSPLIT>
 struct TcCfg;
 template <>
 struct TcCfg<2> {
-  static constexpr int STAGES = 4, NACC = 4;
+  static constexpr int STAGES = 4, SF = 4, NACC = 4;
 };
 template <>
 struct TcCfg<3> {
-  static constexpr int STAGES = 4, NACC = 4;
+  static constexpr int STAGES = 3, SF = 3, NACC = 4;
 };
 template <int NSPLIT>
 constexpr int tc_smem_bytes() {
-  return 1024 + TcCfg<NSPLIT>::STAGES * NSPLIT * (A_TERM + B_TERM);
+  return 1024 + TcCfg<NSPLIT>::STAGES * NSPLIT * (A_TERM + B_TERM) + TcCfg<NSPLIT>::SF * X_SLOT;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -143,21 +147,6 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 // named barrier over the four converter / epilogue warps
 __device__ __forceinline__ void conv_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// x = h[0] + h[1] (+ h[2]) to about 8 * NSPLIT bits, each term rounded to nearest
-template <int NSPLIT>
-__device__ __forceinline__ void split_terms(float x, __nv_bfloat16 (&h)[NSPLIT]) {
-  float r = x;
-#pragma unroll
-  for (int t = 0; t < NSPLIT; ++t) {
-    h[t] = __float2bfloat16_rn(r);
-    r = r - __bfloat162float(h[t]);
-  }
-}
-
 // (A term, B term) of every product kept at each split depth
 __device__ __forceinline__ void prod_terms(int nsplit, int q, int* ta, int* tb) {
   const int a2[3] = {0, 0, 1}, b2[3] = {0, 1, 0};
@@ -176,16 +165,30 @@ struct TcPass {
   float scale;    // sqrt(2 / (n + 1))
 };
 
-// The TBK pencil values of K tile kt for this thread's row (zero past n or past the last pencil).
-__device__ __forceinline__ void load_row_tile(const TcPass& P, bool rok, int64_t rb, int kt, float (&x)[TBK]) {
+// Asynchronous 4-byte copy global -> shared; src_bytes = 0 writes a zero.
+__device__ __forceinline__ void cp_async4(void* dst_smem, const float* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst_smem)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// Fetch the TBK pencil values of K tile kt of this thread's row into its staging row
+// (zeros past n or past the last pencil), one commit group per tile.
+__device__ __forceinline__ void fetch_row_tile(const TcPass& P, bool rok, int64_t rb, int kt, float* xrow) {
 #pragma unroll
   for (int e = 0; e < TBK; ++e) {
     const int k = kt * TBK + e;
-    x[e] = (rok && k < P.n) ? __ldg(P.in + rb + (int64_t)k * P.inner) : 0.f;
+    const bool in = rok && k < P.n;
+    cp_async4(xrow + e, in ? P.in + rb + (int64_t)k * P.inner : P.in, in ? 4 : 0);
   }
 }
 
-// Split one row's K tile and store the NSPLIT bfloat16 terms in the core-matrix layout.
+// Split one row's K tile and store the NSPLIT bfloat16 terms in the core-matrix layout
+// (pairs of values converted together: cvt.rn.bf16x2.f32).
 template <int NSPLIT>
 __device__ __forceinline__ void store_row_tile(unsigned char* A, int row, const float (&x)[TBK]) {
 #pragma unroll
@@ -193,11 +196,16 @@ __device__ __forceinline__ void store_row_tile(unsigned char* A, int row, const 
     uint32_t pk[NSPLIT][4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
-      __nv_bfloat16 h0[NSPLIT], h1[NSPLIT];
-      split_terms<NSPLIT>(x[8 * c + e], h0);
-      split_terms<NSPLIT>(x[8 * c + e + 1], h1);
+      float r0 = x[8 * c + e], r1 = x[8 * c + e + 1];
 #pragma unroll
-      for (int t = 0; t < NSPLIT; ++t) pk[t][e / 2] = pack_bf16(h0[t], h1[t]);
+      for (int t = 0; t < NSPLIT; ++t) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);  // .x = r0 (low half)
+        pk[t][e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+        if (t + 1 < NSPLIT) {
+          r0 -= __low2float(h);
+          r1 -= __high2float(h);
+        }
+      }
     }
 #pragma unroll
     for (int t = 0; t < NSPLIT; ++t)
@@ -246,36 +254,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dst_kernel(const __grid_cons
   const uint32_t tmem = tmem_slot;
 
   if (warp < 4) {
-    // split-operand producers: thread tid owns pencil row tid of the tile; the next
-    // K tile's loads are issued before the current one is split (two tiles in flight)
+    // split-operand producers: thread tid owns pencil row tid of the tile.  Its float32
+    // K tiles arrive by cp.async in its own staging row, SF - 1 tiles ahead of the
+    // split, so no barrier is needed between the copy and the split.
+    constexpr int SF = TcCfg<NSPLIT>::SF;
     const int64_t p = m0 + tid;
     const bool rok = p < P.rows;
     const int64_t rb = rok ? (p / P.inner) * (int64_t)P.n * P.inner + (p % P.inner) : 0;
-    float xa[TBK], xb[TBK];
-    load_row_tile(P, rok, rb, 0, xa);
-    for (int kt = 0; kt < KT; kt += 2) {
-      // even tile from xa, odd tile from xb (no register copies)
+    float* xs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);  // [SF][TBM][XROW]
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int k = kt + h;
-        if (k >= KT) break;
-        if (k + 1 < KT) {
-          if (h == 0) load_row_tile(P, rok, rb, k + 1, xb);
-          else load_row_tile(P, rok, rb, k + 1, xa);
-        }
-        const int s = k % STAGES;
-        if (k >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)(((k / STAGES) - 1) & 1))) {
-          atomicExch(err, 4);
-          s_fail = 1;
-          kt = KT;  // leave both loops
-          break;
-        }
-        if (h == 0) store_row_tile<NSPLIT>(smem + s * STAGE_BYTES, tid, xa);
-        else store_row_tile<NSPLIT>(smem + s * STAGE_BYTES, tid, xb);
-        fence_proxy_async();
-        mbar_arrive(&fullA[s]);
-      }
+    for (int f = 0; f < SF - 1; ++f) {
+      if (f < KT) fetch_row_tile(P, rok, rb, f, xs + (f * TBM + tid) * XROW);
+      cp_async_commit();
     }
+    for (int kt = 0; kt < KT; ++kt) {
+      const int kf = kt + SF - 1;
+      if (kf < KT) fetch_row_tile(P, rok, rb, kf, xs + ((kf % SF) * TBM + tid) * XROW);
+      cp_async_commit();
+      cp_async_wait<SF - 1>();  // tile kt has landed
+      float x[TBK];
+      const float* xr = xs + ((kt % SF) * TBM + tid) * XROW;
+#pragma unroll
+      for (int e = 0; e < TBK; ++e) x[e] = xr[e];
+      const int s = kt % STAGES;
+      if (kt >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)(((kt / STAGES) - 1) & 1))) {
+        atomicExch(err, 4);
+        s_fail = 1;
+        break;
+      }
+      store_row_tile<NSPLIT>(smem + s * STAGE_BYTES, tid, x);
+      fence_proxy_async();
+      mbar_arrive(&fullA[s]);
+    }
+    cp_async_wait<0>();
   } else if (tid == 128) {
     // TMA producer of the split DST matrix and MMA issuer
     const uint32_t idesc = instr_desc_bf16(TBM, TBN);
