@@ -28,7 +28,7 @@ def _rel(a, b, w):
 
 
 def _mixed_batch():
-    """Uneven small problems: d = 1, 2, 3, different R (1..20), N, M, q, p, D, boxes."""
+    """Uneven small problems: d = 1, 2, 3, different R (1..20), N, M (2..400), q, p, D, boxes."""
     probs = []
     for i in range(10):
         p = I.config4_problem(i)
@@ -44,6 +44,11 @@ def _mixed_batch():
                            u0, f + I.gaussian_bumps(rng, 3, 3), 3, 1e-12))
     probs.append(I.Problem(2, (5, 5), ((0.0, 1.0),) * 2, 1.0, 0.0, 1.0, 1, 2, I.uniform_nodes(2),
                            I.uniform_nodes(1), I.sin_mode(2, ((0.0, 1.0),) * 2, 1.0)[0], (), 3, 1e-12))
+    # many substeps and 39 stage columns: two [M][KC] float blocks exceed the staging buffer,
+    # so the mixed fine item stages its time factors chunk by chunk
+    u0, f, _ = I.sin_mode(1, box1, 0.3)
+    probs.append(I.Problem(1, (90,), box1, 0.3, 0.0, 0.5, 3, 400, I.uniform_nodes(4), I.uniform_nodes(2),
+                           u0, f + I.gaussian_bumps(rng, 1, 19), 3, 1e-12))
     return probs
 
 

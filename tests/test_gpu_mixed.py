@@ -3,6 +3,8 @@
 Bound: relative L2 <= 1e-6 (the precision workload's stated bound before
 float64 refinement).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -77,3 +79,39 @@ def test_float64_refinement_reaches_float64_parity(pe, which):
     assert 1e-12 < before <= TOL_MIXED
     assert after <= 1e-12
     assert 0.0 < r <= TOL_MIXED  # the refinement's residual is the size of the mixed-precision error
+
+
+def _term_mix(kinds, seed):
+    """Separable terms with the given time kinds ('e' exponential, 's' sinusoid), drawn from a
+    SplitMix64 stream (frequencies up to 200, several turns per substep)."""
+    rng = I.SplitMix64(seed)
+    out = []
+    for k in kinds:
+        facs = (I.Factor(I.S_SIN, (math.pi * (1 + int(4 * rng.uniform())), 0.0)),
+                I.Factor(I.S_GAUSS, (rng.uniform(), 0.05 + 0.1 * rng.uniform())))
+        amp = 2.0 * rng.uniform() - 1.0
+        if k == "e":
+            out.append(I.Term(amp, facs, I.T_EXP, (8.0 * rng.uniform() - 6.0, 0.0)))
+        else:
+            out.append(I.Term(amp, facs, I.T_SIN, (200.0 * rng.uniform(), 2.0 * math.pi * rng.uniform())))
+    return tuple(out)
+
+
+# (time kinds, substeps): K = 1, 2, 3, 26, 64, 50 columns.  Two [M][KC] float blocks of at most
+# 48 KB run in the persistent kernel (cp.async double buffer over (tile, slice) items); the last
+# two cases (M * KC = 6208 and 13000 floats) take the chunked per-slice kernel.
+@pytest.mark.parametrize("kinds,M", [("e", 7), ("s", 9), ("es", 64), ("esse" * 4 + "s", 33), ("s" * 32, 97),
+                                     ("ses" * 10, 250)])
+def test_mixed_stage_contraction_column_classes(pe, kinds, M):
+    box = ((0.0, 1.0), (0.0, 1.0))
+    u0, _, _ = I.sin_mode(2, box, 0.05)
+    prob = I.Problem(2, (47, 61), box, 0.05, 0.1, 0.6, 5, M, I.draw_random_nodes(5, 77), I.uniform_nodes(2), u0,
+                     _term_mix(kinds, len(kinds)), 3, 1e-12)
+    sys_ = osolver.ModalSystem(prob)
+    ref = osolver.parareal(sys_, tol=0.0, k_max=2)
+    with pe.Solver(prob, precision=pe.PE_MIXED) as s:
+        s.set_problem()
+        for k in range(1, 3):
+            s.iterate()
+            for n in range(1, prob.N + 1):
+                assert _rel(s.modal(n), ref.history[k][n], sys_.norm_w) <= TOL_MIXED, (k, n)
