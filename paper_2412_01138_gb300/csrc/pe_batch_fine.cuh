@@ -37,8 +37,8 @@ __device__ __forceinline__ void b_wait() { asm volatile("cp.async.wait_group %0;
 template <int KC, int MPT>
 __device__ __forceinline__ void b_mixed_substeps(const float* sY, int mc, int K, const float (&W)[MPT][KC],
                                                  const float (&eh)[MPT], const float (&el)[MPT], float (&w)[MPT]) {
-  // two substeps per trip: the second substep's loads and FMA chains overlap the first's latency
-#pragma unroll 2
+  // four substeps per trip: the later substeps' loads and FMA chains overlap the earlier ones' latency
+#pragma unroll 4
   for (int m = 0; m < mc; ++m) {
     const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
     float acc[MPT];

@@ -49,6 +49,9 @@ struct FineTile {
   double* Fn;             // F^M(U^n), or F^M(0) when from_zero
 };
 
+// Modes per thread of the mixed tile: as many as the registers allow (W takes MPT * K).
+__host__ __device__ constexpr int fine_mixed_mpt(int K) { return K <= 17 ? 6 : (K <= 24 ? 4 : (K <= 40 ? 2 : 1)); }
+
 // Mixed precision, K columns stored as KC = roundup(K, 4) floats per substep
 // (zero padding, [N][M][KC] in the float time table) so that each float4
 // broadcast load feeds 4*MPT FMAs; the padding lanes are skipped.
@@ -80,9 +83,9 @@ template <int K, int MPT>
 __device__ __forceinline__ void mixed_substeps(const float* sY, int mc, const float (&W)[MPT][K],
                                                const float (&eh)[MPT], const float (&el)[MPT], float (&w)[MPT]) {
   constexpr int KC = (K + 3) / 4 * 4;
-  // two substeps per trip: the second substep's broadcast loads and FMA chains are
-  // independent of the first one's recurrence, so they overlap its latency
-#pragma unroll 2
+  // four substeps per trip: the later substeps' broadcast loads and FMA chains are
+  // independent of the earlier ones' recurrence, so they overlap its latency
+#pragma unroll 4
   for (int m = 0; m < mc; ++m) {
     const float4* y4 = reinterpret_cast<const float4*>(sY + m * KC);
     float acc[MPT];
@@ -152,11 +155,16 @@ __device__ __forceinline__ void y_wait() { asm volatile("cp.async.wait_group %0;
 // in registers until the range crosses a tile boundary (once or twice per CTA
 // instead of once per slice), and the next item's [M][KC] time factors are staged
 // by cp.async into the other half of a double buffer while the current item runs.
+//
+// 128 threads per CTA; MPT = 6 (K <= 17) at three CTAs per SM, otherwise four CTAs per SM
+// (at most 128 registers).
+constexpr int kMixedThreads = 128;
 template <int K, int MPT>
-__global__ void __launch_bounds__(256, 2) fine_mixed_persistent_kernel(FineTile t, int N, int64_t n_items) {
+__global__ void __launch_bounds__(kMixedThreads, MPT >= 6 ? 3 : 4)
+    fine_mixed_persistent_kernel(FineTile t, int N, int64_t n_items) {
   constexpr int KC = (K + 3) / 4 * 4;
   extern __shared__ __align__(16) float sYb[];
-  const int B = blockDim.x;
+  const int B = kMixedThreads;
   const int64_t nd = t.ndof;
   const int slab = t.M * KC;  // floats per slice, a multiple of 4
   const int64_t i0 = (int64_t)blockIdx.x * n_items / gridDim.x;
@@ -272,23 +280,26 @@ pe_status fine_launch(pe_ctx* c, int precision, int from_zero, double* out) {
   t.Un = c->U;
   t.Fn = out;
   if (precision == PE_MIXED) {
-    constexpr int MPT = K <= 24 ? 4 : (K <= 40 ? 2 : 1);
+    constexpr int MPT = fine_mixed_mpt(K);
     constexpr int KC = (K + 3) / 4 * 4;
-    const int64_t per_cta = (int64_t)threads * MPT;
-    const int64_t tiles = (c->g.ndof + per_cta - 1) / per_cta;
     const size_t slab_bytes = sizeof(float) * (size_t)c->M * KC;
     if (2 * slab_bytes <= 48 * 1024) {
+      const int64_t per_cta = (int64_t)kMixedThreads * MPT;
+      const int64_t tiles = (c->g.ndof + per_cta - 1) / per_cta;
       // persistent: one resident wave of CTAs over the (tile, slice) items
       int dev = 0, sms = 0, occ = 0;
       PE_CUDA_TRY(cudaGetDevice(&dev));
       PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fine_mixed_persistent_kernel<K, MPT>,
-                                                                threads, 2 * slab_bytes));
+                                                                kMixedThreads, 2 * slab_bytes));
       if (occ < 1) return pe_fail(PE_EINVAL, "fine sweep: persistent kernel does not fit an SM");
       const int64_t items = tiles * c->N;
       const int64_t grid = items < (int64_t)sms * occ ? items : (int64_t)sms * occ;
-      fine_mixed_persistent_kernel<K, MPT><<<(unsigned)grid, threads, 2 * slab_bytes, c->stream>>>(t, c->N, items);
+      fine_mixed_persistent_kernel<K, MPT><<<(unsigned)grid, kMixedThreads, 2 * slab_bytes, c->stream>>>(t, c->N,
+                                                                                                          items);
     } else {
+      const int64_t per_cta = (int64_t)threads * MPT;
+      const int64_t tiles = (c->g.ndof + per_cta - 1) / per_cta;
       t.mchunk = pick_mchunk(c->M, KC, sizeof(float));
       dim3 grid((unsigned)tiles, c->N);
       fine_mixed_kernel<K, MPT><<<grid, threads, sizeof(float) * t.mchunk * KC, c->stream>>>(
