@@ -530,6 +530,24 @@ def run_general(pe, args, barrier, u0_dev):
     return out
 
 
+def allmax(x, dist=None, device="cpu"):
+    """The maximum of x over all ranks (x itself without a process group): the timed region of
+    a replica run ends when the slowest rank ends."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, max_ms, world):
+    """Whole-job throughput of `world` independent replicas: all ranks' units over the slowest
+    rank's time (weak scaling: the per-rank workload is fixed)."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle as it stands, on a bounded sample of the workload."""
     if rank != 0:
@@ -672,16 +690,9 @@ def main():
     clock = clocks.summary()
 
     # max over ranks
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     for r in results.values():
-        r["total_ms"] = allmax(r["total_ms"])
-        r["e2e_s"] = allmax(r["e2e_s"])
+        r["total_ms"] = allmax(r["total_ms"], dist, dev)
+        r["e2e_s"] = allmax(r["e2e_s"], dist, dev)
 
     if rank != 0:
         if dist is not None:
@@ -690,8 +701,8 @@ def main():
 
     def summarize(r):
         k = r["infos"][-1]["k"]
-        units = prob.ndof * prob.N * prob.M * sum(i["fine_sweeps"] for i in r["infos"]) * world
-        value = units / (r["total_ms"] / 1e3)
+        units = prob.ndof * prob.N * prob.M * sum(i["fine_sweeps"] for i in r["infos"])
+        value = replica_throughput(units, r["total_ms"], world)
         e2e_units = prob.ndof * prob.N * prob.M * k * args.steps * world
         ms_fine = np.mean([i["ms_fine_kernel"] / max(i["fine_sweeps"], 1) for i in r["infos"]])
         phases = {key: float(np.mean([i[key] for i in r["infos"]]))
