@@ -128,7 +128,7 @@ void free_ctx(pe_ctx* c) {
                   c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Gold, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
-                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz};
+                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -281,6 +281,9 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->out_nodal, nd);
   if (st == PE_OK) st = dev_alloc(&c->partials, 2 * (size_t)c->max_blocks + 64);
   if (st == PE_OK) st = dev_alloc(&c->red, 2);
+  if (st == PE_OK) st = dev_alloc(&c->done_ctr, 1);
+  if (st == PE_OK && cudaMemset(c->done_ctr, 0, sizeof(unsigned int)) != cudaSuccess)
+    st = pe_fail(PE_ECUDA, "pe_setup: counter initialisation failed");
   if (st == PE_OK) st = dev_alloc(&c->axisF, MT * nsum);
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->axisF32, MT * nsum);
   if (st == PE_OK) st = dev_alloc(&c->axisU0, MT * nsum);

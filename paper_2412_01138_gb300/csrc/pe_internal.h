@@ -100,6 +100,7 @@ struct pe_ctx {
   double* out_nodal = nullptr;  // [ndof] inverse DST of U^N after pe_solve
   double* partials = nullptr;   // [2 * max_blocks]
   double* red = nullptr;        // [2] device
+  unsigned int* done_ctr = nullptr;  // correction: CTAs finished (0 between launches)
   double* h_red = nullptr;      // [2] pinned host
   int max_blocks = 0;
   // forcing (set by pe_set_problem)

@@ -9,7 +9,8 @@
 //   coarse sweep   U^{n+1,(0)} = G(U^{n,(0)}) = E_G U^n + gG_n, stored G(U^{n,(0)});
 //                  the coarse forcing gG_n (independent of the iterate) is kept.
 //   correction     U^{n+1,(k+1)} = G(U^{n,(k+1)}) + Fbar^{n+1} - G(U^{n,(k)})
-//                  and the float64 sums  sum mu^M_J (U^{new} - U^{old})^2, sum mu^M_J (U^{new})^2.
+//                  and the float64 sums  sum mu^M_J (U^{new} - U^{old})^2, sum mu^M_J (U^{new})^2
+//                  (per-CTA partial sums, added by the last CTA to finish).
 #include "pe_internal.h"
 
 namespace {
@@ -168,8 +169,10 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
                                                          const double* __restrict__ coefG,
                                                          const double* __restrict__ gG,
                                                          const double* __restrict__ Fbar, double* __restrict__ Gold,
-                                                         double* __restrict__ U, double* __restrict__ partials) {
+                                                         double* __restrict__ U, double* __restrict__ partials,
+                                                         unsigned int* __restrict__ done, double* __restrict__ red) {
   __shared__ double sh[32];
+  __shared__ bool s_last;
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double sd = 0.0, su = 0.0, w = 0.0;
   if (J < g.ndof) {
@@ -231,24 +234,28 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
   su *= w;
   sd = block_sum(sd, sh);
   su = block_sum(su, sh);
+  // the last CTA to finish adds the per-CTA partial sums (in CTA order) and re-arms the counter
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = sd;
     partials[2 * blockIdx.x + 1] = su;
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
   }
-}
-
-__global__ void final_reduce_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
-  __shared__ double sh[32];
-  double sd = 0.0, su = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    sd += partials[2 * b];
-    su += partials[2 * b + 1];
-  }
-  sd = block_sum(sd, sh);
-  su = block_sum(su, sh);
-  if (threadIdx.x == 0) {
-    out[0] = sd;
-    out[1] = su;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double td = 0.0, tu = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      td += __ldcg(partials + 2 * b);
+      tu += __ldcg(partials + 2 * b + 1);
+    }
+    td = block_sum(td, sh);
+    tu = block_sum(tu, sh);
+    if (threadIdx.x == 0) {
+      red[0] = td;
+      red[1] = tu;
+      *done = 0u;
+    }
   }
 }
 
@@ -283,10 +290,8 @@ pe_status launch_correction(pe_ctx* c, double* num, double* den) {
   const int blocks = (int)((c->g.ndof + threads - 1) / threads);
   if (blocks > c->max_blocks) return pe_fail(PE_EINVAL, "correction: partials buffer too small");
   correction_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->muM_axis, c->coefG, c->gG, c->Fbar, c->Gold,
-                                                       c->U, c->partials);
-  PE_CUDA_TRY(cudaGetLastError());
-  final_reduce_kernel<<<1, 1024, 0, c->stream>>>(c->partials, blocks, c->red);
-  c->launches += 2;
+                                                       c->U, c->partials, c->done_ctr, c->red);
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   PE_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));

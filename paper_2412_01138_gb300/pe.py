@@ -241,21 +241,26 @@ class Solver:
         self.close()
 
     # -- problem data -------------------------------------------------------
+    # The term arrays of u0 and f are marshalled once per solver (the problem is fixed for
+    # its lifetime; the library copies them in on every call and keeps no pointer).
+    def _u0_terms(self):
+        if getattr(self, "_u0_arr", None) is None:
+            self._u0_arr = make_terms(self.prob.u0)
+        return self._u0_arr
+
     def _field(self, kind: int, nodal=None):
         prob = self.prob
         if kind == PE_FIELD_NODAL:
             return pe_field(kind, 0, None, _ptr(nodal))
-        terms = make_terms(prob.u0)
-        self._keep.append(terms)
-        return pe_field(kind, len(prob.u0), C.cast(terms, C.POINTER(pe_term)), None)
+        return pe_field(kind, len(prob.u0), C.cast(self._u0_terms(), C.POINTER(pe_term)), None)
 
     def _forcing(self):
-        terms = make_terms(self.prob.forcing)
-        self._keep.append(terms)
-        return pe_forcing(len(self.prob.forcing), C.cast(terms, C.POINTER(pe_term)))
+        if getattr(self, "_f_struct", None) is None:
+            self._f_arr = make_terms(self.prob.forcing)
+            self._f_struct = pe_forcing(len(self.prob.forcing), C.cast(self._f_arr, C.POINTER(pe_term)))
+        return self._f_struct
 
     def set_problem(self, u0_kind: int = PE_FIELD_TERMS_SEPARABLE, nodal=None):
-        self._keep = []
         f = self._field(u0_kind, nodal)
         _check(self._lib.pe_set_problem(self.ctx, C.byref(f), C.byref(self._forcing())))
 
@@ -272,7 +277,6 @@ class Solver:
 
     def solve(self, tol: Optional[float] = None, u0_kind: int = PE_FIELD_TERMS_SEPARABLE, nodal=None,
               history: int = 64) -> dict:
-        self._keep = []
         f = self._field(u0_kind, nodal)
         hist = (C.c_double * history)()
         res = pe_result()
