@@ -42,21 +42,6 @@ __device__ inline double eval_space(int kind, const double* p, double x, double 
   }
 }
 
-// The same factor in float32 arithmetic (loads of the mixed-precision general path).
-__device__ inline float eval_space_f(int kind, const double* pd, float x, double t = 0.0) {
-  const float p0 = (float)pd[0], p1 = (float)pd[1], p2 = (float)pd[2], p3 = (float)pd[3];
-  switch (kind) {
-    case PE_S_SIN: return sinf(p0 * x + p1);
-    case PE_S_GAUSS: { const float u = x - p0; return expf(-(u * u) / (2.0f * p1 * p1)); }
-    case PE_S_POLY: return p0 + x * (p1 + x * (p2 + x * p3));
-    case PE_S_MOVING_HAT: {
-      const float c = p0 + p1 * (float)sinpi(2.0 * pd[2] * t);
-      return fmaxf(1.0f - fabsf(x - c) / p3, 0.0f);
-    }
-    default: return 1.0f;
-  }
-}
-
 __device__ inline double eval_time(const pe_term& t, double tt) {
   if (t.tkind == PE_T_SIN) return sin(t.tp[0] * tt + t.tp[1]);
   return exp(t.tp[0] * tt);

@@ -52,11 +52,30 @@ __device__ inline double stage_time(const StageGen& G, int idx) {
 // right node and h int g (1-s) ds to its left node; each element's quadrature is evaluated
 // once (into shared memory) and node k sums the rising part of element k and the falling
 // part of element k+1.  TL = float evaluates the factors in float32 (mixed precision).
+// Per block (one term, axis and stage) the factor's parameters, the moving hat's centre at
+// t_st and the quadrature weights w_q s_q, w_q (1 - s_q) are converted once into shared
+// memory; per element only the node positions are formed in float64 (lo + m h + s_q h).
+
+// The spatial factor at x from parameters already in TL (the moving hat's centre in p[0]).
+template <typename TL>
+__device__ __forceinline__ TL eval_factor(int kind, const TL* p, TL x) {
+  switch (kind) {
+    case PE_S_SIN: return sin(p[0] * x + p[1]);
+    case PE_S_GAUSS: { const TL u = x - p[0]; return exp(-(u * u) / (TL(2) * p[1] * p[1])); }
+    case PE_S_POLY: return p[0] + x * (p[1] + x * (p[2] + x * p[3]));
+    case PE_S_MOVING_HAT: return fmax(TL(1) - fabs(x - p[0]) / p[3], TL(0));
+    default: return TL(1);
+  }
+}
+
 template <typename TL>
 __global__ void __launch_bounds__(128) gen_loads_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2,
                                                         double h0, double h1, double h2, Gauss Q, StageGen SG,
                                                         int nsum, TL* __restrict__ L) {
   __shared__ TL rise[129], fall[129];
+  __shared__ TL sp[4], sws[8], sw1s[8];
+  __shared__ double ssh[8];
+  __shared__ int skind;
   const int st = blockIdx.z;
   const int ra = blockIdx.y;
   const int r = ra / g.d, a = ra % g.d;
@@ -64,10 +83,30 @@ __global__ void __launch_bounds__(128) gen_loads_kernel(TermsDev T, Geom g, doub
   const int n = g.n[a];
   const int k0 = blockIdx.x * 128;
   if (k0 >= n) return;  // uniform over the block
-  const double t = stage_time(SG, st);
   const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
   const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
-  const pe_term& tm = T.t[r];
+  const int nq = Q.npts;
+  if (threadIdx.x == 0) {
+    const pe_term& tm = T.t[r];
+    const int kind = tm.skind[a];
+    const double* pd = tm.sp[a];
+    double p0 = pd[0];
+    if (kind == PE_S_MOVING_HAT) p0 = pd[0] + pd[1] * sinpi(2.0 * pd[2] * stage_time(SG, st));
+    sp[0] = (TL)p0;
+    sp[1] = (TL)pd[1];
+    sp[2] = (TL)pd[2];
+    sp[3] = (TL)pd[3];
+    skind = kind;
+  } else if (threadIdx.x <= 8) {
+    const int q = threadIdx.x - 1;
+    if (q < nq) {
+      sws[q] = (TL)(Q.w[q] * Q.s[q]);
+      sw1s[q] = (TL)(Q.w[q] * (1.0 - Q.s[q]));
+      ssh[q] = Q.s[q] * h;
+    }
+  }
+  __syncthreads();
+  const int kind = skind;
   // elements k0 .. k0 + 128 (the last one only for its falling part); on a periodic axis
   // node k's elements are k-1 and k, i.e. k0-1 .. k0+127 taken modulo n
   const bool per = g.per[a] != 0;
@@ -76,14 +115,11 @@ __global__ void __launch_bounds__(128) gen_loads_kernel(TermsDev T, Geom g, doub
     if (per) m = (m + n) % n;
     TL up = TL(0), dn = TL(0);
     if (per || m <= n) {
-      for (int qi = 0; qi < Q.npts; ++qi) {
-        const TL x = (TL)(lo + ((double)m + Q.s[qi]) * h);
-        TL gv;
-        if constexpr (sizeof(TL) == 4) gv = eval_space_f(tm.skind[a], tm.sp[a], x, t);
-        else gv = eval_space(tm.skind[a], tm.sp[a], x, t);
-        const TL wg = (TL)Q.w[qi] * gv;
-        up += wg * (TL)Q.s[qi];
-        dn += wg * (TL)(1.0 - Q.s[qi]);
+      const double xm = fma((double)m, h, lo);
+      for (int qi = 0; qi < nq; ++qi) {
+        const TL gv = eval_factor<TL>(kind, sp, (TL)(xm + ssh[qi]));
+        up += sws[qi] * gv;
+        dn += sw1s[qi] * gv;
       }
     }
     rise[i] = up;
