@@ -154,7 +154,7 @@ typedef struct {
 
 /*
  * pe_setup -- validate the problem, allocate the context and its device memory
- * (slice arrays U, G(U) and F^M(U) of N x Ndof float64 each, plus tables).
+ * (slice arrays U, F^M(U) and the coarse forcing of N x Ndof float64 each, plus tables).
  * d in 1..3; n: host int32[d], n_a >= 1; box: host double[2d] as lo0,hi0,lo1,hi1,..;
  * D > 0; T > 0; n_slices = N >= 1; n_substeps = M >= 1; fine (q nodes) and
  * coarse (p nodes) tableaux; opt may be NULL (defaults).  On success *out owns
@@ -236,7 +236,8 @@ pe_status pe_forcing_modal(pe_ctx* ctx, double t, double* out);
 /* Interpolation nodes actually used (which = 0 fine, 1 coarse) into host c_out[s]. */
 pe_status pe_get_nodes(pe_ctx* ctx, int32_t which, double* c_out);
 
-/* Parareal state (k, U, G(U)) to / from a host buffer: resume gives identical results.
+/* Parareal state (k, U^0..U^N) to / from a host buffer: resume gives identical results
+ * (the correction needs no stored coarse values: G is affine in its argument).
  * pe_save_state with buf == NULL reports the size in *bytes. */
 pe_status pe_save_state(pe_ctx* ctx, void* buf, size_t* bytes);
 pe_status pe_load_state(pe_ctx* ctx, const void* buf, size_t bytes);

@@ -126,7 +126,7 @@ void free_ctx(pe_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->muM_axis, c->ratio_axis, c->S[0], c->S[1], c->S[2], c->S32[0], c->S32[1], c->S32[2],
                   c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
-                  c->coefF32, c->U, c->Gold, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
+                  c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
                   c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr};
   for (void* p : ptrs)
@@ -272,7 +272,6 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->coefG, (size_t)(c->p + 1) * nd);
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->coefF32, (size_t)(c->q + 2) * nd);
   if (st == PE_OK) st = dev_alloc(&c->U, (N + 1) * nd);
-  if (st == PE_OK) st = dev_alloc(&c->Gold, N * nd);
   if (st == PE_OK) st = dev_alloc(&c->Fbar, N * nd);
   if (st == PE_OK && c->cache_forced) st = dev_alloc(&c->Fz, N * nd);
   if (st == PE_OK) st = dev_alloc(&c->gG, N * nd);
@@ -621,13 +620,13 @@ struct StateHeader {
   int64_t ndof;
   int32_t n[3], pad2;
 };
-const uint64_t kStateMagic = 0x3130353135504550ull;  // "PEP51501"
+const uint64_t kStateMagic = 0x3230353135504550ull;  // "PEP51502"
 }  // namespace
 
 extern "C" pe_status pe_save_state(pe_ctx* c, void* buf, size_t* bytes) {
   if (!c || !bytes) return pe_fail(PE_EINVAL, "pe_save_state: NULL argument");
   const size_t nd = (size_t)c->g.ndof, N = (size_t)c->N;
-  const size_t need = sizeof(StateHeader) + sizeof(double) * ((N + 1) * nd + N * nd);
+  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + 1) * nd;
   if (!buf) {
     *bytes = need;
     return PE_OK;
@@ -641,8 +640,6 @@ extern "C" pe_status pe_save_state(pe_ctx* c, void* buf, size_t* bytes) {
   memcpy(buf, &h, sizeof(h));
   char* p = (char*)buf + sizeof(h);
   PE_CUDA_TRY(cudaMemcpyAsync(p, c->U, sizeof(double) * (N + 1) * nd, cudaMemcpyDeviceToHost, c->stream));
-  PE_CUDA_TRY(cudaMemcpyAsync(p + sizeof(double) * (N + 1) * nd, c->Gold, sizeof(double) * N * nd,
-                              cudaMemcpyDeviceToHost, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   *bytes = need;
   return PE_OK;
@@ -652,7 +649,7 @@ extern "C" pe_status pe_load_state(pe_ctx* c, const void* buf, size_t bytes) {
   if (!c || !buf) return pe_fail(PE_EINVAL, "pe_load_state: NULL argument");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_load_state: set the same problem first (pe_set_problem)");
   const size_t nd = (size_t)c->g.ndof, N = (size_t)c->N;
-  const size_t need = sizeof(StateHeader) + sizeof(double) * ((N + 1) * nd + N * nd);
+  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + 1) * nd;
   if (bytes < need) return pe_fail(PE_EINVAL, "pe_load_state: buffer too small");
   StateHeader h;
   memcpy(&h, buf, sizeof(h));
@@ -660,8 +657,6 @@ extern "C" pe_status pe_load_state(pe_ctx* c, const void* buf, size_t bytes) {
     return pe_fail(PE_EINVAL, "pe_load_state: state does not match this context");
   const char* p = (const char*)buf + sizeof(h);
   PE_CUDA_TRY(cudaMemcpyAsync(c->U, p, sizeof(double) * (N + 1) * nd, cudaMemcpyHostToDevice, c->stream));
-  PE_CUDA_TRY(cudaMemcpyAsync(c->Gold, p + sizeof(double) * (N + 1) * nd, sizeof(double) * N * nd,
-                              cudaMemcpyHostToDevice, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->k = h.k;
   c->have_output = false;

@@ -283,8 +283,7 @@ template <typename TF>
 __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__ probs,
                                                        const ModeItem* __restrict__ items, int n_items,
                                                        const double* __restrict__ axisF, const TF* __restrict__ AG,
-                                                       const double* __restrict__ coefG, double* __restrict__ U,
-                                                       double* __restrict__ Gold, double* __restrict__ gG) {
+                                                       const double* __restrict__ coefG, double* __restrict__ U) {
   extern __shared__ __align__(16) unsigned char sP_raw[];
   TF* sP = reinterpret_cast<TF*>(sP_raw);  // [PE_BATCH_MAX_TERMS][256]
   const int tid = threadIdx.x, BD = blockDim.x;
@@ -307,8 +306,6 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
     TF b[PE_MAX_S];
     for (int i = 0; i < B.p; ++i) b[i] = (TF)cg[(1 + i) * nd + J];
     double* Up = U + B.oU;
-    double* Gp = Gold + B.oS;
-    double* gp = gG + B.oS;
     const TF* ag = AG + B.oAG;
     double c = Up[J];
     for (int n = 0; n < B.N; ++n) {
@@ -319,10 +316,8 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
         for (int r = 0; r < R; ++r) gi = fma(__ldg(arow + r), sP[r * BD + tid], gi);
         acc = fma(b[i], gi, acc);
       }
-      gp[(int64_t)n * nd + J] = (double)acc;
       c = fma(E, c, (double)acc);
       Up[(int64_t)(n + 1) * nd + J] = c;
-      Gp[(int64_t)n * nd + J] = c;
     }
   }
 }
@@ -343,14 +338,15 @@ __device__ inline T block_sum(T v, T* sh) {
   return out;
 }
 
-// correction + residual partial sums of every active problem (item-strided grid)
+// correction + residual partial sums of every active problem (item-strided grid).  G is
+// affine in its argument, so U^{n+1,(k+1)} = G(U^{n,(k+1)}) + Fbar^{n+1} - G(U^{n,(k)}) is
+// evaluated as Fbar^{n+1} + E_G (U^{n,(k+1)} - U^{n,(k)}) (no stored coarse values).
 __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restrict__ probs,
                                                            const ModeItem* __restrict__ items, int n_items,
                                                            const int* __restrict__ active,
                                                            const double* __restrict__ muM,
                                                            const double* __restrict__ coefG,
-                                                           const double* __restrict__ gG,
-                                                           const double* __restrict__ Fbar, double* __restrict__ Gold,
+                                                           const double* __restrict__ Fbar,
                                                            double* __restrict__ U, double* __restrict__ partials) {
   __shared__ double sh[32];
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -368,20 +364,17 @@ __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restri
       for (int a = 1; a < B.g.d; ++a) w *= muM[B.oMu + B.g.off[a] + j[a]];
       const double E = coefG[B.oCG + J];
       double* Up = U + B.oU;
-      double* Gp = Gold + B.oS;
-      const double* gp = gG + B.oS;
       const double* fp = Fbar + B.oS;
-      double unew = Up[J];
-      // the loads of the next kPF slices are issued while the current kPF are combined
-      double g0[kPF], f0[kPF], o0[kPF], u0[kPF], g1[kPF], f1[kPF], o1[kPF], u1[kPF];
+      // U^0 is the same in every iterate; the loads of the next kPF slices are issued
+      // while the current kPF are combined
+      double u_new = Up[J], u_old = u_new;
+      double f0[kPF], o0[kPF], f1[kPF], o1[kPF];
 #pragma unroll
       for (int e = 0; e < kPF; ++e) {
         const int64_t o = (int64_t)e * nd + J;
         const bool in = e < N;
-        g0[e] = in ? gp[o] : 0.0;
         f0[e] = in ? fp[o] : 0.0;
-        o0[e] = in ? Gp[o] : 0.0;
-        u0[e] = in ? Up[o + nd] : 0.0;
+        o0[e] = in ? Up[o + nd] : 0.0;
       }
       for (int n0 = 0; n0 < N; n0 += kPF) {
 #pragma unroll
@@ -389,32 +382,26 @@ __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restri
           const int n = n0 + kPF + e;
           const int64_t o = (int64_t)n * nd + J;
           const bool in = n < N;
-          g1[e] = in ? gp[o] : 0.0;
           f1[e] = in ? fp[o] : 0.0;
-          o1[e] = in ? Gp[o] : 0.0;
-          u1[e] = in ? Up[o + nd] : 0.0;
+          o1[e] = in ? Up[o + nd] : 0.0;
         }
 #pragma unroll
         for (int e = 0; e < kPF; ++e) {
           const int n = n0 + e;
           if (n < N) {
-            const int64_t o = (int64_t)n * nd + J;
-            const double Gn = fma(E, unew, g0[e]);
-            const double nxt = (Gn + f0[e]) - o0[e];
-            Gp[o] = Gn;
-            Up[o + nd] = nxt;
-            const double df = nxt - u0[e];
+            const double nxt = fma(E, u_new - u_old, f0[e]);
+            Up[(int64_t)(n + 1) * nd + J] = nxt;
+            const double df = nxt - o0[e];
             sd = fma(df, df, sd);
             su = fma(nxt, nxt, su);
-            unew = nxt;
+            u_new = nxt;
+            u_old = o0[e];
           }
         }
 #pragma unroll
         for (int e = 0; e < kPF; ++e) {
-          g0[e] = g1[e];
           f0[e] = f1[e];
           o0[e] = o1[e];
-          u0[e] = u1[e];
         }
       }
     }
@@ -517,10 +504,10 @@ pe_status batch_launch_prepare(pe_batch* b) {
   // form evaluates it in float32, the recurrence stays float64
   if (b->precision == PE_MIXED)
     b_coarse_kernel<float><<<grid_items, 256, sizeof(float) * PE_BATCH_MAX_TERMS * 256, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, b->Gold, b->gG);
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U);
   else
     b_coarse_kernel<double><<<grid_items, 256, sizeof(double) * PE_BATCH_MAX_TERMS * 256, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, b->Gold, b->gG);
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U);
   b->launches += 5;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
@@ -559,7 +546,7 @@ pe_status batch_enqueue_iteration(pe_batch* b, cudaStream_t st, double tol) {
   PE_CUDA_TRY(cudaMemsetAsync(b->n_active, 0, sizeof(int), st));
   PE_TRY(launch_fine(b, st, b->tune_threads, b->tune_ctas));
   b_correction_kernel<<<b->sm_count * 8, 256, 0, st>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->active,
-                                                       b->muM, b->coefG, b->gG, b->Fbar, b->Gold, b->U, b->partials);
+                                                       b->muM, b->coefG, b->Fbar, b->U, b->partials);
   b_reduce_kernel<<<b->P, 256, 0, st>>>(b->d_probs, b->P, b->partials, b->active, b->kcount, b->resid, tol,
                                         b->n_active, b->nonfinite);
   PE_CUDA_TRY(cudaMemcpyAsync(b->h_flags, b->n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -19,7 +19,7 @@ struct BProb {
   double cF[PE_MAX_S], cG[PE_MAX_S];
   double lagF[PE_MAX_S][PE_MAX_S], lagG[PE_MAX_S][PE_MAX_S];
   int64_t oU;    // U arena: (N+1)*ndof
-  int64_t oS;    // Gold/Fbar/gG arenas: N*ndof
+  int64_t oS;    // Fbar arena: N*ndof
   int64_t oCF;   // coefF / coefF32 arenas: (q+2)*ndof
   int64_t oCG;   // coefG arena: (p+1)*ndof
   int64_t oAx;   // axisF / axisF32: R*nsum
@@ -103,7 +103,7 @@ struct pe_batch {
   double *muM = nullptr, *ratio = nullptr;
   double *coefF = nullptr, *coefG = nullptr;
   float* coefF32 = nullptr;
-  double *U = nullptr, *Gold = nullptr, *Fbar = nullptr, *gG = nullptr;
+  double *U = nullptr, *Fbar = nullptr;
   double *axisF = nullptr, *axisU0 = nullptr;
   float* axisF32 = nullptr;
   double *AF = nullptr, *AG = nullptr;

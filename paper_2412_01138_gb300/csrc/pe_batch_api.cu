@@ -39,7 +39,7 @@ void free_batch(pe_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   void* ptrs[] = {b->d_probs, b->d_terms, b->d_mode_items, b->fine128.d_items, b->fine256.d_items,
                   b->d_factor_jobs, b->d_mu_prefix, b->d_tt_prefix, b->muM, b->ratio, b->coefF, b->coefG,
-                  b->coefF32, b->U, b->Gold, b->Fbar, b->gG, b->axisF, b->axisU0, b->axisF32, b->AF, b->AG,
+                  b->coefF32, b->U, b->Fbar, b->axisF, b->axisU0, b->axisF32, b->AF, b->AG,
                   b->AF32, b->partials, b->active, b->kcount, b->resid, b->counter, b->dflags,
                   b->W, b->W32, b->Z, b->d_cols, b->AG32, b->Z32};
   for (void* p : ptrs)
@@ -254,9 +254,7 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
   if (st == PE_OK && mixed) st = balloc(&b->coefF32, oCF);
   if (st == PE_OK) st = balloc(&b->coefG, oCG);
   if (st == PE_OK) st = balloc(&b->U, oU);
-  if (st == PE_OK) st = balloc(&b->Gold, oS);
   if (st == PE_OK) st = balloc(&b->Fbar, oS);
-  if (st == PE_OK) st = balloc(&b->gG, oS);
   if (st == PE_OK) st = balloc(&b->axisF, oAx);
   if (st == PE_OK && mixed) st = balloc(&b->axisF32, oAx);
   if (st == PE_OK) st = balloc(&b->axisU0, oAxU);

@@ -89,7 +89,6 @@ struct pe_ctx {
   double* coefG = nullptr;      // [(p+1) * ndof]: E, dT*b_1..p
   float* coefF32 = nullptr;     // [(q+2) * ndof]: E_hi, E_lo, dt*b_i (float)
   double* U = nullptr;          // [(N+1) * ndof]
-  double* Gold = nullptr;       // [N * ndof]
   double* Fz = nullptr;         // [N * ndof] cached F^M(0) per slice (cache_forced)
   int fz_prec = -1;             // precision Fz was computed in, -1: none for this problem
   int64_t sweeps = 0;           // fine sweeps executed since the last reset

@@ -6,10 +6,15 @@
 // one mode and walks the slices n = 0..N-1 sequentially (the "sequential"
 // parts of Algorithm 1 are sequential in n only).
 //
-//   coarse sweep   U^{n+1,(0)} = G(U^{n,(0)}) = E_G U^n + gG_n, stored G(U^{n,(0)});
-//                  the coarse forcing gG_n (independent of the iterate) is kept.
-//   correction     U^{n+1,(k+1)} = G(U^{n,(k+1)}) + Fbar^{n+1} - G(U^{n,(k)})
-//                  and the float64 sums  sum mu^M_J (U^{new} - U^{old})^2, sum mu^M_J (U^{new})^2
+//   coarse sweep   U^{n+1,(0)} = G(U^{n,(0)}) = E_G U^n + gG_n.
+//   correction     U^{n+1,(k+1)} = G(U^{n,(k+1)}) + Fbar^{n+1} - G(U^{n,(k)}).  G is affine
+//                  in its argument, G(v) = E_G v + gG_n (a learned correction adds a term
+//                  that does not depend on v), so the update is evaluated as
+//                    U^{n+1,(k+1)} = Fbar^{n+1} + E_G (U^{n,(k+1)} - U^{n,(k)}):
+//                  the same value, without G(U^{n,(k)}) stored between iterations and
+//                  without the cancellation of the two G terms; it reads Fbar and the
+//                  old U and writes the new U (3 words per mode and slice instead of 6).
+//                  Float64 sums  sum mu^M_J (U^{new} - U^{old})^2, sum mu^M_J (U^{new})^2
 //                  (per-CTA partial sums, added by the last CTA to finish).
 #include "pe_internal.h"
 
@@ -120,7 +125,7 @@ constexpr int kPF = 4;
 // Sequential coarse sweep U^{n+1,(0)} = E_G U^{n,(0)} + gG_n (one thread per mode).
 __global__ void __launch_bounds__(256) coarse_recurrence_kernel(Geom g, int N, const double* __restrict__ coefG,
                                                                const double* __restrict__ gG,
-                                                               double* __restrict__ U, double* __restrict__ Gold) {
+                                                               double* __restrict__ U) {
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   const int64_t nd = g.ndof;
@@ -141,7 +146,6 @@ __global__ void __launch_bounds__(256) coarse_recurrence_kernel(Geom g, int N, c
       if (n < N) {
         c = fma(E, c, cur[e]);
         U[(int64_t)(n + 1) * nd + J] = c;
-        Gold[(int64_t)n * nd + J] = c;
       }
     }
 #pragma unroll
@@ -167,9 +171,8 @@ __device__ inline T block_sum(T v, T* sh) {
 
 __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const double* __restrict__ muM_axis,
                                                          const double* __restrict__ coefG,
-                                                         const double* __restrict__ gG,
-                                                         const double* __restrict__ Fbar, double* __restrict__ Gold,
-                                                         double* __restrict__ U, double* __restrict__ partials,
+                                                         const double* __restrict__ Fbar, double* __restrict__ U,
+                                                         double* __restrict__ partials,
                                                          unsigned int* __restrict__ done, double* __restrict__ red) {
   __shared__ double sh[32];
   __shared__ bool s_last;
@@ -182,17 +185,16 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
     w = muM_axis[g.off[0] + j[0]];
     for (int a = 1; a < g.d; ++a) w *= muM_axis[g.off[a] + j[a]];
     const double E = coefG[J];
-    double unew = U[J];
-    // per slice n: gG_n, Fbar^{n+1}, G(U^{n,(k)}) and the old U^{n+1} (for the residual)
-    double g0[kPF], f0[kPF], o0[kPF], u0[kPF], g1[kPF], f1[kPF], o1[kPF], u1[kPF];
+    // U^0 is the same in every iterate: U^{0,(k+1)} - U^{0,(k)} = 0
+    double u_new = U[J], u_old = u_new;
+    // per slice n: Fbar^{n+1} = F(U^{n,(k)}) and the old U^{n+1} (the next step's U^{n,(k)})
+    double f0[kPF], o0[kPF], f1[kPF], o1[kPF];
 #pragma unroll
     for (int e = 0; e < kPF; ++e) {
       const int64_t o = (int64_t)e * nd + J;
       const bool in = e < N;
-      g0[e] = in ? gG[o] : 0.0;
       f0[e] = in ? Fbar[o] : 0.0;
-      o0[e] = in ? Gold[o] : 0.0;
-      u0[e] = in ? U[o + nd] : 0.0;
+      o0[e] = in ? U[o + nd] : 0.0;
     }
     for (int n0 = 0; n0 < N; n0 += kPF) {
 #pragma unroll
@@ -200,32 +202,26 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
         const int n = n0 + kPF + e;
         const int64_t o = (int64_t)n * nd + J;
         const bool in = n < N;
-        g1[e] = in ? gG[o] : 0.0;
         f1[e] = in ? Fbar[o] : 0.0;
-        o1[e] = in ? Gold[o] : 0.0;
-        u1[e] = in ? U[o + nd] : 0.0;
+        o1[e] = in ? U[o + nd] : 0.0;
       }
 #pragma unroll
       for (int e = 0; e < kPF; ++e) {
         const int n = n0 + e;
         if (n < N) {
-          const int64_t o = (int64_t)n * nd + J;
-          const double Gn = fma(E, unew, g0[e]);
-          const double nxt = (Gn + f0[e]) - o0[e];
-          Gold[o] = Gn;
-          U[o + nd] = nxt;
-          const double df = nxt - u0[e];
+          const double nxt = fma(E, u_new - u_old, f0[e]);
+          U[(int64_t)(n + 1) * nd + J] = nxt;
+          const double df = nxt - o0[e];
           sd = fma(df, df, sd);
           su = fma(nxt, nxt, su);
-          unew = nxt;
+          u_new = nxt;
+          u_old = o0[e];
         }
       }
 #pragma unroll
       for (int e = 0; e < kPF; ++e) {
-        g0[e] = g1[e];
         f0[e] = f1[e];
         o0[e] = o1[e];
-        u0[e] = u1[e];
       }
     }
   }
@@ -266,7 +262,7 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
   const unsigned blocks = (unsigned)((c->g.ndof + threads - 1) / threads);
   if (c->forcing_path == PE_FORCING_GENERAL) {
     PE_TRY(launch_general_coarse_forcing(c));
-    coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U, c->Gold);
+    coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U);
     c->launches += 1;
     PE_CUDA_TRY(cudaGetLastError());
     return PE_OK;
@@ -279,7 +275,7 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
   else PE_TRY(launch_coarse_forcing_t<double>(c, blocks, threads, SL, c->axisF, c->AG));
   // learned correction G'(v) = G(v) + delta^ (no-op unless a trained network is attached)
   PE_TRY(launch_learned_correction(c));
-  coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U, c->Gold);
+  coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U);
   c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
@@ -289,8 +285,8 @@ pe_status launch_correction(pe_ctx* c, double* num, double* den) {
   const int threads = 256;
   const int blocks = (int)((c->g.ndof + threads - 1) / threads);
   if (blocks > c->max_blocks) return pe_fail(PE_EINVAL, "correction: partials buffer too small");
-  correction_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->muM_axis, c->coefG, c->gG, c->Fbar, c->Gold,
-                                                       c->U, c->partials, c->done_ctr, c->red);
+  correction_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->muM_axis, c->coefG, c->Fbar, c->U,
+                                                       c->partials, c->done_ctr, c->red);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   PE_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
