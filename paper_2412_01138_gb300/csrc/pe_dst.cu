@@ -236,6 +236,122 @@ __global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, 
   }
 }
 
+// Half-length DST-I of one pencil pair per CTA, for float64 passes with few pencils: the
+// fold, complex FFT of N = n + 1 points and unfold of the half-length form (see the warp
+// kernel below), with the radix-2 butterflies and the prefix sum spread over the CTA so
+// that all four SM sub-partitions' float64 units work on the pair (about half the float64
+// work of the odd extension).  Shared memory: the pair (N + 1 values), the FFT buffer (N)
+// and the warp totals of the scan.
+template <typename T>
+__global__ void __launch_bounds__(256) dst_half_block_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
+                                                             int logN, int64_t inner, int64_t npencils, T scale,
+                                                             const Cplx<T>* __restrict__ tw,
+                                                             const T* __restrict__ sinN) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN, H = N / 2;
+  Cplx<T>* x = reinterpret_cast<Cplx<T>*>(smem_raw);  // x_j of both pencils, j = 0..N
+  Cplx<T>* z = x + (N + 1);                           // FFT buffer, bit-reversed fold
+  Cplx<T>* wsum = z + N;                              // warp totals of the scan
+  const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t pa = 2 * (int64_t)blockIdx.x, pb = pa + 1;
+  const bool has_b = pb < npencils;
+  const int64_t oa = (pa / inner) * (int64_t)n * inner + (pa % inner);
+  const int64_t ob = has_b ? (pb / inner) * (int64_t)n * inner + (pb % inner) : 0;
+  for (int j = tid; j <= N; j += B) {
+    T va = T(0), vb = T(0);
+    if (j >= 1 && j <= n) {
+      va = in[oa + (int64_t)(j - 1) * inner];
+      if (has_b) vb = in[ob + (int64_t)(j - 1) * inner];
+    }
+    x[j] = Cplx<T>{va, vb};
+  }
+  __syncthreads();
+  // fold y_j = sin(pi j/N)(x_j + x_{N-j}) + (x_j - x_{N-j})/2 of both pencils, z = y^a + i y^b
+  const int shift = 32 - logN;
+  for (int j = tid; j < N; j += B) {
+    const Cplx<T> xj = x[j];
+    const Cplx<T> xm = j == 0 ? Cplx<T>{T(0), T(0)} : x[N - j];
+    const T sj = sinN[j];
+    z[__brev((unsigned)j) >> shift] = Cplx<T>{sj * (xj.re + xm.re) + T(0.5) * (xj.re - xm.re),
+                                              sj * (xj.im + xm.im) + T(0.5) * (xj.im - xm.im)};
+  }
+  __syncthreads();
+  // radix-2 decimation in time, twiddles e^{-2 pi i k/N}
+  for (int st = 1; st <= logN; ++st) {
+    const int half = 1 << (st - 1), tstride = N >> st;
+    for (int b = tid; b < H; b += B) {
+      const int grp = b >> (st - 1), pos = b & (half - 1);
+      const int i0 = grp * 2 * half + pos, i1 = i0 + half;
+      const Cplx<T> w = tw[pos * tstride];
+      const Cplx<T> u = z[i0], v = z[i1];
+      const T tr = w.re * v.re - w.im * v.im;
+      const T ti = w.re * v.im + w.im * v.re;
+      z[i0] = Cplx<T>{u.re + tr, u.im + ti};
+      z[i1] = Cplx<T>{u.re - tr, u.im - ti};
+    }
+    __syncthreads();
+  }
+  // unfold: F_{2k} = I_k, F_{2k+1} = R_0/2 + R_1 + ... + R_k (k < N/2) for both pencils;
+  // thread tid owns the contiguous k = tid*C .. tid*C + C - 1
+  constexpr int CMAX = 2;  // N <= 1024 and 256 threads
+  const int C = (H + B - 1) / B;
+  T ia[CMAX], ib[CMAX], sa[CMAX], sb[CMAX];
+  T ta = T(0), tb = T(0);
+#pragma unroll
+  for (int c = 0; c < CMAX; ++c) {
+    const int k = tid * C + c;
+    ia[c] = ib[c] = sa[c] = sb[c] = T(0);
+    if (c < C && k < H) {
+      const Cplx<T> Z = z[k];
+      const Cplx<T> Wm = z[(N - k) & (N - 1)];
+      T ra = T(0.5) * (Z.re + Wm.re), rb = T(0.5) * (Z.im + Wm.im);
+      ia[c] = T(0.5) * (Wm.im - Z.im);
+      ib[c] = T(0.5) * (Z.re - Wm.re);
+      if (k == 0) {
+        ra *= T(0.5);
+        rb *= T(0.5);
+      }
+      ta += ra;
+      tb += rb;
+    }
+    sa[c] = ta;
+    sb[c] = tb;
+  }
+  // exclusive scan of the thread totals: within the warp by shuffles, then over the warps
+  T ea = ta, eb = tb;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T ua = __shfl_up_sync(0xffffffffu, ea, d), ub = __shfl_up_sync(0xffffffffu, eb, d);
+    if (lane >= d) {
+      ea += ua;
+      eb += ub;
+    }
+  }
+  if (lane == 31) wsum[warp] = Cplx<T>{ea, eb};
+  __syncthreads();
+  T pre_a = T(0), pre_b = T(0);
+  for (int w = 0; w < warp; ++w) {
+    pre_a += wsum[w].re;
+    pre_b += wsum[w].im;
+  }
+  ea += pre_a - ta;
+  eb += pre_b - tb;
+#pragma unroll
+  for (int c = 0; c < CMAX; ++c) {
+    const int k = tid * C + c;
+    if (c < C && k < H) {
+      if (k > 0) x[2 * k] = Cplx<T>{ia[c], ib[c]};
+      x[2 * k + 1] = Cplx<T>{sa[c] + ea, sb[c] + eb};
+    }
+  }
+  __syncthreads();
+  for (int m = tid + 1; m <= n; m += B) {
+    const Cplx<T> F = x[m];
+    out[oa + (int64_t)(m - 1) * inner] = F.re * scale;
+    if (has_b) out[ob + (int64_t)(m - 1) * inner] = F.im * scale;
+  }
+}
+
 inline bool fft_size_ok(int n, int* logL) {
   const int np1 = n + 1;
   if (np1 < 2 || np1 > 1024 || (np1 & (np1 - 1)) != 0) return false;
@@ -1009,9 +1125,25 @@ pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int
   bool done = false;
   // Few pencils (small problems, the per-axis source factors): a warp per pencil pair
   // would leave most SMs idle behind the FFT's chain of dependent float64 latencies, so
-  // those go to the block-wide kernel, which spreads every pencil pair over a CTA.
+  // those go to the block-wide kernels, which spread every pencil pair over a CTA (float64
+  // in the half-length form from N = n + 1 = 16 on).
   if (npencils > kFewPencils) PE_TRY(fft_warp_axis<T>(in, out, outer, n, inner, logL, st, &done));
   if (done) return PE_OK;
+  if constexpr (sizeof(T) == 8) {
+    const int logN = logL - 1;
+    if (npencils <= kFewPencils && logN >= 4) {
+      const Cplx<T>* twN = twiddles<T>(logN, st);
+      const T* sinN = half_sines<T>(logN, st);
+      if (!twN || !sinN) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+      const int N = 1 << logN;
+      const size_t smem = sizeof(Cplx<T>) * ((size_t)2 * N + 1 + 8);
+      const int threads = N / 2 >= 256 ? 256 : (N / 2 >= 128 ? 128 : (N / 2 >= 64 ? 64 : 32));
+      dst_half_block_kernel<T><<<(unsigned)((npencils + 1) / 2), threads, smem, st>>>(
+          in, out, n, logN, inner, npencils, (T)sqrt(2.0 / (double)N), twN, sinN);
+      PE_CUDA_TRY(cudaGetLastError());
+      return PE_OK;
+    }
+  }
   // few pencils, short transforms (n + 1 < 16) and float64 at n + 1 = 1024: the block-wide radix-2 kernel;
   // pencil pairs per CTA: as many as keep >= 2 CTAs per SM, bounded by shared memory
   int max_pairs = (int)((48 * 1024) / ((size_t)L * sizeof(Cplx<T>)));
