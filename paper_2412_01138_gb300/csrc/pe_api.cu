@@ -134,6 +134,9 @@ void free_ctx(pe_ctx* c) {
   if (c->h_red) cudaFreeHost(c->h_red);
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -311,6 +314,10 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   }
   for (int i = 0; i < 8 && st == PE_OK; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = pe_cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  if (st == PE_OK && (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    st = pe_cuda_fail(cudaGetLastError(), "pe_setup: side stream");
   if (st == PE_OK) st = launch_axis_tables(c);
   for (int a = 0; a < d && st == PE_OK; ++a) st = build_dst_matrix(n[a], c->S[a], c->stream, c->g.per[a]);
   for (int a = 0; a < d && st == PE_OK; ++a)
@@ -437,6 +444,25 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     for (int i = 0; i < nf; ++i) c->terms[i] = f->terms[i];
     PE_TRY(expand_dirichlet_terms(c));
   }
+  // Nodal u0: its copy and forward transform (independent of the forcing) run on the side
+  // stream while the forcing tables are made on the main one; joined before the coarse sweep.
+  double* U0 = c->U;
+  const bool fork_u0 = u0->kind == PE_FIELD_NODAL && u0->nodal != nullptr;
+  if (fork_u0) {
+    PE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
+    PE_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    const bool dev = pe_is_device_ptr(u0->nodal);
+    cudaStream_t main_stream = c->stream;
+    c->stream = c->side;
+    pe_status st = PE_OK;
+    const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->g.ndof,
+                                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_set_problem: u0 copy");
+    if (st == PE_OK) st = dst_nd_f64(c, c->work0, U0);
+    c->stream = main_stream;
+    PE_TRY(st);
+    PE_CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+  }
   // The phi/b coefficient tables depend only on lam, dt, dT and the nodes: pe_setup made them.
   // Forcing: time factors, per-axis modal factors and the stage weights of the fine step.
   if (!general) {
@@ -446,8 +472,9 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   }
   PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
   // U^0 = P_h u0
-  double* U0 = c->U;
-  if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {
+  if (fork_u0) {
+    PE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  } else if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {
     PE_TRY(pe_validate_terms(u0->n_terms, u0->terms, c->g.d, "u0"));
     if (u0->n_terms == 0) {
       PE_CUDA_TRY(cudaMemsetAsync(U0, 0, sizeof(double) * c->g.ndof, c->stream));

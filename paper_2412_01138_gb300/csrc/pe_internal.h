@@ -100,6 +100,8 @@ struct pe_ctx {
   double* partials = nullptr;   // [2 * max_blocks]
   double* red = nullptr;        // [2] device
   unsigned int* done_ctr = nullptr;  // correction: CTAs finished (0 between launches)
+  cudaStream_t side = nullptr;  // second stream: the nodal u0 transform beside the forcing tables
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_red = nullptr;      // [2] pinned host
   int max_blocks = 0;
   // forcing (set by pe_set_problem)
