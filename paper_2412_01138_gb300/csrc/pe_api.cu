@@ -444,36 +444,40 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     for (int i = 0; i < nf; ++i) c->terms[i] = f->terms[i];
     PE_TRY(expand_dirichlet_terms(c));
   }
-  // Nodal u0: its copy and forward transform (independent of the forcing) run on the side
-  // stream while the forcing tables are made on the main one; joined before the coarse sweep.
+  // Work that does not depend on the per-axis forcing factors runs on the side stream while
+  // those are made on the main one: the copy and forward transform of nodal u0 and the time
+  // tables.  The main stream waits for it before the stage weights (which need the time
+  // tables' shifts) and the coarse sweep.
   double* U0 = c->U;
   const bool fork_u0 = u0->kind == PE_FIELD_NODAL && u0->nodal != nullptr;
-  if (fork_u0) {
+  const bool fork = fork_u0 || !general;
+  if (fork) {
     PE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
     PE_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    const bool dev = pe_is_device_ptr(u0->nodal);
     cudaStream_t main_stream = c->stream;
     c->stream = c->side;
     pe_status st = PE_OK;
-    const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->g.ndof,
-                                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_set_problem: u0 copy");
-    if (st == PE_OK) st = dst_nd_f64(c, c->work0, U0);
+    if (fork_u0) {
+      const bool dev = pe_is_device_ptr(u0->nodal);
+      const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->g.ndof,
+                                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_set_problem: u0 copy");
+      if (st == PE_OK) st = dst_nd_f64(c, c->work0, U0);
+    }
+    if (st == PE_OK && !general) st = launch_time_tables(c);
     c->stream = main_stream;
     PE_TRY(st);
     PE_CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
   }
   // The phi/b coefficient tables depend only on lam, dt, dT and the nodes: pe_setup made them.
-  // Forcing: time factors, per-axis modal factors and the stage weights of the fine step.
-  if (!general) {
-    PE_TRY(launch_time_tables(c));
-    PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1, c->lkind));
-    PE_TRY(launch_stage_weights(c));
-  }
+  // Forcing: per-axis modal factors, then (after the join) the stage weights of the fine step.
+  if (!general) PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1, c->lkind));
+  if (fork) PE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  if (!general) PE_TRY(launch_stage_weights(c));
   PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
   // U^0 = P_h u0
   if (fork_u0) {
-    PE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    // made on the side stream above
   } else if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {
     PE_TRY(pe_validate_terms(u0->n_terms, u0->terms, c->g.d, "u0"));
     if (u0->n_terms == 0) {
