@@ -242,26 +242,20 @@ __global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, 
 // that all four SM sub-partitions' float64 units work on the pair (about half the float64
 // work of the odd extension).  Shared memory: the pair (N + 1 values), the FFT buffer (N)
 // and the warp totals of the scan.
+// The CTA's pencil pair (a at in_a, b at in_b, stride `inner`, b absent when !has_b) in
+// x[1..n] on return: x[m] = (F^a_m, F^b_m), the unscaled sine sums.  x, z and wsum are
+// shared buffers of N + 1, N and 8 complex values.
 template <typename T>
-__global__ void __launch_bounds__(256) dst_half_block_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
-                                                             int logN, int64_t inner, int64_t npencils, T scale,
-                                                             const Cplx<T>* __restrict__ tw,
-                                                             const T* __restrict__ sinN) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void half_block_pair(const T* __restrict__ in_a, const T* __restrict__ in_b, bool has_b,
+                                                int64_t inner, int n, int logN, const Cplx<T>* __restrict__ tw,
+                                                const T* __restrict__ sinN, Cplx<T>* x, Cplx<T>* z, Cplx<T>* wsum) {
   const int N = 1 << logN, H = N / 2;
-  Cplx<T>* x = reinterpret_cast<Cplx<T>*>(smem_raw);  // x_j of both pencils, j = 0..N
-  Cplx<T>* z = x + (N + 1);                           // FFT buffer, bit-reversed fold
-  Cplx<T>* wsum = z + N;                              // warp totals of the scan
   const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t pa = 2 * (int64_t)blockIdx.x, pb = pa + 1;
-  const bool has_b = pb < npencils;
-  const int64_t oa = (pa / inner) * (int64_t)n * inner + (pa % inner);
-  const int64_t ob = has_b ? (pb / inner) * (int64_t)n * inner + (pb % inner) : 0;
   for (int j = tid; j <= N; j += B) {
     T va = T(0), vb = T(0);
     if (j >= 1 && j <= n) {
-      va = in[oa + (int64_t)(j - 1) * inner];
-      if (has_b) vb = in[ob + (int64_t)(j - 1) * inner];
+      va = in_a[(int64_t)(j - 1) * inner];
+      if (has_b) vb = in_b[(int64_t)(j - 1) * inner];
     }
     x[j] = Cplx<T>{va, vb};
   }
@@ -300,7 +294,7 @@ __global__ void __launch_bounds__(256) dst_half_block_kernel(const T* __restrict
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) {
     const int k = tid * C + c;
-    ia[c] = ib[c] = sa[c] = sb[c] = T(0);
+    ia[c] = ib[c] = T(0);
     if (c < C && k < H) {
       const Cplx<T> Z = z[k];
       const Cplx<T> Wm = z[(N - k) & (N - 1)];
@@ -345,10 +339,66 @@ __global__ void __launch_bounds__(256) dst_half_block_kernel(const T* __restrict
     }
   }
   __syncthreads();
-  for (int m = tid + 1; m <= n; m += B) {
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) dst_half_block_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
+                                                             int logN, int64_t inner, int64_t npencils, T scale,
+                                                             const Cplx<T>* __restrict__ tw,
+                                                             const T* __restrict__ sinN) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 1 << logN;
+  Cplx<T>* x = reinterpret_cast<Cplx<T>*>(smem_raw);
+  Cplx<T>* z = x + (N + 1);
+  Cplx<T>* wsum = z + N;
+  const int64_t pa = 2 * (int64_t)blockIdx.x, pb = pa + 1;
+  const bool has_b = pb < npencils;
+  const int64_t oa = (pa / inner) * (int64_t)n * inner + (pa % inner);
+  const int64_t ob = has_b ? (pb / inner) * (int64_t)n * inner + (pb % inner) : 0;
+  half_block_pair<T>(in + oa, in + ob, has_b, inner, n, logN, tw, sinN, x, z, wsum);
+  for (int m = threadIdx.x + 1; m <= n; m += blockDim.x) {
     const Cplx<T> F = x[m];
     out[oa + (int64_t)(m - 1) * inner] = F.re * scale;
     if (has_b) out[ob + (int64_t)(m - 1) * inner] = F.im * scale;
+  }
+}
+
+// The per-axis source factors of every axis in one launch (blockIdx.y = axis, blockIdx.x =
+// pair of terms): the consistent loads L[R off_a + r n_a + j] are transformed along their
+// axis and divided by mu^M_a(j), into fac (float64) and fac32 (float32, may be null).
+struct AxisFactorJob {
+  int d, R;
+  int n[PE_MAX_D], off[PE_MAX_D], logN[PE_MAX_D];
+  const Cplx<double>* tw[PE_MAX_D];
+  const double* sinN[PE_MAX_D];
+};
+__global__ void __launch_bounds__(256) axis_factor_dst_kernel(AxisFactorJob J, const double* __restrict__ loads,
+                                                              const double* __restrict__ muM,
+                                                              double* __restrict__ fac, float* __restrict__ fac32) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int a = blockIdx.y;
+  const int n = J.n[a], logN = J.logN[a], N = 1 << logN;
+  const int ra = 2 * blockIdx.x, rb = ra + 1;
+  if (ra >= J.R) return;  // uniform over the CTA
+  const bool has_b = rb < J.R;
+  Cplx<double>* x = reinterpret_cast<Cplx<double>*>(smem_raw);
+  Cplx<double>* z = x + (N + 1);
+  Cplx<double>* wsum = z + N;
+  const int64_t oa = (int64_t)J.R * J.off[a] + (int64_t)ra * n;
+  const int64_t ob = has_b ? oa + n : 0;
+  half_block_pair<double>(loads + oa, loads + ob, has_b, 1, n, logN, J.tw[a], J.sinN[a], x, z, wsum);
+  const double scale = sqrt(2.0 / (double)N);
+  for (int m = threadIdx.x + 1; m <= n; m += blockDim.x) {
+    const Cplx<double> F = x[m];
+    const double mu = muM[J.off[a] + m - 1];
+    const double va = F.re * scale / mu;
+    fac[oa + m - 1] = va;
+    if (fac32) fac32[oa + m - 1] = (float)va;
+    if (has_b) {
+      const double vb = F.im * scale / mu;
+      fac[ob + m - 1] = vb;
+      if (fac32) fac32[ob + m - 1] = (float)vb;
+    }
   }
 }
 
@@ -1256,6 +1306,37 @@ pe_status dst_axis_f64(const double* S, const double* in, double* out, int64_t o
 pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t outer, int n, int64_t inner,
                        cudaStream_t st, int periodic) {
   return dst_axis<float>(S, in, out, outer, n, inner, st, periodic);
+}
+
+// Per-axis source factors (a3), all axes in one launch: loads -> DST-I along the axis ->
+// division by mu^M.  Returns *done = false (nothing launched) unless every axis is a
+// Dirichlet axis with n_a + 1 a power of two between 16 and 1024.
+pe_status axis_factors_fused(pe_ctx* c, int R, const double* loads, double* fac, float* fac32, bool* done) {
+  *done = false;
+  AxisFactorJob J{};
+  J.d = c->g.d;
+  J.R = R;
+  size_t smem = 0;
+  for (int a = 0; a < c->g.d; ++a) {
+    int logL = 0;
+    if (c->g.per[a] || !fft_size_ok(c->g.n[a], &logL) || logL - 1 < 4) return PE_OK;
+    J.n[a] = c->g.n[a];
+    J.off[a] = c->g.off[a];
+    J.logN[a] = logL - 1;
+    J.tw[a] = twiddles<double>(logL - 1, c->stream);
+    J.sinN[a] = half_sines<double>(logL - 1, c->stream);
+    if (!J.tw[a] || !J.sinN[a]) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+    smem = std::max(smem, sizeof(Cplx<double>) * ((size_t)2 * (c->g.n[a] + 1) + 1 + 8));
+  }
+  int nmax = 1;
+  for (int a = 0; a < c->g.d; ++a) nmax = std::max(nmax, c->g.n[a] + 1);
+  const int threads = nmax / 2 >= 256 ? 256 : (nmax / 2 >= 128 ? 128 : (nmax / 2 >= 64 ? 64 : 32));
+  axis_factor_dst_kernel<<<dim3((unsigned)((R + 1) / 2), (unsigned)c->g.d), threads, smem, c->stream>>>(
+      J, loads, c->muM_axis, fac, fac32);
+  PE_CUDA_TRY(cudaGetLastError());
+  c->launches += 1;
+  *done = true;
+  return PE_OK;
 }
 
 pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out) {

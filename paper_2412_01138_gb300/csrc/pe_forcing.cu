@@ -285,13 +285,18 @@ pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, 
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   if (mode == 0) return PE_OK;
+  const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
+  if (mode == 1) {
+    bool done = false;
+    PE_TRY(axis_factors_fused(c, nterms, loads, axis_out, f32 ? c->axisF32 : nullptr, &done));
+    if (done) return PE_OK;
+  }
   for (int a = 0; a < c->g.d; ++a) {
     const int64_t base = (int64_t)nterms * c->g.off[a];
     PE_TRY(dst_axis_f64(c->S[a], loads + base, axis_out + base, nterms, c->g.n[a], 1, c->stream, c->g.per[a]));
     c->launches += 1;
   }
   if (mode == 2) return PE_OK;  // V^T of nodal values: no division by mu^M
-  const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
   divide_axis_mu_kernel<<<grid, 128, 0, c->stream>>>(c->g, nterms, c->muM_axis, axis_out,
                                                      f32 ? c->axisF32 : nullptr);
   c->launches += 1;

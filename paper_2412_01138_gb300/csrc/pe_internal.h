@@ -180,6 +180,9 @@ pe_status dst_axis_f64(const double* S, const double* in, double* out, int64_t o
 pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t outer, int n, int64_t inner,
                        cudaStream_t st, int periodic = 0);
 pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);  // uses c->S, c->work1
+// Per-axis source factors of every axis in one launch (loads -> DST-I -> / mu^M); *done = false when
+// an axis is periodic or n_a + 1 is not a power of two in 16..1024 (nothing launched then).
+pe_status axis_factors_fused(pe_ctx* c, int R, const double* loads, double* fac, float* fac32, bool* done);
 
 // pe_sweep.cu
 pe_status launch_coarse_sweep(pe_ctx* c);
