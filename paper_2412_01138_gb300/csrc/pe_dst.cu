@@ -556,11 +556,12 @@ __device__ __forceinline__ void dft_regs(Cplx<T> (&v)[R]) {
 }
 
 // Radix (as log2) of the pass that starts with `left` of the LOGL bits still to combine:
-// float32 uses 32-point passes from L = 512 on ([16, 32], [32, 32], [32, 32, 2]); float64
-// keeps 16-point passes (register budget).
+// float32 uses 32-point passes from L = 1024 on ([32, 32], [32, 32, 2]); L = 512 takes
+// [16, 16, 2] (a 32-point pass there leaves half the lanes idle: 16 groups of 32), and
+// float64 keeps 16-point passes (register budget).
 template <typename T>
 __host__ __device__ constexpr int pass_bits(int left, int logl) {
-  return (sizeof(T) == 4 && logl >= 9 && left >= 5 && !(logl == 9 && left == 9)) ? 5 : (left >= 4 ? 4 : left);
+  return (sizeof(T) == 4 && logl >= 10 && left >= 5) ? 5 : (left >= 4 ? 4 : left);
 }
 
 // One Stockham pass of radix R after NS points have been combined; tw = this pass's
