@@ -115,6 +115,99 @@ pe_status launch_coarse_forcing_t(pe_ctx* c, unsigned blocks, int threads, int S
   return PE_OK;
 }
 
+// Coarse sweep of k = 0 with the coarse forcing made on the fly (no learned correction to
+// add in between): one thread per mode walks the slices, forming gG_n = sum_i b_i sum_r
+// A_r(T_n + c_i dT) P_{r,J} from its register weights and the time factors of all slices
+// (staged in shared memory, rows of RB) and applying U^{n+1} = E_G U^n + gG_n, so gG is
+// neither written nor read back.
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) coarse_fused_kernel(Geom g, int N, int p, int R,
+                                                          const T* __restrict__ axisF, const T* __restrict__ AG,
+                                                          const double* __restrict__ coefG, double* __restrict__ U) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);  // [N * p][RB]
+  for (int e = threadIdx.x; e < N * p * RB; e += blockDim.x) {
+    const int row = e / RB, r = e - row * RB;
+    sA[e] = r < R ? AG[(int64_t)row * R + r] : T(0);
+  }
+  __syncthreads();
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= g.ndof) return;
+  const int64_t nd = g.ndof;
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
+  T P[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    T v = T(0);
+    if (r < R) {
+      v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+      for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+    }
+    P[r] = v;
+  }
+  T b[PE_MAX_S];
+#pragma unroll
+  for (int i = 0; i < PE_MAX_S; ++i) b[i] = i < p ? (T)coefG[(1 + i) * nd + J] : T(0);
+  const double E = coefG[J];
+  double c = U[J];
+  for (int n = 0; n < N; ++n) {
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < PE_MAX_S; ++i) {
+      if (i < p) {
+        const T* a = sA + ((int64_t)n * p + i) * RB;
+        T gi = T(0);
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+          for (int r = 0; r < RB; r += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(a + r);
+            gi = fmaf(v.x, P[r], gi);
+            gi = fmaf(v.y, P[r + 1], gi);
+            gi = fmaf(v.z, P[r + 2], gi);
+            gi = fmaf(v.w, P[r + 3], gi);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < RB; r += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(a + r);
+            gi = fma(v.x, P[r], gi);
+            gi = fma(v.y, P[r + 1], gi);
+          }
+        }
+        acc = fma(b[i], gi, acc);
+      }
+    }
+    c = fma(E, c, (double)acc);
+    U[(int64_t)(n + 1) * nd + J] = c;
+  }
+}
+
+// The fused coarse sweep when the time factors of all slices fit 48 KB of shared memory;
+// *done = false (nothing launched) otherwise.
+template <typename T>
+pe_status launch_coarse_fused_t(pe_ctx* c, unsigned blocks, int threads, const T* axisF, const T* AG, bool* done) {
+  *done = false;
+  const int RB = c->R < 4 ? 4 : (c->R + 3) / 4 * 4;
+  const size_t smem = sizeof(T) * (size_t)c->N * c->p * RB;
+  if (smem > 48 * 1024) return PE_OK;
+  switch (RB) {
+#define PE_CF_CASE(X)                                                                                     \
+  case X:                                                                                                 \
+    coarse_fused_kernel<T, X><<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, axisF, AG, \
+                                                                    c->coefG, c->U);                    \
+    break;
+    PE_CF_CASE(4) PE_CF_CASE(8) PE_CF_CASE(12) PE_CF_CASE(16) PE_CF_CASE(20) PE_CF_CASE(24) PE_CF_CASE(28)
+    PE_CF_CASE(32)
+#undef PE_CF_CASE
+    default:
+      return pe_fail(PE_EINVAL, "coarse sweep: too many source terms");
+  }
+  PE_CUDA_TRY(cudaGetLastError());
+  *done = true;
+  return PE_OK;
+}
+
 // Slices of loads each thread keeps in flight in the sequential sweeps below.
 // The recurrence carries one value per mode; its inputs do not depend on it,
 // so the loads of the next kPF slices are issued while the current kPF are
@@ -266,6 +359,15 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
     c->launches += 1;
     PE_CUDA_TRY(cudaGetLastError());
     return PE_OK;
+  }
+  if (!c->mlp) {
+    bool done = false;
+    if (c->precision == PE_MIXED) PE_TRY(launch_coarse_fused_t<float>(c, blocks, threads, c->axisF32, c->AG32, &done));
+    else PE_TRY(launch_coarse_fused_t<double>(c, blocks, threads, c->axisF, c->AG, &done));
+    if (done) {
+      c->launches += 1;
+      return PE_OK;
+    }
   }
   // slices per thread: enough CTAs to cover the GPU twice, at least one slice each
   int64_t want = (2 * 152 * 2 + blocks - 1) / blocks;
