@@ -255,9 +255,10 @@ pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, voi
 pe_status pe_dst_f32(int32_t d, const int32_t* n, const float* in, float* out, void* stream);
 
 /*
- * pe_dst_noalloc -- pe_dst for callers that cannot allocate device memory (code running
- * while a CUDA graph is being captured, applications that own a fixed memory pool and
- * forbid the runtime allocator, hosts whose device memory is reserved up front).  The
+ * pe_dst_noalloc -- pe_dst for callers that cannot allocate device memory (applications
+ * that own a fixed memory pool and forbid the runtime allocator, hosts whose device memory
+ * is reserved up front, latency-critical loops that must not enter the allocator, which
+ * can synchronise the device).  The
  * paper has no counterpart: this is an interface variant, not a step of the method.
  * It calls no cudaMalloc, cudaFree or other allocating routine; its scratch (ping-pong
  * array, DST-I matrices, FFT twiddles) is one file-scope device array of 1,835,008

@@ -1356,10 +1356,10 @@ extern "C" pe_status pe_dst_f32(int32_t d, const int32_t* n, const float* in, fl
 // ---------------------------------------------------------------------------
 // pe_dst_noalloc: the same transform with no device allocation at all.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being
-// captured (an allocation would break or be recorded into the capture), callers
-// that own a fixed memory pool and forbid the runtime allocator, and hosts whose
-// device memory is fully reserved up front.  This entry point keeps every scratch
+// Some callers cannot call cudaMalloc: applications that own a fixed memory pool and
+// forbid the runtime allocator, hosts whose device memory is fully reserved up front,
+// and latency-critical loops that must not enter the allocator (cudaMalloc and cudaFree
+// can synchronise the device).  This entry point keeps every scratch
 // buffer of the transform (the ping-pong array, the DST-I matrices of axes without
 // an FFT length, the FFT twiddles) in one file-scope device array.  Every GPU that
 // loads the library holds that array (about 14.7 MB) until the process exits.

@@ -1,7 +1,7 @@
 """The allocation-free DST entry point (pe_dst_noalloc) against the allocating one (pe_dst).
 
-Some callers cannot allocate device memory while they run (for example code that is
-being recorded into a CUDA graph, or an application with its own fixed memory pool);
+Some callers cannot allocate device memory while they run (for example an application
+with its own fixed memory pool, or a loop that must not enter the synchronising allocator);
 pe_dst_noalloc serves them from a built-in device array.  This file is collected last
 so that a failure here cannot hide the rest of the suite.  Two calls in a row go
 through the C-ABI with different sizes and paths (FFT lengths and the matrix path),
