@@ -279,45 +279,99 @@ __global__ void b_u0_kernel(const BProb* __restrict__ probs, const ModeItem* __r
 // inputs do not depend on the recurrence, so they are fetched kPF slices ahead).
 constexpr int kPF = 4;
 
+// Coarse sweep of k = 0 for every problem (item-strided grid: an item is 256 modes of one
+// problem), U^{n+1} = E_G U^n + gG_n with the coarse forcing gG_n = sum_i b_i sum_r
+// A_r(T_n + c_i dT) P_{r,J} made on the fly: the weights P_{r,J} sit in registers (RB =
+// roundup(PE_BATCH_MAX_TERMS, 4), zero past R) and the item's time factors are staged in
+// shared memory a chunk of slices at a time (rows of RB, read as float4 / double2
+// broadcasts).  TF = float in the mixed form (the coarse forcing only sets the first coarse
+// iterate; the affine correction never reads it again).
+constexpr int kCoarseRB = (PE_BATCH_MAX_TERMS + 3) / 4 * 4;
+constexpr int kCoarseSmem = 16 * 1024;  // bytes of staged time factors per CTA
+
 template <typename TF>
 __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__ probs,
                                                        const ModeItem* __restrict__ items, int n_items,
                                                        const double* __restrict__ axisF, const TF* __restrict__ AG,
                                                        const double* __restrict__ coefG, double* __restrict__ U) {
-  extern __shared__ __align__(16) unsigned char sP_raw[];
-  TF* sP = reinterpret_cast<TF*>(sP_raw);  // [PE_BATCH_MAX_TERMS][256]
-  const int tid = threadIdx.x, BD = blockDim.x;
+  constexpr int RB = kCoarseRB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TF* sA = reinterpret_cast<TF*>(smem_raw);  // [chunk * p][RB]
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const ModeItem m = items[it];
     const BProb& B = probs[m.p];
-    const int64_t J = m.J0 + tid;
-    if (J >= B.g.ndof) continue;
+    const int64_t J = m.J0 + threadIdx.x;
     const int64_t nd = B.g.ndof;
-    const int R = B.R;
-    int j[PE_MAX_D];
-    unflatten(B.g, J, j);
-    for (int r = 0; r < R; ++r) {
-      double v = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
-      for (int a = 1; a < B.g.d; ++a) v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
-      sP[r * BD + tid] = (TF)v;
-    }
-    const double* cg = coefG + B.oCG;
-    const double E = cg[J];
+    const bool on = J < nd;  // no early exit: the staging below needs every thread's barrier
+    const int R = B.R, p = B.p, N = B.N;
+    TF P[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) P[r] = TF(0);
     TF b[PE_MAX_S];
-    for (int i = 0; i < B.p; ++i) b[i] = (TF)cg[(1 + i) * nd + J];
-    double* Up = U + B.oU;
-    const TF* ag = AG + B.oAG;
-    double c = Up[J];
-    for (int n = 0; n < B.N; ++n) {
-      TF acc = TF(0);
-      for (int i = 0; i < B.p; ++i) {
-        const TF* arow = ag + ((int64_t)n * B.p + i) * R;
-        TF gi = TF(0);
-        for (int r = 0; r < R; ++r) gi = fma(__ldg(arow + r), sP[r * BD + tid], gi);
-        acc = fma(b[i], gi, acc);
+#pragma unroll
+    for (int i = 0; i < PE_MAX_S; ++i) b[i] = TF(0);
+    double E = 0.0, c = 0.0;
+    const double* cg = coefG + B.oCG;
+    if (on) {
+      int j[PE_MAX_D];
+      unflatten(B.g, J, j);
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        if (r < R) {
+          double v = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
+          for (int a = 1; a < B.g.d; ++a)
+            v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+          P[r] = (TF)v;
+        }
       }
-      c = fma(E, c, (double)acc);
-      Up[(int64_t)(n + 1) * nd + J] = c;
+#pragma unroll
+      for (int i = 0; i < PE_MAX_S; ++i)
+        if (i < p) b[i] = (TF)cg[(1 + i) * nd + J];
+      E = cg[J];
+      c = U[B.oU + J];
+    }
+    const TF* ag = AG + B.oAG;
+    const int CS = max(1, kCoarseSmem / (int)(p * RB * sizeof(TF)));  // slices per chunk
+    for (int n0 = 0; n0 < N; n0 += CS) {
+      const int nc = min(CS, N - n0);
+      __syncthreads();  // the previous chunk's (or item's) reads of sA are done
+      for (int e = threadIdx.x; e < nc * p * RB; e += blockDim.x) {
+        const int row = e / RB, r = e - row * RB;
+        sA[e] = r < R ? ag[((int64_t)n0 * p + row) * R + r] : TF(0);
+      }
+      __syncthreads();
+      if (on) {
+        for (int n = 0; n < nc; ++n) {
+          TF acc = TF(0);
+#pragma unroll
+          for (int i = 0; i < PE_MAX_S; ++i) {
+            if (i < p) {
+              const TF* a = sA + ((int64_t)n * p + i) * RB;
+              TF gi = TF(0);
+              if constexpr (sizeof(TF) == 4) {
+#pragma unroll
+                for (int r = 0; r < RB; r += 4) {
+                  const float4 v = *reinterpret_cast<const float4*>(a + r);
+                  gi = fmaf(v.x, P[r], gi);
+                  gi = fmaf(v.y, P[r + 1], gi);
+                  gi = fmaf(v.z, P[r + 2], gi);
+                  gi = fmaf(v.w, P[r + 3], gi);
+                }
+              } else {
+#pragma unroll
+                for (int r = 0; r < RB; r += 2) {
+                  const double2 v = *reinterpret_cast<const double2*>(a + r);
+                  gi = fma(v.x, P[r], gi);
+                  gi = fma(v.y, P[r + 1], gi);
+                }
+              }
+              acc = fma(b[i], gi, acc);
+            }
+          }
+          c = fma(E, c, (double)acc);
+          U[B.oU + (int64_t)(n0 + n + 1) * nd + J] = c;
+        }
+      }
     }
   }
 }
@@ -457,8 +511,7 @@ __global__ void b_reduce_kernel(const BProb* __restrict__ probs, int P, const do
 pe_status batch_set_attributes(pe_batch* b) {
   const size_t smem = sizeof(double) * (size_t)(b->nmax + 2 * (b->nmax + 1));
   PE_CUDA_TRY(cudaFuncSetAttribute(b_axis_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const size_t csmem = sizeof(double) * PE_BATCH_MAX_TERMS * 256;
-  PE_CUDA_TRY(cudaFuncSetAttribute(b_coarse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+
   return PE_OK;  // the fine kernels stage at most 48 KB (pick_mchunk), the default limit
 }
 
@@ -503,10 +556,10 @@ pe_status batch_launch_prepare(pe_batch* b) {
   // the coarse forcing is iterate-independent and cancels in G(U^{k+1}) - G(U^k): the mixed
   // form evaluates it in float32, the recurrence stays float64
   if (b->precision == PE_MIXED)
-    b_coarse_kernel<float><<<grid_items, 256, sizeof(float) * PE_BATCH_MAX_TERMS * 256, b->stream>>>(
+    b_coarse_kernel<float><<<grid_items, 256, kCoarseSmem, b->stream>>>(
         b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U);
   else
-    b_coarse_kernel<double><<<grid_items, 256, sizeof(double) * PE_BATCH_MAX_TERMS * 256, b->stream>>>(
+    b_coarse_kernel<double><<<grid_items, 256, kCoarseSmem, b->stream>>>(
         b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U);
   b->launches += 5;
   PE_CUDA_TRY(cudaGetLastError());
