@@ -514,8 +514,8 @@ extern "C" pe_status pe_set_learned(pe_ctx* c, const pe_mlp* m) {
 }
 
 // Called by pe_set_problem after the coarse forcing, before the coarse recurrence.
-pe_status launch_learned_correction(pe_ctx* c) {
-  if (!c->mlp) return PE_OK;
+pe_status launch_learned_tables(pe_ctx* c, LearnedTerms* L) {
+  if (!c->mlp) return pe_fail(PE_ESTATE, "learned G: no network attached");
   if (!c->Ktab) {
     if (cudaMalloc((void**)&c->Ktab, sizeof(double) * 2 * PE_MAX_TERMS * PE_LEARNED_BANDS) != cudaSuccess) {
       cudaGetLastError();
@@ -557,11 +557,40 @@ pe_status launch_learned_correction(pe_ctx* c) {
   }
   phase_table_kernel<<<(c->R * c->N + 127) / 128, 128, 0, c->stream>>>(T, c->N, c->dT, c->t0,
                                                                        (float2*)c->phase_tab);
+  c->launches += 2;
+  PE_CUDA_TRY(cudaGetLastError());
+  L->NB = NB;
+  L->loglo = loglo;
+  L->logstep = step;
+  L->dT = c->dT;
+  L->Ktab = c->Ktab;
+  L->cs = (const float2*)c->phase_tab;
+  for (int r = 0; r < PE_MAX_TERMS; ++r) {
+    L->is_sin[r] = r < c->R ? T.is_sin[r] : 0;
+    L->amp[r] = r < c->R ? T.amp[r] : 0.0;
+  }
+  return PE_OK;
+}
+
+pe_status launch_learned_correction(pe_ctx* c) {
+  if (!c->mlp) return PE_OK;
+  LearnedTerms L{};
+  PE_TRY(launch_learned_tables(c, &L));
+  TermsW T{};
+  T.R = c->R;
+  for (int r = 0; r < c->R; ++r) {
+    T.is_sin[r] = L.is_sin[r];
+    T.omega[r] = c->terms[r].tp[0];
+    T.phase[r] = c->terms[r].tp[1];
+    T.amp[r] = L.amp[r];
+  }
+  const int NB = L.NB;
+  const double loglo = L.loglo, step = L.logstep;
   const int threads = 256;
   const size_t smem = sizeof(float) * 2 * (size_t)c->R * threads;
   learned_correction_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, smem, c->stream>>>(
       c->g, c->N, c->R, NB, loglo, step, c->dT, T, c->lam, c->axisF, c->Ktab, (const float2*)c->phase_tab, c->gG);
-  c->launches += 3;
+  c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

@@ -31,4 +31,18 @@ struct TermsW {
   double amp[PE_MAX_TERMS];
 };
 
+// What the coarse sweep needs to add the learned term itself: the band table K^(lam, w_r)
+// (Ktab, NB bands log-spaced from loglo by logstep in log(lam dT)), the phase table
+// (cos, sin)(w_r T_n + phi_r) [R][N] (cs), and per term the sine flag and amplitude.
+struct LearnedTerms {
+  int NB;
+  double loglo, logstep, dT;
+  const double* Ktab;
+  const float2* cs;
+  int is_sin[PE_MAX_TERMS];
+  double amp[PE_MAX_TERMS];
+};
+
+// Band and phase tables of the attached network (two launches); fills *L.
+pe_status launch_learned_tables(pe_ctx* c, LearnedTerms* L);
 pe_status launch_learned_correction(pe_ctx* c);

@@ -17,6 +17,7 @@
 //                  Float64 sums  sum mu^M_J (U^{new} - U^{old})^2, sum mu^M_J (U^{new})^2
 //                  (per-CTA partial sums, added by the last CTA to finish).
 #include "pe_internal.h"
+#include "pe_learned.h"
 
 namespace {
 
@@ -115,20 +116,32 @@ pe_status launch_coarse_forcing_t(pe_ctx* c, unsigned blocks, int threads, int S
   return PE_OK;
 }
 
-// Coarse sweep of k = 0 with the coarse forcing made on the fly (no learned correction to
-// add in between): one thread per mode walks the slices, forming gG_n = sum_i b_i sum_r
-// A_r(T_n + c_i dT) P_{r,J} from its register weights and the time factors of all slices
-// (staged in shared memory, rows of RB) and applying U^{n+1} = E_G U^n + gG_n, so gG is
-// neither written nor read back.
-template <typename T, int RB>
+// Coarse sweep of k = 0 with the coarse forcing made on the fly: one thread per mode walks
+// the slices, forming gG_n = sum_i b_i sum_r A_r(T_n + c_i dT) P_{r,J} from its register
+// weights and the time factors of all slices (staged in shared memory, rows of RB) and
+// applying U^{n+1} = E_G U^n + gG_n, so gG is neither written nor read back.  LEARN adds the
+// learned term of G' = G + delta^ per slice, sum_r (A_r cos_{r,n} + B_r sin_{r,n}) with
+// A_r = P_{r,J} amp_r Im K^, B_r = P_{r,J} amp_r Re K^ (K^ interpolated linearly in
+// log(lam dT) between the band centres) and the phase table staged beside the time factors:
+// the same float32 sum, added to gG_n in float64, as the separate learned-correction kernel.
+template <typename T, int RB, bool LEARN>
 __global__ void __launch_bounds__(256) coarse_fused_kernel(Geom g, int N, int p, int R,
                                                           const T* __restrict__ axisF, const T* __restrict__ AG,
-                                                          const double* __restrict__ coefG, double* __restrict__ U) {
+                                                          const double* __restrict__ coefG, double* __restrict__ U,
+                                                          LearnedTerms L, const double* __restrict__ axisF64,
+                                                          const double* __restrict__ lam) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sA = reinterpret_cast<T*>(smem_raw);  // [N * p][RB]
+  float2* sCS = reinterpret_cast<float2*>(smem_raw);                // [N][RB] (LEARN only)
+  T* sA = reinterpret_cast<T*>(smem_raw + (LEARN ? sizeof(float2) * (size_t)N * RB : 0));  // [N * p][RB]
   for (int e = threadIdx.x; e < N * p * RB; e += blockDim.x) {
     const int row = e / RB, r = e - row * RB;
     sA[e] = r < R ? AG[(int64_t)row * R + r] : T(0);
+  }
+  if constexpr (LEARN) {
+    for (int e = threadIdx.x; e < N * RB; e += blockDim.x) {
+      const int n = e / RB, r = e - n * RB;
+      sCS[e] = r < R ? L.cs[(int64_t)r * N + n] : make_float2(0.f, 0.f);
+    }
   }
   __syncthreads();
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,6 +158,28 @@ __global__ void __launch_bounds__(256) coarse_fused_kernel(Geom g, int N, int p,
       for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     }
     P[r] = v;
+  }
+  float LA[LEARN ? RB : 1], LB[LEARN ? RB : 1];
+  if constexpr (LEARN) {
+    double pos = (log(lam[J] * L.dT) - L.loglo) / L.logstep;
+    pos = fmin(fmax(pos, 0.0), (double)(L.NB - 1) - 1e-9);
+    const int b0 = (int)pos;
+    const double f = pos - (double)b0;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      LA[r] = 0.f;
+      LB[r] = 0.f;
+      if (r < R && L.is_sin[r]) {
+        double Pd = axisF64[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
+        for (int a = 1; a < g.d; ++a) Pd *= axisF64[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+        const double* k0 = L.Ktab + 2 * ((int64_t)r * L.NB + b0);
+        const double Kre = (1.0 - f) * k0[0] + f * k0[2];
+        const double Kim = (1.0 - f) * k0[1] + f * k0[3];
+        const double cc = Pd * L.amp[r];
+        LA[r] = (float)(cc * Kim);
+        LB[r] = (float)(cc * Kre);
+      }
+    }
   }
   T b[PE_MAX_S];
 #pragma unroll
@@ -178,24 +213,40 @@ __global__ void __launch_bounds__(256) coarse_fused_kernel(Geom g, int N, int p,
         acc = fma(b[i], gi, acc);
       }
     }
-    c = fma(E, c, (double)acc);
+    double gn = (double)acc;
+    if constexpr (LEARN) {
+      float dl = 0.f;
+      const float2* e = sCS + (int64_t)n * RB;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) dl = fmaf(LA[r], e[r].x, fmaf(LB[r], e[r].y, dl));
+      gn += (double)dl;
+    }
+    c = fma(E, c, gn);
     U[(int64_t)(n + 1) * nd + J] = c;
   }
 }
 
-// The fused coarse sweep when the time factors of all slices fit 48 KB of shared memory;
-// *done = false (nothing launched) otherwise.
+// The fused coarse sweep when its shared tables fit 48 KB; *done = false (nothing launched)
+// otherwise.  L is null without a learned correction.
 template <typename T>
-pe_status launch_coarse_fused_t(pe_ctx* c, unsigned blocks, int threads, const T* axisF, const T* AG, bool* done) {
+pe_status launch_coarse_fused_t(pe_ctx* c, unsigned blocks, int threads, const T* axisF, const T* AG,
+                                const LearnedTerms* L, bool* done) {
   *done = false;
   const int RB = c->R < 4 ? 4 : (c->R + 3) / 4 * 4;
-  const size_t smem = sizeof(T) * (size_t)c->N * c->p * RB;
+  const size_t smem = sizeof(T) * (size_t)c->N * c->p * RB + (L ? sizeof(float2) * (size_t)c->N * RB : 0);
   if (smem > 48 * 1024) return PE_OK;
+  const LearnedTerms Lv = L ? *L : LearnedTerms{};
   switch (RB) {
-#define PE_CF_CASE(X)                                                                                     \
-  case X:                                                                                                 \
-    coarse_fused_kernel<T, X><<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, axisF, AG, \
-                                                                    c->coefG, c->U);                    \
+#define PE_CF_CASE(X)                                                                                          \
+  case X:                                                                                                      \
+    if (L)                                                                                                     \
+      coarse_fused_kernel<T, X, true><<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, axisF, AG, \
+                                                                            c->coefG, c->U, Lv, c->axisF,     \
+                                                                            c->lam);                           \
+    else                                                                                                       \
+      coarse_fused_kernel<T, X, false><<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, axisF,   \
+                                                                             AG, c->coefG, c->U, Lv, c->axisF, \
+                                                                             c->lam);                          \
     break;
     PE_CF_CASE(4) PE_CF_CASE(8) PE_CF_CASE(12) PE_CF_CASE(16) PE_CF_CASE(20) PE_CF_CASE(24) PE_CF_CASE(28)
     PE_CF_CASE(32)
@@ -360,10 +411,14 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
     PE_CUDA_TRY(cudaGetLastError());
     return PE_OK;
   }
-  if (!c->mlp) {
+  {
+    // fused sweep; with a learned correction its band and phase tables are made first
+    LearnedTerms L{};
+    if (c->mlp) PE_TRY(launch_learned_tables(c, &L));
+    const LearnedTerms* Lp = c->mlp ? &L : nullptr;
     bool done = false;
-    if (c->precision == PE_MIXED) PE_TRY(launch_coarse_fused_t<float>(c, blocks, threads, c->axisF32, c->AG32, &done));
-    else PE_TRY(launch_coarse_fused_t<double>(c, blocks, threads, c->axisF, c->AG, &done));
+    if (c->precision == PE_MIXED) PE_TRY(launch_coarse_fused_t<float>(c, blocks, threads, c->axisF32, c->AG32, Lp, &done));
+    else PE_TRY(launch_coarse_fused_t<double>(c, blocks, threads, c->axisF, c->AG, Lp, &done));
     if (done) {
       c->launches += 1;
       return PE_OK;
