@@ -530,6 +530,37 @@ def run_general(pe, args, barrier, u0_dev):
     return out
 
 
+EX4_PAIRS = ((0.01, 1.0), (0.01, 10.0), (0.1, 1.0), (0.1, 10.0))
+
+
+def run_example4(pe, args, barrier):
+    """Example 4 of Sec. 5 at the paper's size (N_x = 1024, 4 x 16 slices, three stage and three
+    coarse nodes, moving hat source) through the general forcing path: set-up plus k = 4 Parareal
+    iterations for every (alpha, f) pair, float64 and mixed.  A launch-bound 1D workload."""
+
+    out = {"workload": "ex4_Nx1024_4x16_q3_p3 general forcing path, k = 4"}
+    for alpha, freq in EX4_PAIRS:
+        prob = I.example4(1024, alpha, freq, 4, 16, 3, 3)
+        rec = {}
+        for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
+            with pe.Solver(prob, precision=prec, forcing_path=pe.PE_FORCING_GENERAL) as s:
+                def run():
+                    s.set_problem()
+                    return [s.iterate() for _ in range(4)]
+                for _ in range(max(1, args.warmup)):
+                    run()
+                barrier()
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    res = run()
+                barrier()
+                dt = (time.perf_counter() - t0) / args.steps
+            rec[name] = {"ms": 1e3 * dt, "residuals": res,
+                         "value": prob.ndof * prob.N * prob.M * 4 / dt, "unit": UNIT}
+        out[f"a{alpha}_f{freq}"] = rec
+    return out
+
+
 def allmax(x, dist=None, device="cpu"):
     """The maximum of x over all ranks (x itself without a process group): the timed region of
     a replica run ends when the slowest rank ends."""
@@ -593,8 +624,9 @@ def main():
     ap.add_argument("--no-cached", action="store_true", help="skip the cached-F^M(0) line")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-data line")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-axis line")
+    ap.add_argument("--no-example4", action="store_true", help="skip the Example 4 paper-size line")
     ap.add_argument("--only", choices=["batch", "learned", "general", "dst", "precision", "cached", "dirichlet",
-                                       "periodic"],
+                                       "periodic", "example4"],
                     help="run one secondary workload alone and print its record (for profiling)")
     args = ap.parse_args()
 
@@ -657,7 +689,8 @@ def main():
                "precision": lambda: run_precision(pe, args, barrier),
                "cached": lambda: run_cached(pe, args, barrier, u0_dev, u0_host),
                "dirichlet": lambda: run_dirichlet(pe, args, barrier),
-               "periodic": lambda: run_periodic(pe, args, barrier)}[args.only]
+               "periodic": lambda: run_periodic(pe, args, barrier),
+               "example4": lambda: run_example4(pe, args, barrier)}[args.only]
         rec = run()
         if rank == 0:
             print(json.dumps({"section": args.only, **rec}))
@@ -687,6 +720,7 @@ def main():
         cached = None if args.no_cached else run_cached(pe, args, barrier, u0_dev, u0_host)
         dirichlet = None if args.no_dirichlet else run_dirichlet(pe, args, barrier)
         periodic = None if args.no_periodic else run_periodic(pe, args, barrier)
+        example4 = None if args.no_example4 else run_example4(pe, args, barrier)
     clock = clocks.summary()
 
     # max over ranks
@@ -793,6 +827,7 @@ def main():
         "affine_cached": cached,
         "dirichlet": dirichlet,
         "periodic": periodic,
+        "example4": example4,
     }
     print(json.dumps(line))
     if dist is not None:
