@@ -58,6 +58,15 @@ enum { PE_FP64 = 0,   /* every step in float64 */
                          homogeneous part e^{-lam M dt} v, tables, correction and
                          residual in float64 */ };
 
+/* engine of the mixed-precision fine sweep (pe_options.fine_engine), separable forcing only:
+ * SIMT = float32 FMAs on the CUDA cores; TC = the stage contraction of every 128 modes x
+ * (slice group) on the tensor cores (tcgen05, three-term bfloat16 split of both operands,
+ * six products, float32 accumulation; about the accuracy of the float32 form), the
+ * recurrence and the float64 homogeneous term on the CUDA cores.  TC needs M (substeps
+ * per slice) a multiple of 16 in 16..128: pe_setup returns PE_EINVAL otherwise, and for
+ * PE_FP64 or PE_FORCING_GENERAL.  The float64 refinement (pe_refine) is unaffected. */
+enum { PE_FINE_SIMT = 0, PE_FINE_TC = 1 };
+
 /* DST-I backend of the general forcing path (pe_options.dst_backend): AUTO = radix-2 FFT
  * when n+1 is a power of two, else the matrix form; TC = tensor cores (mixed precision
  * only, split bfloat16, about 3e-6 relative per pass at n = 255) */
@@ -115,6 +124,7 @@ typedef struct {
                              (DHT) in place of the DST-I, theta_j = 2 pi j / n_a, and the mode
                              j = 0 of an all-periodic problem has lam = 0.  Not with Dirichlet
                              data or the learned correction. */
+  int32_t fine_engine;    /* PE_FINE_SIMT (default) | PE_FINE_TC, see above */
 } pe_options;
 
 /* Initial data: u0 = sum of separable terms (time factors ignored), projected

@@ -128,7 +128,7 @@ void free_ctx(pe_ctx* c) {
                   c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
-                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr};
+                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -255,6 +255,17 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     delete c;
     return pe_fail(PE_EINVAL, "pe_setup: cache_forced needs PE_FORCING_SEPARABLE");
   }
+  if (o.fine_engine != PE_FINE_SIMT && o.fine_engine != PE_FINE_TC) {
+    delete c;
+    return pe_fail(PE_EINVAL, "pe_setup: bad fine_engine");
+  }
+  if (o.fine_engine == PE_FINE_TC &&
+      (o.precision != PE_MIXED || o.forcing_path != PE_FORCING_SEPARABLE || !fine_tc_supported(n_substeps))) {
+    delete c;
+    return pe_fail(PE_EINVAL,
+                   "pe_setup: PE_FINE_TC needs PE_MIXED, PE_FORCING_SEPARABLE and M a multiple of 16 in 16..128");
+  }
+  c->fine_engine = o.fine_engine;
   c->forcing_path = o.forcing_path;
   c->cache_forced = o.cache_forced ? 1 : 0;
   c->precision = o.precision;
@@ -284,6 +295,12 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->partials, 2 * (size_t)c->max_blocks + 64);
   if (st == PE_OK) st = dev_alloc(&c->red, 2);
   if (st == PE_OK) st = dev_alloc(&c->done_ctr, 1);
+  if (st == PE_OK && c->fine_engine == PE_FINE_TC) {
+    st = dev_alloc(&c->tcB, fine_tc_buffer_bytes(n_substeps, n_slices));
+    if (st == PE_OK) st = dev_alloc(&c->tc_err, 1);
+    if (st == PE_OK && cudaMemset(c->tc_err, 0, sizeof(int)) != cudaSuccess)
+      st = pe_fail(PE_ECUDA, "pe_setup: error flag initialisation failed");
+  }
   if (st == PE_OK && cudaMemset(c->done_ctr, 0, sizeof(unsigned int)) != cudaSuccess)
     st = pe_fail(PE_ECUDA, "pe_setup: counter initialisation failed");
   if (st == PE_OK) st = dev_alloc(&c->axisF, MT * nsum);
@@ -536,6 +553,7 @@ static pe_status iter_impl(pe_ctx* c, double* r_out, int precision) {
   c->k += 1;
   if (!isfinite(num) || !isfinite(den)) {
     c->have_problem = false;
+    if (precision == PE_MIXED && c->fine_engine == PE_FINE_TC) PE_TRY(fine_tc_status(c));
     return pe_fail(PE_ENONFINITE, "Parareal residual is not finite (NaN/Inf in the iterate)");
   }
   const double r = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);

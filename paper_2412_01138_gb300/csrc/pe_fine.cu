@@ -34,15 +34,22 @@ __global__ void affine_fine_kernel(int64_t ndof, int N, const double* __restrict
 }
 }  // namespace
 
+// one sweep of the fine propagator over every slice (the tensor-core engine for the mixed
+// form when it was chosen at setup)
+static pe_status run_sweep(pe_ctx* c, int precision, int from_zero, double* out) {
+  if (precision == PE_MIXED && c->fine_engine == PE_FINE_TC) return launch_fine_tc(c, from_zero, out);
+  return Table::run(c->K, c, precision, from_zero, out);
+}
+
 pe_status launch_fine_sweep(pe_ctx* c, int precision) {
   if (precision != PE_MIXED) PE_TRY(launch_stage_weights_f64(c));
   if (!c->cache_forced) {
     c->sweeps += 1;
-    return Table::run(c->K, c, precision, 0, c->Fbar);
+    return run_sweep(c, precision, 0, c->Fbar);
   }
   // affine cache: one sweep from zero per problem and precision, then E^M U + F^M(0)
   if (c->fz_prec != precision) {
-    PE_TRY(Table::run(c->K, c, precision, 1, c->Fz));
+    PE_TRY(run_sweep(c, precision, 1, c->Fz));
     c->fz_prec = precision;
     c->sweeps += 1;
   }

@@ -1,0 +1,441 @@
+// Tensor-core engine of the mixed-precision fine sweep (pe_options.fine_engine = PE_FINE_TC).
+//
+// The forced part of the fine propagator over one slice n (the EIFE stage recurrence of
+// Sec. 3 with its stage columns contracted) is, per mode J,
+//   w_{m+1} = E_F w_m + a_m,   a_m = sum_k W[k][J] Y_n[m][k],   m = 0..M-1,   w_0 = 0,
+// and F^M(U^n)_J = exp(-lam_J M dt) U^n_J + w_M.  For a tile of 128 modes and a group of G
+// slices the inputs a_m of all G*M substeps form one dense contraction
+//   D[J][s*M + m] = sum_k W[k][J] Y_{gG+s}[m][k]        (128 x NR, NR = G*M <= 256, K <= 64),
+// which runs on the 5th-generation tensor cores: both operands are split into three
+// bfloat16 terms x = x0 + x1 + x2 (about 24 bits together) and the six products whose
+// weight is at least 2^-24 (x0y0, x0y1, x1y0, x0y2, x1y1, x2y0) are accumulated in float32
+// in tensor memory, the five small ones first.  The recurrence (hi/lo E_F, float32) and
+// the float64 homogeneous term then run per mode on the CUDA cores from tcgen05.ld rows.
+//
+// Kernel roles (one persistent CTA per SM, 288 threads, items = (slice group, mode tile)
+// pairs, group-major, a contiguous range per CTA):
+//   * warps 0-7: split W of the next item's 128 modes into the core-matrix layout of the
+//     A operand (double buffer, then fence.proxy.async + mbarrier arrive), then the
+//     epilogue of the current item: wait for its accumulator, read rows with tcgen05.ld
+//     (warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 take the even slices of the
+//     group, warps 4-7 the odd ones, two slices' recurrences interleaved), write F;
+//   * warp 8, one thread: the split time factors of the current slice group (prepared
+//     once per sweep in global memory in the exact shared-memory layout, so that one
+//     bulk copy moves them), and the tcgen05.mma issue into one of two accumulators
+//     (2 x NR TMEM columns), released by tcgen05.commit.
+// Every mbarrier wait is bounded; on expiry the CTA records an error code, writes a NaN
+// into the first output value (so that the Parareal residual reports it), frees its
+// tensor memory and exits.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "pe_internal.h"
+#include "pe_tc_common.cuh"
+
+namespace {
+
+constexpr int FT_ROWS = 128;                 // modes of a tile (TMEM lanes)
+constexpr int FT_WORKERS = 256;              // warps 0-7
+constexpr int FT_THREADS = FT_WORKERS + 32;  // + warp 8 (copies and MMA issue)
+constexpr int FT_CHUNK = 16 * 1024;          // bytes per bulk copy instruction
+constexpr int FT_MIN_SMEM = 120 * 1024;      // at most one CTA per SM (its TMEM allocation)
+
+// rows of the B operand (G*M) a K padding allows, and the shared-memory budget
+__host__ __device__ constexpr int ft_rows_max(int KP) { return KP <= 48 ? 256 : 128; }
+__host__ __device__ constexpr int ft_a_bytes(int KP) { return 3 * FT_ROWS * KP * 2; }
+__host__ __device__ constexpr int ft_smem_bytes(int KP) {
+  return std::max(1024 + 3 * ft_rows_max(KP) * KP * 2 + 2 * ft_a_bytes(KP), FT_MIN_SMEM);
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Three bfloat16 terms of eight consecutive values (x = t0 + t1 + t2 up to about 2^-24
+// relative), each packed as one 16-byte core-matrix row.
+__device__ __forceinline__ void split8(const float (&x)[8], uint4 (&o)[3]) {
+  uint32_t pk[3][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float r0 = x[2 * e], r1 = x[2 * e + 1];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);  // .x = r0 (low half)
+      pk[t][e] = *reinterpret_cast<const uint32_t*>(&h);
+      r0 -= __low2float(h);
+      r1 -= __high2float(h);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 3; ++t) o[t] = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+}
+
+// Split time factors of every slice group, in the B-operand layout of the kernel below:
+// group g occupies 3 * NR * KP * 2 bytes, [term][k / 8][row r][k % 8], row r = s * M + m
+// holding Y_{gG+s}[m][k] (zero past the last slice and past K).
+__global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, int K, int KC, int G, int NR,
+                                     int KP, int ngroups, uint4* __restrict__ Bsp) {
+  const int chunks = KP / 8;
+  const int64_t total = (int64_t)ngroups * NR * chunks;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int c = (int)(e % chunks);
+  const int64_t gr = e / chunks;
+  const int r = (int)(gr % NR);
+  const int g = (int)(gr / NR);
+  const int s = r / M, m = r - s * M, n = g * G + s;
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = 8 * c + j;
+    x[j] = (n < N && k < K) ? Y[((int64_t)n * M + m) * KC + k] : 0.f;
+  }
+  uint4 o[3];
+  split8(x, o);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) Bsp[(((int64_t)g * 3 + t) * chunks + c) * NR + r] = o[t];
+}
+
+struct FtArgs {
+  const float* W32;      // stage weights [K][ndof]
+  const float* coefF32;  // E_hi [ndof], E_lo [ndof]
+  const double* EM;      // exp(-lam M dt) [ndof]
+  const double* U;       // U^n at n * ndof
+  double* out;           // F^M(U^n) (or F^M(0)) at n * ndof
+  const unsigned char* Bsp;
+  int64_t ndof, tiles, items;
+  int N, M, K, G, NR, from_zero;
+  int* err;
+};
+
+template <int KP>
+__global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
+  constexpr int CH = KP / 8;                        // core-matrix columns of 8 K values
+  constexpr int A_TERM = FT_ROWS * KP * 2;          // one split term of the A operand
+  constexpr int A_BYTES = 3 * A_TERM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t fullA[2], fullD[2], emptyD[2], fullB, freeB, drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sB = smem;
+  unsigned char* sA = smem + 3 * ft_rows_max(KP) * KP * 2;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int NR = a.NR, M = a.M;
+  const int B_BYTES = 3 * NR * KP * 2;
+  const int64_t nd = a.ndof;
+  const int64_t i0 = (int64_t)blockIdx.x * a.items / gridDim.x;
+  const int64_t i1 = (int64_t)(blockIdx.x + 1) * a.items / gridDim.x;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(2 * NR)) ncols <<= 1;
+  volatile int* fail = &s_fail;
+  auto set_fail = [&](int code) {
+    atomicExch(a.err, code);
+    *fail = 1;
+    a.out[0] = __longlong_as_double(0x7ff8000000000000LL);
+  };
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&fullA[b], FT_WORKERS);
+      mbar_init(&fullD[b], 1);
+      mbar_init(&emptyD[b], FT_WORKERS);
+    }
+    mbar_init(&fullB, 1);
+    mbar_init(&freeB, 1);
+    mbar_init(&drain, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp < 8) {
+    const int r = tid & (FT_ROWS - 1), h = tid >> 7;
+    constexpr int CT = CH / 2;  // K chunks of 8 this thread splits: h, h + 2, ...
+    constexpr int UP = 4;       // slices of an item whose U is prefetched (further ones read in place)
+    // Global loads run one item ahead of their use, so that their latency hides behind the
+    // current item: W of the next A operand, and E_hi, E_lo, exp(-lam M dt), U of the next
+    // epilogue.
+    float wv[CT][8];
+    float eh_n = 0.f, el_n = 0.f;
+    double em_n = 0.0, u_n[UP];
+    auto load_W = [&](int64_t i) {
+      const int64_t J = (i % a.tiles) * FT_ROWS + r;
+#pragma unroll
+      for (int ct = 0; ct < CT; ++ct) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int k = 8 * (h + 2 * ct) + e;
+          wv[ct][e] = (J < nd && k < a.K) ? __ldg(a.W32 + (int64_t)k * nd + J) : 0.f;
+        }
+      }
+    };
+    // split into A buffer (i - i0) % 2; that buffer was last read by the MMAs of item i - 2,
+    // whose accumulator this thread has already waited for
+    auto store_A = [&](int64_t i) {
+      unsigned char* A = sA + ((i - i0) & 1) * A_BYTES;
+#pragma unroll
+      for (int ct = 0; ct < CT; ++ct) {
+        const int c = h + 2 * ct;
+        uint4 o[3];
+        split8(wv[ct], o);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) *reinterpret_cast<uint4*>(A + t * A_TERM + c * (FT_ROWS * 16) + r * 16) = o[t];
+      }
+      fence_proxy_async();
+      mbar_arrive(&fullA[(i - i0) & 1]);
+    };
+    auto load_epi = [&](int64_t i) {
+      const int64_t g = i / a.tiles, J = (i % a.tiles) * FT_ROWS + r;
+      const bool ok = J < nd;
+      eh_n = ok ? a.coefF32[J] : 0.f;
+      el_n = ok ? a.coefF32[nd + J] : 0.f;
+      em_n = ok ? a.EM[J] : 0.0;
+#pragma unroll
+      for (int t = 0; t < UP; ++t) {
+        const int s = h + 2 * t;
+        const int64_t n = g * a.G + s;
+        u_n[t] = (!a.from_zero && ok && s < a.G && n < a.N) ? a.U[n * nd + J] : 0.0;
+      }
+    };
+    if (i0 < i1) {
+      load_W(i0);
+      store_A(i0);
+      if (i0 + 1 < i1) load_W(i0 + 1);
+      load_epi(i0);
+    }
+    for (int64_t i = i0; i < i1; ++i) {
+      if (*fail) break;
+      const int j = (int)(i - i0);
+      const float eh = eh_n, el = el_n;
+      const double em = em_n;
+      double u[UP];
+#pragma unroll
+      for (int t = 0; t < UP; ++t) u[t] = u_n[t];
+      if (i + 1 < i1) store_A(i + 1);
+      if (i + 2 < i1) load_W(i + 2);
+      if (i + 1 < i1) load_epi(i + 1);
+      if (!mbar_wait(&fullD[j & 1], (uint32_t)((j >> 1) & 1))) {
+        set_fail(5);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t g = i / a.tiles;
+      const int64_t J = (i % a.tiles) * FT_ROWS + r;
+      const bool ok = J < nd;
+      const uint32_t row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((j & 1) * NR);
+      // this thread's slices s = h + 2t of the group, two recurrences interleaved
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int s0 = h + 4 * p, s1 = s0 + 2;
+        if (s0 >= a.G) break;
+        const bool two = s1 < a.G;  // warp-uniform
+        float w0 = 0.f, w1 = 0.f;
+        for (int m0 = 0; m0 < M; m0 += 16) {
+          float v0[16], v1[16];
+          tmem_ld16(row + (uint32_t)(s0 * M + m0), v0);
+          if (two) tmem_ld16(row + (uint32_t)(s1 * M + m0), v1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            w0 = fmaf(eh, w0, fmaf(el, w0, v0[e]));
+            if (two) w1 = fmaf(eh, w1, fmaf(el, w1, v1[e]));
+          }
+        }
+        if (ok) {
+          const int64_t n0 = g * a.G + s0, n1 = g * a.G + s1;
+          if (n0 < a.N) {
+            const double u0 = 2 * p < UP ? u[2 * p] : (a.from_zero ? 0.0 : a.U[n0 * nd + J]);
+            a.out[n0 * nd + J] = a.from_zero ? (double)w0 : fma(em, u0, (double)w0);
+          }
+          if (two && n1 < a.N) {
+            const double u1 = 2 * p + 1 < UP ? u[2 * p + 1] : (a.from_zero ? 0.0 : a.U[n1 * nd + J]);
+            a.out[n1 * nd + J] = a.from_zero ? (double)w1 : fma(em, u1, (double)w1);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&emptyD[j & 1]);
+    }
+  } else if (tid == FT_WORKERS) {
+    const uint32_t idesc = instr_desc_bf16(FT_ROWS, NR);
+    const int ta[6] = {2, 1, 0, 1, 0, 0}, tb[6] = {0, 1, 2, 0, 1, 0};  // small products first
+    int64_t gcur = -1;
+    int nB = 0;
+    bool issued = false;
+    for (int64_t i = i0; i < i1; ++i) {
+      const int j = (int)(i - i0);
+      const int64_t g = i / a.tiles;
+      if (g != gcur) {
+        // the previous group's MMAs must be done with sB before it is overwritten
+        if (gcur >= 0) {
+          mma_commit(&freeB);
+          if (!mbar_wait(&freeB, (uint32_t)((nB - 1) & 1))) {
+            set_fail(6);
+            break;
+          }
+        }
+        mbar_expect_tx(&fullB, (uint32_t)B_BYTES);
+        const unsigned char* src = a.Bsp + g * (int64_t)B_BYTES;
+        for (int off = 0; off < B_BYTES; off += FT_CHUNK)
+          bulk_g2s(sB + off, src + off, (uint32_t)(B_BYTES - off < FT_CHUNK ? B_BYTES - off : FT_CHUNK), &fullB);
+        if (!mbar_wait(&fullB, (uint32_t)(nB & 1))) {
+          set_fail(7);
+          break;
+        }
+        ++nB;
+        gcur = g;
+      }
+      if (!mbar_wait(&fullA[j & 1], (uint32_t)((j >> 1) & 1))) {
+        set_fail(8);
+        break;
+      }
+      if (j >= 2 && !mbar_wait(&emptyD[j & 1], (uint32_t)(((j >> 1) - 1) & 1))) {
+        set_fail(9);
+        break;
+      }
+      if (*fail) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + (j & 1) * A_BYTES), b0 = smem_u32(sB);
+      const uint32_t d = tmem + (uint32_t)((j & 1) * NR);
+      bool first = true;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+#pragma unroll
+        for (int ks = 0; ks < KP / 16; ++ks) {
+          const uint64_t da = smem_desc(a0 + ta[q] * A_TERM + (2 * ks) * (FT_ROWS * 16), FT_ROWS * 16, 128);
+          const uint64_t db = smem_desc(b0 + tb[q] * (NR * KP * 2) + (2 * ks) * (NR * 16), NR * 16, 128);
+          mma_bf16(d, da, db, idesc, first ? 0u : 1u);
+          first = false;
+        }
+      }
+      mma_commit(&fullD[j & 1]);
+      issued = true;
+    }
+    // every MMA of this CTA has completed before the tensor memory is freed
+    if (issued) {
+      mma_commit(&drain);
+      if (!mbar_wait(&drain, 0)) set_fail(10);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 8) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+template <int KP>
+pe_status ft_launch(const FtArgs& args, int grid, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(fine_tc_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft_smem_bytes(KP));
+  });
+  if (attr != cudaSuccess) return pe_cuda_fail(attr, "fine sweep (tensor cores): shared-memory attribute");
+  fine_tc_kernel<KP><<<grid, FT_THREADS, ft_smem_bytes(KP), st>>>(args);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+// slice-group shape of a column padding KP at M substeps: G slices, NR = G * M rows
+void ft_shape(int KP, int M, int N, int* G, int* NR, int* ngroups) {
+  *G = std::max(1, ft_rows_max(KP) / M);
+  *NR = *G * M;
+  *ngroups = (N + *G - 1) / *G;
+}
+
+}  // namespace
+
+bool fine_tc_supported(int M) { return M >= 16 && M <= 128 && M % 16 == 0; }
+
+size_t fine_tc_buffer_bytes(int M, int N) {
+  size_t most = 0;
+  for (int KP = 16; KP <= 64; KP += 16) {
+    int G, NR, ng;
+    ft_shape(KP, M, N, &G, &NR, &ng);
+    most = std::max(most, (size_t)ng * 3 * NR * KP * 2);
+  }
+  return most;
+}
+
+pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
+  const int M = c->M, K = c->K, N = c->N;
+  if (!fine_tc_supported(M) || K < 1 || K > 64 || !c->tcB || !c->tc_err)
+    return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported shape");
+  const int KP = (K + 15) / 16 * 16, KC = (K + 3) / 4 * 4;
+  int G, NR, ngroups;
+  ft_shape(KP, M, N, &G, &NR, &ngroups);
+  const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
+  ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
+                                                                                 ngroups, (uint4*)c->tcB);
+  PE_CUDA_TRY(cudaGetLastError());
+  FtArgs args{};
+  args.W32 = c->Wst32;
+  args.coefF32 = c->coefF32;
+  args.EM = c->coefF + (int64_t)(c->q + 1) * c->g.ndof;
+  args.U = c->U;
+  args.out = out;
+  args.Bsp = c->tcB;
+  args.ndof = c->g.ndof;
+  args.tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
+  args.items = args.tiles * ngroups;
+  args.N = N;
+  args.M = M;
+  args.K = K;
+  args.G = G;
+  args.NR = NR;
+  args.from_zero = from_zero;
+  args.err = c->tc_err;
+  int dev = 0, sms = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = (int)std::min<int64_t>(args.items, sms);
+  pe_status st = PE_OK;
+  switch (KP) {
+    case 16: st = ft_launch<16>(args, grid, c->stream); break;
+    case 32: st = ft_launch<32>(args, grid, c->stream); break;
+    case 48: st = ft_launch<48>(args, grid, c->stream); break;
+    default: st = ft_launch<64>(args, grid, c->stream); break;
+  }
+  c->launches += 2;
+  return st;
+}
+
+pe_status fine_tc_status(pe_ctx* c) {
+  if (!c->tc_err) return PE_OK;
+  int herr = 0;
+  PE_CUDA_TRY(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (herr != 0) {
+    cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream);
+    return pe_fail(PE_ETIMEOUT, "fine sweep (tensor cores): a pipeline wait expired (code " + std::to_string(herr) + ")");
+  }
+  return PE_OK;
+}

@@ -74,6 +74,7 @@ struct pe_ctx {
   int nsum;  // sum_a n_a
   // options
   int precision, dst_backend, quad_pts, max_iter, forcing_path, cache_forced;
+  int fine_engine = 0;  // PE_FINE_SIMT | PE_FINE_TC
   cudaStream_t stream;
   // device memory
   double* muM_axis = nullptr;   // [nsum]
@@ -100,6 +101,8 @@ struct pe_ctx {
   double* partials = nullptr;   // [2 * max_blocks]
   double* red = nullptr;        // [2] device
   unsigned int* done_ctr = nullptr;  // correction: CTAs finished (0 between launches)
+  unsigned char* tcB = nullptr;  // tensor-core fine engine: split time factors of every slice group
+  int* tc_err = nullptr;         // tensor-core fine engine: error code of an expired wait (0: none)
   cudaStream_t side = nullptr;  // second stream: the nodal u0 transform beside the forcing tables
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_red = nullptr;      // [2] pinned host
@@ -197,3 +200,9 @@ pe_status launch_learned_correction(pe_ctx* c);
 int general_slices_per_chunk(const pe_ctx* c);
 pe_status launch_general_coarse_forcing(pe_ctx* c);
 pe_status launch_general_fine_sweep(pe_ctx* c, int precision);
+
+// pe_fine_tc.cu (tensor-core engine of the mixed fine sweep)
+bool fine_tc_supported(int M);                 // M a multiple of 16 in 16..128
+size_t fine_tc_buffer_bytes(int M, int N);     // split time factors, any K <= 64
+pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out);
+pe_status fine_tc_status(pe_ctx* c);           // PE_ETIMEOUT if a pipeline wait expired

@@ -23,6 +23,7 @@ PE_OK, PE_EINVAL, PE_ENOMEM, PE_ECUDA, PE_ENOCONV, PE_ENONFINITE, PE_ETIMEOUT, P
 PE_FP64, PE_MIXED = 0, 1
 PE_DST_AUTO, PE_DST_MATRIX, PE_DST_TC = 0, 1, 2
 PE_FORCING_SEPARABLE, PE_FORCING_GENERAL = 0, 1
+PE_FINE_SIMT, PE_FINE_TC = 0, 1
 PE_FIELD_TERMS_SEPARABLE, PE_FIELD_TERMS_QUADRATURE, PE_FIELD_NODAL = 0, 1, 2
 PE_MAX_TERMS = 32
 
@@ -57,7 +58,7 @@ class pe_tableau(C.Structure):
 class pe_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("dst_backend", C.c_int32), ("quad_pts", C.c_int32),
                 ("max_iter", C.c_int32), ("cuda_stream", C.c_void_p), ("forcing_path", C.c_int32),
-                ("cache_forced", C.c_int32), ("periodic_mask", C.c_int32)]
+                ("cache_forced", C.c_int32), ("periodic_mask", C.c_int32), ("fine_engine", C.c_int32)]
 
 
 class pe_field(C.Structure):
@@ -195,7 +196,7 @@ class Solver:
 
     def __init__(self, prob: "_in.Problem", precision: int = PE_FP64, stream=None, max_iter: int = 0,
                  random_coarse_seed: Optional[int] = None, forcing_path: int = PE_FORCING_SEPARABLE,
-                 dst_backend: int = PE_DST_AUTO, cache_forced: bool = False):
+                 dst_backend: int = PE_DST_AUTO, cache_forced: bool = False, fine_engine: int = PE_FINE_SIMT):
         self.prob = prob
         self._lib = lib()
         n = (C.c_int32 * prob.d)(*prob.n)
@@ -209,7 +210,7 @@ class Solver:
             coarse = pe_tableau(prob.p, None, 1, random_coarse_seed)
         mask = sum(1 << a for a, p in enumerate(getattr(prob, "periodic", ())) if p)
         opt = pe_options(precision, dst_backend, prob.quad_pts, max_iter, stream_handle(stream), forcing_path,
-                         1 if cache_forced else 0, mask)
+                         1 if cache_forced else 0, mask, fine_engine)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup(C.byref(ctx), prob.d, n, box, prob.D, prob.t0, prob.T, prob.N, prob.M,
                                   C.byref(fine), C.byref(coarse), C.byref(opt)))
