@@ -698,8 +698,10 @@ def main():
 
     results = {}
     with ClockSampler(local if world > 1 else 0) as clocks:
-        for name, precision in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-            with pe.Solver(prob, precision=precision, stream=stream) as s:
+        for name, precision, engine in (("fp64", pe.PE_FP64, pe.PE_FINE_SIMT),
+                                        ("mixed_simt", pe.PE_MIXED, pe.PE_FINE_SIMT),
+                                        ("mixed", pe.PE_MIXED, pe.PE_FINE_TC)):
+            with pe.Solver(prob, precision=precision, stream=stream, fine_engine=engine) as s:
                 total_ms, infos = timed_steps(s, args.steps, args.warmup, u0_dev)
                 modal = s.modal(prob.N)
                 # end to end through the C-ABI with host buffers: H2D of u0, D2H of the solution
@@ -747,6 +749,7 @@ def main():
 
     plain = summarize(results["fp64"])
     chosen = summarize(results["mixed"])
+    simt = summarize(results["mixed_simt"])
 
     # parity of both forms on sampled modes against the oracle (outside the timed region);
     # the same run is the CPU baseline (the oracle as it stands, one core)
@@ -767,6 +770,7 @@ def main():
         return float(np.sqrt(np.sum(w * (a[idx] - ref.U[-1]) ** 2)) / np.sqrt(np.sum(w * ref.U[-1] ** 2)))
 
     err_plain, err_chosen = rel(results["fp64"]["modal"]), rel(results["mixed"]["modal"])
+    err_simt = rel(results["mixed_simt"]["modal"])
     cpu = None
     if not args.no_cpu_baseline:
         cpu = {"value": cpu_units / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -800,7 +804,9 @@ def main():
         "time_to_tol_ms": plain["ms_per_step"],
         "iterations": plain["k"],
         "rel_l2_vs_oracle": err_plain,
-        "chosen": {"form": "mixed: float32 fine stages (hi/lo E), float64 tables, correction, residual",
+        "chosen": {"form": "mixed: stage contraction on the tensor cores (tcgen05, three-term bfloat16 split, "
+                           "six products, float32 accumulators), float32 recurrence (hi/lo E), float64 tables, "
+                           "correction, residual",
                    "value": chosen["value"], "unit": UNIT, "time_to_tol_ms": chosen["ms_per_step"],
                    "iterations": chosen["k"], "rel_l2_vs_oracle": err_chosen, "dtype": "f32",
                    "speedup_time_to_tol": plain["ms_per_step"] / chosen["ms_per_step"],
@@ -809,6 +815,13 @@ def main():
                    / (chosen["ms_fine_launch"] / 1e3) / 1e12,
                    "fp32_peak_tflops": fp32_peak_tflops(sm_mhz),
                    "e2e": chosen["e2e"], "phases_ms": chosen["phases"]},
+        "mixed_simt": {"form": "mixed, float32 stage contraction on the CUDA cores (K + 2 FMAs per DoF*substep)",
+                       "value": simt["value"], "unit": UNIT, "time_to_tol_ms": simt["ms_per_step"],
+                       "iterations": simt["k"], "rel_l2_vs_oracle": err_simt,
+                       "fine_kernel_ms": simt["ms_fine_launch"],
+                       "fine_kernel_tflops": fine_flops_per_unit(prob, mixed=True) * prob.ndof * prob.N * prob.M
+                       / (simt["ms_fine_launch"] / 1e3) / 1e12,
+                       "e2e": simt["e2e"]},
         "phases_ms": plain["phases"],
         "roofline": {"kernel": "fine_f64_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,

@@ -128,7 +128,7 @@ void free_ctx(pe_ctx* c) {
                   c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
-                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err};
+                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err, c->tcA};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);

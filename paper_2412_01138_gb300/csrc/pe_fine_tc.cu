@@ -12,17 +12,17 @@
 // in tensor memory, the five small ones first.  The recurrence (hi/lo E_F, float32) and
 // the float64 homogeneous term then run per mode on the CUDA cores from tcgen05.ld rows.
 //
-// Kernel roles (one persistent CTA per SM, 288 threads, items = (slice group, mode tile)
+// Kernel roles (one persistent CTA per SM, 544 threads, items = (slice group, mode tile)
 // pairs, group-major, a contiguous range per CTA):
-//   * warps 0-7: split W of the next item's 128 modes into the core-matrix layout of the
-//     A operand (double buffer, then fence.proxy.async + mbarrier arrive), then the
-//     epilogue of the current item: wait for its accumulator, read rows with tcgen05.ld
-//     (warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 take the even slices of the
-//     group, warps 4-7 the odd ones, two slices' recurrences interleaved), write F;
-//   * warp 8, one thread: the split time factors of the current slice group (prepared
-//     once per sweep in global memory in the exact shared-memory layout, so that one
-//     bulk copy moves them), and the tcgen05.mma issue into one of two accumulators
-//     (2 x NR TMEM columns), released by tcgen05.commit.
+//   * warps 0-15 (four warpgroups): the epilogue of each item: wait for its accumulator,
+//     read rows with tcgen05.ld (warp w reads TMEM lanes 32 (w % 4) ..; warpgroup h takes
+//     the slices h, h + 4, ... of the group), run the recurrence four substeps per step,
+//     write F; the next item's epilogue inputs are loaded meanwhile;
+//   * warp 16, one thread: bulk copies of the split operands, both prepared once per sweep
+//     in global memory in the exact shared-memory layout (the time factors of the current
+//     slice group; the stage weights of each item's mode tile, a ring of three), and the
+//     tcgen05.mma issue into one of two accumulators (2 x NR TMEM columns), released by
+//     tcgen05.commit.
 // Every mbarrier wait is bounded; on expiry the CTA records an error code, writes a NaN
 // into the first output value (so that the Parareal residual reports it), frees its
 // tensor memory and exits.
@@ -37,16 +37,41 @@
 namespace {
 
 constexpr int FT_ROWS = 128;                 // modes of a tile (TMEM lanes)
-constexpr int FT_WORKERS = 256;              // warps 0-7
-constexpr int FT_THREADS = FT_WORKERS + 32;  // + warp 8 (copies and MMA issue)
+constexpr int FT_WORKERS = 512;              // warps 0-15: four warpgroups
+constexpr int FT_THREADS = FT_WORKERS + 32;  // + warp 16 (copies and MMA issue)
 constexpr int FT_CHUNK = 16 * 1024;          // bytes per bulk copy instruction
 constexpr int FT_MIN_SMEM = 120 * 1024;      // at most one CTA per SM (its TMEM allocation)
+constexpr int FT_ABUF = 3;                   // ring of A-operand tiles
 
 // rows of the B operand (G*M) a K padding allows, and the shared-memory budget
-__host__ __device__ constexpr int ft_rows_max(int KP) { return KP <= 48 ? 256 : 128; }
+__host__ __device__ constexpr int ft_rows_max(int KP) { return KP <= 32 ? 256 : 128; }
 __host__ __device__ constexpr int ft_a_bytes(int KP) { return 3 * FT_ROWS * KP * 2; }
 __host__ __device__ constexpr int ft_smem_bytes(int KP) {
-  return std::max(1024 + 3 * ft_rows_max(KP) * KP * 2 + 2 * ft_a_bytes(KP), FT_MIN_SMEM);
+  return std::max(1024 + 3 * ft_rows_max(KP) * KP * 2 + FT_ABUF * ft_a_bytes(KP), FT_MIN_SMEM);
+}
+
+// Operand images use the swizzled K-major layout whose swizzle width equals a row of KP
+// bfloat16 (32, 64 or 128 bytes): row r of a term at r * KP * 2 bytes, its 16-byte chunk c
+// stored at chunk c ^ ((byte offset >> 7) & (KP / 8 - 1)) (address bits 4.. XOR bits 7..),
+// so that the tensor core reads whole rows without bank conflicts.  Terms start on
+// 1024-byte boundaries, as the pattern requires.
+__host__ __device__ constexpr int ft_kpad(int K) { return K <= 16 ? 16 : (K <= 32 ? 32 : 64); }
+__device__ __forceinline__ int64_t ft_swz(int64_t off, int KP) {
+  return off ^ (((off >> 7) & (KP / 8 - 1)) << 4);
+}
+// shared-memory descriptor of a swizzled K-major operand: start address, stride between
+// 8-row groups (8 rows of KP * 2 bytes), version 1, layout type 6 / 4 / 2 (32 / 64 / 128-byte
+// swizzle); the leading offset is not used by these layouts
+__device__ __forceinline__ uint64_t smem_desc_swz(uint32_t saddr, int KP) {
+  const uint32_t sbo = 8u * (uint32_t)KP * 2u;
+  const uint64_t layout = KP == 16 ? 6 : (KP == 32 ? 4 : 2);
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= layout << 61;
+  return d;
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -67,6 +92,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
+// hi + lo pair squared in float32 arithmetic (a double-float product: the low word collects
+// the exact rounding error of hi * hi from an FMA and the cross term 2 hi lo; about 2^-44
+// relative)
+__device__ __forceinline__ void df_square(float h, float l, float& oh, float& ol) {
+  const float p = h * h;
+  float e = fmaf(h, h, -p);
+  e = fmaf(2.f * h, l, e);
+  oh = p + e;
+  ol = e - (oh - p);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Three bfloat16 terms of eight consecutive values (x = t0 + t1 + t2 up to about 2^-24
@@ -89,7 +125,7 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4 (&o)[3]) {
 }
 
 // Split time factors of every slice group, in the B-operand layout of the kernel below:
-// group g occupies 3 * NR * KP * 2 bytes, [term][k / 8][row r][k % 8], row r = s * M + m
+// group g occupies 3 * NR * KP * 2 bytes, [term][row r][k] swizzled as above, row r = s * M + m
 // holding Y_{gG+s}[m][k] (zero past the last slice and past K).
 __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, int K, int KC, int G, int NR,
                                      int KP, int ngroups, uint4* __restrict__ Bsp) {
@@ -110,8 +146,37 @@ __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, 
   }
   uint4 o[3];
   split8(x, o);
+  const int64_t term = (int64_t)NR * KP * 2;
 #pragma unroll
-  for (int t = 0; t < 3; ++t) Bsp[(((int64_t)g * 3 + t) * chunks + c) * NR + r] = o[t];
+  for (int t = 0; t < 3; ++t)
+    Bsp[(((int64_t)g * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
+}
+
+// Split stage weights of every mode tile, in the A-operand layout of the kernel below:
+// tile q occupies 3 * 128 * KP * 2 bytes, [term][row r][k] swizzled as above, row r holding
+// W[k][128 q + r] (zero past the last mode and past K).
+__global__ void ft_split_w_kernel(const float* __restrict__ W, int64_t nd, int K, int KP, int64_t tiles,
+                                  uint4* __restrict__ Asp) {
+  const int chunks = KP / 8;
+  const int64_t total = tiles * FT_ROWS * chunks;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int r = (int)(e % FT_ROWS);
+  const int64_t rest = e / FT_ROWS;
+  const int c = (int)(rest % chunks);
+  const int64_t tile = rest / chunks;
+  const int64_t J = tile * FT_ROWS + r;
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = 8 * c + j;
+    x[j] = (J < nd && k < K) ? W[(int64_t)k * nd + J] : 0.f;
+  }
+  uint4 o[3];
+  split8(x, o);
+  const int64_t term = (int64_t)FT_ROWS * KP * 2;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) Asp[((tile * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
 }
 
 struct FtArgs {
@@ -120,7 +185,8 @@ struct FtArgs {
   const double* EM;      // exp(-lam M dt) [ndof]
   const double* U;       // U^n at n * ndof
   double* out;           // F^M(U^n) (or F^M(0)) at n * ndof
-  const unsigned char* Bsp;
+  const unsigned char* Asp;  // split stage weights of every mode tile
+  const unsigned char* Bsp;  // split time factors of every slice group
   int64_t ndof, tiles, items;
   int N, M, K, G, NR, from_zero;
   int* err;
@@ -128,11 +194,10 @@ struct FtArgs {
 
 template <int KP>
 __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
-  constexpr int CH = KP / 8;                        // core-matrix columns of 8 K values
   constexpr int A_TERM = FT_ROWS * KP * 2;          // one split term of the A operand
   constexpr int A_BYTES = 3 * A_TERM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t fullA[2], fullD[2], emptyD[2], fullB, freeB, drain;
+  __shared__ __align__(8) uint64_t fullA[FT_ABUF], emptyA[FT_ABUF], fullD[2], emptyD[2], fullB, freeB, drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -153,10 +218,13 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
     a.out[0] = __longlong_as_double(0x7ff8000000000000LL);
   };
   if (tid == 0) {
+    for (int b = 0; b < FT_ABUF; ++b) {
+      mbar_init(&fullA[b], 1);
+      mbar_init(&emptyA[b], 1);
+    }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&fullA[b], FT_WORKERS);
       mbar_init(&fullD[b], 1);
-      mbar_init(&emptyD[b], FT_WORKERS);
+      mbar_init(&emptyD[b], FT_WORKERS / 32);
     }
     mbar_init(&fullB, 1);
     mbar_init(&freeB, 1);
@@ -164,7 +232,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == FT_WORKERS / 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(ncols)
                  : "memory");
@@ -175,123 +243,101 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (warp < 8) {
-    const int r = tid & (FT_ROWS - 1), h = tid >> 7;
-    constexpr int CT = CH / 2;  // K chunks of 8 this thread splits: h, h + 2, ...
-    constexpr int UP = 4;       // slices of an item whose U is prefetched (further ones read in place)
-    // Global loads run one item ahead of their use, so that their latency hides behind the
-    // current item: W of the next A operand, and E_hi, E_lo, exp(-lam M dt), U of the next
-    // epilogue.
-    float wv[CT][8];
-    float eh_n = 0.f, el_n = 0.f;
-    double em_n = 0.0, u_n[UP];
-    auto load_W = [&](int64_t i) {
-      const int64_t J = (i % a.tiles) * FT_ROWS + r;
-#pragma unroll
-      for (int ct = 0; ct < CT; ++ct) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int k = 8 * (h + 2 * ct) + e;
-          wv[ct][e] = (J < nd && k < a.K) ? __ldg(a.W32 + (int64_t)k * nd + J) : 0.f;
-        }
-      }
+  if (warp < FT_WORKERS / 32) {
+    // thread (h, r): warpgroup h of four, row r of the tile (TMEM lane r)
+    const int r = tid & (FT_ROWS - 1), h = tid >> 7, lane = tid & 31;
+    constexpr int UP = 2;  // slices of an item whose U is prefetched (further ones read in place)
+    // the epilogue inputs of item i + 1 (E_hi, E_lo, exp(-lam M dt), U) are loaded while item
+    // i waits for its accumulator and runs, into two alternating register sets
+    struct Pre {
+      float eh, el;
+      double em, u[UP];
     };
-    // split into A buffer (i - i0) % 2; that buffer was last read by the MMAs of item i - 2,
-    // whose accumulator this thread has already waited for
-    auto store_A = [&](int64_t i) {
-      unsigned char* A = sA + ((i - i0) & 1) * A_BYTES;
-#pragma unroll
-      for (int ct = 0; ct < CT; ++ct) {
-        const int c = h + 2 * ct;
-        uint4 o[3];
-        split8(wv[ct], o);
-#pragma unroll
-        for (int t = 0; t < 3; ++t) *reinterpret_cast<uint4*>(A + t * A_TERM + c * (FT_ROWS * 16) + r * 16) = o[t];
-      }
-      fence_proxy_async();
-      mbar_arrive(&fullA[(i - i0) & 1]);
-    };
-    auto load_epi = [&](int64_t i) {
+    Pre P0, P1;
+    auto load_epi = [&](Pre& P, int64_t i) {
       const int64_t g = i / a.tiles, J = (i % a.tiles) * FT_ROWS + r;
       const bool ok = J < nd;
-      eh_n = ok ? a.coefF32[J] : 0.f;
-      el_n = ok ? a.coefF32[nd + J] : 0.f;
-      em_n = ok ? a.EM[J] : 0.0;
+      P.eh = ok ? a.coefF32[J] : 0.f;
+      P.el = ok ? a.coefF32[nd + J] : 0.f;
+      P.em = ok ? a.EM[J] : 0.0;
 #pragma unroll
       for (int t = 0; t < UP; ++t) {
-        const int s = h + 2 * t;
+        const int s = h + 4 * t;
         const int64_t n = g * a.G + s;
-        u_n[t] = (!a.from_zero && ok && s < a.G && n < a.N) ? a.U[n * nd + J] : 0.0;
+        P.u[t] = (!a.from_zero && ok && s < a.G && n < a.N) ? a.U[n * nd + J] : 0.0;
       }
     };
-    if (i0 < i1) {
-      load_W(i0);
-      store_A(i0);
-      if (i0 + 1 < i1) load_W(i0 + 1);
-      load_epi(i0);
-    }
-    for (int64_t i = i0; i < i1; ++i) {
-      if (*fail) break;
+    auto step = [&](int64_t i, const Pre& cur, Pre& nxt) -> bool {
       const int j = (int)(i - i0);
-      const float eh = eh_n, el = el_n;
-      const double em = em_n;
-      double u[UP];
-#pragma unroll
-      for (int t = 0; t < UP; ++t) u[t] = u_n[t];
-      if (i + 1 < i1) store_A(i + 1);
-      if (i + 2 < i1) load_W(i + 2);
-      if (i + 1 < i1) load_epi(i + 1);
+      if (i + 1 < i1) load_epi(nxt, i + 1);
       if (!mbar_wait(&fullD[j & 1], (uint32_t)((j >> 1) & 1))) {
         set_fail(5);
-        break;
+        return false;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float e2h, e2l, e4h, e4l;
+      df_square(cur.eh, cur.el, e2h, e2l);
+      df_square(e2h, e2l, e4h, e4l);
+      const float eh = cur.eh, e2 = e2h, e3 = e2h * eh;
       const int64_t g = i / a.tiles;
       const int64_t J = (i % a.tiles) * FT_ROWS + r;
       const bool ok = J < nd;
       const uint32_t row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((j & 1) * NR);
-      // this thread's slices s = h + 2t of the group, two recurrences interleaved
+      // this thread's slices s = h + 4t of the group (warp-uniform)
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int s0 = h + 4 * p, s1 = s0 + 2;
+      for (int t = 0; t < 4; ++t) {
+        const int s0 = h + 4 * t;
         if (s0 >= a.G) break;
-        const bool two = s1 < a.G;  // warp-uniform
-        float w0 = 0.f, w1 = 0.f;
+        // four substeps per step of the chain: w <- E^4 w + (E^3 a_m + E^2 a_{m+1} + E a_{m+2}
+        // + a_{m+3}); the bracket does not depend on w, and E^4 is applied as a hi/lo pair
+        float w0 = 0.f;
         for (int m0 = 0; m0 < M; m0 += 16) {
-          float v0[16], v1[16];
+          float v0[16];
           tmem_ld16(row + (uint32_t)(s0 * M + m0), v0);
-          if (two) tmem_ld16(row + (uint32_t)(s1 * M + m0), v1);
           tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            w0 = fmaf(eh, w0, fmaf(el, w0, v0[e]));
-            if (two) w1 = fmaf(eh, w1, fmaf(el, w1, v1[e]));
+          for (int e = 0; e < 16; e += 4) {
+            const float b0 = fmaf(e3, v0[e], fmaf(e2, v0[e + 1], fmaf(eh, v0[e + 2], v0[e + 3])));
+            w0 = fmaf(e4h, w0, fmaf(e4l, w0, b0));
           }
         }
-        if (ok) {
-          const int64_t n0 = g * a.G + s0, n1 = g * a.G + s1;
-          if (n0 < a.N) {
-            const double u0 = 2 * p < UP ? u[2 * p] : (a.from_zero ? 0.0 : a.U[n0 * nd + J]);
-            a.out[n0 * nd + J] = a.from_zero ? (double)w0 : fma(em, u0, (double)w0);
-          }
-          if (two && n1 < a.N) {
-            const double u1 = 2 * p + 1 < UP ? u[2 * p + 1] : (a.from_zero ? 0.0 : a.U[n1 * nd + J]);
-            a.out[n1 * nd + J] = a.from_zero ? (double)w1 : fma(em, u1, (double)w1);
-          }
+        const int64_t n0 = g * a.G + s0;
+        if (ok && n0 < a.N) {
+          const double u0 = t < UP ? cur.u[t] : (a.from_zero ? 0.0 : a.U[n0 * nd + J]);
+          a.out[n0 * nd + J] = a.from_zero ? (double)w0 : fma(cur.em, u0, (double)w0);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&emptyD[j & 1]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyD[j & 1]);
+      return true;
+    };
+    if (i0 < i1) load_epi(P0, i0);
+    for (int64_t i = i0; i < i1; i += 2) {
+      if (*fail || !step(i, P0, P1)) break;
+      if (i + 1 < i1 && (*fail || !step(i + 1, P1, P0))) break;
     }
   } else if (tid == FT_WORKERS) {
     const uint32_t idesc = instr_desc_bf16(FT_ROWS, NR);
     const int ta[6] = {2, 1, 0, 1, 0, 0}, tb[6] = {0, 1, 2, 0, 1, 0};  // small products first
+    const int n = (int)(i1 - i0);
+    // item i0 + jj's split weights into A buffer jj % FT_ABUF
+    auto load_A = [&](int jj) {
+      const int b = jj % FT_ABUF;
+      const unsigned char* src = a.Asp + ((i0 + jj) % a.tiles) * (int64_t)A_BYTES;
+      mbar_expect_tx(&fullA[b], (uint32_t)A_BYTES);
+      for (int off = 0; off < A_BYTES; off += FT_CHUNK)
+        bulk_g2s(sA + b * A_BYTES + off, src + off, (uint32_t)(A_BYTES - off < FT_CHUNK ? A_BYTES - off : FT_CHUNK),
+                 &fullA[b]);
+    };
+    int nl = 0;  // items whose A copy has been issued
+    for (; nl < FT_ABUF && nl < n; ++nl) load_A(nl);
+    int j = 0;
     int64_t gcur = -1;
     int nB = 0;
     bool issued = false;
-    for (int64_t i = i0; i < i1; ++i) {
-      const int j = (int)(i - i0);
-      const int64_t g = i / a.tiles;
+    for (; j < n; ++j) {
+      const int64_t g = (i0 + j) / a.tiles;
       if (g != gcur) {
         // the previous group's MMAs must be done with sB before it is overwritten
         if (gcur >= 0) {
@@ -312,7 +358,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
         ++nB;
         gcur = g;
       }
-      if (!mbar_wait(&fullA[j & 1], (uint32_t)((j >> 1) & 1))) {
+      const int b = j % FT_ABUF;
+      if (!mbar_wait(&fullA[b], (uint32_t)((j / FT_ABUF) & 1))) {
         set_fail(8);
         break;
       }
@@ -322,23 +369,36 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
       }
       if (*fail) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA + (j & 1) * A_BYTES), b0 = smem_u32(sB);
+      const uint32_t a0 = smem_u32(sA + b * A_BYTES), b0 = smem_u32(sB);
       const uint32_t d = tmem + (uint32_t)((j & 1) * NR);
       bool first = true;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
 #pragma unroll
         for (int ks = 0; ks < KP / 16; ++ks) {
-          const uint64_t da = smem_desc(a0 + ta[q] * A_TERM + (2 * ks) * (FT_ROWS * 16), FT_ROWS * 16, 128);
-          const uint64_t db = smem_desc(b0 + tb[q] * (NR * KP * 2) + (2 * ks) * (NR * 16), NR * 16, 128);
+          const uint64_t da = smem_desc_swz(a0 + ta[q] * A_TERM + 32 * ks, KP);
+          const uint64_t db = smem_desc_swz(b0 + tb[q] * (NR * KP * 2) + 32 * ks, KP);
           mma_bf16(d, da, db, idesc, first ? 0u : 1u);
           first = false;
         }
       }
       mma_commit(&fullD[j & 1]);
+      mma_commit(&emptyA[b]);
       issued = true;
+      // refill the buffer of item j - 1 (its MMAs ran ahead of item j's) with item j + 2
+      if (j >= 1 && j + FT_ABUF - 1 < n) {
+        if (!mbar_wait(&emptyA[(j - 1) % FT_ABUF], (uint32_t)(((j - 1) / FT_ABUF) & 1))) {
+          set_fail(11);
+          break;
+        }
+        load_A(j + FT_ABUF - 1);
+        ++nl;
+      }
     }
-    // every MMA of this CTA has completed before the tensor memory is freed
+    // after a failure: wait (bounded) for the A copies still in flight into shared memory
+    if (*fail)
+      for (int jj = j; jj < nl; ++jj) mbar_wait(&fullA[jj % FT_ABUF], (uint32_t)((jj / FT_ABUF) & 1));
+    // every MMA and copy of this CTA has completed before the tensor memory is freed
     if (issued) {
       mma_commit(&drain);
       if (!mbar_wait(&drain, 0)) set_fail(10);
@@ -346,7 +406,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 8) {
+  if (warp == FT_WORKERS / 32) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
   }
 }
@@ -377,7 +437,7 @@ bool fine_tc_supported(int M) { return M >= 16 && M <= 128 && M % 16 == 0; }
 
 size_t fine_tc_buffer_bytes(int M, int N) {
   size_t most = 0;
-  for (int KP = 16; KP <= 64; KP += 16) {
+  for (int KP = 16; KP <= 64; KP *= 2) {
     int G, NR, ng;
     ft_shape(KP, M, N, &G, &NR, &ng);
     most = std::max(most, (size_t)ng * 3 * NR * KP * 2);
@@ -389,12 +449,25 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   const int M = c->M, K = c->K, N = c->N;
   if (!fine_tc_supported(M) || K < 1 || K > 64 || !c->tcB || !c->tc_err)
     return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported shape");
-  const int KP = (K + 15) / 16 * 16, KC = (K + 3) / 4 * 4;
+  const int KP = ft_kpad(K), KC = (K + 3) / 4 * 4;
   int G, NR, ngroups;
   ft_shape(KP, M, N, &G, &NR, &ngroups);
+  const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
+  const size_t a_need = (size_t)tiles * ft_a_bytes(KP);
+  if (a_need > c->tcA_cap) {
+    if (c->tcA) PE_CUDA_TRY(cudaFree(c->tcA));
+    c->tcA = nullptr;
+    c->tcA_cap = 0;
+    PE_CUDA_TRY(cudaMalloc((void**)&c->tcA, a_need));
+    c->tcA_cap = a_need;
+  }
   const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
   ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
                                                                                  ngroups, (uint4*)c->tcB);
+  PE_CUDA_TRY(cudaGetLastError());
+  const int64_t nsw = tiles * FT_ROWS * (KP / 8);
+  ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
+                                                                           (uint4*)c->tcA);
   PE_CUDA_TRY(cudaGetLastError());
   FtArgs args{};
   args.W32 = c->Wst32;
@@ -402,9 +475,10 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   args.EM = c->coefF + (int64_t)(c->q + 1) * c->g.ndof;
   args.U = c->U;
   args.out = out;
+  args.Asp = c->tcA;
   args.Bsp = c->tcB;
   args.ndof = c->g.ndof;
-  args.tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
+  args.tiles = tiles;
   args.items = args.tiles * ngroups;
   args.N = N;
   args.M = M;
@@ -421,10 +495,9 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   switch (KP) {
     case 16: st = ft_launch<16>(args, grid, c->stream); break;
     case 32: st = ft_launch<32>(args, grid, c->stream); break;
-    case 48: st = ft_launch<48>(args, grid, c->stream); break;
     default: st = ft_launch<64>(args, grid, c->stream); break;
   }
-  c->launches += 2;
+  c->launches += 3;
   return st;
 }
 

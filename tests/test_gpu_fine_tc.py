@@ -4,9 +4,10 @@ against the float64 oracle.
 The stage contraction runs on tcgen05 with three-term bfloat16 splits of both operands and six
 products accumulated in float32, so the engine keeps the mixed form's bound: relative L2
 <= 1e-6 against the oracle on the workloads, and no more than the float32 form's own error on
-stress mixes of many high-frequency terms.  Cases span every column padding (K = 1 .. 64: 16, 32, 48 and 64
-columns), substep counts 16 .. 128 (slice groups of 1 .. 16 slices, the last group ragged),
-mode counts that leave a partial tile, and the cached forced part.
+stress mixes of many high-frequency terms.  Cases span every column padding (K = 1 .. 64:
+16, 32 and 64 columns, 32-, 64- and 128-byte swizzled operand rows), substep counts 16 .. 128
+(slice groups of 1 .. 16 slices, the last group ragged), mode counts that leave a partial
+tile, and the cached forced part.
 """
 import math
 
@@ -56,9 +57,9 @@ def _term_mix(kinds, seed):
 # to about 1.5e-6 from the oracle, so these cases check the engine against the SIMT float32
 # form slice by slice (no more than 10% above its error) under a 2e-6 cap; the 1e-6 bound is
 # checked on the workloads below.
-# (time kinds, substeps, slices): K = 1, 2, 28, 34, 40, 64, 61 columns (paddings 16, 16, 32, 48,
-# 48, 64, 64); M = 16 (16 slices per group), 32 (8, or 4 at padding 64), 64 (4), 96 (2), 48 (5),
-# 128 (1); N chosen so that the last slice group is partial.
+# (time kinds, substeps, slices): K = 1, 2, 28, 34, 40, 64, 61 columns (paddings 16, 16, 32, 64,
+# 64, 64, 64); M = 16 (16 slices per group), 32 (8, or 4 at padding 64), 64 (4), 96 (1 at
+# padding 64), 48 (2), 128 (1); N chosen so that the last slice group is partial.
 @pytest.mark.parametrize("kinds,M,N", [("e", 16, 21), ("s", 32, 9), ("esses" * 3 + "ss", 64, 7),
                                        ("esse" * 4 + "s" * 5, 96, 5), ("s" * 20, 48, 11),
                                        ("s" * 32, 128, 3), ("s" * 30 + "e", 32, 6)])
