@@ -452,6 +452,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   const bool any_periodic = c->g.per[0] || c->g.per[1] || c->g.per[2];
   if (any_periodic && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: periodic axes and the learned correction");
   memset(c->lkind, 0, sizeof(c->lkind));
+  c->tc_split_ok = false;
   if (nf == 0 && c->nbd == 0) {
     // no source: one zero term keeps every kernel shape valid
     c->R = 1;

@@ -18,7 +18,7 @@
 //     read rows with tcgen05.ld (warp w reads TMEM lanes 32 (w % 4) ..; warpgroup h takes
 //     the slices h, h + 4, ... of the group), run the recurrence four substeps per step,
 //     write F; the next item's epilogue inputs are loaded meanwhile;
-//   * warp 16, one thread: bulk copies of the split operands, both prepared once per sweep
+//   * warp 16, one thread: bulk copies of the split operands, both prepared once per problem
 //     in global memory in the exact shared-memory layout (the time factors of the current
 //     slice group; the stage weights of each item's mode tile, a ring of three), and the
 //     tcgen05.mma issue into one of two accumulators (2 x NR TMEM columns), released by
@@ -460,15 +460,22 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
     c->tcA_cap = 0;
     PE_CUDA_TRY(cudaMalloc((void**)&c->tcA, a_need));
     c->tcA_cap = a_need;
+    c->tc_split_ok = false;
   }
-  const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
-  ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
-                                                                                 ngroups, (uint4*)c->tcB);
-  PE_CUDA_TRY(cudaGetLastError());
-  const int64_t nsw = tiles * FT_ROWS * (KP / 8);
-  ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
-                                                                           (uint4*)c->tcA);
-  PE_CUDA_TRY(cudaGetLastError());
+  // the split operand images depend only on the problem (stage weights, time factors):
+  // made at the first sweep after pe_set_problem and reused by later sweeps
+  if (!c->tc_split_ok) {
+    const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
+    ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
+                                                                                   ngroups, (uint4*)c->tcB);
+    PE_CUDA_TRY(cudaGetLastError());
+    const int64_t nsw = tiles * FT_ROWS * (KP / 8);
+    ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
+                                                                             (uint4*)c->tcA);
+    PE_CUDA_TRY(cudaGetLastError());
+    c->tc_split_ok = true;
+    c->launches += 2;
+  }
   FtArgs args{};
   args.W32 = c->Wst32;
   args.coefF32 = c->coefF32;
@@ -497,7 +504,7 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
     case 32: st = ft_launch<32>(args, grid, c->stream); break;
     default: st = ft_launch<64>(args, grid, c->stream); break;
   }
-  c->launches += 3;
+  c->launches += 1;
   return st;
 }
 

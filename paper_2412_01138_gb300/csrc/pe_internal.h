@@ -104,6 +104,7 @@ struct pe_ctx {
   unsigned char* tcB = nullptr;  // tensor-core fine engine: split time factors of every slice group
   unsigned char* tcA = nullptr;  // tensor-core fine engine: split stage weights of every mode tile
   size_t tcA_cap = 0;            // bytes allocated in tcA
+  bool tc_split_ok = false;      // tcA / tcB hold the current problem's split operands
   int* tc_err = nullptr;         // tensor-core fine engine: error code of an expired wait (0: none)
   cudaStream_t side = nullptr;  // second stream: the nodal u0 transform beside the forcing tables
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
