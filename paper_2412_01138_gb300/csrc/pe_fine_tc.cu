@@ -12,13 +12,14 @@
 // in tensor memory, the five small ones first.  The recurrence (hi/lo E_F, float32) and
 // the float64 homogeneous term then run per mode on the CUDA cores from tcgen05.ld rows.
 //
-// Kernel roles (one persistent CTA per SM, 544 threads, items = (slice group, mode tile)
+// Kernel roles (one persistent CTA per SM, 288 threads, items = (slice group, mode tile)
 // pairs, group-major, a contiguous range per CTA):
-//   * warps 0-15 (four warpgroups): the epilogue of each item: wait for its accumulator,
-//     read rows with tcgen05.ld (warp w reads TMEM lanes 32 (w % 4) ..; warpgroup h takes
-//     the slices h, h + 4, ... of the group), run the recurrence four substeps per step,
-//     write F; the next item's epilogue inputs are loaded meanwhile;
-//   * warp 16, one thread: bulk copies of the split operands, both prepared once per problem
+//   * warps 0-7 (two warpgroups): the epilogue of each item: wait for its accumulator,
+//     read rows with tcgen05.ld, 32 substeps of two slices per read (warp w reads TMEM lanes
+//     32 (w % 4) ..; warpgroup h takes the slices h, h + 2, ... of the group), run the
+//     recurrence four substeps per step, write F; the next item's epilogue inputs are
+//     loaded meanwhile;
+//   * warp 8, one thread: bulk copies of the split operands, both prepared once per problem
 //     in global memory in the exact shared-memory layout (the time factors of the current
 //     slice group; the stage weights of each item's mode tile, a ring of three), and the
 //     tcgen05.mma issue into one of two accumulators (2 x NR TMEM columns), released by
@@ -37,8 +38,8 @@
 namespace {
 
 constexpr int FT_ROWS = 128;                 // modes of a tile (TMEM lanes)
-constexpr int FT_WORKERS = 512;              // warps 0-15: four warpgroups
-constexpr int FT_THREADS = FT_WORKERS + 32;  // + warp 16 (copies and MMA issue)
+constexpr int FT_WORKERS = 256;              // warps 0-7: two warpgroups
+constexpr int FT_THREADS = FT_WORKERS + 32;  // + warp 8 (copies and MMA issue)
 constexpr int FT_CHUNK = 16 * 1024;          // bytes per bulk copy instruction
 constexpr int FT_MIN_SMEM = 120 * 1024;      // at most one CTA per SM (its TMEM allocation)
 constexpr int FT_ABUF = 3;                   // ring of A-operand tiles
@@ -103,6 +104,19 @@ __device__ __forceinline__ void df_square(float h, float l, float& oh, float& ol
   ol = e - (oh - p);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(r[e]);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Three bfloat16 terms of eight consecutive values (x = t0 + t1 + t2 up to about 2^-24
@@ -244,7 +258,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
   const uint32_t tmem = tmem_slot;
 
   if (warp < FT_WORKERS / 32) {
-    // thread (h, r): warpgroup h of four, row r of the tile (TMEM lane r)
+    // thread (h, r): warpgroup h of two, row r of the tile (TMEM lane r)
     const int r = tid & (FT_ROWS - 1), h = tid >> 7, lane = tid & 31;
     constexpr int UP = 2;  // slices of an item whose U is prefetched (further ones read in place)
     // the epilogue inputs of item i + 1 (E_hi, E_lo, exp(-lam M dt), U) are loaded while item
@@ -262,7 +276,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
       P.em = ok ? a.EM[J] : 0.0;
 #pragma unroll
       for (int t = 0; t < UP; ++t) {
-        const int s = h + 4 * t;
+        const int s = h + 2 * t;
         const int64_t n = g * a.G + s;
         P.u[t] = (!a.from_zero && ok && s < a.G && n < a.N) ? a.U[n * nd + J] : 0.0;
       }
@@ -283,29 +297,53 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
       const int64_t J = (i % a.tiles) * FT_ROWS + r;
       const bool ok = J < nd;
       const uint32_t row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((j & 1) * NR);
-      // this thread's slices s = h + 4t of the group (warp-uniform)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int s0 = h + 4 * t;
+      // this thread's slices s = h + 2t of the group, two at a time (warp-uniform); each
+      // TMEM read brings 32 substeps of both, and the chains run four substeps per step:
+      // w <- E^4 w + (E^3 a_m + E^2 a_{m+1} + E a_{m+2} + a_{m+3}), the bracket independent of
+      // w and E^4 applied as a hi/lo pair
+      auto chain4 = [&](float& w, float x0, float x1, float x2, float x3) {
+        const float b = fmaf(e3, x0, fmaf(e2, x1, fmaf(eh, x2, x3)));
+        w = fmaf(e4h, w, fmaf(e4l, w, b));
+      };
+      // the first pair's U was prefetched; later pairs (more than four slices per group) read it here
+      auto finish = [&](bool pre, double upre, int s, float w) {
+        const int64_t n = g * a.G + s;
+        if (ok && n < a.N) {
+          const double u = pre ? upre : (a.from_zero ? 0.0 : a.U[n * nd + J]);
+          a.out[n * nd + J] = a.from_zero ? (double)w : fma(cur.em, u, (double)w);
+        }
+      };
+#pragma unroll 1
+      for (int p = 0; p < 4; ++p) {
+        const int s0 = h + 4 * p, s1 = s0 + 2;
         if (s0 >= a.G) break;
-        // four substeps per step of the chain: w <- E^4 w + (E^3 a_m + E^2 a_{m+1} + E a_{m+2}
-        // + a_{m+3}); the bracket does not depend on w, and E^4 is applied as a hi/lo pair
-        float w0 = 0.f;
-        for (int m0 = 0; m0 < M; m0 += 16) {
-          float v0[16];
+        const bool two = s1 < a.G;
+        float w0 = 0.f, w1 = 0.f;
+        int m0 = 0;
+        for (; m0 + 32 <= M; m0 += 32) {
+          float v0[32], v1[32];
+          tmem_ld32(row + (uint32_t)(s0 * M + m0), v0);
+          if (two) tmem_ld32(row + (uint32_t)(s1 * M + m0), v1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            chain4(w0, v0[e], v0[e + 1], v0[e + 2], v0[e + 3]);
+            if (two) chain4(w1, v1[e], v1[e + 1], v1[e + 2], v1[e + 3]);
+          }
+        }
+        if (m0 < M) {  // a tail of 16 substeps
+          float v0[16], v1[16];
           tmem_ld16(row + (uint32_t)(s0 * M + m0), v0);
+          if (two) tmem_ld16(row + (uint32_t)(s1 * M + m0), v1);
           tmem_wait_ld();
 #pragma unroll
           for (int e = 0; e < 16; e += 4) {
-            const float b0 = fmaf(e3, v0[e], fmaf(e2, v0[e + 1], fmaf(eh, v0[e + 2], v0[e + 3])));
-            w0 = fmaf(e4h, w0, fmaf(e4l, w0, b0));
+            chain4(w0, v0[e], v0[e + 1], v0[e + 2], v0[e + 3]);
+            if (two) chain4(w1, v1[e], v1[e + 1], v1[e + 2], v1[e + 3]);
           }
         }
-        const int64_t n0 = g * a.G + s0;
-        if (ok && n0 < a.N) {
-          const double u0 = t < UP ? cur.u[t] : (a.from_zero ? 0.0 : a.U[n0 * nd + J]);
-          a.out[n0 * nd + J] = a.from_zero ? (double)w0 : fma(cur.em, u0, (double)w0);
-        }
+        finish(p == 0, cur.u[0], s0, w0);
+        if (two) finish(p == 0, cur.u[1], s1, w1);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
