@@ -42,6 +42,12 @@ TOL = 1e-6
 L2_BYTES = 129 * 1024 * 1024
 
 
+def engine(pe, prec):
+    """Fine-sweep engine of a separable-path solve: the tensor cores for the mixed form (the
+    chosen form), the float64 SIMT kernel otherwise."""
+    return pe.PE_FINE_TC if prec == pe.PE_MIXED else pe.PE_FINE_SIMT
+
+
 def workload():
     return I.config2()
 
@@ -287,7 +293,7 @@ def run_learned(pe, args, barrier):
     prob = I.config5(seed=1)
     dev = torch.device("cuda")
     out = {"workload": prob.label}
-    with pe.Solver(prob, precision=pe.PE_MIXED) as s:
+    with pe.Solver(prob, precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC) as s:
         lam = s.lam()
         lo, hi = np.log(lam.min()), np.log(lam.max())
         rng = np.random.default_rng(2024)
@@ -350,7 +356,7 @@ def run_precision(pe, args, barrier):
         return float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) / np.sqrt(np.sum(w * ref.U[-1] ** 2)))
 
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec) as s:
+        with pe.Solver(prob, precision=prec, fine_engine=engine(pe, prec)) as s:
             s.solve(tol=TOL)
             barrier()
             t0 = time.perf_counter()
@@ -382,7 +388,7 @@ def run_cached(pe, args, barrier, u0_dev, u0_host):
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=17, u0_nodal=u0_host)
     w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, cache_forced=True) as s:
+        with pe.Solver(prob, precision=prec, cache_forced=True, fine_engine=engine(pe, prec)) as s:
             for _ in range(max(1, args.warmup)):
                 s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
             barrier()
@@ -417,7 +423,7 @@ def run_dirichlet(pe, args, barrier):
     prob = dirichlet_problem()
     out = {"workload": prob.label}
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec) as s:
+        with pe.Solver(prob, precision=prec, fine_engine=engine(pe, prec)) as s:
             for _ in range(max(1, args.warmup)):
                 s.solve(tol=TOL)
             barrier()
@@ -447,7 +453,7 @@ def run_periodic(pe, args, barrier):
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=19)
     w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec) as s:
+        with pe.Solver(prob, precision=prec, fine_engine=engine(pe, prec)) as s:
             for _ in range(max(1, args.warmup)):
                 s.solve(tol=TOL)
             barrier()
@@ -698,10 +704,10 @@ def main():
 
     results = {}
     with ClockSampler(local if world > 1 else 0) as clocks:
-        for name, precision, engine in (("fp64", pe.PE_FP64, pe.PE_FINE_SIMT),
+        for name, precision, eng in (("fp64", pe.PE_FP64, pe.PE_FINE_SIMT),
                                         ("mixed_simt", pe.PE_MIXED, pe.PE_FINE_SIMT),
                                         ("mixed", pe.PE_MIXED, pe.PE_FINE_TC)):
-            with pe.Solver(prob, precision=precision, stream=stream, fine_engine=engine) as s:
+            with pe.Solver(prob, precision=precision, stream=stream, fine_engine=eng) as s:
                 total_ms, infos = timed_steps(s, args.steps, args.warmup, u0_dev)
                 modal = s.modal(prob.N)
                 # end to end through the C-ABI with host buffers: H2D of u0, D2H of the solution

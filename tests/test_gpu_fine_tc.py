@@ -147,3 +147,32 @@ def test_tc_engine_rejections(pe):
     with pytest.raises(pe.PEError) as ei:
         pe.Solver(prob, precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC, forcing_path=pe.PE_FORCING_GENERAL)
     assert ei.value.status == pe.PE_EINVAL
+
+
+def _builder(module):
+    import importlib.util
+    import os
+
+    spec = importlib.util.spec_from_file_location(module, os.path.join(os.path.dirname(__file__), module + ".py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod._problem
+
+
+@pytest.mark.parametrize("which", ["periodic", "dirichlet", "c3_small"])
+def test_tc_engine_other_separable_problems(pe, which):
+    """Periodic axes (DHT), non-homogeneous Dirichlet data (lifted forcing terms) and a 3D grid
+    through the tensor-core engine: the converged iterate against the oracle's sequential fine
+    solution (the Parareal fixed point), bound 1e-6."""
+    if which == "periodic":
+        prob = _builder("test_gpu_periodic")((128, 27), (True, False), N=4, M=16)
+    elif which == "dirichlet":
+        prob = _builder("test_gpu_dirichlet")(2, (23, 30), N=4, M=16)
+    else:
+        prob = I.scaled(I.config3(), (15, 13, 17), N=8, M=32)
+    sys_ = osolver.ModalSystem(prob)
+    fine = osolver.sequential_fine(sys_)
+    with pe.Solver(prob, precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC) as s:
+        s.solve(tol=1e-6)
+        for n in range(1, prob.N + 1):
+            assert _rel(s.modal(n), fine[n], sys_.norm_w) <= TOL_MIXED, n
