@@ -12,7 +12,8 @@ u0 = nodal values of sin(pi x) sin(pi y), f = manufactured term + 8 seeded
 Gaussian bumps modulated by sin(w t + phi), 32 slices x 64 substeps, RK4 fine
 (c = 0, 1/4, 1/2, 3/4), 2-stage coarse with seeded random nodes.  The main
 line is the float64 path; "chosen" reports the mixed-precision form on the
-same workload.  --impl reference times the CPU oracle instead.
+same workload with its stage contraction on the tensor cores ("mixed_simt": the
+same form on the CUDA cores).  --impl reference times the CPU oracle instead.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        (N > 1: launch with torch.distributed.run; ranks solve independent
