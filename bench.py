@@ -105,7 +105,12 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_rank{device_index}.csv")
+        # raw samples: PE_BENCH_CLOCKS_DIR if set, else the system's temporary directory (the
+        # JSON line carries their summary)
+        import tempfile
+
+        out_dir = os.environ.get("PE_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_bench_rank{device_index}.csv")
 
     def __enter__(self):
         try:
