@@ -68,3 +68,28 @@ def test_invalid_setup_arguments_rejected_before_device_work(lib):
     # NULL context pointers are rejected
     assert lib.pe_parareal_iter(None, None) == pe.PE_EINVAL
     assert lib.pe_dst(0, n, None, None, None) == pe.PE_EINVAL
+
+
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/pe.h, in declaration order."""
+    import os
+    import re
+
+    src = open(os.path.join(os.path.dirname(__file__), "..", "include", "pe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", src, re.S)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if decl:
+            fields.append(re.search(r"(\w+)\s*(\[[^\]]*\])*\s*$", decl).group(1))
+    return fields
+
+
+@pytest.mark.parametrize("name", ["pe_options", "pe_term", "pe_tableau", "pe_field", "pe_forcing", "pe_result"])
+def test_python_struct_mirrors_match_the_header(name):
+    """The ctypes mirrors of the C-ABI structs list the header's fields in the same order."""
+    from paper_2412_01138_gb300 import pe
+
+    assert [f for f, _ in getattr(pe, name)._fields_] == _header_struct_fields(name)
