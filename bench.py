@@ -288,6 +288,37 @@ def run_batch(pe, args, barrier):
     return out
 
 
+def run_config1(pe, args, barrier):
+    """The 1D workload (63 interior nodes, 8 x 16, RK2/RK2, manufactured e^{-t} sin(pi x)): float64 to
+    its own residual tolerance 1e-12 and to 1e-6, and the chosen mixed form (tensor-core stage
+    contraction) to 1e-6; every mode checked against the oracle (a launch- and latency-bound size)."""
+    from oracle import solver as osolver
+
+    prob = I.config1()
+    sys_ = osolver.ModalSystem(prob)
+    out = {"workload": prob.label}
+    for name, prec, eng, tol in (("fp64_tol1e-12", pe.PE_FP64, pe.PE_FINE_SIMT, 1e-12),
+                                 ("fp64", pe.PE_FP64, pe.PE_FINE_SIMT, TOL),
+                                 ("chosen", pe.PE_MIXED, pe.PE_FINE_TC, TOL)):
+        with pe.Solver(prob, precision=prec, fine_engine=eng) as s:
+            for _ in range(max(3, args.warmup)):
+                s.solve(tol=tol)
+            barrier()
+            t0 = time.perf_counter()
+            reps = max(10, args.steps)
+            infos = [s.solve(tol=tol) for _ in range(reps)]
+            barrier()
+            dt = (time.perf_counter() - t0) / reps
+            modal = s.modal(prob.N)
+        ref = osolver.parareal(sys_, tol=tol)
+        out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"], "tol": tol,
+                     "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
+                     "rel_l2_vs_oracle": osolver.rel_l2(modal, ref.U[-1], sys_.norm_w),
+                     "gpu_launches": infos[-1]["kernel_launches"]}
+    out["speedup_time_to_tol"] = out["fp64"]["time_to_tol_ms"] / out["chosen"]["time_to_tol_ms"]
+    return out
+
+
 def run_learned(pe, args, barrier):
     """511^2 workload, 128 x 32: plain coarse step vs the learned coarse correction (mixed form).
 
@@ -337,6 +368,19 @@ def run_learned(pe, args, barrier):
                          "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
                          "residual": infos[-1]["residual"], "modal": modal}
         s.set_learned(None)
+    # the plain float64 form on the same workload (plain G, SIMT float64 fine kernel)
+    with pe.Solver(prob, precision=pe.PE_FP64) as s:
+        for _ in range(max(1, args.warmup)):
+            s.solve(tol=TOL)
+        barrier()
+        t1 = time.perf_counter()
+        steps = max(1, min(args.steps, 3))
+        infos = [s.solve(tol=TOL) for _ in range(steps)]
+        barrier()
+        dt = (time.perf_counter() - t1) / steps
+        res["fp64_plain_G"] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
+                               "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
+                               "residual": infos[-1]["residual"], "modal": s.modal(prob.N)}
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=11)
     w = sys_.norm_w
     for name in res:
@@ -345,6 +389,7 @@ def run_learned(pe, args, barrier):
                                               np.sqrt(np.sum(w * ref.U[-1] ** 2)))
     out.update(res)
     out["speedup_time_to_tol"] = res["plain_G"]["time_to_tol_ms"] / res["learned_G"]["time_to_tol_ms"]
+    out["speedup_vs_fp64"] = res["fp64_plain_G"]["time_to_tol_ms"] / res["learned_G"]["time_to_tol_ms"]
     net.close()
     return out
 
@@ -520,11 +565,15 @@ def run_dst(pe, args, barrier):
     return out
 
 
-def run_general(pe, args, barrier, u0_dev):
+def run_general(pe, args, barrier, u0_dev, u0_host):
     """The 255^2 workload through the general forcing path: consistent load + tensor DST-I at
-    every one of the 32 x 64 x 4 fine stage times, per sweep."""
+    every one of the 32 x 64 x 4 fine stage times, per sweep.  Parity against the oracle on
+    1024 sampled modes (the source is separable: the oracle's element quadrature of it equals
+    its per-axis route, which runs on a mode subset)."""
     prob = workload()
     out = {"workload": prob.label + " general forcing path (DST per stage time)"}
+    rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=23, u0_nodal=u0_host)
+    w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
         with pe.Solver(prob, precision=prec, forcing_path=pe.PE_FORCING_GENERAL) as s:
             for _ in range(max(1, args.warmup)):
@@ -535,10 +584,13 @@ def run_general(pe, args, barrier, u0_dev):
             infos = [s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev) for _ in range(steps)]
             barrier()
             dt = (time.perf_counter() - t1) / steps
+            m = s.modal(prob.N)
         sweeps = infos[-1]["fine_sweeps"]
         out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
                      "value": prob.ndof * prob.N * prob.M * sweeps / dt, "unit": UNIT,
-                     "dst_transforms_per_step": sweeps * prob.N * prob.M * prob.q + prob.N * prob.p + 2}
+                     "dst_transforms_per_step": sweeps * prob.N * prob.M * prob.q + prob.N * prob.p + 2,
+                     "rel_l2_vs_oracle": float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) /
+                                               np.sqrt(np.sum(w * ref.U[-1] ** 2)))}
     return out
 
 
@@ -570,6 +622,56 @@ def run_example4(pe, args, barrier):
             rec[name] = {"ms": 1e3 * dt, "residuals": res,
                          "value": prob.ndof * prob.N * prob.M * 4 / dt, "unit": UNIT}
         out[f"a{alpha}_f{freq}"] = rec
+    return out
+
+
+def fine_tc_tensor_flops(prob):
+    """Tensor FLOPs one fine_tc_kernel launch issues: six split products over the K padding
+    (16, 32 or 64 columns) for every 128-mode tile and slice group of at most 256 substeps."""
+    K = stage_columns(prob)
+    KP = 16 if K <= 16 else (32 if K <= 32 else 64)
+    rows_max = 256 if KP <= 32 else 128
+    G = max(1, rows_max // prob.M)
+    groups = (prob.N + G - 1) // G
+    tiles = (prob.ndof + 127) // 128
+    return tiles * 128 * groups * G * prob.M * KP * 2 * 6
+
+
+def chosen_rooflines(prob, chosen, plain, fma):
+    """Rooflines of the chosen form's kernels and of the float64 correction: per-launch CUDA-event
+    times measured inside the library on the launching stream, algorithmic work per launch."""
+    peaks = measured_peaks() or {}
+    hbm = float(peaks.get("hbm_gbs", 6788.6))
+    bf16 = float(peaks.get("bf16_tflops", 1928.9))
+    nd, N, M, p = prob.ndof, prob.N, prob.M, prob.p
+    out = []
+    ms = chosen["ms_fine_launch"]
+    alg = 2 * (stage_columns(prob) + 1) * nd * N * M
+    issued = fine_tc_tensor_flops(prob)
+    out.append({"kernel": "fine_tc_kernel (chosen)", "bound": "tensor", "ms": ms,
+                "achieved": alg / (ms / 1e3) / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "frac": alg / (ms / 1e3) / 1e12 / bf16,
+                "tensor_issued_tflops": issued / (ms / 1e3) / 1e12,
+                "tensor_issued_frac": issued / (ms / 1e3) / 1e12 / bf16,
+                "flops_per_launch_algorithmic": alg, "tensor_flops_per_launch": issued,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
+                "note": "algorithmic = 2 (K + 1) FLOP per DoF*substep; issued = six bf16 split products over "
+                        "the padded K and the 128-mode tiles"})
+    for name, rec in (("correction_kernel (chosen)", chosen), ("correction_kernel (float64)", plain)):
+        ms = rec["ms_corr_launch"]
+        nbytes = 24 * N * nd + 16 * nd
+        out.append({"kernel": name, "bound": "hbm", "ms": ms, "achieved": nbytes / (ms / 1e3) / 1e9,
+                    "peak": hbm, "unit": "GB/s", "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+                    "bytes_per_launch": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                    "note": "24 B per DoF*slice (F^M(U^n), old U^{n+1} in, new U^{n+1} out) + U^0 and E_G"})
+    ms = chosen["ms_coarse"]
+    nbytes = 8 * N * nd + 8 * (p + 2) * nd
+    out.append({"kernel": "coarse_fused_kernel (chosen, k = 0)", "bound": "hbm", "ms": ms,
+                "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": nbytes / (ms / 1e3) / 1e9 / hbm, "bytes_per_launch": nbytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "note": "U^{n+1} written for every slice (8 B per DoF*slice) + U^0, E_G and the p weights read; "
+                        "the forcing is formed on the fly from per-axis factors"})
     return out
 
 
@@ -637,8 +739,9 @@ def main():
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the Dirichlet-data line")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-axis line")
     ap.add_argument("--no-example4", action="store_true", help="skip the Example 4 paper-size line")
+    ap.add_argument("--no-config1", action="store_true", help="skip the 1D 63-node workload line")
     ap.add_argument("--only", choices=["batch", "learned", "general", "dst", "precision", "cached", "dirichlet",
-                                       "periodic", "example4"],
+                                       "periodic", "example4", "config1"],
                     help="run one secondary workload alone and print its record (for profiling)")
     args = ap.parse_args()
 
@@ -696,7 +799,8 @@ def main():
 
     if args.only:
         run = {"batch": lambda: run_batch(pe, args, barrier), "learned": lambda: run_learned(pe, args, barrier),
-               "general": lambda: run_general(pe, args, barrier, u0_dev),
+               "general": lambda: run_general(pe, args, barrier, u0_dev, u0_host),
+               "config1": lambda: run_config1(pe, args, barrier),
                "dst": lambda: run_dst(pe, args, barrier),
                "precision": lambda: run_precision(pe, args, barrier),
                "cached": lambda: run_cached(pe, args, barrier, u0_dev, u0_host),
@@ -708,6 +812,9 @@ def main():
             print(json.dumps({"section": args.only, **rec}))
         return
 
+    # measured FMA peaks of the CUDA cores (outside every timed region)
+    measured_fma = {"fp64_tflops": pe.measure_fma_peak(pe.PE_FP64, stream),
+                    "fp32_tflops": pe.measure_fma_peak(pe.PE_MIXED, stream)}
     results = {}
     with ClockSampler(local if world > 1 else 0) as clocks:
         for name, precision, eng in (("fp64", pe.PE_FP64, pe.PE_FINE_SIMT),
@@ -728,7 +835,8 @@ def main():
             results[name] = dict(total_ms=total_ms, infos=infos, modal=modal, e2e_s=e2e_s)
         batch = None if args.no_batch else run_batch(pe, args, barrier)
         learned = None if args.no_learned else run_learned(pe, args, barrier)
-        general = None if args.no_general else run_general(pe, args, barrier, u0_dev)
+        general = None if args.no_general else run_general(pe, args, barrier, u0_dev, u0_host)
+        config1 = None if args.no_config1 else run_config1(pe, args, barrier)
         dst = None if args.no_dst else run_dst(pe, args, barrier)
         precision = None if args.no_precision else run_precision(pe, args, barrier)
         cached = None if args.no_cached else run_cached(pe, args, barrier, u0_dev, u0_host)
@@ -754,9 +862,12 @@ def main():
         e2e_units = prob.ndof * prob.N * prob.M * k * args.steps * world
         ms_fine = np.mean([i["ms_fine_kernel"] / max(i["fine_sweeps"], 1) for i in r["infos"]])
         phases = {key: float(np.mean([i[key] for i in r["infos"]]))
-                  for key in ("ms_tables", "ms_prepare", "ms_iterations", "ms_output", "ms_fine_kernel")}
+                  for key in ("ms_tables", "ms_prepare", "ms_iterations", "ms_output", "ms_fine_kernel",
+                              "ms_correction_kernel", "ms_coarse_kernel")}
+        ms_corr = np.mean([i["ms_correction_kernel"] / max(i["k"], 1) for i in r["infos"]])
         return dict(value=value, k=k, ms_per_step=r["total_ms"] / args.steps, e2e=e2e_units / r["e2e_s"],
-                    ms_fine_launch=ms_fine, launches=r["infos"][-1]["kernel_launches"],
+                    ms_fine_launch=ms_fine, ms_corr_launch=float(ms_corr),
+                    ms_coarse=phases["ms_coarse_kernel"], launches=r["infos"][-1]["kernel_launches"],
                     residual=r["infos"][-1]["residual"], phases=phases)
 
     plain = summarize(results["fp64"])
@@ -795,6 +906,8 @@ def main():
     sm_mhz = clock.get("sm_max_mhz") or 2070.0
     peak = fp64_peak_tflops(sm_mhz)
     traffic = fine_f64_traffic()
+    fma = measured_fma
+    kernel_rooflines = chosen_rooflines(prob, chosen, plain, fma)
 
     line = {
         "metric": METRIC,
@@ -826,6 +939,7 @@ def main():
                    "fine_kernel_tflops": fine_flops_per_unit(prob, mixed=True) * prob.ndof * prob.N * prob.M
                    / (chosen["ms_fine_launch"] / 1e3) / 1e12,
                    "fp32_peak_tflops": fp32_peak_tflops(sm_mhz),
+                   "fp32_peak_tflops_measured": measured_fma["fp32_tflops"],
                    "e2e": chosen["e2e"], "phases_ms": chosen["phases"]},
         "mixed_simt": {"form": "mixed, float32 stage contraction on the CUDA cores (K + 2 FMAs per DoF*substep)",
                        "value": simt["value"], "unit": UNIT, "time_to_tol_ms": simt["ms_per_step"],
@@ -838,12 +952,22 @@ def main():
         "roofline": {"kernel": "fine_f64_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x max SM clock",
-                     "flops_per_launch": flops_launch},
+                     "peak_measured": fma["fp64_tflops"], "frac_of_measured": achieved / fma["fp64_tflops"],
+                     "peak_measured_source": "pe_measure_fma_peak(PE_FP64): independent FMA chains, best of 5",
+                     "flops_per_launch": flops_launch,
+                     "flops_per_unit": fine_flops_per_unit(prob),
+                     "unit_of_work": "DoF*substep; 2 (K + 1) FLOP = K + 1 FMAs: the q-stage forcing sum of "
+                                     "Eq. (1-7) contracted exactly to K = 17 time columns (one per exponential, "
+                                     "two per sinusoid) plus the E_F multiply; the stage-by-stage count "
+                                     "q (2R + 2) + 1 = 81 is not what the kernel has to execute"},
+        "kernel_rooflines": kernel_rooflines,
+        "measured_fma_peaks": fma,
         "e2e": {"value": plain["e2e"], "unit": UNIT, "h2d_bytes_per_step": prob.ndof * 8,
                 "d2h_bytes_per_step": prob.ndof * 8 + 16 * plain["k"]},
         "gpu_launches": int(plain["launches"] + 0) * args.steps,
         "clocks": clock,
         "cpu_baseline": cpu,
+        "config1": config1,
         "batched": batch,
         "learned": learned,
         "general": general,

@@ -160,6 +160,8 @@ typedef struct {
   double ms_output;          /* inverse DST of the final slice */
   double ms_fine_kernel;     /* device time of the fine-propagator kernels alone (sum over sweeps) */
   int64_t kernel_launches;   /* kernels this call launched */
+  double ms_correction_kernel; /* device time of the correction + residual kernel (sum over iterations) */
+  double ms_coarse_kernel;   /* device time of the coarse sweep of k = 0 (its kernels alone) */
 } pe_result;
 
 /*
@@ -276,7 +278,8 @@ pe_status pe_dst_f32(int32_t d, const int32_t* n, const float* in, float* out, v
  * exits.  Limits: at most 1,048,576 values in total; an axis whose n+1 is not a power
  * of two must have n <= 512.  Larger sizes return PE_EINVAL with a message.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current: make that first call before any stream capture.
+ * with that device current: make that first call before any stream capture.  The address
+ * is kept for the life of the process: do not use this call across a cudaDeviceReset.
  * Every call shares the one array and leaves its contents behind; nothing in it has to
  * start at zero (each call writes what it reads), but calls that overlap on the GPU
  * (different streams, or different host threads on one device) race on it.
@@ -394,6 +397,31 @@ pe_status pe_set_learned(pe_ctx* ctx, const pe_mlp* m);
  * in the kernel expired (the kernel then skips its output).
  */
 pe_status pe_dst_tc(int32_t d, const int32_t* n, const float* in, float* out, int32_t nsplit, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement and self-check calls (the paper has no counterpart).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * pe_measure_fma_peak -- FMA throughput of the CUDA cores in TFLOP/s (2 FLOP per FMA),
+ * measured by a kernel of independent FMA chains (8 per thread, 2048 threads per SM), the
+ * best of five timed launches after one warm-up: precision PE_FP64 for float64 FMAs,
+ * PE_MIXED for float32 FMAs.  The ALU-bound fine kernels are quoted against it beside
+ * the peak derived from unit counts and the clock.  tflops_out: host.  Allocates 40 KB
+ * with cudaMallocAsync on the stream for the duration of the call.
+ */
+pe_status pe_measure_fma_peak(int32_t precision, double* tflops_out, void* stream);
+
+/*
+ * pe_probe_wait_timeout -- runs the bounded mbarrier wait of the tensor-core kernels
+ * on a barrier that nothing arrives at, in a one-warp kernel with no tensor-core
+ * instruction and no copy in flight, giving up after budget_cycles SM clock cycles
+ * (1..1e8; 2e6 is about a millisecond).  Returns PE_ETIMEOUT (the status the
+ * tensor-core kernels report when one of their waits expires) after the kernel has
+ * recorded the expiry and returned; the context stays usable.  PE_EINVAL for a budget
+ * out of range.  Allocates 4 bytes with cudaMallocAsync for the status word.
+ */
+pe_status pe_probe_wait_timeout(int64_t budget_cycles, void* stream);
 
 /* Most recent error message on this thread ("" if none). */
 const char* pe_last_error(void);

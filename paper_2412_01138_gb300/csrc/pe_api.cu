@@ -132,7 +132,7 @@ void free_ctx(pe_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < PE_NEV; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -207,7 +207,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
 
   pe_ctx* c = new (std::nothrow) pe_ctx();
   if (!c) return pe_fail(PE_ENOMEM, "pe_setup: host allocation failed");
-  for (int i = 0; i < 8; ++i) c->ev[i] = nullptr;
+  for (int i = 0; i < PE_NEV; ++i) c->ev[i] = nullptr;
   c->g.d = d;
   c->g.ndof = ndof;
   c->nsum = nsum;
@@ -329,7 +329,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     cudaGetLastError();
     st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");
   }
-  for (int i = 0; i < 8 && st == PE_OK; ++i)
+  for (int i = 0; i < PE_NEV && st == PE_OK; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = pe_cuda_fail(cudaGetLastError(), "cudaEventCreate");
   if (st == PE_OK && (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
                       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -492,6 +492,8 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   if (!general) PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1, c->lkind));
   if (fork) PE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   if (!general) PE_TRY(launch_stage_weights(c));
+  // the tensor-core engine's split operand images of the stage weights and time factors
+  if (!general && c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC) PE_TRY(fine_tc_prepare(c));
   PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
   // U^0 = P_h u0
   if (fork_u0) {
@@ -526,7 +528,9 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     PE_TRY(add_lift(c, c->t0, -1.0, nodal ? 2 : 1, U0));
   }
   // k = 0: coarse sweep
+  PE_CUDA_TRY(cudaEventRecord(c->ev[8], c->stream));
   PE_TRY(launch_coarse_sweep(c));
+  PE_CUDA_TRY(cudaEventRecord(c->ev[9], c->stream));
   c->fz_prec = -1;
   c->k = 0;
   c->have_problem = true;
@@ -549,8 +553,9 @@ static pe_status iter_impl(pe_ctx* c, double* r_out, int precision) {
   else PE_TRY(launch_fine_sweep(c, precision));
   PE_CUDA_TRY(cudaEventRecord(c->ev[6], c->stream));
   double num = 0.0, den = 0.0;
-  PE_TRY(launch_correction(c, &num, &den));  // synchronises the stream
+  PE_TRY(launch_correction(c, &num, &den, c->ev[7]));  // synchronises the stream
   c->ms_fine += elapsed(c->ev[5], c->ev[6]);
+  c->ms_corr += elapsed(c->ev[6], c->ev[7]);
   c->k += 1;
   if (!isfinite(num) || !isfinite(den)) {
     c->have_problem = false;
@@ -582,6 +587,7 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   c->have_problem = false;
   c->launches = 0;
   c->ms_fine = 0.0;
+  c->ms_corr = 0.0;
   c->sweeps = 0;
   PE_CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
   PE_TRY(set_problem_impl(c, u0, f));
@@ -610,6 +616,8 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
     res->ms_output = elapsed(c->ev[3], c->ev[4]);
     res->ms_fine_kernel = c->ms_fine;
     res->kernel_launches = c->launches;
+    res->ms_correction_kernel = c->ms_corr;
+    res->ms_coarse_kernel = elapsed(c->ev[8], c->ev[9]);
   }
   if (r > tol && c->k < c->N) return pe_fail(PE_ENOCONV, "pe_solve: residual above tol after max_iter iterations");
   return PE_OK;
@@ -664,13 +672,28 @@ extern "C" pe_status pe_get_nodes(pe_ctx* c, int32_t which, double* c_out) {
 }
 
 namespace {
+// the problem a state belongs to: grid (every axis), box, D, time interval and partition
 struct StateHeader {
   uint64_t magic;
-  int32_t d, N, k, pad;
+  int32_t d, N, k, M;
   int64_t ndof;
-  int32_t n[3], pad2;
+  int32_t n[3], periodic_mask;
+  double box[6], D, t0, T;
 };
-const uint64_t kStateMagic = 0x3230353135504550ull;  // "PEP51502"
+const uint64_t kStateMagic = 0x3330353135504550ull;  // "PEP51503"
+
+void fill_header(const pe_ctx* c, StateHeader* h) {
+  memset(h, 0, sizeof(*h));
+  h->magic = kStateMagic;
+  h->d = c->g.d; h->N = c->N; h->k = c->k; h->M = c->M; h->ndof = c->g.ndof;
+  for (int a = 0; a < 3; ++a) {
+    h->n[a] = c->g.n[a];
+    h->periodic_mask |= c->g.per[a] << a;
+    h->box[2 * a] = c->lo[a];
+    h->box[2 * a + 1] = c->hi[a];
+  }
+  h->D = c->D; h->t0 = c->t0; h->T = c->T;
+}
 }  // namespace
 
 extern "C" pe_status pe_save_state(pe_ctx* c, void* buf, size_t* bytes) {
@@ -683,10 +706,8 @@ extern "C" pe_status pe_save_state(pe_ctx* c, void* buf, size_t* bytes) {
   }
   if (*bytes < need) return pe_fail(PE_EINVAL, "pe_save_state: buffer too small");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_save_state: no problem set");
-  StateHeader h{};
-  h.magic = kStateMagic;
-  h.d = c->g.d; h.N = c->N; h.k = c->k; h.ndof = c->g.ndof;
-  for (int a = 0; a < 3; ++a) h.n[a] = c->g.n[a];
+  StateHeader h;
+  fill_header(c, &h);
   memcpy(buf, &h, sizeof(h));
   char* p = (char*)buf + sizeof(h);
   PE_CUDA_TRY(cudaMemcpyAsync(p, c->U, sizeof(double) * (N + 1) * nd, cudaMemcpyDeviceToHost, c->stream));
@@ -701,10 +722,16 @@ extern "C" pe_status pe_load_state(pe_ctx* c, const void* buf, size_t bytes) {
   const size_t nd = (size_t)c->g.ndof, N = (size_t)c->N;
   const size_t need = sizeof(StateHeader) + sizeof(double) * (N + 1) * nd;
   if (bytes < need) return pe_fail(PE_EINVAL, "pe_load_state: buffer too small");
-  StateHeader h;
+  StateHeader h, mine;
   memcpy(&h, buf, sizeof(h));
-  if (h.magic != kStateMagic || h.d != c->g.d || h.N != c->N || h.ndof != c->g.ndof)
-    return pe_fail(PE_EINVAL, "pe_load_state: state does not match this context");
+  fill_header(c, &mine);
+  if (h.magic != kStateMagic) return pe_fail(PE_EINVAL, "pe_load_state: not a libpe state (bad magic)");
+  // everything but k must match: a state of another grid (also the same Ndof with the axes
+  // swapped), box, D, time interval or partition would put the modes in the wrong places
+  mine.k = h.k;
+  if (memcmp(&h, &mine, sizeof(h)) != 0)
+    return pe_fail(PE_EINVAL, "pe_load_state: state belongs to another problem (grid, box, D, time interval "
+                              "or partition differ)");
   const char* p = (const char*)buf + sizeof(h);
   PE_CUDA_TRY(cudaMemcpyAsync(c->U, p, sizeof(double) * (N + 1) * nd, cudaMemcpyHostToDevice, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));

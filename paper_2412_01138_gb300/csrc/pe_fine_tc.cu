@@ -483,7 +483,9 @@ size_t fine_tc_buffer_bytes(int M, int N) {
   return most;
 }
 
-pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
+// The split operand images depend only on the problem (stage weights, time factors): made
+// once by pe_set_problem (after the stage weights) and reused by every sweep of the problem.
+pe_status fine_tc_prepare(pe_ctx* c) {
   const int M = c->M, K = c->K, N = c->N;
   if (!fine_tc_supported(M) || K < 1 || K > 64 || !c->tcB || !c->tc_err)
     return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported shape");
@@ -493,27 +495,35 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
   const size_t a_need = (size_t)tiles * ft_a_bytes(KP);
   if (a_need > c->tcA_cap) {
+    PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->tcA) PE_CUDA_TRY(cudaFree(c->tcA));
     c->tcA = nullptr;
     c->tcA_cap = 0;
     PE_CUDA_TRY(cudaMalloc((void**)&c->tcA, a_need));
     c->tcA_cap = a_need;
-    c->tc_split_ok = false;
   }
-  // the split operand images depend only on the problem (stage weights, time factors):
-  // made at the first sweep after pe_set_problem and reused by later sweeps
-  if (!c->tc_split_ok) {
-    const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
-    ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
-                                                                                   ngroups, (uint4*)c->tcB);
-    PE_CUDA_TRY(cudaGetLastError());
-    const int64_t nsw = tiles * FT_ROWS * (KP / 8);
-    ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
-                                                                             (uint4*)c->tcA);
-    PE_CUDA_TRY(cudaGetLastError());
-    c->tc_split_ok = true;
-    c->launches += 2;
-  }
+  const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
+  ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
+                                                                                 ngroups, (uint4*)c->tcB);
+  PE_CUDA_TRY(cudaGetLastError());
+  const int64_t nsw = tiles * FT_ROWS * (KP / 8);
+  ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
+                                                                           (uint4*)c->tcA);
+  PE_CUDA_TRY(cudaGetLastError());
+  c->tc_split_ok = true;
+  c->launches += 2;
+  return PE_OK;
+}
+
+pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
+  const int M = c->M, K = c->K, N = c->N;
+  if (!fine_tc_supported(M) || K < 1 || K > 64 || !c->tcB || !c->tc_err)
+    return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported shape");
+  if (!c->tc_split_ok) PE_TRY(fine_tc_prepare(c));
+  const int KP = ft_kpad(K);
+  int G, NR, ngroups;
+  ft_shape(KP, M, N, &G, &NR, &ngroups);
+  const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
   FtArgs args{};
   args.W32 = c->Wst32;
   args.coefF32 = c->coefF32;

@@ -10,6 +10,7 @@
 
 #define PE_MAX_D 3
 #define PE_MAX_S 8
+#define PE_NEV 10  // timing events of a context
 
 // ---------------------------------------------------------------------------
 // error reporting (thread-local message behind pe_last_error)
@@ -139,11 +140,12 @@ struct pe_ctx {
   // accounting
   int64_t launches = 0;     // kernels launched since the last reset
   double ms_fine = 0.0;     // device time of fine-propagator kernels since the last reset
+  double ms_corr = 0.0;     // device time of correction kernels since the last reset
   // state
   int k = 0;
   bool have_problem = false;
   bool have_output = false;
-  cudaEvent_t ev[8];
+  cudaEvent_t ev[PE_NEV];
 };
 
 // Substeps of time factors (per_m values each) staged per shared-memory fill.
@@ -193,7 +195,7 @@ pe_status axis_factors_fused(pe_ctx* c, int R, const double* loads, double* fac,
 // pe_sweep.cu
 pe_status launch_coarse_sweep(pe_ctx* c);
 pe_status launch_fine_sweep(pe_ctx* c, int precision);
-pe_status launch_correction(pe_ctx* c, double* num, double* den);
+pe_status launch_correction(pe_ctx* c, double* num, double* den, cudaEvent_t after = nullptr);
 pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse);
 
 // pe_learned.cu
@@ -207,5 +209,6 @@ pe_status launch_general_fine_sweep(pe_ctx* c, int precision);
 // pe_fine_tc.cu (tensor-core engine of the mixed fine sweep)
 bool fine_tc_supported(int M);                 // M a multiple of 16 in 16..128
 size_t fine_tc_buffer_bytes(int M, int N);     // split time factors, any K <= 64
+pe_status fine_tc_prepare(pe_ctx* c);          // split operand images of the current problem
 pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out);
 pe_status fine_tc_status(pe_ctx* c);           // PE_ETIMEOUT if a pipeline wait expired

@@ -438,7 +438,7 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
   return PE_OK;
 }
 
-pe_status launch_correction(pe_ctx* c, double* num, double* den) {
+pe_status launch_correction(pe_ctx* c, double* num, double* den, cudaEvent_t after) {
   const int threads = 256;
   const int blocks = (int)((c->g.ndof + threads - 1) / threads);
   if (blocks > c->max_blocks) return pe_fail(PE_EINVAL, "correction: partials buffer too small");
@@ -446,6 +446,7 @@ pe_status launch_correction(pe_ctx* c, double* num, double* den) {
                                                        c->partials, c->done_ctr, c->red);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
+  if (after) PE_CUDA_TRY(cudaEventRecord(after, c->stream));
   PE_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   *num = c->h_red[0];

@@ -48,13 +48,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: false once about kTcWaitCycles have passed
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait: false once about `budget` SM clock cycles have passed
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kTcWaitCycles) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
+}
+
+// the wait of the tensor-core kernels: false once about kTcWaitCycles have passed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, kTcWaitCycles);
 }
 
 

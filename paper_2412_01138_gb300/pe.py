@@ -37,13 +37,16 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_batch_autotune", "pe_batch_solve", "pe_batch_get_modal", "pe_batch_get_solution", "pe_batch_status",
             "pe_batch_destroy", "pe_mlp_create", "pe_mlp_num_params", "pe_mlp_train", "pe_mlp_gradient",
             "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
-            "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc", "pe_set_dirichlet")
+            "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc", "pe_set_dirichlet", "pe_measure_fma_peak",
+            "pe_probe_wait_timeout")
 
 
 class PEError(RuntimeError):
-    def __init__(self, status: int, msg: str):
+    def __init__(self, status: int, msg: str, result: Optional[dict] = None):
         super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+        #: what the call reported before it failed (pe_solve's pe_result on PE_ENOCONV), else None
+        self.result = result
 
 
 class pe_term(C.Structure):
@@ -74,7 +77,8 @@ class pe_result(C.Structure):
     _fields_ = [("k", C.c_int32), ("residual", C.c_double), ("residual_history", C.POINTER(C.c_double)),
                 ("history_cap", C.c_int32), ("fine_sweeps", C.c_int64), ("ms_tables", C.c_double),
                 ("ms_prepare", C.c_double), ("ms_iterations", C.c_double), ("ms_output", C.c_double),
-                ("ms_fine_kernel", C.c_double), ("kernel_launches", C.c_int64)]
+                ("ms_fine_kernel", C.c_double), ("kernel_launches", C.c_int64),
+                ("ms_correction_kernel", C.c_double), ("ms_coarse_kernel", C.c_double)]
 
 
 class pe_problem(C.Structure):
@@ -133,6 +137,8 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_dst_tc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, C.c_int32, P]),
         "pe_dst_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
         "pe_set_dirichlet": (C.c_int, [P, C.c_int32, P]),
+        "pe_measure_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), P]),
+        "pe_probe_wait_timeout": (C.c_int, [C.c_int64, P]),
         "pe_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -284,11 +290,16 @@ class Solver:
         res.residual_history = C.cast(hist, C.POINTER(C.c_double))
         res.history_cap = history
         tol = self.prob.tol if tol is None else tol
-        _check(self._lib.pe_solve(self.ctx, C.byref(f), C.byref(self._forcing()), tol, C.byref(res)))
-        return {"k": res.k, "residual": res.residual, "history": list(hist[: min(res.k, history)]),
+        st = self._lib.pe_solve(self.ctx, C.byref(f), C.byref(self._forcing()), tol, C.byref(res))
+        info = {"k": res.k, "residual": res.residual, "history": list(hist[: min(res.k, history)]),
                 "fine_sweeps": res.fine_sweeps, "ms_tables": res.ms_tables, "ms_prepare": res.ms_prepare,
                 "ms_iterations": res.ms_iterations, "ms_output": res.ms_output,
-                "ms_fine_kernel": res.ms_fine_kernel, "kernel_launches": res.kernel_launches}
+                "ms_fine_kernel": res.ms_fine_kernel, "kernel_launches": res.kernel_launches,
+                "ms_correction_kernel": res.ms_correction_kernel, "ms_coarse_kernel": res.ms_coarse_kernel}
+        if st != PE_OK:
+            # PE_ENOCONV: the iterations ran and the result is filled in; the caller may want it
+            raise PEError(st, self._lib.pe_last_error().decode(), info if st == PE_ENOCONV else None)
+        return info
 
     # -- outputs ------------------------------------------------------------
     def _out(self, count: int, out):
@@ -349,23 +360,59 @@ class Solver:
         _check(self._lib.pe_load_state(self.ctx, buf, len(blob)))
 
 
+def _device_buffers(name: str, d: int, n: Sequence[int], dtype: str, *bufs):
+    """Checks of the device buffers of a standalone transform before any pointer reaches the
+    library (which trusts its arguments): torch CUDA tensors of the transform's dtype holding at
+    least prod(n) elements, contiguous."""
+    if len(n) != d or d < 1:
+        raise ValueError(f"{name}: n must hold d = {d} sizes")
+    count = 1
+    for v in n:
+        count *= int(v)
+    for b in bufs:
+        if not (hasattr(b, "is_cuda") and b.is_cuda):
+            raise ValueError(f"{name}: buffers must be CUDA tensors")
+        if str(b.dtype) != f"torch.{dtype}":
+            raise ValueError(f"{name}: buffers must be {dtype}, got {b.dtype}")
+        if b.numel() < count:
+            raise ValueError(f"{name}: a buffer holds {b.numel()} values, the transform needs {count}")
+        if not b.is_contiguous():
+            raise ValueError(f"{name}: buffers must be contiguous")
+
+
 def dst_tc(d: int, n: Sequence[int], x_in, x_out, nsplit: int = 3, stream=None):
     """Tensor-core (tcgen05) DST-I of a float32 device buffer, split-bfloat16 operands."""
+    _device_buffers("dst_tc", d, n, "float32", x_in, x_out)
     nn = (C.c_int32 * d)(*n)
     _check(lib().pe_dst_tc(d, nn, _ptr(x_in), _ptr(x_out), nsplit, stream_handle(stream)))
 
 
 def dst_noalloc(d: int, n: Sequence[int], x_in, x_out, stream=None):
     """Float64 DST-I that allocates nothing (scratch in a built-in device array); see pe_dst_noalloc."""
+    _device_buffers("dst_noalloc", d, n, "float64", x_in, x_out)
     nn = (C.c_int32 * d)(*n)
     _check(lib().pe_dst_noalloc(d, nn, _ptr(x_in), _ptr(x_out), stream_handle(stream)))
 
 
 def dst(d: int, n: Sequence[int], x_in, x_out, stream=None, f32: bool = False):
     """Orthonormal tensor DST-I of a device buffer (torch tensor), out may alias in."""
+    _device_buffers("dst", d, n, "float32" if f32 else "float64", x_in, x_out)
     nn = (C.c_int32 * d)(*n)
     fn = lib().pe_dst_f32 if f32 else lib().pe_dst
     _check(fn(d, nn, _ptr(x_in), _ptr(x_out), stream_handle(stream)))
+
+
+def measure_fma_peak(precision: int, stream=None) -> float:
+    """Measured FMA throughput of the CUDA cores (TFLOP/s): PE_FP64 float64, PE_MIXED float32."""
+    out = C.c_double()
+    _check(lib().pe_measure_fma_peak(precision, C.byref(out), stream_handle(stream)))
+    return out.value
+
+
+def probe_wait_timeout(budget_cycles: int, stream=None) -> None:
+    """Run the tensor-core kernels' bounded wait on a barrier nothing arrives at (raises PEError
+    with status PE_ETIMEOUT when the wait expires, which is what it is for)."""
+    _check(lib().pe_probe_wait_timeout(int(budget_cycles), stream_handle(stream)))
 
 
 class BatchSolver:

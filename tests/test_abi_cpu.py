@@ -93,3 +93,28 @@ def test_python_struct_mirrors_match_the_header(name):
     from paper_2412_01138_gb300 import pe
 
     assert [f for f, _ in getattr(pe, name)._fields_] == _header_struct_fields(name)
+
+
+def test_measurement_calls_reject_bad_arguments_before_device_work(lib):
+    from paper_2412_01138_gb300 import pe
+
+    out = C.c_double()
+    assert lib.pe_measure_fma_peak(7, C.byref(out), None) == pe.PE_EINVAL
+    assert lib.pe_measure_fma_peak(pe.PE_FP64, None, None) == pe.PE_EINVAL
+    for budget in (0, -5, 10**9):
+        assert lib.pe_probe_wait_timeout(budget, None) == pe.PE_EINVAL
+        assert "budget" in lib.pe_last_error().decode()
+
+
+def test_transform_wrappers_check_buffers_before_the_library_sees_them(lib):
+    """Host arrays, a wrong dtype or a buffer shorter than prod(n) never reach the kernels."""
+    import numpy as np
+
+    from paper_2412_01138_gb300 import pe
+
+    host = np.zeros(64)
+    for fn, kw in ((pe.dst, {}), (pe.dst, {"f32": True}), (pe.dst_noalloc, {}), (pe.dst_tc, {})):
+        with pytest.raises(ValueError):
+            fn(2, (8, 8), host, host, **kw)
+    with pytest.raises(ValueError):
+        pe.dst(2, (8,), host, host)  # len(n) != d

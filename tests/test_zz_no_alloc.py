@@ -31,7 +31,9 @@ def _rel(a, b):
 def test_noalloc_matches_allocating_dst_on_two_calls_in_a_row(env):
     pe, torch = env
     rng = np.random.default_rng(12)
-    for n in [(255, 255), (100, 37, 9)]:  # FFT path, then the matrix path
+    # FFT path, matrix path, d = 1 at the largest FFT length, and mixed FFT / matrix axes in
+    # both slot orders (2D and 3D)
+    for n in [(255, 255), (100, 37, 9), (1023,), (63, 100), (100, 63, 31)]:
         x = torch.tensor(rng.standard_normal(int(np.prod(n))), device="cuda", dtype=torch.float64)
         ref = torch.empty_like(x)
         got = torch.empty_like(x)
@@ -47,11 +49,12 @@ def test_noalloc_matches_allocating_dst_on_two_calls_in_a_row(env):
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(env):
+    """The caller's buffers are full size (prod(n) values), so that only the size limit, not a
+    short buffer, is what the call is checked against."""
     pe, torch = env
-    x = torch.zeros(2, device="cuda", dtype=torch.float64)
-    with pytest.raises(pe.PEError) as ei:
-        pe.dst_noalloc(3, (1023, 1023, 3), x, x)
-    assert ei.value.status == pe.PE_EINVAL and "1048576" in str(ei.value)
-    with pytest.raises(pe.PEError) as ei:
-        pe.dst_noalloc(1, (600,), x, x)
-    assert ei.value.status == pe.PE_EINVAL and "512" in str(ei.value)
+    for n, word in (((1023, 1023, 3), "1048576"), ((600,), "512")):
+        x = torch.zeros(int(np.prod(n)), device="cuda", dtype=torch.float64)
+        with pytest.raises(pe.PEError) as ei:
+            pe.dst_noalloc(len(n), n, x, x)
+        assert ei.value.status == pe.PE_EINVAL and word in str(ei.value)
+        del x
