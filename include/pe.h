@@ -125,6 +125,26 @@ typedef struct {
                              j = 0 of an all-periodic problem has lam = 0.  Not with Dirichlet
                              data or the learned correction. */
   int32_t fine_engine;    /* PE_FINE_SIMT (default) | PE_FINE_TC, see above */
+  /* Mode sharding (modes are independent after the diagonalisation of Sec. 2.3; only the
+   * residual of the stopping rule couples them).  mode_begin <= j_0 < mode_end: this context
+   * owns the modes whose index along axis 0 (the slowest axis) lies in that range (0-based),
+   * a contiguous block of the C-ordered modal array; both 0: every mode.  A context that owns
+   * a block: pe_get_modal, pe_get_lambda, pe_get_coefficients, pe_forcing_modal and
+   * pe_save_state hold its (mode_end - mode_begin) * prod_{a>0} n_a modes; nodal u0
+   * (PE_FIELD_NODAL) is the whole grid's; pe_get_solution returns the whole grid's nodal
+   * values of its modes alone (the other modes taken as zero), so that the sum of these
+   * fields over contexts covering every mode once is the nodal solution.  Its residual sums
+   * are its own: pe_parareal_iter_sums returns them, and pe_parareal_iter / pe_solve need
+   * residual_reduce to combine them across contexts (PE_EINVAL otherwise).  Separable forcing
+   * only, no Dirichlet data, u0 nodal or PE_FIELD_TERMS_SEPARABLE. */
+  int32_t mode_begin, mode_end;
+  /* Called by pe_parareal_iter / pe_solve after the correction of every iteration with the
+   * two residual sums of this context (sums[0] = sum mu^M (U_new - U_old)^2, sums[1] =
+   * sum mu^M U_new^2 over its modes and slices); it must replace them by their totals over
+   * every context of the solve (an all-reduce: MPI, NCCL, a host loop) and return.  NULL:
+   * the context's own sums are the totals (the unsharded solve). */
+  void (*residual_reduce)(double* sums, void* user);
+  void* residual_reduce_user;
 } pe_options;
 
 /* Initial data: u0 = sum of separable terms (time factors ignored), projected
@@ -211,6 +231,16 @@ pe_status pe_set_dirichlet(pe_ctx* ctx, int32_t n_terms, const pe_term* g);
  * rel_residual_out: host, may be NULL.  Returns PE_ENONFINITE if a sum is not finite.
  */
 pe_status pe_parareal_iter(pe_ctx* ctx, double* rel_residual_out);
+
+/*
+ * pe_parareal_iter_sums -- the same pass as pe_parareal_iter, returning the two float64
+ * residual sums of this context's modes before any combination or division:
+ * sums_out[0] = sum_{n=1}^N sum_J mu^M_J (U^{n,(k+1)}_J - U^{n,(k)}_J)^2 and
+ * sums_out[1] = sum_{n=1}^N sum_J mu^M_J (U^{n,(k+1)}_J)^2 (host, 2 values).  The relative
+ * residual of a mode-sharded solve is sqrt(sum of sums_out[0]) / sqrt(sum of sums_out[1])
+ * over the contexts.  Returns PE_ENONFINITE if a sum is not finite.
+ */
+pe_status pe_parareal_iter_sums(pe_ctx* ctx, double* sums_out);
 
 /*
  * pe_refine -- one Parareal iteration exactly like pe_parareal_iter but with the

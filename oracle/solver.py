@@ -72,7 +72,8 @@ class ModalSystem:
             if any(quadrature.is_time_dependent(f) for term in prob.forcing for f in term.factors):
                 raise ValueError("time-dependent spatial factors need forcing_route='full'")
             self._P = [self._separable_modal(term) for term in prob.forcing]
-            self.c0 = sum(term.amp * self._separable_modal(term) for term in prob.u0)
+            # u0 = sum of its terms; no terms is the zero function (P_h 0 = 0)
+            self.c0 = np.zeros_like(self.lam) + sum(term.amp * self._separable_modal(term) for term in prob.u0)
         elif forcing_route == "full":
             self._P = None
             F0 = quadrature.load_full(prob.u0, None, n, box, qp, self.periodic)

@@ -128,7 +128,8 @@ void free_ctx(pe_ctx* c) {
                   c->gen_L, c->gen_buf, c->gen_tmp, c->lam, c->coefF, c->coefG,
                   c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
-                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err, c->tcA};
+                  c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err, c->tcA,
+                  c->muM_full, c->ratio_full, c->fac_full, c->work2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -265,6 +266,31 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     return pe_fail(PE_EINVAL,
                    "pe_setup: PE_FINE_TC needs PE_MIXED, PE_FORCING_SEPARABLE and M a multiple of 16 in 16..128");
   }
+  // mode sharding: this context owns the axis-0 modes [mode_begin, mode_end)
+  c->gn = c->g;
+  c->nsum_full = nsum;
+  if (!(o.mode_begin == 0 && o.mode_end == 0) && !(o.mode_begin == 0 && o.mode_end == n[0])) {
+    if (o.mode_begin < 0 || o.mode_end <= o.mode_begin || o.mode_end > n[0]) {
+      delete c;
+      return pe_fail(PE_EINVAL, "pe_setup: mode range must satisfy 0 <= mode_begin < mode_end <= n_0");
+    }
+    if (o.forcing_path != PE_FORCING_SEPARABLE) {
+      delete c;
+      return pe_fail(PE_EINVAL, "pe_setup: a context that owns a block of modes needs PE_FORCING_SEPARABLE");
+    }
+    c->sharded = true;
+    c->base0 = o.mode_begin;
+    c->g.n[0] = o.mode_end - o.mode_begin;
+    c->g.ndof = ndof / n[0] * c->g.n[0];
+    int offl = 0;
+    for (int a = 0; a < d; ++a) {
+      c->g.off[a] = offl;
+      offl += c->g.n[a];
+    }
+    c->nsum = offl;
+  }
+  c->reduce = o.residual_reduce;
+  c->reduce_user = o.residual_reduce_user;
   c->fine_engine = o.fine_engine;
   c->forcing_path = o.forcing_path;
   c->cache_forced = o.cache_forced ? 1 : 0;
@@ -275,11 +301,17 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   c->stream = (cudaStream_t)o.cuda_stream;
 
   const int threads = 256;
-  c->max_blocks = (int)((ndof + threads - 1) / threads) + 1;
-  const size_t N = (size_t)n_slices, nd = (size_t)ndof, MT = PE_MAX_TERMS;
+  // modal arrays hold this context's modes (nd); nodal arrays and per-axis loads the whole grid
+  const size_t N = (size_t)n_slices, nd = (size_t)c->g.ndof, ndn = (size_t)ndof, MT = PE_MAX_TERMS;
+  const int nsl = c->nsum;
+  c->max_blocks = (int)((nd + threads - 1) / threads) + 1;
   st = PE_OK;
-  if (st == PE_OK) st = dev_alloc(&c->muM_axis, nsum);
-  if (st == PE_OK) st = dev_alloc(&c->ratio_axis, nsum);
+  if (st == PE_OK) st = dev_alloc(&c->muM_axis, nsl);
+  if (st == PE_OK) st = dev_alloc(&c->ratio_axis, nsl);
+  if (st == PE_OK && c->sharded) st = dev_alloc(&c->muM_full, nsum);
+  if (st == PE_OK && c->sharded) st = dev_alloc(&c->ratio_full, nsum);
+  if (st == PE_OK && c->sharded) st = dev_alloc(&c->fac_full, MT * nsum);
+  if (st == PE_OK && c->sharded) st = dev_alloc(&c->work2, ndn);
   for (int a = 0; a < d && st == PE_OK; ++a) st = dev_alloc(&c->S[a], (size_t)n[a] * n[a]);
   if (st == PE_OK) st = dev_alloc(&c->lam, nd);
   if (st == PE_OK) st = dev_alloc(&c->coefF, (size_t)(c->q + 2) * nd);
@@ -289,9 +321,9 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->Fbar, N * nd);
   if (st == PE_OK && c->cache_forced) st = dev_alloc(&c->Fz, N * nd);
   if (st == PE_OK) st = dev_alloc(&c->gG, N * nd);
-  if (st == PE_OK) st = dev_alloc(&c->work0, nd + 64);
-  if (st == PE_OK) st = dev_alloc(&c->work1, nd + 64);
-  if (st == PE_OK) st = dev_alloc(&c->out_nodal, nd);
+  if (st == PE_OK) st = dev_alloc(&c->work0, ndn + 64);
+  if (st == PE_OK) st = dev_alloc(&c->work1, ndn + 64);
+  if (st == PE_OK) st = dev_alloc(&c->out_nodal, ndn);
   if (st == PE_OK) st = dev_alloc(&c->partials, 2 * (size_t)c->max_blocks + 64);
   if (st == PE_OK) st = dev_alloc(&c->red, 2);
   if (st == PE_OK) st = dev_alloc(&c->done_ctr, 1);
@@ -303,9 +335,9 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   }
   if (st == PE_OK && cudaMemset(c->done_ctr, 0, sizeof(unsigned int)) != cudaSuccess)
     st = pe_fail(PE_ECUDA, "pe_setup: counter initialisation failed");
-  if (st == PE_OK) st = dev_alloc(&c->axisF, MT * nsum);
-  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->axisF32, MT * nsum);
-  if (st == PE_OK) st = dev_alloc(&c->axisU0, MT * nsum);
+  if (st == PE_OK) st = dev_alloc(&c->axisF, MT * nsl);
+  if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->axisF32, MT * nsl);
+  if (st == PE_OK) st = dev_alloc(&c->axisU0, MT * nsl);
   if (st == PE_OK) st = dev_alloc(&c->loads, MT * nsum);
   if (st == PE_OK) st = dev_alloc(&c->AF, N * n_substeps * 2 * MT);
   if (st == PE_OK && c->precision == PE_MIXED) st = dev_alloc(&c->AF32, N * n_substeps * 2 * MT);
@@ -432,10 +464,38 @@ extern "C" pe_status pe_set_dirichlet(pe_ctx* c, int32_t n_terms, const pe_term*
     return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data need PE_FORCING_SEPARABLE");
   if (n_terms > 0 && (c->g.per[0] || c->g.per[1] || c->g.per[2]))
     return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data with periodic axes");
+  if (n_terms > 0 && c->sharded)
+    return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data in a context that owns a block of modes");
   c->nbd = n_terms;
   for (int i = 0; i < n_terms; ++i) c->bterms[i] = g[i];
   c->have_problem = false;  // the next pe_set_problem / pe_solve takes the data into account
   return PE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// nodal <-> modal for the modes this context owns.  A sharded context owns the axis-0 modes
+// [base0, base0 + g.n[0]): a contiguous block of the whole grid's modal array starting at
+// base0 * (the product of the other axes' sizes).
+// ---------------------------------------------------------------------------
+static int64_t slab_offset(const pe_ctx* c) { return (int64_t)c->base0 * (c->gn.ndof / c->gn.n[0]); }
+
+// modal_out = this context's modes of V^T nodal (nodal: whole grid, device; not work1 / work2)
+static pe_status nodal_to_modal(pe_ctx* c, const double* nodal, double* modal_out) {
+  if (!c->sharded) return dst_nd_f64(c, nodal, modal_out);
+  PE_TRY(dst_nd_f64(c, nodal, c->work2));
+  PE_CUDA_TRY(cudaMemcpyAsync(modal_out, c->work2 + slab_offset(c), sizeof(double) * c->g.ndof,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  return PE_OK;
+}
+
+// nodal_out (whole grid, device; not work1 / work2) = V applied to this context's modes, the
+// other modes taken as zero
+static pe_status modal_to_nodal(pe_ctx* c, const double* modal, double* nodal_out) {
+  if (!c->sharded) return dst_nd_f64(c, modal, nodal_out);
+  PE_CUDA_TRY(cudaMemsetAsync(c->work2, 0, sizeof(double) * c->gn.ndof, c->stream));
+  PE_CUDA_TRY(cudaMemcpyAsync(c->work2 + slab_offset(c), modal, sizeof(double) * c->g.ndof,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  return dst_nd_f64(c, c->work2, nodal_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -451,6 +511,8 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   if (c->nbd > 0 && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: Dirichlet data and the learned correction");
   const bool any_periodic = c->g.per[0] || c->g.per[1] || c->g.per[2];
   if (any_periodic && c->mlp) return pe_fail(PE_EINVAL, "pe_set_problem: periodic axes and the learned correction");
+  if (c->sharded && u0->kind == PE_FIELD_TERMS_QUADRATURE)
+    return pe_fail(PE_EINVAL, "pe_set_problem: a context that owns a block of modes takes nodal or separable u0");
   memset(c->lkind, 0, sizeof(c->lkind));
   c->tc_split_ok = false;
   if (nf == 0 && c->nbd == 0) {
@@ -477,10 +539,10 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     pe_status st = PE_OK;
     if (fork_u0) {
       const bool dev = pe_is_device_ptr(u0->nodal);
-      const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->g.ndof,
+      const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->gn.ndof,
                                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
       if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_set_problem: u0 copy");
-      if (st == PE_OK) st = dst_nd_f64(c, c->work0, U0);
+      if (st == PE_OK) st = nodal_to_modal(c, c->work0, U0);
     }
     if (st == PE_OK && !general) st = launch_time_tables(c);
     c->stream = main_stream;
@@ -515,9 +577,9 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   } else if (u0->kind == PE_FIELD_NODAL) {
     if (!u0->nodal) return pe_fail(PE_EINVAL, "pe_set_problem: nodal u0 is NULL");
     const bool dev = pe_is_device_ptr(u0->nodal);
-    PE_CUDA_TRY(cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->g.ndof,
+    PE_CUDA_TRY(cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->gn.ndof,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    PE_TRY(dst_nd_f64(c, c->work0, U0));
+    PE_TRY(nodal_to_modal(c, c->work0, U0));
   } else {
     return pe_fail(PE_EINVAL, "pe_set_problem: unknown u0 kind");
   }
@@ -547,7 +609,9 @@ extern "C" pe_status pe_set_problem(pe_ctx* c, const pe_field* u0, const pe_forc
   return PE_OK;
 }
 
-static pe_status iter_impl(pe_ctx* c, double* r_out, int precision) {
+// One pass of Algorithm 1's loop.  sums_out (may be NULL): this context's two residual sums;
+// r_out (may be NULL): the relative residual of the totals (after residual_reduce, if any).
+static pe_status iter_impl(pe_ctx* c, double* r_out, int precision, double* sums_out = nullptr) {
   PE_CUDA_TRY(cudaEventRecord(c->ev[5], c->stream));
   if (c->forcing_path == PE_FORCING_GENERAL) PE_TRY(launch_general_fine_sweep(c, precision));
   else PE_TRY(launch_fine_sweep(c, precision));
@@ -557,33 +621,69 @@ static pe_status iter_impl(pe_ctx* c, double* r_out, int precision) {
   c->ms_fine += elapsed(c->ev[5], c->ev[6]);
   c->ms_corr += elapsed(c->ev[6], c->ev[7]);
   c->k += 1;
+  if (sums_out) {
+    sums_out[0] = num;
+    sums_out[1] = den;
+  }
   if (!isfinite(num) || !isfinite(den)) {
     c->have_problem = false;
     if (precision == PE_MIXED && c->fine_engine == PE_FINE_TC) PE_TRY(fine_tc_status(c));
     return pe_fail(PE_ENONFINITE, "Parareal residual is not finite (NaN/Inf in the iterate)");
   }
-  const double r = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
-  if (r_out) *r_out = r;
+  if (r_out) {
+    if (c->reduce) {
+      double tot[2] = {num, den};
+      c->reduce(tot, c->reduce_user);
+      num = tot[0];
+      den = tot[1];
+      if (!isfinite(num) || !isfinite(den))
+        return pe_fail(PE_ENONFINITE, "Parareal residual is not finite after the combination across contexts");
+    }
+    *r_out = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+  }
+  return PE_OK;
+}
+
+static pe_status need_totals(const pe_ctx* c, const char* who) {
+  if (c->sharded && !c->reduce)
+    return pe_fail(PE_EINVAL, std::string(who) + ": a context that owns a block of modes needs "
+                              "pe_options.residual_reduce (or pe_parareal_iter_sums)");
   return PE_OK;
 }
 
 extern "C" pe_status pe_parareal_iter(pe_ctx* c, double* rel_residual_out) {
   if (!c) return pe_fail(PE_EINVAL, "pe_parareal_iter: ctx is NULL");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_parareal_iter: no problem set (call pe_set_problem)");
+  PE_TRY(need_totals(c, "pe_parareal_iter"));
   c->have_output = false;
-  return iter_impl(c, rel_residual_out, c->precision);
+  double r = 0.0;
+  PE_TRY(iter_impl(c, &r, c->precision));
+  if (rel_residual_out) *rel_residual_out = r;
+  return PE_OK;
+}
+
+extern "C" pe_status pe_parareal_iter_sums(pe_ctx* c, double* sums_out) {
+  if (!c || !sums_out) return pe_fail(PE_EINVAL, "pe_parareal_iter_sums: NULL argument");
+  if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_parareal_iter_sums: no problem set (call pe_set_problem)");
+  c->have_output = false;
+  return iter_impl(c, nullptr, c->precision, sums_out);
 }
 
 extern "C" pe_status pe_refine(pe_ctx* c, double* rel_residual_out) {
   if (!c) return pe_fail(PE_EINVAL, "pe_refine: ctx is NULL");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_refine: no problem set (call pe_set_problem)");
+  PE_TRY(need_totals(c, "pe_refine"));
   c->have_output = false;
-  return iter_impl(c, rel_residual_out, PE_FP64);
+  double r = 0.0;
+  PE_TRY(iter_impl(c, &r, PE_FP64));
+  if (rel_residual_out) *rel_residual_out = r;
+  return PE_OK;
 }
 
 extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, pe_result* res) {
   if (!c) return pe_fail(PE_EINVAL, "pe_solve: ctx is NULL");
   if (!(tol >= 0.0)) return pe_fail(PE_EINVAL, "pe_solve: tol must be >= 0");
+  PE_TRY(need_totals(c, "pe_solve"));
   c->have_problem = false;
   c->launches = 0;
   c->ms_fine = 0.0;
@@ -601,7 +701,7 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
     if (r <= tol) break;
   }
   PE_CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
-  PE_TRY(dst_nd_f64(c, c->U + (int64_t)c->N * c->g.ndof, c->out_nodal));
+  PE_TRY(modal_to_nodal(c, c->U + (int64_t)c->N * c->g.ndof, c->out_nodal));
   PE_TRY(add_lift(c, c->t0 + c->T, 1.0, 3, c->out_nodal));
   PE_CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -630,10 +730,10 @@ extern "C" pe_status pe_get_solution(pe_ctx* c, int32_t slice, double* nodal_out
   if (!c) return pe_fail(PE_EINVAL, "pe_get_solution: ctx is NULL");
   if (slice < 0 || slice > c->N) return pe_fail(PE_EINVAL, "pe_get_solution: slice out of range");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_get_solution: no problem set");
-  if (slice == c->N && c->have_output) return copy_out(c, c->out_nodal, nodal_out, c->g.ndof);
-  PE_TRY(dst_nd_f64(c, c->U + (int64_t)slice * c->g.ndof, c->work0));
+  if (slice == c->N && c->have_output) return copy_out(c, c->out_nodal, nodal_out, c->gn.ndof);
+  PE_TRY(modal_to_nodal(c, c->U + (int64_t)slice * c->g.ndof, c->work0));
   PE_TRY(add_lift(c, c->t0 + slice * c->dT, 1.0, 3, c->work0));
-  return copy_out(c, c->work0, nodal_out, c->g.ndof);
+  return copy_out(c, c->work0, nodal_out, c->gn.ndof);
 }
 
 extern "C" pe_status pe_get_modal(pe_ctx* c, int32_t slice, double* modal_out) {
@@ -679,6 +779,7 @@ struct StateHeader {
   int64_t ndof;
   int32_t n[3], periodic_mask;
   double box[6], D, t0, T;
+  int32_t mode_begin, mode_end;  // the axis-0 modes of the state (a sharded context's block)
 };
 const uint64_t kStateMagic = 0x3330353135504550ull;  // "PEP51503"
 
@@ -687,12 +788,14 @@ void fill_header(const pe_ctx* c, StateHeader* h) {
   h->magic = kStateMagic;
   h->d = c->g.d; h->N = c->N; h->k = c->k; h->M = c->M; h->ndof = c->g.ndof;
   for (int a = 0; a < 3; ++a) {
-    h->n[a] = c->g.n[a];
+    h->n[a] = c->gn.n[a];
     h->periodic_mask |= c->g.per[a] << a;
     h->box[2 * a] = c->lo[a];
     h->box[2 * a + 1] = c->hi[a];
   }
   h->D = c->D; h->t0 = c->t0; h->T = c->T;
+  h->mode_begin = c->base0;
+  h->mode_end = c->base0 + c->g.n[0];
 }
 }  // namespace
 

@@ -1341,8 +1341,8 @@ pe_status axis_factors_fused(pe_ctx* c, int R, const double* loads, double* fac,
 }
 
 pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out) {
-  c->launches += c->g.d;
-  return dst_nd<double>(c->g.d, c->g.n, c->S, in, out, c->work1, c->stream, c->g.per);
+  c->launches += c->gn.d;
+  return dst_nd<double>(c->gn.d, c->gn.n, c->S, in, out, c->work1, c->stream, c->gn.per);
 }
 
 extern "C" pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, void* stream) {

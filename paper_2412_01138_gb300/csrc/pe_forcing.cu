@@ -268,11 +268,58 @@ pe_status launch_stage_weights_f64(pe_ctx* c) {
   return PE_OK;
 }
 
+// Rows of the whole-axis per-axis tables (layout of gf) that a sharded context owns, in its
+// own layout (gl): out[R off_l[a] + r n_l[a] + j] = in[R off_f[a] + r n_f[a] + j + base_a],
+// base_0 = the first owned axis-0 mode, base_a = 0 for the other axes.
+__global__ void compact_axis_kernel(Geom gf, Geom gl, int base0, int R, const double* __restrict__ in,
+                                    double* __restrict__ out, float* __restrict__ out32) {
+  const int a = blockIdx.z;
+  const int r = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= gl.d || r >= R || j >= gl.n[a]) return;
+  const int jf = j + (a == 0 ? base0 : 0);
+  const double v = in[(int64_t)R * gf.off[a] + (int64_t)r * gf.n[a] + jf];
+  const int64_t o = (int64_t)R * gl.off[a] + (int64_t)r * gl.n[a] + j;
+  out[o] = v;
+  if (out32) out32[o] = (float)v;
+}
+
+static pe_status separable_factors_whole(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode,
+                                         const signed char (*lk)[PE_MAX_D]);
+
+pe_status compact_axis_tables(pe_ctx* c, int R, const double* in, double* out, float* out32) {
+  int nmax = 1;
+  for (int a = 0; a < c->g.d; ++a) nmax = c->g.n[a] > nmax ? c->g.n[a] : nmax;
+  dim3 grid((nmax + 127) / 128, R, c->g.d);
+  compact_axis_kernel<<<grid, 128, 0, c->stream>>>(c->gn, c->g, c->base0, R, in, out, out32);
+  c->launches += 1;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
 // mode 0: 1D loads only (axis_out gets loads); mode 1: modal factors (S_a F)/mu^M;
 // mode 2: S_a F only (the modal coefficients V^T y of a separable nodal vector y).
 // lk (may be NULL): per-term, per-axis load kinds of the Dirichlet lifting (TermsDev).
+// A sharded context computes the factors of the whole axes and keeps the rows of its modes.
 pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode,
                                    const signed char (*lk)[PE_MAX_D]) {
+  if (!c->sharded) return separable_factors_whole(c, terms, nterms, axis_out, mode, lk);
+  if (nterms == 0) return PE_OK;
+  if (mode != 1) return pe_fail(PE_EINVAL, "a context that owns a block of modes takes separable modal factors only");
+  const Geom gl = c->g;
+  double* mu_l = c->muM_axis;
+  c->g = c->gn;
+  c->muM_axis = c->muM_full;
+  const pe_status st = separable_factors_whole(c, terms, nterms, c->fac_full, 1, lk);
+  c->g = gl;
+  c->muM_axis = mu_l;
+  PE_TRY(st);
+  const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
+  return compact_axis_tables(c, nterms, c->fac_full, axis_out, f32 ? c->axisF32 : nullptr);
+}
+
+static pe_status separable_factors_whole(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode,
+                                         const signed char (*lk)[PE_MAX_D]) {
   if (nterms == 0) return PE_OK;
   TermsDev T = pack_terms(terms, nterms, lk);
   Gauss G = make_gauss(c->quad_pts);

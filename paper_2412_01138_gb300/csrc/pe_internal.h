@@ -66,13 +66,25 @@ struct StageCols {
 };
 struct pe_ctx {
   // problem
-  Geom g;
+  Geom g;    // the modes this context owns (every mode unless it owns a block of axis-0 modes)
+  Geom gn;   // the whole grid (nodal arrays, DST-I passes, per-axis loads); equals g unsharded
+  bool sharded = false;  // owns the axis-0 modes [base0, base0 + g.n[0]) of gn.n[0]
+  int base0 = 0;
   double lo[PE_MAX_D], hi[PE_MAX_D], h[PE_MAX_D];
   double D, t0, T, dT, dt;
   int N, M, q, p;
   double cF[PE_MAX_S], cG[PE_MAX_S];
   double lagF[PE_MAX_S][PE_MAX_S], lagG[PE_MAX_S][PE_MAX_S];  // Lagrange monomial coefficients
-  int nsum;  // sum_a n_a
+  int nsum;       // sum_a n_a of g (per-axis modal tables)
+  int nsum_full;  // sum_a n_a of gn (per-axis nodal loads)
+  // a sharded context: per-axis tables of the whole axes (compacted into the tables above),
+  // and a whole-grid buffer for its nodal transforms
+  double* muM_full = nullptr;   // [nsum_full]
+  double* ratio_full = nullptr; // [nsum_full]
+  double* fac_full = nullptr;   // [PE_MAX_TERMS * nsum_full]
+  double* work2 = nullptr;      // [gn.ndof]
+  void (*reduce)(double*, void*) = nullptr;  // residual sums across contexts (pe_options.residual_reduce)
+  void* reduce_user = nullptr;
   // options
   int precision, dst_backend, quad_pts, max_iter, forcing_path, cache_forced;
   int fine_engine = 0;  // PE_FINE_SIMT | PE_FINE_TC
@@ -96,9 +108,9 @@ struct pe_ctx {
   int64_t sweeps = 0;           // fine sweeps executed since the last reset
   double* Fbar = nullptr;       // [N * ndof]
   double* gG = nullptr;         // [N * ndof] coarse forcing of each slice
-  double* work0 = nullptr;      // [ndof] nodal / DST scratch
-  double* work1 = nullptr;      // [ndof]
-  double* out_nodal = nullptr;  // [ndof] inverse DST of U^N after pe_solve
+  double* work0 = nullptr;      // [gn.ndof] nodal / DST scratch
+  double* work1 = nullptr;      // [gn.ndof]
+  double* out_nodal = nullptr;  // [gn.ndof] inverse DST of U^N after pe_solve
   double* partials = nullptr;   // [2 * max_blocks]
   double* red = nullptr;        // [2] device
   unsigned int* done_ctr = nullptr;  // correction: CTAs finished (0 between launches)
@@ -132,7 +144,7 @@ struct pe_ctx {
   bool Wst_valid = false;       // Wst holds the current problem's float64 weights
   double* AG = nullptr;         // [N*p*PE_MAX_TERMS]
   float* AG32 = nullptr;
-  double* loads = nullptr;      // [PE_MAX_TERMS * nsum] 1D loads before the DST
+  double* loads = nullptr;      // [PE_MAX_TERMS * nsum_full] 1D loads before the DST
   // learned coarse correction (optional)
   const struct pe_mlp* mlp = nullptr;
   double* Ktab = nullptr;       // [PE_MAX_TERMS][bands][2]
@@ -175,6 +187,8 @@ pe_status build_dst_matrix_f32(int n, float* S, cudaStream_t st, int periodic = 
 pe_status launch_time_tables(pe_ctx* c);   // also sets c->K, c->cols and Zst
 pe_status launch_stage_weights(pe_ctx* c);  // Wst (float64 form) or Wst32 (mixed form)
 pe_status launch_stage_weights_f64(pe_ctx* c);  // Wst, if not yet made for this problem
+// rows of whole-axis per-axis tables [R * nsum_full] kept by a sharded context, in its layout
+pe_status compact_axis_tables(pe_ctx* c, int R, const double* in, double* out, float* out32);
 pe_status launch_separable_factors(pe_ctx* c, const pe_term* terms, int nterms, double* axis_out, int mode,
                                    const signed char (*lk)[PE_MAX_D] = nullptr);
 pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* terms, int nterms, double* out,
@@ -187,7 +201,7 @@ pe_status dst_axis_f64(const double* S, const double* in, double* out, int64_t o
                        cudaStream_t st, int periodic = 0);
 pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t outer, int n, int64_t inner,
                        cudaStream_t st, int periodic = 0);
-pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);  // uses c->S, c->work1
+pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);  // whole grid (c->gn); uses c->S, c->work1
 // Per-axis source factors of every axis in one launch (loads -> DST-I -> / mu^M); *done = false when
 // an axis is periodic or n_a + 1 is not a power of two in 16..1024 (nothing launched then).
 pe_status axis_factors_fused(pe_ctx* c, int R, const double* loads, double* fac, float* fac32, bool* done);

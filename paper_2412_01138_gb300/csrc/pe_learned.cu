@@ -532,8 +532,8 @@ pe_status launch_learned_tables(pe_ctx* c, LearnedTerms* L) {
   }
   // band range: the closed-form extremes of lam on this grid (slowest and fastest mode)
   double lmin = 0.0, lmax = 0.0;
-  for (int a = 0; a < c->g.d; ++a) {
-    const int n = c->g.n[a];
+  for (int a = 0; a < c->gn.d; ++a) {
+    const int n = c->gn.n[a];
     auto ratio = [&](int j) {
       const double th = M_PI * (double)j / (double)(n + 1);
       const double sh = sin(0.5 * th);

@@ -103,14 +103,22 @@ __global__ void dst_matrix_kernel(int n, double* S, int periodic) {
 
 }  // namespace
 
+// Per-axis eigenvalue tables of the modes this context owns (a sharded context: the whole
+// axes first, then its rows).
 pe_status launch_axis_tables(pe_ctx* c) {
   int nmax = 1;
-  for (int a = 0; a < c->g.d; ++a) nmax = c->g.n[a] > nmax ? c->g.n[a] : nmax;
-  dim3 grid((nmax + 127) / 128, c->g.d);
-  axis_tables_kernel<<<grid, 128, 0, c->stream>>>(c->g, c->h[0], c->g.d > 1 ? c->h[1] : 1.0,
-                                                  c->g.d > 2 ? c->h[2] : 1.0, c->muM_axis, c->ratio_axis);
+  for (int a = 0; a < c->gn.d; ++a) nmax = c->gn.n[a] > nmax ? c->gn.n[a] : nmax;
+  dim3 grid((nmax + 127) / 128, c->gn.d);
+  double* mu = c->sharded ? c->muM_full : c->muM_axis;
+  double* ratio = c->sharded ? c->ratio_full : c->ratio_axis;
+  axis_tables_kernel<<<grid, 128, 0, c->stream>>>(c->gn, c->h[0], c->gn.d > 1 ? c->h[1] : 1.0,
+                                                  c->gn.d > 2 ? c->h[2] : 1.0, mu, ratio);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
+  if (c->sharded) {
+    PE_TRY(compact_axis_tables(c, 1, c->muM_full, c->muM_axis, nullptr));
+    PE_TRY(compact_axis_tables(c, 1, c->ratio_full, c->ratio_axis, nullptr));
+  }
   return PE_OK;
 }
 

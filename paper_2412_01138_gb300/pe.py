@@ -38,7 +38,7 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_batch_destroy", "pe_mlp_create", "pe_mlp_num_params", "pe_mlp_train", "pe_mlp_gradient",
             "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
             "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc", "pe_set_dirichlet", "pe_measure_fma_peak",
-            "pe_probe_wait_timeout")
+            "pe_probe_wait_timeout", "pe_parareal_iter_sums")
 
 
 class PEError(RuntimeError):
@@ -58,10 +58,16 @@ class pe_tableau(C.Structure):
     _fields_ = [("s", C.c_int32), ("c", C.POINTER(C.c_double)), ("random", C.c_int32), ("seed", C.c_uint64)]
 
 
+#: residual_reduce callback of pe_options: void (*)(double* sums, void* user)
+REDUCE_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_void_p)
+
+
 class pe_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("dst_backend", C.c_int32), ("quad_pts", C.c_int32),
                 ("max_iter", C.c_int32), ("cuda_stream", C.c_void_p), ("forcing_path", C.c_int32),
-                ("cache_forced", C.c_int32), ("periodic_mask", C.c_int32), ("fine_engine", C.c_int32)]
+                ("cache_forced", C.c_int32), ("periodic_mask", C.c_int32), ("fine_engine", C.c_int32),
+                ("mode_begin", C.c_int32), ("mode_end", C.c_int32), ("residual_reduce", REDUCE_FN),
+                ("residual_reduce_user", C.c_void_p)]
 
 
 class pe_field(C.Structure):
@@ -104,6 +110,7 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
                                C.POINTER(pe_tableau), C.POINTER(pe_options)]),
         "pe_set_problem": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing)]),
         "pe_parareal_iter": (C.c_int, [P, C.POINTER(C.c_double)]),
+        "pe_parareal_iter_sums": (C.c_int, [P, C.POINTER(C.c_double)]),
         "pe_refine": (C.c_int, [P, C.POINTER(C.c_double)]),
         "pe_solve": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing), C.c_double, C.POINTER(pe_result)]),
         "pe_get_solution": (C.c_int, [P, C.c_int32, P]),
@@ -202,9 +209,22 @@ class Solver:
 
     def __init__(self, prob: "_in.Problem", precision: int = PE_FP64, stream=None, max_iter: int = 0,
                  random_coarse_seed: Optional[int] = None, forcing_path: int = PE_FORCING_SEPARABLE,
-                 dst_backend: int = PE_DST_AUTO, cache_forced: bool = False, fine_engine: int = PE_FINE_SIMT):
+                 dst_backend: int = PE_DST_AUTO, cache_forced: bool = False, fine_engine: int = PE_FINE_SIMT,
+                 mode_range: Optional[Sequence[int]] = None, residual_reduce=None):
+        """mode_range = (begin, end): own only the modes with axis-0 index in [begin, end) (a shard of
+        a mode-sharded solve); residual_reduce(sums) -> totals: combines the two residual sums of
+        this context with those of the other shards (pe_options.residual_reduce)."""
         self.prob = prob
         self._lib = lib()
+        b, e = mode_range if mode_range is not None else (0, 0)
+        self.mode_range = (b, e) if mode_range is not None else (0, prob.n[0])
+        self.ndof_local = prob.ndof // prob.n[0] * (self.mode_range[1] - self.mode_range[0])
+        self._reduce = None
+        if residual_reduce is not None:
+            def _cb(sums, _user, fn=residual_reduce):
+                tot = fn(np.array([sums[0], sums[1]]))
+                sums[0], sums[1] = float(tot[0]), float(tot[1])
+            self._reduce = REDUCE_FN(_cb)
         n = (C.c_int32 * prob.d)(*prob.n)
         box = (C.c_double * (2 * prob.d))(*[v for lohi in prob.box for v in lohi])
         self._cF = (C.c_double * prob.q)(*prob.fine_nodes)
@@ -216,7 +236,8 @@ class Solver:
             coarse = pe_tableau(prob.p, None, 1, random_coarse_seed)
         mask = sum(1 << a for a, p in enumerate(getattr(prob, "periodic", ())) if p)
         opt = pe_options(precision, dst_backend, prob.quad_pts, max_iter, stream_handle(stream), forcing_path,
-                         1 if cache_forced else 0, mask, fine_engine)
+                         1 if cache_forced else 0, mask, fine_engine, b, e,
+                         self._reduce if self._reduce is not None else REDUCE_FN(), None)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup(C.byref(ctx), prob.d, n, box, prob.D, prob.t0, prob.T, prob.N, prob.M,
                                   C.byref(fine), C.byref(coarse), C.byref(opt)))
@@ -276,6 +297,12 @@ class Solver:
         _check(self._lib.pe_parareal_iter(self.ctx, C.byref(r)))
         return r.value
 
+    def iterate_sums(self) -> np.ndarray:
+        """One Parareal iteration; this context's residual sums (sum mu (dU)^2, sum mu U^2)."""
+        out = (C.c_double * 2)()
+        _check(self._lib.pe_parareal_iter_sums(self.ctx, out))
+        return np.array([out[0], out[1]])
+
     def refine(self) -> float:
         """One float64 Parareal iteration (float64 refinement of a mixed-precision iterate)."""
         r = C.c_double()
@@ -306,28 +333,29 @@ class Solver:
         return np.empty(count, dtype=np.float64) if out is None else out
 
     def solution(self, slice_: int, out=None):
+        """Nodal values of the whole grid (a shard: of its modes alone)."""
         out = self._out(self.prob.ndof, out)
         _check(self._lib.pe_get_solution(self.ctx, slice_, _ptr(out)))
         return out
 
     def modal(self, slice_: int, out=None):
-        out = self._out(self.prob.ndof, out)
+        out = self._out(self.ndof_local, out)
         _check(self._lib.pe_get_modal(self.ctx, slice_, _ptr(out)))
         return out
 
     def lam(self, out=None):
-        out = self._out(self.prob.ndof, out)
+        out = self._out(self.ndof_local, out)
         _check(self._lib.pe_get_lambda(self.ctx, _ptr(out)))
         return out
 
     def coefficients(self, which: int, out=None):
         s = self.prob.q if which == 0 else self.prob.p
-        out = self._out((s + 1) * self.prob.ndof, out)
+        out = self._out((s + 1) * self.ndof_local, out)
         _check(self._lib.pe_get_coefficients(self.ctx, which, _ptr(out)))
-        return out.reshape(s + 1, self.prob.ndof) if isinstance(out, np.ndarray) else out
+        return out.reshape(s + 1, self.ndof_local) if isinstance(out, np.ndarray) else out
 
     def forcing_modal(self, t: float, out=None):
-        out = self._out(self.prob.ndof, out)
+        out = self._out(self.ndof_local, out)
         _check(self._lib.pe_forcing_modal(self.ctx, t, _ptr(out)))
         return out
 
@@ -441,7 +469,7 @@ class BatchSolver:
             q.u0 = pe_field(PE_FIELD_TERMS_SEPARABLE, len(p.u0), C.cast(tu, C.POINTER(pe_term)), None)
             q.forcing = pe_forcing(len(p.forcing), C.cast(tf, C.POINTER(pe_term)))
         opt = pe_options(precision, PE_DST_AUTO, self.probs[0].quad_pts, 0, stream_handle(stream),
-                         PE_FORCING_SEPARABLE)
+                         PE_FORCING_SEPARABLE, 0, 0, PE_FINE_SIMT, 0, 0, REDUCE_FN(), None)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup_batch(C.byref(ctx), len(self.probs), arr, C.byref(opt)))
         self.ctx = ctx

@@ -82,8 +82,14 @@ def _header_struct_fields(name):
     fields = []
     for decl in m.group(1).split(";"):
         decl = decl.strip()
-        if decl:
-            fields.append(re.search(r"(\w+)\s*(\[[^\]]*\])*\s*$", decl).group(1))
+        if not decl:
+            continue
+        fp = re.search(r"\(\s*\*\s*(\w+)\s*\)\s*\(", decl)  # function pointer: ret (*name)(args)
+        if fp:
+            fields.append(fp.group(1))
+            continue
+        for part in decl.split(","):  # "int32_t a, b" declares a and b
+            fields.append(re.search(r"(\w+)\s*(\[[^\]]*\])*\s*$", part.strip()).group(1))
     return fields
 
 

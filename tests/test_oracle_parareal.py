@@ -126,3 +126,19 @@ def test_mode_subset_equals_full_run():
     a = solver.parareal(full, tol=0.0, k_max=2).U[-1][idx]
     b = solver.parareal(sub, tol=0.0, k_max=2).U[-1]
     np.testing.assert_allclose(b, a, rtol=1e-15, atol=0)
+
+
+def test_zero_initial_data_is_the_zero_function():
+    """No u0 terms means u0 = 0: the oracle's U^0 is the zero vector of the right length, and the
+    solve is driven by the source alone (the coarse sweep of a zero state under zero forcing is zero)."""
+    import numpy as np
+
+    from oracle import solver as osolver
+    from paper_2412_01138_gb300 import inputs as I
+
+    box = ((0.0, 1.0),)
+    prob = I.Problem(1, (15,), box, 0.5, 0.0, 1.0, 3, 2, I.uniform_nodes(2), I.uniform_nodes(2), (), (), 3, 1e-12)
+    sys_ = osolver.ModalSystem(prob)
+    assert isinstance(sys_.c0, np.ndarray) and sys_.c0.shape == (15,) and not sys_.c0.any()
+    ref = osolver.parareal(sys_, tol=0.0, k_max=1)
+    assert all(not u.any() for u in ref.U)
