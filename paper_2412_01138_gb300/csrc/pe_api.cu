@@ -129,7 +129,7 @@ void free_ctx(pe_ctx* c) {
                   c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
                   c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err, c->tcA,
-                  c->muM_full, c->ratio_full, c->fac_full, c->work2};
+                  c->muM_full, c->ratio_full, c->fac_full, c->work2, c->tcYr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -304,7 +304,8 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   // modal arrays hold this context's modes (nd); nodal arrays and per-axis loads the whole grid
   const size_t N = (size_t)n_slices, nd = (size_t)c->g.ndof, ndn = (size_t)ndof, MT = PE_MAX_TERMS;
   const int nsl = c->nsum;
-  c->max_blocks = (int)((nd + threads - 1) / threads) + 1;
+  // CTAs of the correction kernel: at least 8 modes per CTA (32 slice chunks of one mode)
+  c->max_blocks = (int)((nd + 7) / 8) + 1;
   st = PE_OK;
   if (st == PE_OK) st = dev_alloc(&c->muM_axis, nsl);
   if (st == PE_OK) st = dev_alloc(&c->ratio_axis, nsl);
@@ -329,6 +330,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->done_ctr, 1);
   if (st == PE_OK && c->fine_engine == PE_FINE_TC) {
     st = dev_alloc(&c->tcB, fine_tc_buffer_bytes(n_substeps, n_slices));
+    if (st == PE_OK) st = dev_alloc(&c->tcYr, (size_t)2 * n_slices * n_substeps);
     if (st == PE_OK) st = dev_alloc(&c->tc_err, 1);
     if (st == PE_OK && cudaMemset(c->tc_err, 0, sizeof(int)) != cudaSuccess)
       st = pe_fail(PE_ECUDA, "pe_setup: error flag initialisation failed");

@@ -116,6 +116,7 @@ struct pe_ctx {
   unsigned int* done_ctr = nullptr;  // correction: CTAs finished (0 between launches)
   unsigned char* tcB = nullptr;  // tensor-core fine engine: split time factors of every slice group
   unsigned char* tcA = nullptr;  // tensor-core fine engine: split stage weights of every mode tile
+  float* tcYr = nullptr;         // tensor-core fine engine: time factors of its CUDA-core columns [2][N*M]
   size_t tcA_cap = 0;            // bytes allocated in tcA
   bool tc_split_ok = false;      // tcA / tcB hold the current problem's split operands
   int* tc_err = nullptr;         // tensor-core fine engine: error code of an expired wait (0: none)
