@@ -43,10 +43,13 @@ TOL = 1e-6
 L2_BYTES = 129 * 1024 * 1024
 
 
-def engine(pe, prec):
-    """Fine-sweep engine of a separable-path solve: the tensor cores for the mixed form (the
-    chosen form), the float64 SIMT kernel otherwise."""
-    return pe.PE_FINE_TC if prec == pe.PE_MIXED else pe.PE_FINE_SIMT
+def chosen_kw(pe, prec):
+    """Solver options of a separable-path solve: the mixed form (the chosen form) runs its stage
+    contraction on the tensor cores and its Parareal loop on the device; float64 is the plain
+    form (SIMT kernel, host-driven loop of Algorithm 1)."""
+    if prec == pe.PE_MIXED:
+        return {"fine_engine": pe.PE_FINE_TC, "device_loop": 1}
+    return {"fine_engine": pe.PE_FINE_SIMT}
 
 
 def workload():
@@ -297,10 +300,10 @@ def run_config1(pe, args, barrier):
     prob = I.config1()
     sys_ = osolver.ModalSystem(prob)
     out = {"workload": prob.label}
-    for name, prec, eng, tol in (("fp64_tol1e-12", pe.PE_FP64, pe.PE_FINE_SIMT, 1e-12),
-                                 ("fp64", pe.PE_FP64, pe.PE_FINE_SIMT, TOL),
-                                 ("chosen", pe.PE_MIXED, pe.PE_FINE_TC, TOL)):
-        with pe.Solver(prob, precision=prec, fine_engine=eng) as s:
+    for name, prec, eng, tol, dl in (("fp64_tol1e-12", pe.PE_FP64, pe.PE_FINE_SIMT, 1e-12, 0),
+                                     ("fp64", pe.PE_FP64, pe.PE_FINE_SIMT, TOL, 0),
+                                     ("chosen", pe.PE_MIXED, pe.PE_FINE_TC, TOL, 1)):
+        with pe.Solver(prob, precision=prec, fine_engine=eng, device_loop=dl) as s:
             for _ in range(max(3, args.warmup)):
                 s.solve(tol=tol)
             barrier()
@@ -330,7 +333,7 @@ def run_learned(pe, args, barrier):
     prob = I.config5(seed=1)
     dev = torch.device("cuda")
     out = {"workload": prob.label}
-    with pe.Solver(prob, precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC) as s:
+    with pe.Solver(prob, precision=pe.PE_MIXED, **chosen_kw(pe, pe.PE_MIXED)) as s:
         lam = s.lam()
         lo, hi = np.log(lam.min()), np.log(lam.max())
         rng = np.random.default_rng(2024)
@@ -407,7 +410,7 @@ def run_precision(pe, args, barrier):
         return float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) / np.sqrt(np.sum(w * ref.U[-1] ** 2)))
 
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, fine_engine=engine(pe, prec)) as s:
+        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec)) as s:
             s.solve(tol=TOL)
             barrier()
             t0 = time.perf_counter()
@@ -439,7 +442,7 @@ def run_cached(pe, args, barrier, u0_dev, u0_host):
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=17, u0_nodal=u0_host)
     w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, cache_forced=True, fine_engine=engine(pe, prec)) as s:
+        with pe.Solver(prob, precision=prec, cache_forced=True, **chosen_kw(pe, prec)) as s:
             for _ in range(max(1, args.warmup)):
                 s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
             barrier()
@@ -474,7 +477,7 @@ def run_dirichlet(pe, args, barrier):
     prob = dirichlet_problem()
     out = {"workload": prob.label}
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, fine_engine=engine(pe, prec)) as s:
+        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec)) as s:
             for _ in range(max(1, args.warmup)):
                 s.solve(tol=TOL)
             barrier()
@@ -504,7 +507,7 @@ def run_periodic(pe, args, barrier):
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=19)
     w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, fine_engine=engine(pe, prec)) as s:
+        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec)) as s:
             for _ in range(max(1, args.warmup)):
                 s.solve(tol=TOL)
             barrier()
@@ -817,10 +820,10 @@ def main():
                     "fp32_tflops": pe.measure_fma_peak(pe.PE_MIXED, stream)}
     results = {}
     with ClockSampler(local if world > 1 else 0) as clocks:
-        for name, precision, eng in (("fp64", pe.PE_FP64, pe.PE_FINE_SIMT),
-                                        ("mixed_simt", pe.PE_MIXED, pe.PE_FINE_SIMT),
-                                        ("mixed", pe.PE_MIXED, pe.PE_FINE_TC)):
-            with pe.Solver(prob, precision=precision, stream=stream, fine_engine=eng) as s:
+        for name, precision, eng, dl in (("fp64", pe.PE_FP64, pe.PE_FINE_SIMT, 0),
+                                         ("mixed_simt", pe.PE_MIXED, pe.PE_FINE_SIMT, 0),
+                                         ("mixed", pe.PE_MIXED, pe.PE_FINE_TC, 1)):
+            with pe.Solver(prob, precision=precision, stream=stream, fine_engine=eng, device_loop=dl) as s:
                 total_ms, infos = timed_steps(s, args.steps, args.warmup, u0_dev)
                 modal = s.modal(prob.N)
                 # end to end through the C-ABI with host buffers: H2D of u0, D2H of the solution
@@ -833,6 +836,11 @@ def main():
                     s.solution(prob.N, out=out_host)
                 e2e_s = time.perf_counter() - t0
             results[name] = dict(total_ms=total_ms, infos=infos, modal=modal, e2e_s=e2e_s)
+        # per-kernel device times of the chosen form's kernels (its device-resident loop does not
+        # time kernels one by one): the same solve with the host-driven loop
+        with pe.Solver(prob, precision=pe.PE_MIXED, stream=stream, fine_engine=pe.PE_FINE_TC) as s:
+            _, kinfos = timed_steps(s, args.steps, args.warmup, u0_dev)
+        results["mixed"]["kernel_infos"] = kinfos
         batch = None if args.no_batch else run_batch(pe, args, barrier)
         learned = None if args.no_learned else run_learned(pe, args, barrier)
         general = None if args.no_general else run_general(pe, args, barrier, u0_dev, u0_host)
@@ -857,14 +865,16 @@ def main():
 
     def summarize(r):
         k = r["infos"][-1]["k"]
+        kin = r.get("kernel_infos", r["infos"])
         units = prob.ndof * prob.N * prob.M * sum(i["fine_sweeps"] for i in r["infos"])
         value = replica_throughput(units, r["total_ms"], world)
         e2e_units = prob.ndof * prob.N * prob.M * k * args.steps * world
-        ms_fine = np.mean([i["ms_fine_kernel"] / max(i["fine_sweeps"], 1) for i in r["infos"]])
+        ms_fine = np.mean([i["ms_fine_kernel"] / max(i["fine_sweeps"], 1) for i in kin])
         phases = {key: float(np.mean([i[key] for i in r["infos"]]))
-                  for key in ("ms_tables", "ms_prepare", "ms_iterations", "ms_output", "ms_fine_kernel",
-                              "ms_correction_kernel", "ms_coarse_kernel")}
-        ms_corr = np.mean([i["ms_correction_kernel"] / max(i["k"], 1) for i in r["infos"]])
+                  for key in ("ms_tables", "ms_prepare", "ms_iterations", "ms_output", "ms_coarse_kernel")}
+        for key in ("ms_fine_kernel", "ms_correction_kernel"):
+            phases[key] = float(np.mean([i[key] for i in kin]))
+        ms_corr = np.mean([i["ms_correction_kernel"] / max(i["k"], 1) for i in kin])
         return dict(value=value, k=k, ms_per_step=r["total_ms"] / args.steps, e2e=e2e_units / r["e2e_s"],
                     ms_fine_launch=ms_fine, ms_corr_launch=float(ms_corr),
                     ms_coarse=phases["ms_coarse_kernel"], launches=r["infos"][-1]["kernel_launches"],
@@ -931,7 +941,8 @@ def main():
         "rel_l2_vs_oracle": err_plain,
         "chosen": {"form": "mixed: stage contraction on the tensor cores (tcgen05, three-term bfloat16 split, "
                            "six products, float32 accumulators), float32 recurrence (hi/lo E), float64 tables, "
-                           "correction, residual",
+                           "correction, residual; Parareal loop on the device (one CUDA graph with a conditional "
+                           "while node; kernel times from the same solve with the host-driven loop)",
                    "value": chosen["value"], "unit": UNIT, "time_to_tol_ms": chosen["ms_per_step"],
                    "iterations": chosen["k"], "rel_l2_vs_oracle": err_chosen, "dtype": "f32",
                    "speedup_time_to_tol": plain["ms_per_step"] / chosen["ms_per_step"],

@@ -145,6 +145,15 @@ typedef struct {
    * the context's own sums are the totals (the unsharded solve). */
   void (*residual_reduce)(double* sums, void* user);
   void* residual_reduce_user;
+  /* 1: pe_solve runs Algorithm 1's loop on the device -- one CUDA graph whose conditional
+   * (while) node repeats {fine sweep, correction + residual} and whose correction kernel
+   * decides, from the float64 residual, whether to go on (r > tol and k < max_iter) -- so the
+   * host waits once per solve instead of once per iteration.  Same kernels and results as the
+   * host-driven loop; per-kernel times (pe_result.ms_fine_kernel, ms_correction_kernel) are not
+   * measured in this mode (0).  The graph is built at the first such solve of a column count K
+   * and reused.  Falls back to the host loop for cache_forced, the general forcing path and
+   * contexts with residual_reduce.  0 (default): the host-driven loop of the paper's Algorithm 1. */
+  int32_t device_loop;
 } pe_options;
 
 /* Initial data: u0 = sum of separable terms (time factors ignored), projected

@@ -129,10 +129,12 @@ void free_ctx(pe_ctx* c) {
                   c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
                   c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err, c->tcA,
-                  c->muM_full, c->ratio_full, c->fac_full, c->work2, c->tcYr};
+                  c->muM_full, c->ratio_full, c->fac_full, c->work2, c->loopctl, c->loop_hist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->h_loop) cudaFreeHost(c->h_loop);
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
   for (int i = 0; i < PE_NEV; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -291,6 +293,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   }
   c->reduce = o.residual_reduce;
   c->reduce_user = o.residual_reduce_user;
+  c->device_loop = o.device_loop ? 1 : 0;
   c->fine_engine = o.fine_engine;
   c->forcing_path = o.forcing_path;
   c->cache_forced = o.cache_forced ? 1 : 0;
@@ -304,8 +307,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   // modal arrays hold this context's modes (nd); nodal arrays and per-axis loads the whole grid
   const size_t N = (size_t)n_slices, nd = (size_t)c->g.ndof, ndn = (size_t)ndof, MT = PE_MAX_TERMS;
   const int nsl = c->nsum;
-  // CTAs of the correction kernel: at least 8 modes per CTA (32 slice chunks of one mode)
-  c->max_blocks = (int)((nd + 7) / 8) + 1;
+  c->max_blocks = (int)((nd + threads - 1) / threads) + 1;
   st = PE_OK;
   if (st == PE_OK) st = dev_alloc(&c->muM_axis, nsl);
   if (st == PE_OK) st = dev_alloc(&c->ratio_axis, nsl);
@@ -330,7 +332,6 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->done_ctr, 1);
   if (st == PE_OK && c->fine_engine == PE_FINE_TC) {
     st = dev_alloc(&c->tcB, fine_tc_buffer_bytes(n_substeps, n_slices));
-    if (st == PE_OK) st = dev_alloc(&c->tcYr, (size_t)2 * n_slices * n_substeps);
     if (st == PE_OK) st = dev_alloc(&c->tc_err, 1);
     if (st == PE_OK && cudaMemset(c->tc_err, 0, sizeof(int)) != cudaSuccess)
       st = pe_fail(PE_ECUDA, "pe_setup: error flag initialisation failed");
@@ -362,6 +363,14 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK && cudaMallocHost((void**)&c->h_red, 4 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");
+  }
+  if (st == PE_OK && c->device_loop) {
+    st = dev_alloc(&c->loopctl, 1);
+    if (st == PE_OK) st = dev_alloc(&c->loop_hist, N);
+    if (st == PE_OK && cudaMallocHost((void**)&c->h_loop, sizeof(LoopCtl)) != cudaSuccess) {
+      cudaGetLastError();
+      st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");
+    }
   }
   for (int i = 0; i < PE_NEV && st == PE_OK; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = pe_cuda_fail(cudaGetLastError(), "cudaEventCreate");
@@ -682,6 +691,107 @@ extern "C" pe_status pe_refine(pe_ctx* c, double* rel_residual_out) {
   return PE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// device-resident Parareal loop: a CUDA graph with one conditional (while) node whose body is
+// one pass of Algorithm 1's loop -- the fine sweep from every slice and the correction, whose
+// last CTA appends r_k, advances k and sets the condition (r > tol and k < max_iter)
+// ---------------------------------------------------------------------------
+static bool loop_on_device(const pe_ctx* c) {
+  return c->device_loop && !c->cache_forced && c->forcing_path == PE_FORCING_SEPARABLE && !c->reduce &&
+         !c->sharded;
+}
+
+static pe_status build_loop_graph(pe_ctx* c) {
+  if (c->loop_exec && c->loop_K == c->K && c->loop_prec == c->precision) return PE_OK;
+  if (c->loop_exec) {
+    PE_CUDA_TRY(cudaGraphExecDestroy(c->loop_exec));
+    c->loop_exec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  PE_CUDA_TRY(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle handle;
+  pe_status st = PE_OK;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np{};
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return pe_cuda_fail(e, "device loop: conditional node");
+  }
+  // the body: the launches of one iteration, captured on the side stream (the context's own
+  // stream may be the legacy default stream, which cannot be captured)
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t main_stream = c->stream;
+  const int64_t launches0 = c->launches, sweeps0 = c->sweeps;
+  e = cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    c->stream = c->side;
+    st = launch_fine_sweep(c, c->precision);
+    if (st == PE_OK) st = launch_correction_kernel(c, c->loopctl, (unsigned long long)handle);
+    c->stream = main_stream;
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->side, &captured);
+    if (st == PE_OK && e2 != cudaSuccess) st = pe_cuda_fail(e2, "device loop: capture");
+  } else {
+    st = pe_cuda_fail(e, "device loop: begin capture");
+  }
+  c->loop_body_launches = c->launches - launches0;
+  c->launches = launches0;
+  c->sweeps = sweeps0;
+  if (st == PE_OK) {
+    e = cudaGraphInstantiate(&c->loop_exec, graph, 0);
+    if (e != cudaSuccess) st = pe_cuda_fail(e, "device loop: instantiate");
+  }
+  cudaGraphDestroy(graph);
+  if (st != PE_OK) {
+    cudaGetLastError();
+    c->loop_exec = nullptr;
+    return st;
+  }
+  c->loop_K = c->K;
+  c->loop_prec = c->precision;
+  return PE_OK;
+}
+
+// Iterations of pe_solve on the device: returns the last residual in *r and fills the history.
+static pe_status solve_loop_on_device(pe_ctx* c, double tol, pe_result* res, double* r) {
+  PE_TRY(build_loop_graph(c));
+  LoopCtl* h = c->h_loop;
+  h->k = 0;
+  h->max_iter = c->max_iter;
+  h->nonfinite = 0;
+  h->hist_cap = c->N;
+  h->tol = tol;
+  h->r = INFINITY;
+  h->hist = c->loop_hist;
+  PE_CUDA_TRY(cudaMemcpyAsync(c->loopctl, h, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->stream));
+  PE_CUDA_TRY(cudaGraphLaunch(c->loop_exec, c->stream));
+  PE_CUDA_TRY(cudaMemcpyAsync(h, c->loopctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->stream));
+  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int k = h->k;
+  c->k += k;
+  c->sweeps += k;
+  c->launches += (int64_t)k * c->loop_body_launches + 1;
+  *r = h->r;
+  if (res && res->residual_history && res->history_cap > 0) {
+    const int cnt = std::min(k, res->history_cap);
+    PE_CUDA_TRY(cudaMemcpy(res->residual_history, c->loop_hist, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+  }
+  if (h->nonfinite) {
+    c->have_problem = false;
+    if (c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC) PE_TRY(fine_tc_status(c));
+    return pe_fail(PE_ENONFINITE, "Parareal residual is not finite (NaN/Inf in the iterate)");
+  }
+  return PE_OK;
+}
+
 extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, pe_result* res) {
   if (!c) return pe_fail(PE_EINVAL, "pe_solve: ctx is NULL");
   if (!(tol >= 0.0)) return pe_fail(PE_EINVAL, "pe_solve: tol must be >= 0");
@@ -696,11 +806,15 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   PE_CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
   double r = INFINITY;
   int hist = 0;
-  while (c->k < c->max_iter) {
-    PE_TRY(iter_impl(c, &r, c->precision));
-    if (res && res->residual_history && hist < res->history_cap) res->residual_history[hist] = r;
-    ++hist;
-    if (r <= tol) break;
+  if (loop_on_device(c)) {
+    PE_TRY(solve_loop_on_device(c, tol, res, &r));
+  } else {
+    while (c->k < c->max_iter) {
+      PE_TRY(iter_impl(c, &r, c->precision));
+      if (res && res->residual_history && hist < res->history_cap) res->residual_history[hist] = r;
+      ++hist;
+      if (r <= tol) break;
+    }
   }
   PE_CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
   PE_TRY(modal_to_nodal(c, c->U + (int64_t)c->N * c->g.ndof, c->out_nodal));

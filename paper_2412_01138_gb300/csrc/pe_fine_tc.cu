@@ -57,21 +57,6 @@ __host__ __device__ constexpr int ft_smem_bytes(int KP) {
 // so that the tensor core reads whole rows without bank conflicts.  Terms start on
 // 1024-byte boundaries, as the pattern requires.
 __host__ __device__ constexpr int ft_kpad(int K) { return K <= 16 ? 16 : (K <= 32 ? 32 : 64); }
-// Columns of the contraction: KT = KP on the tensor cores (zero padded past K) and KR on the
-// CUDA cores.  One or two columns past 16 or 32 (K = 17, 18, 33, 34: one exponential source
-// and 8 or 16 sinusoidal ones) are added in the epilogue as float32 FMAs instead of doubling
-// the tensor work by padding to the next width.
-constexpr int FT_MAX_REM = 2;
-inline void ft_columns(int K, int* KP, int* KR) {
-  const int rem = K % 16;
-  if ((K == 17 || K == 18 || K == 33 || K == 34) && rem <= FT_MAX_REM) {
-    *KP = K - rem;
-    *KR = rem;
-  } else {
-    *KP = ft_kpad(K);
-    *KR = 0;
-  }
-}
 __device__ __forceinline__ int64_t ft_swz(int64_t off, int KP) {
   return off ^ (((off >> 7) & (KP / 8 - 1)) << 4);
 }
@@ -181,17 +166,6 @@ __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, 
     Bsp[(((int64_t)g * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
 }
 
-// Time factors of the CUDA-core columns k = KP .. KP + KR - 1, one contiguous row per column:
-// Yr[e][n * M + m] = Y_n[m][KP + e] (from the float table of rows of KC columns).
-__global__ void ft_rem_time_kernel(const float* __restrict__ Y, int NM, int KC, int KP, int KR,
-                                   float* __restrict__ Yr) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)KR * NM) return;
-  const int col = (int)(e / NM);
-  const int64_t row = e - (int64_t)col * NM;
-  Yr[e] = Y[row * KC + KP + col];
-}
-
 // Split stage weights of every mode tile, in the A-operand layout of the kernel below:
 // tile q occupies 3 * 128 * KP * 2 bytes, [term][row r][k] swizzled as above, row r holding
 // W[k][128 q + r] (zero past the last mode and past K).
@@ -219,31 +193,8 @@ __global__ void ft_split_w_kernel(const float* __restrict__ W, int64_t nd, int K
   for (int t = 0; t < 3; ++t) Asp[((tile * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
 }
 
-// a_m += sum_{e < KR} wr[e] Y_e[m] for the CNT substeps held in v (y: Y_0 at the first of them,
-// Y_e at y + e * NM; null past the last slice)
-template <int KR, int CNT>
-__device__ __forceinline__ void ft_add_rem(float (&v)[CNT], const float* wr, const float* y, int64_t NM) {
-  if constexpr (KR > 0) {
-    if (y == nullptr) return;
-#pragma unroll
-    for (int e = 0; e < KR; ++e) {
-      const float4* row = reinterpret_cast<const float4*>(y + e * NM);
-#pragma unroll
-      for (int q = 0; q < CNT / 4; ++q) {
-        const float4 t = __ldg(row + q);
-        v[4 * q] = fmaf(wr[e], t.x, v[4 * q]);
-        v[4 * q + 1] = fmaf(wr[e], t.y, v[4 * q + 1]);
-        v[4 * q + 2] = fmaf(wr[e], t.z, v[4 * q + 2]);
-        v[4 * q + 3] = fmaf(wr[e], t.w, v[4 * q + 3]);
-      }
-    }
-  }
-}
-
 struct FtArgs {
   const float* W32;      // stage weights [K][ndof]
-  const float* Wr;       // stage weights of the CUDA-core columns [KR][ndof] (= W32 + KP * ndof)
-  const float* Yr;       // time factors of the CUDA-core columns [KR][N * M]
   const float* coefF32;  // E_hi [ndof], E_lo [ndof]
   const double* EM;      // exp(-lam M dt) [ndof]
   const double* U;       // U^n at n * ndof
@@ -255,7 +206,7 @@ struct FtArgs {
   int* err;
 };
 
-template <int KP, int KR>
+template <int KP>
 __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
   constexpr int A_TERM = FT_ROWS * KP * 2;          // one split term of the A operand
   constexpr int A_BYTES = 3 * A_TERM;
@@ -315,7 +266,6 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
     struct Pre {
       float eh, el;
       double em, u[UP];
-      float wr[KR > 0 ? KR : 1];  // stage weights of the CUDA-core columns
     };
     Pre P0, P1;
     auto load_epi = [&](Pre& P, int64_t i) {
@@ -324,8 +274,6 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
       P.eh = ok ? a.coefF32[J] : 0.f;
       P.el = ok ? a.coefF32[nd + J] : 0.f;
       P.em = ok ? a.EM[J] : 0.0;
-#pragma unroll
-      for (int e = 0; e < KR; ++e) P.wr[e] = ok ? a.Wr[(int64_t)e * nd + J] : 0.f;
 #pragma unroll
       for (int t = 0; t < UP; ++t) {
         const int s = h + 2 * t;
@@ -357,13 +305,6 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
         const float b = fmaf(e3, x0, fmaf(e2, x1, fmaf(eh, x2, x3)));
         w = fmaf(e4h, w, fmaf(e4l, w, b));
       };
-      // the CUDA-core columns: a_m += sum_e wr_e Y_e[n][m] for the substeps from m0 of slice s
-      auto rem_row = [&](int s, int m0) -> const float* {
-        const int64_t n = g * a.G + s;
-        return n < a.N ? a.Yr + n * M + m0 : nullptr;
-      };
-      const int64_t NM = (int64_t)a.N * M;
-#define add_rem(v, s, m0) ft_add_rem<KR>(v, cur.wr, rem_row(s, m0), NM)
       // the first pair's U was prefetched; later pairs (more than four slices per group) read it here
       auto finish = [&](bool pre, double upre, int s, float w) {
         const int64_t n = g * a.G + s;
@@ -379,27 +320,22 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
         const bool two = s1 < a.G;
         float w0 = 0.f, w1 = 0.f;
         int m0 = 0;
-        // with CUDA-core columns the 16-wide reads keep the epilogue within its registers
-        for (; KR == 0 && m0 + 32 <= M; m0 += 32) {
+        for (; m0 + 32 <= M; m0 += 32) {
           float v0[32], v1[32];
           tmem_ld32(row + (uint32_t)(s0 * M + m0), v0);
           if (two) tmem_ld32(row + (uint32_t)(s1 * M + m0), v1);
           tmem_wait_ld();
-          add_rem(v0, s0, m0);
-          if (two) add_rem(v1, s1, m0);
 #pragma unroll
           for (int e = 0; e < 32; e += 4) {
             chain4(w0, v0[e], v0[e + 1], v0[e + 2], v0[e + 3]);
             if (two) chain4(w1, v1[e], v1[e + 1], v1[e + 2], v1[e + 3]);
           }
         }
-        for (; m0 < M; m0 += 16) {  // 16 substeps at a time (the tail of the 32-wide reads)
+        if (m0 < M) {  // a tail of 16 substeps
           float v0[16], v1[16];
           tmem_ld16(row + (uint32_t)(s0 * M + m0), v0);
           if (two) tmem_ld16(row + (uint32_t)(s1 * M + m0), v1);
           tmem_wait_ld();
-          add_rem(v0, s0, m0);
-          if (two) add_rem(v1, s1, m0);
 #pragma unroll
           for (int e = 0; e < 16; e += 4) {
             chain4(w0, v0[e], v0[e + 1], v0[e + 2], v0[e + 3]);
@@ -409,7 +345,6 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
         finish(p == 0, cur.u[0], s0, w0);
         if (two) finish(p == 0, cur.u[1], s1, w1);
       }
-#undef add_rem
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyD[j & 1]);
@@ -514,16 +449,15 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
   }
 }
 
-template <int KP, int KR>
+template <int KP>
 pe_status ft_launch(const FtArgs& args, int grid, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(fine_tc_kernel<KP, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                ft_smem_bytes(KP));
+    attr = cudaFuncSetAttribute(fine_tc_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft_smem_bytes(KP));
   });
   if (attr != cudaSuccess) return pe_cuda_fail(attr, "fine sweep (tensor cores): shared-memory attribute");
-  fine_tc_kernel<KP, KR><<<grid, FT_THREADS, ft_smem_bytes(KP), st>>>(args);
+  fine_tc_kernel<KP><<<grid, FT_THREADS, ft_smem_bytes(KP), st>>>(args);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -555,10 +489,7 @@ pe_status fine_tc_prepare(pe_ctx* c) {
   const int M = c->M, K = c->K, N = c->N;
   if (!fine_tc_supported(M) || K < 1 || K > 64 || !c->tcB || !c->tc_err)
     return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported shape");
-  int KP = 16, KR = 0;
-  ft_columns(K, &KP, &KR);
-  const int KT = K - KR;  // columns on the tensor cores (the split images hold these, zero padded to KP)
-  const int KC = (K + 3) / 4 * 4;
+  const int KP = ft_kpad(K), KC = (K + 3) / 4 * 4;
   int G, NR, ngroups;
   ft_shape(KP, M, N, &G, &NR, &ngroups);
   const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
@@ -572,22 +503,15 @@ pe_status fine_tc_prepare(pe_ctx* c) {
     c->tcA_cap = a_need;
   }
   const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
-  ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, KT, KC, G, NR, KP,
+  ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
                                                                                  ngroups, (uint4*)c->tcB);
   PE_CUDA_TRY(cudaGetLastError());
   const int64_t nsw = tiles * FT_ROWS * (KP / 8);
-  ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, KT, KP, tiles,
+  ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
                                                                            (uint4*)c->tcA);
   PE_CUDA_TRY(cudaGetLastError());
-  c->launches += 2;
-  if (KR > 0) {
-    const int64_t NM = (int64_t)N * M;
-    ft_rem_time_kernel<<<(unsigned)((KR * NM + 255) / 256), 256, 0, c->stream>>>(c->AF32, (int)NM, KC, KP, KR,
-                                                                                  c->tcYr);
-    PE_CUDA_TRY(cudaGetLastError());
-    c->launches += 1;
-  }
   c->tc_split_ok = true;
+  c->launches += 2;
   return PE_OK;
 }
 
@@ -596,15 +520,12 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   if (!fine_tc_supported(M) || K < 1 || K > 64 || !c->tcB || !c->tc_err)
     return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported shape");
   if (!c->tc_split_ok) PE_TRY(fine_tc_prepare(c));
-  int KP = 16, KR = 0;
-  ft_columns(K, &KP, &KR);
+  const int KP = ft_kpad(K);
   int G, NR, ngroups;
   ft_shape(KP, M, N, &G, &NR, &ngroups);
   const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
   FtArgs args{};
   args.W32 = c->Wst32;
-  args.Wr = c->Wst32 + (int64_t)KP * c->g.ndof;
-  args.Yr = c->tcYr;
   args.coefF32 = c->coefF32;
   args.EM = c->coefF + (int64_t)(c->q + 1) * c->g.ndof;
   args.U = c->U;
@@ -626,13 +547,11 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = (int)std::min<int64_t>(args.items, sms);
   pe_status st = PE_OK;
-  if (KP == 16 && KR == 0) st = ft_launch<16, 0>(args, grid, c->stream);
-  else if (KP == 16 && KR == 1) st = ft_launch<16, 1>(args, grid, c->stream);
-  else if (KP == 16 && KR == 2) st = ft_launch<16, 2>(args, grid, c->stream);
-  else if (KP == 32 && KR == 0) st = ft_launch<32, 0>(args, grid, c->stream);
-  else if (KP == 32 && KR == 1) st = ft_launch<32, 1>(args, grid, c->stream);
-  else if (KP == 32 && KR == 2) st = ft_launch<32, 2>(args, grid, c->stream);
-  else st = ft_launch<64, 0>(args, grid, c->stream);
+  switch (KP) {
+    case 16: st = ft_launch<16>(args, grid, c->stream); break;
+    case 32: st = ft_launch<32>(args, grid, c->stream); break;
+    default: st = ft_launch<64>(args, grid, c->stream); break;
+  }
   c->launches += 1;
   return st;
 }

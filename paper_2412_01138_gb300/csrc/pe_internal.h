@@ -64,6 +64,14 @@ struct StageCols {
   signed char term[2 * PE_MAX_TERMS];
   signed char kind[2 * PE_MAX_TERMS];
 };
+// Device-resident state of a solve whose Parareal loop runs as a CUDA graph (device_loop):
+// the correction kernel's last CTA appends r_k, advances k and sets the graph's loop condition.
+struct LoopCtl {
+  int k, max_iter, nonfinite, hist_cap;
+  double tol, r;
+  double* hist;  // [hist_cap] residuals r_1 .. r_k (device)
+};
+
 struct pe_ctx {
   // problem
   Geom g;    // the modes this context owns (every mode unless it owns a block of axis-0 modes)
@@ -116,7 +124,6 @@ struct pe_ctx {
   unsigned int* done_ctr = nullptr;  // correction: CTAs finished (0 between launches)
   unsigned char* tcB = nullptr;  // tensor-core fine engine: split time factors of every slice group
   unsigned char* tcA = nullptr;  // tensor-core fine engine: split stage weights of every mode tile
-  float* tcYr = nullptr;         // tensor-core fine engine: time factors of its CUDA-core columns [2][N*M]
   size_t tcA_cap = 0;            // bytes allocated in tcA
   bool tc_split_ok = false;      // tcA / tcB hold the current problem's split operands
   int* tc_err = nullptr;         // tensor-core fine engine: error code of an expired wait (0: none)
@@ -159,6 +166,14 @@ struct pe_ctx {
   bool have_problem = false;
   bool have_output = false;
   cudaEvent_t ev[PE_NEV];
+  // device-resident Parareal loop (pe_options.device_loop)
+  int device_loop = 0;
+  cudaGraphExec_t loop_exec = nullptr;
+  int loop_K = -1, loop_prec = -1;  // what the graph was built for
+  int64_t loop_body_launches = 0;   // kernels of one pass of the graph's body
+  LoopCtl* loopctl = nullptr;       // device
+  LoopCtl* h_loop = nullptr;        // pinned host copy
+  double* loop_hist = nullptr;      // device [N]
 };
 
 // Substeps of time factors (per_m values each) staged per shared-memory fill.
@@ -211,6 +226,9 @@ pe_status axis_factors_fused(pe_ctx* c, int R, const double* loads, double* fac,
 pe_status launch_coarse_sweep(pe_ctx* c);
 pe_status launch_fine_sweep(pe_ctx* c, int precision);
 pe_status launch_correction(pe_ctx* c, double* num, double* den, cudaEvent_t after = nullptr);
+// the correction kernel alone; with loop != NULL its last CTA also runs the stopping decision of a
+// device-resident loop (appends r, advances k, sets the graph condition `handle`)
+pe_status launch_correction_kernel(pe_ctx* c, LoopCtl* loop, unsigned long long handle);
 pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse);
 
 // pe_learned.cu

@@ -313,80 +313,81 @@ __device__ inline T block_sum(T v, T* sh) {
   return out;
 }
 
-// The correction as a linear recurrence in the slice index.  With
-// delta^n = U^{n,(k+1)} - U^{n,(k)} (delta^0 = 0: U^0 is the same in every iterate) the
-// affine update U^{n+1,(k+1)} = Fbar^{n+1} + E_G delta^n reads
-//   delta^{n+1} = E_G delta^n + (Fbar^{n+1} - U^{n+1,(k)}),   U^{n+1,(k+1)} = U^{n+1,(k)} + delta^{n+1},
-// a first-order recurrence whose coefficient E_G is the same for every slice of a mode.  It is
-// split into CH chunks of consecutive slices, one thread per (mode, chunk): each thread runs
-// its chunk from delta = 0 (phase 1, its S <= 8 inputs held in registers), the chunks' end
-// values are chained through shared memory (phase 2: carry_c = E_G^{S} carry_{c-1} + end_{c-1}),
-// and each thread adds E_G^{i} carry to its i-th value (phase 3) and writes U and the residual
-// terms.  Same values as the sequential sweep up to rounding, with CH times the loads in
-// flight (the sequential sweep of one thread per mode leaves HBM mostly idle).
-constexpr int kCorrSlots = 8;  // slices of a chunk held in registers
+// Stopping decision of a device-resident loop, run by one thread after the residual sums are
+// complete: r_k appended to the history, k advanced, and the graph's while condition set to
+// continue while r > tol and k < max_iter (a non-finite sum stops the loop and is flagged).
+__device__ void loop_decide(LoopCtl* L, unsigned long long handle, double num, double den) {
+  const bool finite = isfinite(num) && isfinite(den);
+  const double r = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+  const int k = L->k;
+  if (k < L->hist_cap) L->hist[k] = r;
+  L->k = k + 1;
+  L->r = r;
+  if (!finite) L->nonfinite = 1;
+  cudaGraphSetConditional((cudaGraphConditionalHandle)handle,
+                          (finite && r > L->tol && k + 1 < L->max_iter) ? 1u : 0u);
+}
 
-template <int CH>
+// The correction: one thread per mode walks the slices.  With d = U^{n,(k+1)} - U^{n,(k)}
+// (d = 0 at n = 0: U^0 is the same in every iterate)
+//   U^{n+1,(k+1)} = fma(E_G, d, Fbar^{n+1}),   d <- U^{n+1,(k+1)} - U^{n+1,(k)},
+// and the residual terms fma(d, d, sd), fma(U, U, su): four float64 operations per mode and
+// slice.  GB300 executes float64 at 2 lanes per SM and clock, so this HBM-shaped step is bound
+// by those operations (at 255^2 x 32 slices: about 13 us at the full float64 rate); the loads of
+// the next kCorrPF slices are issued before the current kCorrPF are combined.
+constexpr int kCorrPF = 8;
+
 __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const double* __restrict__ muM_axis,
                                                          const double* __restrict__ coefG,
                                                          const double* __restrict__ Fbar, double* __restrict__ U,
                                                          double* __restrict__ partials,
-                                                         unsigned int* __restrict__ done, double* __restrict__ red) {
-  constexpr int MB = 256 / CH;  // modes per CTA
+                                                         unsigned int* __restrict__ done, double* __restrict__ red,
+                                                         LoopCtl* loop, unsigned long long handle) {
   __shared__ double sh[32];
-  __shared__ double s_end[CH][MB];
   __shared__ bool s_last;
-  const int c = threadIdx.x / MB, jm = threadIdx.x % MB;
-  const int64_t J = (int64_t)blockIdx.x * MB + jm;
-  const int S = (N + CH - 1) / CH;              // slices per chunk (<= kCorrSlots)
-  const int n0 = c * S, n1 = min(N, n0 + S);     // this chunk updates U^{n+1}, n0 <= n < n1
-  const bool live = J < g.ndof;
-  const int64_t nd = g.ndof;
-  double E = 0.0, w = 0.0;
-  double dl[kCorrSlots], uo[kCorrSlots];
-  double d = 0.0;
-  if (live) {
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double sd = 0.0, su = 0.0, w = 0.0;
+  if (J < g.ndof) {
+    const int64_t nd = g.ndof;
     int j[PE_MAX_D];
     unflatten(g, J, j);
     w = muM_axis[g.off[0] + j[0]];
     for (int a = 1; a < g.d; ++a) w *= muM_axis[g.off[a] + j[a]];
-    E = coefG[J];
-    // phase 1: all loads of the chunk first, then the local recurrence from delta = 0
-    double fb[kCorrSlots];
+    const double E = coefG[J];
+    double d = 0.0;
+    // per slice n: Fbar^{n+1} = F(U^{n,(k)}) and the old U^{n+1}
+    double f0[kCorrPF], o0[kCorrPF], f1[kCorrPF], o1[kCorrPF];
 #pragma unroll
-    for (int i = 0; i < kCorrSlots; ++i) {
-      const int n = n0 + i;
-      const bool in = n < n1;
-      fb[i] = in ? Fbar[(int64_t)n * nd + J] : 0.0;
-      uo[i] = in ? U[(int64_t)(n + 1) * nd + J] : 0.0;
+    for (int e = 0; e < kCorrPF; ++e) {
+      const int64_t o = (int64_t)e * nd + J;
+      const bool in = e < N;
+      f0[e] = in ? Fbar[o] : 0.0;
+      o0[e] = in ? U[o + nd] : 0.0;
     }
+    for (int n0 = 0; n0 < N; n0 += kCorrPF) {
 #pragma unroll
-    for (int i = 0; i < kCorrSlots; ++i) {
-      if (n0 + i < n1) d = fma(E, d, fb[i] - uo[i]);
-      dl[i] = d;
-    }
-  }
-  s_end[c][jm] = d;
-  __syncthreads();
-  double sd = 0.0, su = 0.0;
-  if (live && n0 < n1) {
-    // phase 2: delta at this chunk's start, chained over the earlier chunks
-    double ES = 1.0;  // E_G^S
-    for (int i = 0; i < S; ++i) ES *= E;
-    double carry = 0.0;
-    for (int cc = 0; cc < c; ++cc) carry = fma(ES, carry, s_end[cc][jm]);
-    // phase 3
-    double pw = E;
+      for (int e = 0; e < kCorrPF; ++e) {
+        const int n = n0 + kCorrPF + e;
+        const int64_t o = (int64_t)n * nd + J;
+        const bool in = n < N;
+        f1[e] = in ? Fbar[o] : 0.0;
+        o1[e] = in ? U[o + nd] : 0.0;
+      }
 #pragma unroll
-    for (int i = 0; i < kCorrSlots; ++i) {
-      const int n = n0 + i;
-      if (n < n1) {
-        const double dn = fma(pw, carry, dl[i]);
-        const double un = uo[i] + dn;
-        U[(int64_t)(n + 1) * nd + J] = un;
-        sd = fma(dn, dn, sd);
-        su = fma(un, un, su);
-        pw *= E;
+      for (int e = 0; e < kCorrPF; ++e) {
+        const int n = n0 + e;
+        if (n < N) {
+          const double un = fma(E, d, f0[e]);
+          U[(int64_t)(n + 1) * nd + J] = un;
+          d = un - o0[e];
+          sd = fma(d, d, sd);
+          su = fma(un, un, su);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kCorrPF; ++e) {
+        f0[e] = f1[e];
+        o0[e] = o1[e];
       }
     }
   }
@@ -416,61 +417,7 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
       red[0] = td;
       red[1] = tu;
       *done = 0u;
-    }
-  }
-}
-
-// the sequential correction for long slice ranges (more than 32 chunks of kCorrSlots)
-__global__ void __launch_bounds__(256) correction_seq_kernel(Geom g, int N, const double* __restrict__ muM_axis,
-                                                             const double* __restrict__ coefG,
-                                                             const double* __restrict__ Fbar, double* __restrict__ U,
-                                                             double* __restrict__ partials,
-                                                             unsigned int* __restrict__ done, double* __restrict__ red) {
-  __shared__ double sh[32];
-  __shared__ bool s_last;
-  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double sd = 0.0, su = 0.0, w = 0.0;
-  if (J < g.ndof) {
-    const int64_t nd = g.ndof;
-    int j[PE_MAX_D];
-    unflatten(g, J, j);
-    w = muM_axis[g.off[0] + j[0]];
-    for (int a = 1; a < g.d; ++a) w *= muM_axis[g.off[a] + j[a]];
-    const double E = coefG[J];
-    double d = 0.0;
-    for (int n = 0; n < N; ++n) {
-      const double uo = U[(int64_t)(n + 1) * nd + J];
-      d = fma(E, d, Fbar[(int64_t)n * nd + J] - uo);
-      const double un = uo + d;
-      U[(int64_t)(n + 1) * nd + J] = un;
-      sd = fma(d, d, sd);
-      su = fma(un, un, su);
-    }
-  }
-  sd *= w;
-  su *= w;
-  sd = block_sum(sd, sh);
-  su = block_sum(su, sh);
-  if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = sd;
-    partials[2 * blockIdx.x + 1] = su;
-    __threadfence();
-    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    double td = 0.0, tu = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-      td += __ldcg(partials + 2 * b);
-      tu += __ldcg(partials + 2 * b + 1);
-    }
-    td = block_sum(td, sh);
-    tu = block_sum(tu, sh);
-    if (threadIdx.x == 0) {
-      red[0] = td;
-      red[1] = tu;
-      *done = 0u;
+      if (loop) loop_decide(loop, handle, td, tu);
     }
   }
 }
@@ -515,30 +462,22 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
 }
 
 pe_status launch_correction(pe_ctx* c, double* num, double* den, cudaEvent_t after) {
-  // chunks per mode: the fewest (a power of two, at most 32) whose chunks hold <= 8 slices
-  int CH = 1;
-  while (CH < 32 && (c->N + CH - 1) / CH > kCorrSlots) CH *= 2;
-  const bool seq = (c->N + CH - 1) / CH > kCorrSlots;
-  const int MB = seq ? 256 : 256 / CH;
-  const int64_t blocks64 = (c->g.ndof + MB - 1) / MB;
-  if (blocks64 > (int64_t)c->max_blocks)
-    return pe_fail(PE_EINVAL, "correction: partials buffer too small");
-  const unsigned blocks = (unsigned)blocks64;
-#define PE_CORR_ARGS c->g, c->N, c->muM_axis, c->coefG, c->Fbar, c->U, c->partials, c->done_ctr, c->red
-  if (seq) correction_seq_kernel<<<blocks, 256, 0, c->stream>>>(PE_CORR_ARGS);
-  else if (CH == 1) correction_kernel<1><<<blocks, 256, 0, c->stream>>>(PE_CORR_ARGS);
-  else if (CH == 2) correction_kernel<2><<<blocks, 256, 0, c->stream>>>(PE_CORR_ARGS);
-  else if (CH == 4) correction_kernel<4><<<blocks, 256, 0, c->stream>>>(PE_CORR_ARGS);
-  else if (CH == 8) correction_kernel<8><<<blocks, 256, 0, c->stream>>>(PE_CORR_ARGS);
-  else if (CH == 16) correction_kernel<16><<<blocks, 256, 0, c->stream>>>(PE_CORR_ARGS);
-  else correction_kernel<32><<<blocks, 256, 0, c->stream>>>(PE_CORR_ARGS);
-#undef PE_CORR_ARGS
-  c->launches += 1;
-  PE_CUDA_TRY(cudaGetLastError());
+  PE_TRY(launch_correction_kernel(c, nullptr, 0ull));
   if (after) PE_CUDA_TRY(cudaEventRecord(after, c->stream));
   PE_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   *num = c->h_red[0];
   *den = c->h_red[1];
+  return PE_OK;
+}
+
+pe_status launch_correction_kernel(pe_ctx* c, LoopCtl* loop, unsigned long long handle) {
+  const int threads = 256;
+  const int64_t blocks = (c->g.ndof + threads - 1) / threads;
+  if (blocks > (int64_t)c->max_blocks) return pe_fail(PE_EINVAL, "correction: partials buffer too small");
+  correction_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(c->g, c->N, c->muM_axis, c->coefG, c->Fbar, c->U,
+                                                                 c->partials, c->done_ctr, c->red, loop, handle);
+  c->launches += 1;
+  PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

@@ -67,7 +67,7 @@ class pe_options(C.Structure):
                 ("max_iter", C.c_int32), ("cuda_stream", C.c_void_p), ("forcing_path", C.c_int32),
                 ("cache_forced", C.c_int32), ("periodic_mask", C.c_int32), ("fine_engine", C.c_int32),
                 ("mode_begin", C.c_int32), ("mode_end", C.c_int32), ("residual_reduce", REDUCE_FN),
-                ("residual_reduce_user", C.c_void_p)]
+                ("residual_reduce_user", C.c_void_p), ("device_loop", C.c_int32)]
 
 
 class pe_field(C.Structure):
@@ -210,7 +210,7 @@ class Solver:
     def __init__(self, prob: "_in.Problem", precision: int = PE_FP64, stream=None, max_iter: int = 0,
                  random_coarse_seed: Optional[int] = None, forcing_path: int = PE_FORCING_SEPARABLE,
                  dst_backend: int = PE_DST_AUTO, cache_forced: bool = False, fine_engine: int = PE_FINE_SIMT,
-                 mode_range: Optional[Sequence[int]] = None, residual_reduce=None):
+                 mode_range: Optional[Sequence[int]] = None, residual_reduce=None, device_loop: int = 0):
         """mode_range = (begin, end): own only the modes with axis-0 index in [begin, end) (a shard of
         a mode-sharded solve); residual_reduce(sums) -> totals: combines the two residual sums of
         this context with those of the other shards (pe_options.residual_reduce)."""
@@ -237,7 +237,7 @@ class Solver:
         mask = sum(1 << a for a, p in enumerate(getattr(prob, "periodic", ())) if p)
         opt = pe_options(precision, dst_backend, prob.quad_pts, max_iter, stream_handle(stream), forcing_path,
                          1 if cache_forced else 0, mask, fine_engine, b, e,
-                         self._reduce if self._reduce is not None else REDUCE_FN(), None)
+                         self._reduce if self._reduce is not None else REDUCE_FN(), None, device_loop)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup(C.byref(ctx), prob.d, n, box, prob.D, prob.t0, prob.T, prob.N, prob.M,
                                   C.byref(fine), C.byref(coarse), C.byref(opt)))
@@ -469,7 +469,7 @@ class BatchSolver:
             q.u0 = pe_field(PE_FIELD_TERMS_SEPARABLE, len(p.u0), C.cast(tu, C.POINTER(pe_term)), None)
             q.forcing = pe_forcing(len(p.forcing), C.cast(tf, C.POINTER(pe_term)))
         opt = pe_options(precision, PE_DST_AUTO, self.probs[0].quad_pts, 0, stream_handle(stream),
-                         PE_FORCING_SEPARABLE, 0, 0, PE_FINE_SIMT, 0, 0, REDUCE_FN(), None)
+                         PE_FORCING_SEPARABLE, 0, 0, PE_FINE_SIMT, 0, 0, REDUCE_FN(), None, 0)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup_batch(C.byref(ctx), len(self.probs), arr, C.byref(opt)))
         self.ctx = ctx

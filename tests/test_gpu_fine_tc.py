@@ -7,8 +7,7 @@ products accumulated in float32, so the engine keeps the mixed form's bound: rel
 stress mixes of many high-frequency terms.  Cases span every column padding (K = 1 .. 64:
 16, 32 and 64 columns, 32-, 64- and 128-byte swizzled operand rows), substep counts 16 .. 128
 (slice groups of 1 .. 16 slices, the last group ragged), mode counts that leave a partial
-tile, and the cached forced part.  Column counts just past 16 or 32 (K = 17, 18, 33, 34) run
-16 or 32 columns on the tensor cores and the other one or two as float32 FMAs in the epilogue.
+tile, and the cached forced part.
 """
 import math
 
@@ -58,11 +57,9 @@ def _term_mix(kinds, seed):
 # to about 1.5e-6 from the oracle, so these cases check the engine against the SIMT float32
 # form slice by slice (no more than 10% above its error) under a 2e-6 cap; the 1e-6 bound is
 # checked on the workloads below.
-# (time kinds, substeps, slices): K = 1, 2, 28, 34, 40, 64, 61, 18 columns (tensor widths 16, 16,
-# 32, 32 + 2 columns on the CUDA cores, 64, 64, 64, 16 + 2 on the CUDA cores); M = 16 (16 slices
-# per group), 32 (8, or 4 at width 64), 64 (4), 96 (2 at width 32), 48 (2), 128 (1); N chosen so
-# that the last slice group is partial.  K = 17 and 33 (16 or 32 + 1) are the workloads' own
-# counts, checked below.
+# (time kinds, substeps, slices): K = 1, 2, 28, 34, 40, 64, 61, 18 columns (paddings 16, 16, 32, 64,
+# 64, 64, 64, 32); M = 16 (16 slices per group), 32 (8, or 4 at padding 64), 64 (4), 96 (1 at
+# padding 64), 48 (2), 128 (1); N chosen so that the last slice group is partial.
 @pytest.mark.parametrize("kinds,M,N", [("e", 16, 21), ("s", 32, 9), ("esses" * 3 + "ss", 64, 7),
                                        ("esse" * 4 + "s" * 5, 96, 5), ("s" * 20, 48, 11),
                                        ("s" * 32, 128, 3), ("s" * 30 + "e", 32, 6), ("s" * 9, 32, 7)])
