@@ -43,12 +43,17 @@ TOL = 1e-6
 L2_BYTES = 129 * 1024 * 1024
 
 
-def chosen_kw(pe, prec):
+TC_MIN_DOF = 4096  # below this the split operand images cost more than the tensor cores save
+
+
+def chosen_kw(pe, prec, prob=None):
     """Solver options of a separable-path solve: the mixed form (the chosen form) runs its stage
-    contraction on the tensor cores and its Parareal loop on the device; float64 is the plain
-    form (SIMT kernel, host-driven loop of Algorithm 1)."""
+    contraction on the tensor cores (on the CUDA cores for grids under TC_MIN_DOF nodes, which are
+    launch-bound) and its Parareal loop on the device; float64 is the plain form (SIMT kernel,
+    host-driven loop of Algorithm 1)."""
     if prec == pe.PE_MIXED:
-        return {"fine_engine": pe.PE_FINE_TC, "device_loop": 1}
+        small = prob is not None and prob.ndof < TC_MIN_DOF
+        return {"fine_engine": pe.PE_FINE_SIMT if small else pe.PE_FINE_TC, "device_loop": 1}
     return {"fine_engine": pe.PE_FINE_SIMT}
 
 
@@ -300,10 +305,9 @@ def run_config1(pe, args, barrier):
     prob = I.config1()
     sys_ = osolver.ModalSystem(prob)
     out = {"workload": prob.label}
-    for name, prec, eng, tol, dl in (("fp64_tol1e-12", pe.PE_FP64, pe.PE_FINE_SIMT, 1e-12, 0),
-                                     ("fp64", pe.PE_FP64, pe.PE_FINE_SIMT, TOL, 0),
-                                     ("chosen", pe.PE_MIXED, pe.PE_FINE_TC, TOL, 1)):
-        with pe.Solver(prob, precision=prec, fine_engine=eng, device_loop=dl) as s:
+    for name, prec, tol in (("fp64_tol1e-12", pe.PE_FP64, 1e-12), ("fp64", pe.PE_FP64, TOL),
+                            ("chosen", pe.PE_MIXED, TOL)):
+        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec, prob)) as s:
             for _ in range(max(3, args.warmup)):
                 s.solve(tol=tol)
             barrier()
@@ -317,7 +321,10 @@ def run_config1(pe, args, barrier):
         out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"], "tol": tol,
                      "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
                      "rel_l2_vs_oracle": osolver.rel_l2(modal, ref.U[-1], sys_.norm_w),
-                     "gpu_launches": infos[-1]["kernel_launches"]}
+                     "gpu_launches": infos[-1]["kernel_launches"],
+                     "phases_ms": {k: infos[-1][k] for k in ("ms_tables", "ms_prepare", "ms_iterations",
+                                                             "ms_output")},
+                     "options": {k: v for k, v in chosen_kw(pe, prec, prob).items()}}
     out["speedup_time_to_tol"] = out["fp64"]["time_to_tol_ms"] / out["chosen"]["time_to_tol_ms"]
     return out
 

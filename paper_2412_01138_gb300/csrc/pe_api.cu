@@ -512,6 +512,9 @@ static pe_status modal_to_nodal(pe_ctx* c, const double* modal, double* nodal_ou
 // ---------------------------------------------------------------------------
 // problem, iteration, solve
 // ---------------------------------------------------------------------------
+// grids below this many nodes run pe_set_problem on one stream (their kernels are launch-bound)
+constexpr int64_t kForkMinDof = 4096;
+
 static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
   if (!u0) return pe_fail(PE_EINVAL, "pe_set_problem: u0 is NULL");
   const int nf = f ? f->n_terms : 0;
@@ -539,9 +542,11 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   // those are made on the main one: the copy and forward transform of nodal u0 and the time
   // tables.  The main stream waits for it before the stage weights (which need the time
   // tables' shifts) and the coarse sweep.
+  // (Small grids, whose kernels are launch-bound, keep everything on the main stream.)
   double* U0 = c->U;
   const bool fork_u0 = u0->kind == PE_FIELD_NODAL && u0->nodal != nullptr;
-  const bool fork = fork_u0 || !general;
+  const bool fork = (fork_u0 || !general) && c->gn.ndof >= kForkMinDof;
+  const bool inline_u0 = fork_u0 && !fork;  // nodal u0, transformed below on the main stream
   if (fork) {
     PE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
     PE_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -559,6 +564,8 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     c->stream = main_stream;
     PE_TRY(st);
     PE_CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+  } else if (!general) {
+    PE_TRY(launch_time_tables(c));
   }
   // The phi/b coefficient tables depend only on lam, dt, dT and the nodes: pe_setup made them.
   // Forcing: per-axis modal factors, then (after the join) the stage weights of the fine step.
@@ -569,7 +576,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   if (!general && c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC) PE_TRY(fine_tc_prepare(c));
   PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
   // U^0 = P_h u0
-  if (fork_u0) {
+  if (fork_u0 && !inline_u0) {
     // made on the side stream above
   } else if (u0->kind == PE_FIELD_TERMS_SEPARABLE || u0->kind == PE_FIELD_TERMS_QUADRATURE) {
     PE_TRY(pe_validate_terms(u0->n_terms, u0->terms, c->g.d, "u0"));
