@@ -358,11 +358,22 @@ def run_learned(pe, args, barrier):
         t = torch.empty((L.size, 2), device=dev, dtype=torch.float32)
         t0 = time.perf_counter()
         s.learned_samples(lam_d, om_d, x, t)
-        net = pe.MLP(seed=3)
-        loss = net.train(x, t, epochs=max(1, 60000 // ((L.size + 4095) // 4096)), batch=4096, lr=3e-3)
         torch.cuda.synchronize()
+        t_samples = time.perf_counter() - t0
+        net = pe.MLP(seed=3)
+        epochs = max(1, 60000 // ((L.size + 4095) // 4096))
+        t1 = time.perf_counter()
+        loss = net.train(x, t, epochs=epochs, batch=4096, lr=3e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t1
+        steps = epochs * ((L.size + 4095) // 4096)
+        # 6 FLOP per weight and sample (2 forward, 4 backward: input and weight gradients)
+        weights = 2 * 64 + 64 * 64 + 64 * 2
+        flops = 6.0 * weights * float(L.size) * epochs
         out["training"] = {"pairs": int(L.size), "seeds": "100000..101999", "final_loss": loss,
-                           "seconds": time.perf_counter() - t0}
+                           "adam_steps": steps, "batch": 4096, "seconds_samples": t_samples,
+                           "seconds_training": t_train, "training_tflops": flops / t_train / 1e12,
+                           "flops_note": "6 FLOP per weight (4352 weights) per sample and step"}
         res = {}
         for name, mlp in (("plain_G", None), ("learned_G", net)):
             s.set_learned(mlp)

@@ -22,6 +22,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "pe_learned.h"
@@ -89,112 +91,225 @@ __global__ void samples_kernel(int n, const double* __restrict__ lam, const doub
 }
 
 // ---------------------------------------------------------------------------
-// training
+// training: one persistent cooperative launch runs every Adam step.  Per step
+//   1. every CTA loads the float32 parameters into shared memory and runs the forward and
+//      backward pass of its share of the batch, a warp per sample (rounds of TR_ROUND
+//      samples per CTA, activations and pre-activation gradients kept in shared memory);
+//   2. its threads sum the per-parameter products over those samples (a partial gradient
+//      per CTA, written as column c of partial[k][c]);
+//   3. grid barrier; each CTA owns a contiguous range of parameters and adds their G partials
+//      in CTA order (deterministic), then applies Adam (or, for a gradient evaluation, writes
+//      the gradient);
+//   4. grid barrier (the next step reads the updated parameters).
+// Barriers are bounded waits: on expiry the CTA records an error and returns (every other
+// CTA then expires at its next wait); the host reports PE_ETIMEOUT.
 // ---------------------------------------------------------------------------
-// One thread per sample: forward, loss, backward to the pre-activations; stores
-// h1, h2, dz1, dz2, dy for the weight-gradient reduction.
-__global__ void __launch_bounds__(128) fwd_bwd_kernel(const float* __restrict__ params, const float* __restrict__ x,
-                                                      const float* __restrict__ t, int nb, float inv_n,
-                                                      float* __restrict__ H1, float* __restrict__ H2,
-                                                      float* __restrict__ DZ1, float* __restrict__ DZ2,
-                                                      float* __restrict__ DY, float* __restrict__ loss) {
-  __shared__ float P[NPARAM];
-  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) P[i] = params[i];
+constexpr int TR_THREADS = 256;
+constexpr int TR_WARPS = TR_THREADS / 32;
+constexpr int TR_ROUND = 32;          // samples per CTA per round
+constexpr int W2P = H + 1;            // padded row stride of W2 in shared memory (no bank conflicts)
+constexpr int NPARAM_L = NPARAM + 1;  // the gradient slots plus one slot for the loss
+constexpr int TR_PER_THREAD = (NPARAM_L + TR_THREADS - 1) / TR_THREADS;
+constexpr long long kGridWaitCycles = 2000000000LL;  // about a second
+
+struct TrainArgs {
+  float* params;
+  float* adam_m;
+  float* adam_v;
+  float* partial;        // [NPARAM_L][G]
+  const float* x;        // [n][2]
+  const float* t;        // [n][2]
+  int n, batch, steps_per_epoch, total, it0, nsteps;
+  float lr, b1, b2, eps;
+  long long adam_step0;  // Adam steps taken before this launch
+  float inv_n;           // > 0: fixed loss weight (gradient evaluation); 0: 1 / (batch size)
+  float* grad_out;       // gradient evaluation: the reduced gradient and loss [NPARAM_L]; else null
+  unsigned* bar_count;
+  unsigned* bar_gen;
+  int* err;
+};
+
+struct TrainSmem {
+  float W1[2 * H], b1[H], W2[H * W2P], b2[H], W3[2 * H], b3[2];
+  float H1[TR_ROUND][H], H2[TR_ROUND][H], DZ1[TR_ROUND][H], DZ2[TR_ROUND][H];
+  float X[TR_ROUND][2], DY[TR_ROUND][2], L[TR_ROUND];
+};
+
+// grid-wide barrier of a cooperative launch; false if the wait expired
+__device__ bool grid_barrier(const TrainArgs& a, int* s_ok) {
   __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nb) return;
-  const float x0 = x[2 * s], x1 = x[2 * s + 1];
-  float h1[H], h2[H];
-#pragma unroll
-  for (int j = 0; j < H; ++j) h1[j] = tanhf(fmaf(P[OW1 + 2 * j], x0, fmaf(P[OW1 + 2 * j + 1], x1, P[OB1 + j])));
-#pragma unroll 4
-  for (int i = 0; i < H; ++i) {
-    float z = P[OB2 + i];
-#pragma unroll
-    for (int j = 0; j < H; ++j) z = fmaf(P[OW2 + H * i + j], h1[j], z);
-    h2[i] = tanhf(z);
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* gen = a.bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
+      *a.bar_count = 0u;
+      __threadfence();
+      atomicExch(a.bar_gen, g + 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (*(volatile int*)a.err || clock64() - t0 > kGridWaitCycles) {
+          atomicExch(a.err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
   }
-  float y0 = P[OB3], y1 = P[OB3 + 1];
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    y0 = fmaf(P[OW3 + i], h2[i], y0);
-    y1 = fmaf(P[OW3 + H + i], h2[i], y1);
-  }
-  const float e0 = y0 - t[2 * s], e1 = y1 - t[2 * s + 1];
-  loss[s] = 0.5f * (e0 * e0 + e1 * e1) * inv_n;
-  const float d0 = e0 * inv_n, d1 = e1 * inv_n;
-  DY[2 * s] = d0;
-  DY[2 * s + 1] = d1;
-  float dz2[H];
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    const float dh = fmaf(P[OW3 + i], d0, P[OW3 + H + i] * d1);
-    dz2[i] = dh * (1.f - h2[i] * h2[i]);
-    H2[(size_t)s * H + i] = h2[i];
-    DZ2[(size_t)s * H + i] = dz2[i];
-  }
-#pragma unroll 4
-  for (int j = 0; j < H; ++j) {
-    float dh = 0.f;
-#pragma unroll
-    for (int i = 0; i < H; ++i) dh = fmaf(P[OW2 + H * i + j], dz2[i], dh);
-    H1[(size_t)s * H + j] = h1[j];
-    DZ1[(size_t)s * H + j] = dh * (1.f - h1[j] * h1[j]);
-  }
-}
-
-// One thread per parameter: its gradient summed over the batch (deterministic order).
-__global__ void grad_kernel(const float* __restrict__ x, const float* __restrict__ H1, const float* __restrict__ H2,
-                            const float* __restrict__ DZ1, const float* __restrict__ DZ2,
-                            const float* __restrict__ DY, int nb, float* __restrict__ grad) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= NPARAM) return;
-  float acc = 0.f;
-  if (k < OB1) {  // W1[j][c] = sum dz1[j] x[c]
-    const int j = (k - OW1) / 2, c = (k - OW1) % 2;
-    for (int s = 0; s < nb; ++s) acc = fmaf(DZ1[(size_t)s * H + j], x[2 * s + c], acc);
-  } else if (k < OW2) {
-    const int j = k - OB1;
-    for (int s = 0; s < nb; ++s) acc += DZ1[(size_t)s * H + j];
-  } else if (k < OB2) {  // W2[i][j] = sum dz2[i] h1[j]
-    const int i = (k - OW2) / H, j = (k - OW2) % H;
-    for (int s = 0; s < nb; ++s) acc = fmaf(DZ2[(size_t)s * H + i], H1[(size_t)s * H + j], acc);
-  } else if (k < OW3) {
-    const int i = k - OB2;
-    for (int s = 0; s < nb; ++s) acc += DZ2[(size_t)s * H + i];
-  } else if (k < OB3) {  // W3[o][i] = sum dy[o] h2[i]
-    const int o = (k - OW3) / H, i = (k - OW3) % H;
-    for (int s = 0; s < nb; ++s) acc = fmaf(DY[2 * s + o], H2[(size_t)s * H + i], acc);
-  } else {
-    const int o = k - OB3;
-    for (int s = 0; s < nb; ++s) acc += DY[2 * s + o];
-  }
-  grad[k] = acc;
-}
-
-__global__ void adam_kernel(float* __restrict__ params, const float* __restrict__ grad, float* __restrict__ m,
-                            float* __restrict__ v, float lr, float b1, float b2, float eps, float bc1, float bc2) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= NPARAM) return;
-  const float g = grad[k];
-  const float mk = b1 * m[k] + (1.f - b1) * g;
-  const float vk = b2 * v[k] + (1.f - b2) * g * g;
-  m[k] = mk;
-  v[k] = vk;
-  params[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
-}
-
-__global__ void sum_kernel(const float* __restrict__ a, int n, float* __restrict__ out) {
-  __shared__ float sh[256];
-  float acc = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += a[i];
-  sh[threadIdx.x] = acc;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(TR_THREADS) train_kernel(TrainArgs a) {
+  extern __shared__ __align__(16) unsigned char tr_smem[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(tr_smem);
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x, c = blockIdx.x;
+  // parameters this CTA reduces and updates
+  const int k0 = (int)((int64_t)c * NPARAM_L / G), k1 = (int)((int64_t)(c + 1) * NPARAM_L / G);
+  for (int s = 0; s < a.nsteps; ++s) {
+    const int it = a.it0 + s;
+    const int sidx = it % a.steps_per_epoch;
+    const int off = sidx * a.batch;
+    const int nb = min(a.batch, a.n - off);
+    const float inv_n = a.inv_n > 0.f ? a.inv_n : 1.0f / (float)nb;
+    // 1. parameters into shared memory (from L2: other CTAs updated them in the last step)
+    for (int i = tid; i < 2 * H; i += TR_THREADS) {
+      S.W1[i] = __ldcg(a.params + OW1 + i);
+      S.W3[i] = __ldcg(a.params + OW3 + i);
+    }
+    for (int i = tid; i < H; i += TR_THREADS) {
+      S.b1[i] = __ldcg(a.params + OB1 + i);
+      S.b2[i] = __ldcg(a.params + OB2 + i);
+    }
+    for (int i = tid; i < H * H; i += TR_THREADS) S.W2[(i / H) * W2P + (i % H)] = __ldcg(a.params + OW2 + i);
+    if (tid < 2) S.b3[tid] = __ldcg(a.params + OB3 + tid);
     __syncthreads();
+    // this CTA's samples of the batch
+    const int s0 = off + (int)((int64_t)c * nb / G), s1 = off + (int)((int64_t)(c + 1) * nb / G);
+    float acc[TR_PER_THREAD];
+#pragma unroll
+    for (int e = 0; e < TR_PER_THREAD; ++e) acc[e] = 0.f;
+    for (int r0 = s0; r0 < s1; r0 += TR_ROUND) {
+      const int cnt = min(TR_ROUND, s1 - r0);
+      for (int q = warp; q < cnt; q += TR_WARPS) {
+        const int smp = r0 + q;
+        const float x0 = a.x[2 * smp], x1 = a.x[2 * smp + 1];
+        // layer 1: lane holds j = lane, lane + 32
+        float h1a = tanhf(fmaf(S.W1[2 * lane], x0, fmaf(S.W1[2 * lane + 1], x1, S.b1[lane])));
+        float h1b = tanhf(fmaf(S.W1[2 * (lane + 32)], x0, fmaf(S.W1[2 * (lane + 32) + 1], x1, S.b1[lane + 32])));
+        S.H1[q][lane] = h1a;
+        S.H1[q][lane + 32] = h1b;
+        __syncwarp();
+        // layer 2: lane holds i = lane, lane + 32
+        float za = S.b2[lane], zb = S.b2[lane + 32];
+#pragma unroll 16
+        for (int j = 0; j < H; ++j) {
+          const float hj = S.H1[q][j];
+          za = fmaf(S.W2[lane * W2P + j], hj, za);
+          zb = fmaf(S.W2[(lane + 32) * W2P + j], hj, zb);
+        }
+        const float h2a = tanhf(za), h2b = tanhf(zb);
+        S.H2[q][lane] = h2a;
+        S.H2[q][lane + 32] = h2b;
+        // layer 3 (warp sums)
+        float y0 = fmaf(S.W3[lane], h2a, S.W3[lane + 32] * h2b);
+        float y1 = fmaf(S.W3[H + lane], h2a, S.W3[H + lane + 32] * h2b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+          y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+        }
+        y0 += S.b3[0];
+        y1 += S.b3[1];
+        const float e0 = y0 - a.t[2 * smp], e1 = y1 - a.t[2 * smp + 1];
+        const float d0 = e0 * inv_n, d1 = e1 * inv_n;
+        // backward to the pre-activations
+        const float dza = fmaf(S.W3[lane], d0, S.W3[H + lane] * d1) * (1.f - h2a * h2a);
+        const float dzb = fmaf(S.W3[lane + 32], d0, S.W3[H + lane + 32] * d1) * (1.f - h2b * h2b);
+        S.DZ2[q][lane] = dza;
+        S.DZ2[q][lane + 32] = dzb;
+        __syncwarp();
+        float ga = 0.f, gb = 0.f;
+#pragma unroll 16
+        for (int i = 0; i < H; ++i) {
+          const float di = S.DZ2[q][i];
+          ga = fmaf(S.W2[i * W2P + lane], di, ga);
+          gb = fmaf(S.W2[i * W2P + lane + 32], di, gb);
+        }
+        S.DZ1[q][lane] = ga * (1.f - h1a * h1a);
+        S.DZ1[q][lane + 32] = gb * (1.f - h1b * h1b);
+        if (lane == 0) {
+          S.X[q][0] = x0;
+          S.X[q][1] = x1;
+          S.DY[q][0] = d0;
+          S.DY[q][1] = d1;
+          S.L[q] = 0.5f * (e0 * e0 + e1 * e1) * inv_n;
+        }
+      }
+      __syncthreads();
+      // 2. per-parameter sums over this round's samples
+#pragma unroll
+      for (int e = 0; e < TR_PER_THREAD; ++e) {
+        const int k = tid + e * TR_THREADS;
+        float v = 0.f;
+        if (k < OB1) {
+          const int j = (k - OW1) >> 1, cc = (k - OW1) & 1;
+          for (int q = 0; q < cnt; ++q) v = fmaf(S.DZ1[q][j], S.X[q][cc], v);
+        } else if (k < OW2) {
+          for (int q = 0; q < cnt; ++q) v += S.DZ1[q][k - OB1];
+        } else if (k < OB2) {
+          const int i = (k - OW2) / H, j = (k - OW2) % H;
+          for (int q = 0; q < cnt; ++q) v = fmaf(S.DZ2[q][i], S.H1[q][j], v);
+        } else if (k < OW3) {
+          for (int q = 0; q < cnt; ++q) v += S.DZ2[q][k - OB2];
+        } else if (k < OB3) {
+          const int o = (k - OW3) / H, i = (k - OW3) % H;
+          for (int q = 0; q < cnt; ++q) v = fmaf(S.DY[q][o], S.H2[q][i], v);
+        } else if (k < NPARAM) {
+          for (int q = 0; q < cnt; ++q) v += S.DY[q][k - OB3];
+        } else if (k == NPARAM) {
+          for (int q = 0; q < cnt; ++q) v += S.L[q];
+        }
+        acc[e] += v;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int e = 0; e < TR_PER_THREAD; ++e) {
+      const int k = tid + e * TR_THREADS;
+      if (k < NPARAM_L) a.partial[(int64_t)k * G + c] = acc[e];
+    }
+    if (!grid_barrier(a, &s_ok)) return;
+    // 3. this CTA's parameters: the G partials in CTA order, then Adam (or the gradient out)
+    const long long step = a.adam_step0 + s + 1;
+    const float bc1 = 1.f - powf(a.b1, (float)step), bc2 = 1.f - powf(a.b2, (float)step);
+    const float cosv = 0.5f * (1.f + cospif((float)it / (float)a.total));
+    const float lr_t = a.lr * (0.01f + 0.99f * cosv);
+    for (int k = k0 + warp; k < k1; k += TR_WARPS) {
+      float g = 0.f;
+      for (int cc = lane; cc < G; cc += 32) g += __ldcg(a.partial + (int64_t)k * G + cc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+      if (lane == 0) {
+        if (a.grad_out) {
+          a.grad_out[k] = g;
+        } else if (k < NPARAM) {
+          const float mk = a.b1 * a.adam_m[k] + (1.f - a.b1) * g;
+          const float vk = a.b2 * a.adam_v[k] + (1.f - a.b2) * g * g;
+          a.adam_m[k] = mk;
+          a.adam_v[k] = vk;
+          a.params[k] -= lr_t * (mk / bc1) / (sqrtf(vk / bc2) + a.eps);
+        }
+      }
+    }
+    if (!grid_barrier(a, &s_ok)) return;
   }
-  if (threadIdx.x == 0) *out = sh[0];
 }
 
 __global__ void to_half_kernel(const float* __restrict__ p, __half* __restrict__ h) {
@@ -357,7 +472,8 @@ extern "C" pe_status pe_mlp_create(pe_mlp** out, uint64_t seed) {
   };
   al((void**)&m->params, sizeof(float) * NPARAM);
   al((void**)&m->params16, sizeof(__half) * NPARAM);
-  al((void**)&m->grad, sizeof(float) * NPARAM);
+  al((void**)&m->grad, sizeof(float) * NPARAM_L);
+  al((void**)&m->sync, sizeof(unsigned) * 4);
   al((void**)&m->adam_m, sizeof(float) * NPARAM);
   al((void**)&m->adam_v, sizeof(float) * NPARAM);
   al((void**)&m->loss_dev, sizeof(float));
@@ -379,7 +495,7 @@ extern "C" pe_status pe_mlp_create(pe_mlp** out, uint64_t seed) {
 
 extern "C" void pe_mlp_destroy(pe_mlp* m) {
   if (!m) return;
-  void* ptrs[] = {m->params, m->params16, m->grad, m->adam_m, m->adam_v, m->loss_dev, m->scratch};
+  void* ptrs[] = {m->params, m->params16, m->grad, m->adam_m, m->adam_v, m->loss_dev, m->partial, m->sync};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete m;
@@ -387,78 +503,99 @@ extern "C" void pe_mlp_destroy(pe_mlp* m) {
 
 extern "C" int32_t pe_mlp_num_params(void) { return NPARAM; }
 
-static pe_status ensure_scratch(pe_mlp* m, int nb) {
-  if (m->scratch_cap >= nb) return PE_OK;
-  if (m->scratch) cudaFree(m->scratch);
-  m->scratch = nullptr;
-  m->scratch_cap = 0;
-  const size_t per = (size_t)4 * H + 2 + 1;  // H1, H2, DZ1, DZ2, DY, loss
-  if (cudaMalloc((void**)&m->scratch, sizeof(float) * per * (size_t)nb) != cudaSuccess) {
-    cudaGetLastError();
-    return pe_fail(PE_ENOMEM, "pe_mlp: scratch allocation failed");
+// One launch of the persistent training kernel: nsteps steps from step index it0 of a schedule
+// of `total` steps over epochs of steps_per_epoch batches (grad_out != null: one gradient
+// evaluation of the whole range, no update).
+static pe_status run_train(pe_mlp* m, const float* x, const float* t, int n, int batch, int steps_per_epoch,
+                           int total, int it0, int nsteps, float lr, float inv_n, float* grad_out,
+                           cudaStream_t st) {
+  int dev = 0, sms = 0, coop = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return pe_fail(PE_ECUDA, "pe_mlp: the device does not support cooperative launches");
+  const size_t smem = sizeof(TrainSmem);
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [smem] {
+    attr = cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr != cudaSuccess) return pe_cuda_fail(attr, "pe_mlp: shared-memory attribute");
+  int per_sm = 0;
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, train_kernel, TR_THREADS, smem));
+  if (per_sm < 1) return pe_fail(PE_ECUDA, "pe_mlp: the training kernel does not fit an SM");
+  const int G = sms;  // one CTA per SM: all co-resident, as the grid barriers need
+  if (m->partial_cap < G) {
+    if (m->partial) cudaFree(m->partial);
+    m->partial = nullptr;
+    m->partial_cap = 0;
+    if (cudaMalloc((void**)&m->partial, sizeof(float) * (size_t)NPARAM_L * G) != cudaSuccess) {
+      cudaGetLastError();
+      return pe_fail(PE_ENOMEM, "pe_mlp: partial-gradient allocation failed");
+    }
+    m->partial_cap = G;
   }
-  m->scratch_cap = nb;
-  return PE_OK;
-}
-
-// gradient of the mean loss over samples [0, nb) into m->grad; loss into m->loss_dev
-static pe_status grad_batch(pe_mlp* m, const float* x, const float* t, int nb, float inv_n, cudaStream_t st) {
-  PE_TRY(ensure_scratch(m, nb));
-  float* H1 = m->scratch;
-  float* H2 = H1 + (size_t)H * nb;
-  float* DZ1 = H2 + (size_t)H * nb;
-  float* DZ2 = DZ1 + (size_t)H * nb;
-  float* DY = DZ2 + (size_t)H * nb;
-  float* L = DY + (size_t)2 * nb;
-  fwd_bwd_kernel<<<(nb + 127) / 128, 128, 0, st>>>(m->params, x, t, nb, inv_n, H1, H2, DZ1, DZ2, DY, L);
-  grad_kernel<<<(NPARAM + 127) / 128, 128, 0, st>>>(x, H1, H2, DZ1, DZ2, DY, nb, m->grad);
-  sum_kernel<<<1, 256, 0, st>>>(L, nb, m->loss_dev);
+  PE_CUDA_TRY(cudaMemsetAsync(m->sync, 0, 3 * sizeof(unsigned), st));  // barrier count, generation, error
+  TrainArgs a{};
+  a.params = m->params;
+  a.adam_m = m->adam_m;
+  a.adam_v = m->adam_v;
+  a.partial = m->partial;
+  a.x = x;
+  a.t = t;
+  a.n = n;
+  a.batch = batch;
+  a.steps_per_epoch = steps_per_epoch;
+  a.total = total;
+  a.it0 = it0;
+  a.nsteps = nsteps;
+  a.lr = lr;
+  a.b1 = 0.9f;
+  a.b2 = 0.999f;
+  a.eps = 1e-8f;
+  a.adam_step0 = m->step;
+  a.inv_n = inv_n;
+  a.grad_out = grad_out;
+  a.bar_count = m->sync;
+  a.bar_gen = m->sync + 1;
+  a.err = (int*)(m->sync + 2);
+  void* args[] = {&a};
+  PE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)train_kernel, dim3(G), dim3(TR_THREADS), args, smem, st));
   PE_CUDA_TRY(cudaGetLastError());
+  unsigned herr = 0;
+  PE_CUDA_TRY(cudaMemcpyAsync(&herr, m->sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  PE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr) return pe_fail(PE_ETIMEOUT, "pe_mlp: a grid barrier of the training kernel expired");
+  if (!grad_out) m->step += nsteps;
   return PE_OK;
 }
 
 extern "C" pe_status pe_mlp_gradient(pe_mlp* m, const float* x, const float* t, int32_t n, float* grad_out,
                                      float* loss_out) {
   if (!m || !x || !t || n < 1) return pe_fail(PE_EINVAL, "pe_mlp_gradient: bad arguments");
-  PE_TRY(grad_batch(m, x, t, n, 1.0f / (float)n, nullptr));
+  PE_TRY(run_train(m, x, t, n, n, 1, 1, 0, 1, 0.f, 1.0f / (float)n, m->grad, nullptr));
   if (grad_out) PE_CUDA_TRY(cudaMemcpy(grad_out, m->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
-  if (loss_out) PE_CUDA_TRY(cudaMemcpy(loss_out, m->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
+  if (loss_out) PE_CUDA_TRY(cudaMemcpy(loss_out, m->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost));
   return PE_OK;
 }
+
+// steps per launch of the persistent kernel (about 0.1 s each)
+constexpr int kTrainStepsPerLaunch = 16384;
 
 extern "C" pe_status pe_mlp_train(pe_mlp* m, const float* x, const float* t, int32_t n, int32_t epochs,
                                   int32_t batch, float lr, float* final_loss) {
   if (!m || !x || !t || n < 1 || epochs < 1 || batch < 1) return pe_fail(PE_EINVAL, "pe_mlp_train: bad arguments");
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const int steps_per_epoch = (n + batch - 1) / batch;
-  const int total = epochs * steps_per_epoch;
+  const int64_t total64 = (int64_t)epochs * steps_per_epoch;
+  if (total64 > (int64_t)1 << 30) return pe_fail(PE_EINVAL, "pe_mlp_train: too many steps");
+  const int total = (int)total64;
+  for (int it = 0; it < total; it += kTrainStepsPerLaunch)
+    PE_TRY(run_train(m, x, t, n, batch, steps_per_epoch, total, it, std::min(kTrainStepsPerLaunch, total - it), lr,
+                     0.f, nullptr, nullptr));
+  // mean loss of the final parameters over every sample
+  PE_TRY(run_train(m, x, t, n, n, 1, 1, 0, 1, 0.f, 1.0f / (float)n, m->grad, nullptr));
   float last = 0.f;
-  for (int e = 0; e < epochs; ++e) {
-    for (int sidx = 0; sidx < steps_per_epoch; ++sidx) {
-      const int off = sidx * batch;
-      const int nb = std::min(batch, n - off);
-      // cosine decay of the step size to lr/100
-      const int it = e * steps_per_epoch + sidx;
-      const float cosv = 0.5f * (1.f + cosf(3.14159265f * (float)it / (float)total));
-      const float lr_t = lr * (0.01f + 0.99f * cosv);
-      PE_TRY(grad_batch(m, x + 2 * (size_t)off, t + 2 * (size_t)off, nb, 1.0f / (float)nb, nullptr));
-      m->step += 1;
-      const float bc1 = 1.f - powf(b1, (float)m->step), bc2 = 1.f - powf(b2, (float)m->step);
-      adam_kernel<<<(NPARAM + 255) / 256, 256>>>(m->params, m->grad, m->adam_m, m->adam_v, lr_t, b1, b2, eps, bc1,
-                                                 bc2);
-    }
-  }
-  PE_CUDA_TRY(cudaGetLastError());
-  // loss of the final parameters over the whole set (in batches)
-  double acc = 0.0;
-  for (int off = 0; off < n; off += batch) {
-    const int nb = std::min(batch, n - off);
-    PE_TRY(grad_batch(m, x + 2 * (size_t)off, t + 2 * (size_t)off, nb, 1.0f / (float)n, nullptr));
-    float l = 0.f;
-    PE_CUDA_TRY(cudaMemcpy(&l, m->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
-    acc += l;
-  }
-  last = (float)acc;
+  PE_CUDA_TRY(cudaMemcpy(&last, m->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost));
   to_half_kernel<<<(NPARAM + 255) / 256, 256>>>(m->params, (__half*)m->params16);
   PE_CUDA_TRY(cudaDeviceSynchronize());
   if (final_loss) *final_loss = last;

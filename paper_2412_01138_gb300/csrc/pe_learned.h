@@ -13,8 +13,9 @@ struct pe_mlp {
   float* adam_m = nullptr;
   float* adam_v = nullptr;
   float* loss_dev = nullptr;
-  float* scratch = nullptr;   // per-sample activations of one batch
-  int scratch_cap = 0;
+  float* partial = nullptr;   // per-CTA partial gradients of the training kernel [NPARAM + 1][CTAs]
+  int partial_cap = 0;        // CTAs partial has room for
+  unsigned* sync = nullptr;   // grid barrier of the training kernel: count, generation, error flag
   int64_t step = 0;
 };
 
