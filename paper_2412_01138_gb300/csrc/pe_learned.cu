@@ -104,7 +104,7 @@ __global__ void samples_kernel(int n, const double* __restrict__ lam, const doub
 // Barriers are bounded waits: on expiry the CTA records an error and returns (every other
 // CTA then expires at its next wait); the host reports PE_ETIMEOUT.
 // ---------------------------------------------------------------------------
-constexpr int TR_THREADS = 256;
+constexpr int TR_THREADS = 512;
 constexpr int TR_WARPS = TR_THREADS / 32;
 constexpr int TR_ROUND = 32;          // samples per CTA per round
 constexpr int W2P = H + 1;            // padded row stride of W2 in shared memory (no bank conflicts)
