@@ -166,13 +166,11 @@ __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, 
     Bsp[(((int64_t)g * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
 }
 
-// Stage weights of every mode tile computed and split in one pass, in the A-operand layout of
-// the kernel below (the same arithmetic as the float32 stage-weight table of the SIMT engine:
-// W[k][J] = P_{r(k),J} sum_i (dt b_i)_J Z_k(c_i dt), P_{r,J} the product of the per-axis modal
-// factors), so the float32 table itself is never written or read.
-__global__ void ft_weights_image_kernel(Geom g, StageCols C, int R, int q, const float* __restrict__ axisF,
-                                        const float* __restrict__ coef_b, const double* __restrict__ Z, int K,
-                                        int KP, int64_t tiles, uint4* __restrict__ Asp) {
+// Split stage weights of every mode tile, in the A-operand layout of the kernel below:
+// tile q occupies 3 * 128 * KP * 2 bytes, [term][row r][k] swizzled as above, row r holding
+// W[k][128 q + r] (zero past the last mode and past K).
+__global__ void ft_split_w_kernel(const float* __restrict__ W, int64_t nd, int K, int KP, int64_t tiles,
+                                  uint4* __restrict__ Asp) {
   const int chunks = KP / 8;
   const int64_t total = tiles * FT_ROWS * chunks;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -182,33 +180,11 @@ __global__ void ft_weights_image_kernel(Geom g, StageCols C, int R, int q, const
   const int c = (int)(rest % chunks);
   const int64_t tile = rest / chunks;
   const int64_t J = tile * FT_ROWS + r;
-  const int64_t nd = g.ndof;
   float x[8];
-  if (J < nd) {
-    int j[PE_MAX_D];
-    unflatten(g, J, j);
-    float b[PE_MAX_S];
 #pragma unroll
-    for (int i = 0; i < PE_MAX_S; ++i) b[i] = i < q ? coef_b[(int64_t)i * nd + J] : 0.f;
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int k = 8 * c + jj;
-      float v = 0.f;
-      if (k < K) {
-        const int rt = C.term[k];
-        float P = axisF[(int64_t)R * g.off[0] + (int64_t)rt * g.n[0] + j[0]];
-        for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)rt * g.n[a] + j[a]];
-        float sw = 0.f;
-#pragma unroll
-        for (int i = 0; i < PE_MAX_S; ++i)
-          if (i < q) sw = fmaf(b[i], (float)Z[i * K + k], sw);
-        v = P * sw;
-      }
-      x[jj] = v;
-    }
-  } else {
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) x[jj] = 0.f;
+  for (int j = 0; j < 8; ++j) {
+    const int k = 8 * c + j;
+    x[j] = (J < nd && k < K) ? W[(int64_t)k * nd + J] : 0.f;
   }
   uint4 o[3];
   split8(x, o);
@@ -218,6 +194,7 @@ __global__ void ft_weights_image_kernel(Geom g, StageCols C, int R, int q, const
 }
 
 struct FtArgs {
+  const float* W32;      // stage weights [K][ndof]
   const float* coefF32;  // E_hi [ndof], E_lo [ndof]
   const double* EM;      // exp(-lam M dt) [ndof]
   const double* U;       // U^n at n * ndof
@@ -530,8 +507,8 @@ pe_status fine_tc_prepare(pe_ctx* c) {
                                                                                  ngroups, (uint4*)c->tcB);
   PE_CUDA_TRY(cudaGetLastError());
   const int64_t nsw = tiles * FT_ROWS * (KP / 8);
-  ft_weights_image_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(
-      c->g, c->cols, c->R, c->q, c->axisF32, c->coefF32 + 2 * c->g.ndof, c->Zst, K, KP, tiles, (uint4*)c->tcA);
+  ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
+                                                                           (uint4*)c->tcA);
   PE_CUDA_TRY(cudaGetLastError());
   c->tc_split_ok = true;
   c->launches += 2;
@@ -548,6 +525,7 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   ft_shape(KP, M, N, &G, &NR, &ngroups);
   const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
   FtArgs args{};
+  args.W32 = c->Wst32;
   args.coefF32 = c->coefF32;
   args.EM = c->coefF + (int64_t)(c->q + 1) * c->g.ndof;
   args.U = c->U;

@@ -140,46 +140,6 @@ __global__ void loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, doub
   out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = h * left + h * right;
 }
 
-// Per-axis source factors by the matrix form of the transform, spread over many CTAs (the
-// per-axis loads are a few KB; an FFT per (term, axis) pencil would leave most SMs idle behind
-// float64 latency):  fac[R off_a + r n_a + j] = (sum_k S_a[k][j] L[R off_a + r n_a + k]) / mu^M_a(j)
-// (divide = 0: without the division).  S_a (DST-I, or the DHT of a periodic axis) is symmetric,
-// so the reads S_a[k][j] of consecutive threads j are coalesced.
-constexpr int kFactorRows = 32;
-__global__ void __launch_bounds__(kFactorRows) axis_factor_matrix_kernel(Geom g, int R, const double* __restrict__ S0,
-                                                                         const double* __restrict__ S1,
-                                                                         const double* __restrict__ S2,
-                                                                         const double* __restrict__ loads,
-                                                                         const double* __restrict__ muM,
-                                                                         double* __restrict__ fac,
-                                                                         float* __restrict__ fac32, int divide) {
-  __shared__ double sL[1024];
-  const int a = blockIdx.z, r = blockIdx.y;
-  if (a >= g.d || r >= R) return;
-  const int n = g.n[a];
-  if ((int)(blockIdx.x * blockDim.x) >= n) return;  // uniform over the CTA
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const double* S = a == 0 ? S0 : (a == 1 ? S1 : S2);
-  const int64_t base = (int64_t)R * g.off[a] + (int64_t)r * n;
-  double acc = 0.0;
-  for (int k0 = 0; k0 < n; k0 += 1024) {
-    const int cnt = min(1024, n - k0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) sL[i] = loads[base + k0 + i];
-    __syncthreads();
-    if (j < n) {
-      const double* col = S + (int64_t)k0 * n + j;
-#pragma unroll 8
-      for (int k = 0; k < cnt; ++k) acc = fma(col[(int64_t)k * n], sL[k], acc);
-    }
-  }
-  if (j < n) {
-    const double v = divide ? acc / muM[g.off[a] + j] : acc;
-    fac[base + j] = v;
-    if (fac32) fac32[base + j] = (float)v;
-  }
-}
-
 __global__ void divide_axis_mu_kernel(Geom g, int R, const double* __restrict__ muM, double* __restrict__ x,
                                       float* __restrict__ x32) {
   const int a = blockIdx.z;
@@ -281,13 +241,6 @@ pe_status launch_stage_weights(pe_ctx* c) {
   }
   const int threads = 256;
   const unsigned blocks = (unsigned)((c->g.ndof + threads - 1) / threads);
-  if (c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC && c->forcing_path == PE_FORCING_SEPARABLE) {
-    // the tensor-core engine computes its float32 weights inside the kernel that splits them
-    // into its operand image (fine_tc_prepare); the float64 ones follow on the first float64
-    // sweep (pe_refine)
-    c->Wst_valid = false;
-    return PE_OK;
-  }
   if (c->precision == PE_MIXED) {
     // the float32 fine sweeps need only the float32 weights; the float64 ones follow on the
     // first float64 sweep (pe_refine)
@@ -372,24 +325,14 @@ static pe_status separable_factors_whole(pe_ctx* c, const pe_term* terms, int nt
   Gauss G = make_gauss(c->quad_pts);
   int nmax = 1;
   for (int a = 0; a < c->g.d; ++a) nmax = c->g.n[a] > nmax ? c->g.n[a] : nmax;
-  // 32 nodes per CTA: the loads' float64 exponentials and sines spread over the SMs
-  dim3 grid((nmax + 31) / 32, nterms, c->g.d);
+  dim3 grid((nmax + 127) / 128, nterms, c->g.d);
   double* loads = mode == 0 ? axis_out : c->loads;
-  loads_1d_kernel<<<grid, 32, 0, c->stream>>>(T, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2],
-                                               G, loads);
+  loads_1d_kernel<<<grid, 128, 0, c->stream>>>(T, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2],
+                                                G, loads);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   if (mode == 0) return PE_OK;
   const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
-  if (nmax <= 1024) {
-    dim3 mgrid((nmax + kFactorRows - 1) / kFactorRows, nterms, c->g.d);
-    axis_factor_matrix_kernel<<<mgrid, kFactorRows, 0, c->stream>>>(
-        c->g, nterms, c->S[0], c->g.d > 1 ? c->S[1] : c->S[0], c->g.d > 2 ? c->S[2] : c->S[0], loads, c->muM_axis,
-        axis_out, f32 ? c->axisF32 : nullptr, mode == 1 ? 1 : 0);
-    c->launches += 1;
-    PE_CUDA_TRY(cudaGetLastError());
-    return PE_OK;
-  }
   if (mode == 1) {
     bool done = false;
     PE_TRY(axis_factors_fused(c, nterms, loads, axis_out, f32 ? c->axisF32 : nullptr, &done));
