@@ -257,24 +257,29 @@ def run_batch(pe, args, barrier):
     """512 uneven 2D problems: batched persistent mixed form vs a per-problem float64 loop."""
     probs = I.config4(count=args.batch_count)
     out = {"workload": f"{len(probs)} uneven 2D problems (n 31..511, 16-64 slices x 32 substeps, RK4/RK2)"}
-    with pe.BatchSolver(probs, precision=pe.PE_MIXED) as b:
-        b.autotune(None)
-        for _ in range(max(1, args.warmup)):
-            b.solve(tol=TOL)
-        barrier()
-        t0 = time.perf_counter()
-        infos = [b.solve(tol=TOL) for _ in range(args.steps)]
-        barrier()
-        dt = (time.perf_counter() - t0) / args.steps
-        r, k = b.status()
-    units = infos[-1]["fine_dof_substeps"]
-    out["chosen"] = {"form": "batched persistent launch, CUDA graph per iteration, float32 fine stages",
-                     "time_to_tol_ms": 1e3 * dt, "value": units / dt, "unit": UNIT,
+    for name, eng, form in (("chosen", pe.PE_FINE_TC, "batched persistent launches, CUDA graph per iteration, "
+                                                      "stage contraction on the tensor cores (problem x slice group x "
+                                                      "128-mode tile items), float32 recurrence, float64 residual"),
+                            ("simt", pe.PE_FINE_SIMT, "batched persistent launch, CUDA graph per iteration, float32 "
+                                                      "fine stages on the CUDA cores")):
+        with pe.BatchSolver(probs, precision=pe.PE_MIXED, fine_engine=eng) as b:
+            b.autotune(None)
+            for _ in range(max(1, args.warmup)):
+                b.solve(tol=TOL)
+            barrier()
+            t0 = time.perf_counter()
+            infos = [b.solve(tol=TOL) for _ in range(args.steps)]
+            barrier()
+            dt = (time.perf_counter() - t0) / args.steps
+            r, k = b.status()
+        units = infos[-1]["fine_dof_substeps"]
+        out[name] = {"form": form, "time_to_tol_ms": 1e3 * dt, "value": units / dt, "unit": UNIT,
                      "max_iterations": int(k.max()), "max_residual": float(r.max()),
                      "graph_replays": infos[-1]["graph_replays"], "launch_shape": [infos[-1]["threads"],
                                                                                   infos[-1]["ctas_per_sm"]],
                      "ms_prepare": infos[-1]["ms_prepare"], "ms_iterations": infos[-1]["ms_iterations"],
                      "gpu_launches": infos[-1]["kernel_launches"]}
+    dt = out["chosen"]["time_to_tol_ms"] / 1e3
     # plain: one problem after another, float64, host-driven iteration loop (solvers set up
     # before the timed region, as the batch is)
     solvers = [pe.Solver(prob, precision=pe.PE_FP64) for prob in probs]

@@ -363,8 +363,11 @@ typedef struct {
 
 /* Validate and lay out all problems (one arena per array kind), compute their
  * spectra and DST-I-free 1D factor transforms.  opt->precision selects the fine
- * stages (PE_MIXED: float32 stages, float64 tables/correction/residual).
- * problems: host array of n_problems. */
+ * stages (PE_MIXED: float32 stages, float64 tables/correction/residual);
+ * opt->fine_engine = PE_FINE_TC (PE_MIXED only) runs the stage contraction of every
+ * problem on the tensor cores (work items: problem x slice group x 128-mode tile, one
+ * persistent launch per column padding; every problem needs M a multiple of 16 in
+ * 16..128, else PE_EINVAL).  problems: host array of n_problems. */
 pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe_problem* problems, const pe_options* opt);
 
 /* Pick the persistent fine kernel's launch shape (threads per CTA x CTAs per SM)

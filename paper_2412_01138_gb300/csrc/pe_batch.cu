@@ -553,6 +553,8 @@ pe_status batch_launch_prepare(pe_batch* b) {
         b->d_probs, b->d_mode_items, b->n_mode_items, b->d_cols, b->axisF, b->coefF, b->Z, b->W);
   b_u0_kernel<<<grid_items, 256, 0, b->stream>>>(b->d_probs, b->d_mode_items, b->n_mode_items, b->d_terms, b->axisU0,
                                                  b->U);
+  // the tensor-core engine's split operand images of every problem
+  if (b->fine_engine == PE_FINE_TC) PE_TRY(batch_tc_prepare(b, b->stream));
   // the coarse forcing is iterate-independent and cancels in G(U^{k+1}) - G(U^k): the mixed
   // form evaluates it in float32, the recurrence stays float64
   if (b->precision == PE_MIXED)
@@ -569,6 +571,7 @@ pe_status batch_launch_prepare(pe_batch* b) {
 // One persistent launch per column class present in the batch, each over its own items
 // and counter (counter[c]); grids never exceed the class's item count.
 static pe_status launch_fine(pe_batch* b, cudaStream_t st, int threads, int ctas_per_sm) {
+  if (b->fine_engine == PE_FINE_TC) return batch_tc_fine(b, st);
   const FineItems& fi = threads == 128 ? b->fine128 : b->fine256;
   BatchArrays A{};
   A.W = b->W; A.W32 = b->W32; A.AF = b->AF; A.AF32 = b->AF32;
@@ -590,6 +593,10 @@ static pe_status launch_fine(pe_batch* b, cudaStream_t st, int threads, int ctas
 
 int batch_fine_launches(const pe_batch* b) {
   int k = 0;
+  if (b->fine_engine == PE_FINE_TC) {
+    for (int c = 0; c < 3; ++c) k += b->tc.begin[c + 1] > b->tc.begin[c];
+    return k;
+  }
   for (int c = 0; c < kBatchClasses; ++c) k += b->fine256.begin[c + 1] > b->fine256.begin[c];
   return k;
 }

@@ -33,6 +33,30 @@ struct BProb {
   int64_t oMu;   // muM / ratio: nsum
   int64_t oItems;  // first mode item of this problem
   int nItems;
+  // tensor-core fine engine (pe_options.fine_engine = PE_FINE_TC): column padding KP, slice
+  // groups of TG slices (NR = TG * M rows of the B operand), the operand images' byte offsets
+  int KP, TG, NR, groups;
+  int64_t tiles;  // 128-mode tiles
+  int64_t oTA;    // split stage weights, tiles * 3 * 128 * KP bf16
+  int64_t oTB;    // split time factors, groups * 3 * NR * KP bf16
+};
+
+// A work item of the batched tensor-core fine sweep: slice group g and 128-mode tile t of problem p.
+struct BTcItem {
+  int p, g;
+  int64_t t;
+};
+
+// tensor-core images of one batch and its work items (one list per column padding 16 / 32 / 64)
+struct BatchTc {
+  unsigned char* A = nullptr;  // split stage weights of every problem's tiles
+  unsigned char* B = nullptr;  // split time factors of every problem's slice groups
+  BTcItem* d_items = nullptr;
+  int begin[4] = {};           // items of padding class c (KP = 16 << c): [begin[c], begin[c + 1])
+  int64_t* d_w_prefix = nullptr;  // per problem: first split-weight job (tiles * 128 * KP / 8)
+  int64_t* d_y_prefix = nullptr;  // per problem: first split-time job (groups * NR * KP / 8)
+  int64_t w_jobs = 0, y_jobs = 0;
+  int* err = nullptr;          // error code of an expired pipeline wait (0: none)
 };
 
 // Modes per thread of the mixed-precision fine tile for a problem with K stage columns
@@ -127,6 +151,9 @@ struct pe_batch {
   cudaGraphExec_t graph_exec = nullptr;
   double graph_tol = -1.0;
   int graph_threads = 0, graph_ctas = 0;
+  // tensor-core fine engine (PE_FINE_TC)
+  int fine_engine = PE_FINE_SIMT;
+  BatchTc tc;
   // launch shape of the persistent fine kernel
   int tune_threads = 256, tune_ctas = 2;
   bool tuned = false;
@@ -143,6 +170,11 @@ pe_status batch_launch_prepare(pe_batch* b);
 pe_status batch_enqueue_iteration(pe_batch* b, cudaStream_t st, double tol);
 pe_status batch_time_fine(pe_batch* b, int threads, int ctas, float* ms);
 int batch_fine_launches(const pe_batch* b);  // fine kernels per iteration (one per column class)
+// pe_fine_tc.cu: the batched tensor-core fine sweep
+bool batch_tc_shape(int K, int M, int* KP, int* TG, int* NR);  // false: M unsupported
+pe_status batch_tc_prepare(pe_batch* b, cudaStream_t st);        // split images of every problem
+pe_status batch_tc_fine(pe_batch* b, cudaStream_t st);           // one launch per padding class present
+pe_status batch_tc_status(pe_batch* b);                          // PE_ETIMEOUT if a wait expired
 // pe_batch_fine_*.cu (KC: the column class of the launch)
 pe_status batch_launch_fine_mixed(int KC, const BProb* probs, const FineItem* items, int n_items, const int* active,
                                   int* counter, BatchArrays A, int grid, int threads, size_t smem, cudaStream_t st);

@@ -41,7 +41,8 @@ void free_batch(pe_batch* b) {
                   b->d_factor_jobs, b->d_mu_prefix, b->d_tt_prefix, b->muM, b->ratio, b->coefF, b->coefG,
                   b->coefF32, b->U, b->Fbar, b->axisF, b->axisU0, b->axisF32, b->AF, b->AG,
                   b->AF32, b->partials, b->active, b->kcount, b->resid, b->counter, b->dflags,
-                  b->W, b->W32, b->Z, b->d_cols, b->AG32, b->Z32};
+                  b->W, b->W32, b->Z, b->d_cols, b->AG32, b->Z32, b->tc.A, b->tc.B, b->tc.d_items,
+                  b->tc.d_w_prefix, b->tc.d_y_prefix, b->tc.err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_flags) cudaFreeHost(b->h_flags);
@@ -100,11 +101,16 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
   if (o.precision != PE_FP64 && o.precision != PE_MIXED) return pe_fail(PE_EINVAL, "pe_setup_batch: bad precision");
   if (o.quad_pts == 0) o.quad_pts = 3;
   if (o.quad_pts < 1 || o.quad_pts > 8) return pe_fail(PE_EINVAL, "pe_setup_batch: quad_pts must be in 1..8");
+  if (o.fine_engine != PE_FINE_SIMT && o.fine_engine != PE_FINE_TC)
+    return pe_fail(PE_EINVAL, "pe_setup_batch: bad fine_engine");
+  if (o.fine_engine == PE_FINE_TC && o.precision != PE_MIXED)
+    return pe_fail(PE_EINVAL, "pe_setup_batch: PE_FINE_TC needs PE_MIXED");
 
   pe_batch* b = new (std::nothrow) pe_batch();
   if (!b) return pe_fail(PE_ENOMEM, "pe_setup_batch: host allocation failed");
   b->P = n_problems;
   b->precision = o.precision;
+  b->fine_engine = o.fine_engine;
   b->quad_pts = o.quad_pts;
   b->user_stream = (cudaStream_t)o.cuda_stream;
   b->gauss = make_gauss(o.quad_pts);
@@ -125,8 +131,8 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
 
   // ---- validate and lay out every problem --------------------------------
   int64_t oU = 0, oS = 0, oCF = 0, oCG = 0, oAx = 0, oAxU = 0, oAF = 0, oAF32 = 0, oAG = 0, oMu = 0, oItems = 0;
-  int64_t oW = 0, oZ = 0;
-  std::vector<int64_t> mu_prefix, tt_prefix;
+  int64_t oW = 0, oZ = 0, oTA = 0, oTB = 0, wjobs = 0, yjobs = 0;
+  std::vector<int64_t> mu_prefix, tt_prefix, w_prefix, y_prefix;
   std::vector<short> cols;
   int64_t tt = 0;
   uint64_t sig = 0xcbf29ce484222325ull;
@@ -235,6 +241,24 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
     B.oItems = oItems;
     B.nItems = (int)((ndof + 255) / 256);
     oItems += B.nItems;
+    if (b->fine_engine == PE_FINE_TC) {
+      // tensor-core operand images: split stage weights per 128-mode tile, split time factors
+      // per slice group, each in the byte layout the kernel copies into shared memory
+      if (!batch_tc_shape(B.K, B.M, &B.KP, &B.TG, &B.NR)) {
+        st = pe_fail(PE_EINVAL, tag + "PE_FINE_TC needs M a multiple of 16 in 16..128");
+        break;
+      }
+      B.groups = (B.N + B.TG - 1) / B.TG;
+      B.tiles = (ndof + 127) / 128;
+      B.oTA = oTA;
+      oTA += B.tiles * 3 * 128 * B.KP * 2;
+      B.oTB = oTB;
+      oTB += (int64_t)B.groups * 3 * B.NR * B.KP * 2;
+      w_prefix.push_back(wjobs);
+      wjobs += B.tiles * 128 * (B.KP / 8);
+      y_prefix.push_back(yjobs);
+      yjobs += (int64_t)B.groups * B.NR * (B.KP / 8);
+    }
     sig = fnv1a(sig, &B.g, sizeof(B.g));
     sig = fnv1a(sig, &B.N, sizeof(int) * 6);
   }
@@ -242,7 +266,7 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
     free_batch(b);
     return st;
   }
-  b->signature = fnv1a(sig, &b->precision, sizeof(int));
+  b->signature = fnv1a(fnv1a(sig, &b->precision, sizeof(int)), &b->fine_engine, sizeof(int));
   b->mu_total = oMu;
   b->tt_total = tt;
 
@@ -273,6 +297,15 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
   if (st == PE_OK) st = balloc(&b->resid, (size_t)b->P);
   if (st == PE_OK) st = balloc(&b->counter, (size_t)kBatchClasses);
   if (st == PE_OK) st = balloc(&b->dflags, 2);
+  if (st == PE_OK && b->fine_engine == PE_FINE_TC) {
+    st = balloc(&b->tc.A, (size_t)oTA);
+    if (st == PE_OK) st = balloc(&b->tc.B, (size_t)oTB);
+    if (st == PE_OK) st = balloc(&b->tc.err, 1);
+    if (st == PE_OK && cudaMemset(b->tc.err, 0, sizeof(int)) != cudaSuccess)
+      st = pe_cuda_fail(cudaGetLastError(), "pe_setup_batch: error flag");
+    b->tc.w_jobs = wjobs;
+    b->tc.y_jobs = yjobs;
+  }
   if (st == PE_OK && cudaMallocHost((void**)&b->h_flags, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     st = pe_fail(PE_ENOMEM, "pe_setup_batch: pinned allocation failed");
@@ -309,6 +342,25 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
     if (st == PE_OK) st = upload(&b->d_cols, cols, b->stream);
     if (st == PE_OK) st = build_fine_items(b, 128, &b->fine128);
     if (st == PE_OK) st = build_fine_items(b, 256, &b->fine256);
+    if (st == PE_OK && b->fine_engine == PE_FINE_TC) {
+      // items per column padding (16, 32, 64), each problem's (slice group, tile) pairs
+      // group-major, so that a CTA's consecutive items share the group's B operand
+      std::vector<BTcItem> titems;
+      for (int cls = 0; cls < 3; ++cls) {
+        b->tc.begin[cls] = (int)titems.size();
+        for (int p = 0; p < b->P; ++p) {
+          const BProb& B = b->probs[p];
+          if (B.KP != (16 << cls)) continue;
+          for (int g = 0; g < B.groups; ++g)
+            for (int64_t t = 0; t < B.tiles; ++t) titems.push_back(BTcItem{p, g, t});
+        }
+      }
+      if (titems.size() > (size_t)INT32_MAX) st = pe_fail(PE_EINVAL, "batch: too many tensor-core work items");
+      b->tc.begin[3] = (int)titems.size();
+      if (st == PE_OK) st = upload(&b->tc.d_items, titems, b->stream);
+      if (st == PE_OK) st = upload(&b->tc.d_w_prefix, w_prefix, b->stream);
+      if (st == PE_OK) st = upload(&b->tc.d_y_prefix, y_prefix, b->stream);
+    }
   }
   if (st == PE_OK) st = batch_set_attributes(b);
   if (st == PE_OK) st = batch_launch_axis_tables(b);
@@ -382,6 +434,10 @@ float ms_between(cudaEvent_t a, cudaEvent_t b) {
 
 extern "C" pe_status pe_batch_autotune(pe_batch* b, const char* cache_path) {
   if (!b) return pe_fail(PE_EINVAL, "pe_batch_autotune: NULL batch");
+  if (b->fine_engine == PE_FINE_TC) {  // one CTA of 288 threads per SM: no launch shape to choose
+    b->tuned = true;
+    return PE_OK;
+  }
   cudaDeviceProp prop;
   int dev = 0;
   PE_CUDA_TRY(cudaGetDevice(&dev));
@@ -462,6 +518,7 @@ extern "C" pe_status pe_batch_solve(pe_batch* b, double tol, pe_batch_result* re
     b->launches += batch_fine_launches(b) + 2;  // graph: fine kernels, correction, reduction
     if (b->h_flags[1]) {
       b->have_problem = false;
+      if (b->fine_engine == PE_FINE_TC) PE_TRY(batch_tc_status(b));
       return pe_fail(PE_ENONFINITE, "batch: a problem's Parareal residual is not finite");
     }
     if (b->h_flags[0] == 0 || replays >= maxN) break;
@@ -491,8 +548,8 @@ extern "C" pe_status pe_batch_solve(pe_batch* b, double tol, pe_batch_result* re
     res->ms_prepare = ms_between(ev[0], ev[1]);
     res->ms_iterations = ms_between(ev[1], ev[2]);
     res->kernel_launches = b->launches;
-    res->threads = b->tune_threads;
-    res->ctas_per_sm = b->tune_ctas;
+    res->threads = b->fine_engine == PE_FINE_TC ? 288 : b->tune_threads;
+    res->ctas_per_sm = b->fine_engine == PE_FINE_TC ? 1 : b->tune_ctas;
   }
   for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
   return PE_OK;

@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "pe_batch.h"
 #include "pe_internal.h"
 #include "pe_tc_common.cuh"
 
@@ -449,6 +450,344 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched form: the same engine over the work items (problem p, slice group g, mode tile t)
+// of many problems at once, one persistent launch per column padding KP.  Each item reads
+// its problem's record (sizes, slice-group shape NR = TG * M, arena offsets); the B operand
+// (the group's split time factors) is reloaded when (p, g) changes, the A operand (the tile's
+// split stage weights) every item through the same ring; the MMA instruction takes the item's
+// N = NR.  Items of converged problems run too (the batched correction leaves those problems
+// unchanged), which keeps both pipeline sides' item sequences fixed inside the captured graph.
+// ---------------------------------------------------------------------------
+struct BtcArgs {
+  const BProb* probs;
+  const BTcItem* items;
+  int64_t n_items;
+  const float* coefF32;  // arena: E_hi, E_lo at oCF
+  const double* coefF;   // arena: exp(-lam M dt) at oCF + (q + 1) ndof
+  const double* U;       // arena at oU
+  double* Fbar;          // arena at oS
+  const unsigned char* A;
+  const unsigned char* B;
+  int* err;
+};
+
+template <int KP>
+__global__ void __launch_bounds__(FT_THREADS, 1) b_fine_tc_kernel(BtcArgs a) {
+  constexpr int A_TERM = FT_ROWS * KP * 2;
+  constexpr int A_BYTES = 3 * A_TERM;
+  constexpr int NRMAX = ft_rows_max(KP);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t fullA[FT_ABUF], emptyA[FT_ABUF], fullD[2], emptyD[2], fullB, freeB, drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sB = smem;
+  unsigned char* sA = smem + 3 * NRMAX * KP * 2;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * a.n_items / gridDim.x;
+  const int64_t i1 = (int64_t)(blockIdx.x + 1) * a.n_items / gridDim.x;
+  constexpr uint32_t ncols = 2 * NRMAX;  // 512 or 256: a power of two
+  volatile int* fail = &s_fail;
+  auto set_fail = [&](int code) {
+    atomicExch(a.err, code);
+    *fail = 1;
+    a.Fbar[0] = __longlong_as_double(0x7ff8000000000000LL);
+  };
+  if (tid == 0) {
+    for (int b = 0; b < FT_ABUF; ++b) {
+      mbar_init(&fullA[b], 1);
+      mbar_init(&emptyA[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&fullD[b], 1);
+      mbar_init(&emptyD[b], FT_WORKERS / 32);
+    }
+    mbar_init(&fullB, 1);
+    mbar_init(&freeB, 1);
+    mbar_init(&drain, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == FT_WORKERS / 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp < FT_WORKERS / 32) {
+    const int r = tid & (FT_ROWS - 1), h = tid >> 7, lane = tid & 31;
+    constexpr int UP = 2;
+    struct Pre {
+      float eh, el;
+      double em, u[UP];
+    };
+    Pre P0, P1;
+    auto load_epi = [&](Pre& P, int64_t i) {
+      const BTcItem it = a.items[i];
+      const BProb& B = a.probs[it.p];
+      const int64_t nd = B.g.ndof, J = it.t * FT_ROWS + r;
+      const bool ok = J < nd;
+      P.eh = ok ? a.coefF32[B.oCF + J] : 0.f;
+      P.el = ok ? a.coefF32[B.oCF + nd + J] : 0.f;
+      P.em = ok ? a.coefF[B.oCF + (int64_t)(B.q + 1) * nd + J] : 0.0;
+#pragma unroll
+      for (int t = 0; t < UP; ++t) {
+        const int s = h + 2 * t;
+        const int64_t n = (int64_t)it.g * B.TG + s;
+        P.u[t] = (ok && s < B.TG && n < B.N) ? a.U[B.oU + n * nd + J] : 0.0;
+      }
+    };
+    auto step = [&](int64_t i, const Pre& cur, Pre& nxt) -> bool {
+      const int j = (int)(i - i0);
+      if (i + 1 < i1) load_epi(nxt, i + 1);
+      if (!mbar_wait(&fullD[j & 1], (uint32_t)((j >> 1) & 1))) {
+        set_fail(5);
+        return false;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const BTcItem it = a.items[i];
+      const BProb& B = a.probs[it.p];
+      const int M = B.M, TG = B.TG, N = B.N;
+      const int64_t nd = B.g.ndof;
+      float e2h, e2l, e4h, e4l;
+      df_square(cur.eh, cur.el, e2h, e2l);
+      df_square(e2h, e2l, e4h, e4l);
+      const float eh = cur.eh, e2 = e2h, e3 = e2h * eh;
+      const int64_t J = it.t * FT_ROWS + r;
+      const bool ok = J < nd;
+      const uint32_t row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((j & 1) * NRMAX);
+      auto chain4 = [&](float& w, float x0, float x1, float x2, float x3) {
+        const float bsum = fmaf(e3, x0, fmaf(e2, x1, fmaf(eh, x2, x3)));
+        w = fmaf(e4h, w, fmaf(e4l, w, bsum));
+      };
+      auto finish = [&](bool pre, double upre, int s, float w) {
+        const int64_t n = (int64_t)it.g * TG + s;
+        if (ok && n < N) {
+          const double u = pre ? upre : a.U[B.oU + n * nd + J];
+          a.Fbar[B.oS + n * nd + J] = fma(cur.em, u, (double)w);
+        }
+      };
+#pragma unroll 1
+      for (int pq = 0; pq < 8; ++pq) {
+        const int s0 = h + 4 * pq, s1 = s0 + 2;
+        if (s0 >= TG) break;
+        const bool two = s1 < TG;
+        float w0 = 0.f, w1 = 0.f;
+        int m0 = 0;
+        for (; m0 + 32 <= M; m0 += 32) {
+          float v0[32], v1[32];
+          tmem_ld32(row + (uint32_t)(s0 * M + m0), v0);
+          if (two) tmem_ld32(row + (uint32_t)(s1 * M + m0), v1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            chain4(w0, v0[e], v0[e + 1], v0[e + 2], v0[e + 3]);
+            if (two) chain4(w1, v1[e], v1[e + 1], v1[e + 2], v1[e + 3]);
+          }
+        }
+        if (m0 < M) {
+          float v0[16], v1[16];
+          tmem_ld16(row + (uint32_t)(s0 * M + m0), v0);
+          if (two) tmem_ld16(row + (uint32_t)(s1 * M + m0), v1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; e += 4) {
+            chain4(w0, v0[e], v0[e + 1], v0[e + 2], v0[e + 3]);
+            if (two) chain4(w1, v1[e], v1[e + 1], v1[e + 2], v1[e + 3]);
+          }
+        }
+        finish(pq == 0, cur.u[0], s0, w0);
+        if (two) finish(pq == 0, cur.u[1], s1, w1);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyD[j & 1]);
+      return true;
+    };
+    if (i0 < i1) load_epi(P0, i0);
+    for (int64_t i = i0; i < i1; i += 2) {
+      if (*fail || !step(i, P0, P1)) break;
+      if (i + 1 < i1 && (*fail || !step(i + 1, P1, P0))) break;
+    }
+  } else if (tid == FT_WORKERS) {
+    const int ta[6] = {2, 1, 0, 1, 0, 0}, tb[6] = {0, 1, 2, 0, 1, 0};
+    const int n = (int)(i1 - i0);
+    auto load_A = [&](int jj) {
+      const int b = jj % FT_ABUF;
+      const BTcItem it = a.items[i0 + jj];
+      const unsigned char* src = a.A + a.probs[it.p].oTA + it.t * (int64_t)A_BYTES;
+      mbar_expect_tx(&fullA[b], (uint32_t)A_BYTES);
+      for (int off = 0; off < A_BYTES; off += FT_CHUNK)
+        bulk_g2s(sA + b * A_BYTES + off, src + off, (uint32_t)(A_BYTES - off < FT_CHUNK ? A_BYTES - off : FT_CHUNK),
+                 &fullA[b]);
+    };
+    int nl = 0;
+    for (; nl < FT_ABUF && nl < n; ++nl) load_A(nl);
+    int j = 0;
+    int cur_p = -1, cur_g = -1, nB = 0;
+    bool issued = false;
+    for (; j < n; ++j) {
+      const BTcItem it = a.items[i0 + j];
+      const BProb& B = a.probs[it.p];
+      const int NR = B.NR;
+      if (it.p != cur_p || it.g != cur_g) {
+        if (cur_p >= 0) {
+          mma_commit(&freeB);
+          if (!mbar_wait(&freeB, (uint32_t)((nB - 1) & 1))) {
+            set_fail(6);
+            break;
+          }
+        }
+        const int B_BYTES = 3 * NR * KP * 2;
+        mbar_expect_tx(&fullB, (uint32_t)B_BYTES);
+        const unsigned char* src = a.B + B.oTB + (int64_t)it.g * B_BYTES;
+        for (int off = 0; off < B_BYTES; off += FT_CHUNK)
+          bulk_g2s(sB + off, src + off, (uint32_t)(B_BYTES - off < FT_CHUNK ? B_BYTES - off : FT_CHUNK), &fullB);
+        if (!mbar_wait(&fullB, (uint32_t)(nB & 1))) {
+          set_fail(7);
+          break;
+        }
+        ++nB;
+        cur_p = it.p;
+        cur_g = it.g;
+      }
+      const int b = j % FT_ABUF;
+      if (!mbar_wait(&fullA[b], (uint32_t)((j / FT_ABUF) & 1))) {
+        set_fail(8);
+        break;
+      }
+      if (j >= 2 && !mbar_wait(&emptyD[j & 1], (uint32_t)(((j >> 1) - 1) & 1))) {
+        set_fail(9);
+        break;
+      }
+      if (*fail) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = instr_desc_bf16(FT_ROWS, NR);
+      const uint32_t a0 = smem_u32(sA + b * A_BYTES), b0 = smem_u32(sB);
+      const uint32_t d = tmem + (uint32_t)((j & 1) * NRMAX);
+      bool first = true;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+#pragma unroll
+        for (int ks = 0; ks < KP / 16; ++ks) {
+          const uint64_t da = smem_desc_swz(a0 + ta[q] * A_TERM + 32 * ks, KP);
+          const uint64_t db = smem_desc_swz(b0 + tb[q] * (NR * KP * 2) + 32 * ks, KP);
+          mma_bf16(d, da, db, idesc, first ? 0u : 1u);
+          first = false;
+        }
+      }
+      mma_commit(&fullD[j & 1]);
+      mma_commit(&emptyA[b]);
+      issued = true;
+      if (j >= 1 && j + FT_ABUF - 1 < n) {
+        if (!mbar_wait(&emptyA[(j - 1) % FT_ABUF], (uint32_t)(((j - 1) / FT_ABUF) & 1))) {
+          set_fail(11);
+          break;
+        }
+        load_A(j + FT_ABUF - 1);
+        ++nl;
+      }
+    }
+    if (*fail)
+      for (int jj = j; jj < nl; ++jj) mbar_wait(&fullA[jj % FT_ABUF], (uint32_t)((jj / FT_ABUF) & 1));
+    if (issued) {
+      mma_commit(&drain);
+      if (!mbar_wait(&drain, 0)) set_fail(10);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == FT_WORKERS / 32) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+// Split images of every problem of a batch.  Job index e of a prefix table: the problem whose
+// first job is the largest prefix <= e (binary search), then that problem's local job.
+__device__ inline int prefix_owner(const int64_t* __restrict__ prefix, int P, int64_t e) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void b_split_time_kernel(const BProb* __restrict__ probs, const int64_t* __restrict__ prefix, int P,
+                                    int64_t total, const float* __restrict__ AF32, unsigned char* __restrict__ Bimg) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int p = prefix_owner(prefix, P, e);
+  const BProb& B = probs[p];
+  const int KP = B.KP, chunks = KP / 8, NR = B.NR, M = B.M, K = B.K, KC = (K + 3) / 4 * 4;
+  const int64_t le = e - prefix[p];
+  const int c = (int)(le % chunks);
+  const int64_t gr = le / chunks;
+  const int rr = (int)(gr % NR);
+  const int g = (int)(gr / NR);
+  const int sl = rr / M, m = rr - sl * M, n = g * B.TG + sl;
+  float x[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int k = 8 * c + jj;
+    x[jj] = (n < B.N && k < K) ? AF32[B.oAF32 + ((int64_t)n * M + m) * KC + k] : 0.f;
+  }
+  uint4 o[3];
+  split8(x, o);
+  const int64_t term = (int64_t)NR * KP * 2;
+  uint4* dst = reinterpret_cast<uint4*>(Bimg + B.oTB);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) dst[(((int64_t)g * 3 + t) * term + ft_swz((int64_t)rr * KP * 2 + c * 16, KP)) / 16] = o[t];
+}
+
+__global__ void b_split_w_kernel(const BProb* __restrict__ probs, const int64_t* __restrict__ prefix, int P,
+                                 int64_t total, const float* __restrict__ W32, unsigned char* __restrict__ Aimg) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int p = prefix_owner(prefix, P, e);
+  const BProb& B = probs[p];
+  const int KP = B.KP, chunks = KP / 8, K = B.K;
+  const int64_t nd = B.g.ndof;
+  const int64_t le = e - prefix[p];
+  const int rr = (int)(le % FT_ROWS);
+  const int64_t rest = le / FT_ROWS;
+  const int c = (int)(rest % chunks);
+  const int64_t tile = rest / chunks;
+  const int64_t J = tile * FT_ROWS + rr;
+  float x[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int k = 8 * c + jj;
+    x[jj] = (J < nd && k < K) ? W32[B.oW + (int64_t)k * nd + J] : 0.f;
+  }
+  uint4 o[3];
+  split8(x, o);
+  const int64_t term = (int64_t)FT_ROWS * KP * 2;
+  uint4* dst = reinterpret_cast<uint4*>(Aimg + B.oTA);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) dst[((tile * 3 + t) * term + ft_swz((int64_t)rr * KP * 2 + c * 16, KP)) / 16] = o[t];
+}
+
+template <int KP>
+pe_status btc_launch(const BtcArgs& args, int grid, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(b_fine_tc_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft_smem_bytes(KP));
+  });
+  if (attr != cudaSuccess) return pe_cuda_fail(attr, "batched fine sweep (tensor cores): shared-memory attribute");
+  b_fine_tc_kernel<KP><<<grid, FT_THREADS, ft_smem_bytes(KP), st>>>(args);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
 template <int KP>
 pe_status ft_launch(const FtArgs& args, int grid, cudaStream_t st) {
   static std::once_flag once;
@@ -564,6 +903,65 @@ pe_status fine_tc_status(pe_ctx* c) {
   if (herr != 0) {
     cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream);
     return pe_fail(PE_ETIMEOUT, "fine sweep (tensor cores): a pipeline wait expired (code " + std::to_string(herr) + ")");
+  }
+  return PE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched form (pe_batch with fine_engine = PE_FINE_TC)
+// ---------------------------------------------------------------------------
+bool batch_tc_shape(int K, int M, int* KP, int* TG, int* NR) {
+  if (!fine_tc_supported(M) || K < 1 || K > 64) return false;
+  *KP = ft_kpad(K);
+  int ng = 0;
+  ft_shape(*KP, M, 1, TG, NR, &ng);
+  return true;
+}
+
+pe_status batch_tc_prepare(pe_batch* b, cudaStream_t st) {
+  const unsigned threads = 256;
+  if (b->tc.y_jobs > 0)
+    b_split_time_kernel<<<(unsigned)((b->tc.y_jobs + threads - 1) / threads), threads, 0, st>>>(
+        b->d_probs, b->tc.d_y_prefix, b->P, b->tc.y_jobs, b->AF32, b->tc.B);
+  if (b->tc.w_jobs > 0)
+    b_split_w_kernel<<<(unsigned)((b->tc.w_jobs + threads - 1) / threads), threads, 0, st>>>(
+        b->d_probs, b->tc.d_w_prefix, b->P, b->tc.w_jobs, b->W32, b->tc.A);
+  b->launches += 2;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+pe_status batch_tc_fine(pe_batch* b, cudaStream_t st) {
+  for (int cls = 0; cls < 3; ++cls) {
+    const int n = b->tc.begin[cls + 1] - b->tc.begin[cls];
+    if (n == 0) continue;
+    BtcArgs args{};
+    args.probs = b->d_probs;
+    args.items = b->tc.d_items + b->tc.begin[cls];
+    args.n_items = n;
+    args.coefF32 = b->coefF32;
+    args.coefF = b->coefF;
+    args.U = b->U;
+    args.Fbar = b->Fbar;
+    args.A = b->tc.A;
+    args.B = b->tc.B;
+    args.err = b->tc.err;
+    const int grid = std::min(n, b->sm_count);
+    if (cls == 0) PE_TRY(btc_launch<16>(args, grid, st));
+    else if (cls == 1) PE_TRY(btc_launch<32>(args, grid, st));
+    else PE_TRY(btc_launch<64>(args, grid, st));
+  }
+  return PE_OK;
+}
+
+pe_status batch_tc_status(pe_batch* b) {
+  if (!b->tc.err) return PE_OK;
+  int herr = 0;
+  PE_CUDA_TRY(cudaMemcpy(&herr, b->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr != 0) {
+    cudaMemset(b->tc.err, 0, sizeof(int));
+    return pe_fail(PE_ETIMEOUT, "batched fine sweep (tensor cores): a pipeline wait expired (code " +
+                                    std::to_string(herr) + ")");
   }
   return PE_OK;
 }

@@ -446,7 +446,8 @@ def probe_wait_timeout(budget_cycles: int, stream=None) -> None:
 class BatchSolver:
     """One pe_batch: many independent problems advanced by shared persistent launches."""
 
-    def __init__(self, probs: Sequence["_in.Problem"], precision: int = PE_MIXED, stream=None):
+    def __init__(self, probs: Sequence["_in.Problem"], precision: int = PE_MIXED, stream=None,
+                 fine_engine: int = PE_FINE_SIMT):
         self.probs = list(probs)
         self._lib = lib()
         arr = (pe_problem * len(self.probs))()
@@ -469,7 +470,7 @@ class BatchSolver:
             q.u0 = pe_field(PE_FIELD_TERMS_SEPARABLE, len(p.u0), C.cast(tu, C.POINTER(pe_term)), None)
             q.forcing = pe_forcing(len(p.forcing), C.cast(tf, C.POINTER(pe_term)))
         opt = pe_options(precision, PE_DST_AUTO, self.probs[0].quad_pts, 0, stream_handle(stream),
-                         PE_FORCING_SEPARABLE, 0, 0, PE_FINE_SIMT, 0, 0, REDUCE_FN(), None, 0)
+                         PE_FORCING_SEPARABLE, 0, 0, fine_engine, 0, 0, REDUCE_FN(), None, 0)
         ctx = C.c_void_p()
         _check(self._lib.pe_setup_batch(C.byref(ctx), len(self.probs), arr, C.byref(opt)))
         self.ctx = ctx
