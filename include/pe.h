@@ -428,6 +428,11 @@ pe_status pe_learned_samples(pe_ctx* ctx, int32_t n, const double* lam, const do
 /* Attach (m != NULL) or detach the learned correction; takes effect at the next pe_set_problem / pe_solve.
  * The network must outlive its use by the context. */
 pe_status pe_set_learned(pe_ctx* ctx, const pe_mlp* m);
+/* Attach (m != NULL) or detach the learned coarse correction for every problem of the batch
+ * (G'(v) = G(v) + delta^ per problem, as pe_set_learned does for one context; band tables of
+ * 2048 log-spaced bands per problem and sine term, the learned term summed inside the batched
+ * coarse sweep); takes effect at the next pe_batch_solve.  The network must outlive its use. */
+pe_status pe_batch_set_learned(pe_batch* b, const pe_mlp* m);
 
 /*
  * pe_dst_tc -- the same orthonormal tensor DST-I for float32 data on the tensor cores:

@@ -289,11 +289,23 @@ constexpr int kPF = 4;
 constexpr int kCoarseRB = (PE_BATCH_MAX_TERMS + 3) / 4 * 4;
 constexpr int kCoarseSmem = 16 * 1024;  // bytes of staged time factors per CTA
 
-template <typename TF>
+// LEARN: the learned term of G' = G + delta^ is added per slice, sum_r (A_r cos_{r,n} + B_r sin_{r,n})
+// with A_r = P_{r,J} amp_r Im K^, B_r = P_{r,J} amp_r Re K^ (K^ interpolated linearly in
+// log(lam dT) between the problem's band centres), as the single-problem coarse sweep does.
+struct BLearn {
+  const double* ratio;    // per-axis mu^K / mu^M (lam = D sum_a ratio)
+  const pe_term* terms;
+  const double* Kt;       // band tables
+  const float2* Ph;       // phase tables
+  int NB;
+};
+
+template <typename TF, bool LEARN>
 __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__ probs,
                                                        const ModeItem* __restrict__ items, int n_items,
                                                        const double* __restrict__ axisF, const TF* __restrict__ AG,
-                                                       const double* __restrict__ coefG, double* __restrict__ U) {
+                                                       const double* __restrict__ coefG, double* __restrict__ U,
+                                                       BLearn L) {
   constexpr int RB = kCoarseRB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TF* sA = reinterpret_cast<TF*>(smem_raw);  // [chunk * p][RB]
@@ -312,9 +324,37 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
     for (int i = 0; i < PE_MAX_S; ++i) b[i] = TF(0);
     double E = 0.0, c = 0.0;
     const double* cg = coefG + B.oCG;
+    float LA[LEARN ? kCoarseRB : 1], LB[LEARN ? kCoarseRB : 1];
+#pragma unroll
+    for (int r = 0; r < (LEARN ? kCoarseRB : 1); ++r) {
+      LA[r] = 0.f;
+      LB[r] = 0.f;
+    }
     if (on) {
       int j[PE_MAX_D];
       unflatten(B.g, J, j);
+      if constexpr (LEARN) {
+        double s = 0.0;
+        for (int a = 0; a < B.g.d; ++a) s += L.ratio[B.oMu + B.g.off[a] + j[a]];
+        double pos = (log(B.D * s * B.dT) - B.lloglo) / B.lstep;
+        pos = fmin(fmax(pos, 0.0), (double)(L.NB - 1) - 1e-9);
+        const int b0 = (int)pos;
+        const double f = pos - (double)b0;
+#pragma unroll
+        for (int r = 0; r < kCoarseRB; ++r) {
+          if (r < R && L.terms[B.tf + r].tkind == PE_T_SIN) {
+            double Pd = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
+            for (int a = 1; a < B.g.d; ++a)
+              Pd *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+            const double* k0 = L.Kt + B.oKt + 2 * ((int64_t)r * L.NB + b0);
+            const double Kre = (1.0 - f) * k0[0] + f * k0[2];
+            const double Kim = (1.0 - f) * k0[1] + f * k0[3];
+            const double cc = Pd * L.terms[B.tf + r].amp;
+            LA[r] = (float)(cc * Kim);
+            LB[r] = (float)(cc * Kre);
+          }
+        }
+      }
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         if (r < R) {
@@ -368,7 +408,19 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
               acc = fma(b[i], gi, acc);
             }
           }
-          c = fma(E, c, (double)acc);
+          double gn = (double)acc;
+          if constexpr (LEARN) {
+            float dl = 0.f;
+            const float2* ph = L.Ph + B.oPh + n0 + n;
+#pragma unroll
+            for (int r = 0; r < kCoarseRB; ++r)
+              if (r < R) {
+                const float2 e = __ldg(ph + (int64_t)r * N);
+                dl = fmaf(LA[r], e.x, fmaf(LB[r], e.y, dl));
+              }
+            gn += (double)dl;
+          }
+          c = fma(E, c, gn);
           U[B.oU + (int64_t)(n0 + n + 1) * nd + J] = c;
         }
       }
@@ -557,12 +609,28 @@ pe_status batch_launch_prepare(pe_batch* b) {
   if (b->fine_engine == PE_FINE_TC) PE_TRY(batch_tc_prepare(b, b->stream));
   // the coarse forcing is iterate-independent and cancels in G(U^{k+1}) - G(U^k): the mixed
   // form evaluates it in float32, the recurrence stays float64
-  if (b->precision == PE_MIXED)
-    b_coarse_kernel<float><<<grid_items, 256, kCoarseSmem, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U);
+  // learned correction: band and phase tables first, the term summed inside the coarse sweep
+  BLearn L{};
+  if (b->mlp) {
+    PE_TRY(batch_learned_tables(b, b->stream));
+    L.ratio = b->ratio;
+    L.terms = b->d_terms;
+    L.Kt = b->Kt;
+    L.Ph = b->Ph;
+    L.NB = kBatchLearnedBands;
+  }
+  if (b->precision == PE_MIXED && b->mlp)
+    b_coarse_kernel<float, true><<<grid_items, 256, kCoarseSmem, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, L);
+  else if (b->precision == PE_MIXED)
+    b_coarse_kernel<float, false><<<grid_items, 256, kCoarseSmem, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, L);
+  else if (b->mlp)
+    b_coarse_kernel<double, true><<<grid_items, 256, kCoarseSmem, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, L);
   else
-    b_coarse_kernel<double><<<grid_items, 256, kCoarseSmem, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U);
+    b_coarse_kernel<double, false><<<grid_items, 256, kCoarseSmem, b->stream>>>(
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, L);
   b->launches += 5;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;

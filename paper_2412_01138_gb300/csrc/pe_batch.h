@@ -39,6 +39,11 @@ struct BProb {
   int64_t tiles;  // 128-mode tiles
   int64_t oTA;    // split stage weights, tiles * 3 * 128 * KP bf16
   int64_t oTB;    // split time factors, groups * 3 * NR * KP bf16
+  // learned coarse correction (pe_batch_set_learned): band table K^[r][band] (re, im) at oKt,
+  // bands log-spaced in log(lam dT) from lloglo by lstep; phase table (cos, sin)(w_r T_n + phi_r)
+  // [r][n] at oPh
+  int64_t oKt, oPh;
+  double lloglo, lstep;
 };
 
 // A work item of the batched tensor-core fine sweep: slice group g and 128-mode tile t of problem p.
@@ -151,6 +156,13 @@ struct pe_batch {
   cudaGraphExec_t graph_exec = nullptr;
   double graph_tol = -1.0;
   int graph_threads = 0, graph_ctas = 0;
+  // learned coarse correction (pe_batch_set_learned)
+  const struct pe_mlp* mlp = nullptr;
+  double* Kt = nullptr;       // band tables of every problem
+  float2* Ph = nullptr;       // phase tables of every problem
+  int64_t* d_kt_prefix = nullptr;  // per problem: first band-table job (R * bands)
+  int64_t* d_ph_prefix = nullptr;  // per problem: first phase-table job (R * N)
+  int64_t kt_jobs = 0, ph_jobs = 0;
   // tensor-core fine engine (PE_FINE_TC)
   int fine_engine = PE_FINE_SIMT;
   BatchTc tc;
@@ -170,6 +182,9 @@ pe_status batch_launch_prepare(pe_batch* b);
 pe_status batch_enqueue_iteration(pe_batch* b, cudaStream_t st, double tol);
 pe_status batch_time_fine(pe_batch* b, int threads, int ctas, float* ms);
 int batch_fine_launches(const pe_batch* b);  // fine kernels per iteration (one per column class)
+// pe_learned.cu: band and phase tables of the learned correction for every problem of a batch
+constexpr int kBatchLearnedBands = 2048;
+pe_status batch_learned_tables(pe_batch* b, cudaStream_t st);
 // pe_fine_tc.cu: the batched tensor-core fine sweep
 bool batch_tc_shape(int K, int M, int* KP, int* TG, int* NR);  // false: M unsupported
 pe_status batch_tc_prepare(pe_batch* b, cudaStream_t st);        // split images of every problem

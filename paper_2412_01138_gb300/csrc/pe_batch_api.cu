@@ -42,7 +42,8 @@ void free_batch(pe_batch* b) {
                   b->coefF32, b->U, b->Fbar, b->axisF, b->axisU0, b->axisF32, b->AF, b->AG,
                   b->AF32, b->partials, b->active, b->kcount, b->resid, b->counter, b->dflags,
                   b->W, b->W32, b->Z, b->d_cols, b->AG32, b->Z32, b->tc.A, b->tc.B, b->tc.d_items,
-                  b->tc.d_w_prefix, b->tc.d_y_prefix, b->tc.err};
+                  b->tc.d_w_prefix, b->tc.d_y_prefix, b->tc.err, b->Kt, b->Ph, b->d_kt_prefix,
+                  b->d_ph_prefix};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_flags) cudaFreeHost(b->h_flags);
@@ -587,6 +588,62 @@ extern "C" pe_status pe_batch_get_solution(pe_batch* b, int32_t problem, double*
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (st == PE_OK && e != cudaSuccess) st = pe_cuda_fail(e, "pe_batch_get_solution");
   return st;
+}
+
+// Learned correction for every problem: the band range of each problem (its slowest and fastest
+// closed-form lam, times dT), table offsets and job prefixes; the tables themselves are made by
+// the next pe_batch_solve (batch_learned_tables).
+extern "C" pe_status pe_batch_set_learned(pe_batch* b, const pe_mlp* m) {
+  if (!b) return pe_fail(PE_EINVAL, "pe_batch_set_learned: NULL batch");
+  if (!m) {
+    b->mlp = nullptr;
+    return PE_OK;
+  }
+  PE_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  const int NB = kBatchLearnedBands;
+  std::vector<int64_t> kp, pp;
+  int64_t okt = 0, oph = 0;
+  for (int p = 0; p < b->P; ++p) {
+    BProb& B = b->probs[p];
+    double lmin = 0.0, lmax = 0.0;
+    for (int a = 0; a < B.g.d; ++a) {
+      const int n = B.g.n[a];
+      auto ratio = [&](int j) {
+        const double th = M_PI * (double)j / (double)(n + 1);
+        const double sh = sin(0.5 * th);
+        return ((4.0 / B.h[a]) * sh * sh) / ((B.h[a] / 3.0) * (2.0 + cos(th)));
+      };
+      lmin += ratio(1);
+      lmax += ratio(n);
+    }
+    const double loglo = log(B.D * lmin * B.dT) - 1e-6, loghi = log(B.D * lmax * B.dT) + 1e-6;
+    B.lloglo = loglo;
+    B.lstep = (loghi - loglo) / (double)(NB - 1);
+    B.oKt = okt;
+    kp.push_back(okt / 2);
+    okt += 2 * (int64_t)B.R * NB;
+    B.oPh = oph;
+    pp.push_back(oph);
+    oph += (int64_t)B.R * B.N;
+  }
+  if (b->Kt) cudaFree(b->Kt);
+  if (b->Ph) cudaFree(b->Ph);
+  if (b->d_kt_prefix) cudaFree(b->d_kt_prefix);
+  if (b->d_ph_prefix) cudaFree(b->d_ph_prefix);
+  b->Kt = nullptr;
+  b->Ph = nullptr;
+  b->d_kt_prefix = nullptr;
+  b->d_ph_prefix = nullptr;
+  PE_TRY(balloc(&b->Kt, (size_t)okt));
+  PE_TRY(balloc(&b->Ph, (size_t)oph));
+  PE_TRY(upload(&b->d_kt_prefix, kp, b->stream));
+  PE_TRY(upload(&b->d_ph_prefix, pp, b->stream));
+  PE_CUDA_TRY(cudaMemcpyAsync(b->d_probs, b->probs.data(), sizeof(BProb) * b->P, cudaMemcpyHostToDevice, b->stream));
+  PE_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->kt_jobs = okt / 2;
+  b->ph_jobs = oph;
+  b->mlp = m;
+  return PE_OK;
 }
 
 extern "C" pe_status pe_batch_status(pe_batch* b, double* residuals, int32_t* iterations) {

@@ -26,6 +26,7 @@
 #include <mutex>
 #include <vector>
 
+#include "pe_batch.h"
 #include "pe_learned.h"
 #include "pe_phi.cuh"
 
@@ -434,7 +435,78 @@ __global__ void __launch_bounds__(256) learned_correction_kernel(Geom g, int N, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// batched form: band and phase tables of every problem of a batch, jobs flattened through
+// per-problem prefix tables (the owner of job e is the problem with the largest prefix <= e)
+// ---------------------------------------------------------------------------
+__device__ inline int job_owner(const int64_t* __restrict__ prefix, int P, int64_t e) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void b_band_table_kernel(const __half* __restrict__ params16, const BProb* __restrict__ probs,
+                                    const pe_term* __restrict__ terms, const int64_t* __restrict__ prefix, int P,
+                                    int64_t total, int NB, double* __restrict__ Kt) {
+  __shared__ __half Ps[NPARAM];
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) Ps[i] = params16[i];
+  __syncthreads();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int p = job_owner(prefix, P, e);
+  const BProb& B = probs[p];
+  const int64_t le = e - prefix[p];
+  const int r = (int)(le / NB), band = (int)(le % NB);
+  const pe_term& t = terms[B.tf + r];
+  double Kre = 0.0, Kim = 0.0;
+  if (t.tkind == PE_T_SIN) {
+    const double w = t.tp[0];
+    const double ll = B.lloglo + B.lstep * (double)band;  // log(lam dT)
+    const double wd = w * B.dT;
+    float y0, y1;
+    mlp_eval_half(Ps, (float)(ll / 6.0), (float)(wd - 1.0), &y0, &y1);
+    const double unscale = (B.dT * wd * wd) / (4.0 * (1.0 + exp(ll)));
+    Kre = (double)y0 * unscale;
+    Kim = (double)y1 * unscale;
+  }
+  Kt[B.oKt + 2 * le] = Kre;
+  Kt[B.oKt + 2 * le + 1] = Kim;
+}
+
+__global__ void b_phase_table_kernel(const BProb* __restrict__ probs, const pe_term* __restrict__ terms,
+                                     const int64_t* __restrict__ prefix, int P, int64_t total,
+                                     float2* __restrict__ Ph) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int p = job_owner(prefix, P, e);
+  const BProb& B = probs[p];
+  const int64_t le = e - prefix[p];
+  const int r = (int)(le / B.N), n = (int)(le % B.N);
+  const pe_term& t = terms[B.tf + r];
+  double sn = 0.0, cs = 0.0;
+  if (t.tkind == PE_T_SIN) sincos(t.tp[0] * (B.t0 + (double)n * B.dT) + t.tp[1], &sn, &cs);
+  Ph[B.oPh + le] = make_float2((float)cs, (float)sn);
+}
+
 }  // namespace
+
+pe_status batch_learned_tables(pe_batch* b, cudaStream_t st) {
+  if (!b->mlp) return PE_OK;
+  if (b->kt_jobs > 0)
+    b_band_table_kernel<<<(unsigned)((b->kt_jobs + 127) / 128), 128, 0, st>>>(
+        (const __half*)b->mlp->params16, b->d_probs, b->d_terms, b->d_kt_prefix, b->P, b->kt_jobs,
+        kBatchLearnedBands, b->Kt);
+  if (b->ph_jobs > 0)
+    b_phase_table_kernel<<<(unsigned)((b->ph_jobs + 255) / 256), 256, 0, st>>>(b->d_probs, b->d_terms, b->d_ph_prefix,
+                                                                               b->P, b->ph_jobs, b->Ph);
+  b->launches += 2;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
 
 // ---------------------------------------------------------------------------
 // host API

@@ -38,7 +38,7 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_batch_destroy", "pe_mlp_create", "pe_mlp_num_params", "pe_mlp_train", "pe_mlp_gradient",
             "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
             "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc", "pe_set_dirichlet", "pe_measure_fma_peak",
-            "pe_probe_wait_timeout", "pe_parareal_iter_sums")
+            "pe_probe_wait_timeout", "pe_parareal_iter_sums", "pe_batch_set_learned")
 
 
 class PEError(RuntimeError):
@@ -141,6 +141,7 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_mlp_destroy": (None, [P]),
         "pe_learned_samples": (C.c_int, [P, C.c_int32, P, P, P, P, P]),
         "pe_set_learned": (C.c_int, [P, P]),
+        "pe_batch_set_learned": (C.c_int, [P, P]),
         "pe_dst_tc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, C.c_int32, P]),
         "pe_dst_noalloc": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), P, P, P]),
         "pe_set_dirichlet": (C.c_int, [P, C.c_int32, P]),
@@ -491,6 +492,11 @@ class BatchSolver:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_learned(self, mlp: Optional["MLP"]):
+        """Attach a trained network as learned coarse correction of every problem (None detaches)."""
+        _check(self._lib.pe_batch_set_learned(self.ctx, mlp.ctx if mlp is not None else None))
+        self._mlp = mlp
 
     def autotune(self, cache_path: Optional[str] = None):
         _check(self._lib.pe_batch_autotune(self.ctx, cache_path.encode() if cache_path else None))

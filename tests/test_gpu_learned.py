@@ -140,3 +140,27 @@ def test_learned_coarse_correction_saves_a_sweep(env, trained, precision):
     bound = 1e-12 if precision == "fp64" else 1e-6
     for n in range(1, prob.N + 1):
         assert osolver.rel_l2(got[n], fine[n], sys_.norm_w) <= bound, n
+
+
+@pytest.mark.parametrize("engine", ["tc", "simt"])
+def test_batched_learned_correction_saves_a_sweep(env, trained, engine):
+    """The mixed, batched form with the learned coarse correction (and the tensor-core fine
+    engine): three problems of the learned workload's family in one batch stop after one fine
+    sweep each, at the fine solution (<= 1e-6)."""
+    pe, torch = env
+    net = trained[0]
+    probs = [_prob(seed=s) for s in (1, 2, 3)]
+    eng = pe.PE_FINE_TC if engine == "tc" else pe.PE_FINE_SIMT
+    with pe.BatchSolver(probs, precision=pe.PE_MIXED, fine_engine=eng) as b:
+        plain = b.solve(tol=1e-6)
+        _, k_plain = b.status()
+        b.set_learned(net)
+        info = b.solve(tol=1e-6)
+        r, k = b.status()
+        got = [b.modal(i, p.N) for i, p in enumerate(probs)]
+    assert list(k_plain) == [2, 2, 2] and plain["graph_replays"] == 2
+    assert list(k) == [1, 1, 1] and info["graph_replays"] == 1 and float(r.max()) <= 1e-6
+    for prob, g in zip(probs, got):
+        sys_ = osolver.ModalSystem(prob)
+        fine = osolver.sequential_fine(sys_)
+        assert osolver.rel_l2(g, fine[-1], sys_.norm_w) <= 1e-6
