@@ -253,6 +253,59 @@ def oracle_sample(prob, n_modes: int, seed: int = 0, u0_nodal=None):
     return units / dt, dt, len(idx), res.k, sys_, res, idx
 
 
+def run_batch_learned(pe, args, barrier, probs):
+    """The batched workload in the mixed, batched, learned-G form: a network trained on pairs the
+    method generates over the batch family's ranges of lam dT and w dT (problems of the held-apart
+    seed 7: their slice lengths, source frequencies and spectra), attached to every problem."""
+    import torch
+
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(77)
+    ref = I.config4_problem(0)
+    dT0 = ref.T / ref.N
+    LT, WT = [], []
+    for i in range(400):  # held-apart problems of the family (base seed 7)
+        pr = I.config4_problem(i, base_seed=7)
+        dT = pr.T / pr.N
+        lmin = pr.D * sum(np.pi ** 2 / (hi - lo) ** 2 for lo, hi in pr.box)
+        lmax = pr.D * sum(12.0 * (n + 1) ** 2 / (hi - lo) ** 2 for n, (lo, hi) in zip(pr.n, pr.box))
+        ws = [t.tp[0] for t in pr.forcing if t.tkind == I.T_SIN]
+        ls = np.exp(rng.uniform(np.log(lmin * dT), np.log(lmax * dT), 256))
+        LT.append(np.repeat(ls, len(ws)))
+        WT.append(np.tile(np.array(ws) * dT, 256))
+    LT, WT = np.concatenate(LT), np.concatenate(WT)
+    perm = rng.permutation(LT.size)
+    out = {"training_pairs": int(LT.size), "seeds": "batch family, base seed 7, problems 0..399"}
+    with pe.Solver(ref, precision=pe.PE_MIXED) as s:  # the unit response is a function of (lam dT, w dT)
+        lam_d = torch.tensor(LT[perm] / dT0, device=dev)
+        om_d = torch.tensor(WT[perm] / dT0, device=dev)
+        x = torch.empty((LT.size, 2), device=dev, dtype=torch.float32)
+        t = torch.empty((LT.size, 2), device=dev, dtype=torch.float32)
+        s.learned_samples(lam_d, om_d, x, t)
+    net = pe.MLP(seed=5)
+    t1 = time.perf_counter()
+    out["final_loss"] = net.train(x, t, epochs=max(1, 60000 // ((LT.size + 4095) // 4096)), batch=4096, lr=3e-3)
+    torch.cuda.synchronize()
+    out["seconds_training"] = time.perf_counter() - t1
+    with pe.BatchSolver(probs, precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC) as b:
+        b.set_learned(net)
+        for _ in range(max(1, args.warmup)):
+            b.solve(tol=TOL)
+        barrier()
+        t0 = time.perf_counter()
+        infos = [b.solve(tol=TOL) for _ in range(args.steps)]
+        barrier()
+        dt = (time.perf_counter() - t0) / args.steps
+        r, k = b.status()
+    out.update({"form": "batched, tensor-core fine engine, learned coarse correction", "time_to_tol_ms": 1e3 * dt,
+                "value": infos[-1]["fine_dof_substeps"] / dt, "unit": UNIT,
+                "iterations_histogram": {int(v): int((k == v).sum()) for v in np.unique(k)},
+                "max_residual": float(r.max()), "graph_replays": infos[-1]["graph_replays"],
+                "ms_prepare": infos[-1]["ms_prepare"], "ms_iterations": infos[-1]["ms_iterations"]})
+    net.close()
+    return out
+
+
 def run_batch(pe, args, barrier):
     """512 uneven 2D problems: batched persistent mixed form vs a per-problem float64 loop."""
     probs = I.config4(count=args.batch_count)
@@ -279,6 +332,8 @@ def run_batch(pe, args, barrier):
                                                                                   infos[-1]["ctas_per_sm"]],
                      "ms_prepare": infos[-1]["ms_prepare"], "ms_iterations": infos[-1]["ms_iterations"],
                      "gpu_launches": infos[-1]["kernel_launches"]}
+    if not args.no_learned:
+        out["learned"] = run_batch_learned(pe, args, barrier, probs)
     dt = out["chosen"]["time_to_tol_ms"] / 1e3
     # plain: one problem after another, float64, host-driven iteration loop (solvers set up
     # before the timed region, as the batch is)
@@ -416,6 +471,45 @@ def run_learned(pe, args, barrier):
     out.update(res)
     out["speedup_time_to_tol"] = res["plain_G"]["time_to_tol_ms"] / res["learned_G"]["time_to_tol_ms"]
     out["speedup_vs_fp64"] = res["fp64_plain_G"]["time_to_tol_ms"] / res["learned_G"]["time_to_tol_ms"]
+    # the mixed, batched, learned-G form: four problems of the family (seeds 1..4) in one batch
+    probs = [I.config5(seed=sd) for sd in (1, 2, 3, 4)]
+    bat = {"workload": "4 problems of the family (seeds 1..4), one batch"}
+    with pe.BatchSolver(probs, precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC) as b:
+        for name, mlp in (("batched_plain_G", None), ("batched_learned_G", net)):
+            b.set_learned(mlp)
+            for _ in range(max(1, args.warmup)):
+                b.solve(tol=TOL)
+            barrier()
+            t1 = time.perf_counter()
+            steps = max(1, min(args.steps, 5))
+            infos = [b.solve(tol=TOL) for _ in range(steps)]
+            barrier()
+            dt = (time.perf_counter() - t1) / steps
+            r, k = b.status()
+            bat[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": [int(v) for v in k],
+                         "max_residual": float(r.max()), "value": infos[-1]["fine_dof_substeps"] / dt, "unit": UNIT,
+                         "ms_prepare": infos[-1]["ms_prepare"], "ms_iterations": infos[-1]["ms_iterations"]}
+            if mlp is not None:
+                m1 = b.modal(0, prob.N)
+        b.set_learned(None)
+    bat["rel_l2_vs_oracle_problem0"] = float(np.sqrt(np.sum(w * (m1[idx] - ref.U[-1]) ** 2)) /
+                                             np.sqrt(np.sum(w * ref.U[-1] ** 2)))
+    # the plain form on the same four problems: float64, one problem after another
+    solvers = [pe.Solver(pr, precision=pe.PE_FP64) for pr in probs]
+    try:
+        for sv in solvers:
+            sv.solve(tol=TOL)
+        barrier()
+        t1 = time.perf_counter()
+        for sv in solvers:
+            sv.solve(tol=TOL)
+        barrier()
+        bat["fp64_per_problem_loop_ms"] = 1e3 * (time.perf_counter() - t1)
+    finally:
+        for sv in solvers:
+            sv.close()
+    bat["speedup_vs_fp64"] = bat["fp64_per_problem_loop_ms"] / bat["batched_learned_G"]["time_to_tol_ms"]
+    out["batched"] = bat
     net.close()
     return out
 
