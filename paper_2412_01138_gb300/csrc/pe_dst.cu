@@ -564,6 +564,16 @@ __host__ __device__ constexpr int pass_bits(int left, int logl) {
   return (sizeof(T) == 4 && logl >= 10 && left >= 5) ? 5 : (left >= 4 ? 4 : left);
 }
 
+// radix plans of the pass twiddle tables: the one-warp form (pass_bits), the half-length form
+// (half_pass_bits) and the team form (team_pass_bits: radix 16 while 4 bits remain)
+constexpr int kPlanWarp = 0, kPlanHalf = 1, kPlanTeam = 2;
+__host__ __device__ constexpr int team_pass_bits(int left) { return left >= 4 ? 4 : left; }
+constexpr int team_tw_entries(int left, int ns) {
+  return left == 0 ? 0
+                   : (ns > 1 ? ns * (1 << team_pass_bits(left)) : 0) +
+                         team_tw_entries(left - team_pass_bits(left), ns * (1 << team_pass_bits(left)));
+}
+
 // One Stockham pass of radix R after NS points have been combined; tw = this pass's
 // table [r][k] = e^{-2 pi i k r / (NS R)}, k < NS (unused when NS == 1).
 template <typename T, int LOGL, int R, int NS>
@@ -950,16 +960,179 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Team form of the odd-extension FFT for long float32 pencils (L = 2(n+1) = 1024, 2048): a team
+// of TW warps (TS = 32 TW threads, synchronised by a named barrier) owns one pencil pair, so a
+// lane holds L / (16 TS) radix-16 groups -- 16 complex values -- instead of the L/32 of the
+// one-warp form (32 or 64 values, which capped that form at one CTA of 8 warps per SM).
+// Passes: radix 16 while at least 4 bits remain, then the remainder ([16, 16, 4] at L = 1024,
+// [16, 16, 8] at 2048).  Same loads, stores and odd extension as dst_fft_warp_kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void team_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <typename T, int LOGL, int R, int NS, int TS>
+__device__ __forceinline__ void stockham_team_pass(Cplx<T>* a, const Cplx<T>* tw, int tl, int bar) {
+  constexpr int L = 1 << LOGL, NG = L / R, G = (NG + TS - 1) / TS;
+  Cplx<T> v[G][R];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = tl + TS * g;
+    if (NG % TS == 0 || j < NG) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[g][r] = a[fpad(j + r * NG)];
+      if (NS > 1) {
+        const int k = j & (NS - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[g][r] = cmul(v[g][r], ldg_cplx(tw + r * NS + k));
+      }
+      dft_regs<T, R>(v[g]);
+    }
+  }
+  team_sync(bar, TS);
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = tl + TS * g;
+    if (NG % TS == 0 || j < NG) {
+      const int k = j & (NS - 1);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[fpad(base + r * NS)] = v[g][brevc(r, ilog2c(R))];
+    }
+  }
+  team_sync(bar, TS);
+}
+
+template <typename T, int LOGL, int LEFT, int NS, int TS>
+struct TeamPasses {
+  static __device__ __forceinline__ void run(Cplx<T>* a, const Cplx<T>* tw, int tl, int bar) {
+    constexpr int RB = team_pass_bits(LEFT);
+    constexpr int R = 1 << RB;
+    stockham_team_pass<T, LOGL, R, NS, TS>(a, tw, tl, bar);
+    TeamPasses<T, LOGL, LEFT - RB, NS * R, TS>::run(a, tw + (NS > 1 ? NS * R : 0), tl, bar);
+  }
+};
+template <typename T, int LOGL, int NS, int TS>
+struct TeamPasses<T, LOGL, 0, NS, TS> {
+  static __device__ __forceinline__ void run(Cplx<T>*, const Cplx<T>*, int, int) {}
+};
+
+constexpr int kTeamThreads = 256;  // CTA size of the team kernel
+
+// blockDim.x = kTeamThreads: kTeamThreads / TS teams, one pencil pair each (P = 2 teams pencils
+// per block of strided work).
+template <typename T, int LOGL, int TW>
+__global__ void __launch_bounds__(kTeamThreads) dst_fft_team_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                                                     int n, int64_t inner, int64_t npencils,
+                                                                     T scale, const Cplx<T>* __restrict__ ptw) {
+  constexpr int L = 1 << LOGL, N = L / 2, PADL = L + L / 16, PS = PADL + 1, TS = 32 * TW;
+  constexpr int TEAMS = kTeamThreads / TS, P = 2 * TEAMS, logP = ilog2c(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<T>* bufs = reinterpret_cast<Cplx<T>*>(smem_raw);
+  int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)TEAMS * PS);
+  const int tid = threadIdx.x, team = tid / TS, tl = tid & (TS - 1), bar = 1 + team;
+  Cplx<T>* a = bufs + (size_t)team * PS;
+  if (inner == 1) {
+    // contiguous pencils: each team loads, transforms and stores its own pencil pairs
+    constexpr int JL = (N + TS - 1) / TS;
+    const int64_t npairs = (npencils + 1) / 2;
+    for (int64_t pr = (int64_t)blockIdx.x * TEAMS + team; pr < npairs; pr += (int64_t)gridDim.x * TEAMS) {
+      const int64_t pa = 2 * pr, pb = pa + 1;
+      const bool has_b = pb < npencils;
+      const T* xa = in + pa * n;
+      const T* xb = in + pb * n;
+      T ra[JL], rb[JL];
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int j = tl + TS * t;
+        ra[t] = j < n ? xa[j] : T(0);
+        rb[t] = (j < n && has_b) ? xb[j] : T(0);
+      }
+      if (tl == 0) {
+        a[fpad(0)] = Cplx<T>{T(0), T(0)};
+        a[fpad(N)] = Cplx<T>{T(0), T(0)};
+      }
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int j = tl + TS * t;
+        if (j < n) {
+          a[fpad(j + 1)] = Cplx<T>{ra[t], rb[t]};
+          a[fpad(L - 1 - j)] = Cplx<T>{-ra[t], -rb[t]};
+        }
+      }
+      team_sync(bar, TS);
+      TeamPasses<T, LOGL, LOGL, 1, TS>::run(a, ptw, tl, bar);
+      T* ya = out + pa * n;
+      T* yb = out + pb * n;
+#pragma unroll
+      for (int t = 0; t < JL; ++t) {
+        const int k = tl + TS * t;
+        if (k < n) {
+          const Cplx<T> Z = a[fpad(k + 1)];
+          ya[k] = -Z.im * scale;
+          if (has_b) yb[k] = Z.re * scale;
+        }
+      }
+      team_sync(bar, TS);
+    }
+    return;
+  }
+  // strided pencils: blocks of P consecutive pencils staged row by row (cp.async), the next block
+  // staged while this one is transformed
+  const int64_t nblk = (npencils + P - 1) / P;
+  int64_t* offs[2] = {off, off + P};
+  T* stage = reinterpret_cast<T*>(off + 2 * P);
+  int cur = 0;
+  if ((int64_t)blockIdx.x < nblk) {
+    block_offsets(blockIdx.x, P, n, inner, npencils, offs[0]);
+    __syncthreads();
+    stage_block_async(in, offs[0], P, logP, n, inner, stage);
+  }
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x, cur ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid < 2 * TEAMS) {
+      Cplx<T>* at = bufs + (size_t)(tid >> 1) * PS;
+      at[fpad((tid & 1) ? N : 0)] = Cplx<T>{T(0), T(0)};
+    }
+    for (int e = tid; e < P * n; e += kTeamThreads) {
+      const int pl = e & (P - 1), j = e >> logP;
+      const T v = stage[pl * n + j];
+      Cplx<T>* at = bufs + (size_t)(pl >> 1) * PS;
+      reinterpret_cast<T*>(at + fpad(j + 1))[pl & 1] = v;
+      reinterpret_cast<T*>(at + fpad(L - 1 - j))[pl & 1] = -v;
+    }
+    __syncthreads();
+    const int64_t next = blk + gridDim.x;
+    if (next < nblk) {
+      block_offsets(next, P, n, inner, npencils, offs[cur ^ 1]);
+      __syncthreads();
+      stage_block_async(in, offs[cur ^ 1], P, logP, n, inner, stage);
+    }
+    TeamPasses<T, LOGL, LOGL, 1, TS>::run(a, ptw, tl, bar);
+    __syncthreads();
+    for (int e = tid; e < P * n; e += kTeamThreads) {
+      const int pl = e & (P - 1), k = e >> logP;
+      const Cplx<T> Z = bufs[(size_t)(pl >> 1) * PS + fpad(k + 1)];
+      const T val = (pl & 1) ? Z.re * scale : -Z.im * scale;
+      const int64_t o = offs[cur][pl];
+      if (o >= 0) out[o + (int64_t)k * inner] = val;
+    }
+  }
+}
+
 // Pass twiddle tables of one length 2^logl, in pass order, each laid out [r][k] (k fastest):
 // entry = e^{-2 pi i k r / (NS R)}, evaluated in float64 and rounded to T.  HALF selects the
 // radix plan of the half-length form.
-template <typename T, bool HALF>
+template <typename T, int PLAN>
 __global__ void pass_twiddle_kernel(int logl, int total, Cplx<T>* out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= total) return;
   int e0 = 0, ns = 1, left = logl;
   while (left > 0) {
-    const int rb = HALF ? half_pass_bits<T>(left, logl) : pass_bits<T>(left, logl);
+    const int rb = PLAN == kPlanHalf ? half_pass_bits<T>(left, logl)
+                                     : (PLAN == kPlanTeam ? team_pass_bits(left) : pass_bits<T>(left, logl));
     const int R = 1 << rb;
     if (ns > 1) {
       if (e < e0 + ns * R) {
@@ -984,7 +1157,7 @@ __global__ void sin_table_kernel(int N, T* out) {
 }
 
 // Device-resident tables (pass twiddles, the fold's sines), built once per device and length.
-template <typename T, bool HALF>
+template <typename T, int PLAN>
 const Cplx<T>* pass_twiddles(int logl, int total, cudaStream_t st) {
   static Cplx<T>* table[64][12] = {};
   static std::mutex mu;
@@ -998,7 +1171,7 @@ const Cplx<T>* pass_twiddles(int logl, int total, cudaStream_t st) {
     cudaGetLastError();
     return nullptr;
   }
-  if (total > 0) pass_twiddle_kernel<T, HALF><<<(total + 255) / 256, 256, 0, st>>>(logl, total, p);
+  if (total > 0) pass_twiddle_kernel<T, PLAN><<<(total + 255) / 256, 256, 0, st>>>(logl, total, p);
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(p);
@@ -1060,7 +1233,7 @@ template <typename T, int LOGN>
 pe_status fft_dht_launch(const T* in, T* out, int64_t inner, int64_t npencils, cudaStream_t st) {
   constexpr int N = 1 << LOGN, PADN = N + N / 16;
   constexpr int NTW = half_tw_entries<T>(LOGN, 1, LOGN);
-  const Cplx<T>* ptw = pass_twiddles<T, true>(LOGN, NTW, st);
+  const Cplx<T>* ptw = pass_twiddles<T, kPlanHalf>(LOGN, NTW, st);
   if (!ptw) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
   auto kern = dst_half_warp_kernel<T, LOGN, true>;
   int warps = 1;
@@ -1094,7 +1267,7 @@ template <typename T, int LOGN>
 pe_status fft_half_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, cudaStream_t st) {
   constexpr int N = 1 << LOGN, PADN = N + N / 16;
   constexpr int NTW = half_tw_entries<T>(LOGN, 1, LOGN);
-  const Cplx<T>* ptw = pass_twiddles<T, true>(LOGN, NTW, st);
+  const Cplx<T>* ptw = pass_twiddles<T, kPlanHalf>(LOGN, NTW, st);
   const T* sinN = half_sines<T>(LOGN, st);
   if (!ptw || !sinN) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
   auto kern = dst_half_warp_kernel<T, LOGN>;
@@ -1113,7 +1286,7 @@ template <typename T, int LOGL>
 pe_status fft_warp_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, T scale, cudaStream_t st) {
   constexpr int L = 1 << LOGL, PADL = L + L / 16;
   constexpr int NTW = pass_tw_entries<T>(LOGL, 1, LOGL);
-  const Cplx<T>* ptw = pass_twiddles<T, false>(LOGL, NTW, st);
+  const Cplx<T>* ptw = pass_twiddles<T, kPlanWarp>(LOGL, NTW, st);
   if (!ptw) return pe_fail(PE_ECUDA, "dst: pass twiddle table allocation failed");
   auto kern = dst_fft_warp_kernel<T, LOGL>;
   int warps = 1;
@@ -1122,6 +1295,27 @@ pe_status fft_warp_launch(const T* in, T* out, int n, int64_t inner, int64_t npe
   PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * (PADL + 1), inner > 1 ? sizeof(T) * n : 0, &warps,
                      &smem, &grid));
   kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, ptw);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+template <typename T, int LOGL, int TW>
+pe_status fft_team_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, T scale, cudaStream_t st) {
+  constexpr int L = 1 << LOGL, PADL = L + L / 16, TS = 32 * TW, TEAMS = kTeamThreads / TS, P = 2 * TEAMS;
+  constexpr int NTW = team_tw_entries(LOGL, 1);
+  const Cplx<T>* ptw = pass_twiddles<T, kPlanTeam>(LOGL, NTW, st);
+  if (!ptw) return pe_fail(PE_ECUDA, "dst: pass twiddle table allocation failed");
+  auto kern = dst_fft_team_kernel<T, LOGL, TW>;
+  const size_t smem = sizeof(Cplx<T>) * (size_t)TEAMS * (PADL + 1) + 2 * sizeof(int64_t) * P +
+                      (inner > 1 ? sizeof(T) * (size_t)P * n : 0);
+  if (smem > 48 * 1024) PE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTeamThreads, smem));
+  const int64_t work = inner > 1 ? (npencils + P - 1) / P : ((npencils + 1) / 2 + TEAMS - 1) / TEAMS;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)sms * std::max(per_sm, 1)));
+  kern<<<(unsigned)grid, kTeamThreads, smem, st>>>(in, out, n, inner, npencils, scale, ptw);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -1154,8 +1348,9 @@ pe_status fft_warp_axis(const T* in, T* out, int64_t outer, int n, int64_t inner
       case 7: return fft_warp_launch<T, 7>(in, out, n, inner, np, scale, st);
       case 8: return fft_warp_launch<T, 8>(in, out, n, inner, np, scale, st);
       case 9: return fft_warp_launch<T, 9>(in, out, n, inner, np, scale, st);
-      case 10: return fft_warp_launch<T, 10>(in, out, n, inner, np, scale, st);
-      case 11: return fft_warp_launch<T, 11>(in, out, n, inner, np, scale, st);
+      // 1024 and 2048 points: two or four warps per pencil pair (16 complex values per lane)
+      case 10: return fft_team_launch<T, 10, 2>(in, out, n, inner, np, scale, st);
+      case 11: return fft_team_launch<T, 11, 4>(in, out, n, inner, np, scale, st);
       default:
         break;
     }
