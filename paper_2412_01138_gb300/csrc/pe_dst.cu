@@ -1019,15 +1019,15 @@ struct TeamPasses<T, LOGL, 0, NS, TS> {
 };
 
 constexpr int kTeamThreads = 256;  // CTA size of the team kernel
-constexpr int kTeamBlock = 32;     // strided pencils per staged block (128-byte rows in float32)
 
-// blockDim.x = kTeamThreads: kTeamThreads / TS teams, one pencil pair at a time each.
+// blockDim.x = kTeamThreads: kTeamThreads / TS teams, one pencil pair each (P = 2 teams pencils
+// per block of strided work).
 template <typename T, int LOGL, int TW>
 __global__ void __launch_bounds__(kTeamThreads) dst_fft_team_kernel(const T* __restrict__ in, T* __restrict__ out,
                                                                      int n, int64_t inner, int64_t npencils,
                                                                      T scale, const Cplx<T>* __restrict__ ptw) {
   constexpr int L = 1 << LOGL, N = L / 2, PADL = L + L / 16, PS = PADL + 1, TS = 32 * TW;
-  constexpr int TEAMS = kTeamThreads / TS;
+  constexpr int TEAMS = kTeamThreads / TS, P = 2 * TEAMS, logP = ilog2c(P);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<T>* bufs = reinterpret_cast<Cplx<T>*>(smem_raw);
   int64_t* off = reinterpret_cast<int64_t*>(bufs + (size_t)TEAMS * PS);
@@ -1078,50 +1078,46 @@ __global__ void __launch_bounds__(kTeamThreads) dst_fft_team_kernel(const T* __r
     }
     return;
   }
-  // strided pencils: blocks of PB = 32 consecutive pencils, each row j of a block one 128-byte
-  // run; the block is staged in shared memory, every team transforms pencil pairs of it in turn
-  // and writes its outputs back over the consumed inputs, and the block is stored row by row
-  const int64_t nblk = (npencils + kTeamBlock - 1) / kTeamBlock;
-  T* stage = reinterpret_cast<T*>(off + kTeamBlock);  // [kTeamBlock * n]
-  constexpr int logPB = ilog2c(kTeamBlock);
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    __syncthreads();  // the previous block's stores have read the stage
-    block_offsets(blk, kTeamBlock, n, inner, npencils, off);
+  // strided pencils: blocks of P consecutive pencils staged row by row (cp.async), the next block
+  // staged while this one is transformed
+  const int64_t nblk = (npencils + P - 1) / P;
+  int64_t* offs[2] = {off, off + P};
+  T* stage = reinterpret_cast<T*>(off + 2 * P);
+  int cur = 0;
+  if ((int64_t)blockIdx.x < nblk) {
+    block_offsets(blockIdx.x, P, n, inner, npencils, offs[0]);
     __syncthreads();
-    for (int e = tid; e < kTeamBlock * n; e += kTeamThreads) {
-      const int pl = e & (kTeamBlock - 1), j = e >> logPB;
-      const int64_t o = off[pl];
-      stage[pl * n + j] = o >= 0 ? __ldg(in + o + (int64_t)j * inner) : T(0);
+    stage_block_async(in, offs[0], P, logP, n, inner, stage);
+  }
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x, cur ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid < 2 * TEAMS) {
+      Cplx<T>* at = bufs + (size_t)(tid >> 1) * PS;
+      at[fpad((tid & 1) ? N : 0)] = Cplx<T>{T(0), T(0)};
+    }
+    for (int e = tid; e < P * n; e += kTeamThreads) {
+      const int pl = e & (P - 1), j = e >> logP;
+      const T v = stage[pl * n + j];
+      Cplx<T>* at = bufs + (size_t)(pl >> 1) * PS;
+      reinterpret_cast<T*>(at + fpad(j + 1))[pl & 1] = v;
+      reinterpret_cast<T*>(at + fpad(L - 1 - j))[pl & 1] = -v;
     }
     __syncthreads();
-    for (int q = team; q < kTeamBlock / 2; q += TEAMS) {
-      const T* sa = stage + (2 * q) * n;
-      const T* sb = sa + n;
-      if (tl == 0) {
-        a[fpad(0)] = Cplx<T>{T(0), T(0)};
-        a[fpad(N)] = Cplx<T>{T(0), T(0)};
-      }
-      for (int j = tl; j < n; j += TS) {
-        const T va = sa[j], vb = sb[j];
-        a[fpad(j + 1)] = Cplx<T>{va, vb};
-        a[fpad(L - 1 - j)] = Cplx<T>{-va, -vb};
-      }
-      team_sync(bar, TS);
-      TeamPasses<T, LOGL, LOGL, 1, TS>::run(a, ptw, tl, bar);
-      T* da = stage + (2 * q) * n;
-      T* db = da + n;
-      for (int k = tl; k < n; k += TS) {
-        const Cplx<T> Z = a[fpad(k + 1)];
-        da[k] = -Z.im * scale;
-        db[k] = Z.re * scale;
-      }
-      team_sync(bar, TS);
+    const int64_t next = blk + gridDim.x;
+    if (next < nblk) {
+      block_offsets(next, P, n, inner, npencils, offs[cur ^ 1]);
+      __syncthreads();
+      stage_block_async(in, offs[cur ^ 1], P, logP, n, inner, stage);
     }
+    TeamPasses<T, LOGL, LOGL, 1, TS>::run(a, ptw, tl, bar);
     __syncthreads();
-    for (int e = tid; e < kTeamBlock * n; e += kTeamThreads) {
-      const int pl = e & (kTeamBlock - 1), k = e >> logPB;
-      const int64_t o = off[pl];
-      if (o >= 0) out[o + (int64_t)k * inner] = stage[pl * n + k];
+    for (int e = tid; e < P * n; e += kTeamThreads) {
+      const int pl = e & (P - 1), k = e >> logP;
+      const Cplx<T> Z = bufs[(size_t)(pl >> 1) * PS + fpad(k + 1)];
+      const T val = (pl & 1) ? Z.re * scale : -Z.im * scale;
+      const int64_t o = offs[cur][pl];
+      if (o >= 0) out[o + (int64_t)k * inner] = val;
     }
   }
 }
@@ -1305,12 +1301,12 @@ pe_status fft_warp_launch(const T* in, T* out, int n, int64_t inner, int64_t npe
 
 template <typename T, int LOGL, int TW>
 pe_status fft_team_launch(const T* in, T* out, int n, int64_t inner, int64_t npencils, T scale, cudaStream_t st) {
-  constexpr int L = 1 << LOGL, PADL = L + L / 16, TS = 32 * TW, TEAMS = kTeamThreads / TS, P = kTeamBlock;
+  constexpr int L = 1 << LOGL, PADL = L + L / 16, TS = 32 * TW, TEAMS = kTeamThreads / TS, P = 2 * TEAMS;
   constexpr int NTW = team_tw_entries(LOGL, 1);
   const Cplx<T>* ptw = pass_twiddles<T, kPlanTeam>(LOGL, NTW, st);
   if (!ptw) return pe_fail(PE_ECUDA, "dst: pass twiddle table allocation failed");
   auto kern = dst_fft_team_kernel<T, LOGL, TW>;
-  const size_t smem = sizeof(Cplx<T>) * (size_t)TEAMS * (PADL + 1) + sizeof(int64_t) * P +
+  const size_t smem = sizeof(Cplx<T>) * (size_t)TEAMS * (PADL + 1) + 2 * sizeof(int64_t) * P +
                       (inner > 1 ? sizeof(T) * (size_t)P * n : 0);
   if (smem > 48 * 1024) PE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, per_sm = 0;
