@@ -49,11 +49,12 @@ TC_MIN_DOF = 4096  # below this the split operand images cost more than the tens
 def chosen_kw(pe, prec, prob=None):
     """Solver options of a separable-path solve: the mixed form (the chosen form) runs its stage
     contraction on the tensor cores (on the CUDA cores for grids under TC_MIN_DOF nodes, which are
-    launch-bound) and its Parareal loop on the device; float64 is the plain form (SIMT kernel,
-    host-driven loop of Algorithm 1)."""
+    launch-bound) and its Parareal loop on the device, with the set-up and output phases of a
+    repeated solve replayed as graphs; float64 is the plain form (SIMT kernel, host-driven loop
+    of Algorithm 1)."""
     if prec == pe.PE_MIXED:
         small = prob is not None and prob.ndof < TC_MIN_DOF
-        return {"fine_engine": pe.PE_FINE_SIMT if small else pe.PE_FINE_TC, "device_loop": 1}
+        return {"fine_engine": pe.PE_FINE_SIMT if small else pe.PE_FINE_TC, "device_loop": 2}
     return {"fine_engine": pe.PE_FINE_SIMT}
 
 
@@ -941,7 +942,7 @@ def main():
     with ClockSampler(local if world > 1 else 0) as clocks:
         for name, precision, eng, dl in (("fp64", pe.PE_FP64, pe.PE_FINE_SIMT, 0),
                                          ("mixed_simt", pe.PE_MIXED, pe.PE_FINE_SIMT, 0),
-                                         ("mixed", pe.PE_MIXED, pe.PE_FINE_TC, 1)):
+                                         ("mixed", pe.PE_MIXED, pe.PE_FINE_TC, 2)):
             with pe.Solver(prob, precision=precision, stream=stream, fine_engine=eng, device_loop=dl) as s:
                 total_ms, infos = timed_steps(s, args.steps, args.warmup, u0_dev)
                 modal = s.modal(prob.N)

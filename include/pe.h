@@ -152,7 +152,14 @@ typedef struct {
    * host-driven loop; per-kernel times (pe_result.ms_fine_kernel, ms_correction_kernel) are not
    * measured in this mode (0).  The graph is built at the first such solve of a column count K
    * and reused.  Falls back to the host loop for cache_forced, the general forcing path and
-   * contexts with residual_reduce.  0 (default): the host-driven loop of the paper's Algorithm 1. */
+   * contexts with residual_reduce.  0 (default): the host-driven loop of the paper's Algorithm 1.
+   * 2: as 1, and a problem solved again -- the same u0 description (or the same device pointer
+   * of nodal u0: its values are read anew each solve), forcing terms, Dirichlet data and network
+   * pointer -- replays the set-up (transform of u0, forcing factors, stage weights, coarse
+   * sweep) and output (inverse transform, lifting) phases as CUDA graphs captured at its second
+   * solve, so that a solve costs a few graph launches.  Same kernels, same results.  Nodal u0 in
+   * host memory, or any pe_set_problem / pe_set_dirichlet / pe_set_learned call in between, runs
+   * the phases directly (and drops the graphs).  Other values: PE_EINVAL. */
   int32_t device_loop;
 } pe_options;
 

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <new>
 #include <string>
 
@@ -135,6 +136,9 @@ void free_ctx(pe_ctx* c) {
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->h_loop) cudaFreeHost(c->h_loop);
   if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  if (c->setup_exec) cudaGraphExecDestroy(c->setup_exec);
+  if (c->out_exec) cudaGraphExecDestroy(c->out_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (int i = 0; i < PE_NEV; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -293,7 +297,11 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   }
   c->reduce = o.residual_reduce;
   c->reduce_user = o.residual_reduce_user;
-  c->device_loop = o.device_loop ? 1 : 0;
+  if (o.device_loop < 0 || o.device_loop > 2) {
+    delete c;
+    return pe_fail(PE_EINVAL, "pe_setup: device_loop must be 0, 1 or 2");
+  }
+  c->device_loop = o.device_loop;
   c->fine_engine = o.fine_engine;
   c->forcing_path = o.forcing_path;
   c->cache_forced = o.cache_forced ? 1 : 0;
@@ -364,6 +372,9 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     cudaGetLastError();
     st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");
   }
+  if (st == PE_OK && c->device_loop == 2 &&
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    st = pe_cuda_fail(cudaGetLastError(), "pe_setup: capture stream");
   if (st == PE_OK && c->device_loop) {
     st = dev_alloc(&c->loopctl, 1);
     if (st == PE_OK) st = dev_alloc(&c->loop_hist, N);
@@ -466,6 +477,16 @@ static pe_status add_lift(pe_ctx* c, double t, double sign, int kind, double* ou
   return launch_outer_sum(c, c->axisU0, tt, c->nbd, out, 1);
 }
 
+// The set-up and output graphs of a repeated problem (pe_options.device_loop = 2) hold the host
+// state of the solve that captured them; every call that changes that state drops them.
+void drop_solve_graphs(pe_ctx* c) {
+  if (c->setup_exec) cudaGraphExecDestroy(c->setup_exec);
+  if (c->out_exec) cudaGraphExecDestroy(c->out_exec);
+  c->setup_exec = c->out_exec = nullptr;
+  c->graph_key = 0;
+  c->graph_key_seen = 0;
+}
+
 extern "C" pe_status pe_set_dirichlet(pe_ctx* c, int32_t n_terms, const pe_term* g) {
   if (!c) return pe_fail(PE_EINVAL, "pe_set_dirichlet: ctx is NULL");
   if (n_terms < 0 || n_terms > PE_MAX_TERMS) return pe_fail(PE_EINVAL, "pe_set_dirichlet: n_terms out of range");
@@ -473,6 +494,7 @@ extern "C" pe_status pe_set_dirichlet(pe_ctx* c, int32_t n_terms, const pe_term*
   PE_TRY(pe_validate_terms(n_terms, g, c->g.d, "Dirichlet data"));
   if (n_terms > 0 && c->forcing_path == PE_FORCING_GENERAL)
     return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data need PE_FORCING_SEPARABLE");
+  drop_solve_graphs(c);
   if (n_terms > 0 && (c->g.per[0] || c->g.per[1] || c->g.per[2]))
     return pe_fail(PE_EINVAL, "pe_set_dirichlet: Dirichlet data with periodic axes");
   if (n_terms > 0 && c->sharded)
@@ -515,6 +537,12 @@ static pe_status modal_to_nodal(pe_ctx* c, const double* modal, double* nodal_ou
 // grids below this many nodes run pe_set_problem on one stream (their kernels are launch-bound)
 constexpr int64_t kForkMinDof = 4096;
 
+// A timing event on the context's stream; inside a captured phase it becomes an event-record node
+// of the graph, so that its replays record it too.
+static cudaError_t record_timing(pe_ctx* c, cudaEvent_t e) {
+  return cudaEventRecordWithFlags(e, c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
   if (!u0) return pe_fail(PE_EINVAL, "pe_set_problem: u0 is NULL");
   const int nf = f ? f->n_terms : 0;
@@ -554,7 +582,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     c->stream = c->side;
     pe_status st = PE_OK;
     if (fork_u0) {
-      const bool dev = pe_is_device_ptr(u0->nodal);
+      const bool dev = c->u0_dev_hint >= 0 ? c->u0_dev_hint == 1 : pe_is_device_ptr(u0->nodal);
       const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->gn.ndof,
                                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
       if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_set_problem: u0 copy");
@@ -574,7 +602,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
   if (!general) PE_TRY(launch_stage_weights(c));
   // the tensor-core engine's split operand images of the stage weights and time factors
   if (!general && c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC) PE_TRY(fine_tc_prepare(c));
-  PE_CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
+  PE_CUDA_TRY(record_timing(c, c->ev[1]));
   // U^0 = P_h u0
   if (fork_u0 && !inline_u0) {
     // made on the side stream above
@@ -594,7 +622,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     }
   } else if (u0->kind == PE_FIELD_NODAL) {
     if (!u0->nodal) return pe_fail(PE_EINVAL, "pe_set_problem: nodal u0 is NULL");
-    const bool dev = pe_is_device_ptr(u0->nodal);
+    const bool dev = c->u0_dev_hint >= 0 ? c->u0_dev_hint == 1 : pe_is_device_ptr(u0->nodal);
     PE_CUDA_TRY(cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->gn.ndof,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     PE_TRY(nodal_to_modal(c, c->work0, U0));
@@ -608,9 +636,9 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     PE_TRY(add_lift(c, c->t0, -1.0, nodal ? 2 : 1, U0));
   }
   // k = 0: coarse sweep
-  PE_CUDA_TRY(cudaEventRecord(c->ev[8], c->stream));
+  PE_CUDA_TRY(record_timing(c, c->ev[8]));
   PE_TRY(launch_coarse_sweep(c));
-  PE_CUDA_TRY(cudaEventRecord(c->ev[9], c->stream));
+  PE_CUDA_TRY(record_timing(c, c->ev[9]));
   c->fz_prec = -1;
   c->k = 0;
   c->have_problem = true;
@@ -621,6 +649,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
 extern "C" pe_status pe_set_problem(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
   if (!c) return pe_fail(PE_EINVAL, "pe_set_problem: ctx is NULL");
   c->have_problem = false;
+  drop_solve_graphs(c);
   PE_CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
   PE_TRY(set_problem_impl(c, u0, f));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -767,8 +796,8 @@ static pe_status build_loop_graph(pe_ctx* c) {
   return PE_OK;
 }
 
-// Iterations of pe_solve on the device: returns the last residual in *r and fills the history.
-static pe_status solve_loop_on_device(pe_ctx* c, double tol, pe_result* res, double* r) {
+// Iterations of pe_solve on the device, enqueued: the loop state in, the graph, the state back out.
+static pe_status enqueue_loop_on_device(pe_ctx* c, double tol) {
   PE_TRY(build_loop_graph(c));
   LoopCtl* h = c->h_loop;
   h->k = 0;
@@ -781,7 +810,12 @@ static pe_status solve_loop_on_device(pe_ctx* c, double tol, pe_result* res, dou
   PE_CUDA_TRY(cudaMemcpyAsync(c->loopctl, h, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->stream));
   PE_CUDA_TRY(cudaGraphLaunch(c->loop_exec, c->stream));
   PE_CUDA_TRY(cudaMemcpyAsync(h, c->loopctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->stream));
-  PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PE_OK;
+}
+
+// After the stream has completed: k, the last residual in *r, the history.
+static pe_status finish_loop_on_device(pe_ctx* c, pe_result* res, double* r) {
+  LoopCtl* h = c->h_loop;
   const int k = h->k;
   c->k += k;
   c->sweeps += k;
@@ -799,6 +833,72 @@ static pe_status solve_loop_on_device(pe_ctx* c, double tol, pe_result* res, dou
   return PE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// device_loop = 2: a problem solved again (same u0 description or device pointer, same source,
+// Dirichlet data and network) replays its set-up and output phases as CUDA graphs captured at its
+// second solve (the first solve runs them directly, which makes every lazily built table and
+// buffer exist before the capture).  The graphs re-execute every kernel; only the per-launch
+// overhead goes.
+// ---------------------------------------------------------------------------
+static uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 0x100000001B3ull;
+  }
+  return h;
+}
+
+static uint64_t problem_key(const pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  h = fnv(h, &u0->kind, sizeof(u0->kind));
+  h = fnv(h, &u0->n_terms, sizeof(u0->n_terms));
+  if (u0->terms && u0->n_terms > 0) h = fnv(h, u0->terms, sizeof(pe_term) * (size_t)u0->n_terms);
+  h = fnv(h, &u0->nodal, sizeof(u0->nodal));
+  const int nf = f ? f->n_terms : 0;
+  h = fnv(h, &nf, sizeof(nf));
+  if (nf > 0 && f->terms) h = fnv(h, f->terms, sizeof(pe_term) * (size_t)nf);
+  h = fnv(h, &c->nbd, sizeof(c->nbd));
+  if (c->nbd > 0) h = fnv(h, c->bterms, sizeof(pe_term) * (size_t)c->nbd);
+  h = fnv(h, &c->mlp, sizeof(c->mlp));
+  return h;
+}
+
+// Captures body() (which enqueues on c->stream) into *exec; *launches = the kernels it enqueued.
+// Returns false, with nothing enqueued and *exec null, when the phase cannot be captured.
+template <typename F>
+static bool capture_phase(pe_ctx* c, cudaGraphExec_t* exec, int64_t* launches, F body) {
+  cudaStream_t main_stream = c->stream;
+  const int64_t l0 = c->launches;
+  *exec = nullptr;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->stream = c->cap_stream;
+  c->capturing = 1;
+  const pe_status st = body();
+  c->capturing = 0;
+  c->stream = main_stream;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  *launches = c->launches - l0;
+  c->launches = l0;
+  bool ok = st == PE_OK && e == cudaSuccess && g != nullptr;
+  if (ok && cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    *exec = nullptr;
+    ok = false;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+static pe_status output_phase(pe_ctx* c) {
+  PE_TRY(modal_to_nodal(c, c->U + (int64_t)c->N * c->g.ndof, c->out_nodal));
+  return add_lift(c, c->t0 + c->T, 1.0, 3, c->out_nodal);
+}
+
 extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, pe_result* res) {
   if (!c) return pe_fail(PE_EINVAL, "pe_solve: ctx is NULL");
   if (!(tol >= 0.0)) return pe_fail(PE_EINVAL, "pe_solve: tol must be >= 0");
@@ -808,13 +908,47 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   c->ms_fine = 0.0;
   c->ms_corr = 0.0;
   c->sweeps = 0;
+  // graphs of the set-up and output phases: a device-resident loop, and u0 not in host memory
+  // (a copy from pageable host memory cannot be captured)
+  bool use_graphs = false;
+  c->u0_dev_hint = -1;
+  if (c->device_loop == 2 && loop_on_device(c) && u0) {
+    const bool host_u0 = u0->kind == PE_FIELD_NODAL && u0->nodal && !pe_is_device_ptr(u0->nodal);
+    if (!host_u0) {
+      if (u0->kind == PE_FIELD_NODAL) c->u0_dev_hint = 1;
+      const uint64_t key = problem_key(c, u0, f);
+      if (key != c->graph_key) {
+        drop_solve_graphs(c);
+        c->graph_key = key;
+      }
+      use_graphs = ++c->graph_key_seen >= 2;
+    }
+  }
   PE_CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
-  PE_TRY(set_problem_impl(c, u0, f));
+  if (use_graphs && !c->setup_exec &&
+      !capture_phase(c, &c->setup_exec, &c->setup_launches, [&] { return set_problem_impl(c, u0, f); })) {
+    use_graphs = false;  // not capturable: this problem runs its phases directly from now on
+    c->graph_key_seen = INT_MIN / 2;
+  }
+  if (use_graphs) {
+    // the host-side state is that of the previous solve of this problem (any other call that
+    // changes it drops the graphs); only the iteration state restarts
+    c->fz_prec = -1;
+    c->k = 0;
+    c->have_problem = true;
+    c->have_output = false;
+    PE_CUDA_TRY(cudaGraphLaunch(c->setup_exec, c->stream));
+    c->launches += c->setup_launches;
+  } else {
+    PE_TRY(set_problem_impl(c, u0, f));
+  }
+  c->u0_dev_hint = -1;
   PE_CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
   double r = INFINITY;
   int hist = 0;
-  if (loop_on_device(c)) {
-    PE_TRY(solve_loop_on_device(c, tol, res, &r));
+  const bool on_device = loop_on_device(c);
+  if (on_device) {
+    PE_TRY(enqueue_loop_on_device(c, tol));
   } else {
     while (c->k < c->max_iter) {
       PE_TRY(iter_impl(c, &r, c->precision));
@@ -824,10 +958,17 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
     }
   }
   PE_CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
-  PE_TRY(modal_to_nodal(c, c->U + (int64_t)c->N * c->g.ndof, c->out_nodal));
-  PE_TRY(add_lift(c, c->t0 + c->T, 1.0, 3, c->out_nodal));
+  if (use_graphs && !c->out_exec && !capture_phase(c, &c->out_exec, &c->out_launches, [&] { return output_phase(c); }))
+    use_graphs = false;
+  if (use_graphs) {
+    PE_CUDA_TRY(cudaGraphLaunch(c->out_exec, c->stream));
+    c->launches += c->out_launches;
+  } else {
+    PE_TRY(output_phase(c));
+  }
   PE_CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (on_device) PE_TRY(finish_loop_on_device(c, res, &r));
   c->have_output = true;
   if (res) {
     res->k = c->k;

@@ -174,6 +174,14 @@ struct pe_ctx {
   LoopCtl* loopctl = nullptr;       // device
   LoopCtl* h_loop = nullptr;        // pinned host copy
   double* loop_hist = nullptr;      // device [N]
+  // device_loop = 2: the set-up and output phases of a repeated problem replayed as CUDA graphs
+  cudaStream_t cap_stream = nullptr;  // capture stream (the context's own may be the legacy stream)
+  cudaGraphExec_t setup_exec = nullptr, out_exec = nullptr;
+  uint64_t graph_key = 0;           // problem the graphs were captured for
+  int graph_key_seen = 0;           // solves of graph_key so far (captured at the second)
+  int64_t setup_launches = 0, out_launches = 0;
+  int u0_dev_hint = -1;             // u0 nodal pointer is device memory (1) / host (0) / unknown (-1)
+  int capturing = 0;                // the phase being run is captured (timing events become graph nodes)
 };
 
 // Substeps of time factors (per_m values each) staged per shared-memory fill.
@@ -242,6 +250,8 @@ pe_status launch_general_fine_sweep(pe_ctx* c, int precision);
 // pe_fine_tc.cu (tensor-core engine of the mixed fine sweep)
 bool fine_tc_supported(int M);                 // M a multiple of 16 in 16..128
 size_t fine_tc_buffer_bytes(int M, int N);     // split time factors, any K <= 64
+// Drops the cached set-up and output graphs of a repeated problem (pe_api.cu).
+void drop_solve_graphs(pe_ctx* c);
 pe_status fine_tc_prepare(pe_ctx* c);          // split operand images of the current problem
 pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out);
 pe_status fine_tc_status(pe_ctx* c);           // PE_ETIMEOUT if a pipeline wait expired

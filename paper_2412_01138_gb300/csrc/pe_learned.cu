@@ -718,6 +718,7 @@ extern "C" pe_status pe_learned_samples(pe_ctx* c, int32_t n, const double* lam,
 
 extern "C" pe_status pe_set_learned(pe_ctx* c, const pe_mlp* m) {
   if (!c) return pe_fail(PE_EINVAL, "pe_set_learned: ctx is NULL");
+  drop_solve_graphs(c);
   c->mlp = m;
   return PE_OK;
 }
