@@ -130,7 +130,7 @@ void free_ctx(pe_ctx* c) {
                   c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
                   c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err, c->tcA,
-                  c->muM_full, c->ratio_full, c->fac_full, c->work2, c->loopctl, c->loop_hist};
+                  c->muM_full, c->ratio_full, c->fac_full, c->work2, c->loopctl, c->loop_hist, c->io32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -315,7 +315,15 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   // modal arrays hold this context's modes (nd); nodal arrays and per-axis loads the whole grid
   const size_t N = (size_t)n_slices, nd = (size_t)c->g.ndof, ndn = (size_t)ndof, MT = PE_MAX_TERMS;
   const int nsl = c->nsum;
-  c->max_blocks = (int)((nd + threads - 1) / threads) + 1;
+  // CTAs of the one-thread-per-mode kernels: at most one per 64 modes (per_mode_block)
+  c->max_blocks = (int)((nd + 63) / 64) + 1;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      c->sms = 0;
+    }
+  }
   st = PE_OK;
   if (st == PE_OK) st = dev_alloc(&c->muM_axis, nsl);
   if (st == PE_OK) st = dev_alloc(&c->ratio_axis, nsl);
@@ -334,6 +342,10 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK) st = dev_alloc(&c->gG, N * nd);
   if (st == PE_OK) st = dev_alloc(&c->work0, ndn + 64);
   if (st == PE_OK) st = dev_alloc(&c->work1, ndn + 64);
+  // the mixed form transforms u0 and the solution in float32 (grids of at least 4096 nodes whose
+  // axes all have FFT forms; below that the float64 transform is cheaper than the two conversions)
+  if (st == PE_OK && o.precision == PE_MIXED && ndn >= 4096 && dst_nd_f32_ok(c->gn))
+    st = dev_alloc(&c->io32, 3 * ndn + 64);
   if (st == PE_OK) st = dev_alloc(&c->out_nodal, ndn);
   if (st == PE_OK) st = dev_alloc(&c->partials, 2 * (size_t)c->max_blocks + 64);
   if (st == PE_OK) st = dev_alloc(&c->red, 2);
@@ -513,9 +525,15 @@ extern "C" pe_status pe_set_dirichlet(pe_ctx* c, int32_t n_terms, const pe_term*
 static int64_t slab_offset(const pe_ctx* c) { return (int64_t)c->base0 * (c->gn.ndof / c->gn.n[0]); }
 
 // modal_out = this context's modes of V^T nodal (nodal: whole grid, device; not work1 / work2)
+// the whole grid's transform: float32 arithmetic in the mixed form (where every axis has an FFT
+// form), float64 otherwise
+static pe_status dst_whole(pe_ctx* c, const double* in, double* out) {
+  return c->io32 ? dst_nd_mixed(c, in, out) : dst_nd_f64(c, in, out);
+}
+
 static pe_status nodal_to_modal(pe_ctx* c, const double* nodal, double* modal_out) {
-  if (!c->sharded) return dst_nd_f64(c, nodal, modal_out);
-  PE_TRY(dst_nd_f64(c, nodal, c->work2));
+  if (!c->sharded) return dst_whole(c, nodal, modal_out);
+  PE_TRY(dst_whole(c, nodal, c->work2));
   PE_CUDA_TRY(cudaMemcpyAsync(modal_out, c->work2 + slab_offset(c), sizeof(double) * c->g.ndof,
                               cudaMemcpyDeviceToDevice, c->stream));
   return PE_OK;
@@ -524,11 +542,11 @@ static pe_status nodal_to_modal(pe_ctx* c, const double* nodal, double* modal_ou
 // nodal_out (whole grid, device; not work1 / work2) = V applied to this context's modes, the
 // other modes taken as zero
 static pe_status modal_to_nodal(pe_ctx* c, const double* modal, double* nodal_out) {
-  if (!c->sharded) return dst_nd_f64(c, modal, nodal_out);
+  if (!c->sharded) return dst_whole(c, modal, nodal_out);
   PE_CUDA_TRY(cudaMemsetAsync(c->work2, 0, sizeof(double) * c->gn.ndof, c->stream));
   PE_CUDA_TRY(cudaMemcpyAsync(c->work2 + slab_offset(c), modal, sizeof(double) * c->g.ndof,
                               cudaMemcpyDeviceToDevice, c->stream));
-  return dst_nd_f64(c, c->work2, nodal_out);
+  return dst_whole(c, c->work2, nodal_out);
 }
 
 // ---------------------------------------------------------------------------

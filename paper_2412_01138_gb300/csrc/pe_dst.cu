@@ -1540,6 +1540,46 @@ pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out) {
   return dst_nd<double>(c->gn.d, c->gn.n, c->S, in, out, c->work1, c->stream, c->gn.per);
 }
 
+namespace {
+__global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void f32_to_f64_kernel(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+}  // namespace
+
+// Every axis has an FFT form (n + 1 a power of two, or a periodic axis of 128..1024 points),
+// so the float32 transform needs no DST-I matrices.
+bool dst_nd_f32_ok(const Geom& g) {
+  for (int a = 0; a < g.d; ++a) {
+    int logL = 0;
+    const int n = g.n[a];
+    const bool ok = g.per[a] ? (n == 128 || n == 256 || n == 512 || n == 1024) : fft_size_ok(n, &logL);
+    if (!ok) return false;
+  }
+  return true;
+}
+
+// The mixed form's transforms between nodal values and modal coefficients (u0 in, the solution
+// out): float64 data rounded to float32, the tensor DST-I in float32, widened back to float64.
+pe_status dst_nd_mixed(pe_ctx* c, const double* in, double* out) {
+  const int64_t nd = c->gn.ndof;
+  float* a = c->io32;
+  float* b = a + nd;
+  float* t = b + nd;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)std::min<int64_t>((nd + threads - 1) / threads, 8 * 152);
+  f64_to_f32_kernel<<<blocks, threads, 0, c->stream>>>(nd, in, a);
+  PE_TRY(dst_nd<float>(c->gn.d, c->gn.n, c->S32, a, b, t, c->stream, c->gn.per));
+  f32_to_f64_kernel<<<blocks, threads, 0, c->stream>>>(nd, b, out);
+  c->launches += c->gn.d + 2;
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
 extern "C" pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, void* stream) {
   return standalone_dst<double>(d, n, in, out, stream);
 }

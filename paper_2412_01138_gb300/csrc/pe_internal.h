@@ -118,6 +118,7 @@ struct pe_ctx {
   double* gG = nullptr;         // [N * ndof] coarse forcing of each slice
   double* work0 = nullptr;      // [gn.ndof] nodal / DST scratch
   double* work1 = nullptr;      // [gn.ndof]
+  float* io32 = nullptr;        // [3 gn.ndof] float32 transform scratch of the mixed form (null: float64 transforms)
   double* out_nodal = nullptr;  // [gn.ndof] inverse DST of U^N after pe_solve
   double* partials = nullptr;   // [2 * max_blocks]
   double* red = nullptr;        // [2] device
@@ -131,6 +132,7 @@ struct pe_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* h_red = nullptr;      // [2] pinned host
   int max_blocks = 0;
+  int sms = 0;                      // SMs of the context's device
   // forcing (set by pe_set_problem)
   int R = 0;
   pe_term terms[PE_MAX_TERMS];
@@ -225,7 +227,10 @@ pe_status dst_axis_f64(const double* S, const double* in, double* out, int64_t o
                        cudaStream_t st, int periodic = 0);
 pe_status dst_axis_f32(const float* S, const float* in, float* out, int64_t outer, int n, int64_t inner,
                        cudaStream_t st, int periodic = 0);
-pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);  // whole grid (c->gn); uses c->S, c->work1
+pe_status dst_nd_f64(pe_ctx* c, const double* in, double* out);
+// float64 data transformed in float32 arithmetic through c->io32 (FFT-length axes only)
+bool dst_nd_f32_ok(const Geom& g);
+pe_status dst_nd_mixed(pe_ctx* c, const double* in, double* out);  // whole grid (c->gn); uses c->S, c->work1
 // Per-axis source factors of every axis in one launch (loads -> DST-I -> / mu^M); *done = false when
 // an axis is periodic or n_a + 1 is not a power of two in 16..1024 (nothing launched then).
 pe_status axis_factors_fused(pe_ctx* c, int R, const double* loads, double* fac, float* fac32, bool* done);
@@ -250,6 +255,17 @@ pe_status launch_general_fine_sweep(pe_ctx* c, int precision);
 // pe_fine_tc.cu (tensor-core engine of the mixed fine sweep)
 bool fine_tc_supported(int M);                 // M a multiple of 16 in 16..128
 size_t fine_tc_buffer_bytes(int M, int N);     // split time factors, any K <= 64
+// Threads per CTA of a kernel with one thread per mode: when the modes fit one wave of CTAs,
+// as many warps as an even share of the SMs needs (every SM then runs one CTA of equal size,
+// rather than some SMs two CTAs of 256 threads and others one); 256 otherwise.
+inline int per_mode_block(int64_t units, int sms) {
+  if (sms <= 0) return 256;
+  const int64_t per_sm = (units + sms - 1) / sms;
+  if (per_sm > 512) return 256;
+  const int64_t t = (per_sm + 31) / 32 * 32;
+  return (int)(t < 64 ? 64 : t);
+}
+
 // Drops the cached set-up and output graphs of a repeated problem (pe_api.cu).
 void drop_solve_graphs(pe_ctx* c);
 pe_status fine_tc_prepare(pe_ctx* c);          // split operand images of the current problem

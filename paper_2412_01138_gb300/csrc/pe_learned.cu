@@ -94,30 +94,34 @@ __global__ void samples_kernel(int n, const double* __restrict__ lam, const doub
 // ---------------------------------------------------------------------------
 // training: one persistent cooperative launch runs every Adam step.  Per step
 //   1. every CTA loads the float32 parameters into shared memory and runs the forward and
-//      backward pass of its share of the batch, a warp per sample (rounds of TR_ROUND
-//      samples per CTA, activations and pre-activation gradients kept in shared memory);
-//   2. its threads sum the per-parameter products over those samples (a partial gradient
-//      per CTA, written as column c of partial[k][c]);
-//   3. grid barrier; each CTA owns a contiguous range of parameters and adds their G partials
-//      in CTA order (deterministic), then applies Adam (or, for a gradient evaluation, writes
-//      the gradient);
+//      backward pass of its share of the batch in rounds of TR_ROUND samples: the 2 -> 64 and
+//      64 -> 2 layers on the CUDA cores, the 64 x 64 layer's three contractions -- forward
+//      Z2 = H1 W2^T, backward dH1 = dZ2 W2 and the weight gradient dW2 = dZ2^T H1 -- as warp-level
+//      tensor-core MMAs (m16n8k8, TF32 operands split in two, float32 accumulation);
+//   2. the other parameters' gradients are summed per thread over the round's samples; each CTA
+//      writes its partial gradient as row c of partial[c][k];
+//   3. grid barrier; each CTA owns a contiguous range of parameters (a lane per parameter) and
+//      adds their G partials in a fixed order (deterministic), then applies Adam (or, for a
+//      gradient evaluation, writes the gradient);
 //   4. grid barrier (the next step reads the updated parameters).
 // Barriers are bounded waits: on expiry the CTA records an error and returns (every other
 // CTA then expires at its next wait); the host reports PE_ETIMEOUT.
 // ---------------------------------------------------------------------------
 constexpr int TR_THREADS = 512;
 constexpr int TR_WARPS = TR_THREADS / 32;
-constexpr int TR_ROUND = 32;          // samples per CTA per round
-constexpr int W2P = H + 1;            // padded row stride of W2 in shared memory (no bank conflicts)
-constexpr int NPARAM_L = NPARAM + 1;  // the gradient slots plus one slot for the loss
-constexpr int TR_PER_THREAD = (NPARAM_L + TR_THREADS - 1) / TR_THREADS;
+constexpr int TR_ROUND = 32;            // samples per CTA per round: the M of the MMA tiles
+constexpr int AP = H + 4;               // padded row stride of W2 and the activations in shared memory
+constexpr int NPARAM_L = NPARAM + 1;    // the gradient slots plus one slot for the loss
+constexpr int NSIMT = NPARAM_L - H * H;  // slots summed on the CUDA cores: all but W2
+static_assert(NSIMT <= TR_THREADS, "one CUDA-core gradient slot per thread");
+static_assert(TR_WARPS == 16 && TR_ROUND == 32 && H == 64, "MMA tile assignment below");
 constexpr long long kGridWaitCycles = 2000000000LL;  // about a second
 
 struct TrainArgs {
   float* params;
   float* adam_m;
   float* adam_v;
-  float* partial;        // [NPARAM_L][G]
+  float* partial;        // [G][NPARAM_L]: CTA c's partial gradient in row c
   const float* x;        // [n][2]
   const float* t;        // [n][2]
   int n, batch, steps_per_epoch, total, it0, nsteps;
@@ -126,36 +130,32 @@ struct TrainArgs {
   float inv_n;           // > 0: fixed loss weight (gradient evaluation); 0: 1 / (batch size)
   float* grad_out;       // gradient evaluation: the reduced gradient and loss [NPARAM_L]; else null
   unsigned* bar_count;
-  unsigned* bar_gen;
   int* err;
+  int own_cap;           // parameters a CTA owns at most (its Adam state stays in shared memory)
 };
 
 struct TrainSmem {
-  float W1[2 * H], b1[H], W2[H * W2P], b2[H], W3[2 * H], b3[2];
-  float H1[TR_ROUND][H], H2[TR_ROUND][H], DZ1[TR_ROUND][H], DZ2[TR_ROUND][H];
-  float X[TR_ROUND][2], DY[TR_ROUND][2], L[TR_ROUND];
+  float W2[H * AP];  // W2[i][j] at i * AP + j
+  float W1[2 * H], b1[H], b2[H], W3[2 * H], b3[2];
+  float H1[TR_ROUND * AP], H2[TR_ROUND * AP], DZ1[TR_ROUND * AP], DZ2[TR_ROUND * AP];  // [q][unit]
+  float X[TR_ROUND][2], TG[TR_ROUND][2], DY[TR_ROUND][2], L[TR_ROUND];
 };
 
-// grid-wide barrier of a cooperative launch; false if the wait expired
-__device__ bool grid_barrier(const TrainArgs& a, int* s_ok) {
+// Grid-wide barrier of a cooperative launch: the arrival counter only grows (the host zeroes it
+// before the launch), so barrier b of the launch is passed once it reads G (b + 1); every CTA
+// waits on the counter itself (no last-arriver broadcast).  False if the wait expired.
+__device__ bool grid_barrier(const TrainArgs& a, unsigned target, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned* gen = a.bar_gen;
-    const unsigned g = *gen;
     __threadfence();
-    if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
-      *a.bar_count = 0u;
-      __threadfence();
-      atomicExch(a.bar_gen, g + 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g) {
-        if (*(volatile int*)a.err || clock64() - t0 > kGridWaitCycles) {
-          atomicExch(a.err, 1);
-          ok = 0;
-          break;
-        }
+    atomicAdd(a.bar_count, 1u);
+    const long long t0 = clock64();
+    while (*(volatile unsigned*)a.bar_count < target) {
+      if (*(volatile int*)a.err || clock64() - t0 > kGridWaitCycles) {
+        atomicExch(a.err, 1);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -165,6 +165,51 @@ __device__ bool grid_barrier(const TrainArgs& a, int* s_ok) {
   return *s_ok != 0;
 }
 
+// --- warp-level TF32 MMA (m16n8k8, row-major A, column-major B, float32 accumulators) ---------
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// x = hi + lo, both TF32 (10 explicit mantissa bits each): hi + lo carries about 21 bits
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_bits(x);
+  lo = tf32_bits(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d += A[m0:m0+16, k0:k0+8] B[k0:k0+8, n0:n0+8] with A(m, k) = A_at(m, k), B(k, n) = B_at(k, n).
+// Three products of the split operands (lo hi, hi lo, hi hi; the lo lo term is below float32
+// rounding).  Fragment layout of m16n8k8: lane = 4 g + t holds A rows g, g + 8 at columns t,
+// t + 4, B rows t, t + 4 at column g, and D rows g, g + 8 at columns 2t, 2t + 1.
+template <class FA, class FB>
+__device__ __forceinline__ void mma3_tf32(float (&d)[4], FA A_at, FB B_at, int m0, int n0, int k0, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const float av[4] = {A_at(m0 + g, k0 + t), A_at(m0 + g + 8, k0 + t), A_at(m0 + g, k0 + t + 4),
+                       A_at(m0 + g + 8, k0 + t + 4)};
+  const float bv[2] = {B_at(k0 + t, n0 + g), B_at(k0 + t + 4, n0 + g)};
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tf32_split(av[i], ah[i], al[i]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) tf32_split(bv[i], bh[i], bl[i]);
+  mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+
+// D fragment element r of a tile at (m0, n0): row and column
+__device__ __forceinline__ int frag_row(int m0, int lane, int r) { return m0 + (lane >> 2) + (r >= 2 ? 8 : 0); }
+__device__ __forceinline__ int frag_col(int n0, int lane, int r) { return n0 + 2 * (lane & 3) + (r & 1); }
+
 __global__ void __launch_bounds__(TR_THREADS) train_kernel(TrainArgs a) {
   extern __shared__ __align__(16) unsigned char tr_smem[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(tr_smem);
@@ -173,13 +218,45 @@ __global__ void __launch_bounds__(TR_THREADS) train_kernel(TrainArgs a) {
   const int G = gridDim.x, c = blockIdx.x;
   // parameters this CTA reduces and updates
   const int k0 = (int)((int64_t)c * NPARAM_L / G), k1 = (int)((int64_t)(c + 1) * NPARAM_L / G);
+  // their parameter values and Adam moments, read once per launch and written back at its end
+  float* own_p = reinterpret_cast<float*>(tr_smem + sizeof(TrainSmem));
+  float* own_m = own_p + a.own_cap;
+  float* own_v = own_m + a.own_cap;
+  const bool adam = a.grad_out == nullptr;
+  if (adam) {
+    for (int k = k0 + tid; k < k1 && k < NPARAM; k += TR_THREADS) {
+      own_p[k - k0] = a.params[k];
+      own_m[k - k0] = a.adam_m[k];
+      own_v[k - k0] = a.adam_v[k];
+    }
+  }
+  // this thread's CUDA-core gradient slot: W1 and b1, then b2, W3, b3 and the loss
+  const int ks = tid < OW2 ? tid : tid + H * H;
+  // MMA tiles: forward / backward (32 x 64 outputs, 16 tiles of 16 x 8): one per warp;
+  // weight gradient (64 x 64, 32 tiles): two per warp
+  const int fm = (warp >> 3) * 16, fn = (warp & 7) * 8;
+  const int gm = (warp >> 2) * 16, gn = (warp & 3) * 16;
+  auto load_round = [&](int r0, int cnt) {
+    if (tid < TR_ROUND) {
+      const bool live = tid < cnt;
+      const int smp = r0 + tid;
+      S.X[tid][0] = live ? a.x[2 * smp] : 0.f;
+      S.X[tid][1] = live ? a.x[2 * smp + 1] : 0.f;
+      S.TG[tid][0] = live ? a.t[2 * smp] : 0.f;
+      S.TG[tid][1] = live ? a.t[2 * smp + 1] : 0.f;
+    }
+  };
   for (int s = 0; s < a.nsteps; ++s) {
     const int it = a.it0 + s;
     const int sidx = it % a.steps_per_epoch;
     const int off = sidx * a.batch;
     const int nb = min(a.batch, a.n - off);
     const float inv_n = a.inv_n > 0.f ? a.inv_n : 1.0f / (float)nb;
-    // 1. parameters into shared memory (from L2: other CTAs updated them in the last step)
+    // this CTA's samples of the batch
+    const int s0 = off + (int)((int64_t)c * nb / G), s1 = off + (int)((int64_t)(c + 1) * nb / G);
+    // 1. the first round's samples and the parameters into shared memory (parameters from L2:
+    //    other CTAs updated them in the last step)
+    load_round(s0, min(TR_ROUND, s1 - s0));
     for (int i = tid; i < 2 * H; i += TR_THREADS) {
       S.W1[i] = __ldcg(a.params + OW1 + i);
       S.W3[i] = __ldcg(a.params + OW3 + i);
@@ -188,37 +265,37 @@ __global__ void __launch_bounds__(TR_THREADS) train_kernel(TrainArgs a) {
       S.b1[i] = __ldcg(a.params + OB1 + i);
       S.b2[i] = __ldcg(a.params + OB2 + i);
     }
-    for (int i = tid; i < H * H; i += TR_THREADS) S.W2[(i / H) * W2P + (i % H)] = __ldcg(a.params + OW2 + i);
+    for (int i = tid; i < H * H; i += TR_THREADS) S.W2[(i >> 6) * AP + (i & (H - 1))] = __ldcg(a.params + OW2 + i);
     if (tid < 2) S.b3[tid] = __ldcg(a.params + OB3 + tid);
     __syncthreads();
-    // this CTA's samples of the batch
-    const int s0 = off + (int)((int64_t)c * nb / G), s1 = off + (int)((int64_t)(c + 1) * nb / G);
-    float acc[TR_PER_THREAD];
-#pragma unroll
-    for (int e = 0; e < TR_PER_THREAD; ++e) acc[e] = 0.f;
+    float gw[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};  // dW2 tiles of this warp
+    float gs = 0.f;                                                 // CUDA-core slot ks
     for (int r0 = s0; r0 < s1; r0 += TR_ROUND) {
       const int cnt = min(TR_ROUND, s1 - r0);
-      for (int q = warp; q < cnt; q += TR_WARPS) {
-        const int smp = r0 + q;
-        const float x0 = a.x[2 * smp], x1 = a.x[2 * smp + 1];
-        // layer 1: lane holds j = lane, lane + 32
-        float h1a = tanhf(fmaf(S.W1[2 * lane], x0, fmaf(S.W1[2 * lane + 1], x1, S.b1[lane])));
-        float h1b = tanhf(fmaf(S.W1[2 * (lane + 32)], x0, fmaf(S.W1[2 * (lane + 32) + 1], x1, S.b1[lane + 32])));
-        S.H1[q][lane] = h1a;
-        S.H1[q][lane + 32] = h1b;
-        __syncwarp();
-        // layer 2: lane holds i = lane, lane + 32
-        float za = S.b2[lane], zb = S.b2[lane + 32];
-#pragma unroll 16
-        for (int j = 0; j < H; ++j) {
-          const float hj = S.H1[q][j];
-          za = fmaf(S.W2[lane * W2P + j], hj, za);
-          zb = fmaf(S.W2[(lane + 32) * W2P + j], hj, zb);
+      // layer 1 (rows past cnt hold x = 0; their output gradients are zero below)
+      for (int e = tid; e < TR_ROUND * H; e += TR_THREADS) {
+        const int q = e >> 6, j = e & (H - 1);
+        S.H1[q * AP + j] = tanhf(fmaf(S.W1[2 * j], S.X[q][0], fmaf(S.W1[2 * j + 1], S.X[q][1], S.b1[j])));
+      }
+      __syncthreads();
+      // layer 2: Z2 = H1 W2^T (K = 64), H2 = tanh(Z2 + b2)
+      {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 0; kk < H; kk += 8)
+          mma3_tf32(
+              d, [&](int m, int k) { return S.H1[m * AP + k]; }, [&](int k, int n) { return S.W2[n * AP + k]; },
+              fm, fn, kk, lane);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int q = frag_row(fm, lane, r), i = frag_col(fn, lane, r);
+          S.H2[q * AP + i] = tanhf(d[r] + S.b2[i]);
         }
-        const float h2a = tanhf(za), h2b = tanhf(zb);
-        S.H2[q][lane] = h2a;
-        S.H2[q][lane + 32] = h2b;
-        // layer 3 (warp sums)
+      }
+      __syncthreads();
+      // layer 3, loss and the output gradients (a warp per sample)
+      for (int q = warp; q < TR_ROUND; q += TR_WARPS) {
+        const float h2a = S.H2[q * AP + lane], h2b = S.H2[q * AP + lane + 32];
         float y0 = fmaf(S.W3[lane], h2a, S.W3[lane + 32] * h2b);
         float y1 = fmaf(S.W3[H + lane], h2a, S.W3[H + lane + 32] * h2b);
 #pragma unroll
@@ -228,88 +305,126 @@ __global__ void __launch_bounds__(TR_THREADS) train_kernel(TrainArgs a) {
         }
         y0 += S.b3[0];
         y1 += S.b3[1];
-        const float e0 = y0 - a.t[2 * smp], e1 = y1 - a.t[2 * smp + 1];
-        const float d0 = e0 * inv_n, d1 = e1 * inv_n;
-        // backward to the pre-activations
-        const float dza = fmaf(S.W3[lane], d0, S.W3[H + lane] * d1) * (1.f - h2a * h2a);
-        const float dzb = fmaf(S.W3[lane + 32], d0, S.W3[H + lane + 32] * d1) * (1.f - h2b * h2b);
-        S.DZ2[q][lane] = dza;
-        S.DZ2[q][lane + 32] = dzb;
-        __syncwarp();
-        float ga = 0.f, gb = 0.f;
-#pragma unroll 16
-        for (int i = 0; i < H; ++i) {
-          const float di = S.DZ2[q][i];
-          ga = fmaf(S.W2[i * W2P + lane], di, ga);
-          gb = fmaf(S.W2[i * W2P + lane + 32], di, gb);
-        }
-        S.DZ1[q][lane] = ga * (1.f - h1a * h1a);
-        S.DZ1[q][lane + 32] = gb * (1.f - h1b * h1b);
+        const bool live = q < cnt;
+        const float e0 = y0 - S.TG[q][0], e1 = y1 - S.TG[q][1];
+        const float d0 = live ? e0 * inv_n : 0.f, d1 = live ? e1 * inv_n : 0.f;
+        S.DZ2[q * AP + lane] = fmaf(S.W3[lane], d0, S.W3[H + lane] * d1) * (1.f - h2a * h2a);
+        S.DZ2[q * AP + lane + 32] = fmaf(S.W3[lane + 32], d0, S.W3[H + lane + 32] * d1) * (1.f - h2b * h2b);
         if (lane == 0) {
-          S.X[q][0] = x0;
-          S.X[q][1] = x1;
           S.DY[q][0] = d0;
           S.DY[q][1] = d1;
-          S.L[q] = 0.5f * (e0 * e0 + e1 * e1) * inv_n;
+          S.L[q] = live ? 0.5f * (e0 * e0 + e1 * e1) * inv_n : 0.f;
         }
       }
       __syncthreads();
-      // 2. per-parameter sums over this round's samples
+      // backward through layer 2: dH1 = dZ2 W2 (K = 64), dZ1 = dH1 (1 - H1^2)
+      {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int e = 0; e < TR_PER_THREAD; ++e) {
-        const int k = tid + e * TR_THREADS;
+        for (int kk = 0; kk < H; kk += 8)
+          mma3_tf32(
+              d, [&](int m, int k) { return S.DZ2[m * AP + k]; }, [&](int k, int n) { return S.W2[k * AP + n]; },
+              fm, fn, kk, lane);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int q = frag_row(fm, lane, r), j = frag_col(fn, lane, r);
+          const float h = S.H1[q * AP + j];
+          S.DZ1[q * AP + j] = d[r] * (1.f - h * h);
+        }
+      }
+      // weight gradient dW2 += dZ2^T H1 (K = the round's 32 samples)
+#pragma unroll
+      for (int tt = 0; tt < 2; ++tt) {
+#pragma unroll
+        for (int kk = 0; kk < TR_ROUND; kk += 8)
+          mma3_tf32(
+              gw[tt], [&](int m, int k) { return S.DZ2[k * AP + m]; },
+              [&](int k, int n) { return S.H1[k * AP + n]; }, gm, gn + 8 * tt, kk, lane);
+      }
+      __syncthreads();
+      // 2. the CUDA-core gradient slots over this round's samples
+      if (tid < NSIMT) {
+        const int k = ks;
         float v = 0.f;
         if (k < OB1) {
           const int j = (k - OW1) >> 1, cc = (k - OW1) & 1;
-          for (int q = 0; q < cnt; ++q) v = fmaf(S.DZ1[q][j], S.X[q][cc], v);
+          for (int q = 0; q < cnt; ++q) v = fmaf(S.DZ1[q * AP + j], S.X[q][cc], v);
         } else if (k < OW2) {
-          for (int q = 0; q < cnt; ++q) v += S.DZ1[q][k - OB1];
-        } else if (k < OB2) {
-          const int i = (k - OW2) / H, j = (k - OW2) % H;
-          for (int q = 0; q < cnt; ++q) v = fmaf(S.DZ2[q][i], S.H1[q][j], v);
+          for (int q = 0; q < cnt; ++q) v += S.DZ1[q * AP + (k - OB1)];
         } else if (k < OW3) {
-          for (int q = 0; q < cnt; ++q) v += S.DZ2[q][k - OB2];
+          for (int q = 0; q < cnt; ++q) v += S.DZ2[q * AP + (k - OB2)];
         } else if (k < OB3) {
           const int o = (k - OW3) / H, i = (k - OW3) % H;
-          for (int q = 0; q < cnt; ++q) v = fmaf(S.DY[q][o], S.H2[q][i], v);
+          for (int q = 0; q < cnt; ++q) v = fmaf(S.DY[q][o], S.H2[q * AP + i], v);
         } else if (k < NPARAM) {
           for (int q = 0; q < cnt; ++q) v += S.DY[q][k - OB3];
-        } else if (k == NPARAM) {
+        } else {
           for (int q = 0; q < cnt; ++q) v += S.L[q];
         }
-        acc[e] += v;
+        gs += v;
       }
       __syncthreads();
+      if (r0 + TR_ROUND < s1) {
+        load_round(r0 + TR_ROUND, min(TR_ROUND, s1 - r0 - TR_ROUND));
+        __syncthreads();
+      }
     }
+    float* prow = a.partial + (int64_t)c * NPARAM_L;
+    if (tid < NSIMT) prow[ks] = gs;
 #pragma unroll
-    for (int e = 0; e < TR_PER_THREAD; ++e) {
-      const int k = tid + e * TR_THREADS;
-      if (k < NPARAM_L) a.partial[(int64_t)k * G + c] = acc[e];
-    }
-    if (!grid_barrier(a, &s_ok)) return;
-    // 3. this CTA's parameters: the G partials in CTA order, then Adam (or the gradient out)
+    for (int tt = 0; tt < 2; ++tt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = frag_row(gm, lane, r), j = frag_col(gn + 8 * tt, lane, r);
+        prow[OW2 + i * H + j] = gw[tt][r];
+      }
+    if (!grid_barrier(a, (unsigned)G * (unsigned)(2 * s + 1), &s_ok)) return;
+    // 3. this CTA's parameters: lane l of warp w adds the partials of parameter kb + l of the
+    //    CTAs w, w + 16, ...; warp 0 adds the 16 warp sums in warp order, then Adam (or the
+    //    gradient out)
     const long long step = a.adam_step0 + s + 1;
     const float bc1 = 1.f - powf(a.b1, (float)step), bc2 = 1.f - powf(a.b2, (float)step);
     const float cosv = 0.5f * (1.f + cospif((float)it / (float)a.total));
     const float lr_t = a.lr * (0.01f + 0.99f * cosv);
-    for (int k = k0 + warp; k < k1; k += TR_WARPS) {
-      float g = 0.f;
-      for (int cc = lane; cc < G; cc += 32) g += __ldcg(a.partial + (int64_t)k * G + cc);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-      if (lane == 0) {
-        if (a.grad_out) {
-          a.grad_out[k] = g;
-        } else if (k < NPARAM) {
-          const float mk = a.b1 * a.adam_m[k] + (1.f - a.b1) * g;
-          const float vk = a.b2 * a.adam_v[k] + (1.f - a.b2) * g * g;
-          a.adam_m[k] = mk;
-          a.adam_v[k] = vk;
-          a.params[k] -= lr_t * (mk / bc1) / (sqrtf(vk / bc2) + a.eps);
-        }
+    auto apply = [&](int k, float g) {
+      if (!adam) {
+        a.grad_out[k] = g;
+      } else if (k < NPARAM) {
+        const int i = k - k0;
+        const float mk = a.b1 * own_m[i] + (1.f - a.b1) * g;
+        const float vk = a.b2 * own_v[i] + (1.f - a.b2) * g * g;
+        own_m[i] = mk;
+        own_v[i] = vk;
+        const float pk = own_p[i] - lr_t * (mk / bc1) / (sqrtf(vk / bc2) + a.eps);
+        own_p[i] = pk;
+        a.params[k] = pk;
       }
+    };
+    float* wsum = S.H2;  // [TR_WARPS][32] (the activations are dead until the next step)
+    for (int kb = k0; kb < k1; kb += 32) {
+      const int k = kb + lane;
+      float g = 0.f;
+      if (k < k1) {
+#pragma unroll 4
+        for (int cc = warp; cc < G; cc += TR_WARPS) g += __ldcg(a.partial + (int64_t)cc * NPARAM_L + k);
+      }
+      wsum[warp * 32 + lane] = g;
+      __syncthreads();
+      if (warp == 0 && k < k1) {
+        float tot = 0.f;
+#pragma unroll
+        for (int w = 0; w < TR_WARPS; ++w) tot += wsum[w * 32 + lane];
+        apply(k, tot);
+      }
+      __syncthreads();
     }
-    if (!grid_barrier(a, &s_ok)) return;
+    if (!grid_barrier(a, (unsigned)G * (unsigned)(2 * s + 2), &s_ok)) return;
+  }
+  if (adam) {
+    for (int k = k0 + tid; k < k1 && k < NPARAM; k += TR_THREADS) {
+      a.adam_m[k] = own_m[k - k0];
+      a.adam_v[k] = own_v[k - k0];
+    }
   }
 }
 
@@ -586,11 +701,13 @@ static pe_status run_train(pe_mlp* m, const float* x, const float* t, int n, int
   PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   PE_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return pe_fail(PE_ECUDA, "pe_mlp: the device does not support cooperative launches");
-  const size_t smem = sizeof(TrainSmem);
+  const int own_cap = (NPARAM_L + sms - 1) / sms + 1;
+  const size_t smem = sizeof(TrainSmem) + 3 * sizeof(float) * (size_t)own_cap;
+  if (smem > 200 * 1024) return pe_fail(PE_ECUDA, "pe_mlp: too few SMs for the training kernel");
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [smem] {
-    attr = cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   if (attr != cudaSuccess) return pe_cuda_fail(attr, "pe_mlp: shared-memory attribute");
   int per_sm = 0;
@@ -607,7 +724,7 @@ static pe_status run_train(pe_mlp* m, const float* x, const float* t, int n, int
     }
     m->partial_cap = G;
   }
-  PE_CUDA_TRY(cudaMemsetAsync(m->sync, 0, 3 * sizeof(unsigned), st));  // barrier count, generation, error
+  PE_CUDA_TRY(cudaMemsetAsync(m->sync, 0, 3 * sizeof(unsigned), st));  // barrier count, (unused), error
   TrainArgs a{};
   a.params = m->params;
   a.adam_m = m->adam_m;
@@ -629,8 +746,8 @@ static pe_status run_train(pe_mlp* m, const float* x, const float* t, int n, int
   a.inv_n = inv_n;
   a.grad_out = grad_out;
   a.bar_count = m->sync;
-  a.bar_gen = m->sync + 1;
   a.err = (int*)(m->sync + 2);
+  a.own_cap = own_cap;
   void* args[] = {&a};
   PE_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)train_kernel, dim3(G), dim3(TR_THREADS), args, smem, st));
   PE_CUDA_TRY(cudaGetLastError());

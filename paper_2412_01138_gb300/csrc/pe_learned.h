@@ -13,9 +13,9 @@ struct pe_mlp {
   float* adam_m = nullptr;
   float* adam_v = nullptr;
   float* loss_dev = nullptr;
-  float* partial = nullptr;   // per-CTA partial gradients of the training kernel [NPARAM + 1][CTAs]
+  float* partial = nullptr;   // per-CTA partial gradients of the training kernel [CTAs][NPARAM + 1]
   int partial_cap = 0;        // CTAs partial has room for
-  unsigned* sync = nullptr;   // grid barrier of the training kernel: count, generation, error flag
+  unsigned* sync = nullptr;   // grid barrier of the training kernel: arrival count, unused, error flag
   int64_t step = 0;
 };
 

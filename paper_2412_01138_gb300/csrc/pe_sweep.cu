@@ -125,7 +125,7 @@ pe_status launch_coarse_forcing_t(pe_ctx* c, unsigned blocks, int threads, int S
 // log(lam dT) between the band centres) and the phase table staged beside the time factors:
 // the same float32 sum, added to gG_n in float64, as the separate learned-correction kernel.
 template <typename T, int RB, bool LEARN>
-__global__ void __launch_bounds__(256) coarse_fused_kernel(Geom g, int N, int p, int R,
+__global__ void __launch_bounds__(512) coarse_fused_kernel(Geom g, int N, int p, int R,
                                                           const T* __restrict__ axisF, const T* __restrict__ AG,
                                                           const double* __restrict__ coefG, double* __restrict__ U,
                                                           LearnedTerms L, const double* __restrict__ axisF64,
@@ -337,7 +337,7 @@ __device__ void loop_decide(LoopCtl* L, unsigned long long handle, double num, d
 // the next kCorrPF slices are issued before the current kCorrPF are combined.
 constexpr int kCorrPF = 8;
 
-__global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const double* __restrict__ muM_axis,
+__global__ void __launch_bounds__(512) correction_kernel(Geom g, int N, const double* __restrict__ muM_axis,
                                                          const double* __restrict__ coefG,
                                                          const double* __restrict__ Fbar, double* __restrict__ U,
                                                          double* __restrict__ partials,
@@ -427,6 +427,8 @@ __global__ void __launch_bounds__(256) correction_kernel(Geom g, int N, const do
 pe_status launch_coarse_sweep(pe_ctx* c) {
   const int threads = 256;
   const unsigned blocks = (unsigned)((c->g.ndof + threads - 1) / threads);
+  const int fthreads = per_mode_block(c->g.ndof, c->sms);
+  const unsigned fblocks = (unsigned)((c->g.ndof + fthreads - 1) / fthreads);
   if (c->forcing_path == PE_FORCING_GENERAL) {
     PE_TRY(launch_general_coarse_forcing(c));
     coarse_recurrence_kernel<<<blocks, threads, 0, c->stream>>>(c->g, c->N, c->coefG, c->gG, c->U);
@@ -440,8 +442,8 @@ pe_status launch_coarse_sweep(pe_ctx* c) {
     if (c->mlp) PE_TRY(launch_learned_tables(c, &L));
     const LearnedTerms* Lp = c->mlp ? &L : nullptr;
     bool done = false;
-    if (c->precision == PE_MIXED) PE_TRY(launch_coarse_fused_t<float>(c, blocks, threads, c->axisF32, c->AG32, Lp, &done));
-    else PE_TRY(launch_coarse_fused_t<double>(c, blocks, threads, c->axisF, c->AG, Lp, &done));
+    if (c->precision == PE_MIXED) PE_TRY(launch_coarse_fused_t<float>(c, fblocks, fthreads, c->axisF32, c->AG32, Lp, &done));
+    else PE_TRY(launch_coarse_fused_t<double>(c, fblocks, fthreads, c->axisF, c->AG, Lp, &done));
     if (done) {
       c->launches += 1;
       return PE_OK;
@@ -472,7 +474,7 @@ pe_status launch_correction(pe_ctx* c, double* num, double* den, cudaEvent_t aft
 }
 
 pe_status launch_correction_kernel(pe_ctx* c, LoopCtl* loop, unsigned long long handle) {
-  const int threads = 256;
+  const int threads = per_mode_block(c->g.ndof, c->sms);
   const int64_t blocks = (c->g.ndof + threads - 1) / threads;
   if (blocks > (int64_t)c->max_blocks) return pe_fail(PE_EINVAL, "correction: partials buffer too small");
   correction_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(c->g, c->N, c->muM_axis, c->coefG, c->Fbar, c->U,

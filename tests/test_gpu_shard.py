@@ -6,7 +6,7 @@ an all-reduce across GPUs would.  Per mode the shards run the same arithmetic as
 unsharded context (the per-axis tables are the rows of the same whole-axis tables), so their
 modal iterates are bitwise those of the unsharded solve; the combined residual equals the
 unsharded one up to summation order (1e-15), and so does the sum of the shards' nodal
-fields.  A third test drives pe_solve of one shard with the residual_reduce callback
+fields (to float32 rounding in the mixed form, whose output transform runs in float32).  A third test drives pe_solve of one shard with the residual_reduce callback
 adding the other shard's recorded sums.
 """
 import numpy as np
@@ -62,7 +62,10 @@ def test_two_shards_in_turn_match_the_unsharded_solve(pe, name, n, prec, engine)
             got = np.concatenate([s.modal(sl) for s in shards])
             assert np.array_equal(got, ref_modal[sl]), sl
         nodal = sum(s.solution(prob.N) for s in shards)
-        assert np.abs(nodal - ref_nodal).max() <= 1e-14 * np.abs(ref_nodal).max()
+        # the mixed form transforms its output in float32: the shards' sum then agrees with the
+        # whole transform to float32 rounding
+        bound = 1e-14 if prec == 0 else 1e-6
+        assert np.abs(nodal - ref_nodal).max() <= bound * np.abs(ref_nodal).max()
         # the shard's own tables are rows of the whole tables
         lam_full = osolver.ModalSystem(prob).lam
         inner = prob.ndof // n[0]
