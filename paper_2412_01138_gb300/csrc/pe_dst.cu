@@ -566,8 +566,10 @@ __host__ __device__ constexpr int pass_bits(int left, int logl) {
 
 // radix plans of the pass twiddle tables: the one-warp form (pass_bits), the half-length form
 // (half_pass_bits) and the team form (team_pass_bits: radix 16 while 4 bits remain)
-constexpr int kPlanWarp = 0, kPlanHalf = 1, kPlanTeam = 2;
+constexpr int kPlanWarp = 0, kPlanHalf = 1, kPlanTeam = 2, kPlanTwo = 3;
 __host__ __device__ constexpr int team_pass_bits(int left) { return left >= 4 ? 4 : left; }
+// the two-pass float32 form at L = 512: radix 32, then radix 16
+__host__ __device__ constexpr int two_pass_bits(int left, int logl) { return left == logl ? 5 : left; }
 constexpr int team_tw_entries(int left, int ns) {
   return left == 0 ? 0
                    : (ns > 1 ? ns * (1 << team_pass_bits(left)) : 0) +
@@ -961,6 +963,297 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
 }
 
 // ---------------------------------------------------------------------------
+// Two-pass form of the float32 odd-extension FFT at L = 512 points (n = 255), contiguous
+// pencils (the last axis).  A warp owns two pencil pairs, lanes 16 h + j (h = 0, 1) the pair
+// h.  Pass 1 (radix 32 over the 16 groups j of a pair) takes its inputs straight from the
+// rows in global memory -- z_ext[j + 16 r] = z[j + 16 r - 1] for r < 16 -- and the mirrored
+// half z_ext[m] = -z_ext[512 - m] (r >= 16) from the lane 16 - j of the same pair by shuffles;
+// its outputs cross shared memory once; pass 2 (radix 16 over the 32 groups of a pair, the
+// whole warp on one pair at a time) yields X[j + 32 r] in natural order, of which the DST
+// needs only m = 1..255 (r < 8), stored straight to the output rows.  Shared memory carries
+// one write and one read per point (the one-warp form: the odd extension and three Stockham
+// passes).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 2) dst512_contig_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                               int64_t npencils, float scale,
+                                                               const Cplx<float>* __restrict__ tw2) {
+  constexpr int L = 512, n = 255, PS = L + L / 16 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, WARPS = blockDim.x >> 5;
+  const int h = lane >> 4, j = lane & 15;
+  Cplx<float>* buf = reinterpret_cast<Cplx<float>*>(smem_raw) + (size_t)warp * 2 * PS;
+  const int64_t npairs = (npencils + 1) / 2, nquads = (npairs + 1) / 2;
+  const int src = ((16 - j) & 15) | (h << 4);
+  for (int64_t q = (int64_t)blockIdx.x * WARPS + warp; q < nquads; q += (int64_t)gridDim.x * WARPS) {
+    const int64_t pa = 2 * (2 * q + h), pb = pa + 1;
+    const bool has_a = pa < npencils, has_b = pb < npencils;
+    const float* xa = in + pa * n;
+    const float* xb = in + pb * n;
+    Cplx<float> v[32];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int m = j + 16 * r;
+      v[r].re = (m >= 1 && has_a) ? xa[m - 1] : 0.f;
+      v[r].im = (m >= 1 && has_b) ? xb[m - 1] : 0.f;
+    }
+#pragma unroll
+    for (int r = 16; r < 32; ++r) {
+      // 512 - m = 16 (31 - r) + (16 - j) for j >= 1; 16 (32 - r) for j = 0 (lane 0's own row)
+      float re = __shfl_sync(0xffffffffu, v[31 - r].re, src);
+      float im = __shfl_sync(0xffffffffu, v[31 - r].im, src);
+      if (j == 0) {
+        re = r == 16 ? 0.f : v[32 - r].re;
+        im = r == 16 ? 0.f : v[32 - r].im;
+      }
+      v[r] = Cplx<float>{-re, -im};
+    }
+    dft_regs<float, 32>(v);
+    Cplx<float>* a = buf + h * PS;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) a[fpad(32 * j + r)] = v[brevc(r, 5)];
+    __syncwarp();
+#pragma unroll 1
+    for (int p = 0; p < 2; ++p) {
+      const Cplx<float>* b = buf + p * PS;
+      Cplx<float> u[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) u[r] = b[fpad(lane + 32 * r)];
+#pragma unroll
+      for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], ldg_cplx(tw2 + 32 * r + lane));
+      dft_regs<float, 16>(u);
+      const int64_t qa = 2 * (2 * q + p), qb = qa + 1;
+      float* ya = out + qa * n;
+      float* yb = out + qb * n;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int m = lane + 32 * r;
+        if (m >= 1) {
+          const Cplx<float> X = u[brevc(r, 4)];
+          if (qa < npencils) ya[m - 1] = -X.im * scale;
+          if (qb < npencils) yb[m - 1] = X.re * scale;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// The same two passes for strided pencils: a CTA of W warps owns blocks of 4 W consecutive
+// pencils (warp w: pencils 4w .. 4w + 3), staged row by row (row j: the 4 W values of one
+// position, contiguous when the pencils are) by cp.async into a double buffer, padded to 4 W + 2
+// floats so that a lane reads its pencil pair as one float2; pass 1 reads the rows of the stage,
+// pass 2 writes the DST values back into the same stage, and the rows leave it coalesced.
+// W warps per CTA: blocks of P = 4 W pencils, stage rows of P + 2 floats.
+template <int W>
+__global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                                int64_t inner, int64_t npencils, float scale,
+                                                                const Cplx<float>* __restrict__ tw2) {
+  constexpr int L = 512, n = 255, PS = L + L / 16 + 1, P = 4 * W, SP = P + 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int h = lane >> 4, j = lane & 15;
+  float* stage[2] = {reinterpret_cast<float*>(smem_raw), reinterpret_cast<float*>(smem_raw) + n * SP};
+  Cplx<float>* buf = reinterpret_cast<Cplx<float>*>(stage[1] + n * SP) + (size_t)warp * 2 * PS;
+  __shared__ int64_t offs[2][P];
+  const int64_t nblk = (npencils + P - 1) / P;
+  const int src = ((16 - j) & 15) | (h << 4);
+  // thread tid copies column pl = tid % 32 of rows tid / 32, + 8, ... (a warp: one 128-byte row)
+  const int pl = tid & (P - 1), row0 = tid / P;
+  constexpr int RSTEP = 32 * W / P;
+  auto issue = [&](int64_t blk, int b) {
+    if (tid < P) {
+      const int64_t p = blk * P + tid;
+      offs[b][tid] = p < npencils ? (p / inner) * (int64_t)n * inner + (p % inner) : -1;
+    }
+    __syncthreads();
+    const int64_t o = offs[b][pl];
+    float* dst = stage[b] + row0 * SP + pl;
+    if (o >= 0) {
+      const float* srcp = in + o + (int64_t)row0 * inner;
+      const int64_t step = (int64_t)RSTEP * inner;
+      for (int jj = row0; jj < n; jj += RSTEP, dst += RSTEP * SP, srcp += step) cp_async_elem(dst, srcp);
+    } else {
+      for (int jj = row0; jj < n; jj += RSTEP, dst += RSTEP * SP) *dst = 0.f;
+    }
+    cp_async_commit();
+  };
+  int cur = 0;
+  if ((int64_t)blockIdx.x < nblk) issue(blockIdx.x, 0);
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x, cur ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t next = blk + gridDim.x;
+    if (next < nblk) issue(next, cur ^ 1);
+    const float* st = stage[cur];
+    // pass 1 on this warp's pencil pair h: columns 4 warp + 2 h, + 1 of the stage rows
+    const int col = 4 * warp + 2 * h;
+    Cplx<float> v[32];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int m = j + 16 * r;
+      if (m >= 1) {
+        const float2 z = *reinterpret_cast<const float2*>(st + (m - 1) * SP + col);
+        v[r] = Cplx<float>{z.x, z.y};
+      } else {
+        v[r] = Cplx<float>{0.f, 0.f};
+      }
+    }
+#pragma unroll
+    for (int r = 16; r < 32; ++r) {
+      float re = __shfl_sync(0xffffffffu, v[31 - r].re, src);
+      float im = __shfl_sync(0xffffffffu, v[31 - r].im, src);
+      if (j == 0) {
+        re = r == 16 ? 0.f : v[32 - r].re;
+        im = r == 16 ? 0.f : v[32 - r].im;
+      }
+      v[r] = Cplx<float>{-re, -im};
+    }
+    dft_regs<float, 32>(v);
+    Cplx<float>* a = buf + h * PS;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) a[fpad(32 * j + r)] = v[brevc(r, 5)];
+    // a warp reads and writes only its own four columns of the stage, so its DST values go back
+    // into them once its own lanes are done (the pair buffers are per warp too)
+    __syncwarp();
+    float* ost = stage[cur];
+#pragma unroll 1
+    for (int p = 0; p < 2; ++p) {
+      const Cplx<float>* b = buf + p * PS;
+      Cplx<float> u[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) u[r] = b[fpad(lane + 32 * r)];
+#pragma unroll
+      for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], ldg_cplx(tw2 + 32 * r + lane));
+      dft_regs<float, 16>(u);
+      const int oc = 4 * warp + 2 * p;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int m = lane + 32 * r;
+        if (m >= 1) {
+          const Cplx<float> X = u[brevc(r, 4)];
+          *reinterpret_cast<float2*>(ost + (m - 1) * SP + oc) = make_float2(-X.im * scale, X.re * scale);
+        }
+      }
+    }
+    __syncthreads();
+    {
+      const int64_t o = offs[cur][pl];
+      if (o >= 0) {
+        float* dstp = out + o + (int64_t)row0 * inner;
+        const float* sp = ost + row0 * SP + pl;
+        const int64_t step = (int64_t)RSTEP * inner;
+        for (int k = row0; k < n; k += RSTEP, sp += RSTEP * SP, dstp += step) *dstp = *sp;
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+// Two passes at L = 1024 points (n = 511), strided pencils: radix 32 over the 32 groups of a
+// pair (a whole warp, the mirrored half of the extension from lane 32 - j), one exchange through
+// shared memory, radix 32 again, of whose outputs X[j + 32 r] the DST needs r < 16.  A CTA of W
+// warps owns blocks of 4 W consecutive pencils staged as above (511 rows, double buffered); a warp runs its two pencil pairs one after the other through one pair buffer and
+// keeps their outputs in registers until every warp is done with the stage.
+template <int W>
+__global__ void __launch_bounds__(32 * W) dst1024_strided_kernel(const float* __restrict__ in,
+                                                                 float* __restrict__ out, int64_t inner,
+                                                                 int64_t npencils, float scale,
+                                                                 const Cplx<float>* __restrict__ tw2) {
+  constexpr int L = 1024, n = 511, PS = L + L / 16 + 1, P = 4 * W, SP = P + 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* stage[2] = {reinterpret_cast<float*>(smem_raw), reinterpret_cast<float*>(smem_raw) + n * SP};
+  Cplx<float>* a = reinterpret_cast<Cplx<float>*>(stage[1] + n * SP) + (size_t)warp * PS;
+  __shared__ int64_t offs[2][P];
+  const int64_t nblk = (npencils + P - 1) / P;
+  const int src = (32 - lane) & 31;
+  const int pl = tid & (P - 1), row0 = tid / P;
+  constexpr int RSTEP = 32 * W / P;
+  auto issue = [&](int64_t blk, int b) {
+    if (tid < P) {
+      const int64_t p = blk * P + tid;
+      offs[b][tid] = p < npencils ? (p / inner) * (int64_t)n * inner + (p % inner) : -1;
+    }
+    __syncthreads();
+    const int64_t o = offs[b][pl];
+    float* dst = stage[b] + row0 * SP + pl;
+    if (o >= 0) {
+      const float* srcp = in + o + (int64_t)row0 * inner;
+      const int64_t step = (int64_t)RSTEP * inner;
+      for (int jj = row0; jj < n; jj += RSTEP, dst += RSTEP * SP, srcp += step) cp_async_elem(dst, srcp);
+    } else {
+      for (int jj = row0; jj < n; jj += RSTEP, dst += RSTEP * SP) *dst = 0.f;
+    }
+    cp_async_commit();
+  };
+  int cur = 0;
+  if ((int64_t)blockIdx.x < nblk) issue(blockIdx.x, 0);
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x, cur ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t next = blk + gridDim.x;
+    if (next < nblk) issue(next, cur ^ 1);
+    float* st = stage[cur];
+    // a warp reads and writes only its own four columns of the stage: the DST values of a pair
+    // go back into the columns its inputs came from as soon as they are ready
+#pragma unroll 1
+    for (int p = 0; p < 2; ++p) {
+      const int col = 4 * warp + 2 * p;
+      Cplx<float> v[32];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int m = lane + 32 * r;
+        if (m >= 1) {
+          const float2 z = *reinterpret_cast<const float2*>(st + (m - 1) * SP + col);
+          v[r] = Cplx<float>{z.x, z.y};
+        } else {
+          v[r] = Cplx<float>{0.f, 0.f};
+        }
+      }
+#pragma unroll
+      for (int r = 16; r < 32; ++r) {
+        // 1024 - m = 32 (31 - r) + (32 - j) for j >= 1; 32 (32 - r) for j = 0 (lane 0's own row)
+        float re = __shfl_sync(0xffffffffu, v[31 - r].re, src);
+        float im = __shfl_sync(0xffffffffu, v[31 - r].im, src);
+        if (lane == 0) {
+          re = r == 16 ? 0.f : v[32 - r].re;
+          im = r == 16 ? 0.f : v[32 - r].im;
+        }
+        v[r] = Cplx<float>{-re, -im};
+      }
+      dft_regs<float, 32>(v);
+      __syncwarp();  // the previous pair's reads of the pair buffer are done
+#pragma unroll
+      for (int r = 0; r < 32; ++r) a[fpad(32 * lane + r)] = v[brevc(r, 5)];
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = a[fpad(lane + 32 * r)];
+#pragma unroll
+      for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], ldg_cplx(tw2 + 32 * r + lane));
+      dft_regs<float, 32>(v);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int m = lane + 32 * r;
+        const Cplx<float> X = v[brevc(r, 5)];
+        if (m >= 1) *reinterpret_cast<float2*>(st + (m - 1) * SP + col) = make_float2(-X.im * scale, X.re * scale);
+      }
+    }
+    __syncthreads();
+    const float* ost = st;
+    {
+      const int64_t o = offs[cur][pl];
+      if (o >= 0) {
+        float* dstp = out + o + (int64_t)row0 * inner;
+        const float* sp = ost + row0 * SP + pl;
+        const int64_t step = (int64_t)RSTEP * inner;
+        for (int k = row0; k < n; k += RSTEP, sp += RSTEP * SP, dstp += step) *dstp = *sp;
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------
 // Team form of the odd-extension FFT for long float32 pencils (L = 2(n+1) = 1024, 2048): a team
 // of TW warps (TS = 32 TW threads, synchronised by a named barrier) owns one pencil pair, so a
 // lane holds L / (16 TS) radix-16 groups -- 16 complex values -- instead of the L/32 of the
@@ -1131,8 +1424,10 @@ __global__ void pass_twiddle_kernel(int logl, int total, Cplx<T>* out) {
   if (e >= total) return;
   int e0 = 0, ns = 1, left = logl;
   while (left > 0) {
-    const int rb = PLAN == kPlanHalf ? half_pass_bits<T>(left, logl)
-                                     : (PLAN == kPlanTeam ? team_pass_bits(left) : pass_bits<T>(left, logl));
+    const int rb = PLAN == kPlanHalf   ? half_pass_bits<T>(left, logl)
+                   : PLAN == kPlanTeam ? team_pass_bits(left)
+                   : PLAN == kPlanTwo  ? two_pass_bits(left, logl)
+                                       : pass_bits<T>(left, logl);
     const int R = 1 << rb;
     if (ns > 1) {
       if (e < e0 + ns * R) {
@@ -1320,6 +1615,81 @@ pe_status fft_team_launch(const T* in, T* out, int n, int64_t inner, int64_t npe
   return PE_OK;
 }
 
+// the two-pass float32 kernel: contiguous pencils of n = 255 (L = 512)
+pe_status fft512_contig_launch(const float* in, float* out, int64_t npencils, float scale, cudaStream_t st) {
+  constexpr int PS = 512 + 512 / 16 + 1, WARPS = 8;
+  const size_t smem = sizeof(Cplx<float>) * 2 * PS * WARPS;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [smem] {
+    attr = cudaFuncSetAttribute(dst512_contig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr != cudaSuccess) return pe_cuda_fail(attr, "dst: shared-memory attribute");
+  constexpr int NTW = 16 * 32;
+  const Cplx<float>* tw2 = pass_twiddles<float, kPlanTwo>(9, NTW, st);
+  if (!tw2) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  int dev = 0, sms = 0, per_sm = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_contig_kernel, 32 * WARPS, smem));
+  const int64_t nquads = ((npencils + 1) / 2 + 1) / 2;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nquads + WARPS - 1) / WARPS,
+                                                              (int64_t)sms * std::max(per_sm, 1)));
+  dst512_contig_kernel<<<(unsigned)grid, 32 * WARPS, smem, st>>>(in, out, npencils, scale, tw2);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+// the two-pass float32 kernel: strided pencils of n = 255 (L = 512)
+constexpr int kStridedWarps = 8;  // warps per CTA of the strided two-pass kernels (32 pencils per block)
+pe_status fft512_strided_launch(const float* in, float* out, int64_t inner, int64_t npencils, float scale,
+                                cudaStream_t st) {
+  constexpr int PS = 512 + 512 / 16 + 1, W = kStridedWarps, P = 4 * W;
+  const size_t smem = sizeof(float) * 2 * 255 * (P + 2) + sizeof(Cplx<float>) * 2 * PS * W;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [smem] {
+    attr = cudaFuncSetAttribute(dst512_strided_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr != cudaSuccess) return pe_cuda_fail(attr, "dst: shared-memory attribute");
+  const Cplx<float>* tw2 = pass_twiddles<float, kPlanTwo>(9, 16 * 32, st);
+  if (!tw2) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  int dev = 0, sms = 0, per_sm = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_strided_kernel<W>, 32 * W, smem));
+  const int64_t nblk = (npencils + P - 1) / P;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * std::max(per_sm, 1)));
+  dst512_strided_kernel<W><<<(unsigned)grid, 32 * W, smem, st>>>(in, out, inner, npencils, scale, tw2);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+// the two-pass float32 kernel: strided pencils of n = 511 (L = 1024)
+pe_status fft1024_strided_launch(const float* in, float* out, int64_t inner, int64_t npencils, float scale,
+                                 cudaStream_t st) {
+  constexpr int PS = 1024 + 1024 / 16 + 1, W = kStridedWarps, P = 4 * W;
+  const size_t smem = sizeof(float) * 2 * 511 * (P + 2) + sizeof(Cplx<float>) * PS * W;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [smem] {
+    attr = cudaFuncSetAttribute(dst1024_strided_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr != cudaSuccess) return pe_cuda_fail(attr, "dst: shared-memory attribute");
+  const Cplx<float>* tw2 = pass_twiddles<float, kPlanTwo>(10, 32 * 32, st);
+  if (!tw2) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  int dev = 0, sms = 0, per_sm = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst1024_strided_kernel<W>, 32 * W, smem));
+  if (per_sm < 1) return pe_fail(PE_ECUDA, "dst: the 1024-point strided kernel does not fit an SM");
+  const int64_t nblk = (npencils + P - 1) / P;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * per_sm));
+  dst1024_strided_kernel<W><<<(unsigned)grid, 32 * W, smem, st>>>(in, out, inner, npencils, scale, tw2);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
 template <typename T>
 pe_status fft_warp_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int logL, cudaStream_t st,
                         bool* done) {
@@ -1347,9 +1717,13 @@ pe_status fft_warp_axis(const T* in, T* out, int64_t outer, int n, int64_t inner
       case 6: return fft_warp_launch<T, 6>(in, out, n, inner, np, scale, st);
       case 7: return fft_warp_launch<T, 7>(in, out, n, inner, np, scale, st);
       case 8: return fft_warp_launch<T, 8>(in, out, n, inner, np, scale, st);
-      case 9: return fft_warp_launch<T, 9>(in, out, n, inner, np, scale, st);
+      case 9:
+        if (inner == 1) return fft512_contig_launch(in, out, np, scale, st);
+        return fft512_strided_launch(in, out, inner, np, scale, st);
       // 1024 and 2048 points: two or four warps per pencil pair (16 complex values per lane)
-      case 10: return fft_team_launch<T, 10, 2>(in, out, n, inner, np, scale, st);
+      case 10:
+        if (inner > 1) return fft1024_strided_launch(in, out, inner, np, scale, st);
+        return fft_team_launch<T, 10, 2>(in, out, n, inner, np, scale, st);
       case 11: return fft_team_launch<T, 11, 4>(in, out, n, inner, np, scale, st);
       default:
         break;
@@ -1459,6 +1833,43 @@ __global__ void dst_matrix_kernel_t(int n, T* S) {
   S[(int64_t)j * n + k] = (T)(sqrt(2.0 / (double)(n + 1)) * sinpi((double)m / (double)(n + 1)));
 }
 
+// The library's own stream-ordered memory pool of a device for the scratch of the standalone
+// transforms: it keeps freed memory (release threshold unlimited), so that repeated calls of
+// one size do not map and unmap it from the driver each time; the process's default pool is
+// left as it is.
+cudaMemPool_t scratch_pool() {
+  static cudaMemPool_t pools[64] = {};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+template <typename T>
+cudaError_t scratch_alloc(T** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = scratch_pool();
+  return pool ? cudaMallocFromPoolAsync((void**)p, bytes, pool, st) : cudaMallocAsync((void**)p, bytes, st);
+}
+
 template <typename T>
 pe_status standalone_dst(int32_t d, const int32_t* n, const T* in, T* out, void* stream) {
   if (d < 1 || d > PE_MAX_D || !n || !in || !out) return pe_fail(PE_EINVAL, "pe_dst: bad arguments");
@@ -1473,14 +1884,17 @@ pe_status standalone_dst(int32_t d, const int32_t* n, const T* in, T* out, void*
   T* S[PE_MAX_D] = {nullptr, nullptr, nullptr};
   T* tmp = nullptr;
   pe_status rc = PE_OK;
+  // the DST-I matrix only of axes without an FFT form (n + 1 not a power of two)
   for (int a = 0; a < d && rc == PE_OK; ++a) {
-    cudaError_t e = cudaMallocAsync((void**)&S[a], sizeof(T) * (size_t)nn[a] * nn[a], st);
+    int logL = 0;
+    if (fft_size_ok(nn[a], &logL)) continue;
+    cudaError_t e = scratch_alloc(&S[a], sizeof(T) * (size_t)nn[a] * nn[a], st);
     if (e != cudaSuccess) { rc = pe_cuda_fail(e, "cudaMallocAsync(S)"); break; }
     dim3 grid((nn[a] + 127) / 128, nn[a]);
     dst_matrix_kernel_t<T><<<grid, 128, 0, st>>>(nn[a], S[a]);
   }
   if (rc == PE_OK && (d > 1 || in == out)) {
-    cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(T) * (size_t)ndof, st);
+    cudaError_t e = scratch_alloc(&tmp, sizeof(T) * (size_t)ndof, st);
     if (e != cudaSuccess) rc = pe_cuda_fail(e, "cudaMallocAsync(tmp)");
   }
   if (rc == PE_OK) rc = dst_nd<T>(d, nn, S, in, out, tmp, st);
