@@ -974,7 +974,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
 // one write and one read per point (the one-warp form: the odd extension and three Stockham
 // passes).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 2) dst512_contig_kernel(const float* __restrict__ in, float* __restrict__ out,
+// TI, TO: the input and output element types (float64 data is rounded to float32 on load and
+// the float32 result widened on store: the mixed form's transforms of float64 fields).
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256, 2) dst512_contig_kernel(const TI* __restrict__ in, TO* __restrict__ out,
                                                                int64_t npencils, float scale,
                                                                const Cplx<float>* __restrict__ tw2) {
   constexpr int L = 512, n = 255, PS = L + L / 16 + 1;
@@ -987,14 +990,14 @@ __global__ void __launch_bounds__(256, 2) dst512_contig_kernel(const float* __re
   for (int64_t q = (int64_t)blockIdx.x * WARPS + warp; q < nquads; q += (int64_t)gridDim.x * WARPS) {
     const int64_t pa = 2 * (2 * q + h), pb = pa + 1;
     const bool has_a = pa < npencils, has_b = pb < npencils;
-    const float* xa = in + pa * n;
-    const float* xb = in + pb * n;
+    const TI* xa = in + pa * n;
+    const TI* xb = in + pb * n;
     Cplx<float> v[32];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int m = j + 16 * r;
-      v[r].re = (m >= 1 && has_a) ? xa[m - 1] : 0.f;
-      v[r].im = (m >= 1 && has_b) ? xb[m - 1] : 0.f;
+      v[r].re = (m >= 1 && has_a) ? (float)xa[m - 1] : 0.f;
+      v[r].im = (m >= 1 && has_b) ? (float)xb[m - 1] : 0.f;
     }
 #pragma unroll
     for (int r = 16; r < 32; ++r) {
@@ -1022,15 +1025,15 @@ __global__ void __launch_bounds__(256, 2) dst512_contig_kernel(const float* __re
       for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], ldg_cplx(tw2 + 32 * r + lane));
       dft_regs<float, 16>(u);
       const int64_t qa = 2 * (2 * q + p), qb = qa + 1;
-      float* ya = out + qa * n;
-      float* yb = out + qb * n;
+      TO* ya = out + qa * n;
+      TO* yb = out + qb * n;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int m = lane + 32 * r;
         if (m >= 1) {
           const Cplx<float> X = u[brevc(r, 4)];
-          if (qa < npencils) ya[m - 1] = -X.im * scale;
-          if (qb < npencils) yb[m - 1] = X.re * scale;
+          if (qa < npencils) ya[m - 1] = (TO)(-X.im * scale);
+          if (qb < npencils) yb[m - 1] = (TO)(X.re * scale);
         }
       }
     }
@@ -1044,8 +1047,9 @@ __global__ void __launch_bounds__(256, 2) dst512_contig_kernel(const float* __re
 // floats so that a lane reads its pencil pair as one float2; pass 1 reads the rows of the stage,
 // pass 2 writes the DST values back into the same stage, and the rows leave it coalesced.
 // W warps per CTA: blocks of P = 4 W pencils, stage rows of P + 2 floats.
-template <int W>
-__global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const float* __restrict__ in, float* __restrict__ out,
+// (TI = double: the rows are converted on the way into the stage by plain loads.)
+template <int W, typename TI, typename TO>
+__global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const TI* __restrict__ in, TO* __restrict__ out,
                                                                 int64_t inner, int64_t npencils, float scale,
                                                                 const Cplx<float>* __restrict__ tw2) {
   constexpr int L = 512, n = 255, PS = L + L / 16 + 1, P = 4 * W, SP = P + 2;
@@ -1069,9 +1073,20 @@ __global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const float* __r
     const int64_t o = offs[b][pl];
     float* dst = stage[b] + row0 * SP + pl;
     if (o >= 0) {
-      const float* srcp = in + o + (int64_t)row0 * inner;
+      const TI* srcp = in + o + (int64_t)row0 * inner;
       const int64_t step = (int64_t)RSTEP * inner;
-      for (int jj = row0; jj < n; jj += RSTEP, dst += RSTEP * SP, srcp += step) cp_async_elem(dst, srcp);
+      if constexpr (sizeof(TI) == 4) {
+        for (int jj = row0; jj < n; jj += RSTEP, dst += RSTEP * SP, srcp += step) cp_async_elem(dst, srcp);
+      } else {
+        // every load of the thread's rows issued before the first store
+        constexpr int NR = (n + RSTEP - 1) / RSTEP;
+        float vals[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) vals[q] = row0 + q * RSTEP < n ? (float)__ldg(srcp + q * step) : 0.f;
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+          if (row0 + q * RSTEP < n) dst[q * RSTEP * SP] = vals[q];
+      }
     } else {
       for (int jj = row0; jj < n; jj += RSTEP, dst += RSTEP * SP) *dst = 0.f;
     }
@@ -1139,10 +1154,10 @@ __global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const float* __r
     {
       const int64_t o = offs[cur][pl];
       if (o >= 0) {
-        float* dstp = out + o + (int64_t)row0 * inner;
+        TO* dstp = out + o + (int64_t)row0 * inner;
         const float* sp = ost + row0 * SP + pl;
         const int64_t step = (int64_t)RSTEP * inner;
-        for (int k = row0; k < n; k += RSTEP, sp += RSTEP * SP, dstp += step) *dstp = *sp;
+        for (int k = row0; k < n; k += RSTEP, sp += RSTEP * SP, dstp += step) *dstp = (TO)*sp;
       }
     }
   }
@@ -1615,41 +1630,17 @@ pe_status fft_team_launch(const T* in, T* out, int n, int64_t inner, int64_t npe
   return PE_OK;
 }
 
-// the two-pass float32 kernel: contiguous pencils of n = 255 (L = 512)
-pe_status fft512_contig_launch(const float* in, float* out, int64_t npencils, float scale, cudaStream_t st) {
-  constexpr int PS = 512 + 512 / 16 + 1, WARPS = 8;
-  const size_t smem = sizeof(Cplx<float>) * 2 * PS * WARPS;
+// the two-pass float32 kernels at n = 255 (L = 512); warps per CTA: 8, or 1 when the pencils
+// are too few to give every SM a CTA of 8 warps (the mixed form's transforms of small grids)
+template <typename TI, typename TO>
+pe_status fft512_contig_launch(const TI* in, TO* out, int64_t npencils, float scale, cudaStream_t st) {
+  constexpr int PS = 512 + 512 / 16 + 1;
+  const size_t smem8 = sizeof(Cplx<float>) * 2 * PS * 8;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [smem] {
-    attr = cudaFuncSetAttribute(dst512_contig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  if (attr != cudaSuccess) return pe_cuda_fail(attr, "dst: shared-memory attribute");
-  constexpr int NTW = 16 * 32;
-  const Cplx<float>* tw2 = pass_twiddles<float, kPlanTwo>(9, NTW, st);
-  if (!tw2) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
-  int dev = 0, sms = 0, per_sm = 0;
-  PE_CUDA_TRY(cudaGetDevice(&dev));
-  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_contig_kernel, 32 * WARPS, smem));
-  const int64_t nquads = ((npencils + 1) / 2 + 1) / 2;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nquads + WARPS - 1) / WARPS,
-                                                              (int64_t)sms * std::max(per_sm, 1)));
-  dst512_contig_kernel<<<(unsigned)grid, 32 * WARPS, smem, st>>>(in, out, npencils, scale, tw2);
-  PE_CUDA_TRY(cudaGetLastError());
-  return PE_OK;
-}
-
-// the two-pass float32 kernel: strided pencils of n = 255 (L = 512)
-constexpr int kStridedWarps = 8;  // warps per CTA of the strided two-pass kernels (32 pencils per block)
-pe_status fft512_strided_launch(const float* in, float* out, int64_t inner, int64_t npencils, float scale,
-                                cudaStream_t st) {
-  constexpr int PS = 512 + 512 / 16 + 1, W = kStridedWarps, P = 4 * W;
-  const size_t smem = sizeof(float) * 2 * 255 * (P + 2) + sizeof(Cplx<float>) * 2 * PS * W;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [smem] {
-    attr = cudaFuncSetAttribute(dst512_strided_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  std::call_once(once, [smem8] {
+    attr = cudaFuncSetAttribute(dst512_contig_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem8);
   });
   if (attr != cudaSuccess) return pe_cuda_fail(attr, "dst: shared-memory attribute");
   const Cplx<float>* tw2 = pass_twiddles<float, kPlanTwo>(9, 16 * 32, st);
@@ -1657,12 +1648,51 @@ pe_status fft512_strided_launch(const float* in, float* out, int64_t inner, int6
   int dev = 0, sms = 0, per_sm = 0;
   PE_CUDA_TRY(cudaGetDevice(&dev));
   PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_strided_kernel<W>, 32 * W, smem));
-  const int64_t nblk = (npencils + P - 1) / P;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * std::max(per_sm, 1)));
-  dst512_strided_kernel<W><<<(unsigned)grid, 32 * W, smem, st>>>(in, out, inner, npencils, scale, tw2);
+  const int64_t nquads = ((npencils + 1) / 2 + 1) / 2;
+  const int warps = nquads < 8 * (int64_t)sms ? 1 : 8;
+  const size_t smem = sizeof(Cplx<float>) * 2 * PS * warps;
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_contig_kernel<TI, TO>, 32 * warps, smem));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nquads + warps - 1) / warps,
+                                                              (int64_t)sms * std::max(per_sm, 1)));
+  dst512_contig_kernel<TI, TO><<<(unsigned)grid, 32 * warps, smem, st>>>(in, out, npencils, scale, tw2);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
+}
+
+constexpr int kStridedWarps = 8;  // warps per CTA of the strided two-pass kernels (32 pencils per block)
+template <int W, typename TI, typename TO>
+pe_status fft512_strided_launch_w(const TI* in, TO* out, int64_t inner, int64_t npencils, float scale,
+                                  cudaStream_t st) {
+  constexpr int PS = 512 + 512 / 16 + 1, P = 4 * W;
+  const size_t smem = sizeof(float) * 2 * 255 * (P + 2) + sizeof(Cplx<float>) * 2 * PS * W;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [smem] {
+    attr = cudaFuncSetAttribute(dst512_strided_kernel<W, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  });
+  if (attr != cudaSuccess) return pe_cuda_fail(attr, "dst: shared-memory attribute");
+  const Cplx<float>* tw2 = pass_twiddles<float, kPlanTwo>(9, 16 * 32, st);
+  if (!tw2) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  int dev = 0, sms = 0, per_sm = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_strided_kernel<W, TI, TO>, 32 * W, smem));
+  const int64_t nblk = (npencils + P - 1) / P;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * std::max(per_sm, 1)));
+  dst512_strided_kernel<W, TI, TO><<<(unsigned)grid, 32 * W, smem, st>>>(in, out, inner, npencils, scale, tw2);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
+}
+
+template <typename TI, typename TO>
+pe_status fft512_strided_launch(const TI* in, TO* out, int64_t inner, int64_t npencils, float scale, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  PE_CUDA_TRY(cudaGetDevice(&dev));
+  PE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (npencils < 4 * kStridedWarps * (int64_t)sms)
+    return fft512_strided_launch_w<1, TI, TO>(in, out, inner, npencils, scale, st);
+  return fft512_strided_launch_w<kStridedWarps, TI, TO>(in, out, inner, npencils, scale, st);
 }
 
 // the two-pass float32 kernel: strided pencils of n = 511 (L = 1024)
@@ -1979,11 +2009,44 @@ bool dst_nd_f32_ok(const Geom& g) {
 
 // The mixed form's transforms between nodal values and modal coefficients (u0 in, the solution
 // out): float64 data rounded to float32, the tensor DST-I in float32, widened back to float64.
+namespace {
+template <typename TI, typename TO>
+pe_status fft512_axis(const TI* in, TO* out, int64_t inner, int64_t npencils, float scale, cudaStream_t st) {
+  if (inner == 1) return fft512_contig_launch<TI, TO>(in, out, npencils, scale, st);
+  return fft512_strided_launch<TI, TO>(in, out, inner, npencils, scale, st);
+}
+}  // namespace
+
 pe_status dst_nd_mixed(pe_ctx* c, const double* in, double* out) {
   const int64_t nd = c->gn.ndof;
   float* a = c->io32;
   float* b = a + nd;
   float* t = b + nd;
+  // every axis n = 255: the two-pass kernels, the first reading the float64 input and the last
+  // writing the float64 output (no conversion launches)
+  bool two = true;
+  for (int ax = 0; ax < c->gn.d; ++ax) two = two && !c->gn.per[ax] && c->gn.n[ax] == 255;
+  if (two) {
+    const int d = c->gn.d;
+    const float scale = (float)(0.5 * sqrt(2.0 / 256.0));
+    const int64_t np = nd / 255;
+    const float* src = nullptr;
+    for (int ax = 0; ax < d; ++ax) {
+      int64_t inner = 1;
+      for (int q = ax + 1; q < d; ++q) inner *= c->gn.n[q];
+      float* dstf = (ax & 1) ? b : a;
+      const bool first = ax == 0, last = ax == d - 1;
+      pe_status st = PE_OK;
+      if (first && last) st = fft512_axis<double, double>(in, out, inner, np, scale, c->stream);
+      else if (first) st = fft512_axis<double, float>(in, dstf, inner, np, scale, c->stream);
+      else if (last) st = fft512_axis<float, double>(src, out, inner, np, scale, c->stream);
+      else st = fft512_axis<float, float>(src, dstf, inner, np, scale, c->stream);
+      PE_TRY(st);
+      src = dstf;
+    }
+    c->launches += d;
+    return PE_OK;
+  }
   const int threads = 256;
   const unsigned blocks = (unsigned)std::min<int64_t>((nd + threads - 1) / threads, 8 * 152);
   f64_to_f32_kernel<<<blocks, threads, 0, c->stream>>>(nd, in, a);
