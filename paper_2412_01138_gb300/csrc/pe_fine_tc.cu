@@ -167,35 +167,60 @@ __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, 
     Bsp[(((int64_t)g * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
 }
 
-// Split stage weights of every mode tile, in the A-operand layout of the kernel below:
-// tile q occupies 3 * 128 * KP * 2 bytes, [term][row r][k] swizzled as above, row r holding
-// W[k][128 q + r] (zero past the last mode and past K).
-__global__ void ft_split_w_kernel(const float* __restrict__ W, int64_t nd, int K, int KP, int64_t tiles,
-                                  uint4* __restrict__ Asp) {
-  const int chunks = KP / 8;
-  const int64_t total = tiles * FT_ROWS * chunks;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  const int r = (int)(e % FT_ROWS);
-  const int64_t rest = e / FT_ROWS;
-  const int c = (int)(rest % chunks);
-  const int64_t tile = rest / chunks;
-  const int64_t J = tile * FT_ROWS + r;
-  float x[8];
+// Stage weights of every mode tile formed and split in one pass, in the A-operand layout of the
+// kernel below: tile q occupies 3 * 128 * KP * 2 bytes, [term][row r][k] swizzled as above, row
+// r holding W[k][128 q + r] (zero past the last mode and past K).  A thread per row: the same
+// float32 arithmetic as the SIMT engine's stage-weight table, W[k][J] = P_{r(k),J} sum_i
+// (dt b_i)_J Z_k(c_i dt) with P the product of the per-axis modal factors, so that table is never
+// written or read by this engine.
+__global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols C, int R, int q,
+                                                               const float* __restrict__ axisF,
+                                                               const float* __restrict__ coef_b,
+                                                               const double* __restrict__ Z, int KP, int64_t tiles,
+                                                               uint4* __restrict__ Asp) {
+  __shared__ float sZ[PE_MAX_S * 2 * PE_MAX_TERMS];
+  __shared__ int sTerm[2 * PE_MAX_TERMS];
+  const int K = C.K;
+  for (int e = threadIdx.x; e < q * K; e += blockDim.x) sZ[e] = (float)Z[e];
+  for (int e = threadIdx.x; e < K; e += blockDim.x) sTerm[e] = C.term[e];
+  __syncthreads();
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= tiles * FT_ROWS) return;
+  const int r = (int)(J % FT_ROWS);
+  const int64_t tile = J / FT_ROWS, nd = g.ndof;
+  const bool ok = J < nd;
+  int j[PE_MAX_D] = {0, 0, 0};
+  float b[PE_MAX_S];
+  if (ok) unflatten(g, J, j);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int k = 8 * c + j;
-    x[j] = (J < nd && k < K) ? W[(int64_t)k * nd + J] : 0.f;
-  }
-  uint4 o[3];
-  split8(x, o);
+  for (int i = 0; i < PE_MAX_S; ++i) b[i] = (ok && i < q) ? coef_b[(int64_t)i * nd + J] : 0.f;
   const int64_t term = (int64_t)FT_ROWS * KP * 2;
+  for (int c = 0; c < KP / 8; ++c) {
+    float x[8];
 #pragma unroll
-  for (int t = 0; t < 3; ++t) Asp[((tile * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
+    for (int jj = 0; jj < 8; ++jj) {
+      const int k = 8 * c + jj;
+      float v = 0.f;
+      if (ok && k < K) {
+        const int rt = sTerm[k];
+        float P = axisF[(int64_t)R * g.off[0] + (int64_t)rt * g.n[0] + j[0]];
+        for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)rt * g.n[a] + j[a]];
+        float sw = 0.f;
+#pragma unroll
+        for (int i = 0; i < PE_MAX_S; ++i)
+          if (i < q) sw = fmaf(b[i], sZ[i * K + k], sw);
+        v = P * sw;
+      }
+      x[jj] = v;
+    }
+    uint4 o[3];
+    split8(x, o);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) Asp[((tile * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = o[t];
+  }
 }
 
 struct FtArgs {
-  const float* W32;      // stage weights [K][ndof]
   const float* coefF32;  // E_hi [ndof], E_lo [ndof]
   const double* EM;      // exp(-lam M dt) [ndof]
   const double* U;       // U^n at n * ndof
@@ -845,9 +870,9 @@ pe_status fine_tc_prepare(pe_ctx* c) {
   ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
                                                                                  ngroups, (uint4*)c->tcB);
   PE_CUDA_TRY(cudaGetLastError());
-  const int64_t nsw = tiles * FT_ROWS * (KP / 8);
-  ft_split_w_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(c->Wst32, c->g.ndof, K, KP, tiles,
-                                                                           (uint4*)c->tcA);
+  const int64_t nsw = tiles * FT_ROWS;
+  ft_weights_image_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(
+      c->g, c->cols, c->R, c->q, c->axisF32, c->coefF32 + 2 * c->g.ndof, c->Zst, KP, tiles, (uint4*)c->tcA);
   PE_CUDA_TRY(cudaGetLastError());
   c->tc_split_ok = true;
   c->launches += 2;
@@ -864,7 +889,6 @@ pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out) {
   ft_shape(KP, M, N, &G, &NR, &ngroups);
   const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
   FtArgs args{};
-  args.W32 = c->Wst32;
   args.coefF32 = c->coefF32;
   args.EM = c->coefF + (int64_t)(c->q + 1) * c->g.ndof;
   args.U = c->U;

@@ -241,6 +241,12 @@ pe_status launch_stage_weights(pe_ctx* c) {
   }
   const int threads = 256;
   const unsigned blocks = (unsigned)((c->g.ndof + threads - 1) / threads);
+  if (c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC && c->forcing_path == PE_FORCING_SEPARABLE) {
+    // the tensor-core engine forms its float32 weights inside its operand split
+    // (fine_tc_prepare); the float64 ones follow on the first float64 sweep (pe_refine)
+    c->Wst_valid = false;
+    return PE_OK;
+  }
   if (c->precision == PE_MIXED) {
     // the float32 fine sweeps need only the float32 weights; the float64 ones follow on the
     // first float64 sweep (pe_refine)
