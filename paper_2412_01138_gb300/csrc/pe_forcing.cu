@@ -104,25 +104,35 @@ __global__ void stage_weights_kernel(Geom g, StageCols C, int R, int q, const T*
 }
 
 // 1D consistent loads of every (term, axis): out[R*off[a] + r*n_a + k] = int g_{r,a} phi_{k+1}.
-__global__ void loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2, double h0, double h1,
-                                double h2, Gauss G, double* __restrict__ out) {
+// Eight lanes per node (blockDim = 8 x 32 nodes): lane s evaluates the quadrature points
+// e = s, s + 8, ... of the node's 2 npts (its left element's points, then its right element's),
+// and the eight partial sums are added by shuffles in a fixed order.  The float64 exponentials
+// and sines of the factors thus spread over eight times more warps than a thread per node.
+constexpr int kLoadLanes = 8;
+__global__ void __launch_bounds__(256) loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2,
+                                                       double h0, double h1, double h2, Gauss G,
+                                                       double* __restrict__ out) {
   const int a = blockIdx.z;
   const int r = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // 0-based node, node number k+1
-  if (a >= g.d || r >= T.n || k >= g.n[a]) return;
+  const int sub = threadIdx.x & (kLoadLanes - 1);
+  const int k = blockIdx.x * (blockDim.x / kLoadLanes) + threadIdx.x / kLoadLanes;  // 0-based node
+  if (a >= g.d || r >= T.n || k >= g.n[a]) return;  // whole groups of eight lanes leave together
   const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
   const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
   const pe_term& t = T.t[r];
   const int lk = T.lk[r][a];
+  const unsigned grp = 0xFFu << (threadIdx.x & 24);  // this node's eight lanes of the warp
   if (lk != 0) {
     // lifting of Dirichlet data: the factor at full-grid nodes k, k+1, k+2 (x = lo + i h)
-    const double g0 = eval_space(t.skind[a], t.sp[a], lo + (double)k * h);
-    const double g1 = eval_space(t.skind[a], t.sp[a], lo + (double)(k + 1) * h);
-    const double g2 = eval_space(t.skind[a], t.sp[a], lo + (double)(k + 2) * h);
-    double v = g1;
-    if (lk == 1) v = (h / 6.0) * (g0 + 4.0 * g1 + g2);
-    else if (lk == 2) v = (1.0 / h) * (2.0 * g1 - g0 - g2);
-    out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = v;
+    if (sub == 0) {
+      const double g0 = eval_space(t.skind[a], t.sp[a], lo + (double)k * h);
+      const double g1 = eval_space(t.skind[a], t.sp[a], lo + (double)(k + 1) * h);
+      const double g2 = eval_space(t.skind[a], t.sp[a], lo + (double)(k + 2) * h);
+      double v = g1;
+      if (lk == 1) v = (h / 6.0) * (g0 + 4.0 * g1 + g2);
+      else if (lk == 2) v = (1.0 / h) * (2.0 * g1 - g0 - g2);
+      out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = v;
+    }
     return;
   }
   // Dirichlet: node k sits at lo + (k+1) h; element k ([lo + k h, lo + (k+1) h]) has it as
@@ -130,14 +140,16 @@ __global__ void loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, doub
   // at lo + k h; the elements are k-1 (element n-1 for k = 0) and k.
   const int el = g.per[a] ? (k == 0 ? g.n[a] - 1 : k - 1) : k;
   const int er = g.per[a] ? k : k + 1;
-  double left = 0.0, right = 0.0;
-  for (int qi = 0; qi < G.npts; ++qi) {
-    const double xl = lo + ((double)el + G.s[qi]) * h;
-    const double xr = lo + ((double)er + G.s[qi]) * h;
-    left += G.w[qi] * eval_space(t.skind[a], t.sp[a], xl) * G.s[qi];
-    right += G.w[qi] * eval_space(t.skind[a], t.sp[a], xr) * (1.0 - G.s[qi]);
+  double part = 0.0;
+  for (int e = sub; e < 2 * G.npts; e += kLoadLanes) {
+    const bool left = e < G.npts;
+    const int qi = left ? e : e - G.npts;
+    const double x = lo + ((double)(left ? el : er) + G.s[qi]) * h;
+    part += G.w[qi] * eval_space(t.skind[a], t.sp[a], x) * (left ? G.s[qi] : 1.0 - G.s[qi]);
   }
-  out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = h * left + h * right;
+#pragma unroll
+  for (int o = kLoadLanes / 2; o > 0; o >>= 1) part += __shfl_xor_sync(grp, part, o);
+  if (sub == 0) out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = h * part;
 }
 
 __global__ void divide_axis_mu_kernel(Geom g, int R, const double* __restrict__ muM, double* __restrict__ x,
@@ -332,9 +344,10 @@ static pe_status separable_factors_whole(pe_ctx* c, const pe_term* terms, int nt
   int nmax = 1;
   for (int a = 0; a < c->g.d; ++a) nmax = c->g.n[a] > nmax ? c->g.n[a] : nmax;
   dim3 grid((nmax + 127) / 128, nterms, c->g.d);
+  dim3 lgrid((nmax + 31) / 32, nterms, c->g.d);  // 32 nodes of eight lanes per CTA
   double* loads = mode == 0 ? axis_out : c->loads;
-  loads_1d_kernel<<<grid, 128, 0, c->stream>>>(T, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0], c->h[1], c->h[2],
-                                                G, loads);
+  loads_1d_kernel<<<lgrid, 32 * kLoadLanes, 0, c->stream>>>(T, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0],
+                                                            c->h[1], c->h[2], G, loads);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   if (mode == 0) return PE_OK;
