@@ -305,7 +305,9 @@ pe_status pe_load_state(pe_ctx* ctx, const void* buf, size_t bytes);
  * applied along every axis of a C-ordered float64 array: out = (kron_a S_a) in.
  * V is symmetric and orthogonal, so the same call is the forward and the inverse
  * transform (Sec. 2.3).  in/out: device, Ndof values, may alias.  d in 1..3.
- * stream: cudaStream_t or NULL.
+ * stream: cudaStream_t or NULL.  Scratch (a ping-pong array; the DST-I matrix of axes whose
+ * n + 1 is not a power of two) comes stream-ordered from a memory pool the library creates per
+ * device, which keeps freed memory for the next call until the process exits.
  */
 pe_status pe_dst(int32_t d, const int32_t* n, const double* in, double* out, void* stream);
 
