@@ -286,12 +286,11 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
   if (warp < FT_WORKERS / 32) {
     // thread (h, r): warpgroup h of two, row r of the tile (TMEM lane r)
     const int r = tid & (FT_ROWS - 1), h = tid >> 7, lane = tid & 31;
-    constexpr int UP = 2;  // slices of an item whose U is prefetched (further ones read in place)
-    // the epilogue inputs of item i + 1 (E_hi, E_lo, exp(-lam M dt), U) are loaded while item
-    // i waits for its accumulator and runs, into two alternating register sets
+    // the epilogue inputs of item i + 1 (E_hi, E_lo, exp(-lam M dt)) are loaded while item i
+    // waits for its accumulator and runs, into two alternating register sets
     struct Pre {
       float eh, el;
-      double em, u[UP];
+      double em;
     };
     Pre P0, P1;
     auto load_epi = [&](Pre& P, int64_t i) {
@@ -300,16 +299,20 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
       P.eh = ok ? a.coefF32[J] : 0.f;
       P.el = ok ? a.coefF32[nd + J] : 0.f;
       P.em = ok ? a.EM[J] : 0.0;
-#pragma unroll
-      for (int t = 0; t < UP; ++t) {
-        const int s = h + 2 * t;
-        const int64_t n = g * a.G + s;
-        P.u[t] = (!a.from_zero && ok && s < a.G && n < a.N) ? a.U[n * nd + J] : 0.0;
-      }
     };
     auto step = [&](int64_t i, const Pre& cur, Pre& nxt) -> bool {
       const int j = (int)(i - i0);
       if (i + 1 < i1) load_epi(nxt, i + 1);
+      // U^n of the slices, loaded ahead: the first pair's before the wait for the accumulator,
+      // each later pair's (more than four slices per group) while the pair before it runs
+      const int64_t g = i / a.tiles;
+      const int64_t J = (i % a.tiles) * FT_ROWS + r;
+      const bool ok = J < nd;
+      auto load_u = [&](int s) -> double {
+        const int64_t n = g * a.G + s;
+        return (!a.from_zero && ok && s < a.G && n < a.N) ? a.U[n * nd + J] : 0.0;
+      };
+      double u0 = load_u(h), u1 = load_u(h + 2);
       if (!mbar_wait(&fullD[j & 1], (uint32_t)((j >> 1) & 1))) {
         set_fail(5);
         return false;
@@ -319,9 +322,6 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
       df_square(cur.eh, cur.el, e2h, e2l);
       df_square(e2h, e2l, e4h, e4l);
       const float eh = cur.eh, e2 = e2h, e3 = e2h * eh;
-      const int64_t g = i / a.tiles;
-      const int64_t J = (i % a.tiles) * FT_ROWS + r;
-      const bool ok = J < nd;
       const uint32_t row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((j & 1) * NR);
       // this thread's slices s = h + 2t of the group, two at a time (warp-uniform); each
       // TMEM read brings 32 substeps of both, and the chains run four substeps per step:
@@ -331,19 +331,16 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
         const float b = fmaf(e3, x0, fmaf(e2, x1, fmaf(eh, x2, x3)));
         w = fmaf(e4h, w, fmaf(e4l, w, b));
       };
-      // the first pair's U was prefetched; later pairs (more than four slices per group) read it here
-      auto finish = [&](bool pre, double upre, int s, float w) {
+      auto finish = [&](double u, int s, float w) {
         const int64_t n = g * a.G + s;
-        if (ok && n < a.N) {
-          const double u = pre ? upre : (a.from_zero ? 0.0 : a.U[n * nd + J]);
-          a.out[n * nd + J] = a.from_zero ? (double)w : fma(cur.em, u, (double)w);
-        }
+        if (ok && n < a.N) a.out[n * nd + J] = a.from_zero ? (double)w : fma(cur.em, u, (double)w);
       };
 #pragma unroll 1
       for (int p = 0; p < 4; ++p) {
         const int s0 = h + 4 * p, s1 = s0 + 2;
         if (s0 >= a.G) break;
         const bool two = s1 < a.G;
+        const double n0 = load_u(s0 + 4), n1 = load_u(s1 + 4);
         float w0 = 0.f, w1 = 0.f;
         int m0 = 0;
         for (; m0 + 32 <= M; m0 += 32) {
@@ -368,8 +365,10 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
             if (two) chain4(w1, v1[e], v1[e + 1], v1[e + 2], v1[e + 3]);
           }
         }
-        finish(p == 0, cur.u[0], s0, w0);
-        if (two) finish(p == 0, cur.u[1], s1, w1);
+        finish(u0, s0, w0);
+        if (two) finish(u1, s1, w1);
+        u0 = n0;
+        u1 = n1;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -547,10 +546,9 @@ __global__ void __launch_bounds__(FT_THREADS, 1) b_fine_tc_kernel(BtcArgs a) {
 
   if (warp < FT_WORKERS / 32) {
     const int r = tid & (FT_ROWS - 1), h = tid >> 7, lane = tid & 31;
-    constexpr int UP = 2;
     struct Pre {
       float eh, el;
-      double em, u[UP];
+      double em;
     };
     Pre P0, P1;
     auto load_epi = [&](Pre& P, int64_t i) {
@@ -561,48 +559,46 @@ __global__ void __launch_bounds__(FT_THREADS, 1) b_fine_tc_kernel(BtcArgs a) {
       P.eh = ok ? a.coefF32[B.oCF + J] : 0.f;
       P.el = ok ? a.coefF32[B.oCF + nd + J] : 0.f;
       P.em = ok ? a.coefF[B.oCF + (int64_t)(B.q + 1) * nd + J] : 0.0;
-#pragma unroll
-      for (int t = 0; t < UP; ++t) {
-        const int s = h + 2 * t;
-        const int64_t n = (int64_t)it.g * B.TG + s;
-        P.u[t] = (ok && s < B.TG && n < B.N) ? a.U[B.oU + n * nd + J] : 0.0;
-      }
     };
     auto step = [&](int64_t i, const Pre& cur, Pre& nxt) -> bool {
       const int j = (int)(i - i0);
       if (i + 1 < i1) load_epi(nxt, i + 1);
+      const BTcItem it = a.items[i];
+      const BProb& B = a.probs[it.p];
+      const int M = B.M, TG = B.TG, N = B.N;
+      const int64_t nd = B.g.ndof;
+      const int64_t J = it.t * FT_ROWS + r;
+      const bool ok = J < nd;
+      // U^n loaded ahead, as in the single-problem kernel: the first pair's before the wait
+      auto load_u = [&](int s) -> double {
+        const int64_t n = (int64_t)it.g * TG + s;
+        return (ok && s < TG && n < N) ? a.U[B.oU + n * nd + J] : 0.0;
+      };
+      double u0 = load_u(h), u1 = load_u(h + 2);
       if (!mbar_wait(&fullD[j & 1], (uint32_t)((j >> 1) & 1))) {
         set_fail(5);
         return false;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const BTcItem it = a.items[i];
-      const BProb& B = a.probs[it.p];
-      const int M = B.M, TG = B.TG, N = B.N;
-      const int64_t nd = B.g.ndof;
       float e2h, e2l, e4h, e4l;
       df_square(cur.eh, cur.el, e2h, e2l);
       df_square(e2h, e2l, e4h, e4l);
       const float eh = cur.eh, e2 = e2h, e3 = e2h * eh;
-      const int64_t J = it.t * FT_ROWS + r;
-      const bool ok = J < nd;
       const uint32_t row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((j & 1) * NRMAX);
       auto chain4 = [&](float& w, float x0, float x1, float x2, float x3) {
         const float bsum = fmaf(e3, x0, fmaf(e2, x1, fmaf(eh, x2, x3)));
         w = fmaf(e4h, w, fmaf(e4l, w, bsum));
       };
-      auto finish = [&](bool pre, double upre, int s, float w) {
+      auto finish = [&](double u, int s, float w) {
         const int64_t n = (int64_t)it.g * TG + s;
-        if (ok && n < N) {
-          const double u = pre ? upre : a.U[B.oU + n * nd + J];
-          a.Fbar[B.oS + n * nd + J] = fma(cur.em, u, (double)w);
-        }
+        if (ok && n < N) a.Fbar[B.oS + n * nd + J] = fma(cur.em, u, (double)w);
       };
 #pragma unroll 1
       for (int pq = 0; pq < 8; ++pq) {
         const int s0 = h + 4 * pq, s1 = s0 + 2;
         if (s0 >= TG) break;
         const bool two = s1 < TG;
+        const double n0 = load_u(s0 + 4), n1 = load_u(s1 + 4);
         float w0 = 0.f, w1 = 0.f;
         int m0 = 0;
         for (; m0 + 32 <= M; m0 += 32) {
@@ -627,8 +623,10 @@ __global__ void __launch_bounds__(FT_THREADS, 1) b_fine_tc_kernel(BtcArgs a) {
             if (two) chain4(w1, v1[e], v1[e + 1], v1[e + 2], v1[e + 3]);
           }
         }
-        finish(pq == 0, cur.u[0], s0, w0);
-        if (two) finish(pq == 0, cur.u[1], s1, w1);
+        finish(u0, s0, w0);
+        if (two) finish(u1, s1, w1);
+        u0 = n0;
+        u1 = n1;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
