@@ -130,7 +130,7 @@ void free_ctx(pe_ctx* c) {
                   c->coefF32, c->U, c->Fbar, c->gG, c->work0, c->work1, c->out_nodal, c->partials,
                   c->red, c->axisF, c->axisF32, c->axisU0, c->AF, c->AF32, c->AG, c->AG32, c->loads,
                   c->Ktab, c->phase_tab, c->Zst, c->Wst, c->Wst32, c->Fz, c->done_ctr, c->tcB, c->tc_err, c->tcA,
-                  c->muM_full, c->ratio_full, c->fac_full, c->work2, c->loopctl, c->loop_hist, c->io32};
+                  c->muM_full, c->ratio_full, c->fac_full, c->work2, c->loopctl, c->loop_hist, c->io32, c->muM_inv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -326,6 +326,7 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   }
   st = PE_OK;
   if (st == PE_OK) st = dev_alloc(&c->muM_axis, nsl);
+  if (st == PE_OK) st = dev_alloc(&c->muM_inv, nsum);
   if (st == PE_OK) st = dev_alloc(&c->ratio_axis, nsl);
   if (st == PE_OK && c->sharded) st = dev_alloc(&c->muM_full, nsum);
   if (st == PE_OK && c->sharded) st = dev_alloc(&c->ratio_full, nsum);
@@ -584,14 +585,13 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     for (int i = 0; i < nf; ++i) c->terms[i] = f->terms[i];
     PE_TRY(expand_dirichlet_terms(c));
   }
-  // Work that does not depend on the per-axis forcing factors runs on the side stream while
-  // those are made on the main one: the copy and forward transform of nodal u0 and the time
-  // tables.  The main stream waits for it before the stage weights (which need the time
-  // tables' shifts) and the coarse sweep.
+  // The forward transform of nodal u0 (after its copy, for host u0) runs on the side stream
+  // while the main one makes the time tables and the per-axis forcing factors; the main stream
+  // waits for it before the stage weights and the coarse sweep.
   // (Small grids, whose kernels are launch-bound, keep everything on the main stream.)
   double* U0 = c->U;
   const bool fork_u0 = u0->kind == PE_FIELD_NODAL && u0->nodal != nullptr;
-  const bool fork = (fork_u0 || !general) && c->gn.ndof >= kForkMinDof;
+  const bool fork = fork_u0 && c->gn.ndof >= kForkMinDof;
   const bool inline_u0 = fork_u0 && !fork;  // nodal u0, transformed below on the main stream
   if (fork) {
     PE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
@@ -600,19 +600,22 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     c->stream = c->side;
     pe_status st = PE_OK;
     if (fork_u0) {
+      // device u0 is read in place by the transform; host u0 is copied in first
       const bool dev = c->u0_dev_hint >= 0 ? c->u0_dev_hint == 1 : pe_is_device_ptr(u0->nodal);
-      const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->gn.ndof,
-                                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
-      if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_set_problem: u0 copy");
-      if (st == PE_OK) st = nodal_to_modal(c, c->work0, U0);
+      const double* src = static_cast<const double*>(u0->nodal);
+      if (!dev) {
+        const cudaError_t e = cudaMemcpyAsync(c->work0, u0->nodal, sizeof(double) * c->gn.ndof,
+                                              cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) st = pe_cuda_fail(e, "pe_set_problem: u0 copy");
+        src = c->work0;
+      }
+      if (st == PE_OK) st = nodal_to_modal(c, src, U0);
     }
-    if (st == PE_OK && !general) st = launch_time_tables(c);
     c->stream = main_stream;
     PE_TRY(st);
     PE_CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
-  } else if (!general) {
-    PE_TRY(launch_time_tables(c));
   }
+  if (!general) PE_TRY(launch_time_tables(c));
   // The phi/b coefficient tables depend only on lam, dt, dT and the nodes: pe_setup made them.
   // Forcing: per-axis modal factors, then (after the join) the stage weights of the fine step.
   if (!general) PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1, c->lkind));

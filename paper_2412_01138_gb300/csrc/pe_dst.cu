@@ -981,6 +981,7 @@ __global__ void __launch_bounds__(256, 2) dst512_contig_kernel(const TI* __restr
                                                                int64_t npencils, float scale,
                                                                const Cplx<float>* __restrict__ tw2) {
   constexpr int L = 512, n = 255, PS = L + L / 16 + 1;
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, WARPS = blockDim.x >> 5;
   const int h = lane >> 4, j = lane & 15;
@@ -1053,6 +1054,7 @@ __global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const TI* __rest
                                                                 int64_t inner, int64_t npencils, float scale,
                                                                 const Cplx<float>* __restrict__ tw2) {
   constexpr int L = 512, n = 255, PS = L + L / 16 + 1, P = 4 * W, SP = P + 2;
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int h = lane >> 4, j = lane & 15;
@@ -1175,6 +1177,7 @@ __global__ void __launch_bounds__(32 * W) dst1024_strided_kernel(const float* __
                                                                  int64_t npencils, float scale,
                                                                  const Cplx<float>* __restrict__ tw2) {
   constexpr int L = 1024, n = 511, PS = L + L / 16 + 1, P = 4 * W, SP = P + 2;
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* stage[2] = {reinterpret_cast<float*>(smem_raw), reinterpret_cast<float*>(smem_raw) + n * SP};
@@ -1654,7 +1657,8 @@ pe_status fft512_contig_launch(const TI* in, TO* out, int64_t npencils, float sc
   PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_contig_kernel<TI, TO>, 32 * warps, smem));
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nquads + warps - 1) / warps,
                                                               (int64_t)sms * std::max(per_sm, 1)));
-  dst512_contig_kernel<TI, TO><<<(unsigned)grid, 32 * warps, smem, st>>>(in, out, npencils, scale, tw2);
+  PE_CUDA_TRY(launch_pdl(dst512_contig_kernel<TI, TO>, dim3((unsigned)grid), dim3(32 * warps), smem, st, in, out,
+                         npencils, scale, tw2));
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -1680,7 +1684,8 @@ pe_status fft512_strided_launch_w(const TI* in, TO* out, int64_t inner, int64_t 
   PE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst512_strided_kernel<W, TI, TO>, 32 * W, smem));
   const int64_t nblk = (npencils + P - 1) / P;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * std::max(per_sm, 1)));
-  dst512_strided_kernel<W, TI, TO><<<(unsigned)grid, 32 * W, smem, st>>>(in, out, inner, npencils, scale, tw2);
+  PE_CUDA_TRY(launch_pdl(dst512_strided_kernel<W, TI, TO>, dim3((unsigned)grid), dim3(32 * W), smem, st, in, out,
+                         inner, npencils, scale, tw2));
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
@@ -1715,7 +1720,8 @@ pe_status fft1024_strided_launch(const float* in, float* out, int64_t inner, int
   if (per_sm < 1) return pe_fail(PE_ECUDA, "dst: the 1024-point strided kernel does not fit an SM");
   const int64_t nblk = (npencils + P - 1) / P;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)sms * per_sm));
-  dst1024_strided_kernel<W><<<(unsigned)grid, 32 * W, smem, st>>>(in, out, inner, npencils, scale, tw2);
+  PE_CUDA_TRY(launch_pdl(dst1024_strided_kernel<W>, dim3((unsigned)grid), dim3(32 * W), smem, st, in, out, inner,
+                         npencils, scale, tw2));
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

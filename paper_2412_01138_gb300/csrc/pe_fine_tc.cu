@@ -144,6 +144,7 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4 (&o)[3]) {
 // holding Y_{gG+s}[m][k] (zero past the last slice and past K).
 __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, int K, int KC, int G, int NR,
                                      int KP, int ngroups, uint4* __restrict__ Bsp) {
+  pdl_wait();
   const int chunks = KP / 8;
   const int64_t total = (int64_t)ngroups * NR * chunks;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols
                                                                const float* __restrict__ coef_b,
                                                                const double* __restrict__ Z, int KP, int64_t tiles,
                                                                uint4* __restrict__ Asp) {
+  pdl_wait();
   __shared__ float sZ[PE_MAX_S * 2 * PE_MAX_TERMS];
   __shared__ int sTerm[2 * PE_MAX_TERMS];
   const int K = C.K;
@@ -234,6 +236,7 @@ struct FtArgs {
 
 template <int KP>
 __global__ void __launch_bounds__(FT_THREADS, 1) fine_tc_kernel(FtArgs a) {
+  pdl_wait();
   constexpr int A_TERM = FT_ROWS * KP * 2;          // one split term of the A operand
   constexpr int A_BYTES = 3 * A_TERM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -819,8 +822,7 @@ pe_status ft_launch(const FtArgs& args, int grid, cudaStream_t st) {
     attr = cudaFuncSetAttribute(fine_tc_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft_smem_bytes(KP));
   });
   if (attr != cudaSuccess) return pe_cuda_fail(attr, "fine sweep (tensor cores): shared-memory attribute");
-  fine_tc_kernel<KP><<<grid, FT_THREADS, ft_smem_bytes(KP), st>>>(args);
-  PE_CUDA_TRY(cudaGetLastError());
+  PE_CUDA_TRY(launch_pdl(fine_tc_kernel<KP>, dim3(grid), dim3(FT_THREADS), ft_smem_bytes(KP), st, args));
   return PE_OK;
 }
 
@@ -865,13 +867,12 @@ pe_status fine_tc_prepare(pe_ctx* c) {
     c->tcA_cap = a_need;
   }
   const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
-  ft_split_time_kernel<<<(unsigned)((nsplit + 255) / 256), 256, 0, c->stream>>>(c->AF32, N, M, K, KC, G, NR, KP,
-                                                                                 ngroups, (uint4*)c->tcB);
-  PE_CUDA_TRY(cudaGetLastError());
+  PE_CUDA_TRY(launch_pdl(ft_split_time_kernel, dim3((unsigned)((nsplit + 255) / 256)), dim3(256), 0, c->stream,
+                         (const float*)c->AF32, N, M, K, KC, G, NR, KP, ngroups, (uint4*)c->tcB));
   const int64_t nsw = tiles * FT_ROWS;
-  ft_weights_image_kernel<<<(unsigned)((nsw + 255) / 256), 256, 0, c->stream>>>(
-      c->g, c->cols, c->R, c->q, c->axisF32, c->coefF32 + 2 * c->g.ndof, c->Zst, KP, tiles, (uint4*)c->tcA);
-  PE_CUDA_TRY(cudaGetLastError());
+  PE_CUDA_TRY(launch_pdl(ft_weights_image_kernel, dim3((unsigned)((nsw + 255) / 256)), dim3(256), 0, c->stream, c->g,
+                         c->cols, c->R, c->q, (const float*)c->axisF32, (const float*)(c->coefF32 + 2 * c->g.ndof),
+                         (const double*)c->Zst, KP, tiles, (uint4*)c->tcA));
   c->tc_split_ok = true;
   c->launches += 2;
   return PE_OK;

@@ -26,6 +26,7 @@ __global__ void time_tables_kernel(TermsDev T, StageCols C, int N, int M, int q,
                                    double dt, Nodes cF, Nodes cG, double* __restrict__ AF,
                                    float* __restrict__ AF32, double* __restrict__ AG, float* __restrict__ AG32,
                                    double* __restrict__ Z) {
+  pdl_wait();
   const int R = T.n, K = C.K;
   const int64_t nf = (int64_t)N * M * K;
   const int64_t ng = (int64_t)N * p * R;
@@ -112,6 +113,7 @@ constexpr int kLoadLanes = 8;
 __global__ void __launch_bounds__(256) loads_1d_kernel(TermsDev T, Geom g, double lo0, double lo1, double lo2,
                                                        double h0, double h1, double h2, Gauss G,
                                                        double* __restrict__ out) {
+  pdl_wait();
   const int a = blockIdx.z;
   const int r = blockIdx.y;
   const int sub = threadIdx.x & (kLoadLanes - 1);
@@ -150,6 +152,44 @@ __global__ void __launch_bounds__(256) loads_1d_kernel(TermsDev T, Geom g, doubl
 #pragma unroll
   for (int o = kLoadLanes / 2; o > 0; o >>= 1) part += __shfl_xor_sync(grp, part, o);
   if (sub == 0) out[(int64_t)T.n * g.off[a] + (int64_t)r * g.n[a] + k] = h * part;
+}
+
+// Per-axis source factors in matrix form, for grids whose axes are short: out[e],
+// e = R off_a + r n_a + j (the layout of the per-axis tables), is sum_k S_a[j][k] L[R off_a + r
+// n_a + k], times 1 / mu^M_a(j) when muInv is given.  Eight lanes per output split k (a row of the
+// symmetric transform matrix and the term's loads, both contiguous); a shuffle sum in a fixed
+// order.  The float64 work (n FMAs per output) spreads over every SM, where a half-length FFT
+// per pencil pair runs one chain of dependent float64 latencies on a few SMs.
+constexpr int kFactorLanes = 8;
+__global__ void __launch_bounds__(256) axis_factor_matrix_kernel(Geom g, int R, const double* __restrict__ S0,
+                                                                 const double* __restrict__ S1,
+                                                                 const double* __restrict__ S2,
+                                                                 const double* __restrict__ loads,
+                                                                 const double* __restrict__ muInv,
+                                                                 double* __restrict__ fac, float* __restrict__ fac32,
+                                                                 int64_t total) {
+  pdl_wait();
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kFactorLanes;
+  const int sub = threadIdx.x & (kFactorLanes - 1);
+  if (e >= total) return;  // whole groups of eight lanes leave together
+  int a = 0;
+  while (a + 1 < g.d && e >= (int64_t)R * g.off[a + 1]) ++a;
+  const int n = g.n[a];
+  const int64_t local = e - (int64_t)R * g.off[a];
+  const int r = (int)(local / n), j = (int)(local - (int64_t)r * n);
+  const double* S = a == 0 ? S0 : (a == 1 ? S1 : S2);
+  const double* row = S + (int64_t)j * n;
+  const double* L = loads + (int64_t)R * g.off[a] + (int64_t)r * n;
+  double acc = 0.0;
+  for (int k = sub; k < n; k += kFactorLanes) acc = fma(row[k], L[k], acc);
+  const unsigned grp = 0xFFu << (threadIdx.x & 24);
+#pragma unroll
+  for (int o = kFactorLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(grp, acc, o);
+  if (sub == 0) {
+    const double v = muInv ? acc * muInv[g.off[a] + j] : acc;
+    fac[e] = v;
+    if (fac32) fac32[e] = (float)v;
+  }
 }
 
 __global__ void divide_axis_mu_kernel(Geom g, int R, const double* __restrict__ muM, double* __restrict__ x,
@@ -225,9 +265,10 @@ pe_status launch_time_tables(pe_ctx* c) {
   c->K = C.K;
   const int64_t total = (int64_t)c->N * c->M * C.K + (int64_t)c->N * c->p * R + (int64_t)c->q * C.K;
   const int threads = 256;
-  time_tables_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, c->stream>>>(
-      T, C, c->N, c->M, c->q, c->p, c->t0, c->dT, c->dt, nF, nG, c->AF,
-      c->precision == PE_MIXED ? c->AF32 : nullptr, c->AG, c->precision == PE_MIXED ? c->AG32 : nullptr, c->Zst);
+  PE_CUDA_TRY(launch_pdl(time_tables_kernel, dim3((unsigned)((total + threads - 1) / threads)), dim3(threads), 0,
+                         c->stream, T, C, c->N, c->M, c->q, c->p, c->t0, c->dT, c->dt, nF, nG, c->AF,
+                         c->precision == PE_MIXED ? c->AF32 : (float*)nullptr, c->AG,
+                         c->precision == PE_MIXED ? c->AG32 : (float*)nullptr, c->Zst));
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
@@ -346,12 +387,27 @@ static pe_status separable_factors_whole(pe_ctx* c, const pe_term* terms, int nt
   dim3 grid((nmax + 127) / 128, nterms, c->g.d);
   dim3 lgrid((nmax + 31) / 32, nterms, c->g.d);  // 32 nodes of eight lanes per CTA
   double* loads = mode == 0 ? axis_out : c->loads;
-  loads_1d_kernel<<<lgrid, 32 * kLoadLanes, 0, c->stream>>>(T, c->g, c->lo[0], c->lo[1], c->lo[2], c->h[0],
-                                                            c->h[1], c->h[2], G, loads);
+  PE_CUDA_TRY(launch_pdl(loads_1d_kernel, lgrid, dim3(32 * kLoadLanes), 0, c->stream, T, c->g, c->lo[0], c->lo[1],
+                         c->lo[2], c->h[0], c->h[1], c->h[2], G, loads));
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   if (mode == 0) return PE_OK;
   const bool f32 = (axis_out == c->axisF) && c->precision == PE_MIXED;
+  // the matrix form over every SM while its float64 work stays small (R sum_a n_a^2 <= 8M FMAs)
+  int64_t work = 0;
+  for (int a = 0; a < c->g.d; ++a) work += (int64_t)nterms * c->g.n[a] * c->g.n[a];
+  if (c->muM_inv && work <= ((int64_t)8 << 20)) {
+    const int64_t total = (int64_t)nterms * (c->g.off[c->g.d - 1] + c->g.n[c->g.d - 1]);
+    const unsigned blocks = (unsigned)((total * kFactorLanes + 255) / 256);
+    PE_CUDA_TRY(launch_pdl(axis_factor_matrix_kernel, dim3(blocks), dim3(256), 0, c->stream, c->g, nterms,
+                           (const double*)c->S[0], (const double*)(c->g.d > 1 ? c->S[1] : c->S[0]),
+                           (const double*)(c->g.d > 2 ? c->S[2] : c->S[0]), (const double*)loads,
+                           (const double*)(mode == 1 ? c->muM_inv : nullptr), axis_out,
+                           mode == 1 && f32 ? c->axisF32 : (float*)nullptr, total));
+    c->launches += 1;
+    PE_CUDA_TRY(cudaGetLastError());
+    return PE_OK;
+  }
   if (mode == 1) {
     bool done = false;
     PE_TRY(axis_factors_fused(c, nterms, loads, axis_out, f32 ? c->axisF32 : nullptr, &done));

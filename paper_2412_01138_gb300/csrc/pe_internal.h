@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "pe.h"
 
@@ -119,6 +120,7 @@ struct pe_ctx {
   double* work0 = nullptr;      // [gn.ndof] nodal / DST scratch
   double* work1 = nullptr;      // [gn.ndof]
   float* io32 = nullptr;        // [3 gn.ndof] float32 transform scratch of the mixed form (null: float64 transforms)
+  double* muM_inv = nullptr;    // [nsum of the whole grid] 1 / mu^M per axis node
   double* out_nodal = nullptr;  // [gn.ndof] inverse DST of U^N after pe_solve
   double* partials = nullptr;   // [2 * max_blocks]
   double* red = nullptr;        // [2] device
@@ -264,6 +266,32 @@ inline int per_mode_block(int64_t units, int sms) {
   if (per_sm > 512) return 256;
   const int64_t t = (per_sm + 31) / 32 * 32;
   return (int)(t < 64 ? 64 : t);
+}
+
+// Programmatic dependent launch: a kernel launched by launch_pdl may be scheduled while its
+// predecessor on the stream is still running.  Each such kernel calls pdl_wait() first, before
+// it touches global memory: it waits there until the predecessor has completed and its writes
+// are visible, then lets its own successor be scheduled early in turn.  Without the launch
+// attribute (a plain launch) both instructions do nothing.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // Drops the cached set-up and output graphs of a repeated problem (pe_api.cu).

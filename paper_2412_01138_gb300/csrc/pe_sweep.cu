@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(512) coarse_fused_kernel(Geom g, int N, int p,
                                                           const double* __restrict__ coefG, double* __restrict__ U,
                                                           LearnedTerms L, const double* __restrict__ axisF64,
                                                           const double* __restrict__ lam) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sCS = reinterpret_cast<float2*>(smem_raw);                // [N][RB] (LEARN only)
   T* sA = reinterpret_cast<T*>(smem_raw + (LEARN ? sizeof(float2) * (size_t)N * RB : 0));  // [N * p][RB]
@@ -240,13 +241,13 @@ pe_status launch_coarse_fused_t(pe_ctx* c, unsigned blocks, int threads, const T
 #define PE_CF_CASE(X)                                                                                          \
   case X:                                                                                                      \
     if (L)                                                                                                     \
-      coarse_fused_kernel<T, X, true><<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, axisF, AG, \
-                                                                            c->coefG, c->U, Lv, c->axisF,     \
-                                                                            c->lam);                           \
+      PE_CUDA_TRY(launch_pdl(coarse_fused_kernel<T, X, true>, dim3(blocks), dim3(threads), smem, c->stream, c->g, \
+                             c->N, c->p, c->R, axisF, AG, (const double*)c->coefG, c->U, Lv,                    \
+                             (const double*)c->axisF, (const double*)c->lam));                                  \
     else                                                                                                       \
-      coarse_fused_kernel<T, X, false><<<blocks, threads, smem, c->stream>>>(c->g, c->N, c->p, c->R, axisF,   \
-                                                                             AG, c->coefG, c->U, Lv, c->axisF, \
-                                                                             c->lam);                          \
+      PE_CUDA_TRY(launch_pdl(coarse_fused_kernel<T, X, false>, dim3(blocks), dim3(threads), smem, c->stream, c->g, \
+                             c->N, c->p, c->R, axisF, AG, (const double*)c->coefG, c->U, Lv,                     \
+                             (const double*)c->axisF, (const double*)c->lam));                                   \
     break;
     PE_CF_CASE(4) PE_CF_CASE(8) PE_CF_CASE(12) PE_CF_CASE(16) PE_CF_CASE(20) PE_CF_CASE(24) PE_CF_CASE(28)
     PE_CF_CASE(32)
@@ -343,6 +344,7 @@ __global__ void __launch_bounds__(512) correction_kernel(Geom g, int N, const do
                                                          double* __restrict__ partials,
                                                          unsigned int* __restrict__ done, double* __restrict__ red,
                                                          LoopCtl* loop, unsigned long long handle) {
+  pdl_wait();
   __shared__ double sh[32];
   __shared__ bool s_last;
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,8 +479,9 @@ pe_status launch_correction_kernel(pe_ctx* c, LoopCtl* loop, unsigned long long 
   const int threads = per_mode_block(c->g.ndof, c->sms);
   const int64_t blocks = (c->g.ndof + threads - 1) / threads;
   if (blocks > (int64_t)c->max_blocks) return pe_fail(PE_EINVAL, "correction: partials buffer too small");
-  correction_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(c->g, c->N, c->muM_axis, c->coefG, c->Fbar, c->U,
-                                                                 c->partials, c->done_ctr, c->red, loop, handle);
+  PE_CUDA_TRY(launch_pdl(correction_kernel, dim3((unsigned)blocks), dim3(threads), 0, c->stream, c->g, c->N,
+                         (const double*)c->muM_axis, (const double*)c->coefG, (const double*)c->Fbar, c->U,
+                         c->partials, c->done_ctr, c->red, loop, handle));
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;

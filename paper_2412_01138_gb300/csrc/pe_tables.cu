@@ -105,6 +105,11 @@ __global__ void dst_matrix_kernel(int n, double* S, int periodic) {
 
 // Per-axis eigenvalue tables of the modes this context owns (a sharded context: the whole
 // axes first, then its rows).
+__global__ void reciprocal_kernel(int n, const double* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = 1.0 / x[i];
+}
+
 pe_status launch_axis_tables(pe_ctx* c) {
   int nmax = 1;
   for (int a = 0; a < c->gn.d; ++a) nmax = c->gn.n[a] > nmax ? c->gn.n[a] : nmax;
@@ -115,6 +120,12 @@ pe_status launch_axis_tables(pe_ctx* c) {
                                                   c->gn.d > 2 ? c->h[2] : 1.0, mu, ratio);
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());
+  if (c->muM_inv) {  // of the whole axes (the per-axis factors are made for the whole grid)
+    const int nsum = c->gn.off[c->gn.d - 1] + c->gn.n[c->gn.d - 1];
+    reciprocal_kernel<<<(nsum + 255) / 256, 256, 0, c->stream>>>(nsum, mu, c->muM_inv);
+    c->launches += 1;
+    PE_CUDA_TRY(cudaGetLastError());
+  }
   if (c->sharded) {
     PE_TRY(compact_axis_tables(c, 1, c->muM_full, c->muM_axis, nullptr));
     PE_TRY(compact_axis_tables(c, 1, c->ratio_full, c->ratio_axis, nullptr));
