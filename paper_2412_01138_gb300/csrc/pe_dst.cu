@@ -146,6 +146,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) dst_fft_kernel(const T* __restrict__ in, T* __restrict__ out, int n,
                                                       int logL, int64_t inner, int64_t npencils, int pairs,
                                                       T scale, const Cplx<T>* __restrict__ twg) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
   Cplx<T>* buf = reinterpret_cast<Cplx<T>*>(smem_raw);
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(256) dst_half_block_kernel(const T* __restrict
                                                              int logN, int64_t inner, int64_t npencils, T scale,
                                                              const Cplx<T>* __restrict__ tw,
                                                              const T* __restrict__ sinN) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = 1 << logN;
   Cplx<T>* x = reinterpret_cast<Cplx<T>*>(smem_raw);
@@ -1794,8 +1796,8 @@ pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int
       const int N = 1 << logN;
       const size_t smem = sizeof(Cplx<T>) * ((size_t)2 * N + 1 + 8);
       const int threads = N / 2 >= 256 ? 256 : (N / 2 >= 128 ? 128 : (N / 2 >= 64 ? 64 : 32));
-      dst_half_block_kernel<T><<<(unsigned)((npencils + 1) / 2), threads, smem, st>>>(
-          in, out, n, logN, inner, npencils, (T)sqrt(2.0 / (double)N), twN, sinN);
+      PE_CUDA_TRY(launch_pdl(dst_half_block_kernel<T>, dim3((unsigned)((npencils + 1) / 2)), dim3(threads), smem, st,
+                             in, out, n, logN, inner, npencils, (T)sqrt(2.0 / (double)N), twN, sinN));
       PE_CUDA_TRY(cudaGetLastError());
       return PE_OK;
     }
@@ -1813,7 +1815,8 @@ pe_status fft_axis(const T* in, T* out, int64_t outer, int n, int64_t inner, int
   }
   const T scale = (T)(0.5 * sqrt(2.0 / (double)(n + 1)));
   const int threads = L / 2 * pairs >= 256 ? 256 : (L / 2 * pairs >= 128 ? 128 : 64);
-  dst_fft_kernel<T><<<(unsigned)want_ctas, threads, smem, st>>>(in, out, n, logL, inner, npencils, pairs, scale, tw);
+  PE_CUDA_TRY(launch_pdl(dst_fft_kernel<T>, dim3((unsigned)want_ctas), dim3(threads), smem, st, in, out, n, logL, inner,
+                         npencils, pairs, scale, tw));
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }

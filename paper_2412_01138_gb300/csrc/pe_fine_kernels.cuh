@@ -162,6 +162,7 @@ constexpr int kMixedThreads = 128;
 template <int K, int MPT>
 __global__ void __launch_bounds__(kMixedThreads, MPT >= 6 ? 3 : 4)
     fine_mixed_persistent_kernel(FineTile t, int N, int64_t n_items) {
+  pdl_wait();
   constexpr int KC = (K + 3) / 4 * 4;
   extern __shared__ __align__(16) float sYb[];
   const int B = kMixedThreads;
@@ -237,6 +238,7 @@ __device__ __forceinline__ void fine_f64_tile(const FineTile& a, double* sY) {
 
 template <int K, int MPT>
 __global__ void __launch_bounds__(256) fine_mixed_kernel(FineTile t, int64_t slice_stride_y) {
+  pdl_wait();
   extern __shared__ __align__(16) float sYf[];
   const int n = blockIdx.y;
   const int64_t nd = t.ndof;
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(256) fine_mixed_kernel(FineTile t, int64_t sli
 
 template <int K>
 __global__ void __launch_bounds__(256) fine_f64_kernel(FineTile t, int64_t slice_stride_y) {
+  pdl_wait();
   extern __shared__ __align__(16) double sY[];
   const int n = blockIdx.y;
   const int64_t nd = t.ndof;
@@ -295,20 +298,21 @@ pe_status fine_launch(pe_ctx* c, int precision, int from_zero, double* out) {
       if (occ < 1) return pe_fail(PE_EINVAL, "fine sweep: persistent kernel does not fit an SM");
       const int64_t items = tiles * c->N;
       const int64_t grid = items < (int64_t)sms * occ ? items : (int64_t)sms * occ;
-      fine_mixed_persistent_kernel<K, MPT><<<(unsigned)grid, kMixedThreads, 2 * slab_bytes, c->stream>>>(t, c->N,
-                                                                                                          items);
+      PE_CUDA_TRY(launch_pdl(fine_mixed_persistent_kernel<K, MPT>, dim3((unsigned)grid), dim3(kMixedThreads),
+                             2 * slab_bytes, c->stream, t, c->N, items));
     } else {
       const int64_t per_cta = (int64_t)threads * MPT;
       const int64_t tiles = (c->g.ndof + per_cta - 1) / per_cta;
       t.mchunk = pick_mchunk(c->M, KC, sizeof(float));
       dim3 grid((unsigned)tiles, c->N);
-      fine_mixed_kernel<K, MPT><<<grid, threads, sizeof(float) * t.mchunk * KC, c->stream>>>(
-          t, (int64_t)c->M * KC);
+      PE_CUDA_TRY(launch_pdl(fine_mixed_kernel<K, MPT>, grid, dim3(threads), sizeof(float) * t.mchunk * KC, c->stream,
+                             t, (int64_t)c->M * KC));
     }
   } else {
     t.mchunk = pick_mchunk(c->M, K, sizeof(double));
     dim3 grid((unsigned)((c->g.ndof + threads - 1) / threads), c->N);
-    fine_f64_kernel<K><<<grid, threads, sizeof(double) * t.mchunk * K, c->stream>>>(t, (int64_t)c->M * K);
+    PE_CUDA_TRY(launch_pdl(fine_f64_kernel<K>, grid, dim3(threads), sizeof(double) * t.mchunk * K, c->stream, t,
+                           (int64_t)c->M * K));
   }
   c->launches += 1;
   PE_CUDA_TRY(cudaGetLastError());

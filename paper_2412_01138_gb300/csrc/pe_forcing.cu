@@ -78,6 +78,7 @@ __global__ void time_tables_kernel(TermsDev T, StageCols C, int N, int M, int q,
 template <typename T>
 __global__ void stage_weights_kernel(Geom g, StageCols C, int R, int q, const T* __restrict__ axisF,
                                      const T* __restrict__ coef, const double* __restrict__ Z, T* __restrict__ W) {
+  pdl_wait();
   // the shifts Z (converted to T once per CTA) and the column -> term map, in shared memory
   __shared__ T sZ[PE_MAX_S * 2 * PE_MAX_TERMS];
   __shared__ int sTerm[2 * PE_MAX_TERMS];
@@ -207,6 +208,7 @@ __global__ void divide_axis_mu_kernel(Geom g, int R, const double* __restrict__ 
 // out[J] = sum_r w_r prod_a fac[R*off[a] + r*n_a + j_a]
 __global__ void outer_sum_kernel(Geom g, int R, const double* __restrict__ fac, const double* __restrict__ w,
                                  double* __restrict__ out, int accumulate) {
+  pdl_wait();
   const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= g.ndof) return;
   int j[PE_MAX_D];
@@ -236,6 +238,7 @@ __global__ void weights_at_time_kernel(TermsDev T, double t, double* w) {
 }
 
 __global__ void amps_kernel(TermsDev T, double* w) {
+  pdl_wait();
   const int r = threadIdx.x;
   if (r < T.n) w[r] = T.t[r].amp;
 }
@@ -303,12 +306,14 @@ pe_status launch_stage_weights(pe_ctx* c) {
   if (c->precision == PE_MIXED) {
     // the float32 fine sweeps need only the float32 weights; the float64 ones follow on the
     // first float64 sweep (pe_refine)
-    stage_weights_kernel<float><<<blocks, threads, 0, c->stream>>>(c->g, c->cols, c->R, c->q, c->axisF32,
-                                                                   c->coefF32 + 2 * c->g.ndof, c->Zst, c->Wst32);
+    PE_CUDA_TRY(launch_pdl(stage_weights_kernel<float>, dim3(blocks), dim3(threads), 0, c->stream, c->g, c->cols, c->R,
+                           c->q, (const float*)c->axisF32, (const float*)(c->coefF32 + 2 * c->g.ndof),
+                           (const double*)c->Zst, c->Wst32));
     c->Wst_valid = false;
   } else {
-    stage_weights_kernel<double><<<blocks, threads, 0, c->stream>>>(c->g, c->cols, c->R, c->q, c->axisF,
-                                                                    c->coefF + c->g.ndof, c->Zst, c->Wst);
+    PE_CUDA_TRY(launch_pdl(stage_weights_kernel<double>, dim3(blocks), dim3(threads), 0, c->stream, c->g, c->cols,
+                           c->R, c->q, (const double*)c->axisF, (const double*)(c->coefF + c->g.ndof),
+                           (const double*)c->Zst, c->Wst));
     c->Wst_valid = true;
   }
   c->launches += 1;
@@ -432,11 +437,10 @@ pe_status launch_outer_sum(pe_ctx* c, const double* axis_fac, const pe_term* ter
   if (nterms == 0) return PE_OK;
   double* w = c->partials;  // at least PE_MAX_TERMS doubles
   TermsDev T = pack_terms(terms, nterms);
-  amps_kernel<<<1, PE_MAX_TERMS, 0, c->stream>>>(T, w);
+  PE_CUDA_TRY(launch_pdl(amps_kernel, dim3(1), dim3(PE_MAX_TERMS), 0, c->stream, T, w));
   const int threads = 256;
-  outer_sum_kernel<<<(unsigned)((c->g.ndof + threads - 1) / threads), threads, 0, c->stream>>>(c->g, nterms,
-                                                                                               axis_fac, w, out,
-                                                                                               accumulate);
+  PE_CUDA_TRY(launch_pdl(outer_sum_kernel, dim3((unsigned)((c->g.ndof + threads - 1) / threads)), dim3(threads), 0,
+                         c->stream, c->g, nterms, axis_fac, (const double*)w, out, accumulate));
   c->launches += 2;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
