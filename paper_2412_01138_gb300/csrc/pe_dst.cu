@@ -1065,6 +1065,10 @@ __global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const TI* __rest
   __shared__ int64_t offs[2][P];
   const int64_t nblk = (npencils + P - 1) / P;
   const int src = ((16 - j) & 15) | (h << 4);
+  // this lane's pass-2 twiddles e^{-2 pi i lane r / 512}, the same for every pair and block
+  Cplx<float> tw[16];
+#pragma unroll
+  for (int r = 1; r < 16; ++r) tw[r] = ldg_cplx(tw2 + 32 * r + lane);
   // thread tid copies column pl = tid % 32 of rows tid / 32, + 8, ... (a warp: one 128-byte row)
   const int pl = tid & (P - 1), row0 = tid / P;
   constexpr int RSTEP = 32 * W / P;
@@ -1142,7 +1146,7 @@ __global__ void __launch_bounds__(32 * W) dst512_strided_kernel(const TI* __rest
 #pragma unroll
       for (int r = 0; r < 16; ++r) u[r] = b[fpad(lane + 32 * r)];
 #pragma unroll
-      for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], ldg_cplx(tw2 + 32 * r + lane));
+      for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], tw[r]);
       dft_regs<float, 16>(u);
       const int oc = 4 * warp + 2 * p;
 #pragma unroll
@@ -1187,6 +1191,10 @@ __global__ void __launch_bounds__(32 * W) dst1024_strided_kernel(const float* __
   __shared__ int64_t offs[2][P];
   const int64_t nblk = (npencils + P - 1) / P;
   const int src = (32 - lane) & 31;
+  // this lane's pass-2 twiddles e^{-2 pi i lane r / 1024}, the same for every pair and block
+  Cplx<float> tw[32];
+#pragma unroll
+  for (int r = 1; r < 32; ++r) tw[r] = ldg_cplx(tw2 + 32 * r + lane);
   const int pl = tid & (P - 1), row0 = tid / P;
   constexpr int RSTEP = 32 * W / P;
   auto issue = [&](int64_t blk, int b) {
@@ -1249,7 +1257,7 @@ __global__ void __launch_bounds__(32 * W) dst1024_strided_kernel(const float* __
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = a[fpad(lane + 32 * r)];
 #pragma unroll
-      for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], ldg_cplx(tw2 + 32 * r + lane));
+      for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], tw[r]);
       dft_regs<float, 32>(v);
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
