@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
                                                        const ModeItem* __restrict__ items, int n_items,
                                                        const double* __restrict__ axisF, const TF* __restrict__ AG,
                                                        const double* __restrict__ coefG, double* __restrict__ U,
-                                                       BLearn L) {
+                                                       BLearn L, const float* __restrict__ axisF32) {
   constexpr int RB = kCoarseRB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TF* sA = reinterpret_cast<TF*>(smem_raw);  // [chunk * p][RB]
@@ -355,13 +355,22 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
           }
         }
       }
+      // the source weights P_{r,J}: in the mixed form from the float32 factors in float32 (as
+      // the single-problem sweep forms them; no float64 product and conversion per term)
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         if (r < R) {
-          double v = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
-          for (int a = 1; a < B.g.d; ++a)
-            v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
-          P[r] = (TF)v;
+          if constexpr (sizeof(TF) == 4) {
+            float v = axisF32[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
+            for (int a = 1; a < B.g.d; ++a)
+              v *= axisF32[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+            P[r] = v;
+          } else {
+            double v = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
+            for (int a = 1; a < B.g.d; ++a)
+              v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+            P[r] = (TF)v;
+          }
         }
       }
 #pragma unroll
@@ -471,9 +480,11 @@ __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restri
       const double E = coefG[B.oCG + J];
       double* Up = U + B.oU;
       const double* fp = Fbar + B.oS;
-      // U^0 is the same in every iterate; the loads of the next kPF slices are issued
-      // while the current kPF are combined
-      double u_new = Up[J], u_old = u_new;
+      // U^0 is the same in every iterate (d = U^n_new - U^n_old starts at 0); the loads of the
+      // next kPF slices are issued while the current kPF are combined.  Four FP64 operations
+      // per slice: the difference d is both the next slice's correction and this slice's
+      // residual term.
+      double d = 0.0;
       double f0[kPF], o0[kPF], f1[kPF], o1[kPF];
 #pragma unroll
       for (int e = 0; e < kPF; ++e) {
@@ -495,13 +506,11 @@ __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restri
         for (int e = 0; e < kPF; ++e) {
           const int n = n0 + e;
           if (n < N) {
-            const double nxt = fma(E, u_new - u_old, f0[e]);
+            const double nxt = fma(E, d, f0[e]);
             Up[(int64_t)(n + 1) * nd + J] = nxt;
-            const double df = nxt - o0[e];
-            sd = fma(df, df, sd);
+            d = nxt - o0[e];
+            sd = fma(d, d, sd);
             su = fma(nxt, nxt, su);
-            u_new = nxt;
-            u_old = o0[e];
           }
         }
 #pragma unroll
@@ -621,16 +630,16 @@ pe_status batch_launch_prepare(pe_batch* b) {
   }
   if (b->precision == PE_MIXED && b->mlp)
     b_coarse_kernel<float, true><<<grid_items, 256, kCoarseSmem, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, L);
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, L, b->axisF32);
   else if (b->precision == PE_MIXED)
     b_coarse_kernel<float, false><<<grid_items, 256, kCoarseSmem, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, L);
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG32, b->coefG, b->U, L, b->axisF32);
   else if (b->mlp)
     b_coarse_kernel<double, true><<<grid_items, 256, kCoarseSmem, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, L);
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, L, (const float*)nullptr);
   else
     b_coarse_kernel<double, false><<<grid_items, 256, kCoarseSmem, b->stream>>>(
-        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, L);
+        b->d_probs, b->d_mode_items, b->n_mode_items, b->axisF, b->AG, b->coefG, b->U, L, (const float*)nullptr);
   b->launches += 5;
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
