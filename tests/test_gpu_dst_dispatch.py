@@ -115,3 +115,25 @@ def test_dst_bench_grid_on_sampled_slabs(env):
         rel, elem = _errors(got, ref)
         assert rel <= bound_rel and elem <= bound_elem, (dtype, rel, elem)
         del src, out
+
+
+# The two-pass float32 kernels at n = 255 choose one-warp CTAs for passes of fewer than
+# 4 x 8 x (SMs) pencils and eight-warp CTAs above; (255, 17) and (255, 5000) put the strided
+# pass in each class, (17, 255) and (5000, 255) the contiguous one.
+TWO_PASS = [((255, 17), "strided, one-warp CTAs"), ((255, 5000), "strided, eight-warp CTAs"),
+            ((17, 255), "contiguous, one-warp CTAs"), ((5000, 255), "contiguous, eight-warp CTAs"),
+            ((255,), "one pencil")]
+
+
+@pytest.mark.parametrize("n,label", TWO_PASS, ids=[s[1] for s in TWO_PASS])
+def test_two_pass_float32_classes(env, n, label):
+    pe, torch = env
+    rng = np.random.default_rng(int(np.prod(n)) % 9973)
+    x = rng.standard_normal(n)
+    ref = _oracle_dst(x)
+    xf = torch.tensor(x.reshape(-1), device="cuda", dtype=torch.float32)
+    of = torch.empty_like(xf)
+    pe.dst(len(n), n, xf, of, f32=True)
+    torch.cuda.synchronize()
+    rel, elem = _errors(of.double().cpu().numpy(), ref)
+    assert rel <= 2e-6 and elem <= 1e-5, (label, rel, elem)
