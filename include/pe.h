@@ -275,6 +275,32 @@ pe_status pe_refine(pe_ctx* ctx, double* rel_residual_out);
  */
 pe_status pe_solve(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f, double tol, pe_result* out);
 
+/*
+ * pe_solve_out -- pe_solve, and the nodal solution u_h(T_N) = V U^N (Ndof values, the
+ * whole grid also for a context that owns a block of modes: its modes' share) written
+ * into nodal_out (host or device, caller-owned) in the same stream order before the
+ * call returns: what pe_get_solution(ctx, N, nodal_out) gives afterwards, without a
+ * second synchronisation.  PE_EINVAL if nodal_out is NULL; on PE_ENOCONV the buffer is
+ * filled as well.
+ */
+pe_status pe_solve_out(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f, double tol, double* nodal_out,
+                       pe_result* out);
+
+/*
+ * pe_solve_async / pe_solve_wait -- pe_solve_out in two calls.  pe_solve_async enqueues the
+ * whole solve (set-up, Algorithm 1's loop, the inverse DST of U^N and, if nodal_out is not
+ * NULL, its copy into nodal_out) on the context's stream and returns; with the loop on the
+ * device (pe_options.device_loop = 1 or 2) it does not wait for the GPU, with the host-driven
+ * loop it waits for every residual as pe_solve does.  pe_solve_wait waits for the stream and
+ * fills out (may be NULL) and returns what pe_solve would have returned (PE_ENOCONV,
+ * PE_ENONFINITE, ...).  One solve may be pending per context: until pe_solve_wait, the
+ * context's other calls that read or change its state return PE_ESTATE, and nodal_out
+ * (caller-owned) and a device u0 must stay valid.  pe_solve_wait without a pending solve:
+ * PE_ESTATE.
+ */
+pe_status pe_solve_async(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f, double tol, double* nodal_out);
+pe_status pe_solve_wait(pe_ctx* ctx, pe_result* out);
+
 /* Nodal values u_h(T_slice) = V U^{slice} (slice in 0..N) into nodal_out (host or device, Ndof). */
 pe_status pe_get_solution(pe_ctx* ctx, int32_t slice, double* nodal_out);
 

@@ -143,6 +143,7 @@ void free_ctx(pe_ctx* c) {
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_tables) cudaEventDestroy(c->ev_tables);
   if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
@@ -400,7 +401,8 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = pe_cuda_fail(cudaGetLastError(), "cudaEventCreate");
   if (st == PE_OK && (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
                       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+                      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&c->ev_tables, cudaEventDisableTiming) != cudaSuccess))
     st = pe_cuda_fail(cudaGetLastError(), "pe_setup: side stream");
   if (st == PE_OK) st = launch_axis_tables(c);
   for (int a = 0; a < d && st == PE_OK; ++a) st = build_dst_matrix(n[a], c->S[a], c->stream, c->g.per[a]);
@@ -501,6 +503,7 @@ void drop_solve_graphs(pe_ctx* c) {
 }
 
 extern "C" pe_status pe_set_dirichlet(pe_ctx* c, int32_t n_terms, const pe_term* g) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_set_dirichlet: a solve is pending (pe_solve_wait first)");
   if (!c) return pe_fail(PE_EINVAL, "pe_set_dirichlet: ctx is NULL");
   if (n_terms < 0 || n_terms > PE_MAX_TERMS) return pe_fail(PE_EINVAL, "pe_set_dirichlet: n_terms out of range");
   if (n_terms > 0 && !g) return pe_fail(PE_EINVAL, "pe_set_dirichlet: terms is NULL");
@@ -585,21 +588,29 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
     for (int i = 0; i < nf; ++i) c->terms[i] = f->terms[i];
     PE_TRY(expand_dirichlet_terms(c));
   }
-  // The forward transform of nodal u0 (after its copy, for host u0) runs on the side stream
-  // while the main one makes the time tables and the per-axis forcing factors; the main stream
-  // waits for it before the stage weights and the coarse sweep.
+  // Two streams for grids large enough that their set-up kernels run side by side: the side
+  // stream makes the time tables, then the forward transform of nodal u0 (after its copy, for
+  // host u0), then the tensor-core engine's split time factors; the main stream makes the
+  // per-axis forcing factors, waits for the time tables (the stage weights take their shifts
+  // Z), makes the stage weights, and waits for the side stream before the coarse sweep.
   // (Small grids, whose kernels are launch-bound, keep everything on the main stream.)
   double* U0 = c->U;
   const bool fork_u0 = u0->kind == PE_FIELD_NODAL && u0->nodal != nullptr;
   const bool fork = fork_u0 && c->gn.ndof >= kForkMinDof;
   const bool inline_u0 = fork_u0 && !fork;  // nodal u0, transformed below on the main stream
+  const bool tc = !general && c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC;
   if (fork) {
     PE_CUDA_TRY(cudaEventRecord(c->ev_fork, c->stream));
     PE_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     cudaStream_t main_stream = c->stream;
     c->stream = c->side;
     pe_status st = PE_OK;
-    if (fork_u0) {
+    if (!general) {
+      st = launch_time_tables(c);
+      if (st == PE_OK && cudaEventRecord(c->ev_tables, c->side) != cudaSuccess)
+        st = pe_cuda_fail(cudaGetLastError(), "pe_set_problem: event record");
+    }
+    if (st == PE_OK) {
       // device u0 is read in place by the transform; host u0 is copied in first
       const bool dev = c->u0_dev_hint >= 0 ? c->u0_dev_hint == 1 : pe_is_device_ptr(u0->nodal);
       const double* src = static_cast<const double*>(u0->nodal);
@@ -611,18 +622,23 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
       }
       if (st == PE_OK) st = nodal_to_modal(c, src, U0);
     }
+    if (st == PE_OK && tc) st = fine_tc_prepare_time(c);
     c->stream = main_stream;
     PE_TRY(st);
     PE_CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+  } else if (!general) {
+    PE_TRY(launch_time_tables(c));
   }
-  if (!general) PE_TRY(launch_time_tables(c));
   // The phi/b coefficient tables depend only on lam, dt, dT and the nodes: pe_setup made them.
-  // Forcing: per-axis modal factors, then (after the join) the stage weights of the fine step.
+  // Forcing: per-axis modal factors, then the stage weights of the fine step.
   if (!general) PE_TRY(launch_separable_factors(c, c->terms, c->R, c->axisF, 1, c->lkind));
-  if (fork) PE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  if (fork && !general) PE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_tables, 0));
   if (!general) PE_TRY(launch_stage_weights(c));
   // the tensor-core engine's split operand images of the stage weights and time factors
-  if (!general && c->precision == PE_MIXED && c->fine_engine == PE_FINE_TC) PE_TRY(fine_tc_prepare(c));
+  if (tc) PE_TRY(fine_tc_prepare_weights(c));
+  if (tc && !fork) PE_TRY(fine_tc_prepare_time(c));
+  if (fork) PE_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  if (tc) c->tc_split_ok = true;
   PE_CUDA_TRY(record_timing(c, c->ev[1]));
   // U^0 = P_h u0
   if (fork_u0 && !inline_u0) {
@@ -668,6 +684,7 @@ static pe_status set_problem_impl(pe_ctx* c, const pe_field* u0, const pe_forcin
 }
 
 extern "C" pe_status pe_set_problem(pe_ctx* c, const pe_field* u0, const pe_forcing* f) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_set_problem: a solve is pending (pe_solve_wait first)");
   if (!c) return pe_fail(PE_EINVAL, "pe_set_problem: ctx is NULL");
   c->have_problem = false;
   drop_solve_graphs(c);
@@ -720,6 +737,7 @@ static pe_status need_totals(const pe_ctx* c, const char* who) {
 }
 
 extern "C" pe_status pe_parareal_iter(pe_ctx* c, double* rel_residual_out) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_parareal_iter: a solve is pending (pe_solve_wait first)");
   if (!c) return pe_fail(PE_EINVAL, "pe_parareal_iter: ctx is NULL");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_parareal_iter: no problem set (call pe_set_problem)");
   PE_TRY(need_totals(c, "pe_parareal_iter"));
@@ -731,6 +749,7 @@ extern "C" pe_status pe_parareal_iter(pe_ctx* c, double* rel_residual_out) {
 }
 
 extern "C" pe_status pe_parareal_iter_sums(pe_ctx* c, double* sums_out) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_parareal_iter_sums: a solve is pending (pe_solve_wait first)");
   if (!c || !sums_out) return pe_fail(PE_EINVAL, "pe_parareal_iter_sums: NULL argument");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_parareal_iter_sums: no problem set (call pe_set_problem)");
   c->have_output = false;
@@ -738,6 +757,7 @@ extern "C" pe_status pe_parareal_iter_sums(pe_ctx* c, double* sums_out) {
 }
 
 extern "C" pe_status pe_refine(pe_ctx* c, double* rel_residual_out) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_refine: a solve is pending (pe_solve_wait first)");
   if (!c) return pe_fail(PE_EINVAL, "pe_refine: ctx is NULL");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_refine: no problem set (call pe_set_problem)");
   PE_TRY(need_totals(c, "pe_refine"));
@@ -920,8 +940,12 @@ static pe_status output_phase(pe_ctx* c) {
   return add_lift(c, c->t0 + c->T, 1.0, 3, c->out_nodal);
 }
 
-extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, pe_result* res) {
+// The solve in two halves: solve_begin enqueues the whole solve on the context's stream (with
+// the loop on the device nothing in it waits for the GPU; the host-driven loop waits for every
+// residual), solve_end waits for the stream and reports.
+static pe_status solve_begin(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, double* nodal_out) {
   if (!c) return pe_fail(PE_EINVAL, "pe_solve: ctx is NULL");
+  if (c->pend) return pe_fail(PE_ESTATE, "pe_solve: a solve is pending (pe_solve_wait first)");
   if (!(tol >= 0.0)) return pe_fail(PE_EINVAL, "pe_solve: tol must be >= 0");
   PE_TRY(need_totals(c, "pe_solve"));
   c->have_problem = false;
@@ -966,15 +990,14 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
   c->u0_dev_hint = -1;
   PE_CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
   double r = INFINITY;
-  int hist = 0;
   const bool on_device = loop_on_device(c);
+  c->pend_hist.clear();
   if (on_device) {
     PE_TRY(enqueue_loop_on_device(c, tol));
   } else {
     while (c->k < c->max_iter) {
       PE_TRY(iter_impl(c, &r, c->precision));
-      if (res && res->residual_history && hist < res->history_cap) res->residual_history[hist] = r;
-      ++hist;
+      c->pend_hist.push_back(r);
       if (r <= tol) break;
     }
   }
@@ -988,8 +1011,30 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
     PE_TRY(output_phase(c));
   }
   PE_CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
+  // the nodal solution into the caller's buffer in the same stream order
+  if (nodal_out)
+    PE_CUDA_TRY(cudaMemcpyAsync(nodal_out, c->out_nodal, sizeof(double) * c->gn.ndof,
+                                pe_is_device_ptr(nodal_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+  c->pend = true;
+  c->pend_on_device = on_device;
+  c->pend_tol = tol;
+  c->pend_r = r;
+  return PE_OK;
+}
+
+static pe_status solve_end(pe_ctx* c, pe_result* res) {
+  if (!c) return pe_fail(PE_EINVAL, "pe_solve_wait: ctx is NULL");
+  if (!c->pend) return pe_fail(PE_ESTATE, "pe_solve_wait: no solve pending");
+  c->pend = false;
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  if (on_device) PE_TRY(finish_loop_on_device(c, res, &r));
+  double r = c->pend_r;
+  if (c->pend_on_device) {
+    PE_TRY(finish_loop_on_device(c, res, &r));
+  } else if (res && res->residual_history) {
+    const int cnt = std::min((int)c->pend_hist.size(), res->history_cap);
+    for (int i = 0; i < cnt; ++i) res->residual_history[i] = c->pend_hist[i];
+  }
   c->have_output = true;
   if (res) {
     res->k = c->k;
@@ -1004,14 +1049,35 @@ extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f
     res->ms_correction_kernel = c->ms_corr;
     res->ms_coarse_kernel = elapsed(c->ev[8], c->ev[9]);
   }
-  if (r > tol && c->k < c->N) return pe_fail(PE_ENOCONV, "pe_solve: residual above tol after max_iter iterations");
+  if (r > c->pend_tol && c->k < c->N)
+    return pe_fail(PE_ENOCONV, "pe_solve: residual above tol after max_iter iterations");
   return PE_OK;
 }
+
+extern "C" pe_status pe_solve(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, pe_result* res) {
+  PE_TRY(solve_begin(c, u0, f, tol, nullptr));
+  return solve_end(c, res);
+}
+
+extern "C" pe_status pe_solve_out(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol, double* nodal_out,
+                                  pe_result* res) {
+  if (!nodal_out) return pe_fail(PE_EINVAL, "pe_solve_out: nodal_out is NULL");
+  PE_TRY(solve_begin(c, u0, f, tol, nodal_out));
+  return solve_end(c, res);
+}
+
+extern "C" pe_status pe_solve_async(pe_ctx* c, const pe_field* u0, const pe_forcing* f, double tol,
+                                    double* nodal_out) {
+  return solve_begin(c, u0, f, tol, nodal_out);
+}
+
+extern "C" pe_status pe_solve_wait(pe_ctx* c, pe_result* res) { return solve_end(c, res); }
 
 // ---------------------------------------------------------------------------
 // getters, state
 // ---------------------------------------------------------------------------
 extern "C" pe_status pe_get_solution(pe_ctx* c, int32_t slice, double* nodal_out) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_get_solution: a solve is pending (pe_solve_wait first)");
   if (!c) return pe_fail(PE_EINVAL, "pe_get_solution: ctx is NULL");
   if (slice < 0 || slice > c->N) return pe_fail(PE_EINVAL, "pe_get_solution: slice out of range");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_get_solution: no problem set");
@@ -1022,6 +1088,7 @@ extern "C" pe_status pe_get_solution(pe_ctx* c, int32_t slice, double* nodal_out
 }
 
 extern "C" pe_status pe_get_modal(pe_ctx* c, int32_t slice, double* modal_out) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_get_modal: a solve is pending (pe_solve_wait first)");
   if (!c) return pe_fail(PE_EINVAL, "pe_get_modal: ctx is NULL");
   if (slice < 0 || slice > c->N) return pe_fail(PE_EINVAL, "pe_get_modal: slice out of range");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_get_modal: no problem set");
@@ -1085,6 +1152,7 @@ void fill_header(const pe_ctx* c, StateHeader* h) {
 }  // namespace
 
 extern "C" pe_status pe_save_state(pe_ctx* c, void* buf, size_t* bytes) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_save_state: a solve is pending (pe_solve_wait first)");
   if (!c || !bytes) return pe_fail(PE_EINVAL, "pe_save_state: NULL argument");
   const size_t nd = (size_t)c->g.ndof, N = (size_t)c->N;
   const size_t need = sizeof(StateHeader) + sizeof(double) * (N + 1) * nd;
@@ -1105,6 +1173,7 @@ extern "C" pe_status pe_save_state(pe_ctx* c, void* buf, size_t* bytes) {
 }
 
 extern "C" pe_status pe_load_state(pe_ctx* c, const void* buf, size_t bytes) {
+  if (c && c->pend) return pe_fail(PE_ESTATE, "pe_load_state: a solve is pending (pe_solve_wait first)");
   if (!c || !buf) return pe_fail(PE_EINVAL, "pe_load_state: NULL argument");
   if (!c->have_problem) return pe_fail(PE_ESTATE, "pe_load_state: set the same problem first (pe_set_problem)");
   const size_t nd = (size_t)c->g.ndof, N = (size_t)c->N;

@@ -72,7 +72,8 @@ __global__ void b_coef_tables_kernel(const BProb* __restrict__ probs, const Mode
     int j[PE_MAX_D];
     unflatten(B.g, J, j);
     double s = 0.0;
-    for (int a = 0; a < B.g.d; ++a) s += ratio[B.oMu + B.g.off[a] + j[a]];
+#pragma unroll
+    for (int a = 0; a < PE_MAX_D; ++a) if (a < B.g.d) s += ratio[B.oMu + B.g.off[a] + j[a]];
     const double lam = B.D * s;
     Lag LF, LG;
     for (int i = 0; i < PE_MAX_S; ++i)
@@ -193,7 +194,9 @@ __global__ void b_stage_weights_kernel(const BProb* __restrict__ probs, const Mo
     for (int k = 0; k < B.K; ++k) {
       const int r = cols[B.oCol + k] >> 1;
       T P = ax[(int64_t)B.R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
-      for (int a = 1; a < B.g.d; ++a) P *= ax[(int64_t)B.R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+#pragma unroll
+      for (int a = 1; a < PE_MAX_D; ++a) if (a < B.g.d)
+        P *= ax[(int64_t)B.R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
       T sum = T(0);
 #pragma unroll
       for (int i = 0; i < PE_MAX_S; ++i)
@@ -267,7 +270,9 @@ __global__ void b_u0_kernel(const BProb* __restrict__ probs, const ModeItem* __r
     double acc = 0.0;
     for (int t = 0; t < B.Ru; ++t) {
       double v = axisU0[B.oAxU + (int64_t)B.Ru * B.g.off[0] + (int64_t)t * B.g.n[0] + j[0]];
-      for (int a = 1; a < B.g.d; ++a) v *= axisU0[B.oAxU + (int64_t)B.Ru * B.g.off[a] + (int64_t)t * B.g.n[a] + j[a]];
+#pragma unroll
+      for (int a = 1; a < PE_MAX_D; ++a) if (a < B.g.d)
+        v *= axisU0[B.oAxU + (int64_t)B.Ru * B.g.off[a] + (int64_t)t * B.g.n[a] + j[a]];
       acc += terms[B.tu + t].amp * v;
     }
     U[B.oU + J] = acc;
@@ -335,7 +340,8 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
       unflatten(B.g, J, j);
       if constexpr (LEARN) {
         double s = 0.0;
-        for (int a = 0; a < B.g.d; ++a) s += L.ratio[B.oMu + B.g.off[a] + j[a]];
+#pragma unroll
+        for (int a = 0; a < PE_MAX_D; ++a) if (a < B.g.d) s += L.ratio[B.oMu + B.g.off[a] + j[a]];
         double pos = (log(B.D * s * B.dT) - B.lloglo) / B.lstep;
         pos = fmin(fmax(pos, 0.0), (double)(L.NB - 1) - 1e-9);
         const int b0 = (int)pos;
@@ -476,7 +482,8 @@ __global__ void __launch_bounds__(256) b_correction_kernel(const BProb* __restri
       int j[PE_MAX_D];
       unflatten(B.g, J, j);
       w = muM[B.oMu + B.g.off[0] + j[0]];
-      for (int a = 1; a < B.g.d; ++a) w *= muM[B.oMu + B.g.off[a] + j[a]];
+#pragma unroll
+      for (int a = 1; a < PE_MAX_D; ++a) if (a < B.g.d) w *= muM[B.oMu + B.g.off[a] + j[a]];
       const double E = coefG[B.oCG + J];
       double* Up = U + B.oU;
       const double* fp = Fbar + B.oS;

@@ -170,7 +170,8 @@ __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, 
 
 // Stage weights of every mode tile formed and split in one pass, in the A-operand layout of the
 // kernel below: tile q occupies 3 * 128 * KP * 2 bytes, [term][row r][k] swizzled as above, row
-// r holding W[k][128 q + r] (zero past the last mode and past K).  A thread per row: the same
+// r holding W[k][128 q + r] (zero past the last mode and past K).  A thread per row and group of
+// eight columns (consecutive threads: the 16-byte chunks of one row, then the next row): the same
 // float32 arithmetic as the SIMT engine's stage-weight table, W[k][J] = P_{r(k),J} sum_i
 // (dt b_i)_J Z_k(c_i dt) with P the product of the per-axis modal factors, so that table is never
 // written or read by this engine.
@@ -186,8 +187,11 @@ __global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols
   for (int e = threadIdx.x; e < q * K; e += blockDim.x) sZ[e] = (float)Z[e];
   for (int e = threadIdx.x; e < K; e += blockDim.x) sTerm[e] = C.term[e];
   __syncthreads();
-  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (J >= tiles * FT_ROWS) return;
+  const int chunks = KP / 8;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tiles * FT_ROWS * chunks) return;
+  const int c = (int)(e % chunks);
+  const int64_t J = e / chunks;
   const int r = (int)(J % FT_ROWS);
   const int64_t tile = J / FT_ROWS, nd = g.ndof;
   const bool ok = J < nd;
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols
 #pragma unroll
   for (int i = 0; i < PE_MAX_S; ++i) b[i] = (ok && i < q) ? coef_b[(int64_t)i * nd + J] : 0.f;
   const int64_t term = (int64_t)FT_ROWS * KP * 2;
-  for (int c = 0; c < KP / 8; ++c) {
+  {
     float x[8];
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
@@ -206,7 +210,8 @@ __global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols
       if (ok && k < K) {
         const int rt = sTerm[k];
         float P = axisF[(int64_t)R * g.off[0] + (int64_t)rt * g.n[0] + j[0]];
-        for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)rt * g.n[a] + j[a]];
+#pragma unroll
+        for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) P *= axisF[(int64_t)R * g.off[a] + (int64_t)rt * g.n[a] + j[a]];
         float sw = 0.f;
 #pragma unroll
         for (int i = 0; i < PE_MAX_S; ++i)
@@ -849,13 +854,28 @@ size_t fine_tc_buffer_bytes(int M, int N) {
 
 // The split operand images depend only on the problem (stage weights, time factors): made
 // once by pe_set_problem (after the stage weights) and reused by every sweep of the problem.
-pe_status fine_tc_prepare(pe_ctx* c) {
-  const int M = c->M, K = c->K, N = c->N;
-  if (!fine_tc_supported(M) || K < 1 || K > 64 || !c->tcB || !c->tc_err)
+static pe_status ft_check(pe_ctx* c) {
+  if (!fine_tc_supported(c->M) || c->K < 1 || c->K > 64 || !c->tcB || !c->tc_err)
     return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported shape");
+  return PE_OK;
+}
+
+pe_status fine_tc_prepare_time(pe_ctx* c) {
+  PE_TRY(ft_check(c));
+  const int M = c->M, K = c->K, N = c->N;
   const int KP = ft_kpad(K), KC = (K + 3) / 4 * 4;
   int G, NR, ngroups;
   ft_shape(KP, M, N, &G, &NR, &ngroups);
+  const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
+  PE_CUDA_TRY(launch_pdl(ft_split_time_kernel, dim3((unsigned)((nsplit + 255) / 256)), dim3(256), 0, c->stream,
+                         (const float*)c->AF32, N, M, K, KC, G, NR, KP, ngroups, (uint4*)c->tcB));
+  c->launches += 1;
+  return PE_OK;
+}
+
+pe_status fine_tc_prepare_weights(pe_ctx* c) {
+  PE_TRY(ft_check(c));
+  const int KP = ft_kpad(c->K);
   const int64_t tiles = (c->g.ndof + FT_ROWS - 1) / FT_ROWS;
   const size_t a_need = (size_t)tiles * ft_a_bytes(KP);
   if (a_need > c->tcA_cap) {
@@ -866,15 +886,19 @@ pe_status fine_tc_prepare(pe_ctx* c) {
     PE_CUDA_TRY(cudaMalloc((void**)&c->tcA, a_need));
     c->tcA_cap = a_need;
   }
-  const int64_t nsplit = (int64_t)ngroups * NR * (KP / 8);
-  PE_CUDA_TRY(launch_pdl(ft_split_time_kernel, dim3((unsigned)((nsplit + 255) / 256)), dim3(256), 0, c->stream,
-                         (const float*)c->AF32, N, M, K, KC, G, NR, KP, ngroups, (uint4*)c->tcB));
-  const int64_t nsw = tiles * FT_ROWS;
+  // a thread per (row, group of eight columns)
+  const int64_t nsw = tiles * FT_ROWS * (KP / 8);
   PE_CUDA_TRY(launch_pdl(ft_weights_image_kernel, dim3((unsigned)((nsw + 255) / 256)), dim3(256), 0, c->stream, c->g,
                          c->cols, c->R, c->q, (const float*)c->axisF32, (const float*)(c->coefF32 + 2 * c->g.ndof),
                          (const double*)c->Zst, KP, tiles, (uint4*)c->tcA));
+  c->launches += 1;
+  return PE_OK;
+}
+
+pe_status fine_tc_prepare(pe_ctx* c) {
+  PE_TRY(fine_tc_prepare_time(c));
+  PE_TRY(fine_tc_prepare_weights(c));
   c->tc_split_ok = true;
-  c->launches += 2;
   return PE_OK;
 }
 

@@ -96,7 +96,8 @@ __global__ void stage_weights_kernel(Geom g, StageCols C, int R, int q, const T*
   for (int k = 0; k < C.K; ++k) {
     const int r = sTerm[k];
     T P = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-    for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+#pragma unroll
+    for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     T s = T(0);
 #pragma unroll
     for (int i = 0; i < PE_MAX_S; ++i)
@@ -157,11 +158,12 @@ __global__ void __launch_bounds__(256) loads_1d_kernel(TermsDev T, Geom g, doubl
 
 // Per-axis source factors in matrix form, for grids whose axes are short: out[e],
 // e = R off_a + r n_a + j (the layout of the per-axis tables), is sum_k S_a[j][k] L[R off_a + r
-// n_a + k], times 1 / mu^M_a(j) when muInv is given.  Eight lanes per output split k (a row of the
-// symmetric transform matrix and the term's loads, both contiguous); a shuffle sum in a fixed
-// order.  The float64 work (n FMAs per output) spreads over every SM, where a half-length FFT
-// per pencil pair runs one chain of dependent float64 latencies on a few SMs.
-constexpr int kFactorLanes = 8;
+// n_a + k], times 1 / mu^M_a(j) when muInv is given.  A warp per output splits k (a row of the
+// symmetric transform matrix and the term's loads, both contiguous: coalesced reads, several in
+// flight per lane); a shuffle sum in a fixed order.  The float64 work (n FMAs per output) spreads
+// over every SM, where a half-length FFT per pencil pair runs one chain of dependent float64
+// latencies on a few SMs.
+constexpr int kFactorLanes = 32;
 __global__ void __launch_bounds__(256) axis_factor_matrix_kernel(Geom g, int R, const double* __restrict__ S0,
                                                                  const double* __restrict__ S1,
                                                                  const double* __restrict__ S2,
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(256) axis_factor_matrix_kernel(Geom g, int R, 
   pdl_wait();
   const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kFactorLanes;
   const int sub = threadIdx.x & (kFactorLanes - 1);
-  if (e >= total) return;  // whole groups of eight lanes leave together
+  if (e >= total) return;  // whole warps leave together
   int a = 0;
   while (a + 1 < g.d && e >= (int64_t)R * g.off[a + 1]) ++a;
   const int n = g.n[a];
@@ -182,10 +184,10 @@ __global__ void __launch_bounds__(256) axis_factor_matrix_kernel(Geom g, int R, 
   const double* row = S + (int64_t)j * n;
   const double* L = loads + (int64_t)R * g.off[a] + (int64_t)r * n;
   double acc = 0.0;
+#pragma unroll 4
   for (int k = sub; k < n; k += kFactorLanes) acc = fma(row[k], L[k], acc);
-  const unsigned grp = 0xFFu << (threadIdx.x & 24);
 #pragma unroll
-  for (int o = kFactorLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(grp, acc, o);
+  for (int o = kFactorLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
   if (sub == 0) {
     const double v = muInv ? acc * muInv[g.off[a] + j] : acc;
     fac[e] = v;
@@ -216,7 +218,8 @@ __global__ void outer_sum_kernel(Geom g, int R, const double* __restrict__ fac, 
   double acc = 0.0;
   for (int r = 0; r < R; ++r) {
     double P = fac[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-    for (int a = 1; a < g.d; ++a) P *= fac[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+#pragma unroll
+    for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) P *= fac[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     acc += w[r] * P;
   }
   out[J] = accumulate ? out[J] + acc : acc;
@@ -228,7 +231,8 @@ __global__ void scale_mu_kernel(Geom g, const double* __restrict__ muM, double* 
   int j[PE_MAX_D];
   unflatten(g, J, j);
   double mu = muM[g.off[0] + j[0]];
-  for (int a = 1; a < g.d; ++a) mu *= muM[g.off[a] + j[a]];
+#pragma unroll
+  for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) mu *= muM[g.off[a] + j[a]];
   x[J] = inverse ? x[J] / mu : x[J] * mu;
 }
 

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(256) gen_fine_f64_kernel(Geom g, int n0, int M
   int j[PE_MAX_D];
   unflatten(g, J, j);
   double mu = muM_axis[g.off[0] + j[0]];
-  for (int a = 1; a < g.d; ++a) mu *= muM_axis[g.off[a] + j[a]];
+#pragma unroll
+  for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) mu *= muM_axis[g.off[a] + j[a]];
   const double E = coefF[J];
   double b[PE_MAX_S];
 #pragma unroll
@@ -233,7 +234,8 @@ __global__ void __launch_bounds__(256) gen_fine_mixed_kernel(Geom g, int n0, int
   int j[PE_MAX_D];
   unflatten(g, J, j);
   double mu = muM_axis[g.off[0] + j[0]];
-  for (int a = 1; a < g.d; ++a) mu *= muM_axis[g.off[a] + j[a]];
+#pragma unroll
+  for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) mu *= muM_axis[g.off[a] + j[a]];
   const float eh = coefF32[J], el = coefF32[nd + J];
   float b[PE_MAX_S];
 #pragma unroll
@@ -263,7 +265,8 @@ __global__ void gen_coarse_forcing_kernel(Geom g, int N, int p, const double* __
   int j[PE_MAX_D];
   unflatten(g, J, j);
   double mu = muM_axis[g.off[0] + j[0]];
-  for (int a = 1; a < g.d; ++a) mu *= muM_axis[g.off[a] + j[a]];
+#pragma unroll
+  for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) mu *= muM_axis[g.off[a] + j[a]];
   double acc = 0.0;
   for (int i = 0; i < p; ++i) acc = fma(coefG[(1 + i) * nd + J] / mu, Gc[((int64_t)n * p + i) * nd + J], acc);
   gG[(int64_t)n * nd + J] = acc;

@@ -6,6 +6,7 @@
 
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "pe.h"
 
@@ -43,12 +44,27 @@ struct Geom {
   int64_t ndof;
 };
 
-// Decompose a flat C-ordered mode index into per-axis indices (0-based).
+// Decompose a flat C-ordered mode index into per-axis indices (0-based); j[a] for a >= g.d is
+// left unset.  Unrolled over PE_MAX_D axes so that j stays in registers when the caller's axis
+// loops are unrolled too; 32-bit divisions while J fits (every grid of up to 2^32 modes).
 __host__ __device__ inline void unflatten(const Geom& g, int64_t J, int* j) {
-  for (int a = g.d - 1; a >= 0; --a) {
-    j[a] = (int)(J % g.n[a]);
-    J /= g.n[a];
+  if (J >= 0 && J <= (int64_t)0xFFFFFFFFu) {
+    unsigned u = (unsigned)J;
+#pragma unroll
+    for (int a = PE_MAX_D - 1; a >= 0; --a)
+      if (a < g.d) {
+        const unsigned n = (unsigned)g.n[a], q = u / n;
+        j[a] = (int)(u - q * n);
+        u = q;
+      }
+    return;
   }
+#pragma unroll
+  for (int a = PE_MAX_D - 1; a >= 0; --a)
+    if (a < g.d) {
+      j[a] = (int)(J % g.n[a]);
+      J /= g.n[a];
+    }
 }
 
 // Separable forcing, device layout (R terms, K stage-contracted columns):
@@ -131,7 +147,7 @@ struct pe_ctx {
   bool tc_split_ok = false;      // tcA / tcB hold the current problem's split operands
   int* tc_err = nullptr;         // tensor-core fine engine: error code of an expired wait (0: none)
   cudaStream_t side = nullptr;  // second stream: the nodal u0 transform beside the forcing tables
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tables = nullptr;
   double* h_red = nullptr;      // [2] pinned host
   int max_blocks = 0;
   int sms = 0;                      // SMs of the context's device
@@ -183,6 +199,10 @@ struct pe_ctx {
   cudaGraphExec_t setup_exec = nullptr, out_exec = nullptr;
   uint64_t graph_key = 0;           // problem the graphs were captured for
   int graph_key_seen = 0;           // solves of graph_key so far (captured at the second)
+  // a solve enqueued by pe_solve_async (or the first half of pe_solve), reported by pe_solve_wait
+  bool pend = false, pend_on_device = false;
+  double pend_tol = 0.0, pend_r = 0.0;
+  std::vector<double> pend_hist;    // residuals of the host-driven loop
   int64_t setup_launches = 0, out_launches = 0;
   int u0_dev_hint = -1;             // u0 nodal pointer is device memory (1) / host (0) / unknown (-1)
   int capturing = 0;                // the phase being run is captured (timing events become graph nodes)
@@ -297,5 +317,7 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 // Drops the cached set-up and output graphs of a repeated problem (pe_api.cu).
 void drop_solve_graphs(pe_ctx* c);
 pe_status fine_tc_prepare(pe_ctx* c);          // split operand images of the current problem
+pe_status fine_tc_prepare_time(pe_ctx* c);     //   the time factors' image (after the time tables)
+pe_status fine_tc_prepare_weights(pe_ctx* c);  //   the stage weights' image (after tables and factors)
 pe_status launch_fine_tc(pe_ctx* c, int from_zero, double* out);
 pe_status fine_tc_status(pe_ctx* c);           // PE_ETIMEOUT if a pipeline wait expired

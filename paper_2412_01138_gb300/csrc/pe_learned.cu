@@ -529,7 +529,8 @@ __global__ void __launch_bounds__(256) learned_correction_kernel(Geom g, int N, 
     float A = 0.f, Bv = 0.f;
     if (T.is_sin[r]) {
       double P = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-      for (int a = 1; a < g.d; ++a) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+#pragma unroll
+      for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) P *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
       const double* k0 = Ktab + 2 * ((int64_t)r * NB + b0);
       const double Kre = (1.0 - f) * k0[0] + f * k0[2];
       const double Kim = (1.0 - f) * k0[1] + f * k0[3];

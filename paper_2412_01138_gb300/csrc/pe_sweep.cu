@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(256) coarse_forcing_kernel(Geom g, int N, int 
     T v = T(0);
     if (r < R) {
       v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-      for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+#pragma unroll
+      for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     }
     P[r] = v;
   }
@@ -156,7 +157,8 @@ __global__ void __launch_bounds__(512) coarse_fused_kernel(Geom g, int N, int p,
     T v = T(0);
     if (r < R) {
       v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-      for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+#pragma unroll
+      for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     }
     P[r] = v;
   }
@@ -172,7 +174,9 @@ __global__ void __launch_bounds__(512) coarse_fused_kernel(Geom g, int N, int p,
       LB[r] = 0.f;
       if (r < R && L.is_sin[r]) {
         double Pd = axisF64[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-        for (int a = 1; a < g.d; ++a) Pd *= axisF64[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+#pragma unroll
+        for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d)
+          Pd *= axisF64[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
         const double* k0 = L.Ktab + 2 * ((int64_t)r * L.NB + b0);
         const double Kre = (1.0 - f) * k0[0] + f * k0[2];
         const double Kim = (1.0 - f) * k0[1] + f * k0[3];
@@ -354,7 +358,8 @@ __global__ void __launch_bounds__(512) correction_kernel(Geom g, int N, const do
     int j[PE_MAX_D];
     unflatten(g, J, j);
     w = muM_axis[g.off[0] + j[0]];
-    for (int a = 1; a < g.d; ++a) w *= muM_axis[g.off[a] + j[a]];
+#pragma unroll
+    for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) w *= muM_axis[g.off[a] + j[a]];
     const double E = coefG[J];
     double d = 0.0;
     // per slice n: Fbar^{n+1} = F(U^{n,(k)}) and the old U^{n+1}

@@ -12,7 +12,8 @@ __device__ inline void load_P(const Geom& g, int64_t J, const T* __restrict__ ax
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     T v = axisF[(int64_t)R * g.off[0] + (int64_t)r * g.n[0] + j[0]];
-    for (int a = 1; a < g.d; ++a) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
+#pragma unroll
+    for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) v *= axisF[(int64_t)R * g.off[a] + (int64_t)r * g.n[a] + j[a]];
     P[r] = v;
   }
 }

@@ -50,7 +50,8 @@ __global__ void coef_tables_kernel(Geom g, const double* __restrict__ ratio, dou
   int j[PE_MAX_D];
   unflatten(g, J, j);
   double s = 0.0;
-  for (int a = 0; a < g.d; ++a) s += ratio[g.off[a] + j[a]];
+#pragma unroll
+  for (int a = 0; a < PE_MAX_D; ++a) if (a < g.d) s += ratio[g.off[a] + j[a]];
   const double lam = D * s;
   lam_out[J] = lam;
   const int64_t nd = g.ndof;

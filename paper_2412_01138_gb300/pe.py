@@ -38,7 +38,8 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_batch_destroy", "pe_mlp_create", "pe_mlp_num_params", "pe_mlp_train", "pe_mlp_gradient",
             "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
             "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc", "pe_set_dirichlet", "pe_measure_fma_peak",
-            "pe_probe_wait_timeout", "pe_parareal_iter_sums", "pe_batch_set_learned")
+            "pe_probe_wait_timeout", "pe_parareal_iter_sums", "pe_batch_set_learned", "pe_solve_out",
+            "pe_solve_async", "pe_solve_wait")
 
 
 class PEError(RuntimeError):
@@ -113,6 +114,10 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_parareal_iter_sums": (C.c_int, [P, C.POINTER(C.c_double)]),
         "pe_refine": (C.c_int, [P, C.POINTER(C.c_double)]),
         "pe_solve": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing), C.c_double, C.POINTER(pe_result)]),
+        "pe_solve_out": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing), C.c_double, P,
+                                   C.POINTER(pe_result)]),
+        "pe_solve_async": (C.c_int, [P, C.POINTER(pe_field), C.POINTER(pe_forcing), C.c_double, P]),
+        "pe_solve_wait": (C.c_int, [P, C.POINTER(pe_result)]),
         "pe_get_solution": (C.c_int, [P, C.c_int32, P]),
         "pe_get_modal": (C.c_int, [P, C.c_int32, P]),
         "pe_get_lambda": (C.c_int, [P, P]),
@@ -182,6 +187,18 @@ def _ptr(x) -> int:
             raise ValueError("tensor must be contiguous")
         return x.data_ptr()
     raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check_out(x, count: int):
+    """An output buffer of the solver: float64, contiguous (checked by _ptr), >= count values."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or x.size < count:
+            raise ValueError(f"output must hold >= {count} float64 values, got {x.size} {x.dtype}")
+    elif hasattr(x, "numel"):
+        if str(x.dtype) != "torch.float64" or x.numel() < count:
+            raise ValueError(f"output must hold >= {count} float64 values, got {x.numel()} {x.dtype}")
+    else:
+        raise TypeError(f"unsupported buffer type {type(x)}")
 
 
 def make_terms(terms: Sequence["_in.Term"]):
@@ -311,14 +328,48 @@ class Solver:
         return r.value
 
     def solve(self, tol: Optional[float] = None, u0_kind: int = PE_FIELD_TERMS_SEPARABLE, nodal=None,
-              history: int = 64) -> dict:
+              history: int = 64, out=None) -> dict:
+        """pe_solve; with ``out`` (host array or device tensor of ndof float64) pe_solve_out,
+        which also writes the nodal solution of the last slice into it."""
         f = self._field(u0_kind, nodal)
+        res, hist = self._result(history)
+        tol = self.prob.tol if tol is None else tol
+        if out is None:
+            st = self._lib.pe_solve(self.ctx, C.byref(f), C.byref(self._forcing()), tol, C.byref(res))
+        else:
+            _check_out(out, self.prob.ndof)
+            st = self._lib.pe_solve_out(self.ctx, C.byref(f), C.byref(self._forcing()), tol, _ptr(out),
+                                        C.byref(res))
+        return self._report(st, res, hist, history)
+
+    def solve_async(self, tol: Optional[float] = None, u0_kind: int = PE_FIELD_TERMS_SEPARABLE, nodal=None,
+                    out=None) -> None:
+        """pe_solve_async: the whole solve enqueued on the context's stream; ``wait`` reports it.
+        A device u0 and ``out`` must stay alive until then."""
+        f = self._field(u0_kind, nodal)
+        tol = self.prob.tol if tol is None else tol
+        if out is not None:
+            _check_out(out, self.prob.ndof)
+        self._pending = (nodal, out)  # the buffers the enqueued work reads and writes
+        _check(self._lib.pe_solve_async(self.ctx, C.byref(f), C.byref(self._forcing()), tol,
+                                        None if out is None else _ptr(out)))
+
+    def wait(self, history: int = 64) -> dict:
+        """pe_solve_wait: the report of the pending solve (as ``solve`` returns it)."""
+        res, hist = self._result(history)
+        st = self._lib.pe_solve_wait(self.ctx, C.byref(res))
+        self._pending = None
+        return self._report(st, res, hist, history)
+
+    @staticmethod
+    def _result(history: int):
         hist = (C.c_double * history)()
         res = pe_result()
         res.residual_history = C.cast(hist, C.POINTER(C.c_double))
         res.history_cap = history
-        tol = self.prob.tol if tol is None else tol
-        st = self._lib.pe_solve(self.ctx, C.byref(f), C.byref(self._forcing()), tol, C.byref(res))
+        return res, hist
+
+    def _report(self, st: int, res, hist, history: int) -> dict:
         info = {"k": res.k, "residual": res.residual, "history": list(hist[: min(res.k, history)]),
                 "fine_sweeps": res.fine_sweeps, "ms_tables": res.ms_tables, "ms_prepare": res.ms_prepare,
                 "ms_iterations": res.ms_iterations, "ms_output": res.ms_output,

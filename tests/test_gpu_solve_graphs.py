@@ -130,3 +130,55 @@ def test_device_loop_value_is_checked(env):
         with pytest.raises(pe.PEError) as ei:
             pe.Solver(prob, device_loop=bad)
         assert ei.value.status == pe.PE_EINVAL
+
+
+@pytest.mark.parametrize("dl", [0, 2], ids=["host_loop", "replayed"])
+def test_solve_out_writes_the_solution(env, dl):
+    """pe_solve_out: the nodal solution written by the solve itself (host array or device
+    tensor) equals pe_get_solution's, on every solve of a replayed problem as well."""
+    pe, torch = env
+    prob = I.scaled(I.config2(), (71, 65), N=5, M=16)
+    u0 = np.random.default_rng(3).standard_normal(prob.ndof)
+    buf = torch.from_numpy(u0).cuda()
+    with pe.Solver(prob, precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC, device_loop=dl) as s:
+        for rep in range(3):
+            host = np.full(prob.ndof, np.nan)
+            dev = torch.full((prob.ndof,), float("nan"), dtype=torch.float64, device="cuda")
+            s.solve(tol=1e-6, u0_kind=pe.PE_FIELD_NODAL, nodal=buf, out=host)
+            ref = s.solution(prob.N)
+            assert np.array_equal(host, ref), rep
+            s.solve(tol=1e-6, u0_kind=pe.PE_FIELD_NODAL, nodal=buf, out=dev)
+            assert np.array_equal(dev.cpu().numpy(), ref), rep
+        with pytest.raises(ValueError):
+            s.solve(tol=1e-6, u0_kind=pe.PE_FIELD_NODAL, nodal=buf, out=np.empty(prob.ndof, dtype=np.float32))
+        with pytest.raises(ValueError):
+            s.solve(tol=1e-6, u0_kind=pe.PE_FIELD_NODAL, nodal=buf, out=np.empty(prob.ndof - 1))
+
+
+@pytest.mark.parametrize("dl", [0, 1, 2], ids=["host_loop", "device_loop", "replayed"])
+def test_async_solve_equals_solve(env, dl):
+    """pe_solve_async + pe_solve_wait report and produce what pe_solve does (k, residual history,
+    iterates, the nodal output written into the caller's buffer); one solve may be pending."""
+    pe, torch = env
+    prob = I.scaled(I.config2(), (71, 65), N=6, M=16)
+    buf = torch.from_numpy(np.random.default_rng(5).standard_normal(prob.ndof)).cuda()
+    kw = dict(precision=pe.PE_MIXED, fine_engine=pe.PE_FINE_TC, device_loop=dl)
+    with pe.Solver(prob, **kw) as s:
+        ref = [_snapshot(s, prob, s.solve(tol=1e-6, u0_kind=pe.PE_FIELD_NODAL, nodal=buf)) for _ in range(3)]
+    with pe.Solver(prob, **kw) as s:
+        for rep in range(3):
+            out = torch.full((prob.ndof,), float("nan"), dtype=torch.float64, device="cuda")
+            s.solve_async(tol=1e-6, u0_kind=pe.PE_FIELD_NODAL, nodal=buf, out=out)
+            if rep == 0:
+                for call in (lambda: s.solve_async(tol=1e-6, u0_kind=pe.PE_FIELD_NODAL, nodal=buf),
+                             lambda: s.modal(0), lambda: s.solution(prob.N), lambda: s.iterate()):
+                    with pytest.raises(pe.PEError) as ei:
+                        call()
+                    assert ei.value.status == pe.PE_ESTATE
+            info = s.wait()
+            got = _snapshot(s, prob, info)
+            _same(got, ref[rep])
+            assert np.array_equal(out.cpu().numpy(), ref[rep][4]), rep
+        with pytest.raises(pe.PEError) as ei:
+            s.wait()
+        assert ei.value.status == pe.PE_ESTATE
