@@ -175,7 +175,8 @@ __global__ void ft_split_time_kernel(const float* __restrict__ Y, int N, int M, 
 // float32 arithmetic as the SIMT engine's stage-weight table, W[k][J] = P_{r(k),J} sum_i
 // (dt b_i)_J Z_k(c_i dt) with P the product of the per-axis modal factors, so that table is never
 // written or read by this engine.
-__global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols C, int R, int q,
+template <int Q>
+__global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols C, int R,
                                                                const float* __restrict__ axisF,
                                                                const float* __restrict__ coef_b,
                                                                const double* __restrict__ Z, int KP, int64_t tiles,
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols
   __shared__ float sZ[PE_MAX_S * 2 * PE_MAX_TERMS];
   __shared__ int sTerm[2 * PE_MAX_TERMS];
   const int K = C.K;
-  for (int e = threadIdx.x; e < q * K; e += blockDim.x) sZ[e] = (float)Z[e];
+  for (int e = threadIdx.x; e < Q * K; e += blockDim.x) sZ[e] = (float)Z[e];
   for (int e = threadIdx.x; e < K; e += blockDim.x) sTerm[e] = C.term[e];
   __syncthreads();
   const int chunks = KP / 8;
@@ -194,28 +195,37 @@ __global__ void __launch_bounds__(256) ft_weights_image_kernel(Geom g, StageCols
   const int64_t J = e / chunks;
   const int r = (int)(J % FT_ROWS);
   const int64_t tile = J / FT_ROWS, nd = g.ndof;
-  const bool ok = J < nd;
-  int j[PE_MAX_D] = {0, 0, 0};
-  float b[PE_MAX_S];
-  if (ok) unflatten(g, J, j);
-#pragma unroll
-  for (int i = 0; i < PE_MAX_S; ++i) b[i] = (ok && i < q) ? coef_b[(int64_t)i * nd + J] : 0.f;
   const int64_t term = (int64_t)FT_ROWS * KP * 2;
+  if (J >= nd || 8 * c >= K) {
+    // padding rows past the last mode and columns past K: zero in every split term
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      Asp[((tile * 3 + t) * term + ft_swz((int64_t)r * KP * 2 + c * 16, KP)) / 16] = make_uint4(0u, 0u, 0u, 0u);
+    return;
+  }
+  int j[PE_MAX_D];
+  unflatten(g, J, j);
+  // the row's entries of the per-axis factor tables (term rt of axis a at ax[a][rt * n_a])
+  const float* ax[PE_MAX_D];
+#pragma unroll
+  for (int a = 0; a < PE_MAX_D; ++a) ax[a] = axisF + (int64_t)R * g.off[a] + j[a];
+  float b[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) b[i] = coef_b[(int64_t)i * nd + J];
   {
     float x[8];
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
       const int k = 8 * c + jj;
       float v = 0.f;
-      if (ok && k < K) {
+      if (k < K) {
         const int rt = sTerm[k];
-        float P = axisF[(int64_t)R * g.off[0] + (int64_t)rt * g.n[0] + j[0]];
+        float P = ax[0][rt * g.n[0]];
 #pragma unroll
-        for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) P *= axisF[(int64_t)R * g.off[a] + (int64_t)rt * g.n[a] + j[a]];
+        for (int a = 1; a < PE_MAX_D; ++a) if (a < g.d) P *= ax[a][rt * g.n[a]];
         float sw = 0.f;
 #pragma unroll
-        for (int i = 0; i < PE_MAX_S; ++i)
-          if (i < q) sw = fmaf(b[i], sZ[i * K + k], sw);
+        for (int i = 0; i < Q; ++i) sw = fmaf(b[i], sZ[i * K + k], sw);
         v = P * sw;
       }
       x[jj] = v;
@@ -888,9 +898,20 @@ pe_status fine_tc_prepare_weights(pe_ctx* c) {
   }
   // a thread per (row, group of eight columns)
   const int64_t nsw = tiles * FT_ROWS * (KP / 8);
-  PE_CUDA_TRY(launch_pdl(ft_weights_image_kernel, dim3((unsigned)((nsw + 255) / 256)), dim3(256), 0, c->stream, c->g,
-                         c->cols, c->R, c->q, (const float*)c->axisF32, (const float*)(c->coefF32 + 2 * c->g.ndof),
-                         (const double*)c->Zst, KP, tiles, (uint4*)c->tcA));
+  const dim3 grid((unsigned)((nsw + 255) / 256));
+  const float* ax = c->axisF32;
+  const float* cb = c->coefF32 + 2 * c->g.ndof;
+  switch (c->q) {
+#define PE_FW_CASE(Q)                                                                                          \
+  case Q:                                                                                                      \
+    PE_CUDA_TRY(launch_pdl(ft_weights_image_kernel<Q>, grid, dim3(256), 0, c->stream, c->g, c->cols, c->R, ax, cb, \
+                           (const double*)c->Zst, KP, tiles, (uint4*)c->tcA));                                  \
+    break;
+    PE_FW_CASE(1) PE_FW_CASE(2) PE_FW_CASE(3) PE_FW_CASE(4) PE_FW_CASE(5) PE_FW_CASE(6) PE_FW_CASE(7) PE_FW_CASE(8)
+#undef PE_FW_CASE
+    default:
+      return pe_fail(PE_EINVAL, "fine sweep (tensor cores): unsupported number of stages");
+  }
   c->launches += 1;
   return PE_OK;
 }

@@ -159,10 +159,10 @@ __global__ void __launch_bounds__(256) loads_1d_kernel(TermsDev T, Geom g, doubl
 // Per-axis source factors in matrix form, for grids whose axes are short: out[e],
 // e = R off_a + r n_a + j (the layout of the per-axis tables), is sum_k S_a[j][k] L[R off_a + r
 // n_a + k], times 1 / mu^M_a(j) when muInv is given.  A warp per output splits k (a row of the
-// symmetric transform matrix and the term's loads, both contiguous: coalesced reads, several in
-// flight per lane); a shuffle sum in a fixed order.  The float64 work (n FMAs per output) spreads
-// over every SM, where a half-length FFT per pencil pair runs one chain of dependent float64
-// latencies on a few SMs.
+// symmetric transform matrix and the term's loads, both contiguous: coalesced reads, all of a
+// lane's loads in flight at once for n < 256, so a row read from HBM costs one latency); a shuffle
+// sum in a fixed order.  The float64 work (n FMAs per output) spreads over every SM, where a
+// half-length FFT per pencil pair runs one chain of dependent float64 latencies on a few SMs.
 constexpr int kFactorLanes = 32;
 __global__ void __launch_bounds__(256) axis_factor_matrix_kernel(Geom g, int R, const double* __restrict__ S0,
                                                                  const double* __restrict__ S1,
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) axis_factor_matrix_kernel(Geom g, int R, 
   const double* row = S + (int64_t)j * n;
   const double* L = loads + (int64_t)R * g.off[a] + (int64_t)r * n;
   double acc = 0.0;
-#pragma unroll 4
+#pragma unroll 8
   for (int k = sub; k < n; k += kFactorLanes) acc = fma(row[k], L[k], acc);
 #pragma unroll
   for (int o = kFactorLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
