@@ -293,6 +293,21 @@ inline int per_mode_block(int64_t units, int sms) {
 // it touches global memory: it waits there until the predecessor has completed and its writes
 // are visible, then lets its own successor be scheduled early in turn.  Without the launch
 // attribute (a plain launch) both instructions do nothing.
+// Exact float32 -> float64 widening.  GB300 runs the F2F conversion on its float64 pipe (two
+// lanes per SM), where the recurrences that add a float32 sum into a float64 state already
+// spend their float64 budget; a normal float32 is widened here with integer operations instead
+// (IEEE 754 binary32 -> binary64: exponent rebiased by 1023 - 127 = 896, fraction shifted left
+// by 29), zero by its sign alone, and the rare subnormal, infinite or NaN values by the
+// conversion, behind a call so that it is not issued for the common case.
+static __device__ __noinline__ double widen_f32_rare(float x) { return (double)x; }
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned u = __float_as_uint(x), mag = u & 0x7FFFFFFFu;
+  if (mag - 0x00800000u < 0x7F000000u)
+    return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + 0x38000000u)), (int)(u << 29));
+  if (mag == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return widen_f32_rare(x);
+}
+
 __device__ __forceinline__ void pdl_wait() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");

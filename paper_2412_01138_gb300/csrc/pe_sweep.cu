@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(512) coarse_fused_kernel(Geom g, int N, int p,
   for (int i = 0; i < PE_MAX_S; ++i) b[i] = i < p ? (T)coefG[(1 + i) * nd + J] : T(0);
   const double E = coefG[J];
   double c = U[J];
+  // two slices per pass: the forcing sums of the second overlap the float64 step of the first
+#pragma unroll 2
   for (int n = 0; n < N; ++n) {
     T acc = T(0);
 #pragma unroll
@@ -218,7 +220,9 @@ __global__ void __launch_bounds__(512) coarse_fused_kernel(Geom g, int N, int p,
         acc = fma(b[i], gi, acc);
       }
     }
-    double gn = (double)acc;
+    double gn;
+    if constexpr (sizeof(T) == 4) gn = widen_f32(acc);
+    else gn = acc;
     if constexpr (LEARN) {
       float dl = 0.f;
       const float2* e = sCS + (int64_t)n * RB;
