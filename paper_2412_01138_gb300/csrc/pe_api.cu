@@ -392,9 +392,10 @@ extern "C" pe_status pe_setup(pe_ctx** out, int32_t d, const int32_t* n, const d
   if (st == PE_OK && c->device_loop) {
     st = dev_alloc(&c->loopctl, 1);
     if (st == PE_OK) st = dev_alloc(&c->loop_hist, N);
-    if (st == PE_OK && cudaMallocHost((void**)&c->h_loop, sizeof(LoopCtl)) != cudaSuccess) {
+    if (st == PE_OK && (cudaHostAlloc((void**)&c->h_loop, sizeof(LoopCtl), cudaHostAllocMapped) != cudaSuccess ||
+                        cudaHostGetDevicePointer((void**)&c->h_loop_dev, c->h_loop, 0) != cudaSuccess)) {
       cudaGetLastError();
-      st = pe_fail(PE_ENOMEM, "pe_setup: pinned host allocation failed");
+      st = pe_fail(PE_ENOMEM, "pe_setup: mapped pinned host allocation failed");
     }
   }
   for (int i = 0; i < PE_NEV && st == PE_OK; ++i)
@@ -837,30 +838,27 @@ static pe_status build_loop_graph(pe_ctx* c) {
   return PE_OK;
 }
 
-// Iterations of pe_solve on the device, enqueued: the loop state in, the graph, the state back out.
+// Iterations of pe_solve on the device, enqueued: a kernel arms the loop state, the graph runs
+// the loop, and the stop decision of every iteration also writes k, r and the non-finite flag
+// into the mapped pinned mirror that the host reads after the solve's wait (no copies).
 static pe_status enqueue_loop_on_device(pe_ctx* c, double tol) {
   PE_TRY(build_loop_graph(c));
-  LoopCtl* h = c->h_loop;
+  volatile LoopCtl* h = c->h_loop;
   h->k = 0;
-  h->max_iter = c->max_iter;
   h->nonfinite = 0;
-  h->hist_cap = c->N;
-  h->tol = tol;
   h->r = INFINITY;
-  h->hist = c->loop_hist;
-  PE_CUDA_TRY(cudaMemcpyAsync(c->loopctl, h, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->stream));
+  PE_TRY(launch_loop_init(c, tol));
   PE_CUDA_TRY(cudaGraphLaunch(c->loop_exec, c->stream));
-  PE_CUDA_TRY(cudaMemcpyAsync(h, c->loopctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->stream));
   return PE_OK;
 }
 
 // After the stream has completed: k, the last residual in *r, the history.
 static pe_status finish_loop_on_device(pe_ctx* c, pe_result* res, double* r) {
-  LoopCtl* h = c->h_loop;
+  volatile LoopCtl* h = c->h_loop;
   const int k = h->k;
   c->k += k;
   c->sweeps += k;
-  c->launches += (int64_t)k * c->loop_body_launches + 1;
+  c->launches += (int64_t)k * c->loop_body_launches;
   *r = h->r;
   if (res && res->residual_history && res->history_cap > 0) {
     const int cnt = std::min(k, res->history_cap);

@@ -86,7 +86,8 @@ struct StageCols {
 struct LoopCtl {
   int k, max_iter, nonfinite, hist_cap;
   double tol, r;
-  double* hist;  // [hist_cap] residuals r_1 .. r_k (device)
+  double* hist;   // [hist_cap] residuals r_1 .. r_k (device)
+  LoopCtl* host;  // device address of the mapped pinned mirror that receives k, r, nonfinite
 };
 
 struct pe_ctx {
@@ -192,7 +193,8 @@ struct pe_ctx {
   int loop_K = -1, loop_prec = -1;  // what the graph was built for
   int64_t loop_body_launches = 0;   // kernels of one pass of the graph's body
   LoopCtl* loopctl = nullptr;       // device
-  LoopCtl* h_loop = nullptr;        // pinned host copy
+  LoopCtl* h_loop = nullptr;        // mapped pinned mirror of the loop state (host address)
+  LoopCtl* h_loop_dev = nullptr;    //   its device address
   double* loop_hist = nullptr;      // device [N]
   // device_loop = 2: the set-up and output phases of a repeated problem replayed as CUDA graphs
   cudaStream_t cap_stream = nullptr;  // capture stream (the context's own may be the legacy stream)
@@ -264,6 +266,8 @@ pe_status launch_correction(pe_ctx* c, double* num, double* den, cudaEvent_t aft
 // the correction kernel alone; with loop != NULL its last CTA also runs the stopping decision of a
 // device-resident loop (appends r, advances k, sets the graph condition `handle`)
 pe_status launch_correction_kernel(pe_ctx* c, LoopCtl* loop, unsigned long long handle);
+// Arms the device-resident loop's state for one solve (k = 0, tol, the history, the mirror).
+pe_status launch_loop_init(pe_ctx* c, double tol);
 pe_status launch_scale_by_muM(pe_ctx* c, double* x, int inverse);
 
 // pe_learned.cu

@@ -333,8 +333,29 @@ __device__ void loop_decide(LoopCtl* L, unsigned long long handle, double num, d
   L->k = k + 1;
   L->r = r;
   if (!finite) L->nonfinite = 1;
+  // the host reads k, r and the flag from its mapped mirror after the solve's one wait
+  volatile LoopCtl* H = L->host;
+  H->k = k + 1;
+  H->r = r;
+  if (!finite) H->nonfinite = 1;
+  __threadfence_system();
   cudaGraphSetConditional((cudaGraphConditionalHandle)handle,
                           (finite && r > L->tol && k + 1 < L->max_iter) ? 1u : 0u);
+}
+
+__global__ void loop_init_kernel(LoopCtl* L, int max_iter, int hist_cap, double tol, double* hist,
+                                 LoopCtl* host) {
+  pdl_wait();
+  if (threadIdx.x == 0) {
+    L->k = 0;
+    L->max_iter = max_iter;
+    L->nonfinite = 0;
+    L->hist_cap = hist_cap;
+    L->tol = tol;
+    L->r = INFINITY;
+    L->hist = hist;
+    L->host = host;
+  }
 }
 
 // The correction: one thread per mode walks the slices.  With d = U^{n,(k+1)} - U^{n,(k)}
@@ -481,6 +502,13 @@ pe_status launch_correction(pe_ctx* c, double* num, double* den, cudaEvent_t aft
   PE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   *num = c->h_red[0];
   *den = c->h_red[1];
+  return PE_OK;
+}
+
+pe_status launch_loop_init(pe_ctx* c, double tol) {
+  PE_CUDA_TRY(launch_pdl(loop_init_kernel, dim3(1), dim3(32), 0, c->stream, c->loopctl, c->max_iter, c->N, tol,
+                         c->loop_hist, c->h_loop_dev));
+  c->launches += 1;
   return PE_OK;
 }
 
