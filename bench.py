@@ -1063,7 +1063,9 @@ def main():
         "chosen": {"form": "mixed: stage contraction on the tensor cores (tcgen05, three-term bfloat16 split, "
                            "six products, float32 accumulators), float32 recurrence (hi/lo E), float64 tables, "
                            "correction, residual; Parareal loop on the device (one CUDA graph with a conditional "
-                           "while node; kernel times from the same solve with the host-driven loop)",
+                           "while node), set-up and output phases replayed as CUDA graphs, the solve enqueued "
+                           "with pe_solve_async and its nodal output written by the solve; kernel times from "
+                           "the same solve with the host-driven loop",
                    "value": chosen["value"], "unit": UNIT, "time_to_tol_ms": chosen["ms_per_step"],
                    "iterations": chosen["k"], "rel_l2_vs_oracle": err_chosen, "dtype": "f32",
                    "speedup_time_to_tol": plain["ms_per_step"] / chosen["ms_per_step"],

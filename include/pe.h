@@ -295,8 +295,9 @@ pe_status pe_solve_out(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f, dou
  * fills out (may be NULL) and returns what pe_solve would have returned (PE_ENOCONV,
  * PE_ENONFINITE, ...).  One solve may be pending per context: until pe_solve_wait, the
  * context's other calls that read or change its state return PE_ESTATE, and nodal_out
- * (caller-owned) and a device u0 must stay valid.  pe_solve_wait without a pending solve:
- * PE_ESTATE.
+ * (caller-owned) and a device u0 must stay valid.  nodal_out in pageable host memory makes
+ * the copy, and so the call, wait for the solve (device or pinned host memory does not).
+ * pe_solve_wait without a pending solve: PE_ESTATE.
  */
 pe_status pe_solve_async(pe_ctx* ctx, const pe_field* u0, const pe_forcing* f, double tol, double* nodal_out);
 pe_status pe_solve_wait(pe_ctx* ctx, pe_result* out);
