@@ -124,28 +124,50 @@ __global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int6
   const int p = find_prob(tt_prefix, P, idx);
   const BProb& B = probs[p];
   const int R = B.R, K = B.K;
-  const int64_t nf = (int64_t)B.N * B.M * K;
+  const int64_t nrow = (int64_t)B.N * K;
   const int64_t ng = (int64_t)B.N * B.p * R;
   int64_t local = idx - tt_prefix[p];
-  if (local < nf) {
-    int64_t rest = local;
-    const int k = (int)(rest % K); rest /= K;
-    const int m = (int)(rest % B.M); rest /= B.M;
-    const int n = (int)rest;
-    const double t = B.t0 + (double)n * B.dT + (double)m * B.dt;
+  if (local < nrow) {
+    // one thread per (slice n, column k) walks the substeps m: the factor at T_n + m dt from
+    // the one at T_n by the exact step e^{a dt} or the rotation by omega dt (angle addition),
+    // two transcendental evaluations per thread instead of one per entry; the rounding grows
+    // by about one unit in the last place per substep (M <= 128)
+    const int k = (int)(local % K), n = (int)(local / K);
     const int c = cols[B.oCol + k];
     const pe_term& T = terms[B.tf + (c >> 1)];
-    const double v = (c & 1) ? T.amp * cos(T.tp[0] * t + T.tp[1]) : T.amp * eval_time(T, t);
-    AF[B.oAF + local] = v;
-    if (AF32) {
-      const int KC = (K + 3) & ~3;
-      float* row = AF32 + B.oAF32 + ((int64_t)n * B.M + m) * KC;
-      row[k] = (float)v;
-      if (k == K - 1)
-        for (int e = K; e < KC; ++e) row[e] = 0.f;
+    const double tn = B.t0 + (double)n * B.dT;
+    const int KC = (K + 3) & ~3;
+    double* af = AF + B.oAF + (int64_t)n * B.M * K + k;
+    float* row32 = AF32 ? AF32 + B.oAF32 + (int64_t)n * B.M * KC : nullptr;
+    auto put = [&](int m, double v) {
+      af[(int64_t)m * K] = v;
+      if (row32) {
+        float* row = row32 + (int64_t)m * KC;
+        row[k] = (float)v;
+        if (k == K - 1)
+          for (int e = K; e < KC; ++e) row[e] = 0.f;
+      }
+    };
+    if (T.tkind == PE_T_SIN) {
+      double sa, ca, sb, cb;
+      sincos(T.tp[0] * tn + T.tp[1], &sa, &ca);
+      sincos(T.tp[0] * B.dt, &sb, &cb);
+      for (int m = 0; m < B.M; ++m) {
+        put(m, T.amp * ((c & 1) ? ca : sa));
+        const double s2 = fma(sa, cb, ca * sb);
+        ca = fma(ca, cb, -(sa * sb));
+        sa = s2;
+      }
+    } else {
+      double e = exp(T.tp[0] * tn);
+      const double eb = exp(T.tp[0] * B.dt);
+      for (int m = 0; m < B.M; ++m) {
+        put(m, T.amp * e);
+        e *= eb;
+      }
     }
-  } else if (local < nf + ng) {
-    local -= nf;
+  } else if (local < nrow + ng) {
+    local -= nrow;
     int64_t rest = local;
     const int r = (int)(rest % R); rest /= R;
     const int i = (int)(rest % B.p); rest /= B.p;
@@ -157,7 +179,7 @@ __global__ void b_time_tables_kernel(const BProb* __restrict__ probs, const int6
     AG[B.oAG + local] = v;
     if (AG32) AG32[B.oAG + local] = (float)v;
   } else {
-    local -= nf + ng;
+    local -= nrow + ng;
     const int k = (int)(local % K), i = (int)(local / K);
     const int c = cols[B.oCol + k];
     const pe_term& T = terms[B.tf + (c >> 1)];
@@ -423,7 +445,9 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
               acc = fma(b[i], gi, acc);
             }
           }
-          double gn = (double)acc;
+          double gn;
+          if constexpr (sizeof(TF) == 4) gn = widen_f32(acc);  // exact, off the float64 pipe
+          else gn = acc;
           if constexpr (LEARN) {
             float dl = 0.f;
             const float2* ph = L.Ph + B.oPh + n0 + n;
@@ -433,7 +457,7 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
                 const float2 e = __ldg(ph + (int64_t)r * N);
                 dl = fmaf(LA[r], e.x, fmaf(LB[r], e.y, dl));
               }
-            gn += (double)dl;
+            gn += widen_f32(dl);
           }
           c = fma(E, c, gn);
           U[B.oU + (int64_t)(n0 + n + 1) * nd + J] = c;

@@ -238,7 +238,7 @@ extern "C" pe_status pe_setup_batch(pe_batch** out, int32_t n_problems, const pe
     mu_prefix.push_back(oMu);
     oMu += nsum;
     tt_prefix.push_back(tt);
-    tt += (int64_t)B.N * B.M * B.K + (int64_t)B.N * B.p * B.R + (int64_t)B.q * B.K;
+    tt += (int64_t)B.N * B.K + (int64_t)B.N * B.p * B.R + (int64_t)B.q * B.K;  // b_time_tables_kernel's threads
     B.oItems = oItems;
     B.nItems = (int)((ndof + 255) / 256);
     oItems += B.nItems;

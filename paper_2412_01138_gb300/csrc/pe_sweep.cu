@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(512) coarse_fused_kernel(Geom g, int N, int p,
       const float2* e = sCS + (int64_t)n * RB;
 #pragma unroll
       for (int r = 0; r < RB; ++r) dl = fmaf(LA[r], e[r].x, fmaf(LB[r], e[r].y, dl));
-      gn += (double)dl;
+      gn += widen_f32(dl);
     }
     c = fma(E, c, gn);
     U[(int64_t)(n + 1) * nd + J] = c;
