@@ -46,6 +46,43 @@ L2_BYTES = 129 * 1024 * 1024
 TC_MIN_DOF = 4096  # below this the split operand images cost more than the tensor cores save
 
 
+_FLUSH = None
+
+
+def timed_solves(s, steps, warmup, barrier, **kw):
+    """Mean device time (ms) of `steps` solves of one Solver and their reports: each solve is
+    enqueued with pe_solve_async between CUDA events on the current stream (the solver's), L2
+    flushed before each (a 258 MB write), the report read after the closing event."""
+    import torch
+
+    global _FLUSH
+    if _FLUSH is None:
+        _FLUSH = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        s.solve(**kw)
+    barrier()
+    total, infos = 0.0, []
+    for _ in range(steps):
+        _FLUSH.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve_async(**kw)
+        e1.record(stream)
+        infos.append(s.wait())
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    barrier()
+    return total / steps, infos
+
+
+def cur_stream():
+    import torch
+
+    return torch.cuda.current_stream()
+
+
 def chosen_kw(pe, prec, prob=None):
     """Solver options of a separable-path solve: the mixed form (the chosen form) runs its stage
     contraction on the tensor cores (on the CUDA cores for grids under TC_MIN_DOF nodes, which are
@@ -370,15 +407,9 @@ def run_config1(pe, args, barrier):
     out = {"workload": prob.label}
     for name, prec, tol in (("fp64_tol1e-12", pe.PE_FP64, 1e-12), ("fp64", pe.PE_FP64, TOL),
                             ("chosen", pe.PE_MIXED, TOL)):
-        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec, prob)) as s:
-            for _ in range(max(3, args.warmup)):
-                s.solve(tol=tol)
-            barrier()
-            t0 = time.perf_counter()
-            reps = max(10, args.steps)
-            infos = [s.solve(tol=tol) for _ in range(reps)]
-            barrier()
-            dt = (time.perf_counter() - t0) / reps
+        with pe.Solver(prob, precision=prec, stream=cur_stream(), **chosen_kw(pe, prec, prob)) as s:
+            ms, infos = timed_solves(s, max(10, args.steps), max(3, args.warmup), barrier, tol=tol)
+            dt = ms / 1e3
             modal = s.modal(prob.N)
         ref = osolver.parareal(sys_, tol=tol)
         out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"], "tol": tol,
@@ -403,7 +434,7 @@ def run_learned(pe, args, barrier):
     prob = I.config5(seed=1)
     dev = torch.device("cuda")
     out = {"workload": prob.label}
-    with pe.Solver(prob, precision=pe.PE_MIXED, **chosen_kw(pe, pe.PE_MIXED)) as s:
+    with pe.Solver(prob, precision=pe.PE_MIXED, stream=cur_stream(), **chosen_kw(pe, pe.PE_MIXED)) as s:
         lam = s.lam()
         lo, hi = np.log(lam.min()), np.log(lam.max())
         rng = np.random.default_rng(2024)
@@ -440,28 +471,17 @@ def run_learned(pe, args, barrier):
         res = {}
         for name, mlp in (("plain_G", None), ("learned_G", net)):
             s.set_learned(mlp)
-            for _ in range(max(1, args.warmup)):
-                s.solve(tol=TOL)
-            barrier()
-            t1 = time.perf_counter()
-            infos = [s.solve(tol=TOL) for _ in range(args.steps)]
-            barrier()
-            dt = (time.perf_counter() - t1) / args.steps
+            ms, infos = timed_solves(s, args.steps, max(1, args.warmup), barrier, tol=TOL)
+            dt = ms / 1e3
             modal = s.modal(prob.N)
             res[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
                          "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
                          "residual": infos[-1]["residual"], "modal": modal}
         s.set_learned(None)
     # the plain float64 form on the same workload (plain G, SIMT float64 fine kernel)
-    with pe.Solver(prob, precision=pe.PE_FP64) as s:
-        for _ in range(max(1, args.warmup)):
-            s.solve(tol=TOL)
-        barrier()
-        t1 = time.perf_counter()
-        steps = max(1, min(args.steps, 3))
-        infos = [s.solve(tol=TOL) for _ in range(steps)]
-        barrier()
-        dt = (time.perf_counter() - t1) / steps
+    with pe.Solver(prob, precision=pe.PE_FP64, stream=cur_stream()) as s:
+        ms, infos = timed_solves(s, max(1, min(args.steps, 3)), max(1, args.warmup), barrier, tol=TOL)
+        dt = ms / 1e3
         res["fp64_plain_G"] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
                                "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
                                "residual": infos[-1]["residual"], "modal": s.modal(prob.N)}
@@ -530,13 +550,9 @@ def run_precision(pe, args, barrier):
         return float(np.sqrt(np.sum(w * (m[idx] - ref.U[-1]) ** 2)) / np.sqrt(np.sum(w * ref.U[-1] ** 2)))
 
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec)) as s:
-            s.solve(tol=TOL)
-            barrier()
-            t0 = time.perf_counter()
-            infos = [s.solve(tol=TOL) for _ in range(steps)]
-            barrier()
-            dt = (time.perf_counter() - t0) / steps
+        with pe.Solver(prob, precision=prec, stream=cur_stream(), **chosen_kw(pe, prec)) as s:
+            ms, infos = timed_solves(s, steps, 1, barrier, tol=TOL)
+            dt = ms / 1e3
             rec = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
                    "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
                    "rel_l2_vs_oracle": rel(s.modal(prob.N))}
@@ -562,14 +578,10 @@ def run_cached(pe, args, barrier, u0_dev, u0_host):
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=17, u0_nodal=u0_host)
     w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, cache_forced=True, **chosen_kw(pe, prec)) as s:
-            for _ in range(max(1, args.warmup)):
-                s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
-            barrier()
-            t0 = time.perf_counter()
-            infos = [s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev) for _ in range(args.steps)]
-            barrier()
-            dt = (time.perf_counter() - t0) / args.steps
+        with pe.Solver(prob, precision=prec, cache_forced=True, stream=cur_stream(), **chosen_kw(pe, prec)) as s:
+            ms, infos = timed_solves(s, args.steps, max(1, args.warmup), barrier, tol=TOL,
+                                     u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
+            dt = ms / 1e3
             m = s.modal(prob.N)
         out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
                      "fine_sweeps_executed": infos[-1]["fine_sweeps"],
@@ -597,14 +609,9 @@ def run_dirichlet(pe, args, barrier):
     prob = dirichlet_problem()
     out = {"workload": prob.label}
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec)) as s:
-            for _ in range(max(1, args.warmup)):
-                s.solve(tol=TOL)
-            barrier()
-            t0 = time.perf_counter()
-            infos = [s.solve(tol=TOL) for _ in range(args.steps)]
-            barrier()
-            dt = (time.perf_counter() - t0) / args.steps
+        with pe.Solver(prob, precision=prec, stream=cur_stream(), **chosen_kw(pe, prec)) as s:
+            ms, infos = timed_solves(s, args.steps, max(1, args.warmup), barrier, tol=TOL)
+            dt = ms / 1e3
         out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
                      "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT}
     return out
@@ -627,14 +634,9 @@ def run_periodic(pe, args, barrier):
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=19)
     w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, **chosen_kw(pe, prec)) as s:
-            for _ in range(max(1, args.warmup)):
-                s.solve(tol=TOL)
-            barrier()
-            t0 = time.perf_counter()
-            infos = [s.solve(tol=TOL) for _ in range(args.steps)]
-            barrier()
-            dt = (time.perf_counter() - t0) / args.steps
+        with pe.Solver(prob, precision=prec, stream=cur_stream(), **chosen_kw(pe, prec)) as s:
+            ms, infos = timed_solves(s, args.steps, max(1, args.warmup), barrier, tol=TOL)
+            dt = ms / 1e3
             m = s.modal(prob.N)
         out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
                      "value": prob.ndof * prob.N * prob.M * infos[-1]["fine_sweeps"] / dt, "unit": UNIT,
@@ -698,15 +700,10 @@ def run_general(pe, args, barrier, u0_dev, u0_host):
     rate, dtc, nm, k_or, sys_, ref, idx = oracle_sample(prob, 1024, seed=23, u0_nodal=u0_host)
     w = sys_.norm_w
     for name, prec in (("fp64", pe.PE_FP64), ("mixed", pe.PE_MIXED)):
-        with pe.Solver(prob, precision=prec, forcing_path=pe.PE_FORCING_GENERAL) as s:
-            for _ in range(max(1, args.warmup)):
-                s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
-            barrier()
-            t1 = time.perf_counter()
-            steps = max(1, args.steps // 2)
-            infos = [s.solve(tol=TOL, u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev) for _ in range(steps)]
-            barrier()
-            dt = (time.perf_counter() - t1) / steps
+        with pe.Solver(prob, precision=prec, forcing_path=pe.PE_FORCING_GENERAL, stream=cur_stream()) as s:
+            ms, infos = timed_solves(s, max(1, args.steps // 2), max(1, args.warmup), barrier, tol=TOL,
+                                     u0_kind=pe.PE_FIELD_NODAL, nodal=u0_dev)
+            dt = ms / 1e3
             m = s.modal(prob.N)
         sweeps = infos[-1]["fine_sweeps"]
         out[name] = {"time_to_tol_ms": 1e3 * dt, "iterations": infos[-1]["k"],
