@@ -506,6 +506,16 @@ pe_status pe_measure_fma_peak(int32_t precision, double* tflops_out, void* strea
  */
 pe_status pe_probe_wait_timeout(int64_t budget_cycles, void* stream);
 
+/*
+ * pe_probe_widen_f32 -- y[i] = x[i] widened from float32 to float64 by the integer
+ * operations the mixed form's coarse sweeps use in place of the conversion instruction
+ * (normal values: exponent rebiased, fraction shifted; zero, subnormal, infinite and NaN
+ * values as the conversion gives them), for i < n; x (n floats) and y (n doubles) device
+ * memory, enqueued on stream.  A self-check of that step: the result equals the hardware
+ * conversion bit for bit.  PE_EINVAL for n < 0 or NULL buffers with n > 0.
+ */
+pe_status pe_probe_widen_f32(const float* x, double* y, int64_t n, void* stream);
+
 /* Most recent error message on this thread ("" if none). */
 const char* pe_last_error(void);
 

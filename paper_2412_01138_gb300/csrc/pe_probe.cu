@@ -9,7 +9,10 @@
 //                         instruction and no copy in flight), with a caller-given budget: the
 //                         wait gives up, the kernel records the expiry in a status word and
 //                         returns, and the host reports PE_ETIMEOUT exactly as it does for the
-//                         production kernels.
+//                         production kernels;
+//   pe_probe_widen_f32    the integer float32 -> float64 widening of the mixed form's coarse
+//                         sweeps applied to a caller's array, so that a test can compare it bit
+//                         for bit with the hardware conversion.
 #include <stdio.h>
 
 #include <algorithm>
@@ -98,6 +101,23 @@ extern "C" pe_status pe_measure_fma_peak(int32_t precision, double* tflops_out, 
   if (precision == PE_FP64) return fma_peak<double>(tflops_out, st);
   if (precision == PE_MIXED) return fma_peak<float>(tflops_out, st);
   return pe_fail(PE_EINVAL, "pe_measure_fma_peak: precision must be PE_FP64 or PE_MIXED (float32)");
+}
+
+namespace {
+__global__ void widen_probe_kernel(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = widen_f32(x[i]);
+}
+}  // namespace
+
+extern "C" pe_status pe_probe_widen_f32(const float* x, double* y, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return pe_fail(PE_EINVAL, "pe_probe_widen_f32: bad arguments");
+  if (n == 0) return PE_OK;
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > 0x7FFFFFFFLL) return pe_fail(PE_EINVAL, "pe_probe_widen_f32: n too large");
+  widen_probe_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  PE_CUDA_TRY(cudaGetLastError());
+  return PE_OK;
 }
 
 extern "C" pe_status pe_probe_wait_timeout(int64_t budget_cycles, void* stream) {

@@ -39,7 +39,7 @@ EXPORTED = ("pe_setup", "pe_set_problem", "pe_parareal_iter", "pe_refine", "pe_s
             "pe_mlp_forward", "pe_mlp_get_params", "pe_mlp_set_params", "pe_mlp_destroy", "pe_learned_samples",
             "pe_set_learned", "pe_dst_tc", "pe_dst_noalloc", "pe_set_dirichlet", "pe_measure_fma_peak",
             "pe_probe_wait_timeout", "pe_parareal_iter_sums", "pe_batch_set_learned", "pe_solve_out",
-            "pe_solve_async", "pe_solve_wait")
+            "pe_solve_async", "pe_solve_wait", "pe_probe_widen_f32")
 
 
 class PEError(RuntimeError):
@@ -152,6 +152,7 @@ def load_library(path: str = _LIB_PATH) -> C.CDLL:
         "pe_set_dirichlet": (C.c_int, [P, C.c_int32, P]),
         "pe_measure_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), P]),
         "pe_probe_wait_timeout": (C.c_int, [C.c_int64, P]),
+        "pe_probe_widen_f32": (C.c_int, [P, P, C.c_int64, P]),
         "pe_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -493,6 +494,16 @@ def probe_wait_timeout(budget_cycles: int, stream=None) -> None:
     """Run the tensor-core kernels' bounded wait on a barrier nothing arrives at (raises PEError
     with status PE_ETIMEOUT when the wait expires, which is what it is for)."""
     _check(lib().pe_probe_wait_timeout(int(budget_cycles), stream_handle(stream)))
+
+
+def probe_widen_f32(x, y, stream=None) -> None:
+    """y = x widened to float64 by the coarse sweeps' integer widening (float32 and float64 CUDA
+    tensors of equal length)."""
+    if not (getattr(x, "is_cuda", False) and getattr(y, "is_cuda", False)):
+        raise ValueError("probe_widen_f32: buffers must be CUDA tensors")
+    if str(x.dtype) != "torch.float32" or str(y.dtype) != "torch.float64" or y.numel() < x.numel():
+        raise ValueError("probe_widen_f32: x float32, y float64 with at least as many values")
+    _check(lib().pe_probe_widen_f32(_ptr(x), _ptr(y), int(x.numel()), stream_handle(stream)))
 
 
 class BatchSolver:

@@ -110,6 +110,9 @@ def test_measurement_calls_reject_bad_arguments_before_device_work(lib):
     for budget in (0, -5, 10**9):
         assert lib.pe_probe_wait_timeout(budget, None) == pe.PE_EINVAL
         assert "budget" in lib.pe_last_error().decode()
+    assert lib.pe_probe_widen_f32(None, None, -1, None) == pe.PE_EINVAL
+    assert lib.pe_probe_widen_f32(None, None, 4, None) == pe.PE_EINVAL
+    assert lib.pe_probe_widen_f32(None, None, 0, None) == pe.PE_OK
 
 
 def test_transform_wrappers_check_buffers_before_the_library_sees_them(lib):
