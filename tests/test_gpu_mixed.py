@@ -73,12 +73,19 @@ def test_float64_refinement_reaches_float64_parity(pe, which):
     ref = osolver.parareal(sys_, tol=0.0, k_max=2)
     with pe.Solver(prob, precision=pe.PE_MIXED) as s:
         s.solve(tol=1e-6)
-        before = max(_rel(s.modal(n), ref.U[n], sys_.norm_w) for n in range(1, prob.N + 1))
+        mixed = [s.modal(n) for n in range(1, prob.N + 1)]
+        before = max(_rel(m, ref.U[n + 1], sys_.norm_w) for n, m in enumerate(mixed))
         r = s.refine()
         after = max(_rel(s.modal(n), ref.U[n], sys_.norm_w) for n in range(1, prob.N + 1))
     assert 1e-12 < before <= TOL_MIXED
     assert after <= 1e-12
-    assert 0.0 < r <= TOL_MIXED  # the refinement's residual is the size of the mixed-precision error
+    # the refinement's residual measures the change it made, i.e. the mixed iterate's error over
+    # every slice (the refined iterate being the float64 one to 1e-12): the same number
+    w = sys_.norm_w
+    num = sum(float(np.sum(w * (m - ref.U[n + 1]) ** 2)) for n, m in enumerate(mixed))
+    den = sum(float(np.sum(w * ref.U[n] ** 2)) for n in range(1, prob.N + 1))
+    err_all = math.sqrt(num / den)
+    assert abs(r - err_all) <= 1e-3 * err_all, (r, err_all)
 
 
 def _term_mix(kinds, seed):
