@@ -372,8 +372,9 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
         for (int r = 0; r < kCoarseRB; ++r) {
           if (r < R && L.terms[B.tf + r].tkind == PE_T_SIN) {
             double Pd = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
-            for (int a = 1; a < B.g.d; ++a)
-              Pd *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+#pragma unroll
+            for (int a = 1; a < PE_MAX_D; ++a)
+              if (a < B.g.d) Pd *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
             const double* k0 = L.Kt + B.oKt + 2 * ((int64_t)r * L.NB + b0);
             const double Kre = (1.0 - f) * k0[0] + f * k0[2];
             const double Kim = (1.0 - f) * k0[1] + f * k0[3];
@@ -390,13 +391,15 @@ __global__ void __launch_bounds__(256) b_coarse_kernel(const BProb* __restrict__
         if (r < R) {
           if constexpr (sizeof(TF) == 4) {
             float v = axisF32[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
-            for (int a = 1; a < B.g.d; ++a)
-              v *= axisF32[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+#pragma unroll
+            for (int a = 1; a < PE_MAX_D; ++a)
+              if (a < B.g.d) v *= axisF32[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
             P[r] = v;
           } else {
             double v = axisF[B.oAx + (int64_t)R * B.g.off[0] + (int64_t)r * B.g.n[0] + j[0]];
-            for (int a = 1; a < B.g.d; ++a)
-              v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
+#pragma unroll
+            for (int a = 1; a < PE_MAX_D; ++a)
+              if (a < B.g.d) v *= axisF[B.oAx + (int64_t)R * B.g.off[a] + (int64_t)r * B.g.n[a] + j[a]];
             P[r] = (TF)v;
           }
         }
