@@ -143,3 +143,22 @@ def test_checkpoint_of_a_transposed_grid_is_rejected(pe):
     with pe.Solver(base) as s3:  # the same problem still loads
         s3.set_problem()
         s3.load_state(blob)
+
+
+@pytest.mark.parametrize("dl", [0, 1], ids=["host_loop", "device_loop"])
+def test_no_convergence_is_reported_by_the_wait_of_an_asynchronous_solve(pe, dl):
+    """The same stop through pe_solve_async / pe_solve_wait, with the loop on the host and on
+    the device: the wait returns PE_ENOCONV with k = 1 and the oracle's r_1, and the context
+    takes the next solve."""
+    prob = I.config1()
+    sys_ = osolver.ModalSystem(prob)
+    ref = osolver.parareal(sys_, tol=0.0, k_max=1)
+    with pe.Solver(prob, max_iter=1, device_loop=dl) as s:
+        for _ in range(2):
+            s.solve_async(tol=1e-14)
+            with pytest.raises(pe.PEError) as ei:
+                s.wait()
+            assert ei.value.status == pe.PE_ENOCONV
+            res = ei.value.result
+            assert res is not None and res["k"] == 1 and res["history"] == [res["residual"]]
+            assert res["residual"] == pytest.approx(ref.residuals[0], rel=1e-9)
