@@ -787,10 +787,13 @@ constexpr int half_tw_entries(int left, int ns, int logn) {
 
 // Fold (pre-processing), FFT and unfold (post-processing) of one pencil pair held in a:
 // on entry a[fpad(p)] = (x^a_p, x^b_p) for p = 1..N-1 and a[fpad(0)] = 0; on exit
-// a[fpad(m)] = (F^a_m, F^b_m) for m = 1..N-1 (unscaled sine sums).
+// a[fpad(m)] = (4 F^a_m, 4 F^b_m) for m = 1..N-1 (unscaled sine sums times four: the fold is
+// taken times two, y_j = (2s_j + 1) x_j + (2s_j - 1) x_{N-j} with s_j = sin(pi j / N), one
+// multiplication and one FMA per value from the table fold = (2s + 1, 2s - 1), and the unfold
+// without its halvings; the caller's scale carries the 1/4, a power of two).
 template <typename T, int LOGN>
 __device__ __forceinline__ void half_dst_pair(Cplx<T>* a, const Cplx<T>* __restrict__ ptw,
-                                              const T* __restrict__ sinN, int lane) {
+                                              const Cplx<T>* __restrict__ fold, int lane) {
   constexpr int N = 1 << LOGN, V = N / 32, C = N / 64;
   // fold
   Cplx<T> z[V];
@@ -799,8 +802,8 @@ __device__ __forceinline__ void half_dst_pair(Cplx<T>* a, const Cplx<T>* __restr
     const int j = lane + 32 * t;
     const Cplx<T> x = a[fpad(j)];
     const Cplx<T> xm = j == 0 ? Cplx<T>{T(0), T(0)} : a[fpad(N - j)];
-    const T s = __ldg(sinN + j);
-    z[t] = Cplx<T>{s * (x.re + xm.re) + T(0.5) * (x.re - xm.re), s * (x.im + xm.im) + T(0.5) * (x.im - xm.im)};
+    const Cplx<T> f = ldg_cplx(fold + j);
+    z[t] = Cplx<T>{fma(f.re, x.re, f.im * xm.re), fma(f.re, x.im, f.im * xm.im)};
   }
   __syncwarp();
 #pragma unroll
@@ -815,9 +818,9 @@ __device__ __forceinline__ void half_dst_pair(Cplx<T>* a, const Cplx<T>* __restr
     const int k = lane * C + c;
     const Cplx<T> Z = a[fpad(k)];
     const Cplx<T> Wm = a[fpad((N - k) & (N - 1))];
-    T ra = T(0.5) * (Z.re + Wm.re), rb = T(0.5) * (Z.im + Wm.im);
-    ia[c] = T(0.5) * (Wm.im - Z.im);
-    ib[c] = T(0.5) * (Z.re - Wm.re);
+    T ra = Z.re + Wm.re, rb = Z.im + Wm.im;
+    ia[c] = Wm.im - Z.im;
+    ib[c] = Z.re - Wm.re;
     if (k == 0) {
       ra *= T(0.5);
       rb *= T(0.5);
@@ -880,7 +883,7 @@ __device__ __forceinline__ void dht_pair(Cplx<T>* a, const Cplx<T>* __restrict__
 template <typename T, int LOGN, bool DHT = false>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
     dst_half_warp_kernel(const T* __restrict__ in, T* __restrict__ out, int n, int64_t inner, int64_t npencils,
-                         T scale, const Cplx<T>* __restrict__ ptw, const T* __restrict__ sinN) {
+                         T scale, const Cplx<T>* __restrict__ ptw, const Cplx<T>* __restrict__ fold) {
   constexpr int SH = DHT ? 0 : 1;  // buffer position of value j
   constexpr int N = 1 << LOGN, PADN = N + N / 16, PS = PADN + 1, JL = N / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -911,7 +914,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
       }
       __syncwarp();
       if constexpr (DHT) dht_pair<T, LOGN>(a, ptw, lane);
-      else half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
+      else half_dst_pair<T, LOGN>(a, ptw, fold, lane);
       T* ya = out + pa * n;
       T* yb = out + pb * n;
 #pragma unroll
@@ -953,7 +956,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LOGN <= 9) ? 2 : 1)
       stage_block_async(in, offs[cur ^ 1], P, logP, n, inner, stage);
     }
     if constexpr (DHT) dht_pair<T, LOGN>(a, ptw, lane);
-    else half_dst_pair<T, LOGN>(a, ptw, sinN, lane);
+    else half_dst_pair<T, LOGN>(a, ptw, fold, lane);
     __syncthreads();
     for (int e = tid; e < P * n; e += B) {
       const int pl = e & (P - 1), k = e >> logP;
@@ -1479,6 +1482,17 @@ __global__ void sin_table_kernel(int N, T* out) {
   if (j < N) out[j] = (T)sinpi((double)j / (double)N);
 }
 
+// (2 sin(pi j / N) + 1, 2 sin(pi j / N) - 1), j < N: the fold of the half-length form scaled by
+// two, y_j = (2s + 1) x_j + (2s - 1) x_{N-j}, one multiplication and one FMA per value
+template <typename T>
+__global__ void fold_table_kernel(int N, Cplx<T>* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N) {
+    const double s2 = 2.0 * sinpi((double)j / (double)N);
+    out[j] = Cplx<T>{(T)(s2 + 1.0), (T)(s2 - 1.0)};
+  }
+}
+
 // Device-resident tables (pass twiddles, the fold's sines), built once per device and length.
 template <typename T, int PLAN>
 const Cplx<T>* pass_twiddles(int logl, int total, cudaStream_t st) {
@@ -1501,6 +1515,31 @@ const Cplx<T>* pass_twiddles(int logl, int total, cudaStream_t st) {
     return nullptr;
   }
   table[dev][logl] = p;
+  return p;
+}
+
+template <typename T>
+const Cplx<T>* fold_pairs(int logn, cudaStream_t st) {
+  static Cplx<T>* table[64][12] = {};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || logn < 0 || logn > 11) return nullptr;
+  if (table[dev][logn]) return table[dev][logn];
+  const int N = 1 << logn;
+  Cplx<T>* p = nullptr;
+  if (cudaMalloc((void**)&p, sizeof(Cplx<T>) * (size_t)N) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  fold_table_kernel<T><<<(N + 255) / 256, 256, 0, st>>>(N, p);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+    return nullptr;
+  }
+  table[dev][logn] = p;
   return p;
 }
 
@@ -1591,16 +1630,16 @@ pe_status fft_half_launch(const T* in, T* out, int n, int64_t inner, int64_t npe
   constexpr int N = 1 << LOGN, PADN = N + N / 16;
   constexpr int NTW = half_tw_entries<T>(LOGN, 1, LOGN);
   const Cplx<T>* ptw = pass_twiddles<T, kPlanHalf>(LOGN, NTW, st);
-  const T* sinN = half_sines<T>(LOGN, st);
-  if (!ptw || !sinN) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
+  const Cplx<T>* fold = fold_pairs<T>(LOGN, st);
+  if (!ptw || !fold) return pe_fail(PE_ECUDA, "dst: twiddle table allocation failed");
   auto kern = dst_half_warp_kernel<T, LOGN>;
   int warps = 1;
   size_t smem = 0;
   int64_t grid = 1;
   PE_TRY(fft_grid<T>((const void*)kern, npencils, sizeof(Cplx<T>) * (PADN + 1), inner > 1 ? sizeof(T) * n : 0, &warps,
                      &smem, &grid));
-  const T scale = (T)sqrt(2.0 / (double)N);
-  kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, ptw, sinN);
+  const T scale = (T)(0.25 * sqrt(2.0 / (double)N));  // half_dst_pair leaves the sums times four
+  kern<<<(unsigned)grid, warps * 32, smem, st>>>(in, out, n, inner, npencils, scale, ptw, fold);
   PE_CUDA_TRY(cudaGetLastError());
   return PE_OK;
 }
