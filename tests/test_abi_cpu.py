@@ -127,3 +127,19 @@ def test_transform_wrappers_check_buffers_before_the_library_sees_them(lib):
             fn(2, (8, 8), host, host, **kw)
     with pytest.raises(ValueError):
         pe.dst(2, (8,), host, host)  # len(n) != d
+
+
+def test_solver_output_buffers_are_checked_in_the_binding():
+    """pe_solve_out / pe_solve_async receive only float64 buffers of at least ndof values (host
+    arrays here; device tensors take the same checks), checked before any call."""
+    import numpy as np
+
+    from paper_2412_01138_gb300 import pe
+
+    pe._check_out(np.empty(10), 10)
+    pe._check_out(np.empty(12), 10)
+    for bad in (np.empty(9), np.empty(10, dtype=np.float32), np.empty(10, dtype=np.int64)):
+        with pytest.raises(ValueError):
+            pe._check_out(bad, 10)
+    with pytest.raises(TypeError):
+        pe._check_out([0.0] * 10, 10)
